@@ -1,0 +1,188 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds no arithmetic of the multigrid method: it only draws random
+coefficients and evaluates manufactured data at the points where the library's
+interface expects them.
+
+Input layouts (the library interface):
+  log_kappa [E]                     per-element log-diffusivity, e = j*n + i
+  f         [nrhs][(p+1)^2][E]      forcing at the tensor Gauss-Legendre nodes
+                                    of each element, node (a, b) at b*(p+1)+a
+  g_D       [nrhs][p+1][n_edges]    orthonormal-Legendre coefficients of the
+                                    Dirichlet data on boundary edges (entries on
+                                    interior edges are ignored)
+
+Workloads (paper: arXiv:1811.09909):
+  * ``poisson_sine``  : -lap u = f, u = sin(pi x) sin(pi y), kappa = 1, g_D = 0
+    (16 x 16, p = 2, tau = 1 for the 3-level V(1,1)-CG configuration).
+  * ``example1``      : Example I of Sec. 4.1, u = x y exp(x^2 y^3) with its
+    Dirichlet data, kappa = 1.
+  * ``lognormal``     : log kappa iid N(0, sigma^2) per element (seeded), f = 1,
+    g_D = 0 -- the synthetic stand-in for the heterogeneous permeability of
+    Example V (SPE10 layer 75, a dataset that is not used here).
+  * ``checkerboard``  : Example IV's two-block kappa in {1e6, 1}, f = 1, g_D = 0.
+"""
+import math
+
+import numpy as np
+from numpy.polynomial import legendre as npleg
+
+
+def n_edges(n):
+    return 2 * n * (n + 1)
+
+
+def gauss_nodes(p):
+    x, _ = npleg.leggauss(p + 1)
+    return x
+
+
+def nodal(fun, n, p, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+    """Evaluate fun(x, y) at the Gauss-Legendre nodes of every element.
+
+    Returns [(p+1)^2][n*n] float64."""
+    xi = gauss_nodes(p)
+    p1 = p + 1
+    hx = (x1 - x0) / n
+    hy = (y1 - y0) / n
+    e = np.arange(n * n)
+    j, i = np.divmod(e, n)
+    a = np.arange(p1 * p1) % p1
+    b = np.arange(p1 * p1) // p1
+    X = x0 + (i[None, :] + 0.5) * hx + 0.5 * hx * xi[a][:, None]
+    Y = y0 + (j[None, :] + 0.5) * hy + 0.5 * hy * xi[b][:, None]
+    return np.ascontiguousarray(fun(X, Y), dtype=np.float64)
+
+
+def dirichlet(fun, n, p, x0=0.0, x1=1.0, y0=0.0, y1=1.0, nq=None):
+    """Orthonormal-Legendre coefficients of fun on every boundary edge.
+
+    Returns [p+1][n_edges] float64 (zero on interior edges)."""
+    nq = nq if nq is not None else p + 8
+    s, w = npleg.leggauss(nq)
+    hx = (x1 - x0) / n
+    hy = (y1 - y0) / n
+    P = np.stack([npleg.legval(s, np.eye(p + 1)[k]) for k in range(p + 1)])
+    out = np.zeros((p + 1, n_edges(n)))
+    nvert = n * (n + 1)
+
+    def coeffs(xs, ys, length):
+        vals = fun(xs, ys)
+        scale = np.sqrt((2.0 * np.arange(p + 1) + 1.0) / length)
+        return (P * scale[:, None]) @ (w * vals) * (length / 2.0)
+
+    for j in range(n):
+        yc = y0 + (j + 0.5) * hy + 0.5 * hy * s
+        for i in (0, n):
+            xc = np.full_like(s, x0 + i * hx)
+            out[:, j * (n + 1) + i] = coeffs(xc, yc, hy)
+    for jj in (0, n):
+        for i in range(n):
+            xc = x0 + (i + 0.5) * hx + 0.5 * hx * s
+            yc = np.full_like(s, y0 + jj * hy)
+            out[:, nvert + jj * n + i] = coeffs(xc, yc, hx)
+    return out
+
+
+# --------------------------------------------------------------------------
+# manufactured solutions
+# --------------------------------------------------------------------------
+def sine_u(x, y):
+    return np.sin(np.pi * x) * np.sin(np.pi * y)
+
+
+def sine_f(x, y):
+    return 2.0 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+
+
+def sine_q(x, y):
+    """q = -grad u for kappa = 1."""
+    return (-np.pi * np.cos(np.pi * x) * np.sin(np.pi * y),
+            -np.pi * np.sin(np.pi * x) * np.cos(np.pi * y))
+
+
+def ex1_u(x, y):
+    """Example I exact solution u = x y exp(x^2 y^3)."""
+    return x * y * np.exp(x ** 2 * y ** 3)
+
+
+def ex1_f(x, y):
+    """-lap u for u = x y exp(x^2 y^3) (derivatives worked by hand)."""
+    E = np.exp(x ** 2 * y ** 3)
+    return -E * (6 * x * y ** 4 + 4 * x ** 3 * y ** 7 + 12 * x ** 3 * y ** 2 + 9 * x ** 5 * y ** 5)
+
+
+def ex1_q(x, y):
+    E = np.exp(x ** 2 * y ** 3)
+    return (-y * E * (1 + 2 * x ** 2 * y ** 3), -x * E * (1 + 3 * x ** 2 * y ** 3))
+
+
+# --------------------------------------------------------------------------
+# configurations
+# --------------------------------------------------------------------------
+class Workload:
+    """One synthetic problem: mesh size, order, coefficients and data."""
+
+    def __init__(self, name, n, p, log_kappa, f, gD, tau_mode, tau_c,
+                 x0=0.0, x1=1.0, y0=0.0, y1=1.0, seed=None):
+        self.name = name
+        self.n, self.p = n, p
+        self.log_kappa = np.ascontiguousarray(log_kappa, dtype=np.float64)
+        self.f = np.ascontiguousarray(f, dtype=np.float64)
+        self.gD = np.ascontiguousarray(gD, dtype=np.float64)
+        self.tau_mode, self.tau_c = tau_mode, tau_c
+        self.x0, self.x1, self.y0, self.y1 = x0, x1, y0, y1
+        self.seed = seed
+
+    @property
+    def E(self):
+        return self.n * self.n
+
+    @property
+    def interior_trace_dofs(self):
+        return 2 * self.n * (self.n - 1) * (self.p + 1)
+
+    def tau(self):
+        """tau per element as the library computes it (TAU_CONST or c/h_min)."""
+        h = min((self.x1 - self.x0) / self.n, (self.y1 - self.y0) / self.n)
+        return self.tau_c if self.tau_mode == "const" else self.tau_c / h
+
+
+def poisson_sine(n=16, p=2, tau_mode="const", tau_c=1.0):
+    f = nodal(sine_f, n, p)[None]
+    gD = np.zeros((1, p + 1, n_edges(n)))
+    return Workload(f"poisson_sine_{n}_p{p}", n, p, np.zeros(n * n), f, gD, tau_mode, tau_c)
+
+
+def example1(n, p, tau_mode="over_h", tau_c=1.0):
+    f = nodal(ex1_f, n, p)[None]
+    gD = dirichlet(ex1_u, n, p)[None]
+    return Workload(f"example1_{n}_p{p}", n, p, np.zeros(n * n), f, gD, tau_mode, tau_c)
+
+
+def lognormal(n=256, p=4, sigma=1.0, seed=2, tau_mode="over_h", tau_c=1.0, nrhs=1):
+    rng = np.random.default_rng(seed)
+    logk = rng.normal(0.0, sigma, size=n * n)
+    f = np.ones((nrhs, (p + 1) ** 2, n * n))
+    gD = np.zeros((nrhs, p + 1, n_edges(n)))
+    return Workload(f"lognormal_{n}_p{p}_s{seed}", n, p, logk, f, gD, tau_mode, tau_c, seed=seed)
+
+
+def checkerboard(n, p, tau_mode="over_h", tau_c=1.0):
+    """Example IV: kappa = 1e6 on (0,0.56)^2 and (0.56,1)^2, else 1.
+
+    Element centres decide the block."""
+    j, i = np.divmod(np.arange(n * n), n)
+    xc = (i + 0.5) / n
+    yc = (j + 0.5) / n
+    hi = ((xc < 0.56) & (yc < 0.56)) | ((xc > 0.56) & (yc > 0.56))
+    logk = np.where(hi, math.log(1e6), 0.0)
+    f = np.ones((1, (p + 1) ** 2, n * n))
+    gD = np.zeros((1, p + 1, n_edges(n)))
+    return Workload(f"checkerboard_{n}_p{p}", n, p, logk, f, gD, tau_mode, tau_c)
+
+
+def random_vectors(n, nd, count, seed):
+    """Seeded N(0,1) trace vectors [count][nd][n_edges] (for operator checks)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((count, nd, n_edges(n)))
