@@ -1,0 +1,188 @@
+/*
+ * hdgmg.h -- C ABI of a GB300 (sm_103a) library for the hybridized DG trace
+ * system and its DtN-based geometric multigrid (Wildey, Muralikrishnan,
+ * Bui-Thanh, "Unified geometric multigrid algorithm for hybridized high-order
+ * finite element methods", arXiv:1811.09909).
+ *
+ * Problem (Sec. 2, eq. primal_elliptic / mixed_elliptic, K = kappa I):
+ *     -div(kappa grad u) = f in Omega = [x0,x1] x [y0,y1],  u = g_D on dOmega,
+ * discretised by HDG (eqs. HDG_local1, HDG_local2, HDG_flux, conservation)
+ * on a uniform n x n mesh of rectangles, volume space Q_p (tensor Lagrange at
+ * the (p+1)^2 Gauss-Legendre nodes), trace space P_p per edge in the
+ * L2-orthonormal Legendre basis.  Static condensation gives the trace system
+ * A lambda = g of Sec. 3 (eq. trace_linear_system), solved by a Krylov method
+ * preconditioned with the V-cycle of Algorithm 1 (p-coarsening to P_1, Sec.
+ * 3.1.1, then 2x2 agglomeration, Sec. 3.1.2, transfers eqs. n_1_Ik / n_1_Qk,
+ * Galerkin coarse operators eq. coarse, edge block-Jacobi smoothing and the
+ * local correction eq. localCorrection); u and q are then recovered element
+ * by element.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  element   e = j*n + i           (i along x, j along y)
+ *  edges     vertical edge at x_i, row j:   j*(n+1) + i        (i = 0..n)
+ *            horizontal edge at y_j, col i: n*(n+1) + j*n + i  (j = 0..n)
+ *            n_edges = 2 n (n+1); edges with i in {0,n} (vertical) or j in
+ *            {0,n} (horizontal) are Dirichlet edges.
+ *  traces    [mode][edge], mode k = 0..p of psi_k = sqrt((2k+1)/|e|) P_k(s),
+ *            s running along +x on horizontal and +y on vertical edges.
+ *  volume    [node][e], node (a,b) -> b*(p+1)+a at the Gauss-Legendre points
+ *            (a along x).  Flux q: [2][node][e], component x first.
+ *  q         is the flux q = -kappa grad u (the paper writes u for the flux
+ *            and q for the scalar; this interface uses the HDG convention).
+ *
+ * Memory: every pointer argument marked "device" is a CUDA device pointer on
+ * the context's device, owned by the caller, 8-byte aligned; "host" pointers
+ * are ordinary host memory owned by the caller.  The library owns the level
+ * hierarchy and its workspace (allocated in hdgmg_create, released in
+ * hdgmg_destroy).  All work is issued on the stream given to hdgmg_create;
+ * calls return after their work is complete on that stream unless stated.
+ *
+ * Errors: every call returns an hdgmg_status; 0 is success, negative values
+ * are errors, and hdgmg_last_error() returns a thread-local message for the
+ * last failure.  No call aborts or exits the process.
+ */
+#ifndef HDGMG_H
+#define HDGMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HDGMG_OK = 0,
+  HDGMG_EINVAL = -1,      /* invalid argument or unsupported size          */
+  HDGMG_ENOMEM = -2,      /* device allocation failed                      */
+  HDGMG_ECUDA = -3,       /* CUDA runtime error                            */
+  HDGMG_ENOCONV = -4,     /* max_it reached; best iterate and info written */
+  HDGMG_EBREAKDOWN = -5,  /* non-positive pivot, NaN/Inf in the iteration  */
+  HDGMG_ETIMEOUT = -6     /* a bounded device wait expired                 */
+} hdgmg_status;
+
+enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min */
+enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
+enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1 };
+enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1 };
+
+typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
+
+/* Problem statement (Sec. 2).  n must be a multiple of 2^L so that the mesh
+ * halves down to opts.coarsest_n; 1 <= p <= 8. */
+typedef struct {
+  int32_t n;              /* elements per side                               */
+  int32_t p;              /* polynomial order                                */
+  double x0, x1, y0, y1;  /* domain                                          */
+  int32_t tau_mode;       /* HDGMG_TAU_CONST or HDGMG_TAU_OVER_H (Sec. 4.1)  */
+  double tau_c;           /* the constant c                                  */
+} hdgmg_problem;
+
+/* Solver options.  hdgmg_default_opts() fills the documented defaults. */
+typedef struct {
+  int32_t coarsest_n;     /* agglomerate until n <= coarsest_n (>= 2); 2     */
+  int32_t m_fine;         /* smoothing steps m_N on the finest level; 1      */
+  int32_t m_growth;       /* m_{k-1} = m_growth * m_k (Sec. 3.3, beta); 2    */
+  int32_t m_max;          /* cap on m_k (0 = none); 0                        */
+  int32_t local_corr;     /* HDGMG_LC_*: step 3 / steps 3+5 of Alg. 1; BOTH  */
+  double omega;           /* block-Jacobi damping (1 = paper, undamped); 1   */
+  int32_t krylov;         /* NONE = MG as fixed-point solver, CG; CG         */
+  int32_t max_it;         /* outer iterations; 200                           */
+  double rtol;            /* ||g - A lambda||_2 / ||g||_2 target; 1e-10      */
+  int32_t precision;      /* V-cycle arithmetic: FP64 or FP32; FP64          */
+} hdgmg_opts;
+
+typedef struct {
+  int32_t iters;          /* outer iterations = V-cycle applications        */
+  int32_t converged;      /* 1 if rel_res <= rtol                            */
+  double rel_res;         /* ||g - A lambda|| / ||g||, recomputed in FP64    */
+  double t_setup_ms;      /* device time of the last hdgmg_setup             */
+  double t_solve_ms;      /* device time of the last hdgmg_solve             */
+  int32_t n_levels;
+  int64_t trace_dofs;     /* interior trace unknowns 2 n (n-1) (p+1)         */
+} hdgmg_info;
+
+void hdgmg_default_opts(hdgmg_opts* opts);
+
+/* Create a context for one problem: validates sizes, builds the reference
+ * element tables on the host and allocates every device buffer of the
+ * hierarchy on the current device.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  On error *ctx is NULL. */
+hdgmg_status hdgmg_create(hdgmg_ctx** ctx, const hdgmg_problem* problem,
+                          const hdgmg_opts* opts, void* stream);
+
+/* Set-up (Sec. 2 static condensation; Sec. 3.1-3.2 hierarchy):
+ *   log_kappa  device, [n*n] FP64, per-element log-diffusivity.
+ * Runs element condensation (local Cholesky of the u-Schur complement of the
+ * volume block), the edge block-Jacobi inverses, p-coarsening, every 2x2
+ * agglomeration level and the dense Cholesky factorisation of the coarsest
+ * operator.  EBREAKDOWN if a local pivot is not positive (e.g. kappa NaN). */
+hdgmg_status hdgmg_setup(hdgmg_ctx* ctx, const double* log_kappa);
+
+/* Solve (Sec. 2-3) for nrhs right-hand sides, one after another:
+ *   f       device, [nrhs][(p+1)^2][n*n] FP64 forcing at the Gauss nodes
+ *   g_D     device, [nrhs][p+1][n_edges] FP64 Dirichlet trace coefficients
+ *           (entries on interior edges are ignored), or NULL for g_D = 0
+ *   lambda  device, [nrhs][p+1][n_edges] FP64 out (boundary entries = g_D)
+ *   u       device, [nrhs][(p+1)^2][n*n] FP64 out, or NULL
+ *   q       device, [nrhs][2][(p+1)^2][n*n] FP64 out, or NULL
+ *   info    host, out (may be NULL); describes the last right-hand side.
+ * Requires a prior hdgmg_setup.  ENOCONV still writes the last iterate. */
+hdgmg_status hdgmg_solve(hdgmg_ctx* ctx, int32_t nrhs, const double* f,
+                         const double* g_D, double* lambda, double* u,
+                         double* q, hdgmg_info* info);
+
+/* End-to-end call on HOST buffers: copies log_kappa, f, g_D to the device,
+ * runs hdgmg_setup and hdgmg_solve for one right-hand side, copies lambda,
+ * u, q back.  Same layouts as above; every pointer is host memory (pinned
+ * memory gives asynchronous copies); g_D may be NULL. */
+hdgmg_status hdgmg_run_host(hdgmg_ctx* ctx, const double* log_kappa,
+                            const double* f, const double* g_D,
+                            double* lambda, double* u, double* q,
+                            hdgmg_info* info);
+
+/* ---- inspection entry points (used by the parity tests) ---------------- */
+
+/* Number of levels (finest = 0) and the shape of level k: macro-elements per
+ * side *n and trace modes per edge *nd (p+1 on level 0, 2 below). */
+hdgmg_status hdgmg_num_levels(hdgmg_ctx* ctx, int32_t* n_levels);
+hdgmg_status hdgmg_level_shape(hdgmg_ctx* ctx, int32_t level, int32_t* n,
+                               int32_t* nd);
+
+/* Copy the per-element operators of level k (Sec. 3: A_e on level 0, the
+ * Galerkin macro-element operators of eqs. ANm1 / Akm1 below) as full
+ * matrices: out device, [4nd][4nd][n*n] FP64, local order (edge, mode) with
+ * edges left, right, bottom, top.  Levels below 0 are held in the V-cycle
+ * precision and widened to FP64. */
+hdgmg_status hdgmg_copy_element_matrices(hdgmg_ctx* ctx, int32_t level,
+                                         double* out);
+
+/* y = A_k x on level k (eq. trace_partition's A_k restricted to interior
+ * edges): x, y device, [nd][n_edges(level)] FP64; Dirichlet entries of x are
+ * treated as zero and those of y are set to zero.  Level 0 uses the FP64
+ * operator; other levels the V-cycle precision. */
+hdgmg_status hdgmg_apply_operator(hdgmg_ctx* ctx, int32_t level,
+                                  const double* x, double* y);
+
+/* e = B_N r: one V-cycle of Algorithm 1 on the finest level, in the V-cycle
+ * precision; r, e device, [p+1][n_edges] FP64 (Dirichlet entries ignored /
+ * zero). */
+hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* ctx, const double* r, double* e);
+
+/* The condensed right-hand side b = sum_e g_e - A lambda_D on interior
+ * edges (Sec. 2; Dirichlet data applied strongly): f, g_D as in hdgmg_solve
+ * (one right-hand side), b device [p+1][n_edges] FP64 out. */
+hdgmg_status hdgmg_condensed_rhs(hdgmg_ctx* ctx, const double* f,
+                                 const double* g_D, double* b);
+
+/* Thread-local description of the last error ("" if none). */
+const char* hdgmg_last_error(void);
+
+/* Release every device buffer of the context.  NULL is accepted. */
+void hdgmg_destroy(hdgmg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDGMG_H */

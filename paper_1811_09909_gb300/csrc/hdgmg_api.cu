@@ -1,0 +1,666 @@
+// C ABI of the hdgmg library: context, set-up, V-cycle, outer Krylov
+// iteration, recovery (arXiv:1811.09909, Sec. 2-3; see include/hdgmg.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace hdgmg;
+
+namespace {
+thread_local std::string g_last_error;
+
+hdgmg_status fail(hdgmg_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                    \
+  do {                                                                                    \
+    cudaError_t err__ = (call);                                                           \
+    if (err__ != cudaSuccess)                                                             \
+      return fail(err__ == cudaErrorMemoryAllocation ? HDGMG_ENOMEM : HDGMG_ECUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(err__));                 \
+  } while (0)
+
+#define STATUS_TRY(call)                  \
+  do {                                    \
+    hdgmg_status st__ = (call);           \
+    if (st__ != HDGMG_OK) return st__;    \
+  } while (0)
+}  // namespace
+
+struct hdgmg_ctx {
+  hdgmg_problem prob{};
+  hdgmg_opts opts{};
+  cudaStream_t stream = nullptr;
+  double hx = 0, hy = 0, hmin = 0;
+  int p = 0, n = 0, nv = 0, nt = 0;
+  RefElement ref;
+  RefDevice refd{};
+  std::vector<void*> allocs;
+  std::vector<Level> levels;
+  double* logk = nullptr;
+  double* Lfac = nullptr;
+  int* err = nullptr;
+  int* err_h = nullptr;
+  // coarsest level
+  int* freeidx = nullptr;
+  int nf = 0;
+  double* dense = nullptr;
+  double* cwork = nullptr;
+  // outer Krylov vectors (finest level, FP64)
+  double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *b = nullptr;
+  double *lam = nullptr, *partial = nullptr, *scal = nullptr, *scal_h = nullptr;
+  // host-call staging
+  double *st_f = nullptr, *st_g = nullptr, *st_l = nullptr, *st_u = nullptr, *st_q = nullptr;
+  bool setup_done = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double t_setup_ms = 0.0;
+
+  template <typename T>
+  cudaError_t alloc(T** p_, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) {
+      allocs.push_back(q);
+      *p_ = (T*)q;
+    }
+    return e;
+  }
+  int64_t fine_len() const { return (int64_t)(p + 1) * 2 * n * (n + 1); }
+};
+
+namespace {
+
+template <typename T> LevelData<T>& ld(Level& L);
+template <> LevelData<double>& ld<double>(Level& L) { return L.d64; }
+template <> LevelData<float>& ld<float>(Level& L) { return L.d32; }
+
+hdgmg_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(HDGMG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return HDGMG_OK;
+}
+
+// ----------------------------------------------------------- V-cycle (Alg. 1)
+template <typename T>
+void vcycle(hdgmg_ctx* c, int l) {
+  cudaStream_t s = c->stream;
+  Level& L = c->levels[l];
+  LevelData<T>& D = ld<T>(L);
+  const int last = (int)c->levels.size() - 1;
+  if (l == last) {                                          // B_1 = A_1^-1
+    launch_coarse_solve<T>(s, L.n, c->freeidx, c->nf, c->dense, D.r, D.e, c->cwork);
+    return;
+  }
+  const T omega = (T)c->opts.omega;
+  const int lc = c->opts.local_corr;
+  // step 2: pre-smoothing (the first sweep starts from e = 0)
+  launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 1);
+  for (int i = 1; i < L.m; ++i) {
+    launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
+    launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 0);
+  }
+  // step 3: local correction (interior edges of the next level's macro-elements)
+  if (L.transfer == 2 && lc != HDGMG_LC_NONE)
+    launch_local_correction<T>(s, L.n / 2, D.AIIinv, D.Y, D.r, D.e);
+  // step 4: coarse-grid correction
+  Level& Lc = c->levels[l + 1];
+  LevelData<T>& Dc = ld<T>(Lc);
+  launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
+  if (L.transfer == 1)
+    launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
+  else
+    launch_restrict_h<T>(s, Lc.n, D.Pi, D.r, D.y, Dc.r);
+  vcycle<T>(c, l + 1);
+  if (L.transfer == 1)
+    launch_prolong_p<T>(s, L.n, L.nd, Dc.e, D.e);
+  else
+    launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y);
+  // step 5: second local correction (symmetric cycle)
+  if (L.transfer == 2 && lc == HDGMG_LC_BOTH)
+    launch_local_correction<T>(s, L.n / 2, D.AIIinv, D.Y, D.r, D.e);
+  // step 6: post-smoothing
+  for (int i = 0; i < L.m; ++i) {
+    launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
+    launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 0);
+  }
+}
+
+// z = B_N r on FP64 fine vectors
+void apply_B(hdgmg_ctx* c, const double* r, double* z) {
+  cudaStream_t s = c->stream;
+  Level& L0 = c->levels[0];
+  const int64_t len = c->fine_len();
+  if (c->opts.precision == HDGMG_PREC_FP32) {
+    launch_convert<double, float>(s, len, r, L0.d32.r);
+    vcycle<float>(c, 0);
+    launch_convert<float, double>(s, len, L0.d32.e, z);
+  } else {
+    cudaMemcpyAsync(L0.d64.r, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    vcycle<double>(c, 0);
+    cudaMemcpyAsync(z, L0.d64.e, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+  }
+}
+
+// y = A_fine x (FP64, interior rows), y overwritten
+void apply_A64(hdgmg_ctx* c, const double* x, double* y) {
+  cudaMemsetAsync(y, 0, sizeof(double) * c->fine_len(), c->stream);
+  launch_matvec<double>(c->stream, c->n, c->p + 1, c->levels[0].d64.A, x, y, 1.0);
+}
+
+double dot_sync(hdgmg_ctx* c, const double* a, const double* b) {
+  launch_dot(c->stream, c->fine_len(), a, b, c->partial, c->scal + 5);
+  cudaMemcpyAsync(c->scal_h + 5, c->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return c->scal_h[5];
+}
+
+template <typename T>
+hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
+  LevelData<T>& D = ld<T>(L);
+  (void)vec_only_fine;
+  CUDA_TRY(c->alloc(&D.A, (size_t)L.nsym * L.nE));
+  CUDA_TRY(c->alloc(&D.Dinv, (size_t)(L.nd * (L.nd + 1) / 2) * L.nEdge));
+  CUDA_TRY(c->alloc(&D.r, (size_t)L.nd * L.nEdge));
+  CUDA_TRY(c->alloc(&D.e, (size_t)L.nd * L.nEdge));
+  CUDA_TRY(c->alloc(&D.y, (size_t)L.nd * L.nEdge));
+  CUDA_TRY(cudaMemset(D.y, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+  CUDA_TRY(cudaMemset(D.r, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+  CUDA_TRY(cudaMemset(D.e, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+  if (L.transfer == 2) {
+    const size_t nC = (size_t)L.nE / 4;
+    CUDA_TRY(c->alloc(&D.AIIinv, 36 * nC));
+    CUDA_TRY(c->alloc(&D.Y, 128 * nC));
+    CUDA_TRY(c->alloc(&D.Pi, 64 * nC));
+  }
+  return HDGMG_OK;
+}
+
+template <typename T>
+hdgmg_status setup_hierarchy(hdgmg_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int nl = (int)c->levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = c->levels[l];
+    Level& Lc = c->levels[l + 1];
+    LevelData<T>& D = ld<T>(L);
+    LevelData<T>& Dc = ld<T>(Lc);
+    launch_bj_blocks<T>(s, L.n, L.nd, D.A, D.Dinv, c->err);
+    if (L.transfer == 1)
+      launch_pcoarsen<T>(s, L.nE, L.nd, D.A, Dc.A);
+    else
+      launch_agglomerate<T>(s, Lc.n, D.A, Dc.A, D.AIIinv, D.Y, D.Pi, c->err);
+  }
+  Level& Lc = c->levels[nl - 1];
+  launch_coarse_assemble<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
+  launch_coarse_factor(s, c->nf, c->dense, c->err);
+  return check_launch("hierarchy set-up");
+}
+
+hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  CUDA_TRY(cudaMemsetAsync(c->b, 0, sizeof(double) * len, s));
+  launch_rhs(s, c->refd, c->p, c->n, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
+             f, c->b);
+  launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
+  if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->lam, c->b, -1.0);
+  return check_launch("condensed right-hand side");
+}
+
+hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* lam_out,
+                       double* u, double* q, hdgmg_info* info) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const hdgmg_opts& o = c->opts;
+  STATUS_TRY(build_rhs(c, f, gD));
+  CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * len, s));
+  const double bb = dot_sync(c, c->b, c->b);
+  const double nb = std::sqrt(bb);
+  int it = 0;
+  double rel = 0.0;
+  bool conv = true, breakdown = false;
+  if (!(nb > 0.0)) {
+    conv = true;
+    if (!std::isfinite(bb)) breakdown = true;
+  } else if (o.krylov == HDGMG_KRYLOV_CG) {
+    // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle)
+    CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    apply_B(c, c->r, c->z);
+    CUDA_TRY(cudaMemcpyAsync(c->pv, c->z, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_dot(s, len, c->r, c->z, c->partial, c->scal + 0);
+    conv = false;
+    for (it = 1; it <= o.max_it; ++it) {
+      apply_A64(c, c->pv, c->Ap);
+      launch_dot(s, len, c->pv, c->Ap, c->partial, c->scal + 1);
+      launch_cg_scalars(s, c->scal, 0);
+      launch_cg_update(s, len, c->scal, c->x, c->r, c->pv, c->Ap);
+      const double rr = dot_sync(c, c->r, c->r);
+      rel = std::sqrt(rr) / nb;
+      if (!std::isfinite(rr)) { breakdown = true; break; }
+      if (rel <= o.rtol) { conv = true; break; }
+      apply_B(c, c->r, c->z);
+      launch_dot(s, len, c->r, c->z, c->partial, c->scal + 3);
+      launch_cg_scalars(s, c->scal, 1);
+      launch_cg_direction(s, len, c->scal, c->z, c->pv);
+    }
+    if (it > o.max_it) it = o.max_it;
+  } else {
+    // multigrid as a fixed-point solver: x <- x + B_N (b - A x)  (Sec. 3.6)
+    conv = false;
+    for (it = 1; it <= o.max_it; ++it) {
+      apply_A64(c, c->x, c->Ap);
+      CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+      launch_axpby(s, len, -1.0, c->Ap, 1.0, c->r);
+      const double rr = dot_sync(c, c->r, c->r);
+      rel = std::sqrt(rr) / nb;
+      if (!std::isfinite(rr)) { breakdown = true; break; }
+      if (rel > 1e8) break;
+      if (rel <= o.rtol) { conv = true; break; }
+      apply_B(c, c->r, c->z);
+      launch_axpby(s, len, 1.0, c->z, 1.0, c->x);
+    }
+    // iterations = V-cycles applied before the converged check
+    if (conv) it = it - 1;
+    if (it > o.max_it) it = o.max_it;
+  }
+  // true FP64 residual of the final iterate
+  if (nb > 0.0) {
+    apply_A64(c, c->x, c->Ap);
+    CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_axpby(s, len, -1.0, c->Ap, 1.0, c->r);
+    rel = std::sqrt(dot_sync(c, c->r, c->r)) / nb;
+    conv = conv && rel <= o.rtol * 10.0;
+  }
+  // lambda = boundary data + interior solution
+  CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
+  if (u || q)
+    launch_recover(s, c->refd, c->p, c->n, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                   c->Lfac, f, lam_out, u, q);
+  STATUS_TRY(check_launch("solve"));
+  if (info) {
+    info->iters = it;
+    info->converged = conv ? 1 : 0;
+    info->rel_res = rel;
+  }
+  if (breakdown) return fail(HDGMG_EBREAKDOWN, "NaN/Inf in the outer iteration");
+  if (!conv) return fail(HDGMG_ENOCONV, "outer iteration did not reach rtol");
+  return HDGMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hdgmg_default_opts(hdgmg_opts* o) {
+  if (!o) return;
+  o->coarsest_n = 2;
+  o->m_fine = 1;
+  o->m_growth = 2;
+  o->m_max = 0;
+  o->local_corr = HDGMG_LC_BOTH;
+  o->omega = 1.0;
+  o->krylov = HDGMG_KRYLOV_CG;
+  o->max_it = 200;
+  o->rtol = 1e-10;
+  o->precision = HDGMG_PREC_FP64;
+}
+
+const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
+
+void hdgmg_destroy(hdgmg_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->err_h) cudaFreeHost(c->err_h);
+  if (c->scal_h) cudaFreeHost(c->scal_h);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgmg_opts* opts,
+                          void* stream) {
+  if (!out) return fail(HDGMG_EINVAL, "ctx pointer is NULL");
+  *out = nullptr;
+  if (!prob) return fail(HDGMG_EINVAL, "problem is NULL");
+  hdgmg_opts o;
+  if (opts)
+    o = *opts;
+  else
+    hdgmg_default_opts(&o);
+  const hdgmg_problem& P = *prob;
+  if (P.p < 1 || P.p > 8) return fail(HDGMG_EINVAL, "p must be in 1..8");
+  if (P.n < 2) return fail(HDGMG_EINVAL, "n must be >= 2");
+  if (!(P.x1 > P.x0) || !(P.y1 > P.y0)) return fail(HDGMG_EINVAL, "empty domain");
+  if (!(P.tau_c > 0.0)) return fail(HDGMG_EINVAL, "tau_c must be positive");
+  if (P.tau_mode != HDGMG_TAU_CONST && P.tau_mode != HDGMG_TAU_OVER_H)
+    return fail(HDGMG_EINVAL, "unknown tau_mode");
+  if (o.coarsest_n < 2) return fail(HDGMG_EINVAL, "coarsest_n must be >= 2");
+  if (o.m_fine < 1 || o.m_growth < 1 || o.m_max < 0) return fail(HDGMG_EINVAL, "bad smoothing schedule");
+  if (o.local_corr < 0 || o.local_corr > 2) return fail(HDGMG_EINVAL, "unknown local_corr");
+  if (o.krylov < 0 || o.krylov > 1) return fail(HDGMG_EINVAL, "unknown krylov");
+  if (o.precision < 0 || o.precision > 1) return fail(HDGMG_EINVAL, "unknown precision");
+  if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
+  int nn = P.n;
+  while (nn > o.coarsest_n) {
+    if (nn % 2) return fail(HDGMG_EINVAL, "n must halve evenly down to coarsest_n");
+    nn /= 2;
+  }
+  if (nn < 2) return fail(HDGMG_EINVAL, "coarsest mesh would be smaller than 2 x 2");
+  if ((int64_t)P.n * P.n > (1ll << 26)) return fail(HDGMG_EINVAL, "n too large");
+
+  hdgmg_ctx* c = new hdgmg_ctx();
+  c->prob = P;
+  c->opts = o;
+  c->stream = (cudaStream_t)stream;
+  c->n = P.n;
+  c->p = P.p;
+  c->hx = (P.x1 - P.x0) / P.n;
+  c->hy = (P.y1 - P.y0) / P.n;
+  c->hmin = c->hx < c->hy ? c->hx : c->hy;
+  c->ref = build_ref_element(P.p, c->hx, c->hy);
+  c->nv = c->ref.nv;
+  c->nt = c->ref.nt;
+  auto cleanup = [&](hdgmg_status st) {
+    hdgmg_destroy(c);
+    return st;
+  };
+#define CTRY(call)                                                                       \
+  do {                                                                                   \
+    cudaError_t e__ = (call);                                                            \
+    if (e__ != cudaSuccess)                                                              \
+      return cleanup(fail(e__ == cudaErrorMemoryAllocation ? HDGMG_ENOMEM : HDGMG_ECUDA,  \
+                          std::string(#call) + ": " + cudaGetErrorString(e__)));         \
+  } while (0)
+  // reference tables
+  auto upload = [&](double** dst, const std::vector<double>& v) -> cudaError_t {
+    cudaError_t e = c->alloc(dst, v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+  };
+  CTRY(upload(&c->refd.M, c->ref.M));
+  CTRY(upload(&c->refd.G, c->ref.G));
+  CTRY(upload(&c->refd.E, c->ref.E));
+  CTRY(upload(&c->refd.H, c->ref.H));
+  CTRY(upload(&c->refd.F, c->ref.F));
+  CTRY(upload(&c->refd.K, c->ref.K));
+  CTRY(upload(&c->refd.BxT, c->ref.BxT));
+  CTRY(upload(&c->refd.ByT, c->ref.ByT));
+  CTRY(upload(&c->refd.Cx, c->ref.Cx));
+  CTRY(upload(&c->refd.Cy, c->ref.Cy));
+  // levels
+  {
+    Level L;
+    L.n = P.n;
+    L.nd = P.p + 1;
+    c->levels.push_back(L);
+    if (P.p > 1) {
+      Level Lp;
+      Lp.n = P.n;
+      Lp.nd = 2;
+      c->levels.back().transfer = 1;
+      c->levels.push_back(Lp);
+    }
+    while (c->levels.back().n > o.coarsest_n) {
+      Level Lh;
+      Lh.n = c->levels.back().n / 2;
+      Lh.nd = 2;
+      c->levels.back().transfer = 2;
+      c->levels.push_back(Lh);
+    }
+    int m = o.m_fine;
+    for (Level& Lv : c->levels) {
+      Lv.nl = 4 * Lv.nd;
+      Lv.nsym = Lv.nl * (Lv.nl + 1) / 2;
+      Lv.nE = Lv.n * Lv.n;
+      Lv.nEdge = 2 * Lv.n * (Lv.n + 1);
+      Lv.m = m;
+      m *= o.m_growth;
+      if (o.m_max > 0 && m > o.m_max) m = o.m_max;
+    }
+  }
+  const bool fp32 = o.precision == HDGMG_PREC_FP32;
+  for (size_t l = 0; l < c->levels.size(); ++l) {
+    Level& L = c->levels[l];
+    hdgmg_status st;
+    if (fp32) {
+      st = alloc_level<float>(c, L, false);
+      if (st == HDGMG_OK && l == 0) {
+        if (c->alloc(&L.d64.A, (size_t)L.nsym * L.nE) != cudaSuccess) st = fail(HDGMG_ENOMEM, "A64");
+      }
+    } else {
+      st = alloc_level<double>(c, L, false);
+    }
+    if (st != HDGMG_OK) return cleanup(st);
+  }
+  const int64_t len = c->fine_len();
+  CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
+  CTRY(c->alloc(&c->Lfac, (size_t)(c->nv * (c->nv + 1) / 2) * P.n * P.n));
+  CTRY(c->alloc(&c->err, 4));
+  CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
+  CTRY(c->alloc(&c->x, len));
+  CTRY(c->alloc(&c->r, len));
+  CTRY(c->alloc(&c->z, len));
+  CTRY(c->alloc(&c->pv, len));
+  CTRY(c->alloc(&c->Ap, len));
+  CTRY(c->alloc(&c->b, len));
+  CTRY(c->alloc(&c->lam, len));
+  CTRY(c->alloc(&c->partial, kDotBlocks));
+  CTRY(c->alloc(&c->scal, 8));
+  CTRY(cudaMallocHost(&c->scal_h, sizeof(double) * 8));
+  // coarsest level: free-dof numbering of its interior edges
+  {
+    const Level& Lc = c->levels.back();
+    std::vector<int> fidx(Lc.nEdge, -1);
+    int nfe = 0;
+    const int n = Lc.n, nvert = n * (n + 1);
+    for (int e = 0; e < Lc.nEdge; ++e) {
+      bool bnd;
+      if (e < nvert) {
+        const int i = e % (n + 1);
+        bnd = (i == 0 || i == n);
+      } else {
+        const int j = (e - nvert) / n;
+        bnd = (j == 0 || j == n);
+      }
+      if (!bnd) fidx[e] = nfe++;
+    }
+    c->nf = 2 * nfe;
+    CTRY(c->alloc(&c->freeidx, fidx.size()));
+    CTRY(cudaMemcpy(c->freeidx, fidx.data(), sizeof(int) * fidx.size(), cudaMemcpyHostToDevice));
+    CTRY(c->alloc(&c->dense, (size_t)c->nf * c->nf));
+    CTRY(c->alloc(&c->cwork, (size_t)c->nf + 1));
+  }
+  CTRY(cudaEventCreate(&c->ev0));
+  CTRY(cudaEventCreate(&c->ev1));
+  CTRY(cudaDeviceSynchronize());
+#undef CTRY
+  *out = c;
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
+  if (!c || !log_kappa) return fail(HDGMG_EINVAL, "NULL argument");
+  cudaStream_t s = c->stream;
+  const int nE = c->n * c->n;
+  CUDA_TRY(cudaEventRecord(c->ev0, s));
+  CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
+  Level& L0 = c->levels[0];
+  launch_condense(s, c->refd, c->p, nE, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                  L0.d64.A, c->Lfac, c->err);
+  STATUS_TRY(check_launch("condensation"));
+  if (c->opts.precision == HDGMG_PREC_FP32) {
+    launch_convert<double, float>(s, (int64_t)L0.nsym * L0.nE, L0.d64.A, L0.d32.A);
+    STATUS_TRY(setup_hierarchy<float>(c));
+  } else {
+    STATUS_TRY(setup_hierarchy<double>(c));
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, s));
+  CUDA_TRY(cudaMemcpyAsync(c->err_h, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->t_setup_ms = ms;
+  if (c->err_h[0]) {
+    c->setup_done = false;
+    char buf[128];
+    snprintf(buf, sizeof(buf), "non-positive pivot in set-up (flags 0x%x)", c->err_h[0]);
+    return fail(HDGMG_EBREAKDOWN, buf);
+  }
+  c->setup_done = true;
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const double* g_D,
+                         double* lambda, double* u, double* q, hdgmg_info* info) {
+  if (!c || !f || !lambda) return fail(HDGMG_EINVAL, "NULL argument");
+  if (nrhs < 0) return fail(HDGMG_EINVAL, "nrhs < 0");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  const size_t nE = (size_t)c->n * c->n;
+  const int64_t len = c->fine_len();
+  hdgmg_status last = HDGMG_OK;
+  CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+  for (int k = 0; k < nrhs; ++k) {
+    hdgmg_status st = solve_one(c, f + (size_t)k * c->nv * nE, g_D ? g_D + (size_t)k * len : nullptr,
+                                lambda + (size_t)k * len, u ? u + (size_t)k * c->nv * nE : nullptr,
+                                q ? q + (size_t)k * 2 * c->nv * nE : nullptr, info);
+    if (st == HDGMG_ECUDA || st == HDGMG_EINVAL || st == HDGMG_ENOMEM) return st;
+    if (st != HDGMG_OK) last = st;
+  }
+  CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->t_solve_ms = ms;
+    info->t_setup_ms = c->t_setup_ms;
+    info->n_levels = (int)c->levels.size();
+    info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
+  }
+  if (last != HDGMG_OK) return last;
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_run_host(hdgmg_ctx* c, const double* log_kappa, const double* f,
+                            const double* g_D, double* lambda, double* u, double* q,
+                            hdgmg_info* info) {
+  if (!c || !log_kappa || !f || !lambda) return fail(HDGMG_EINVAL, "NULL argument");
+  cudaStream_t s = c->stream;
+  const size_t nE = (size_t)c->n * c->n;
+  const int64_t len = c->fine_len();
+  if (!c->st_f) {
+    CUDA_TRY(c->alloc(&c->st_f, (size_t)c->nv * nE));
+    CUDA_TRY(c->alloc(&c->st_g, len));
+    CUDA_TRY(c->alloc(&c->st_l, len));
+    CUDA_TRY(c->alloc(&c->st_u, (size_t)c->nv * nE));
+    CUDA_TRY(c->alloc(&c->st_q, (size_t)2 * c->nv * nE));
+  }
+  // log_kappa lands in the context's own copy through the staging of setup
+  CUDA_TRY(cudaMemcpyAsync(c->st_u, log_kappa, sizeof(double) * nE, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(c->st_f, f, sizeof(double) * c->nv * nE, cudaMemcpyHostToDevice, s));
+  if (g_D) CUDA_TRY(cudaMemcpyAsync(c->st_g, g_D, sizeof(double) * len, cudaMemcpyHostToDevice, s));
+  STATUS_TRY(hdgmg_setup(c, c->st_u));
+  hdgmg_status st = hdgmg_solve(c, 1, c->st_f, g_D ? c->st_g : nullptr, c->st_l, u ? c->st_u : nullptr,
+                                q ? c->st_q : nullptr, info);
+  if (st == HDGMG_ECUDA || st == HDGMG_EINVAL || st == HDGMG_ENOMEM) return st;
+  CUDA_TRY(cudaMemcpyAsync(lambda, c->st_l, sizeof(double) * len, cudaMemcpyDeviceToHost, s));
+  if (u) CUDA_TRY(cudaMemcpyAsync(u, c->st_u, sizeof(double) * c->nv * nE, cudaMemcpyDeviceToHost, s));
+  if (q) CUDA_TRY(cudaMemcpyAsync(q, c->st_q, sizeof(double) * 2 * c->nv * nE, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+hdgmg_status hdgmg_num_levels(hdgmg_ctx* c, int32_t* n_levels) {
+  if (!c || !n_levels) return fail(HDGMG_EINVAL, "NULL argument");
+  *n_levels = (int32_t)c->levels.size();
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_level_shape(hdgmg_ctx* c, int32_t level, int32_t* n, int32_t* nd) {
+  if (!c || !n || !nd) return fail(HDGMG_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(HDGMG_EINVAL, "level out of range");
+  *n = c->levels[level].n;
+  *nd = c->levels[level].nd;
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_copy_element_matrices(hdgmg_ctx* c, int32_t level, double* out) {
+  if (!c || !out) return fail(HDGMG_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(HDGMG_EINVAL, "level out of range");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  Level& L = c->levels[level];
+  if (level == 0 || c->opts.precision == HDGMG_PREC_FP64)
+    launch_unpack<double>(c->stream, L.nl, L.nE, L.d64.A, out);
+  else
+    launch_unpack<float>(c->stream, L.nl, L.nE, L.d32.A, out);
+  STATUS_TRY(check_launch("copy element matrices"));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_apply_operator(hdgmg_ctx* c, int32_t level, const double* x, double* y) {
+  if (!c || !x || !y) return fail(HDGMG_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(HDGMG_EINVAL, "level out of range");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  cudaStream_t s = c->stream;
+  Level& L = c->levels[level];
+  const int64_t len = (int64_t)L.nd * L.nEdge;
+  if (level == 0 || c->opts.precision == HDGMG_PREC_FP64) {
+    double *xm = nullptr, *ym = nullptr;
+    CUDA_TRY(cudaMalloc(&xm, sizeof(double) * len));
+    CUDA_TRY(cudaMalloc(&ym, sizeof(double) * len));
+    cudaMemcpyAsync(xm, x, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    launch_mask<double>(s, L.n, L.nd, xm);
+    cudaMemsetAsync(ym, 0, sizeof(double) * len, s);
+    launch_matvec<double>(s, L.n, L.nd, L.d64.A, xm, ym, 1.0);
+    cudaMemcpyAsync(y, ym, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    cudaFree(xm);
+    cudaFree(ym);
+  } else {
+    float *xm = nullptr, *ym = nullptr;
+    CUDA_TRY(cudaMalloc(&xm, sizeof(float) * len));
+    CUDA_TRY(cudaMalloc(&ym, sizeof(float) * len));
+    launch_convert<double, float>(s, len, x, xm);
+    launch_mask<float>(s, L.n, L.nd, xm);
+    cudaMemsetAsync(ym, 0, sizeof(float) * len, s);
+    launch_matvec<float>(s, L.n, L.nd, L.d32.A, xm, ym, 1.0f);
+    launch_convert<float, double>(s, len, ym, y);
+    cudaStreamSynchronize(s);
+    cudaFree(xm);
+    cudaFree(ym);
+  }
+  return check_launch("apply operator");
+}
+
+hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* c, const double* r, double* e) {
+  if (!c || !r || !e) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  CUDA_TRY(cudaMemcpyAsync(c->r, r, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  launch_mask<double>(s, c->n, c->p + 1, c->r);
+  apply_B(c, c->r, e);
+  STATUS_TRY(check_launch("apply vcycle"));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return HDGMG_OK;
+}
+
+hdgmg_status hdgmg_condensed_rhs(hdgmg_ctx* c, const double* f, const double* g_D, double* b) {
+  if (!c || !f || !b) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  STATUS_TRY(build_rhs(c, f, g_D));
+  CUDA_TRY(cudaMemcpyAsync(b, c->b, sizeof(double) * c->fine_len(), cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return HDGMG_OK;
+}
+
+}  // extern "C"

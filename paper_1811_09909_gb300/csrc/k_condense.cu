@@ -1,0 +1,259 @@
+// Element-local kernels: static condensation (K1), condensed right-hand side
+// (K5) and local recovery (K12) of the HDG scheme (arXiv:1811.09909, Sec. 2).
+//
+// Per element, with S = kappa G + tau E (SPD, n_v x n_v) and
+// W = kappa H + tau F (n_v x n_t):
+//   K1: S = L L^T (Cholesky: the LU of the volume block after the diagonal
+//       mass block of q is eliminated), V = L^-1 W, A_e = kappa K + tau I - V^T V.
+//   K5: g_e = W^T S^-1 (M f_e), assembled into the edge vector.
+//   K12: u_e = S^-1 (M f_e + W lambda_e),  q_d = kappa M^-1 (B_d^T u - C_d lambda_e).
+#include <cmath>
+
+#include "internal.h"
+
+namespace hdgmg {
+
+namespace {
+
+__device__ __forceinline__ double tau_of(int tau_mode, double tau_c, double hmin) {
+  return tau_mode == HDGMG_TAU_OVER_H ? tau_c / hmin : tau_c;
+}
+
+__device__ __forceinline__ void tri_index(int t, int& i, int& j) {
+  // row-major packed lower triangle: t = i(i+1)/2 + j, 0 <= j <= i
+  int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (r * (r + 1) / 2 > t) --r;
+  while ((r + 1) * (r + 2) / 2 <= t) ++r;
+  i = r;
+  j = t - r * (r + 1) / 2;
+}
+
+// K1: one warp per element, the local matrices in shared memory.
+//   S: nv x nv (full square, lower part used), V: nv x nt.
+__global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
+                                const double* __restrict__ G, const double* __restrict__ Eb,
+                                const double* __restrict__ H, const double* __restrict__ F,
+                                const double* __restrict__ K, const double* __restrict__ logk,
+                                int tau_mode, double tau_c, double hmin,
+                                double* __restrict__ A, double* __restrict__ Lfac,
+                                int* __restrict__ err) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * warps_per_block + warp;
+  if (e >= nE) return;
+  double* S = smem + (size_t)warp * (nv * nv + nv * nt);
+  double* V = S + nv * nv;
+  const double kap = exp(logk[e]);
+  const double tau = tau_of(tau_mode, tau_c, hmin);
+  for (int t = lane; t < nv * nv; t += 32) S[t] = kap * G[t] + tau * Eb[t];
+  for (int t = lane; t < nv * nt; t += 32) V[t] = kap * H[t] + tau * F[t];
+  __syncwarp();
+  bool bad = false;
+  for (int k = 0; k < nv; ++k) {
+    double d = S[k * nv + k];
+    if (!(d > 0.0) || !isfinite(d)) {
+      bad = true;
+      d = 1.0;
+    }
+    d = sqrt(d);
+    const double di = 1.0 / d;
+    __syncwarp();
+    if (lane == 0) S[k * nv + k] = d;
+    for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
+    for (int c = lane; c < nt; c += 32) V[k * nt + c] *= di;
+    __syncwarp();
+    const int m = nv - k - 1;
+    const int ntri = m * (m + 1) / 2;
+    for (int t = lane; t < ntri; t += 32) {
+      int ii, jj;
+      tri_index(t, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      S[i * nv + j] -= S[i * nv + k] * S[j * nv + k];
+    }
+    for (int t = lane; t < m * nt; t += 32) {
+      const int i = k + 1 + t / nt, c = t % nt;
+      V[i * nt + c] -= S[i * nv + k] * V[k * nt + c];
+    }
+    __syncwarp();
+  }
+  if (bad && lane == 0) atomicOr(err, 1);
+  const int nsa = nt * (nt + 1) / 2;
+  for (int t = lane; t < nsa; t += 32) {
+    int r, c;
+    tri_index(t, r, c);
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s += V[i * nt + r] * V[i * nt + c];
+    double a = kap * K[r * nt + c] - s;
+    if (r == c) a += tau;
+    A[(size_t)t * nE + e] = a;
+  }
+  if (Lfac) {
+    const int nsl = nv * (nv + 1) / 2;
+    for (int t = lane; t < nsl; t += 32) {
+      int r, c;
+      tri_index(t, r, c);
+      Lfac[(size_t)t * nE + e] = S[r * nv + c];
+    }
+  }
+}
+
+// Per-thread work vectors live in shared memory as [index][thread] so that
+// the 32 threads of a warp touch 32 consecutive words.
+#define TV(arr, i) arr[(size_t)(i) * blockDim.x + threadIdx.x]
+
+// solve L L^T y = y in place (L packed SoA, element e)
+__device__ __forceinline__ void chol_solve(const double* __restrict__ L, int nv, int nE, int e,
+                                           double* y) {
+  for (int i = 0; i < nv; ++i) {
+    double s = TV(y, i);
+    const int row = i * (i + 1) / 2;
+    for (int j = 0; j < i; ++j) s -= L[(size_t)(row + j) * nE + e] * TV(y, j);
+    TV(y, i) = s / L[(size_t)(row + i) * nE + e];
+  }
+  for (int i = nv - 1; i >= 0; --i) {
+    double s = TV(y, i);
+    for (int j = i + 1; j < nv; ++j) s -= L[(size_t)(j * (j + 1) / 2 + i) * nE + e] * TV(y, j);
+    TV(y, i) = s / L[(size_t)(i * (i + 1) / 2 + i) * nE + e];
+  }
+}
+
+__device__ __forceinline__ void element_edges(int n, int e, int ed[4]) {
+  const int j = e / n, i = e - j * n;
+  const int nvert = n * (n + 1);
+  ed[0] = j * (n + 1) + i;
+  ed[1] = j * (n + 1) + i + 1;
+  ed[2] = nvert + j * n + i;
+  ed[3] = nvert + (j + 1) * n + i;
+}
+
+__device__ __forceinline__ bool is_boundary_edge(int n, int edge) {
+  const int nvert = n * (n + 1);
+  if (edge < nvert) {
+    const int i = edge % (n + 1);
+    return i == 0 || i == n;
+  }
+  const int j = (edge - nvert) / n;
+  return j == 0 || j == n;
+}
+
+// K5: thread per element; shared memory y[nv][blockDim]
+__global__ void rhs_kernel(int p, int n, const double* __restrict__ Mdiag,
+                           const double* __restrict__ H, const double* __restrict__ F,
+                           const double* __restrict__ logk, int tau_mode, double tau_c,
+                           double hmin, const double* __restrict__ L,
+                           const double* __restrict__ f, double* __restrict__ b) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  const double kap = exp(logk[e]);
+  const double tau = tau_of(tau_mode, tau_c, hmin);
+  for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
+  chol_solve(L, nv, nE, e, y);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) {
+    const int edge = ed[c / p1];
+    if (is_boundary_edge(n, edge)) continue;
+    double g = 0.0;
+    for (int a = 0; a < nv; ++a) g += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(y, a);
+    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
+  }
+}
+
+// K12: thread per element; shared memory y[nv][blockDim], le[nt][blockDim]
+__global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
+                               const double* __restrict__ H, const double* __restrict__ F,
+                               const double* __restrict__ BxT, const double* __restrict__ ByT,
+                               const double* __restrict__ Cx, const double* __restrict__ Cy,
+                               const double* __restrict__ logk, int tau_mode, double tau_c,
+                               double hmin, const double* __restrict__ L,
+                               const double* __restrict__ f, const double* __restrict__ lam,
+                               double* __restrict__ u, double* __restrict__ q) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  double* le = smem + (size_t)nv * blockDim.x;
+  const double kap = exp(logk[e]);
+  const double tau = tau_of(tau_mode, tau_c, hmin);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
+  for (int a = 0; a < nv; ++a) {
+    double s = Mdiag[a] * f[(size_t)a * nE + e];
+    for (int c = 0; c < nt; ++c) s += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(le, c);
+    TV(y, a) = s;
+  }
+  chol_solve(L, nv, nE, e, y);
+  if (u)
+    for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
+  if (q) {
+    for (int a = 0; a < nv; ++a) {
+      double sx = 0.0, sy = 0.0;
+      for (int b2 = 0; b2 < nv; ++b2) {
+        sx += BxT[a * nv + b2] * TV(y, b2);
+        sy += ByT[a * nv + b2] * TV(y, b2);
+      }
+      for (int c = 0; c < nt; ++c) {
+        sx -= Cx[a * nt + c] * TV(le, c);
+        sy -= Cy[a * nt + c] * TV(le, c);
+      }
+      const double sc = kap / Mdiag[a];
+      q[(size_t)a * nE + e] = sc * sx;
+      q[(size_t)(nv + a) * nE + e] = sc * sy;
+    }
+  }
+}
+#undef TV
+
+}  // namespace
+
+void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* logk,
+                     int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err) {
+  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const size_t per_warp = sizeof(double) * (size_t)(nv * nv + nv * nt);
+  int wpb = (int)((200 * 1024) / per_warp);
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  const size_t shm = per_warp * wpb;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  const int blocks = (nE + wpb - 1) / wpb;
+  condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
+                                                 logk, tau_mode, tau_c, hmin, A, Lfac, err);
+}
+
+void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* logk,
+                int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
+                double* b) {
+  const int nE = n * n, nv = (p + 1) * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)nv * threads;
+  cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, logk, tau_mode, tau_c, hmin,
+                                          Lfac, f, b);
+}
+
+void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const double* logk,
+                    int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
+                    const double* lam, double* u, double* q) {
+  const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
+  cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
+                                              ref.Cy, logk, tau_mode, tau_c, hmin, Lfac, f, lam,
+                                              u, q);
+}
+
+}  // namespace hdgmg

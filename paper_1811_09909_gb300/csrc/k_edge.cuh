@@ -1,0 +1,174 @@
+// Edge/element kernels templated on the number of trace modes per edge ND:
+//   K6  trace matvec y += alpha A x, one thread per element, packed symmetric
+//       A_e in structure-of-arrays layout, results added into the two edge
+//       owners with atomics (exactly two contributions per entry, so the
+//       sum does not depend on their order)
+//   K2  edge block-Jacobi blocks D = A_e0[edge] + A_e1[edge] and D^-1
+//   K7  block-Jacobi update e += omega D^-1 (r - A e)  (Sec. 4.1)
+// Each (type, ND) pair is compiled in its own translation unit
+// (k_edge_inst.cu) so that the fully unrolled kernels build in parallel.
+#pragma once
+
+#include "k_common.cuh"
+
+namespace hdgmg {
+
+// ---------------------------------------------------------------- K6 matvec
+template <typename T, int ND>
+__global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict__ A,
+                                                     const T* __restrict__ x, T* __restrict__ y,
+                                                     T alpha) {
+  constexpr int NL = 4 * ND;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  const int nedge = 2 * n * (n + 1);
+  int ed[4];
+  elem_edges(n, e, ed);
+  T xl[NL], yl[NL];
+#pragma unroll
+  for (int c = 0; c < NL; ++c) {
+    xl[c] = x[(size_t)(c % ND) * nedge + ed[c / ND]];
+    yl[c] = T(0);
+  }
+#pragma unroll
+  for (int r = 0; r < NL; ++r) {
+#pragma unroll
+    for (int c = 0; c < r; ++c) {
+      const T a = A[(size_t)pk(r, c) * nE + e];
+      yl[r] += a * xl[c];
+      yl[c] += a * xl[r];
+    }
+    yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
+  }
+#pragma unroll
+  for (int le = 0; le < 4; ++le) {
+    if (bnd_edge(n, ed[le])) continue;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * yl[le * ND + k]);
+  }
+}
+
+// ----------------------------------------------------- K2 block-Jacobi blocks
+template <typename T, int ND>
+__global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__ Dinv,
+                                 int* __restrict__ err) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge) return;
+  constexpr int NS = ND * (ND + 1) / 2;
+  if (bnd_edge(n, edge)) {
+#pragma unroll
+    for (int t = 0; t < NS; ++t) Dinv[(size_t)t * nedge + edge] = T(0);
+    return;
+  }
+  const int nE = n * n;
+  const int nvert = n * (n + 1);
+  int e0, le0, e1, le1;
+  if (edge < nvert) {
+    const int j = edge / (n + 1), i = edge % (n + 1);
+    e0 = j * n + i - 1; le0 = 1;    // left element, its right edge
+    e1 = j * n + i;     le1 = 0;    // right element, its left edge
+  } else {
+    const int j = (edge - nvert) / n, i = (edge - nvert) % n;
+    e0 = (j - 1) * n + i; le0 = 3;  // element below, its top edge
+    e1 = j * n + i;       le1 = 2;  // element above, its bottom edge
+  }
+  double D[ND][ND];
+#pragma unroll
+  for (int a = 0; a < ND; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      const double v = (double)A[(size_t)pk(le0 * ND + a, le0 * ND + b) * nE + e0] +
+                       (double)A[(size_t)pk(le1 * ND + a, le1 * ND + b) * nE + e1];
+      D[a][b] = v;
+      D[b][a] = v;
+    }
+  // Cholesky D = L L^T, then D^-1 = L^-T L^-1
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    double d = D[k][k];
+#pragma unroll
+    for (int j = 0; j < k; ++j) d -= D[k][j] * D[k][j];
+    if (!(d > 0.0)) { bad = true; d = 1.0; }
+    d = sqrt(d);
+    D[k][k] = d;
+#pragma unroll
+    for (int i = k + 1; i < ND; ++i) {
+      double s = D[i][k];
+#pragma unroll
+      for (int j = 0; j < k; ++j) s -= D[i][j] * D[k][j];
+      D[i][k] = s / d;
+    }
+  }
+  double Li[ND][ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i)
+#pragma unroll
+    for (int j = 0; j < ND; ++j) Li[i][j] = 0.0;
+#pragma unroll
+  for (int j = 0; j < ND; ++j) {
+    Li[j][j] = 1.0 / D[j][j];
+#pragma unroll
+    for (int i = j + 1; i < ND; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = j; k < i; ++k) s -= D[i][k] * Li[k][j];
+      Li[i][j] = s / D[i][i];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < ND; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = a; k < ND; ++k) s += Li[k][a] * Li[k][b];
+      Dinv[(size_t)pk(a, b) * nedge + edge] = (T)s;
+    }
+  if (bad) atomicOr(err, 2);
+}
+
+// --------------------------------------------------- K7 block-Jacobi update
+template <typename T, int ND>
+__global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __restrict__ r,
+                                 T* __restrict__ y, T* __restrict__ e, T omega, int first) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge || bnd_edge(n, edge)) return;
+  T d[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    const size_t ix = (size_t)k * nedge + edge;
+    d[k] = first ? r[ix] : r[ix] - y[ix];
+    if (!first) y[ix] = T(0);
+  }
+#pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int b = 0; b < ND; ++b) s += Dinv[(size_t)pk_any(a, b) * nedge + edge] * d[b];
+    const size_t ix = (size_t)a * nedge + edge;
+    e[ix] = first ? omega * s : e[ix] + omega * s;
+  }
+}
+
+
+template <typename T, int ND>
+void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha) {
+  matvec_kernel<T, ND><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
+}
+
+template <typename T, int ND>
+void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err) {
+  bj_blocks_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, A, Dinv, err);
+}
+
+template <typename T, int ND>
+void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
+                         int first) {
+  bj_update_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega, first);
+}
+
+}  // namespace hdgmg

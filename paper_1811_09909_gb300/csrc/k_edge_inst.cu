@@ -1,0 +1,20 @@
+// One (type, ND) instantiation of the edge/element kernels of k_edge.cuh;
+// built once per pair with -DHDGMG_REAL=<double|float> -DHDGMG_ND=<2..9>.
+#include "k_edge.cuh"
+
+#ifndef HDGMG_REAL
+#define HDGMG_REAL double
+#endif
+#ifndef HDGMG_ND
+#define HDGMG_ND 2
+#endif
+
+namespace hdgmg {
+template void launch_matvec_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
+                                                     const HDGMG_REAL*, HDGMG_REAL*, HDGMG_REAL);
+template void launch_bj_blocks_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
+                                                        HDGMG_REAL*, int*);
+template void launch_bj_update_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
+                                                        const HDGMG_REAL*, HDGMG_REAL*,
+                                                        HDGMG_REAL*, HDGMG_REAL, int);
+}  // namespace hdgmg

@@ -1,0 +1,735 @@
+// Multigrid kernels for the HDG trace system (arXiv:1811.09909, Sec. 3):
+//   K6  trace matvec y += alpha A x, element by element (packed symmetric A_e)
+//   K2  edge block-Jacobi blocks and their inverses (Sec. 4.1, block-Jacobi)
+//   K7  block-Jacobi update e += omega D^-1 (r - A e)
+//   K3  p-coarsening A_{N-1} = J_N^T A_N J_N (eq. ANm1)
+//   K4  2x2 agglomeration: local Schur complement, prolongation/restriction
+//       blocks and local-correction blocks (eqs. n_1_Ik, n_1_Qk, Akm1,
+//       localCorrection)
+//   K8  local correction, K9 restriction, K11 prolongation
+//   K10 coarsest level: dense Cholesky (assembly, factorisation, solve)
+//
+// Vectors are [nd][n_edges] with Dirichlet (boundary) entries held at zero;
+// every level owns an accumulator y that is zero between kernels: the matvec
+// adds into it and the consumer of y resets it.
+#include <cmath>
+
+#include "internal.h"
+#include "k_common.cuh"
+
+namespace hdgmg {
+
+namespace {
+
+// ------------------------------------------------------- K3 p-coarsening
+template <typename T>
+__global__ void pcoarsen_kernel(int nE, int ndf, const T* __restrict__ Af, T* __restrict__ Ac) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  for (int r = 0; r < 8; ++r)
+    for (int c = 0; c <= r; ++c) {
+      const int rf = (r / 2) * ndf + (r % 2), cf = (c / 2) * ndf + (c % 2);
+      Ac[(size_t)pk(r, c) * nE + e] = Af[(size_t)pk(rf, cf) * nE + e];
+    }
+}
+
+// ---------------------------------------------- 2x2 agglomeration geometry
+// Interior edges of macro-element C = (I, J) (fine mesh n = 2 nc):
+//   ie 0: v(2I+1, 2J)  1: v(2I+1, 2J+1)  2: h(2I, 2J+1)  3: h(2I+1, 2J+1)
+// Perimeter child edges (me, c): me 0 left v(2I, 2J+c), 1 right v(2I+2, 2J+c),
+//   2 bottom h(2I+c, 2J), 3 top h(2I+c, 2J+2); c = 0 is the half at the
+//   lower coordinate.  Local index: interior ie*2+k, boundary (me*2+c)*2+k.
+__device__ __forceinline__ int fine_v(int n, int i, int j) { return j * (n + 1) + i; }
+__device__ __forceinline__ int fine_h(int n, int i, int j) { return n * (n + 1) + j * n + i; }
+
+__device__ __forceinline__ int interior_edge(int n, int I, int J, int ie) {
+  switch (ie) {
+    case 0: return fine_v(n, 2 * I + 1, 2 * J);
+    case 1: return fine_v(n, 2 * I + 1, 2 * J + 1);
+    case 2: return fine_h(n, 2 * I, 2 * J + 1);
+    default: return fine_h(n, 2 * I + 1, 2 * J + 1);
+  }
+}
+
+__device__ __forceinline__ int perimeter_edge(int n, int I, int J, int me, int c) {
+  switch (me) {
+    case 0: return fine_v(n, 2 * I, 2 * J + c);
+    case 1: return fine_v(n, 2 * I + 2, 2 * J + c);
+    case 2: return fine_h(n, 2 * I + c, 2 * J);
+    default: return fine_h(n, 2 * I + c, 2 * J + 2);
+  }
+}
+
+// child ch = cj*2 + ci, local edge le -> (interior?, slot) with slot = ie or me*2+c
+__device__ __forceinline__ void child_map(int ch, int le, bool& interior, int& slot) {
+  const int ci = ch & 1, cj = ch >> 1;
+  switch (le) {
+    case 0: interior = (ci == 1); slot = interior ? cj : (0 * 2 + cj); break;
+    case 1: interior = (ci == 0); slot = interior ? cj : (1 * 2 + cj); break;
+    case 2: interior = (cj == 1); slot = interior ? 2 + ci : (2 * 2 + ci); break;
+    default: interior = (cj == 0); slot = interior ? 2 + ci : (3 * 2 + ci); break;
+  }
+}
+
+__constant__ double c_Jc[2][2][2];   // child injection [child][fine mode][coarse mode]
+
+// -------------------------------------------------- K4 agglomeration setup
+template <typename T>
+__global__ void agglomerate_kernel(int nc, const T* __restrict__ Af, T* __restrict__ Ac,
+                                   T* __restrict__ AIIinv, T* __restrict__ Yout,
+                                   T* __restrict__ Pi, int* __restrict__ err) {
+  const int nC = nc * nc;
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= nC) return;
+  const int J = C / nc, I = C - J * nc;
+  const int n = 2 * nc, nEf = n * n;
+  T AII[8][8], AIB[8][16], ABB[16][16];
+  for (int a = 0; a < 8; ++a) {
+    for (int b = 0; b < 8; ++b) AII[a][b] = T(0);
+    for (int b = 0; b < 16; ++b) AIB[a][b] = T(0);
+  }
+  for (int a = 0; a < 16; ++a)
+    for (int b = 0; b < 16; ++b) ABB[a][b] = T(0);
+  for (int ch = 0; ch < 4; ++ch) {
+    const int ef = (2 * J + (ch >> 1)) * n + 2 * I + (ch & 1);
+    for (int r = 0; r < 8; ++r) {
+      bool ir;
+      int sr;
+      child_map(ch, r / 2, ir, sr);
+      const int lr = sr * 2 + (r & 1);
+      for (int c = 0; c < 8; ++c) {
+        bool ic;
+        int sc;
+        child_map(ch, c / 2, ic, sc);
+        const int lc = sc * 2 + (c & 1);
+        const T a = Af[(size_t)pk_any(r, c) * nEf + ef];
+        if (ir && ic) AII[lr][lc] += a;
+        else if (ir && !ic) AIB[lr][lc] += a;
+        else if (!ir && !ic) ABB[lr][lc] += a;
+      }
+    }
+  }
+  // Cholesky of A_II and its inverse
+  T L[8][8];
+  bool bad = false;
+  for (int k = 0; k < 8; ++k) {
+    T d = AII[k][k];
+    for (int j = 0; j < k; ++j) d -= L[k][j] * L[k][j];
+    if (!(d > T(0))) { bad = true; d = T(1); }
+    d = sqrt(d);
+    L[k][k] = d;
+    for (int i = k + 1; i < 8; ++i) {
+      T s = AII[i][k];
+      for (int j = 0; j < k; ++j) s -= L[i][j] * L[k][j];
+      L[i][k] = s / d;
+    }
+    for (int j = k + 1; j < 8; ++j) L[k][j] = T(0);
+  }
+  T Li[8][8];
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) Li[i][j] = T(0);
+  for (int j = 0; j < 8; ++j) {
+    Li[j][j] = T(1) / L[j][j];
+    for (int i = j + 1; i < 8; ++i) {
+      T s = T(0);
+      for (int k = j; k < i; ++k) s -= L[i][k] * Li[k][j];
+      Li[i][j] = s / L[i][i];
+    }
+  }
+  T Ai[8][8];
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b <= a; ++b) {
+      T s = T(0);
+      for (int k = a; k < 8; ++k) s += Li[k][a] * Li[k][b];
+      Ai[a][b] = s;
+      Ai[b][a] = s;
+      AIIinv[(size_t)pk(a, b) * nC + C] = s;
+    }
+  // Y = -A_II^-1 A_IB (8 x 16)
+  T Y[8][16];
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 16; ++b) {
+      T s = T(0);
+      for (int k = 0; k < 8; ++k) s -= Ai[a][k] * AIB[k][b];
+      Y[a][b] = s;
+      Yout[(size_t)(a * 16 + b) * nC + C] = s;
+    }
+  // S = A_BB + A_BI Y  (A_BI = A_IB^T), 16 x 16
+  // coarse A = J^T S J, Pi = Y J; J[(me*2+c)*2+kf][me*2+kc] = Jc[c][kf][kc]
+  T SJ[16][8];
+  for (int a = 0; a < 16; ++a)
+    for (int cb = 0; cb < 8; ++cb) {
+      const int me = cb >> 1, kc = cb & 1;
+      T s = T(0);
+      for (int c = 0; c < 2; ++c)
+        for (int kf = 0; kf < 2; ++kf) {
+          const int b = (me * 2 + c) * 2 + kf;
+          T sab = ABB[a][b];
+          for (int k = 0; k < 8; ++k) sab += AIB[k][a] * Y[k][b];
+          s += sab * (T)c_Jc[c][kf][kc];
+        }
+      SJ[a][cb] = s;
+    }
+  for (int ca = 0; ca < 8; ++ca) {
+    const int me = ca >> 1, kc = ca & 1;
+    for (int cb = 0; cb <= ca; ++cb) {
+      T s = T(0);
+      for (int c = 0; c < 2; ++c)
+        for (int kf = 0; kf < 2; ++kf) s += (T)c_Jc[c][kf][kc] * SJ[(me * 2 + c) * 2 + kf][cb];
+      Ac[(size_t)pk(ca, cb) * nC + C] = s;
+    }
+  }
+  for (int a = 0; a < 8; ++a)
+    for (int cb = 0; cb < 8; ++cb) {
+      const int me = cb >> 1, kc = cb & 1;
+      T s = T(0);
+      for (int c = 0; c < 2; ++c)
+        for (int kf = 0; kf < 2; ++kf) s += Y[a][(me * 2 + c) * 2 + kf] * (T)c_Jc[c][kf][kc];
+      Pi[(size_t)(a * 8 + cb) * nC + C] = s;
+    }
+  if (bad) atomicOr(err, 4);
+}
+
+// ------------------------------------------------- K8 local correction
+// e_I <- e_I + A_II^-1 (r - A e)_I = A_II^-1 r_I + Y e_B
+template <typename T>
+__global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
+                                        const T* __restrict__ Y, const T* __restrict__ r,
+                                        T* __restrict__ e) {
+  const int nC = nc * nc;
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= nC) return;
+  const int J = C / nc, I = C - J * nc;
+  const int n = 2 * nc;
+  const int nedge = 2 * n * (n + 1);
+  T rI[8], eB[16];
+#pragma unroll
+  for (int ie = 0; ie < 4; ++ie) {
+    const int ed = interior_edge(n, I, J, ie);
+    rI[ie * 2] = r[ed];
+    rI[ie * 2 + 1] = r[(size_t)nedge + ed];
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int ed = perimeter_edge(n, I, J, b >> 1, b & 1);
+    eB[b * 2] = e[ed];
+    eB[b * 2 + 1] = e[(size_t)nedge + ed];
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += AIIinv[(size_t)pk_any(a, k) * nC + C] * rI[k];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) s += Y[(size_t)(a * 16 + b) * nC + C] * eB[b];
+    const int ed = interior_edge(n, I, J, a >> 1);
+    e[(size_t)(a & 1) * nedge + ed] = s;
+  }
+}
+
+__device__ __forceinline__ int coarse_v(int nc, int I, int J) { return J * (nc + 1) + I; }
+__device__ __forceinline__ int coarse_h(int nc, int I, int J) { return nc * (nc + 1) + J * nc + I; }
+
+// --------------------------------------------------------- K9 restriction
+// r_c = J^T s_B + Pi^T s_I (Q_{k-1} of eq. n_1_Qk with Pi^T = -J^T A_BI A_II^-1
+// for symmetric A), s = r - y, y = A e.  One thread per coarse edge.
+template <typename T>
+__global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ r,
+                                  const T* __restrict__ y, T* __restrict__ rc) {
+  const int nedc = 2 * nc * (nc + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedc) return;
+  if (bnd_edge(nc, E)) {
+    rc[E] = T(0);
+    rc[(size_t)nedc + E] = T(0);
+    return;
+  }
+  const int n = 2 * nc, nedge = 2 * n * (n + 1), nC = nc * nc;
+  const int nvc = nc * (nc + 1);
+  int ch[2], Cs[2], mes[2];
+  if (E < nvc) {
+    const int J = E / (nc + 1), I = E % (nc + 1);
+    ch[0] = fine_v(n, 2 * I, 2 * J);
+    ch[1] = fine_v(n, 2 * I, 2 * J + 1);
+    Cs[0] = J * nc + I - 1; mes[0] = 1;    // left macro-element, its right edge
+    Cs[1] = J * nc + I;     mes[1] = 0;
+  } else {
+    const int J = (E - nvc) / nc, I = (E - nvc) % nc;
+    ch[0] = fine_h(n, 2 * I, 2 * J);
+    ch[1] = fine_h(n, 2 * I + 1, 2 * J);
+    Cs[0] = (J - 1) * nc + I; mes[0] = 3;  // macro-element below, its top edge
+    Cs[1] = J * nc + I;       mes[1] = 2;
+  }
+  T acc[2] = {T(0), T(0)};
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T s0 = r[ch[c]] - y[ch[c]];
+    const T s1 = r[(size_t)nedge + ch[c]] - y[(size_t)nedge + ch[c]];
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc)
+      acc[kc] += (T)c_Jc[c][0][kc] * s0 + (T)c_Jc[c][1][kc] * s1;
+  }
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int C = Cs[side];
+    const int J = C / nc, I = C - J * nc;
+#pragma unroll
+    for (int ie = 0; ie < 4; ++ie) {
+      const int ed = interior_edge(n, I, J, ie);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const T s = r[(size_t)k * nedge + ed] - y[(size_t)k * nedge + ed];
+        const int a = ie * 2 + k;
+#pragma unroll
+        for (int kc = 0; kc < 2; ++kc) acc[kc] += Pi[(size_t)(a * 8 + mes[side] * 2 + kc) * nC + C] * s;
+      }
+    }
+  }
+  rc[E] = acc[0];
+  rc[(size_t)nedc + E] = acc[1];
+}
+
+// -------------------------------------------------------- K11 prolongation
+// e_B += J e_c (per coarse edge, its two halves), e_I += Pi e_c(C) (per
+// macro-element); every fine edge is touched exactly once, where y is reset.
+template <typename T>
+__global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ ec,
+                                 T* __restrict__ e, T* __restrict__ y) {
+  const int nC = nc * nc, nedc = 2 * nc * (nc + 1), nvc = nc * (nc + 1);
+  const int n = 2 * nc, nedge = 2 * n * (n + 1);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nC) {
+    const int C = t, J = C / nc, I = C - J * nc;
+    const int ce[4] = {coarse_v(nc, I, J), coarse_v(nc, I + 1, J), coarse_h(nc, I, J),
+                       coarse_h(nc, I, J + 1)};
+    T xc[8];
+#pragma unroll
+    for (int me = 0; me < 4; ++me) {
+      xc[me * 2] = ec[ce[me]];
+      xc[me * 2 + 1] = ec[(size_t)nedc + ce[me]];
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b < 8; ++b) s += Pi[(size_t)(a * 8 + b) * nC + C] * xc[b];
+      const size_t ix = (size_t)(a & 1) * nedge + interior_edge(n, I, J, a >> 1);
+      e[ix] += s;
+      y[ix] = T(0);
+    }
+    return;
+  }
+  const int E = t - nC;
+  if (E >= nedc) return;
+  int ch[2];
+  if (E < nvc) {
+    const int J = E / (nc + 1), I = E % (nc + 1);
+    ch[0] = fine_v(n, 2 * I, 2 * J);
+    ch[1] = fine_v(n, 2 * I, 2 * J + 1);
+  } else {
+    const int J = (E - nvc) / nc, I = (E - nvc) % nc;
+    ch[0] = fine_h(n, 2 * I, 2 * J);
+    ch[1] = fine_h(n, 2 * I + 1, 2 * J);
+  }
+  const T x0 = ec[E], x1 = ec[(size_t)nedc + E];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+#pragma unroll
+    for (int kf = 0; kf < 2; ++kf) {
+      const size_t ix = (size_t)kf * nedge + ch[c];
+      e[ix] += (T)c_Jc[c][kf][0] * x0 + (T)c_Jc[c][kf][1] * x1;
+      y[ix] = T(0);
+    }
+  }
+}
+
+// ------------------------------------------------- p-transfer (J_N, J_N^T)
+template <typename T>
+__global__ void restrict_p_kernel(int n, int nd, const T* __restrict__ r, T* __restrict__ y,
+                                  T* __restrict__ rc) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge) return;
+  rc[edge] = r[edge] - y[edge];
+  rc[(size_t)nedge + edge] = r[(size_t)nedge + edge] - y[(size_t)nedge + edge];
+  for (int k = 0; k < nd; ++k) y[(size_t)k * nedge + edge] = T(0);
+}
+
+template <typename T>
+__global__ void prolong_p_kernel(int n, const T* __restrict__ ec, T* __restrict__ e) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge) return;
+  e[edge] += ec[edge];
+  e[(size_t)nedge + edge] += ec[(size_t)nedge + edge];
+}
+
+// ------------------------------------------------------ K10 coarsest level
+template <typename T>
+__global__ void coarse_assemble_kernel(int n, const T* __restrict__ A, const int* __restrict__ fidx,
+                                       int nf, double* __restrict__ dense) {
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  int ed[4];
+  elem_edges(n, e, ed);
+  for (int r = 0; r < 8; ++r) {
+    const int fr = fidx[ed[r / 2]];
+    if (fr < 0) continue;
+    for (int c = 0; c < 8; ++c) {
+      const int fc = fidx[ed[c / 2]];
+      if (fc < 0) continue;
+      atomicAdd(&dense[(size_t)(fr * 2 + (r & 1)) * nf + fc * 2 + (c & 1)],
+                (double)A[(size_t)pk_any(r, c) * nE + e]);
+    }
+  }
+}
+
+__global__ void coarse_factor_kernel(int nf, double* __restrict__ M, int* __restrict__ err) {
+  __shared__ double dinv;
+  for (int k = 0; k < nf; ++k) {
+    if (threadIdx.x == 0) {
+      double d = M[(size_t)k * nf + k];
+      if (!(d > 0.0)) {
+        atomicOr(err, 8);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      M[(size_t)k * nf + k] = d;
+      dinv = 1.0 / d;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) M[(size_t)i * nf + k] *= dinv;
+    __syncthreads();
+    const int m = nf - k - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) M[(size_t)i * nf + j] -= M[(size_t)i * nf + k] * M[(size_t)j * nf + k];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void coarse_solve_kernel(int n, const int* __restrict__ fidx, int nf,
+                                    const double* __restrict__ L, const T* __restrict__ r,
+                                    T* __restrict__ e, double* __restrict__ w) {
+  const int nedge = 2 * n * (n + 1);
+  for (int ed = threadIdx.x; ed < nedge; ed += blockDim.x) {
+    const int f = fidx[ed];
+    if (f >= 0) {
+      w[f * 2] = (double)r[ed];
+      w[f * 2 + 1] = (double)r[(size_t)nedge + ed];
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < nf; ++k) {           // forward: L z = b
+    const double zk = w[k] / L[(size_t)k * nf + k];
+    __syncthreads();
+    if (threadIdx.x == 0) w[k] = zk;
+    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) w[i] -= L[(size_t)i * nf + k] * zk;
+    __syncthreads();
+  }
+  for (int k = nf - 1; k >= 0; --k) {      // backward: L^T x = z
+    const double xk = w[k] / L[(size_t)k * nf + k];
+    __syncthreads();
+    if (threadIdx.x == 0) w[k] = xk;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) w[i] -= L[(size_t)k * nf + i] * xk;
+    __syncthreads();
+  }
+  for (int ed = threadIdx.x; ed < nedge; ed += blockDim.x) {
+    const int f = fidx[ed];
+    e[ed] = f >= 0 ? (T)w[f * 2] : T(0);
+    e[(size_t)nedge + ed] = f >= 0 ? (T)w[f * 2 + 1] : T(0);
+  }
+}
+
+// ------------------------------------------------------------ vector ops
+__global__ void dot_partial_kernel(int64_t len, const double* __restrict__ a,
+                                   const double* __restrict__ b, double* __restrict__ partial) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void dot_final_kernel(int nparts, const double* __restrict__ partial, double* out) {
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <typename T>
+__global__ void mask_kernel(int n, int nd, T* __restrict__ x) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge || !bnd_edge(n, edge)) return;
+  for (int k = 0; k < nd; ++k) x[(size_t)k * nedge + edge] = T(0);
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(int64_t len, const A* __restrict__ in, B* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (B)in[i];
+}
+
+// scal layout: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 beta, 5 rr
+__global__ void cg_update_kernel(int64_t len, const double* __restrict__ scal, double* __restrict__ x,
+                                 double* __restrict__ r, const double* __restrict__ p,
+                                 const double* __restrict__ Ap) {
+  const double alpha = scal[2];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * Ap[i];
+  }
+}
+
+__global__ void cg_direction_kernel(int64_t len, const double* __restrict__ scal,
+                                    const double* __restrict__ z, double* __restrict__ p) {
+  const double beta = scal[4];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+__global__ void axpby_kernel(int64_t len, double a, const double* __restrict__ x, double b,
+                             double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void cg_scalars_kernel(double* scal, int stage) {
+  if (stage == 0) {            // alpha = rz / pAp
+    scal[2] = scal[0] / scal[1];
+  } else {                     // beta = rz_new / rz, rz = rz_new
+    scal[4] = scal[3] / scal[0];
+    scal[0] = scal[3];
+  }
+}
+
+__global__ void copy_boundary_kernel(int n, int nd, const double* __restrict__ gD,
+                                     double* __restrict__ lam) {
+  const int nedge = 2 * n * (n + 1);
+  const int edge = blockIdx.x * blockDim.x + threadIdx.x;
+  if (edge >= nedge) return;
+  const bool b = bnd_edge(n, edge);
+  for (int k = 0; k < nd; ++k) {
+    const size_t ix = (size_t)k * nedge + edge;
+    lam[ix] = b ? (gD ? gD[ix] : 0.0) : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void unpack_kernel(int nl, int nE, const T* __restrict__ Ap, double* __restrict__ full) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  for (int r = 0; r < nl; ++r)
+    for (int c = 0; c < nl; ++c) full[(size_t)(r * nl + c) * nE + e] = (double)Ap[(size_t)pk_any(r, c) * nE + e];
+}
+
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+#define ND_DISPATCH(nd, MACRO)  \
+  switch (nd) {                 \
+    case 2: MACRO(2); break;    \
+    case 3: MACRO(3); break;    \
+    case 4: MACRO(4); break;    \
+    case 5: MACRO(5); break;    \
+    case 6: MACRO(6); break;    \
+    case 7: MACRO(7); break;    \
+    case 8: MACRO(8); break;    \
+    case 9: MACRO(9); break;    \
+    default: break;             \
+  }
+
+template <typename T>
+void launch_matvec(cudaStream_t s, int n, int nd, const T* A, const T* x, T* y, T alpha) {
+#define MV(ND) launch_matvec_nd<T, ND>(s, n, A, x, y, alpha)
+  ND_DISPATCH(nd, MV)
+#undef MV
+}
+
+template <typename T>
+void launch_bj_blocks(cudaStream_t s, int n, int nd, const T* A, T* Dinv, int* err) {
+#define BJ(ND) launch_bj_blocks_nd<T, ND>(s, n, A, Dinv, err)
+  ND_DISPATCH(nd, BJ)
+#undef BJ
+}
+
+template <typename T>
+void launch_bj_update(cudaStream_t s, int n, int nd, const T* Dinv, const T* r, T* y, T* e,
+                      T omega, int first) {
+#define BU(ND) launch_bj_update_nd<T, ND>(s, n, Dinv, r, y, e, omega, first)
+  ND_DISPATCH(nd, BU)
+#undef BU
+}
+
+template <typename T>
+void launch_pcoarsen(cudaStream_t s, int nE, int ndf, const T* Af, T* Ac) {
+  pcoarsen_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nE, ndf, Af, Ac);
+}
+
+static void upload_jc() {
+  static bool done = false;
+  if (done) return;
+  double J[2][2][2];
+  child_injection(J);
+  cudaMemcpyToSymbol(c_Jc, J, sizeof(J));
+  done = true;
+}
+
+template <typename T>
+void launch_agglomerate(cudaStream_t s, int nc, const T* Af, T* Ac, T* AIIinv, T* Y, T* Pi,
+                        int* err) {
+  upload_jc();
+  agglomerate_kernel<T><<<nblk(nc * nc, 64), 64, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
+}
+
+template <typename T>
+void launch_local_correction(cudaStream_t s, int nc, const T* AIIinv, const T* Y, const T* r,
+                             T* e) {
+  local_correction_kernel<T><<<nblk(nc * nc, 128), 128, 0, s>>>(nc, AIIinv, Y, r, e);
+}
+
+template <typename T>
+void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc) {
+  upload_jc();
+  const int nedc = 2 * nc * (nc + 1);
+  restrict_h_kernel<T><<<nblk(nedc, 128), 128, 0, s>>>(nc, Pi, r, y, rc);
+}
+
+template <typename T>
+void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y) {
+  upload_jc();
+  const int tot = nc * nc + 2 * nc * (nc + 1);
+  prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(nc, Pi, ec, e, y);
+}
+
+template <typename T>
+void launch_restrict_p(cudaStream_t s, int n, int nd, const T* r, T* y, T* rc) {
+  const int ne = 2 * n * (n + 1);
+  restrict_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd, r, y, rc);
+}
+
+template <typename T>
+void launch_prolong_p(cudaStream_t s, int n, int nd, const T* ec, T* e) {
+  (void)nd;
+  const int ne = 2 * n * (n + 1);
+  prolong_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, ec, e);
+}
+
+template <typename T>
+void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
+                            double* dense) {
+  cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)nf * nf, s);
+  coarse_assemble_kernel<T><<<nblk(n * n, 64), 64, 0, s>>>(n, A, freeidx, nf, dense);
+}
+
+void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
+  coarse_factor_kernel<<<1, 1024, 0, s>>>(nf, dense, err);
+}
+
+template <typename T>
+void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, int nf, const double* L,
+                         const T* r, T* e, double* work) {
+  coarse_solve_kernel<T><<<1, 256, 0, s>>>(n, freeidx, nf, L, r, e, work);
+}
+
+void launch_dot(cudaStream_t s, int64_t len, const double* a, const double* b, double* partial,
+                double* out) {
+  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(len, a, b, partial);
+  dot_final_kernel<<<1, 1024, 0, s>>>(kDotBlocks, partial, out);
+}
+
+template <typename T>
+void launch_mask(cudaStream_t s, int n, int nd, T* x) {
+  const int ne = 2 * n * (n + 1);
+  mask_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd, x);
+}
+
+template <typename T>
+void launch_unpack(cudaStream_t s, int nl, int nE, const T* Ap, double* full) {
+  unpack_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nl, nE, Ap, full);
+}
+
+template <typename A, typename B>
+void launch_convert(cudaStream_t s, int64_t len, const A* in, B* out) {
+  int blocks = nblk(len, 256);
+  if (blocks > 4 * 152 * 4) blocks = 4 * 152 * 4;
+  convert_kernel<A, B><<<blocks, 256, 0, s>>>(len, in, out);
+}
+
+void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, double* x, double* r,
+                      const double* p, const double* Ap) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  cg_update_kernel<<<blocks, 256, 0, s>>>(len, scal, x, r, p, Ap);
+}
+
+void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const double* z,
+                         double* p) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  cg_direction_kernel<<<blocks, 256, 0, s>>>(len, scal, z, p);
+}
+
+void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  axpby_kernel<<<blocks, 256, 0, s>>>(len, a, x, b, y);
+}
+
+void launch_cg_scalars(cudaStream_t s, double* scal, int stage) {
+  cg_scalars_kernel<<<1, 1, 0, s>>>(scal, stage);
+}
+
+void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam) {
+  const int ne = 2 * n * (n + 1);
+  copy_boundary_kernel<<<nblk(ne, 128), 128, 0, s>>>(n, nd, gD, lam);
+}
+
+// explicit instantiations
+#define INST(T)                                                                                 \
+  template void launch_matvec<T>(cudaStream_t, int, int, const T*, const T*, T*, T);            \
+  template void launch_bj_blocks<T>(cudaStream_t, int, int, const T*, T*, int*);                \
+  template void launch_bj_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T, int); \
+  template void launch_pcoarsen<T>(cudaStream_t, int, int, const T*, T*);                       \
+  template void launch_agglomerate<T>(cudaStream_t, int, const T*, T*, T*, T*, T*, int*);       \
+  template void launch_local_correction<T>(cudaStream_t, int, const T*, const T*, const T*, T*); \
+  template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);            \
+  template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);             \
+  template void launch_restrict_p<T>(cudaStream_t, int, int, const T*, T*, T*);                 \
+  template void launch_prolong_p<T>(cudaStream_t, int, int, const T*, T*);                      \
+  template void launch_coarse_assemble<T>(cudaStream_t, int, const T*, const int*, int, double*); \
+  template void launch_coarse_solve<T>(cudaStream_t, int, const int*, int, const double*,       \
+                                       const T*, T*, double*);                                  \
+  template void launch_mask<T>(cudaStream_t, int, int, T*);                                     \
+  template void launch_unpack<T>(cudaStream_t, int, int, const T*, double*);
+INST(double)
+INST(float)
+#undef INST
+template void launch_convert<double, float>(cudaStream_t, int64_t, const double*, float*);
+template void launch_convert<float, double>(cudaStream_t, int64_t, const float*, double*);
+template void launch_convert<double, double>(cudaStream_t, int64_t, const double*, double*);
+
+}  // namespace hdgmg

@@ -1,0 +1,241 @@
+"""Thin ctypes binding of the hdgmg C ABI (include/hdgmg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libhdgmg.so``.  Device buffers are torch tensors (float64, CUDA,
+contiguous); the library runs on torch's current CUDA stream.  If the library
+has not been built, loading raises -- there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libhdgmg.so")
+
+TAU_CONST, TAU_OVER_H = 0, 1
+LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
+KRYLOV_NONE, KRYLOV_CG = 0, 1
+PREC_FP64, PREC_FP32 = 0, 1
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
+          -5: "EBREAKDOWN", -6: "ETIMEOUT"}
+
+EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
+            "hdgmg_run_host", "hdgmg_num_levels", "hdgmg_level_shape",
+            "hdgmg_copy_element_matrices", "hdgmg_apply_operator", "hdgmg_apply_vcycle",
+            "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy"]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("tau_mode", ctypes.c_int32), ("tau_c", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("coarsest_n", ctypes.c_int32), ("m_fine", ctypes.c_int32),
+                ("m_growth", ctypes.c_int32), ("m_max", ctypes.c_int32),
+                ("local_corr", ctypes.c_int32), ("omega", ctypes.c_double),
+                ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("precision", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
+                ("t_solve_ms", ctypes.c_double), ("n_levels", ctypes.c_int32),
+                ("trace_dofs", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class HdgmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"hdgmg {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load the in-tree library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "paper_1811_09909_gb300.build.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.hdgmg_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.hdgmg_default_opts.restype = None
+    lib.hdgmg_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Problem), ctypes.POINTER(Opts), P]
+    lib.hdgmg_setup.argtypes = [P, P]
+    lib.hdgmg_solve.argtypes = [P, I32, P, P, P, P, P, ctypes.POINTER(Info)]
+    lib.hdgmg_run_host.argtypes = [P, P, P, P, P, P, P, ctypes.POINTER(Info)]
+    lib.hdgmg_num_levels.argtypes = [P, ctypes.POINTER(I32)]
+    lib.hdgmg_level_shape.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]
+    lib.hdgmg_copy_element_matrices.argtypes = [P, I32, P]
+    lib.hdgmg_apply_operator.argtypes = [P, I32, P, P]
+    lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
+    lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
+    lib.hdgmg_last_error.argtypes = []
+    lib.hdgmg_last_error.restype = ctypes.c_char_p
+    lib.hdgmg_destroy.argtypes = [P]
+    lib.hdgmg_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("hdgmg_default_opts", "hdgmg_last_error", "hdgmg_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise HdgmgError(status, _lib.hdgmg_last_error().decode())
+
+
+def default_opts(**kw):
+    lib = load()
+    o = Opts()
+    lib.hdgmg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expects contiguous CUDA tensors"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """numpy array (float64, C-contiguous) or pinned torch CPU tensor -> pointer."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """One HDG trace problem on the GPU.
+
+    n, p, domain, tau as in hdgmg_problem; options as keyword arguments of
+    hdgmg_opts (coarsest_n, m_fine, m_growth, m_max, local_corr, omega,
+    krylov, max_it, rtol, precision)."""
+
+    def __init__(self, n, p, tau_mode=TAU_OVER_H, tau_c=1.0, domain=(0.0, 1.0, 0.0, 1.0),
+                 stream=None, **opts):
+        import torch
+        lib = load()
+        self.torch = torch
+        self.n, self.p = n, p
+        self.nd = p + 1
+        self.nv = (p + 1) ** 2
+        self.n_edges = 2 * n * (n + 1)
+        prob = Problem(n, p, domain[0], domain[1], domain[2], domain[3], tau_mode, tau_c)
+        self.opts = default_opts(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        _check(lib.hdgmg_create(ctypes.byref(ctx), ctypes.byref(prob), ctypes.byref(self.opts),
+                                ctypes.c_void_p(stream.cuda_stream)))
+        self.ctx = ctx
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.hdgmg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- main calls -------------------------------------------------------
+    def setup(self, log_kappa):
+        _check(self.lib.hdgmg_setup(self.ctx, _ptr(log_kappa)))
+
+    def solve(self, f, gD=None, want_u=True, want_q=True):
+        """f [nrhs][nv][E] (or [nv][E]); returns (lam, u, q, info)."""
+        torch = self.torch
+        single = f.dim() == 2
+        if single:
+            f = f.unsqueeze(0)
+            if gD is not None:
+                gD = gD.unsqueeze(0)
+        nrhs = f.shape[0]
+        dev = f.device
+        lam = torch.empty((nrhs, self.nd, self.n_edges), dtype=torch.float64, device=dev)
+        u = torch.empty((nrhs, self.nv, self.n * self.n), dtype=torch.float64, device=dev) if want_u else None
+        q = torch.empty((nrhs, 2, self.nv, self.n * self.n), dtype=torch.float64, device=dev) if want_q else None
+        info = Info()
+        st = self.lib.hdgmg_solve(self.ctx, nrhs, _ptr(f), _ptr(gD), _ptr(lam), _ptr(u), _ptr(q),
+                                  ctypes.byref(info))
+        if st not in (0, -4):
+            _check(st)
+        if single:
+            lam = lam[0]
+            u = u[0] if u is not None else None
+            q = q[0] if q is not None else None
+        return lam, u, q, info
+
+    def solve_status(self, f, gD, lam, u, q):
+        """Raw call on preallocated outputs; returns (status, info)."""
+        info = Info()
+        nrhs = 1 if f.dim() == 2 else f.shape[0]
+        st = self.lib.hdgmg_solve(self.ctx, nrhs, _ptr(f), _ptr(gD), _ptr(lam), _ptr(u), _ptr(q),
+                                  ctypes.byref(info))
+        return st, info
+
+    def run_host(self, log_kappa, f, gD, lam, u, q):
+        """End-to-end call on host buffers (numpy arrays or pinned tensors)."""
+        info = Info()
+        st = self.lib.hdgmg_run_host(self.ctx, _hptr(log_kappa), _hptr(f), _hptr(gD), _hptr(lam),
+                                     _hptr(u), _hptr(q), ctypes.byref(info))
+        if st not in (0, -4):
+            _check(st)
+        return st, info
+
+    # -- inspection ---------------------------------------------------------
+    def num_levels(self):
+        k = ctypes.c_int32()
+        _check(self.lib.hdgmg_num_levels(self.ctx, ctypes.byref(k)))
+        return k.value
+
+    def level_shape(self, level):
+        n, nd = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.hdgmg_level_shape(self.ctx, level, ctypes.byref(n), ctypes.byref(nd)))
+        return n.value, nd.value
+
+    def element_matrices(self, level=0):
+        n, nd = self.level_shape(level)
+        nl = 4 * nd
+        out = self.torch.empty((nl, nl, n * n), dtype=self.torch.float64, device="cuda")
+        _check(self.lib.hdgmg_copy_element_matrices(self.ctx, level, _ptr(out)))
+        return out
+
+    def apply_operator(self, level, x):
+        y = self.torch.empty_like(x)
+        _check(self.lib.hdgmg_apply_operator(self.ctx, level, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_vcycle(self, r):
+        e = self.torch.empty_like(r)
+        _check(self.lib.hdgmg_apply_vcycle(self.ctx, _ptr(r), _ptr(e)))
+        return e
+
+    def condensed_rhs(self, f, gD=None):
+        b = self.torch.empty((self.nd, self.n_edges), dtype=self.torch.float64, device="cuda")
+        _check(self.lib.hdgmg_condensed_rhs(self.ctx, _ptr(f), _ptr(gD), _ptr(b)))
+        return b

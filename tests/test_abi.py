@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/hdgmg.h declares, and rejects bad arguments before
+touching the GPU.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hdgmg.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hdgmg_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1811_09909_gb300 import build, hdgmg
+    if not os.path.exists(hdgmg.LIB_PATH):
+        build.build()
+    return hdgmg.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("hdgmg_create", "hdgmg_setup", "hdgmg_solve", "hdgmg_destroy",
+                     "hdgmg_last_error", "hdgmg_run_host", "hdgmg_apply_vcycle"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_1811_09909_gb300 import hdgmg
+    assert sorted(hdgmg.EXPORTED) == sorted(n for n in _declared())
+
+
+def test_default_options(lib):
+    from paper_1811_09909_gb300 import hdgmg
+    o = hdgmg.default_opts()
+    assert (o.coarsest_n, o.m_fine, o.m_growth, o.m_max) == (2, 1, 2, 0)
+    assert o.local_corr == hdgmg.LC_BOTH and o.krylov == hdgmg.KRYLOV_CG
+    assert o.omega == 1.0 and o.rtol == 1e-10 and o.max_it == 200
+    assert o.precision == hdgmg.PREC_FP64
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(p=0), "p must"), (dict(p=9), "p must"), (dict(n=1), "n must"),
+    (dict(n=12, coarsest=2), "halve"), (dict(tau_c=-1.0), "tau_c"),
+])
+def test_create_rejects_bad_arguments(lib, kw, msg):
+    from paper_1811_09909_gb300 import hdgmg
+    n = kw.get("n", 16)
+    p = kw.get("p", 2)
+    prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0))
+    o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2))
+    ctx = ctypes.c_void_p()
+    st = lib.hdgmg_create(ctypes.byref(ctx), ctypes.byref(prob), ctypes.byref(o), None)
+    assert st == -1
+    assert ctx.value is None
+    assert msg in lib.hdgmg_last_error().decode()
+
+
+def test_null_arguments(lib):
+    assert lib.hdgmg_create(None, None, None, None) == -1
+    assert lib.hdgmg_setup(None, None) == -1
+    assert lib.hdgmg_solve(None, 1, None, None, None, None, None, None) == -1
+    lib.hdgmg_destroy(None)
