@@ -100,6 +100,8 @@ typedef struct {
   double t_solve_ms;      /* device time of the last hdgmg_solve             */
   int32_t n_levels;
   int64_t trace_dofs;     /* interior trace unknowns 2 n (n-1) (p+1)         */
+  int64_t kernel_launches; /* kernels run by the last setup + solve (graph
+                              nodes counted once per replay)                 */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

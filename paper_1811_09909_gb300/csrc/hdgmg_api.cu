@@ -10,6 +10,14 @@
 
 using namespace hdgmg;
 
+#include <atomic>
+
+namespace hdgmg {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace hdgmg
+
 namespace {
 thread_local std::string g_last_error;
 
@@ -60,6 +68,15 @@ struct hdgmg_ctx {
   bool setup_done = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double t_setup_ms = 0.0;
+  // PCG loop as one CUDA graph with a device-evaluated while condition
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cg_graph = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  int* it_dev = nullptr;
+  int* it_h = nullptr;
+  double* init_h = nullptr;
+  long long cg_body_launches = 0;
+  long long launches_setup = 0, launches_solve = 0, capture_launches = 0;
 
   template <typename T>
   cudaError_t alloc(T** p_, size_t count) {
@@ -213,6 +230,68 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   return check_launch("condensed right-hand side");
 }
 
+// while-condition of the PCG graph: stop on convergence, NaN or max_it
+__global__ void cg_check_kernel(cudaGraphConditionalHandle h, const double* __restrict__ scal,
+                                int* __restrict__ it, int max_it, double tol2) {
+  const int k = ++(*it);
+  const double rr = scal[5], bb = scal[6];
+  const bool done = !(rr > tol2 * bb) || k >= max_it;
+  if (done) cudaGraphSetConditional(h, 0);
+}
+
+// One PCG iteration (reordered so that the test closes the body):
+//   z = B r; beta = (r.z)/rz; p = z + beta p; alpha = (r.z)/(p.Ap);
+//   x += alpha p; r -= alpha Ap; test ||r||^2 <= rtol^2 ||b||^2.
+void cg_body(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  apply_B(c, c->r, c->z);
+  launch_dot(s, len, c->r, c->z, c->partial, c->scal + 3);
+  launch_cg_scalars(s, c->scal, 1);
+  launch_cg_direction(s, len, c->scal, c->z, c->pv);
+  apply_A64(c, c->pv, c->Ap);
+  launch_dot(s, len, c->pv, c->Ap, c->partial, c->scal + 1);
+  launch_cg_scalars(s, c->scal, 0);
+  launch_cg_update(s, len, c->scal, c->x, c->r, c->pv, c->Ap);
+  launch_dot(s, len, c->r, c->r, c->partial, c->scal + 5);
+  note_launch();
+  cg_check_kernel<<<1, 1, 0, s>>>(h, c->scal, c->it_dev, c->opts.max_it,
+                                   c->opts.rtol * c->opts.rtol);
+}
+
+hdgmg_status build_cg_graph(hdgmg_ctx* c) {
+  if (c->cg_exec) return HDGMG_OK;
+  if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(cudaGraphCreate(&g, 0));
+  c->cg_graph = g;
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t saved = c->stream;
+  c->stream = c->cap_stream;
+  const long long l0 = launch_count();
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+  cg_body(c, h);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &captured);
+  c->stream = saved;
+  if (ce != cudaSuccess)
+    return fail(HDGMG_ECUDA, std::string("capture of the PCG loop: ") + cudaGetErrorString(ce));
+  c->cg_body_launches = launch_count() - l0;
+  c->capture_launches += c->cg_body_launches;    // captured, not executed
+  CUDA_TRY(cudaGraphInstantiate(&c->cg_exec, g, 0));
+  return HDGMG_OK;
+}
+
 hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* lam_out,
                        double* u, double* q, hdgmg_info* info) {
   cudaStream_t s = c->stream;
@@ -229,27 +308,26 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     conv = true;
     if (!std::isfinite(bb)) breakdown = true;
   } else if (o.krylov == HDGMG_KRYLOV_CG) {
-    // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle)
+    // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle), the
+    // whole iteration loop replayed as one CUDA graph
+    STATUS_TRY(build_cg_graph(c));
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    apply_B(c, c->r, c->z);
-    CUDA_TRY(cudaMemcpyAsync(c->pv, c->z, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    launch_dot(s, len, c->r, c->z, c->partial, c->scal + 0);
-    conv = false;
-    for (it = 1; it <= o.max_it; ++it) {
-      apply_A64(c, c->pv, c->Ap);
-      launch_dot(s, len, c->pv, c->Ap, c->partial, c->scal + 1);
-      launch_cg_scalars(s, c->scal, 0);
-      launch_cg_update(s, len, c->scal, c->x, c->r, c->pv, c->Ap);
-      const double rr = dot_sync(c, c->r, c->r);
-      rel = std::sqrt(rr) / nb;
-      if (!std::isfinite(rr)) { breakdown = true; break; }
-      if (rel <= o.rtol) { conv = true; break; }
-      apply_B(c, c->r, c->z);
-      launch_dot(s, len, c->r, c->z, c->partial, c->scal + 3);
-      launch_cg_scalars(s, c->scal, 1);
-      launch_cg_direction(s, len, c->scal, c->z, c->pv);
-    }
-    if (it > o.max_it) it = o.max_it;
+    CUDA_TRY(cudaMemsetAsync(c->pv, 0, sizeof(double) * len, s));
+    CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int), s));
+    c->init_h[0] = 1.0;      // rz of the previous iteration (p = 0 makes beta irrelevant)
+    c->init_h[1] = bb;
+    CUDA_TRY(cudaMemcpyAsync(c->scal + 0, &c->init_h[0], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scal + 6, &c->init_h[1], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(c->cg_exec, s));
+    CUDA_TRY(cudaMemcpyAsync(c->it_h, c->it_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scal_h + 5, c->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    it = *c->it_h;
+    c->launches_solve += c->cg_body_launches * it;
+    const double rr = c->scal_h[5];
+    rel = std::sqrt(rr) / nb;
+    breakdown = !std::isfinite(rr);
+    conv = !breakdown && rel <= o.rtol;
   } else {
     // multigrid as a fixed-point solver: x <- x + B_N (b - A x)  (Sec. 3.6)
     conv = false;
@@ -320,6 +398,11 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->err_h) cudaFreeHost(c->err_h);
   if (c->scal_h) cudaFreeHost(c->scal_h);
+  if (c->init_h) cudaFreeHost(c->init_h);
+  if (c->it_h) cudaFreeHost(c->it_h);
+  if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+  if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -455,6 +538,9 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(c->alloc(&c->partial, kDotBlocks));
   CTRY(c->alloc(&c->scal, 8));
   CTRY(cudaMallocHost(&c->scal_h, sizeof(double) * 8));
+  CTRY(cudaMallocHost(&c->init_h, sizeof(double) * 8));
+  CTRY(cudaMallocHost(&c->it_h, sizeof(int) * 2));
+  CTRY(c->alloc(&c->it_dev, 2));
   // coarsest level: free-dof numbering of its interior edges
   {
     const Level& Lc = c->levels.back();
@@ -490,6 +576,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   if (!c || !log_kappa) return fail(HDGMG_EINVAL, "NULL argument");
   cudaStream_t s = c->stream;
   const int nE = c->n * c->n;
+  const long long l0 = launch_count();
   CUDA_TRY(cudaEventRecord(c->ev0, s));
   CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
@@ -509,6 +596,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->t_setup_ms = ms;
+  c->launches_setup = launch_count() - l0;
   if (c->err_h[0]) {
     c->setup_done = false;
     char buf[128];
@@ -527,6 +615,8 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
   const size_t nE = (size_t)c->n * c->n;
   const int64_t len = c->fine_len();
   hdgmg_status last = HDGMG_OK;
+  const long long l0 = launch_count(), cap0 = c->capture_launches;
+  c->launches_solve = 0;
   CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
   for (int k = 0; k < nrhs; ++k) {
     hdgmg_status st = solve_one(c, f + (size_t)k * c->nv * nE, g_D ? g_D + (size_t)k * len : nullptr,
@@ -545,6 +635,8 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }
+  c->launches_solve += launch_count() - l0 - (c->capture_launches - cap0);
+  if (info) info->kernel_launches = c->launches_setup + c->launches_solve;
   if (last != HDGMG_OK) return last;
   return HDGMG_OK;
 }

@@ -150,6 +150,10 @@ void launch_cg_scalars(cudaStream_t s, double* scal, int stage);
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y);
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam);
 
+// host-side count of kernel launches issued by the library (all threads)
+void note_launch();
+long long launch_count();
+
 constexpr int kDotBlocks = 608;   // 4 x 152 SMs; fixed for a deterministic sum
 
 }  // namespace hdgmg

@@ -229,6 +229,7 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
     attr_set = true;
   }
   const int blocks = (nE + wpb - 1) / wpb;
+  note_launch();
   condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
                                                  logk, tau_mode, tau_c, hmin, A, Lfac, err);
 }
@@ -240,6 +241,7 @@ void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)nv * threads;
   cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  note_launch();
   rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, logk, tau_mode, tau_c, hmin,
                                           Lfac, f, b);
 }
@@ -251,6 +253,7 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const do
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
   cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  note_launch();
   recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
                                               ref.Cy, logk, tau_mode, tau_c, hmin, Lfac, f, lam,
                                               u, q);

@@ -157,17 +157,20 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
 
 template <typename T, int ND>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha) {
+  note_launch();
   matvec_kernel<T, ND><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
 }
 
 template <typename T, int ND>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err) {
+  note_launch();
   bj_blocks_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, A, Dinv, err);
 }
 
 template <typename T, int ND>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first) {
+  note_launch();
   bj_update_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega, first);
 }
 

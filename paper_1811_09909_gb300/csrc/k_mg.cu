@@ -586,6 +586,7 @@ void launch_bj_update(cudaStream_t s, int n, int nd, const T* Dinv, const T* r, 
 
 template <typename T>
 void launch_pcoarsen(cudaStream_t s, int nE, int ndf, const T* Af, T* Ac) {
+  note_launch();
   pcoarsen_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nE, ndf, Af, Ac);
 }
 
@@ -602,12 +603,14 @@ template <typename T>
 void launch_agglomerate(cudaStream_t s, int nc, const T* Af, T* Ac, T* AIIinv, T* Y, T* Pi,
                         int* err) {
   upload_jc();
+  note_launch();
   agglomerate_kernel<T><<<nblk(nc * nc, 64), 64, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
 }
 
 template <typename T>
 void launch_local_correction(cudaStream_t s, int nc, const T* AIIinv, const T* Y, const T* r,
                              T* e) {
+  note_launch();
   local_correction_kernel<T><<<nblk(nc * nc, 128), 128, 0, s>>>(nc, AIIinv, Y, r, e);
 }
 
@@ -615,6 +618,7 @@ template <typename T>
 void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc) {
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
+  note_launch();
   restrict_h_kernel<T><<<nblk(nedc, 128), 128, 0, s>>>(nc, Pi, r, y, rc);
 }
 
@@ -622,12 +626,14 @@ template <typename T>
 void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y) {
   upload_jc();
   const int tot = nc * nc + 2 * nc * (nc + 1);
+  note_launch();
   prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(nc, Pi, ec, e, y);
 }
 
 template <typename T>
 void launch_restrict_p(cudaStream_t s, int n, int nd, const T* r, T* y, T* rc) {
   const int ne = 2 * n * (n + 1);
+  note_launch();
   restrict_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd, r, y, rc);
 }
 
@@ -635,6 +641,7 @@ template <typename T>
 void launch_prolong_p(cudaStream_t s, int n, int nd, const T* ec, T* e) {
   (void)nd;
   const int ne = 2 * n * (n + 1);
+  note_launch();
   prolong_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, ec, e);
 }
 
@@ -642,33 +649,40 @@ template <typename T>
 void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
                             double* dense) {
   cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)nf * nf, s);
+  note_launch();
   coarse_assemble_kernel<T><<<nblk(n * n, 64), 64, 0, s>>>(n, A, freeidx, nf, dense);
 }
 
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
+  note_launch();
   coarse_factor_kernel<<<1, 1024, 0, s>>>(nf, dense, err);
 }
 
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, int nf, const double* L,
                          const T* r, T* e, double* work) {
+  note_launch();
   coarse_solve_kernel<T><<<1, 256, 0, s>>>(n, freeidx, nf, L, r, e, work);
 }
 
 void launch_dot(cudaStream_t s, int64_t len, const double* a, const double* b, double* partial,
                 double* out) {
+  note_launch();
   dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(len, a, b, partial);
+  note_launch();
   dot_final_kernel<<<1, 1024, 0, s>>>(kDotBlocks, partial, out);
 }
 
 template <typename T>
 void launch_mask(cudaStream_t s, int n, int nd, T* x) {
   const int ne = 2 * n * (n + 1);
+  note_launch();
   mask_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd, x);
 }
 
 template <typename T>
 void launch_unpack(cudaStream_t s, int nl, int nE, const T* Ap, double* full) {
+  note_launch();
   unpack_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nl, nE, Ap, full);
 }
 
@@ -676,6 +690,7 @@ template <typename A, typename B>
 void launch_convert(cudaStream_t s, int64_t len, const A* in, B* out) {
   int blocks = nblk(len, 256);
   if (blocks > 4 * 152 * 4) blocks = 4 * 152 * 4;
+  note_launch();
   convert_kernel<A, B><<<blocks, 256, 0, s>>>(len, in, out);
 }
 
@@ -683,6 +698,7 @@ void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, double* x
                       const double* p, const double* Ap) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
+  note_launch();
   cg_update_kernel<<<blocks, 256, 0, s>>>(len, scal, x, r, p, Ap);
 }
 
@@ -690,21 +706,25 @@ void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const 
                          double* p) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
+  note_launch();
   cg_direction_kernel<<<blocks, 256, 0, s>>>(len, scal, z, p);
 }
 
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
+  note_launch();
   axpby_kernel<<<blocks, 256, 0, s>>>(len, a, x, b, y);
 }
 
 void launch_cg_scalars(cudaStream_t s, double* scal, int stage) {
+  note_launch();
   cg_scalars_kernel<<<1, 1, 0, s>>>(scal, stage);
 }
 
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam) {
   const int ne = 2 * n * (n + 1);
+  note_launch();
   copy_boundary_kernel<<<nblk(ne, 128), 128, 0, s>>>(n, nd, gD, lam);
 }
 
