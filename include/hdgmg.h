@@ -64,7 +64,7 @@ typedef enum {
 enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min */
 enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
 enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1 };
-enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1 };
+enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
 
@@ -89,11 +89,18 @@ typedef struct {
   int32_t krylov;         /* NONE = MG as fixed-point solver, CG; CG         */
   int32_t max_it;         /* outer iterations; 200                           */
   double rtol;            /* ||g - A lambda||_2 / ||g||_2 target; 1e-10      */
-  int32_t precision;      /* V-cycle arithmetic: FP64 or FP32; FP64          */
+  int32_t precision;      /* FP64: PCG in FP64 with the FP64 V-cycle.
+                             FP32: PCG in FP64 (FP64 operator, residual and
+                             dot products) preconditioned by the FP32 V-cycle.
+                             FP32_IR: iterative refinement -- FP64 residual of
+                             the FP64 operator, inner FP32 PCG with the FP32
+                             V-cycle on the normalised residual; FP64         */
+  double inner_rtol;      /* FP32_IR only: inner PCG tolerance per refinement
+                             step, in (0,1); 1e-5                             */
 } hdgmg_opts;
 
 typedef struct {
-  int32_t iters;          /* outer iterations = V-cycle applications        */
+  int32_t iters;          /* Krylov iterations = V-cycle applications       */
   int32_t converged;      /* 1 if rel_res <= rtol                            */
   double rel_res;         /* ||g - A lambda|| / ||g||, recomputed in FP64    */
   double t_setup_ms;      /* device time of the last hdgmg_setup             */
@@ -102,6 +109,7 @@ typedef struct {
   int64_t trace_dofs;     /* interior trace unknowns 2 n (n-1) (p+1)         */
   int64_t kernel_launches; /* kernels run by the last setup + solve (graph
                               nodes counted once per replay)                 */
+  int32_t refinements;    /* FP32_IR: outer FP64 refinement steps, else 0    */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

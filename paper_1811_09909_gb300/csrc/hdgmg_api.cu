@@ -57,12 +57,15 @@ struct hdgmg_ctx {
   int* err_h = nullptr;
   // coarsest level
   int* freeidx = nullptr;
+  int* fedge = nullptr;
   int nf = 0;
-  double* dense = nullptr;
-  double* cwork = nullptr;
+  double* dense = nullptr;     // coarsest operator, then its Cholesky factor
+  double* clinv = nullptr;     // L^-1
+  double* cinv = nullptr;      // A_1^-1
   // outer Krylov vectors (finest level, FP64)
   double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *b = nullptr;
   double *lam = nullptr, *partial = nullptr, *scal = nullptr, *scal_h = nullptr;
+  unsigned* counter = nullptr;   // last-block counter of the fused reductions
   // host-call staging
   double *st_f = nullptr, *st_g = nullptr, *st_l = nullptr, *st_u = nullptr, *st_q = nullptr;
   bool setup_done = false;
@@ -77,6 +80,17 @@ struct hdgmg_ctx {
   double* init_h = nullptr;
   long long cg_body_launches = 0;
   long long launches_setup = 0, launches_solve = 0, capture_launches = 0;
+  // P1 tail of the hierarchy run by the fused single-block V-cycle kernel
+  int tail_start = -1;
+  // mixed form: inner FP32 PCG (vectors xs, ps, Aps; r and z are level 0's)
+  float *xs = nullptr, *ps = nullptr, *Aps = nullptr;
+  double* scal32 = nullptr;
+  cudaGraph_t cg32_graph = nullptr;
+  cudaGraphExec_t cg32_exec = nullptr;
+  long long cg32_body_launches = 0;
+  int refinements = 0;
+  TailParams<float> tp32;
+  TailParams<double> tp64;
 
   template <typename T>
   cudaError_t alloc(T** p_, size_t count) {
@@ -96,6 +110,102 @@ namespace {
 template <typename T> LevelData<T>& ld(Level& L);
 template <> LevelData<double>& ld<double>(Level& L) { return L.d64; }
 template <> LevelData<float>& ld<float>(Level& L) { return L.d32; }
+template <typename T> TailParams<T>& tailp(hdgmg_ctx* c);
+template <> TailParams<double>& tailp<double>(hdgmg_ctx* c) { return c->tp64; }
+template <> TailParams<float>& tailp<float>(hdgmg_ctx* c) { return c->tp32; }
+
+// Choose the fused tail: the longest run of P1 levels at the bottom of the
+// hierarchy with n <= tail_n whose vectors and operators fit in shared memory.
+template <typename T>
+size_t tail_layout(hdgmg_ctx* c, int start, const std::vector<int>& staged, bool stage_inv,
+                   TailParams<T>* P) {
+  const int last = (int)c->levels.size() - 1;
+  size_t off = 0;                                   // in T units
+  auto take = [&](size_t count) {
+    size_t o = off;
+    off += (count + 3) / 4 * 4;                     // keep 16-byte alignment for floats
+    return o;
+  };
+  for (int k = start; k <= last; ++k) {
+    const Level& L = c->levels[k];
+    TailLevel<T> t;
+    t.n = L.n;
+    t.m = L.m;
+    t.nEdge = L.nEdge;
+    t.voff = (int)take(6 * (size_t)L.nEdge);
+    t.staged = (k < last && staged[k]) ? 1 : 0;
+    if (t.staged) {
+      const size_t nC = (size_t)L.nE / 4;
+      t.a_off = (int)take(36 * (size_t)L.nE);
+      t.dinv_off = (int)take(3 * (size_t)L.nEdge);
+      t.aii_off = (int)take(36 * nC);
+      t.y_off = (int)take(128 * nC);
+      t.pi_off = (int)take(64 * nC);
+    }
+    if (P) P->lv[k - start] = t;
+  }
+  size_t bytes = (off * sizeof(T) + 15) / 16 * 16;
+  const size_t ainv_off = bytes;
+  if (stage_inv) bytes += sizeof(double) * (size_t)c->nf * c->nf;
+  const size_t w_off = bytes;
+  bytes += sizeof(double) * (size_t)(c->nf + 2);
+  if (P) {
+    P->ainv_off = stage_inv ? (int)ainv_off : -1;
+    P->w_off = (int)w_off;
+    P->smem_bytes = (int)bytes;
+  }
+  return bytes;
+}
+
+// Choose the fused tail: P1 levels at the bottom of the hierarchy with
+// n <= tail_n.  The level vectors always live in shared memory; the level
+// operators are staged there too, from the coarsest level upwards, while they
+// fit -- larger levels read them from L2.
+template <typename T>
+void plan_tail(hdgmg_ctx* c, int tail_n) {
+  const int last = (int)c->levels.size() - 1;
+  const size_t cap = (size_t)kTailMaxSmem;
+  std::vector<int> staged(c->levels.size(), 0);
+  const bool stage_inv = tail_layout<T>(c, last, staged, true, nullptr) <= cap;
+  if (tail_layout<T>(c, last, staged, stage_inv, nullptr) > cap) {
+    c->tail_start = -1;                      // coarsest level alone: standalone solve
+    return;
+  }
+  int start = last;
+  while (start - 1 >= 0) {
+    const int k = start - 1;
+    const Level& L = c->levels[k];
+    if (L.nd != 2 || L.transfer != 2 || L.n > tail_n) break;
+    if (last - k + 1 > kMaxTail) break;
+    staged[k] = 1;
+    if (tail_layout<T>(c, k, staged, stage_inv, nullptr) > cap) {
+      staged[k] = 0;
+      if (tail_layout<T>(c, k, staged, stage_inv, nullptr) > cap) break;
+    }
+    start = k;
+  }
+  c->tail_start = start;
+  TailParams<T>& P = tailp<T>(c);
+  P.nlev = last - start + 1;
+  tail_layout<T>(c, start, staged, stage_inv, &P);
+  for (int k = start; k <= last; ++k) {
+    LevelData<T>& D = ld<T>(c->levels[k]);
+    TailLevel<T>& t = P.lv[k - start];
+    t.A = D.A;
+    t.Dinv = D.Dinv;
+    t.AIIinv = D.AIIinv;
+    t.Y = D.Y;
+    t.Pi = D.Pi;
+  }
+  P.r_in = ld<T>(c->levels[start]).r;
+  P.e_out = ld<T>(c->levels[start]).e;
+  P.Ainv = c->cinv;
+  P.fidx = c->freeidx;
+  P.fedge = c->fedge;
+  P.nf = c->nf;
+  P.omega = (T)c->opts.omega;
+  P.lc = c->opts.local_corr;
+}
 
 hdgmg_status check_launch(const char* where) {
   cudaError_t e = cudaGetLastError();
@@ -110,8 +220,12 @@ void vcycle(hdgmg_ctx* c, int l) {
   Level& L = c->levels[l];
   LevelData<T>& D = ld<T>(L);
   const int last = (int)c->levels.size() - 1;
+  if (l == c->tail_start) {                                 // fused P1 tail + B_1 = A_1^-1
+    launch_vcycle_tail<T>(s, tailp<T>(c));
+    return;
+  }
   if (l == last) {                                          // B_1 = A_1^-1
-    launch_coarse_solve<T>(s, L.n, c->freeidx, c->nf, c->dense, D.r, D.e, c->cwork);
+    launch_coarse_solve<T>(s, L.n, c->freeidx, c->fedge, c->nf, c->cinv, D.r, D.e);
     return;
   }
   const T omega = (T)c->opts.omega;
@@ -153,7 +267,7 @@ void apply_B(hdgmg_ctx* c, const double* r, double* z) {
   cudaStream_t s = c->stream;
   Level& L0 = c->levels[0];
   const int64_t len = c->fine_len();
-  if (c->opts.precision == HDGMG_PREC_FP32) {
+  if (c->opts.precision != HDGMG_PREC_FP64) {
     launch_convert<double, float>(s, len, r, L0.d32.r);
     vcycle<float>(c, 0);
     launch_convert<float, double>(s, len, L0.d32.e, z);
@@ -216,6 +330,7 @@ hdgmg_status setup_hierarchy(hdgmg_ctx* c) {
   Level& Lc = c->levels[nl - 1];
   launch_coarse_assemble<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
   launch_coarse_factor(s, c->nf, c->dense, c->err);
+  launch_coarse_inverse(s, c->nf, c->dense, c->clinv, c->cinv);
   return check_launch("hierarchy set-up");
 }
 
@@ -230,41 +345,48 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   return check_launch("condensed right-hand side");
 }
 
-// while-condition of the PCG graph: stop on convergence, NaN or max_it
-__global__ void cg_check_kernel(cudaGraphConditionalHandle h, const double* __restrict__ scal,
-                                int* __restrict__ it, int max_it, double tol2) {
-  const int k = ++(*it);
-  const double rr = scal[5], bb = scal[6];
-  const bool done = !(rr > tol2 * bb) || k >= max_it;
-  if (done) cudaGraphSetConditional(h, 0);
-}
-
 // One PCG iteration (reordered so that the test closes the body):
 //   z = B r; beta = (r.z)/rz; p = z + beta p; alpha = (r.z)/(p.Ap);
-//   x += alpha p; r -= alpha Ap; test ||r||^2 <= rtol^2 ||b||^2.
-void cg_body(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+//   x += alpha p; r -= alpha Ap; test ||r||^2 <= tol^2 ||b||^2.
+// FP64 form: A = the FP64 fine operator, B = the V-cycle.  FP32 form (inner
+// iteration of the refinement): A = the FP32 copy, vectors FP32, scalars and
+// dot products FP64; r and z are the V-cycle's own level-0 buffers.
+void cg_body64(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
   apply_B(c, c->r, c->z);
-  launch_dot(s, len, c->r, c->z, c->partial, c->scal + 3);
-  launch_cg_scalars(s, c->scal, 1);
-  launch_cg_direction(s, len, c->scal, c->z, c->pv);
-  apply_A64(c, c->pv, c->Ap);
-  launch_dot(s, len, c->pv, c->Ap, c->partial, c->scal + 1);
-  launch_cg_scalars(s, c->scal, 0);
-  launch_cg_update(s, len, c->scal, c->x, c->r, c->pv, c->Ap);
-  launch_dot(s, len, c->r, c->r, c->partial, c->scal + 5);
-  note_launch();
-  cg_check_kernel<<<1, 1, 0, s>>>(h, c->scal, c->it_dev, c->opts.max_it,
-                                   c->opts.rtol * c->opts.rtol);
+  launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);
+  launch_cg_direction_zero<double>(s, len, c->scal, c->z, c->pv, c->Ap);
+  launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->pv, c->Ap, 1.0);
+  launch_dot_fused<double>(s, len, c->pv, c->Ap, c->partial, c->counter, c->scal, 0);
+  launch_cg_update_test<double>(s, len, c->scal, c->x, c->r, c->pv, c->Ap, c->partial, c->counter,
+                                h, c->it_dev, c->opts.max_it, c->opts.rtol * c->opts.rtol);
 }
 
-hdgmg_status build_cg_graph(hdgmg_ctx* c) {
-  if (c->cg_exec) return HDGMG_OK;
+void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  Level& L0 = c->levels[0];
+  float* rs = L0.d32.r;
+  float* zs = L0.d32.e;
+  vcycle<float>(c, 0);
+  launch_dot_fused<float>(s, len, rs, zs, c->partial, c->counter, c->scal32, 1);
+  launch_cg_direction_zero<float>(s, len, c->scal32, zs, c->ps, c->Aps);
+  launch_matvec<float>(s, c->n, c->p + 1, L0.d32.A, c->ps, c->Aps, 1.0f);
+  launch_dot_fused<float>(s, len, c->ps, c->Aps, c->partial, c->counter, c->scal32, 0);
+  launch_cg_update_test<float>(s, len, c->scal32, c->xs, rs, c->ps, c->Aps, c->partial, c->counter,
+                               h, c->it_dev, c->opts.max_it,
+                               c->opts.inner_rtol * c->opts.inner_rtol);
+}
+
+hdgmg_status build_loop_graph(hdgmg_ctx* c, void (*body)(hdgmg_ctx*, cudaGraphConditionalHandle),
+                              cudaGraph_t* graph_out, cudaGraphExec_t* exec_out,
+                              long long* body_launches) {
+  if (*exec_out) return HDGMG_OK;
   if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaGraphCreate(&g, 0));
-  c->cg_graph = g;
+  *graph_out = g;
   cudaGraphConditionalHandle h;
   CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np = {};
@@ -274,21 +396,66 @@ hdgmg_status build_cg_graph(hdgmg_ctx* c) {
   np.conditional.size = 1;
   cudaGraphNode_t node;
   CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
   cudaStream_t saved = c->stream;
   c->stream = c->cap_stream;
   const long long l0 = launch_count();
-  CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+  CUDA_TRY(cudaStreamBeginCaptureToGraph(c->cap_stream, bodyg, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeRelaxed));
-  cg_body(c, h);
+  body(c, h);
   cudaGraph_t captured = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &captured);
   c->stream = saved;
   if (ce != cudaSuccess)
     return fail(HDGMG_ECUDA, std::string("capture of the PCG loop: ") + cudaGetErrorString(ce));
-  c->cg_body_launches = launch_count() - l0;
-  c->capture_launches += c->cg_body_launches;    // captured, not executed
-  CUDA_TRY(cudaGraphInstantiate(&c->cg_exec, g, 0));
+  *body_launches = launch_count() - l0;
+  c->capture_launches += *body_launches;    // captured, not executed
+  CUDA_TRY(cudaGraphInstantiate(exec_out, g, 0));
+  return HDGMG_OK;
+}
+
+// FP64 outer iteration with the FP32 PCG as the inner solver (iterative
+// refinement): r = b - A x in FP64, solve A d = r / ||r|| in FP32 to
+// inner_rtol, x += ||r|| d.  Returns the number of inner iterations.
+hdgmg_status refine_solve(hdgmg_ctx* c, double nb, int* iters, int* outer, double* rel,
+                          bool* conv, bool* breakdown) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const hdgmg_opts& o = c->opts;
+  STATUS_TRY(build_loop_graph(c, cg_body32, &c->cg32_graph, &c->cg32_exec, &c->cg32_body_launches));
+  Level& L0 = c->levels[0];
+  *iters = 0;
+  *outer = 0;
+  *conv = false;
+  *breakdown = false;
+  for (;;) {
+    CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_matvec<double>(s, c->n, c->p + 1, L0.d64.A, c->x, c->r, -1.0);
+    launch_dot<double>(s, len, c->r, c->r, c->partial, c->scal + 7);
+    CUDA_TRY(cudaMemcpyAsync(c->scal_h + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double rr = c->scal_h[7];
+    *rel = std::sqrt(rr) / nb;
+    if (!std::isfinite(rr)) { *breakdown = true; break; }
+    if (*rel <= o.rtol) { *conv = true; break; }
+    if (*iters >= o.max_it || !(rr > 0.0)) break;
+    // inner FP32 PCG on the normalised residual
+    launch_scale_to_f32(s, len, c->r, c->scal + 7, L0.d32.r);
+    CUDA_TRY(cudaMemsetAsync(c->xs, 0, sizeof(float) * len, s));
+    CUDA_TRY(cudaMemsetAsync(c->ps, 0, sizeof(float) * len, s));
+    CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int), s));
+    c->init_h[2] = 1.0;
+    c->init_h[3] = 1.0;
+    CUDA_TRY(cudaMemcpyAsync(c->scal32 + 0, &c->init_h[2], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scal32 + 6, &c->init_h[3], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(c->cg32_exec, s));
+    launch_add_f32(s, len, c->scal + 7, c->xs, c->x);
+    CUDA_TRY(cudaMemcpyAsync(c->it_h, c->it_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *iters += *c->it_h;
+    c->launches_solve += c->cg32_body_launches * (*c->it_h);
+    ++*outer;
+  }
   return HDGMG_OK;
 }
 
@@ -297,6 +464,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
   const hdgmg_opts& o = c->opts;
+  c->refinements = 0;
   STATUS_TRY(build_rhs(c, f, gD));
   CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * len, s));
   const double bb = dot_sync(c, c->b, c->b);
@@ -307,10 +475,14 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   if (!(nb > 0.0)) {
     conv = true;
     if (!std::isfinite(bb)) breakdown = true;
+  } else if (o.krylov == HDGMG_KRYLOV_CG && o.precision == HDGMG_PREC_FP32_IR) {
+    int outer = 0;
+    STATUS_TRY(refine_solve(c, nb, &it, &outer, &rel, &conv, &breakdown));
+    c->refinements = outer;
   } else if (o.krylov == HDGMG_KRYLOV_CG) {
     // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle), the
     // whole iteration loop replayed as one CUDA graph
-    STATUS_TRY(build_cg_graph(c));
+    STATUS_TRY(build_loop_graph(c, cg_body64, &c->cg_graph, &c->cg_exec, &c->cg_body_launches));
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemsetAsync(c->pv, 0, sizeof(double) * len, s));
     CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int), s));
@@ -366,6 +538,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     info->iters = it;
     info->converged = conv ? 1 : 0;
     info->rel_res = rel;
+    info->refinements = c->refinements;
   }
   if (breakdown) return fail(HDGMG_EBREAKDOWN, "NaN/Inf in the outer iteration");
   if (!conv) return fail(HDGMG_ENOCONV, "outer iteration did not reach rtol");
@@ -388,6 +561,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->max_it = 200;
   o->rtol = 1e-10;
   o->precision = HDGMG_PREC_FP64;
+  o->inner_rtol = 1e-5;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -402,6 +576,8 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   if (c->it_h) cudaFreeHost(c->it_h);
   if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
   if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
+  if (c->cg32_exec) cudaGraphExecDestroy(c->cg32_exec);
+  if (c->cg32_graph) cudaGraphDestroy(c->cg32_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
@@ -429,8 +605,9 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.m_fine < 1 || o.m_growth < 1 || o.m_max < 0) return fail(HDGMG_EINVAL, "bad smoothing schedule");
   if (o.local_corr < 0 || o.local_corr > 2) return fail(HDGMG_EINVAL, "unknown local_corr");
   if (o.krylov < 0 || o.krylov > 1) return fail(HDGMG_EINVAL, "unknown krylov");
-  if (o.precision < 0 || o.precision > 1) return fail(HDGMG_EINVAL, "unknown precision");
+  if (o.precision < 0 || o.precision > 2) return fail(HDGMG_EINVAL, "unknown precision");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
+  if (!(o.inner_rtol > 0.0) || !(o.inner_rtol < 1.0)) return fail(HDGMG_EINVAL, "inner_rtol must be in (0,1)");
   int nn = P.n;
   while (nn > o.coarsest_n) {
     if (nn % 2) return fail(HDGMG_EINVAL, "n must halve evenly down to coarsest_n");
@@ -509,7 +686,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
       if (o.m_max > 0 && m > o.m_max) m = o.m_max;
     }
   }
-  const bool fp32 = o.precision == HDGMG_PREC_FP32;
+  const bool fp32 = o.precision != HDGMG_PREC_FP64;
   for (size_t l = 0; l < c->levels.size(); ++l) {
     Level& L = c->levels[l];
     hdgmg_status st;
@@ -536,7 +713,15 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(c->alloc(&c->b, len));
   CTRY(c->alloc(&c->lam, len));
   CTRY(c->alloc(&c->partial, kDotBlocks));
+  CTRY(c->alloc(&c->counter, 4));
+  CTRY(cudaMemset(c->counter, 0, sizeof(unsigned) * 4));
   CTRY(c->alloc(&c->scal, 8));
+  CTRY(c->alloc(&c->scal32, 8));
+  if (fp32) {
+    CTRY(c->alloc(&c->xs, len));
+    CTRY(c->alloc(&c->ps, len));
+    CTRY(c->alloc(&c->Aps, len));
+  }
   CTRY(cudaMallocHost(&c->scal_h, sizeof(double) * 8));
   CTRY(cudaMallocHost(&c->init_h, sizeof(double) * 8));
   CTRY(cudaMallocHost(&c->it_h, sizeof(int) * 2));
@@ -561,9 +746,19 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     c->nf = 2 * nfe;
     CTRY(c->alloc(&c->freeidx, fidx.size()));
     CTRY(cudaMemcpy(c->freeidx, fidx.data(), sizeof(int) * fidx.size(), cudaMemcpyHostToDevice));
+    std::vector<int> fedge(nfe > 0 ? nfe : 1, 0);
+    for (int e = 0; e < Lc.nEdge; ++e)
+      if (fidx[e] >= 0) fedge[fidx[e]] = e;
+    CTRY(c->alloc(&c->fedge, fedge.size()));
+    CTRY(cudaMemcpy(c->fedge, fedge.data(), sizeof(int) * fedge.size(), cudaMemcpyHostToDevice));
     CTRY(c->alloc(&c->dense, (size_t)c->nf * c->nf));
-    CTRY(c->alloc(&c->cwork, (size_t)c->nf + 1));
+    CTRY(c->alloc(&c->clinv, (size_t)c->nf * c->nf));
+    CTRY(c->alloc(&c->cinv, (size_t)c->nf * c->nf));
   }
+  if (fp32)
+    plan_tail<float>(c, 32);
+  else
+    plan_tail<double>(c, 16);
   CTRY(cudaEventCreate(&c->ev0));
   CTRY(cudaEventCreate(&c->ev1));
   CTRY(cudaDeviceSynchronize());
@@ -584,7 +779,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   launch_condense(s, c->refd, c->p, nE, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                   L0.d64.A, c->Lfac, c->err);
   STATUS_TRY(check_launch("condensation"));
-  if (c->opts.precision == HDGMG_PREC_FP32) {
+  if (c->opts.precision != HDGMG_PREC_FP64) {
     launch_convert<double, float>(s, (int64_t)L0.nsym * L0.nE, L0.d64.A, L0.d32.A);
     STATUS_TRY(setup_hierarchy<float>(c));
   } else {

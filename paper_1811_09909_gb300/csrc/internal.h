@@ -124,17 +124,53 @@ void launch_restrict_p(cudaStream_t s, int n, int nd, const T* r, T* y, T* rc);
 template <typename T>
 void launch_prolong_p(cudaStream_t s, int n, int nd, const T* ec, T* e);
 
+// fused V-cycle over the P1 tail of the hierarchy (one thread block)
+constexpr int kMaxTail = 8;
+constexpr int kTailMaxSmem = 224 * 1024;
+template <typename T>
+struct TailLevel {
+  int n = 0, m = 1, nEdge = 0;
+  // shared-memory offsets (T units) of [r|e|y] and of the staged operators
+  int voff = 0, a_off = 0, dinv_off = 0, aii_off = 0, y_off = 0, pi_off = 0;
+  int staged = 0;              // operators copied to shared memory (else read from L2)
+  const T* A = nullptr;
+  const T* Dinv = nullptr;
+  const T* AIIinv = nullptr;
+  const T* Y = nullptr;
+  const T* Pi = nullptr;
+};
+template <typename T>
+struct TailParams {
+  int nlev = 0;
+  TailLevel<T> lv[kMaxTail];
+  const T* r_in = nullptr;      // right-hand side of the first tail level (global)
+  T* e_out = nullptr;           // its correction (global)
+  const double* Ainv = nullptr; // coarsest dense inverse (FP64)
+  const int* fidx = nullptr;    // coarsest edge -> free edge number (-1: Dirichlet)
+  const int* fedge = nullptr;   // free edge number -> coarsest edge
+  int nf = 0;
+  T omega = T(1);
+  int lc = 0;
+  int ainv_off = 0, w_off = 0;  // byte offsets of the staged inverse (-1: read from global)
+                                // and of the workspace
+  int smem_bytes = 0;
+};
+template <typename T>
+void launch_vcycle_tail(cudaStream_t s, const TailParams<T>& P);
+
 // coarsest level: dense FP64 Cholesky of the interior operator
 template <typename T>
 void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
                             double* dense);
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err);
+void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, double* Ainv);
 template <typename T>
-void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, int nf, const double* L,
-                         const T* r, T* e, double* work);
+void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
+                         const double* Ainv, const T* r, T* e);
 
 // vector kernels (FP64 unless templated)
-void launch_dot(cudaStream_t s, int64_t len, const double* a, const double* b, double* partial,
+template <typename T>
+void launch_dot(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
                 double* out);
 template <typename T>
 void launch_mask(cudaStream_t s, int n, int nd, T* x);   // zero Dirichlet entries
@@ -142,10 +178,27 @@ template <typename T>
 void launch_unpack(cudaStream_t s, int nl, int nE, const T* Ap, double* full);
 template <typename A, typename B>
 void launch_convert(cudaStream_t s, int64_t len, const A* in, B* out);
-void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, double* x, double* r,
-                      const double* p, const double* Ap);
-void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const double* z,
-                         double* p);
+template <typename T>
+void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, T* x, T* r, const T* p,
+                      const T* Ap);
+template <typename T>
+void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p);
+// fused PCG kernels (scal layout: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 beta,
+// 5 rr, 6 reference norm^2); counter: a zeroed unsigned reset by the kernel
+template <typename T>
+void launch_dot_fused(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
+                      unsigned* counter, double* scal, int mode);
+template <typename T>
+void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p,
+                              T* Ap);
+template <typename T>
+void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r, const T* p,
+                           const T* Ap, double* partial, unsigned* counter,
+                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2);
+// FP64 -> FP32 with 1/sqrt(*scale), and y += sqrt(*scale) x (FP32 -> FP64)
+void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
+                         float* out);
+void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y);
 void launch_cg_scalars(cudaStream_t s, double* scal, int stage);
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y);
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam);

@@ -193,12 +193,10 @@ __global__ void agglomerate_kernel(int nc, const T* __restrict__ Af, T* __restri
 // ------------------------------------------------- K8 local correction
 // e_I <- e_I + A_II^-1 (r - A e)_I = A_II^-1 r_I + Y e_B
 template <typename T>
-__global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
-                                        const T* __restrict__ Y, const T* __restrict__ r,
-                                        T* __restrict__ e) {
+__device__ __forceinline__ void local_correction_item(int nc, const T* __restrict__ AIIinv,
+                                                      const T* __restrict__ Y, const T* r, T* e,
+                                                      int C) {
   const int nC = nc * nc;
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= nC) return;
   const int J = C / nc, I = C - J * nc;
   const int n = 2 * nc;
   const int nedge = 2 * n * (n + 1);
@@ -227,6 +225,14 @@ __global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
   }
 }
 
+template <typename T>
+__global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
+                                        const T* __restrict__ Y, const T* __restrict__ r,
+                                        T* __restrict__ e) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C < nc * nc) local_correction_item<T>(nc, AIIinv, Y, r, e, C);
+}
+
 __device__ __forceinline__ int coarse_v(int nc, int I, int J) { return J * (nc + 1) + I; }
 __device__ __forceinline__ int coarse_h(int nc, int I, int J) { return nc * (nc + 1) + J * nc + I; }
 
@@ -234,11 +240,9 @@ __device__ __forceinline__ int coarse_h(int nc, int I, int J) { return nc * (nc 
 // r_c = J^T s_B + Pi^T s_I (Q_{k-1} of eq. n_1_Qk with Pi^T = -J^T A_BI A_II^-1
 // for symmetric A), s = r - y, y = A e.  One thread per coarse edge.
 template <typename T>
-__global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ r,
-                                  const T* __restrict__ y, T* __restrict__ rc) {
+__device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi, const T* r,
+                                                const T* y, T* rc, int E) {
   const int nedc = 2 * nc * (nc + 1);
-  const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E >= nedc) return;
   if (bnd_edge(nc, E)) {
     rc[E] = T(0);
     rc[(size_t)nedc + E] = T(0);
@@ -289,15 +293,21 @@ __global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __r
   rc[(size_t)nedc + E] = acc[1];
 }
 
+template <typename T>
+__global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ r,
+                                  const T* __restrict__ y, T* __restrict__ rc) {
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E < 2 * nc * (nc + 1)) restrict_h_item<T>(nc, Pi, r, y, rc, E);
+}
+
 // -------------------------------------------------------- K11 prolongation
 // e_B += J e_c (per coarse edge, its two halves), e_I += Pi e_c(C) (per
 // macro-element); every fine edge is touched exactly once, where y is reset.
 template <typename T>
-__global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ ec,
-                                 T* __restrict__ e, T* __restrict__ y) {
+__device__ __forceinline__ void prolong_h_item(int nc, const T* __restrict__ Pi, const T* ec,
+                                               T* e, T* y, int t) {
   const int nC = nc * nc, nedc = 2 * nc * (nc + 1), nvc = nc * (nc + 1);
   const int n = 2 * nc, nedge = 2 * n * (n + 1);
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nC) {
     const int C = t, J = C / nc, I = C - J * nc;
     const int ce[4] = {coarse_v(nc, I, J), coarse_v(nc, I + 1, J), coarse_h(nc, I, J),
@@ -341,6 +351,13 @@ __global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __re
       y[ix] = T(0);
     }
   }
+}
+
+template <typename T>
+__global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ ec,
+                                 T* __restrict__ e, T* __restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nc * nc + 2 * nc * (nc + 1)) prolong_h_item<T>(nc, Pi, ec, e, y, t);
 }
 
 // ------------------------------------------------- p-transfer (J_N, J_N^T)
@@ -410,48 +427,234 @@ __global__ void coarse_factor_kernel(int nf, double* __restrict__ M, int* __rest
   }
 }
 
+// Coarsest level: the dense FP64 inverse A_1^-1 = L^-T L^-1 is formed once at
+// set-up from the Cholesky factor; each V-cycle applies it as one dense
+// matrix-vector product (no sequential triangular sweeps).
+__global__ void chol_linv_kernel(int nf, const double* __restrict__ L, double* __restrict__ Li) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;      // column of L^-1
+  if (j >= nf) return;
+  for (int i = 0; i < j; ++i) Li[(size_t)i * nf + j] = 0.0;
+  for (int i = j; i < nf; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    for (int k = j; k < i; ++k) s -= L[(size_t)i * nf + k] * Li[(size_t)k * nf + j];
+    Li[(size_t)i * nf + j] = s / L[(size_t)i * nf + i];
+  }
+}
+
+__global__ void chol_gram_kernel(int nf, const double* __restrict__ Li, double* __restrict__ Ainv) {
+  const int i = blockIdx.x;                                  // row of A^-1
+  for (int j = threadIdx.x; j < nf; j += blockDim.x) {
+    double s = 0.0;
+    for (int k = (i > j ? i : j); k < nf; ++k) s += Li[(size_t)k * nf + i] * Li[(size_t)k * nf + j];
+    Ainv[(size_t)i * nf + j] = s;
+  }
+}
+
+// e = A_1^-1 r on the coarsest level's interior dofs; w: nf doubles visible
+// to the whole block
 template <typename T>
-__global__ void coarse_solve_kernel(int n, const int* __restrict__ fidx, int nf,
-                                    const double* __restrict__ L, const T* __restrict__ r,
-                                    T* __restrict__ e, double* __restrict__ w) {
+__device__ __forceinline__ void coarse_apply_block(int n, const int* __restrict__ fidx,
+                                                   const int* __restrict__ fedge, int nf,
+                                                   const double* Ainv, const T* r, T* e,
+                                                   double* w) {
   const int nedge = 2 * n * (n + 1);
   for (int ed = threadIdx.x; ed < nedge; ed += blockDim.x) {
     const int f = fidx[ed];
     if (f >= 0) {
       w[f * 2] = (double)r[ed];
       w[f * 2 + 1] = (double)r[(size_t)nedge + ed];
+    } else {
+      e[ed] = T(0);
+      e[(size_t)nedge + ed] = T(0);
     }
   }
   __syncthreads();
-  for (int k = 0; k < nf; ++k) {           // forward: L z = b
-    const double zk = w[k] / L[(size_t)k * nf + k];
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nf; ++j) s += Ainv[(size_t)i * nf + j] * w[j];
+    e[(size_t)(i & 1) * nedge + fedge[i >> 1]] = (T)s;
+  }
+}
+
+template <typename T>
+__global__ void coarse_solve_kernel(int n, const int* __restrict__ fidx, const int* __restrict__ fedge,
+                                    int nf, const double* __restrict__ Ainv, const T* __restrict__ r,
+                                    T* __restrict__ e) {
+  extern __shared__ double cw[];
+  coarse_apply_block<T>(n, fidx, fedge, nf, Ainv, r, e, cw);
+}
+
+// ------------------------------------------- fused V-cycle on the P1 tail
+// P1 (two modes per edge) element matvec y += A x for one element, and the
+// block-Jacobi update of one edge, for the single-block tail kernel.
+template <typename T>
+__device__ __forceinline__ void matvec_p1_item(int n, const T* __restrict__ A, const T* x, T* y,
+                                               int e) {
+  const int nE = n * n, nedge = 2 * n * (n + 1);
+  int ed[4];
+  elem_edges(n, e, ed);
+  T xl[8], yl[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    xl[c] = x[(size_t)(c & 1) * nedge + ed[c >> 1]];
+    yl[c] = T(0);
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+#pragma unroll
+    for (int c = 0; c < r; ++c) {
+      const T a = A[(size_t)pk(r, c) * nE + e];
+      yl[r] += a * xl[c];
+      yl[c] += a * xl[r];
+    }
+    yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
+  }
+#pragma unroll
+  for (int le = 0; le < 4; ++le) {
+    if (bnd_edge(n, ed[le])) continue;
+    atomicAdd(&y[ed[le]], yl[le * 2]);
+    atomicAdd(&y[(size_t)nedge + ed[le]], yl[le * 2 + 1]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void bj_p1_item(int n, const T* __restrict__ Dinv, const T* r, T* y,
+                                           T* e, T omega, bool first, int edge) {
+  const int nedge = 2 * n * (n + 1);
+  if (bnd_edge(n, edge)) return;
+  const T d0 = first ? r[edge] : r[edge] - y[edge];
+  const T d1 = first ? r[nedge + edge] : r[nedge + edge] - y[nedge + edge];
+  if (!first) {
+    y[edge] = T(0);
+    y[nedge + edge] = T(0);
+  }
+  const T a00 = Dinv[edge], a10 = Dinv[(size_t)nedge + edge], a11 = Dinv[(size_t)2 * nedge + edge];
+  const T s0 = a00 * d0 + a10 * d1, s1 = a10 * d0 + a11 * d1;
+  if (first) {
+    e[edge] = omega * s0;
+    e[nedge + edge] = omega * s1;
+  } else {
+    e[edge] += omega * s0;
+    e[nedge + edge] += omega * s1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
+}
+
+// One thread block runs Algorithm 1 on every level of the tail (P1 levels
+// with few macro-elements down to the coarsest).  The level vectors r, e, y
+// and all level operators of the tail are staged into shared memory at the
+// start, and the steps are separated by block barriers instead of kernel
+// launches.
+template <typename T, int NTHR>
+__global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  T* sm = reinterpret_cast<T*>(tail_smem);
+  double* w = reinterpret_cast<double*>(tail_smem + P.w_off);
+  const bool staged_inv = P.ainv_off >= 0;
+  double* ainv_s = reinterpret_cast<double*>(tail_smem + (staged_inv ? P.ainv_off : 0));
+  const double* ainv = staged_inv ? ainv_s : P.Ainv;
+  for (int l = 0; l < P.nlev; ++l) {
+    const TailLevel<T>& L = P.lv[l];
+    T* base = sm + L.voff;
+    for (int i = tid; i < 6 * L.nEdge; i += nth) base[i] = T(0);
+    if (L.staged) {
+      const int nE = L.n * L.n, nC = nE / 4;
+      stage_copy<T>(sm + L.a_off, L.A, 36 * nE);
+      stage_copy<T>(sm + L.dinv_off, L.Dinv, 3 * L.nEdge);
+      stage_copy<T>(sm + L.aii_off, L.AIIinv, 36 * nC);
+      stage_copy<T>(sm + L.y_off, L.Y, 128 * nC);
+      stage_copy<T>(sm + L.pi_off, L.Pi, 64 * nC);
+    }
+  }
+  if (staged_inv) stage_copy<double>(ainv_s, P.Ainv, P.nf * P.nf);
+  __syncthreads();
+  {
+    T* r0 = sm + P.lv[0].voff;
+    for (int i = tid; i < 2 * P.lv[0].nEdge; i += nth) r0[i] = P.r_in[i];
+  }
+  __syncthreads();
+  // down sweep: steps 2-4 of Algorithm 1
+  for (int l = 0; l + 1 < P.nlev; ++l) {
+    const TailLevel<T>& L = P.lv[l];
+    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
+    T* r = sm + L.voff;
+    T* e = r + 2 * ned;
+    T* y = e + 2 * ned;
+    const T* A = L.staged ? sm + L.a_off : L.A;
+    const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
+    const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
+    const T* Yb = L.staged ? sm + L.y_off : L.Y;
+    const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
+    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, true, i);
     __syncthreads();
-    if (threadIdx.x == 0) w[k] = zk;
-    for (int i = k + 1 + threadIdx.x; i < nf; i += blockDim.x) w[i] -= L[(size_t)i * nf + k] * zk;
+    for (int it = 1; it < L.m; ++it) {
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+      __syncthreads();
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, false, i);
+      __syncthreads();
+    }
+    if (P.lc != HDGMG_LC_NONE) {
+      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, AIIinv, Yb, r, e, i);
+      __syncthreads();
+    }
+    for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+    __syncthreads();
+    T* rc = sm + P.lv[l + 1].voff;
+    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Pi, r, y, rc, i);
     __syncthreads();
   }
-  for (int k = nf - 1; k >= 0; --k) {      // backward: L^T x = z
-    const double xk = w[k] / L[(size_t)k * nf + k];
-    __syncthreads();
-    if (threadIdx.x == 0) w[k] = xk;
-    for (int i = threadIdx.x; i < k; i += blockDim.x) w[i] -= L[(size_t)k * nf + i] * xk;
+  {  // B_1 = A_1^-1
+    const TailLevel<T>& L = P.lv[P.nlev - 1];
+    T* r = sm + L.voff;
+    coarse_apply_block<T>(L.n, P.fidx, P.fedge, P.nf, ainv, r, r + 2 * L.nEdge, w);
     __syncthreads();
   }
-  for (int ed = threadIdx.x; ed < nedge; ed += blockDim.x) {
-    const int f = fidx[ed];
-    e[ed] = f >= 0 ? (T)w[f * 2] : T(0);
-    e[(size_t)nedge + ed] = f >= 0 ? (T)w[f * 2 + 1] : T(0);
+  // up sweep: steps 4-6
+  for (int l = P.nlev - 2; l >= 0; --l) {
+    const TailLevel<T>& L = P.lv[l];
+    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
+    T* r = sm + L.voff;
+    T* e = r + 2 * ned;
+    T* y = e + 2 * ned;
+    const T* A = L.staged ? sm + L.a_off : L.A;
+    const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
+    const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
+    const T* Yb = L.staged ? sm + L.y_off : L.Y;
+    const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
+    const T* ec = sm + P.lv[l + 1].voff + 2 * P.lv[l + 1].nEdge;
+    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
+    __syncthreads();
+    if (P.lc == HDGMG_LC_BOTH) {
+      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, AIIinv, Yb, r, e, i);
+      __syncthreads();
+    }
+    for (int it = 0; it < L.m; ++it) {
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+      __syncthreads();
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, false, i);
+      __syncthreads();
+    }
+  }
+  {
+    const T* e0 = sm + P.lv[0].voff + 2 * P.lv[0].nEdge;
+    for (int i = tid; i < 2 * P.lv[0].nEdge; i += nth) P.e_out[i] = e0[i];
   }
 }
 
 // ------------------------------------------------------------ vector ops
-__global__ void dot_partial_kernel(int64_t len, const double* __restrict__ a,
-                                   const double* __restrict__ b, double* __restrict__ partial) {
+template <typename T>
+__global__ void dot_partial_kernel(int64_t len, const T* __restrict__ a,
+                                   const T* __restrict__ b, double* __restrict__ partial) {
   __shared__ double sh[256];
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
-    s += a[i] * b[i];
+    s += (double)a[i] * (double)b[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -489,11 +692,119 @@ __global__ void convert_kernel(int64_t len, const A* __restrict__ in, B* __restr
     out[i] = (B)in[i];
 }
 
+// ---------------------------------------- fused PCG vector kernels
+// Dot products finish in the last block to arrive (fixed reduction order, so
+// the result is deterministic) and apply the scalar recurrences there:
+//   mode 0: scal[1] = p.Ap,     scal[2] = alpha = scal[0] / scal[1]
+//   mode 1: scal[3] = r.z,      scal[4] = beta = scal[3] / scal[0], scal[0] = scal[3]
+//   mode 2: scal[5] = r.r
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// returns true in the last block to finish, after all partials are visible
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return is_last;
+}
+
+__device__ __forceinline__ double sum_partials(const double* partial, int n, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double*)partial)[i];
+  return block_sum(s, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __restrict__ a,
+                                                        const T* __restrict__ b,
+                                                        double* __restrict__ partial,
+                                                        unsigned* __restrict__ counter,
+                                                        double* __restrict__ scal, int mode) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)a[i] * (double)b[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (!last_block(counter)) return;
+  __syncthreads();
+  const double tot = sum_partials(partial, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    if (mode == 0) {
+      scal[1] = tot;
+      scal[2] = scal[0] / tot;
+    } else if (mode == 1) {
+      scal[3] = tot;
+      scal[4] = tot / scal[0];
+      scal[0] = tot;
+    } else {
+      scal[5] = tot;
+    }
+    *counter = 0u;
+  }
+}
+
+// p = z + beta p and Ap = 0
+template <typename T>
+__global__ void cg_direction_zero_kernel(int64_t len, const double* __restrict__ scal,
+                                         const T* __restrict__ z, T* __restrict__ p,
+                                         T* __restrict__ Ap) {
+  const T beta = (T)scal[4];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = z[i] + beta * p[i];
+    Ap[i] = T(0);
+  }
+}
+
+// x += alpha p, r -= alpha Ap, scal[5] = r.r, then the loop test of the
+// graph: stop when r.r <= tol2 * scal[6], on NaN, or after max_it iterations
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_test_kernel(
+    int64_t len, double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
+    const T* __restrict__ p, const T* __restrict__ Ap, double* __restrict__ partial,
+    unsigned* __restrict__ counter, cudaGraphConditionalHandle h, int* __restrict__ it,
+    int max_it, double tol2) {
+  __shared__ double sh[256];
+  const T alpha = (T)scal[2];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const T ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    s += (double)ri * (double)ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (!last_block(counter)) return;
+  __syncthreads();
+  const double rr = sum_partials(partial, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    scal[5] = rr;
+    *counter = 0u;
+    const int k = ++(*it);
+    if (!(rr > tol2 * scal[6]) || k >= max_it) cudaGraphSetConditional(h, 0);
+  }
+}
+
 // scal layout: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 beta, 5 rr
-__global__ void cg_update_kernel(int64_t len, const double* __restrict__ scal, double* __restrict__ x,
-                                 double* __restrict__ r, const double* __restrict__ p,
-                                 const double* __restrict__ Ap) {
-  const double alpha = scal[2];
+template <typename T>
+__global__ void cg_update_kernel(int64_t len, const double* __restrict__ scal, T* __restrict__ x,
+                                 T* __restrict__ r, const T* __restrict__ p,
+                                 const T* __restrict__ Ap) {
+  const T alpha = (T)scal[2];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -501,12 +812,31 @@ __global__ void cg_update_kernel(int64_t len, const double* __restrict__ scal, d
   }
 }
 
+template <typename T>
 __global__ void cg_direction_kernel(int64_t len, const double* __restrict__ scal,
-                                    const double* __restrict__ z, double* __restrict__ p) {
-  const double beta = scal[4];
+                                    const T* __restrict__ z, T* __restrict__ p) {
+  const T beta = (T)scal[4];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
+}
+
+// out = scale * in (FP64 -> FP32), and y += alpha * x (FP32 -> FP64): the
+// hand-over between the FP64 outer and the FP32 inner iteration
+__global__ void scale_to_f32_kernel(int64_t len, const double* __restrict__ in,
+                                    const double* __restrict__ scale, float* __restrict__ out) {
+  const double sc = 1.0 / sqrt(*scale);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)(in[i] * sc);
+}
+
+__global__ void add_f32_kernel(int64_t len, const double* __restrict__ scale,
+                               const float* __restrict__ x, double* __restrict__ y) {
+  const double sc = sqrt(*scale);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += sc * (double)x[i];
 }
 
 __global__ void axpby_kernel(int64_t len, double a, const double* __restrict__ x, double b,
@@ -658,17 +988,39 @@ void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
   coarse_factor_kernel<<<1, 1024, 0, s>>>(nf, dense, err);
 }
 
-template <typename T>
-void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, int nf, const double* L,
-                         const T* r, T* e, double* work) {
+void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, double* Ainv) {
   note_launch();
-  coarse_solve_kernel<T><<<1, 256, 0, s>>>(n, freeidx, nf, L, r, e, work);
+  chol_linv_kernel<<<nblk(nf, 64), 64, 0, s>>>(nf, L, Li);
+  note_launch();
+  chol_gram_kernel<<<nf, 128, 0, s>>>(nf, Li, Ainv);
 }
 
-void launch_dot(cudaStream_t s, int64_t len, const double* a, const double* b, double* partial,
+template <typename T>
+void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
+                         const double* Ainv, const T* r, T* e) {
+  note_launch();
+  coarse_solve_kernel<T><<<1, 256, sizeof(double) * (nf + 1), s>>>(n, freeidx, fedge, nf, Ainv, r, e);
+}
+
+template <typename T>
+void launch_vcycle_tail(cudaStream_t s, const TailParams<T>& P) {
+  // FP64 needs twice the registers per value: half the threads
+  constexpr int NTHR = sizeof(T) == 8 ? 512 : 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(vcycle_tail_kernel<T, NTHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kTailMaxSmem);
+    attr = true;
+  }
+  note_launch();
+  vcycle_tail_kernel<T, NTHR><<<1, NTHR, P.smem_bytes, s>>>(P);
+}
+
+template <typename T>
+void launch_dot(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
                 double* out) {
   note_launch();
-  dot_partial_kernel<<<kDotBlocks, 256, 0, s>>>(len, a, b, partial);
+  dot_partial_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, a, b, partial);
   note_launch();
   dot_final_kernel<<<1, 1024, 0, s>>>(kDotBlocks, partial, out);
 }
@@ -694,20 +1046,61 @@ void launch_convert(cudaStream_t s, int64_t len, const A* in, B* out) {
   convert_kernel<A, B><<<blocks, 256, 0, s>>>(len, in, out);
 }
 
-void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, double* x, double* r,
-                      const double* p, const double* Ap) {
+template <typename T>
+void launch_cg_update(cudaStream_t s, int64_t len, const double* scal, T* x, T* r,
+                      const T* p, const T* Ap) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
   note_launch();
-  cg_update_kernel<<<blocks, 256, 0, s>>>(len, scal, x, r, p, Ap);
+  cg_update_kernel<T><<<blocks, 256, 0, s>>>(len, scal, x, r, p, Ap);
 }
 
-void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const double* z,
-                         double* p) {
+template <typename T>
+void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
   note_launch();
-  cg_direction_kernel<<<blocks, 256, 0, s>>>(len, scal, z, p);
+  cg_direction_kernel<T><<<blocks, 256, 0, s>>>(len, scal, z, p);
+}
+
+template <typename T>
+void launch_dot_fused(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
+                      unsigned* counter, double* scal, int mode) {
+  note_launch();
+  dot_fused_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, a, b, partial, counter, scal, mode);
+}
+
+template <typename T>
+void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p,
+                              T* Ap) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  cg_direction_zero_kernel<T><<<blocks, 256, 0, s>>>(len, scal, z, p, Ap);
+}
+
+template <typename T>
+void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r, const T* p,
+                           const T* Ap, double* partial, unsigned* counter,
+                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2) {
+  note_launch();
+  cg_update_test_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, scal, x, r, p, Ap, partial, counter, h,
+                                                      it, max_it, tol2);
+}
+
+void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
+                         float* out) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  scale_to_f32_kernel<<<blocks, 256, 0, s>>>(len, in, scale, out);
+}
+
+void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  add_f32_kernel<<<blocks, 256, 0, s>>>(len, scale, x, y);
 }
 
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y) {
@@ -741,14 +1134,38 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
   template void launch_restrict_p<T>(cudaStream_t, int, int, const T*, T*, T*);                 \
   template void launch_prolong_p<T>(cudaStream_t, int, int, const T*, T*);                      \
   template void launch_coarse_assemble<T>(cudaStream_t, int, const T*, const int*, int, double*); \
-  template void launch_coarse_solve<T>(cudaStream_t, int, const int*, int, const double*,       \
-                                       const T*, T*, double*);                                  \
+  template void launch_coarse_solve<T>(cudaStream_t, int, const int*, const int*, int,          \
+                                       const double*, const T*, T*);                            \
   template void launch_mask<T>(cudaStream_t, int, int, T*);                                     \
   template void launch_unpack<T>(cudaStream_t, int, int, const T*, double*);
 INST(double)
 INST(float)
 #undef INST
 template void launch_convert<double, float>(cudaStream_t, int64_t, const double*, float*);
+template void launch_vcycle_tail<double>(cudaStream_t, const TailParams<double>&);
+template void launch_dot<double>(cudaStream_t, int64_t, const double*, const double*, double*, double*);
+template void launch_dot_fused<double>(cudaStream_t, int64_t, const double*, const double*, double*,
+                                       unsigned*, double*, int);
+template void launch_dot_fused<float>(cudaStream_t, int64_t, const float*, const float*, double*,
+                                      unsigned*, double*, int);
+template void launch_cg_direction_zero<double>(cudaStream_t, int64_t, const double*, const double*,
+                                               double*, double*);
+template void launch_cg_direction_zero<float>(cudaStream_t, int64_t, const double*, const float*,
+                                              float*, float*);
+template void launch_cg_update_test<double>(cudaStream_t, int64_t, double*, double*, double*,
+                                            const double*, const double*, double*, unsigned*,
+                                            cudaGraphConditionalHandle, int*, int, double);
+template void launch_cg_update_test<float>(cudaStream_t, int64_t, double*, float*, float*,
+                                           const float*, const float*, double*, unsigned*,
+                                           cudaGraphConditionalHandle, int*, int, double);
+template void launch_dot<float>(cudaStream_t, int64_t, const float*, const float*, double*, double*);
+template void launch_cg_update<double>(cudaStream_t, int64_t, const double*, double*, double*,
+                                       const double*, const double*);
+template void launch_cg_update<float>(cudaStream_t, int64_t, const double*, float*, float*,
+                                      const float*, const float*);
+template void launch_cg_direction<double>(cudaStream_t, int64_t, const double*, const double*, double*);
+template void launch_cg_direction<float>(cudaStream_t, int64_t, const double*, const float*, float*);
+template void launch_vcycle_tail<float>(cudaStream_t, const TailParams<float>&);
 template void launch_convert<float, double>(cudaStream_t, int64_t, const float*, double*);
 template void launch_convert<double, double>(cudaStream_t, int64_t, const double*, double*);
 

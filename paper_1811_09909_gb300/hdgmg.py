@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhdgmg.so")
 TAU_CONST, TAU_OVER_H = 0, 1
 LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
 KRYLOV_NONE, KRYLOV_CG = 0, 1
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_IR = 0, 1, 2
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
           -5: "EBREAKDOWN", -6: "ETIMEOUT"}
@@ -37,14 +37,16 @@ class Opts(ctypes.Structure):
                 ("m_growth", ctypes.c_int32), ("m_max", ctypes.c_int32),
                 ("local_corr", ctypes.c_int32), ("omega", ctypes.c_double),
                 ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
-                ("rtol", ctypes.c_double), ("precision", ctypes.c_int32)]
+                ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("t_setup_ms", ctypes.c_double),
                 ("t_solve_ms", ctypes.c_double), ("n_levels", ctypes.c_int32),
-                ("trace_dofs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("trace_dofs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("refinements", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -45,7 +45,7 @@ def test_default_options(lib):
     assert (o.coarsest_n, o.m_fine, o.m_growth, o.m_max) == (2, 1, 2, 0)
     assert o.local_corr == hdgmg.LC_BOTH and o.krylov == hdgmg.KRYLOV_CG
     assert o.omega == 1.0 and o.rtol == 1e-10 and o.max_it == 200
-    assert o.precision == hdgmg.PREC_FP64
+    assert o.precision == hdgmg.PREC_FP64 and o.inner_rtol == 1e-5
 
 
 @pytest.mark.parametrize("kw,msg", [
