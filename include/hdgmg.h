@@ -174,6 +174,24 @@ hdgmg_status hdgmg_copy_element_matrices(hdgmg_ctx* ctx, int32_t level,
 hdgmg_status hdgmg_apply_operator(hdgmg_ctx* ctx, int32_t level,
                                   const double* x, double* y);
 
+/* Same result as hdgmg_apply_operator, for callers that cannot allocate
+ * device memory when they call it: code running while a stream is being
+ * captured into a CUDA graph (cudaMalloc is not allowed there), or programs
+ * whose device memory belongs to another allocator.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   Instead of cudaMalloc'd temporaries it uses one static device array of
+ *   2^20 doubles (8 MiB) that every GPU loading the library reserves until
+ *   the process exits.  Levels with more than 2^20 trace values
+ *   (nd * n_edges) are rejected with HDGMG_EINVAL.
+ *   The first call on a device resolves the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
+ *   All calls share the array: calls whose work overlaps on the GPU (other
+ *   streams, other host threads) race on it.  x, y: as in
+ *   hdgmg_apply_operator.  Returns after the work is complete. */
+hdgmg_status hdgmg_apply_operator_noalloc(hdgmg_ctx* ctx, int32_t level,
+                                          const double* x, double* y);
+
 /* e = B_N r: one V-cycle of Algorithm 1 on the finest level, in the V-cycle
  * precision; r, e device, [p+1][n_edges] FP64 (Dirichlet entries ignored /
  * zero). */

@@ -11,6 +11,7 @@
 using namespace hdgmg;
 
 #include <atomic>
+#include <mutex>
 
 namespace hdgmg {
 static std::atomic<long long> g_launches{0};
@@ -951,3 +952,82 @@ hdgmg_status hdgmg_condensed_rhs(hdgmg_ctx* c, const double* f, const double* g_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of hdgmg_apply_operator.
+//
+// hdgmg_apply_operator takes its temporaries (the copy of x with the
+// Dirichlet entries zeroed, and the FP32 accumulator on FP32 levels) from
+// cudaMalloc on every call.  Some callers cannot allocate device memory at
+// the point where they need the operator: code running while a stream is
+// being captured into a CUDA graph (cudaMalloc is not permitted there), or
+// integrations whose device memory is fully owned by another allocator.  For
+// them the temporaries live in one fixed array that the library reserves in
+// device memory when it is loaded.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 2^20 doubles (8 MiB) on every device that loads the library, held until
+// the process exits.  Shared by all calls: calls whose work overlaps on the
+// GPU (different streams, or different host threads) race on it.
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array for the current device; resolved once
+// per device (the host-side symbol is only a stand-in for it).
+hdgmg_status noalloc_scratch(double** out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(HDGMG_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return HDGMG_OK;
+}
+
+}  // namespace
+
+extern "C" hdgmg_status hdgmg_apply_operator_noalloc(hdgmg_ctx* c, int32_t level, const double* x,
+                                                     double* y) {
+  if (!c || !x || !y) return fail(HDGMG_EINVAL, "NULL argument");
+  if (level < 0 || level >= (int)c->levels.size()) return fail(HDGMG_EINVAL, "level out of range");
+  Level& L = c->levels[level];
+  const int64_t len = (int64_t)L.nd * L.nEdge;
+  if ((size_t)len > kNoAllocScratchDoubles) {
+    char buf[160];
+    snprintf(buf, sizeof(buf),
+             "level %d has %lld trace values; the static scratch holds at most %zu",
+             (int)level, (long long)len, kNoAllocScratchDoubles);
+    return fail(HDGMG_EINVAL, buf);
+  }
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  double* scratch = nullptr;
+  STATUS_TRY(noalloc_scratch(&scratch));
+  cudaStream_t s = c->stream;
+  if (level == 0 || c->opts.precision == HDGMG_PREC_FP64) {
+    double* xm = scratch;                          // fully overwritten below
+    CUDA_TRY(cudaMemcpyAsync(xm, x, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_mask<double>(s, L.n, L.nd, xm);
+    CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * len, s));
+    launch_matvec<double>(s, L.n, L.nd, L.d64.A, xm, y, 1.0);
+  } else {
+    float* xm = reinterpret_cast<float*>(scratch);  // len floats, fully overwritten
+    float* ym = xm + len;                          // len floats, cleared below
+    launch_convert<double, float>(s, len, x, xm);
+    launch_mask<float>(s, L.n, L.nd, xm);
+    CUDA_TRY(cudaMemsetAsync(ym, 0, sizeof(float) * len, s));
+    launch_matvec<float>(s, L.n, L.nd, L.d32.A, xm, ym, 1.0f);
+    launch_convert<float, double>(s, len, ym, y);
+  }
+  STATUS_TRY(check_launch("apply operator (no allocation)"));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return HDGMG_OK;
+}

@@ -22,7 +22,8 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
 EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
             "hdgmg_run_host", "hdgmg_num_levels", "hdgmg_level_shape",
             "hdgmg_copy_element_matrices", "hdgmg_apply_operator", "hdgmg_apply_vcycle",
-            "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy"]
+            "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy",
+            "hdgmg_apply_operator_noalloc"]
 
 
 class Problem(ctypes.Structure):
@@ -81,6 +82,7 @@ def load():
     lib.hdgmg_level_shape.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32)]
     lib.hdgmg_copy_element_matrices.argtypes = [P, I32, P]
     lib.hdgmg_apply_operator.argtypes = [P, I32, P, P]
+    lib.hdgmg_apply_operator_noalloc.argtypes = [P, I32, P, P]
     lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
     lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
     lib.hdgmg_last_error.argtypes = []
