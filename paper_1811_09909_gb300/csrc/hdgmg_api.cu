@@ -53,6 +53,7 @@ struct hdgmg_ctx {
   std::vector<void*> allocs;
   std::vector<Level> levels;
   double* logk = nullptr;
+  double* kap = nullptr;       // exp(log kappa) per element
   double* Lfac = nullptr;
   int* err = nullptr;
   int* err_h = nullptr;
@@ -329,9 +330,11 @@ hdgmg_status setup_hierarchy(hdgmg_ctx* c) {
       launch_agglomerate<T>(s, Lc.n, D.A, Dc.A, D.AIIinv, D.Y, D.Pi, c->err);
   }
   Level& Lc = c->levels[nl - 1];
-  launch_coarse_assemble<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
-  launch_coarse_factor(s, c->nf, c->dense, c->err);
-  launch_coarse_inverse(s, c->nf, c->dense, c->clinv, c->cinv);
+  if (!launch_coarse_setup_smem<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->cinv, c->err)) {
+    launch_coarse_assemble<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
+    launch_coarse_factor(s, c->nf, c->dense, c->err);
+    launch_coarse_inverse(s, c->nf, c->dense, c->clinv, c->cinv);
+  }
   return check_launch("hierarchy set-up");
 }
 
@@ -339,7 +342,7 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
   CUDA_TRY(cudaMemsetAsync(c->b, 0, sizeof(double) * len, s));
-  launch_rhs(s, c->refd, c->p, c->n, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
+  launch_rhs(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
              f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
   if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->lam, c->b, -1.0);
@@ -532,7 +535,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
   if (u || q)
-    launch_recover(s, c->refd, c->p, c->n, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+    launch_recover(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                    c->Lfac, f, lam_out, u, q);
   STATUS_TRY(check_launch("solve"));
   if (info) {
@@ -703,6 +706,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   }
   const int64_t len = c->fine_len();
   CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
+  CTRY(c->alloc(&c->kap, (size_t)P.n * P.n));
   CTRY(c->alloc(&c->Lfac, (size_t)(c->nv * (c->nv + 1) / 2) * P.n * P.n));
   CTRY(c->alloc(&c->err, 4));
   CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
@@ -777,7 +781,8 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
   Level& L0 = c->levels[0];
-  launch_condense(s, c->refd, c->p, nE, c->logk, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+  launch_kappa(s, nE, c->logk, c->kap);
+  launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                   L0.d64.A, c->Lfac, c->err);
   STATUS_TRY(check_launch("condensation"));
   if (c->opts.precision != HDGMG_PREC_FP64) {

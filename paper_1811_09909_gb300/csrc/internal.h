@@ -81,14 +81,16 @@ struct RefDevice {     // device copies of RefElement tables (FP64)
   double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy;
 };
 
+// kap = exp(log kappa) per element; the element kernels take kap
+void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap);
 void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE,
-                     const double* logk, int tau_mode, double tau_c, double hmin,
+                     const double* kap, int tau_mode, double tau_c, double hmin,
                      double* A, double* Lfac, int* err);
 void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n,
-                const double* logk, int tau_mode, double tau_c, double hmin,
+                const double* kap, int tau_mode, double tau_c, double hmin,
                 const double* Lfac, const double* f, double* b);
 void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
-                    const double* logk, int tau_mode, double tau_c, double hmin,
+                    const double* kap, int tau_mode, double tau_c, double hmin,
                     const double* Lfac, const double* f, const double* lam,
                     double* u, double* q);
 
@@ -164,6 +166,10 @@ void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeid
                             double* dense);
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err);
 void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, double* Ainv);
+// assemble + invert in one block when A_1 fits in shared memory; false if not
+template <typename T>
+bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
+                              double* Ainv, int* err);
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
                          const double* Ainv, const T* r, T* e);

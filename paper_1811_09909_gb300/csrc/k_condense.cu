@@ -28,12 +28,24 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
   j = t - r * (r + 1) / 2;
 }
 
+// 1/sqrt(d) for d > 0: FP32 seed, then two Newton-Raphson steps for the
+// inverse square root, y <- y (3 - d y^2) / 2, in FP64 (the error squares at
+// every step: ~1e-7 -> ~1e-14 -> FP64 rounding).
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
 // K1: one warp per element, the local matrices in shared memory.
 //   S: nv x nv (full square, lower part used), V: nv x nt.
+// The FP64 pipe is the bottleneck on GB300, so every pivot's square root and
+// reciprocal is computed by one lane and broadcast.
 __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
                                 const double* __restrict__ G, const double* __restrict__ Eb,
                                 const double* __restrict__ H, const double* __restrict__ F,
-                                const double* __restrict__ K, const double* __restrict__ logk,
+                                const double* __restrict__ K, const double* __restrict__ kapv,
                                 int tau_mode, double tau_c, double hmin,
                                 double* __restrict__ A, double* __restrict__ Lfac,
                                 int* __restrict__ err) {
@@ -43,22 +55,29 @@ __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
   if (e >= nE) return;
   double* S = smem + (size_t)warp * (nv * nv + nv * nt);
   double* V = S + nv * nv;
-  const double kap = exp(logk[e]);
+  const double kap = kapv[e];
   const double tau = tau_of(tau_mode, tau_c, hmin);
-  for (int t = lane; t < nv * nv; t += 32) S[t] = kap * G[t] + tau * Eb[t];
+  const int nsv = nv * (nv + 1) / 2;
+  for (int t = lane; t < nsv; t += 32) {
+    int i, j;
+    tri_index(t, i, j);
+    S[i * nv + j] = kap * G[i * nv + j] + tau * Eb[i * nv + j];
+  }
   for (int t = lane; t < nv * nt; t += 32) V[t] = kap * H[t] + tau * F[t];
   __syncwarp();
   bool bad = false;
   for (int k = 0; k < nv; ++k) {
-    double d = S[k * nv + k];
-    if (!(d > 0.0) || !isfinite(d)) {
-      bad = true;
-      d = 1.0;
+    double di = 0.0;
+    if (lane == 0) {
+      double d = S[k * nv + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = true;
+        d = 1.0;
+      }
+      di = rsqrt_newton(d);
+      S[k * nv + k] = d * di;
     }
-    d = sqrt(d);
-    const double di = 1.0 / d;
-    __syncwarp();
-    if (lane == 0) S[k * nv + k] = d;
+    di = __shfl_sync(0xffffffffu, di, 0);
     for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
     for (int c = lane; c < nt; c += 32) V[k * nt + c] *= di;
     __syncwarp();
@@ -76,7 +95,7 @@ __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
     }
     __syncwarp();
   }
-  if (bad && lane == 0) atomicOr(err, 1);
+  if (bad) atomicOr(err, 1);
   const int nsa = nt * (nt + 1) / 2;
   for (int t = lane; t < nsa; t += 32) {
     int r, c;
@@ -95,6 +114,12 @@ __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
       Lfac[(size_t)t * nE + e] = S[r * nv + c];
     }
   }
+}
+
+// kappa_e = exp(log kappa_e), once per element for all element kernels
+__global__ void kappa_kernel(int nE, const double* __restrict__ logk, double* __restrict__ kap) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nE) kap[e] = exp(logk[e]);
 }
 
 // Per-thread work vectors live in shared memory as [index][thread] so that
@@ -139,7 +164,7 @@ __device__ __forceinline__ bool is_boundary_edge(int n, int edge) {
 // K5: thread per element; shared memory y[nv][blockDim]
 __global__ void rhs_kernel(int p, int n, const double* __restrict__ Mdiag,
                            const double* __restrict__ H, const double* __restrict__ F,
-                           const double* __restrict__ logk, int tau_mode, double tau_c,
+                           const double* __restrict__ kapv, int tau_mode, double tau_c,
                            double hmin, const double* __restrict__ L,
                            const double* __restrict__ f, double* __restrict__ b) {
   extern __shared__ double smem[];
@@ -148,7 +173,7 @@ __global__ void rhs_kernel(int p, int n, const double* __restrict__ Mdiag,
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   double* y = smem;
-  const double kap = exp(logk[e]);
+  const double kap = kapv[e];
   const double tau = tau_of(tau_mode, tau_c, hmin);
   for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
   chol_solve(L, nv, nE, e, y);
@@ -169,7 +194,7 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
                                const double* __restrict__ H, const double* __restrict__ F,
                                const double* __restrict__ BxT, const double* __restrict__ ByT,
                                const double* __restrict__ Cx, const double* __restrict__ Cy,
-                               const double* __restrict__ logk, int tau_mode, double tau_c,
+                               const double* __restrict__ kapv, int tau_mode, double tau_c,
                                double hmin, const double* __restrict__ L,
                                const double* __restrict__ f, const double* __restrict__ lam,
                                double* __restrict__ u, double* __restrict__ q) {
@@ -180,7 +205,7 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
   if (e >= nE) return;
   double* y = smem;
   double* le = smem + (size_t)nv * blockDim.x;
-  const double kap = exp(logk[e]);
+  const double kap = kapv[e];
   const double tau = tau_of(tau_mode, tau_c, hmin);
   int ed[4];
   element_edges(n, e, ed);
@@ -215,7 +240,12 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
 
 }  // namespace
 
-void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* logk,
+void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap) {
+  note_launch();
+  kappa_kernel<<<(nE + 255) / 256, 256, 0, s>>>(nE, logk, kap);
+}
+
+void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
                      int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const size_t per_warp = sizeof(double) * (size_t)(nv * nv + nv * nt);
@@ -231,10 +261,10 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
   const int blocks = (nE + wpb - 1) / wpb;
   note_launch();
   condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
-                                                 logk, tau_mode, tau_c, hmin, A, Lfac, err);
+                                                 kap, tau_mode, tau_c, hmin, A, Lfac, err);
 }
 
-void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* logk,
+void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
                 int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
                 double* b) {
   const int nE = n * n, nv = (p + 1) * (p + 1);
@@ -242,11 +272,11 @@ void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double
   const size_t shm = sizeof(double) * (size_t)nv * threads;
   cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   note_launch();
-  rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, logk, tau_mode, tau_c, hmin,
+  rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau_mode, tau_c, hmin,
                                           Lfac, f, b);
 }
 
-void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const double* logk,
+void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
                     int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
                     const double* lam, double* u, double* q) {
   const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
@@ -255,7 +285,7 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const do
   cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   note_launch();
   recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
-                                              ref.Cy, logk, tau_mode, tau_c, hmin, Lfac, f, lam,
+                                              ref.Cy, kap, tau_mode, tau_c, hmin, Lfac, f, lam,
                                               u, q);
 }
 

@@ -74,13 +74,13 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
     e0 = (j - 1) * n + i; le0 = 3;  // element below, its top edge
     e1 = j * n + i;       le1 = 2;  // element above, its bottom edge
   }
-  double D[ND][ND];
+  T D[ND][ND];
 #pragma unroll
   for (int a = 0; a < ND; ++a)
 #pragma unroll
     for (int b = 0; b <= a; ++b) {
-      const double v = (double)A[(size_t)pk(le0 * ND + a, le0 * ND + b) * nE + e0] +
-                       (double)A[(size_t)pk(le1 * ND + a, le1 * ND + b) * nE + e1];
+      const T v = A[(size_t)pk(le0 * ND + a, le0 * ND + b) * nE + e0] +
+                  A[(size_t)pk(le1 * ND + a, le1 * ND + b) * nE + e1];
       D[a][b] = v;
       D[b][a] = v;
     }
@@ -88,31 +88,31 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < ND; ++k) {
-    double d = D[k][k];
+    T d = D[k][k];
 #pragma unroll
     for (int j = 0; j < k; ++j) d -= D[k][j] * D[k][j];
-    if (!(d > 0.0)) { bad = true; d = 1.0; }
+    if (!(d > T(0))) { bad = true; d = T(1); }
     d = sqrt(d);
     D[k][k] = d;
 #pragma unroll
     for (int i = k + 1; i < ND; ++i) {
-      double s = D[i][k];
+      T s = D[i][k];
 #pragma unroll
       for (int j = 0; j < k; ++j) s -= D[i][j] * D[k][j];
       D[i][k] = s / d;
     }
   }
-  double Li[ND][ND];
+  T Li[ND][ND];
 #pragma unroll
   for (int i = 0; i < ND; ++i)
 #pragma unroll
-    for (int j = 0; j < ND; ++j) Li[i][j] = 0.0;
+    for (int j = 0; j < ND; ++j) Li[i][j] = T(0);
 #pragma unroll
   for (int j = 0; j < ND; ++j) {
-    Li[j][j] = 1.0 / D[j][j];
+    Li[j][j] = T(1) / D[j][j];
 #pragma unroll
     for (int i = j + 1; i < ND; ++i) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
       for (int k = j; k < i; ++k) s -= D[i][k] * Li[k][j];
       Li[i][j] = s / D[i][i];
@@ -122,10 +122,10 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
   for (int a = 0; a < ND; ++a)
 #pragma unroll
     for (int b = 0; b <= a; ++b) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
       for (int k = a; k < ND; ++k) s += Li[k][a] * Li[k][b];
-      Dinv[(size_t)pk(a, b) * nedge + edge] = (T)s;
+      Dinv[(size_t)pk(a, b) * nedge + edge] = s;
     }
   if (bad) atomicOr(err, 2);
 }

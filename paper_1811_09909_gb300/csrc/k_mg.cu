@@ -74,120 +74,149 @@ __device__ __forceinline__ void child_map(int ch, int le, bool& interior, int& s
 __constant__ double c_Jc[2][2][2];   // child injection [child][fine mode][coarse mode]
 
 // -------------------------------------------------- K4 agglomeration setup
-template <typename T>
-__global__ void agglomerate_kernel(int nc, const T* __restrict__ Af, T* __restrict__ Ac,
-                                   T* __restrict__ AIIinv, T* __restrict__ Yout,
-                                   T* __restrict__ Pi, int* __restrict__ err) {
+// One warp per macro-element C: the 24 x 24 local block assembled from the
+// four children lives in shared memory and every product is spread over the
+// 32 lanes:
+//   A_II = L L^T, A_II^-1 = L^-T L^-1, Y = -A_II^-1 A_IB,
+//   S = A_BB + A_IB^T Y, A_c = J^T S J, Pi = Y J.
+template <typename T, int WPB>
+__global__ void __launch_bounds__(32 * WPB) agglomerate_warp_kernel(
+    int nc, const T* __restrict__ Af, T* __restrict__ Ac, T* __restrict__ AIIinv,
+    T* __restrict__ Yout, T* __restrict__ Pi, int* __restrict__ err) {
+  constexpr int PER = 64 + 128 + 256 + 64 + 64 + 128 + 128;
+  __shared__ T sh[WPB * PER];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nC = nc * nc;
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  const int C = blockIdx.x * WPB + warp;
   if (C >= nC) return;
   const int J = C / nc, I = C - J * nc;
   const int n = 2 * nc, nEf = n * n;
-  T AII[8][8], AIB[8][16], ABB[16][16];
-  for (int a = 0; a < 8; ++a) {
-    for (int b = 0; b < 8; ++b) AII[a][b] = T(0);
-    for (int b = 0; b < 16; ++b) AIB[a][b] = T(0);
-  }
-  for (int a = 0; a < 16; ++a)
-    for (int b = 0; b < 16; ++b) ABB[a][b] = T(0);
+  T* AII = sh + warp * PER;      // 8 x 8
+  T* AIB = AII + 64;             // 8 x 16
+  T* ABB = AIB + 128;            // 16 x 16, becomes S
+  T* Lm = ABB + 256;             // 8 x 8 Cholesky factor
+  T* Ai = Lm + 64;               // 8 x 8 A_II^-1
+  T* Yw = Ai + 64;               // 8 x 16
+  T* SJ = Yw + 128;              // 16 x 8, also holds L^-1 before Y is formed
+  for (int t = lane; t < 448; t += 32) AII[t] = T(0);
+  __syncwarp();
   for (int ch = 0; ch < 4; ++ch) {
     const int ef = (2 * J + (ch >> 1)) * n + 2 * I + (ch & 1);
-    for (int r = 0; r < 8; ++r) {
-      bool ir;
-      int sr;
-      child_map(ch, r / 2, ir, sr);
-      const int lr = sr * 2 + (r & 1);
-      for (int c = 0; c < 8; ++c) {
-        bool ic;
-        int sc;
-        child_map(ch, c / 2, ic, sc);
-        const int lc = sc * 2 + (c & 1);
-        const T a = Af[(size_t)pk_any(r, c) * nEf + ef];
-        if (ir && ic) AII[lr][lc] += a;
-        else if (ir && !ic) AIB[lr][lc] += a;
-        else if (!ir && !ic) ABB[lr][lc] += a;
-      }
+    for (int t = lane; t < 64; t += 32) {
+      const int r = t >> 3, c = t & 7;
+      bool ir, ic;
+      int sr, sc;
+      child_map(ch, r >> 1, ir, sr);
+      child_map(ch, c >> 1, ic, sc);
+      const int lr = sr * 2 + (r & 1), lc = sc * 2 + (c & 1);
+      const T a = Af[(size_t)pk_any(r, c) * nEf + ef];
+      if (ir && ic) AII[lr * 8 + lc] += a;
+      else if (ir && !ic) AIB[lr * 16 + lc] += a;
+      else if (!ir && !ic) ABB[lr * 16 + lc] += a;
     }
+    __syncwarp();
   }
-  // Cholesky of A_II and its inverse
-  T L[8][8];
+  // Cholesky of A_II
+  for (int t = lane; t < 64; t += 32) Lm[t] = AII[t];
+  __syncwarp();
   bool bad = false;
   for (int k = 0; k < 8; ++k) {
-    T d = AII[k][k];
-    for (int j = 0; j < k; ++j) d -= L[k][j] * L[k][j];
-    if (!(d > T(0))) { bad = true; d = T(1); }
-    d = sqrt(d);
-    L[k][k] = d;
-    for (int i = k + 1; i < 8; ++i) {
-      T s = AII[i][k];
-      for (int j = 0; j < k; ++j) s -= L[i][j] * L[k][j];
-      L[i][k] = s / d;
+    T di = T(0);
+    if (lane == 0) {
+      T d = Lm[k * 8 + k];
+      if (!(d > T(0))) {
+        bad = true;
+        d = T(1);
+      }
+      di = inv_sqrt(d);
+      Lm[k * 8 + k] = d * di;
     }
-    for (int j = k + 1; j < 8; ++j) L[k][j] = T(0);
+    di = __shfl_sync(0xffffffffu, di, 0);
+    if (lane > k && lane < 8) Lm[lane * 8 + k] *= di;
+    __syncwarp();
+    const int m = 7 - k;
+    if (lane < m * (m + 1) / 2) {
+      int ii, jj;
+      tri_rc(lane, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      Lm[i * 8 + j] -= Lm[i * 8 + k] * Lm[j * 8 + k];
+    }
+    __syncwarp();
   }
-  T Li[8][8];
-  for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 8; ++j) Li[i][j] = T(0);
-  for (int j = 0; j < 8; ++j) {
-    Li[j][j] = T(1) / L[j][j];
-    for (int i = j + 1; i < 8; ++i) {
-      T s = T(0);
-      for (int k = j; k < i; ++k) s -= L[i][k] * Li[k][j];
-      Li[i][j] = s / L[i][i];
-    }
-  }
-  T Ai[8][8];
-  for (int a = 0; a < 8; ++a)
-    for (int b = 0; b <= a; ++b) {
-      T s = T(0);
-      for (int k = a; k < 8; ++k) s += Li[k][a] * Li[k][b];
-      Ai[a][b] = s;
-      Ai[b][a] = s;
-      AIIinv[(size_t)pk(a, b) * nC + C] = s;
-    }
-  // Y = -A_II^-1 A_IB (8 x 16)
-  T Y[8][16];
-  for (int a = 0; a < 8; ++a)
-    for (int b = 0; b < 16; ++b) {
-      T s = T(0);
-      for (int k = 0; k < 8; ++k) s -= Ai[a][k] * AIB[k][b];
-      Y[a][b] = s;
-      Yout[(size_t)(a * 16 + b) * nC + C] = s;
-    }
-  // S = A_BB + A_BI Y  (A_BI = A_IB^T), 16 x 16
-  // coarse A = J^T S J, Pi = Y J; J[(me*2+c)*2+kf][me*2+kc] = Jc[c][kf][kc]
-  T SJ[16][8];
-  for (int a = 0; a < 16; ++a)
-    for (int cb = 0; cb < 8; ++cb) {
-      const int me = cb >> 1, kc = cb & 1;
-      T s = T(0);
-      for (int c = 0; c < 2; ++c)
-        for (int kf = 0; kf < 2; ++kf) {
-          const int b = (me * 2 + c) * 2 + kf;
-          T sab = ABB[a][b];
-          for (int k = 0; k < 8; ++k) sab += AIB[k][a] * Y[k][b];
-          s += sab * (T)c_Jc[c][kf][kc];
-        }
-      SJ[a][cb] = s;
-    }
-  for (int ca = 0; ca < 8; ++ca) {
-    const int me = ca >> 1, kc = ca & 1;
-    for (int cb = 0; cb <= ca; ++cb) {
-      T s = T(0);
-      for (int c = 0; c < 2; ++c)
-        for (int kf = 0; kf < 2; ++kf) s += (T)c_Jc[c][kf][kc] * SJ[(me * 2 + c) * 2 + kf][cb];
-      Ac[(size_t)pk(ca, cb) * nC + C] = s;
-    }
-  }
-  for (int a = 0; a < 8; ++a)
-    for (int cb = 0; cb < 8; ++cb) {
-      const int me = cb >> 1, kc = cb & 1;
-      T s = T(0);
-      for (int c = 0; c < 2; ++c)
-        for (int kf = 0; kf < 2; ++kf) s += Y[a][(me * 2 + c) * 2 + kf] * (T)c_Jc[c][kf][kc];
-      Pi[(size_t)(a * 8 + cb) * nC + C] = s;
-    }
   if (bad) atomicOr(err, 4);
+  // L^-1 (columns by lanes 0..7) into SJ[0..63]
+  if (lane < 8) {
+    const int j = lane;
+    for (int i = 0; i < 8; ++i) {
+      T s = (i == j) ? T(1) : T(0);
+      if (i >= j) {
+        for (int k = j; k < i; ++k) s -= Lm[i * 8 + k] * SJ[k * 8 + j];
+        s = s / Lm[i * 8 + i];
+      }
+      SJ[i * 8 + j] = s;
+    }
+  }
+  __syncwarp();
+  // A_II^-1 = L^-T L^-1
+  for (int t = lane; t < 64; t += 32) {
+    const int a = t >> 3, b = t & 7;
+    T s = T(0);
+    for (int k = (a > b ? a : b); k < 8; ++k) s += SJ[k * 8 + a] * SJ[k * 8 + b];
+    Ai[t] = s;
+  }
+  __syncwarp();
+  // Y = -A_II^-1 A_IB
+  for (int t = lane; t < 128; t += 32) {
+    const int a = t >> 4, b = t & 15;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s -= Ai[a * 8 + k] * AIB[k * 16 + b];
+    Yw[t] = s;
+  }
+  __syncwarp();
+  // S = A_BB + A_IB^T Y (in place)
+  for (int t = lane; t < 256; t += 32) {
+    const int a = t >> 4, b = t & 15;
+    T s = ABB[t];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += AIB[k * 16 + a] * Yw[k * 16 + b];
+    ABB[t] = s;
+  }
+  __syncwarp();
+  // SJ = S J (16 x 8)
+  for (int t = lane; t < 128; t += 32) {
+    const int a = t >> 3, cb = t & 7, me = cb >> 1, kc = cb & 1;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) s += ABB[a * 16 + (me * 2 + c) * 2 + kf] * (T)c_Jc[c][kf][kc];
+    SJ[t] = s;
+  }
+  __syncwarp();
+  // outputs
+  for (int t = lane; t < 36; t += 32) {
+    int ca, cb;
+    tri_rc(t, ca, cb);
+    const int me = ca >> 1, kc = ca & 1;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) s += (T)c_Jc[c][kf][kc] * SJ[((me * 2 + c) * 2 + kf) * 8 + cb];
+    Ac[(size_t)t * nC + C] = s;
+    AIIinv[(size_t)t * nC + C] = Ai[ca * 8 + cb];
+  }
+  for (int t = lane; t < 64; t += 32) {
+    const int a = t >> 3, cb = t & 7, me = cb >> 1, kc = cb & 1;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) s += Yw[a * 16 + (me * 2 + c) * 2 + kf] * (T)c_Jc[c][kf][kc];
+    Pi[(size_t)t * nC + C] = s;
+  }
+  for (int t = lane; t < 128; t += 32) Yout[(size_t)t * nC + C] = Yw[t];
 }
 
 // ------------------------------------------------- K8 local correction
@@ -425,6 +454,55 @@ __global__ void coarse_factor_kernel(int nf, double* __restrict__ M, int* __rest
     }
     __syncthreads();
   }
+}
+
+// Coarsest level, small case (the whole matrix fits in shared memory): one
+// block assembles A_1 from the element matrices and inverts it in place by
+// Gauss-Jordan elimination without pivoting (A_1 is SPD), in FP64.
+template <typename T>
+__global__ void coarse_setup_smem_kernel(int n, const T* __restrict__ A, const int* __restrict__ fidx,
+                                         int nf, double* __restrict__ Ainv, int* __restrict__ err) {
+  extern __shared__ double M[];
+  double* colk = M + (size_t)nf * nf;
+  const int nE = n * n;
+  for (int t = threadIdx.x; t < nf * nf; t += blockDim.x) M[t] = 0.0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < nE * 64; t += blockDim.x) {
+    const int e = t >> 6, r = (t >> 3) & 7, c = t & 7;
+    int ed[4];
+    elem_edges(n, e, ed);
+    const int fr = fidx[ed[r >> 1]], fc = fidx[ed[c >> 1]];
+    if (fr < 0 || fc < 0) continue;
+    atomicAdd(&M[(size_t)(fr * 2 + (r & 1)) * nf + fc * 2 + (c & 1)],
+              (double)A[(size_t)pk_any(r, c) * nE + e]);
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int k = 0; k < nf; ++k) {
+    if (threadIdx.x == 0) {
+      double d = M[(size_t)k * nf + k];
+      if (!(d > 0.0)) {
+        atomicOr(err, 8);
+        d = 1.0;
+      }
+      piv = 1.0 / d;
+      M[(size_t)k * nf + k] = 1.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nf; j += blockDim.x) M[(size_t)k * nf + j] *= piv;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) colk[i] = (i == k) ? 0.0 : M[(size_t)i * nf + k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nf * nf; t += blockDim.x) {
+      const int i = t / nf, j = t - i * nf;
+      if (i == k) continue;
+      if (j == k)
+        M[t] = -colk[i] * M[(size_t)k * nf + k];
+      else
+        M[t] -= colk[i] * M[(size_t)k * nf + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nf * nf; t += blockDim.x) Ainv[t] = M[t];
 }
 
 // Coarsest level: the dense FP64 inverse A_1^-1 = L^-T L^-1 is formed once at
@@ -934,7 +1012,7 @@ void launch_agglomerate(cudaStream_t s, int nc, const T* Af, T* Ac, T* AIIinv, T
                         int* err) {
   upload_jc();
   note_launch();
-  agglomerate_kernel<T><<<nblk(nc * nc, 64), 64, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
+  agglomerate_warp_kernel<T, 4><<<nblk(nc * nc, 4), 128, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
 }
 
 template <typename T>
@@ -986,6 +1064,22 @@ void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeid
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
   note_launch();
   coarse_factor_kernel<<<1, 1024, 0, s>>>(nf, dense, err);
+}
+
+template <typename T>
+bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
+                              double* Ainv, int* err) {
+  const size_t shm = sizeof(double) * ((size_t)nf * nf + nf);
+  if (shm > 200 * 1024) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(coarse_setup_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  note_launch();
+  coarse_setup_smem_kernel<T><<<1, 1024, shm, s>>>(n, A, freeidx, nf, Ainv, err);
+  return true;
 }
 
 void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, double* Ainv) {
@@ -1143,6 +1237,10 @@ INST(float)
 #undef INST
 template void launch_convert<double, float>(cudaStream_t, int64_t, const double*, float*);
 template void launch_vcycle_tail<double>(cudaStream_t, const TailParams<double>&);
+template bool launch_coarse_setup_smem<double>(cudaStream_t, int, const double*, const int*, int,
+                                               double*, int*);
+template bool launch_coarse_setup_smem<float>(cudaStream_t, int, const float*, const int*, int,
+                                              double*, int*);
 template void launch_dot<double>(cudaStream_t, int64_t, const double*, const double*, double*, double*);
 template void launch_dot_fused<double>(cudaStream_t, int64_t, const double*, const double*, double*,
                                        unsigned*, double*, int);
