@@ -151,6 +151,43 @@ hdgmg_status hdgmg_run_host(hdgmg_ctx* ctx, const double* log_kappa,
                             double* lambda, double* u, double* q,
                             hdgmg_info* info);
 
+/* ---- adjoint (gradient with respect to log kappa and f) ----------------- */
+
+/* Gradient of the misfit
+ *   J = 1/2 sum_e (u_e - u_obs,e)^T M (u_e - u_obs,e)
+ * (M: the Gauss-node volume mass matrix, i.e. the L2 norm evaluated by
+ * quadrature on the nodal values) with respect to the per-element
+ * log-diffusivity m_e = log kappa_e given to the last hdgmg_setup and to the
+ * nodal forcing f.  Runs the forward solve, then one solve of the trace
+ * system with right-hand side M (u - u_obs) and homogeneous Dirichlet data
+ * (A is symmetric, so the transposed solve is the same multigrid solve),
+ * its local recovery, and the per-element contraction
+ *   dJ/dm_e = -kappa_e [ w^T (G u - H lambda) + mu^T (K lambda - H^T u) ],
+ *   dJ/df_e = M w,
+ * with (lambda, u) the forward and (mu, w) the adjoint trace and volume
+ * fields (G = sum_d B_d M^-1 B_d^T, H = sum_d B_d M^-1 C_d,
+ * K = sum_d C_d^T M^-1 C_d: the q-eliminated HDG blocks of Sec. 2).
+ *   f, g_D    device, as in hdgmg_solve (one right-hand side; g_D may be NULL)
+ *   u_obs     device, [(p+1)^2][n*n] FP64
+ *   J         host, out (may be NULL)
+ *   dJ_dlogk  device, [n*n] FP64 out (may be NULL)
+ *   dJ_df     device, [(p+1)^2][n*n] FP64 out (may be NULL)
+ *   info      host, out (may be NULL): the adjoint solve.
+ * The local Cholesky factors of the set-up are reused (kept in memory). */
+hdgmg_status hdgmg_gradient(hdgmg_ctx* ctx, const double* f, const double* g_D,
+                            const double* u_obs, double* J, double* dJ_dlogk,
+                            double* dJ_df, hdgmg_info* info);
+
+/* Adjoint of one solve for a general functional L(u): given the forward
+ * trace lambda and volume field u of the last set-up (device, layouts of
+ * hdgmg_solve, one right-hand side) and the nodal sensitivity g_u = dL/du
+ * (device, [(p+1)^2][n*n]), writes dL/dlog kappa [n*n] and dL/df
+ * [(p+1)^2][n*n] (device, either may be NULL).  Used by the torch.autograd
+ * binding. */
+hdgmg_status hdgmg_adjoint(hdgmg_ctx* ctx, const double* lambda, const double* u,
+                           const double* g_u, double* dL_dlogk, double* dL_df,
+                           hdgmg_info* info);
+
 /* ---- inspection entry points (used by the parity tests) ---------------- */
 
 /* Number of levels (finest = 0) and the shape of level k: macro-elements per

@@ -68,6 +68,9 @@ struct hdgmg_ctx {
   double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *b = nullptr;
   double *lam = nullptr, *partial = nullptr, *scal = nullptr, *scal_h = nullptr;
   unsigned* counter = nullptr;   // last-block counter of the fused reductions
+  // adjoint buffers (allocated on first use)
+  double *adj_f = nullptr, *adj_lam = nullptr, *adj_u = nullptr;
+  double *fwd_lam = nullptr, *fwd_u = nullptr, *mis_d = nullptr, *mis_g = nullptr;
   // host-call staging
   double *st_f = nullptr, *st_g = nullptr, *st_l = nullptr, *st_u = nullptr, *st_q = nullptr;
   bool setup_done = false;
@@ -551,6 +554,40 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
 
 }  // namespace
 
+namespace {
+
+hdgmg_status adjoint_buffers(hdgmg_ctx* c) {
+  if (c->adj_f) return HDGMG_OK;
+  const size_t nvE = (size_t)c->nv * c->n * c->n;
+  const int64_t len = c->fine_len();
+  CUDA_TRY(c->alloc(&c->adj_f, nvE));
+  CUDA_TRY(c->alloc(&c->adj_lam, len));
+  CUDA_TRY(c->alloc(&c->adj_u, nvE));
+  CUDA_TRY(c->alloc(&c->fwd_lam, len));
+  CUDA_TRY(c->alloc(&c->fwd_u, nvE));
+  CUDA_TRY(c->alloc(&c->mis_d, nvE));
+  CUDA_TRY(c->alloc(&c->mis_g, nvE));
+  return HDGMG_OK;
+}
+
+// Adjoint of the solve for the sensitivity g_u = dL/du: one more solve of the
+// (symmetric) trace system with right-hand side from g_u and homogeneous
+// Dirichlet data, its local recovery, and the per-element contraction.
+hdgmg_status adjoint_core(hdgmg_ctx* c, const double* lam, const double* u, const double* g_u,
+                          double* dlogk, double* df, hdgmg_info* info) {
+  cudaStream_t s = c->stream;
+  const int nE = c->n * c->n;
+  launch_adjoint_source(s, c->refd, c->nv, nE, g_u, c->adj_f);
+  hdgmg_status st = solve_one(c, c->adj_f, nullptr, c->adj_lam, c->adj_u, nullptr, info);
+  if (st != HDGMG_OK && st != HDGMG_ENOCONV) return st;
+  launch_grad_contract(s, c->refd, c->p, c->n, c->kap, lam, u, c->adj_lam, c->adj_u, dlogk, df);
+  STATUS_TRY(check_launch("adjoint contraction"));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 void hdgmg_default_opts(hdgmg_opts* o) {
@@ -869,6 +906,32 @@ hdgmg_status hdgmg_run_host(hdgmg_ctx* c, const double* log_kappa, const double*
   if (q) CUDA_TRY(cudaMemcpyAsync(q, c->st_q, sizeof(double) * 2 * c->nv * nE, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return st;
+}
+
+hdgmg_status hdgmg_adjoint(hdgmg_ctx* c, const double* lambda, const double* u, const double* g_u,
+                           double* dL_dlogk, double* dL_df, hdgmg_info* info) {
+  if (!c || !lambda || !u || !g_u) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  STATUS_TRY(adjoint_buffers(c));
+  return adjoint_core(c, lambda, u, g_u, dL_dlogk, dL_df, info);
+}
+
+hdgmg_status hdgmg_gradient(hdgmg_ctx* c, const double* f, const double* g_D, const double* u_obs,
+                            double* J, double* dJ_dlogk, double* dJ_df, hdgmg_info* info) {
+  if (!c || !f || !u_obs) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  STATUS_TRY(adjoint_buffers(c));
+  cudaStream_t s = c->stream;
+  const int nE = c->n * c->n;
+  hdgmg_status st = solve_one(c, f, g_D, c->fwd_lam, c->fwd_u, nullptr, info);
+  if (st != HDGMG_OK && st != HDGMG_ENOCONV) return st;
+  launch_misfit(s, c->refd, c->nv, nE, c->fwd_u, u_obs, c->mis_d, c->mis_g);
+  launch_dot<double>(s, (int64_t)c->nv * nE, c->mis_d, c->mis_g, c->partial, c->scal + 7);
+  CUDA_TRY(cudaMemcpyAsync(c->scal_h + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (J) *J = 0.5 * c->scal_h[7];
+  hdgmg_status st2 = adjoint_core(c, c->fwd_lam, c->fwd_u, c->mis_g, dJ_dlogk, dJ_df, info);
+  return st2 != HDGMG_OK ? st2 : st;
 }
 
 hdgmg_status hdgmg_num_levels(hdgmg_ctx* c, int32_t* n_levels) {

@@ -94,6 +94,15 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
                     const double* Lfac, const double* f, const double* lam,
                     double* u, double* q);
 
+// adjoint: per-element derivative contraction (K13), adjoint source, misfit
+void launch_grad_contract(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                          const double* lam, const double* u, const double* mu, const double* w,
+                          double* dlogk, double* df);
+void launch_adjoint_source(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* g,
+                           double* fadj);
+void launch_misfit(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* u,
+                   const double* uobs, double* d, double* gu);
+
 template <typename T>
 void launch_matvec(cudaStream_t s, int n, int nd, const T* A, const T* x, T* y, T alpha);
 // per-ND instantiations (k_edge_inst.cu, one translation unit per type and ND)

@@ -236,9 +236,99 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
     }
   }
 }
+// ---------------------------------------------------------- adjoint (K13)
+// With the forward state (lambda, u) and the adjoint state (mu, w) -- the
+// solution of the same trace system with right-hand side built from g_u and
+// homogeneous Dirichlet data, and its recovered volume field -- the
+// derivatives of L(u) are, per element,
+//   dL/dlog kappa_e = -kappa_e [ w^T (G u - H lambda) + mu^T (K lambda - H^T u) ],
+//   dL/df_e        = M w.
+__global__ void grad_contract_kernel(int p, int n, const double* __restrict__ Mdiag,
+                                     const double* __restrict__ G, const double* __restrict__ H,
+                                     const double* __restrict__ K, const double* __restrict__ kapv,
+                                     const double* __restrict__ lam, const double* __restrict__ u,
+                                     const double* __restrict__ mu, const double* __restrict__ w,
+                                     double* __restrict__ dlogk, double* __restrict__ df) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* le = smem;                                  // lambda_e
+  double* me = smem + (size_t)nt * blockDim.x;        // mu_e
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) {
+    const size_t ix = (size_t)(c % p1) * nedge + ed[c / p1];
+    TV(le, c) = lam[ix];
+    TV(me, c) = mu[ix];
+  }
+  double s = 0.0;
+  for (int a = 0; a < nv; ++a) {           // w^T (G u - H lambda)
+    double t = 0.0;
+    for (int b = 0; b < nv; ++b) t += G[a * nv + b] * u[(size_t)b * nE + e];
+    for (int c = 0; c < nt; ++c) t -= H[a * nt + c] * TV(le, c);
+    const double wa = w[(size_t)a * nE + e];
+    s += wa * t;
+    if (df) df[(size_t)a * nE + e] = Mdiag[a] * wa;
+  }
+  for (int c = 0; c < nt; ++c) {           // mu^T (K lambda - H^T u)
+    double t = 0.0;
+    for (int d = 0; d < nt; ++d) t += K[c * nt + d] * TV(le, d);
+    for (int a = 0; a < nv; ++a) t -= H[a * nt + c] * u[(size_t)a * nE + e];
+    s += TV(me, c) * t;
+  }
+  if (dlogk) dlogk[e] = -kapv[e] * s;
+}
+
+// f_adj = g_u / M (so that the right-hand side M f_adj of the adjoint solve
+// is g_u), and the misfit pieces d = u - u_obs, g_u = M d
+__global__ void adjoint_source_kernel(int nv, int nE, const double* __restrict__ Mdiag,
+                                      const double* __restrict__ g, double* __restrict__ fadj) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nv * nE) return;
+  fadj[i] = g[i] / Mdiag[i / nE];
+}
+
+__global__ void misfit_kernel(int nv, int nE, const double* __restrict__ Mdiag,
+                              const double* __restrict__ u, const double* __restrict__ uobs,
+                              double* __restrict__ d, double* __restrict__ gu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nv * nE) return;
+  const double di = u[i] - uobs[i];
+  d[i] = di;
+  gu[i] = Mdiag[i / nE] * di;
+}
 #undef TV
 
+
 }  // namespace
+
+void launch_grad_contract(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                          const double* lam, const double* u, const double* mu, const double* w,
+                          double* dlogk, double* df) {
+  const int nE = n * n, nt = 4 * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(2 * nt) * threads;
+  note_launch();
+  grad_contract_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.G, ref.H, ref.K, kap, lam, u, mu,
+                                                    w, dlogk, df);
+}
+
+void launch_adjoint_source(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* g,
+                           double* fadj) {
+  const int64_t len = (int64_t)nv * nE;
+  note_launch();
+  adjoint_source_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(nv, nE, ref.M, g, fadj);
+}
+
+void launch_misfit(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* u,
+                   const double* uobs, double* d, double* gu) {
+  const int64_t len = (int64_t)nv * nE;
+  note_launch();
+  misfit_kernel<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(nv, nE, ref.M, u, uobs, d, gu);
+}
 
 void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap) {
   note_launch();

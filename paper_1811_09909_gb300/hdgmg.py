@@ -23,7 +23,7 @@ EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
             "hdgmg_run_host", "hdgmg_num_levels", "hdgmg_level_shape",
             "hdgmg_copy_element_matrices", "hdgmg_apply_operator", "hdgmg_apply_vcycle",
             "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy",
-            "hdgmg_apply_operator_noalloc"]
+            "hdgmg_apply_operator_noalloc", "hdgmg_gradient", "hdgmg_adjoint"]
 
 
 class Problem(ctypes.Structure):
@@ -83,6 +83,8 @@ def load():
     lib.hdgmg_copy_element_matrices.argtypes = [P, I32, P]
     lib.hdgmg_apply_operator.argtypes = [P, I32, P, P]
     lib.hdgmg_apply_operator_noalloc.argtypes = [P, I32, P, P]
+    lib.hdgmg_gradient.argtypes = [P, P, P, P, ctypes.POINTER(D), P, P, ctypes.POINTER(Info)]
+    lib.hdgmg_adjoint.argtypes = [P, P, P, P, P, P, ctypes.POINTER(Info)]
     lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
     lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
     lib.hdgmg_last_error.argtypes = []
@@ -211,6 +213,34 @@ class Solver:
             _check(st)
         return st, info
 
+    # -- adjoint ------------------------------------------------------------
+    def gradient(self, f, u_obs, gD=None):
+        """(J, dJ/dlog kappa [E], dJ/df [nv][E], info) of J = 1/2 |u - u_obs|_M^2."""
+        torch = self.torch
+        E = self.n * self.n
+        gk = torch.empty(E, dtype=torch.float64, device=f.device)
+        gf = torch.empty((self.nv, E), dtype=torch.float64, device=f.device)
+        J = ctypes.c_double()
+        info = Info()
+        st = self.lib.hdgmg_gradient(self.ctx, _ptr(f), _ptr(gD), _ptr(u_obs), ctypes.byref(J),
+                                     _ptr(gk), _ptr(gf), ctypes.byref(info))
+        if st not in (0, -4):
+            _check(st)
+        return J.value, gk, gf, info
+
+    def adjoint(self, lam, u, g_u):
+        """(dL/dlog kappa, dL/df) for the nodal sensitivity g_u = dL/du."""
+        torch = self.torch
+        E = self.n * self.n
+        gk = torch.empty(E, dtype=torch.float64, device=u.device)
+        gf = torch.empty((self.nv, E), dtype=torch.float64, device=u.device)
+        info = Info()
+        st = self.lib.hdgmg_adjoint(self.ctx, _ptr(lam), _ptr(u), _ptr(g_u), _ptr(gk), _ptr(gf),
+                                    ctypes.byref(info))
+        if st not in (0, -4):
+            _check(st)
+        return gk, gf
+
     # -- inspection ---------------------------------------------------------
     def num_levels(self):
         k = ctypes.c_int32()
@@ -243,3 +273,39 @@ class Solver:
         b = self.torch.empty((self.nd, self.n_edges), dtype=self.torch.float64, device="cuda")
         _check(self.lib.hdgmg_condensed_rhs(self.ctx, _ptr(f), _ptr(gD), _ptr(b)))
         return b
+
+
+def _autograd_function():
+    import torch
+
+    class HDGSolve(torch.autograd.Function):
+        """u = HDGSolve.apply(solver, log_kappa, f): set-up and solve on the GPU;
+        the backward pass is the library's adjoint (one transposed multigrid
+        solve plus per-element contractions).  The solver must not be set up
+        again between forward and backward."""
+
+        @staticmethod
+        def forward(ctx, solver, log_kappa, f):
+            solver.setup(log_kappa.detach().contiguous())
+            lam, u, _, info = solver.solve(f.detach().contiguous(), want_q=False)
+            ctx.solver = solver
+            ctx.save_for_backward(lam, u)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            lam, u = ctx.saved_tensors
+            gk, gf = ctx.solver.adjoint(lam, u, grad_u.contiguous())
+            return None, gk, gf
+
+    return HDGSolve
+
+
+def hdg_solve(solver, log_kappa, f):
+    """Differentiable solve: u(log kappa, f) for one right-hand side."""
+    global _HDGSolve
+    try:
+        fn = _HDGSolve
+    except NameError:
+        fn = _HDGSolve = _autograd_function()
+    return fn.apply(solver, log_kappa, f)
