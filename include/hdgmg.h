@@ -188,6 +188,42 @@ hdgmg_status hdgmg_adjoint(hdgmg_ctx* ctx, const double* lambda, const double* u
                            const double* g_u, double* dL_dlogk, double* dL_df,
                            hdgmg_info* info);
 
+/* ---- batching: many independent problems on one GPU ------------------- */
+
+typedef struct hdgmg_batch hdgmg_batch;   /* opaque, library-owned */
+
+/* Create a batch of nprob independent problems (each its own n, p, domain
+ * and tau; one set of options for all).  Every problem gets its own context
+ * and CUDA stream; nthreads host threads (<= 0: 8) drive them so that the
+ * problems run concurrently on the device.  Batch calls are ordered after
+ * the work already queued on `stream` and the work they queue is awaited
+ * by `stream` through events.  (Batching of independent problems and
+ * right-hand sides is not in the paper; every problem is the method of the
+ * single-problem entry points.) */
+hdgmg_status hdgmg_batch_create(hdgmg_batch** batch, int32_t nprob,
+                                const hdgmg_problem* problems,
+                                const hdgmg_opts* opts, int32_t nthreads,
+                                void* stream);
+
+/* Set-up of every problem: log_kappa is a HOST array of nprob device
+ * pointers, each as in hdgmg_setup. */
+hdgmg_status hdgmg_batch_setup(hdgmg_batch* batch,
+                               const double* const* log_kappa);
+
+/* Solve nrhs right-hand sides of every problem: f, g_D, lambda, u, q are HOST
+ * arrays of nprob device pointers laid out as in hdgmg_solve (g_D, u, q and
+ * their entries may be NULL); infos: host array of nprob (or NULL).  Returns
+ * the first failure in problem order (ENOCONV only if nothing worse). */
+hdgmg_status hdgmg_batch_solve(hdgmg_batch* batch, int32_t nrhs,
+                               const double* const* f, const double* const* g_D,
+                               double* const* lambda, double* const* u,
+                               double* const* q, hdgmg_info* infos);
+
+/* The context of problem i (owned by the batch) for the inspection calls. */
+hdgmg_status hdgmg_batch_context(hdgmg_batch* batch, int32_t i, hdgmg_ctx** ctx);
+
+void hdgmg_batch_destroy(hdgmg_batch* batch);
+
 /* ---- inspection entry points (used by the parity tests) ---------------- */
 
 /* Number of levels (finest = 0) and the shape of level k: macro-elements per

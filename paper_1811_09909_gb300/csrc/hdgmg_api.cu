@@ -26,6 +26,13 @@ hdgmg_status fail(hdgmg_status st, const std::string& msg) {
   g_last_error = msg;
   return st;
 }
+}  // namespace
+
+namespace hdgmg {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace hdgmg
+
+namespace {
 
 #define CUDA_TRY(call)                                                                    \
   do {                                                                                    \

@@ -218,6 +218,9 @@ void launch_cg_scalars(cudaStream_t s, double* scal, int stage);
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y);
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam);
 
+// set the calling thread's hdgmg_last_error() message
+void set_last_error(const std::string& msg);
+
 // host-side count of kernel launches issued by the library (all threads)
 void note_launch();
 long long launch_count();

@@ -343,11 +343,11 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
   const size_t shm = per_warp * wpb;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [] {
     cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   const int blocks = (nE + wpb - 1) / wpb;
   note_launch();
   condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
@@ -360,7 +360,11 @@ void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double
   const int nE = n * n, nv = (p + 1) * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)nv * threads;
-  cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  static const bool attr = [] {       // enough for p = 8
+    cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
   note_launch();
   rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau_mode, tau_c, hmin,
                                           Lfac, f, b);
@@ -372,7 +376,11 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const do
   const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
-  cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  static const bool attr = [] {       // enough for p = 8
+    cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
   note_launch();
   recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
                                               ref.Cy, kap, tau_mode, tau_c, hmin, Lfac, f, lam,

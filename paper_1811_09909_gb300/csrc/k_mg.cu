@@ -13,6 +13,7 @@
 // every level owns an accumulator y that is zero between kernels: the matvec
 // adds into it and the consumer of y resets it.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "k_common.cuh"
@@ -999,12 +1000,15 @@ void launch_pcoarsen(cudaStream_t s, int nE, int ndf, const T* Af, T* Ac) {
 }
 
 static void upload_jc() {
-  static bool done = false;
-  if (done) return;
-  double J[2][2][2];
-  child_injection(J);
-  cudaMemcpyToSymbol(c_Jc, J, sizeof(J));
-  done = true;
+  // once per device: the constant-memory copy of the child injection
+  static std::once_flag flags[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(flags[dev & 63], [] {
+    double J[2][2][2];
+    child_injection(J);
+    cudaMemcpyToSymbol(c_Jc, J, sizeof(J));
+  });
 }
 
 template <typename T>
@@ -1071,12 +1075,12 @@ bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* free
                               double* Ainv, int* err) {
   const size_t shm = sizeof(double) * ((size_t)nf * nf + nf);
   if (shm > 200 * 1024) return false;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(coarse_setup_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   note_launch();
   coarse_setup_smem_kernel<T><<<1, 1024, shm, s>>>(n, A, freeidx, nf, Ainv, err);
   return true;
@@ -1100,12 +1104,12 @@ template <typename T>
 void launch_vcycle_tail(cudaStream_t s, const TailParams<T>& P) {
   // FP64 needs twice the registers per value: half the threads
   constexpr int NTHR = sizeof(T) == 8 ? 512 : 1024;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(vcycle_tail_kernel<T, NTHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kTailMaxSmem);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   note_launch();
   vcycle_tail_kernel<T, NTHR><<<1, NTHR, P.smem_bytes, s>>>(P);
 }

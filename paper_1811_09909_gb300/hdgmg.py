@@ -23,7 +23,9 @@ EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
             "hdgmg_run_host", "hdgmg_num_levels", "hdgmg_level_shape",
             "hdgmg_copy_element_matrices", "hdgmg_apply_operator", "hdgmg_apply_vcycle",
             "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy",
-            "hdgmg_apply_operator_noalloc", "hdgmg_gradient", "hdgmg_adjoint"]
+            "hdgmg_apply_operator_noalloc", "hdgmg_gradient", "hdgmg_adjoint",
+            "hdgmg_batch_create", "hdgmg_batch_setup", "hdgmg_batch_solve",
+            "hdgmg_batch_context", "hdgmg_batch_destroy"]
 
 
 class Problem(ctypes.Structure):
@@ -85,6 +87,14 @@ def load():
     lib.hdgmg_apply_operator_noalloc.argtypes = [P, I32, P, P]
     lib.hdgmg_gradient.argtypes = [P, P, P, P, ctypes.POINTER(D), P, P, ctypes.POINTER(Info)]
     lib.hdgmg_adjoint.argtypes = [P, P, P, P, P, P, ctypes.POINTER(Info)]
+    PP = ctypes.POINTER(P)
+    lib.hdgmg_batch_create.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(Problem),
+                                       ctypes.POINTER(Opts), I32, P]
+    lib.hdgmg_batch_setup.argtypes = [P, PP]
+    lib.hdgmg_batch_solve.argtypes = [P, I32, PP, PP, PP, PP, PP, ctypes.POINTER(Info)]
+    lib.hdgmg_batch_context.argtypes = [P, I32, ctypes.POINTER(P)]
+    lib.hdgmg_batch_destroy.argtypes = [P]
+    lib.hdgmg_batch_destroy.restype = None
     lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
     lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
     lib.hdgmg_last_error.argtypes = []
@@ -92,7 +102,8 @@ def load():
     lib.hdgmg_destroy.argtypes = [P]
     lib.hdgmg_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("hdgmg_default_opts", "hdgmg_last_error", "hdgmg_destroy"):
+        if name not in ("hdgmg_default_opts", "hdgmg_last_error", "hdgmg_destroy",
+                        "hdgmg_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -273,6 +284,75 @@ class Solver:
         b = self.torch.empty((self.nd, self.n_edges), dtype=self.torch.float64, device="cuda")
         _check(self.lib.hdgmg_condensed_rhs(self.ctx, _ptr(f), _ptr(gD), _ptr(b)))
         return b
+
+
+def _ptr_array(tensors):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Batch:
+    """Many independent problems solved concurrently on one GPU.
+
+    problems: list of dicts with n, p and optionally tau_mode, tau_c, domain;
+    options as keyword arguments (one set for all problems)."""
+
+    def __init__(self, problems, nthreads=8, stream=None, **opts):
+        import torch
+        lib = load()
+        self.torch = torch
+        self.lib = lib
+        self.problems = []
+        arr = (Problem * len(problems))()
+        for i, pr in enumerate(problems):
+            dom = pr.get("domain", (0.0, 1.0, 0.0, 1.0))
+            arr[i] = Problem(pr["n"], pr["p"], dom[0], dom[1], dom[2], dom[3],
+                             pr.get("tau_mode", TAU_OVER_H), pr.get("tau_c", 1.0))
+            self.problems.append((pr["n"], pr["p"]))
+        self.opts = default_opts(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        b = ctypes.c_void_p()
+        _check(lib.hdgmg_batch_create(ctypes.byref(b), len(problems), arr, ctypes.byref(self.opts),
+                                      nthreads, ctypes.c_void_p(stream.cuda_stream)))
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            self.lib.hdgmg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setup(self, log_kappas):
+        _check(self.lib.hdgmg_batch_setup(self.b, _ptr_array(log_kappas)))
+
+    def solve(self, fs, gDs=None, want_u=True, want_q=False):
+        """fs: list of [nrhs][nv][E] tensors; returns (lams, us, qs, infos)."""
+        torch = self.torch
+        nrhs = fs[0].shape[0]
+        lams, us, qs = [], [], []
+        for (n, p), f in zip(self.problems, fs):
+            assert f.shape[0] == nrhs
+            E, nv, ne = n * n, (p + 1) ** 2, 2 * n * (n + 1)
+            lams.append(torch.empty((nrhs, p + 1, ne), dtype=torch.float64, device=f.device))
+            us.append(torch.empty((nrhs, nv, E), dtype=torch.float64, device=f.device) if want_u else None)
+            qs.append(torch.empty((nrhs, 2, nv, E), dtype=torch.float64, device=f.device) if want_q else None)
+        infos = (Info * len(fs))()
+        st = self.lib.hdgmg_batch_solve(self.b, nrhs, _ptr_array(fs),
+                                        _ptr_array(gDs) if gDs is not None else None,
+                                        _ptr_array(lams), _ptr_array(us) if want_u else None,
+                                        _ptr_array(qs) if want_q else None, infos)
+        if st not in (0, -4):
+            _check(st)
+        return lams, us, qs, list(infos)
 
 
 def _autograd_function():

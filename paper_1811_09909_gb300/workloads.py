@@ -186,3 +186,19 @@ def random_vectors(n, nd, count, seed):
     """Seeded N(0,1) trace vectors [count][nd][n_edges] (for operator checks)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal((count, nd, n_edges(n)))
+
+
+def batched(nprob=64, nrhs=16, seed=4, sizes=(32, 64, 128, 256), orders=(2, 4, 8), sigma=0.5):
+    """Independent diffusion problems: n uniform from `sizes`, p uniform from
+    `orders`, log kappa iid N(0, sigma^2) per element, `nrhs` forcing
+    right-hand sides with iid N(0, 1) nodal values, g_D = 0, tau = 1/h."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(nprob):
+        n = int(rng.choice(sizes))
+        p = int(rng.choice(orders))
+        logk = rng.normal(0.0, sigma, size=n * n)
+        f = rng.standard_normal((nrhs, (p + 1) ** 2, n * n))
+        out.append(Workload(f"batch{k}_{n}_p{p}", n, p, logk, f,
+                            np.zeros((nrhs, p + 1, n_edges(n))), "over_h", 1.0, seed=seed))
+    return out
