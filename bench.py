@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arm", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (64 problems x 16 RHS) and adjoint (1024^2) lines")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -240,7 +242,8 @@ def run_ours(args):
         results[name] = {"ms": ms, "iters": infos[-1].iters, "rel_res": worst,
                          "setup_ms": infos[-1].t_setup_ms, "solve_ms": infos[-1].t_solve_ms,
                          "clocks": ck, "wall_s": wall,
-                         "launches": sum(i.kernel_launches for i in infos)}
+                         "launches": sum(i.kernel_launches for i in infos),
+                         "condense_ms": statistics.mean(i.t_condense_ms for i in infos)}
 
     dofs = wl.interior_trace_dofs
     if args.arm != "both":
@@ -288,8 +291,167 @@ def run_ours(args):
                          "setup_ms": fp64["setup_ms"], "solve_ms": fp64["solve_ms"]},
                 "mixed": {"iters": mixed["iters"], "rel_res": mixed["rel_res"],
                           "setup_ms": mixed["setup_ms"], "solve_ms": mixed["solve_ms"]},
-                "clocks": mixed["clocks"], "e2e": e2e, "gpu_launches": mixed["launches"]}
+                "clocks": mixed["clocks"], "e2e": e2e, "gpu_launches": mixed["launches"],
+                "roofline": roofline_condense(mixed["condense_ms"]),
+                "vcycle": vcycle_bandwidth(arms["mixed"], dev)}
     return line
+
+
+# ------------------------------------------------------------- roofline
+# FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk
+# x 2 flop x 2.07 GHz (a standalone FMA-throughput probe measured 1.18).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one condensation launch at 256^2, p = 4: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
+# (profiles/condense_256_p4.md).
+CONDENSE_TRAFFIC_BYTES = 4834816 + 227343616
+
+
+def condense_flops(p, nE):
+    """Algorithmic flops of K1 per launch: Cholesky of S (n_v x n_v),
+    V = L^-1 W (n_t right-hand sides), V^T V (symmetric, n_t x n_t), as FMAs."""
+    nv, nt = (p + 1) ** 2, 4 * (p + 1)
+    chol = sum(m * (m + 1) // 2 for m in range(nv))
+    fwd = nt * nv * (nv - 1) // 2
+    schur = nt * (nt + 1) // 2 * nv
+    return 2.0 * (chol + fwd + schur) * nE
+
+
+def roofline_condense(ms):
+    flops = condense_flops(P_ORDER, N_MESH * N_MESH)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "condense_kernel (element condensation, FP64)", "bound": "alu",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CONDENSE_TRAFFIC_BYTES,
+            "algorithmic_flops_per_launch": flops, "launch_ms": ms,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz "
+                           "(FMA probe on the box: 1.18 TFLOP/s)"}
+
+
+def vcycle_bytes(solver):
+    """Algorithmic HBM bytes of one FP32 V-cycle application: every operator,
+    block-Jacobi inverse and transfer block read once per use, every trace
+    vector read/written once per kernel that touches it."""
+    nl = solver.num_levels()
+    o = solver.opts
+    total = 0.0
+    m = o.m_fine
+    for k in range(nl - 1):
+        n, nd = solver.level_shape(k)
+        nE, ned = n * n, 2 * n * (n + 1)
+        nsym = 4 * nd * (4 * nd + 1) // 2
+        vec = nd * ned * 4
+        matvecs = (m - 1) + 1 + m
+        sweeps = 2 * m
+        total += matvecs * (nsym * nE * 4 + 3 * vec)
+        total += sweeps * (nd * (nd + 1) // 2 * ned * 4 + 3 * vec)
+        if nd == 2 and k + 1 < nl:
+            nC = nE // 4
+            lcs = 2 if o.local_corr == 2 else (1 if o.local_corr == 1 else 0)
+            total += lcs * (164 * nC * 4 + 2 * vec)
+            total += 2 * (64 * nC * 4 + 2 * vec)
+        else:
+            total += 4 * vec
+        m = min(m * o.m_growth, o.m_max) if o.m_max else m * o.m_growth
+    return total
+
+
+def vcycle_bandwidth(solver, dev, reps=20):
+    import torch
+    r = torch.randn((P_ORDER + 1, 2 * N_MESH * (N_MESH + 1)), dtype=torch.float64, device=dev)
+    for _ in range(3):
+        solver.apply_vcycle(r)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        solver.apply_vcycle(r)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    b = vcycle_bytes(solver)
+    gbs = b / (ms * 1e-3) / 1e9
+    return {"ms": ms, "algorithmic_bytes": b, "achieved_gbs": gbs,
+            "hbm_peak_gbs": 6797.9, "frac": gbs / 6797.9,
+            "note": "FP32 V-cycle launched kernel by kernel (hdgmg_apply_vcycle); L2-resident "
+                    "coarse levels make this latency-bound"}
+
+
+# ------------------------------------------------------- extra workloads
+def run_batched(dev, steps, warmup):
+    """64 independent problems, n in {32,64,128,256}, p in {2,4,8}, log kappa
+    iid N(0, 0.5^2), 16 N(0,1) forcing right-hand sides each, mixed precision,
+    one batch call for set-up and one for all solves."""
+    import numpy as np
+    import torch
+    from paper_1811_09909_gb300 import hdgmg
+    rng = np.random.default_rng(4)
+    shapes = [(int(rng.choice((32, 64, 128, 256))), int(rng.choice((2, 4, 8)))) for _ in range(64)]
+    gen = torch.Generator(device=dev).manual_seed(4)
+    logks = [torch.randn(n * n, generator=gen, device=dev, dtype=torch.float64) * 0.5 for n, p in shapes]
+    fs = [torch.randn((16, (p + 1) ** 2, n * n), generator=gen, device=dev, dtype=torch.float64)
+          for n, p in shapes]
+    b = hdgmg.Batch([dict(n=n, p=p) for n, p in shapes], nthreads=16,
+                    precision=hdgmg.PREC_FP32, **SOLVER_OPTS)
+    dofs = sum(2 * n * (n - 1) * (p + 1) for n, p in shapes) * 16
+    stream = torch.cuda.current_stream(dev)
+    times, worst = [], 0.0
+    for it in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.setup(logks)
+        lams, us, _, infos = b.solve(fs, want_u=True, want_q=False)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+            worst = max(worst, max(i.rel_res for i in infos))
+    del lams, us
+    b.close()
+    ms = statistics.mean(times)
+    return {"value": dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "problems": 64,
+            "rhs_per_problem": 16, "trace_dofs_x_rhs": dofs, "worst_rel_res": worst,
+            "workload": "64 problems, n in {32,64,128,256}, p in {2,4,8}, log kappa iid N(0,0.25), "
+                        "16 N(0,1) right-hand sides each; mixed precision, one batch set-up + solve"}
+
+
+def run_adjoint(dev, steps, warmup):
+    """Misfit gradient at 1024 x 1024, p = 4: set-up, forward solve, misfit,
+    transposed multigrid solve and per-element contraction."""
+    import torch
+    from paper_1811_09909_gb300 import hdgmg
+    n, p = 1024, 4
+    gen = torch.Generator(device=dev).manual_seed(52)
+    logk = torch.randn(n * n, generator=gen, device=dev, dtype=torch.float64)
+    f = torch.ones(((p + 1) ** 2, n * n), device=dev, dtype=torch.float64)
+    s = hdgmg.Solver(n, p, precision=hdgmg.PREC_FP32, **SOLVER_OPTS)
+    s.setup(logk)
+    _, u_ref, _, _ = s.solve(f, want_q=False)
+    u_obs = u_ref * (1.0 + 0.01 * torch.randn(u_ref.shape, generator=gen, device=dev,
+                                              dtype=torch.float64))
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for it in range(warmup + steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.setup(logk)
+        J, gk, gf, info = s.gradient(f, u_obs)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    dofs = 2 * n * (n - 1) * (p + 1)
+    s.close()
+    return {"ms_per_gradient": ms, "trace_dofs": dofs, "parameters": n * n,
+            "adjoint_iters": info.iters, "adjoint_rel_res": info.rel_res,
+            "workload": "1024x1024 quads, p=4, log kappa iid N(0,1), J = 1/2 |u - u_obs|_M^2 with "
+                        "1% noise; set-up + forward + adjoint solve + contraction, mixed precision"}
 
 
 def main():
@@ -302,6 +464,11 @@ def main():
         return
     rank = int(os.environ.get("RANK", "0"))
     line = run_ours(args)
+    if rank == 0 and line is not None and args.arm == "both" and not args.no_extra:
+        import torch
+        dev = torch.device("cuda", 0)
+        line["batched"] = run_batched(dev, steps=2, warmup=1)
+        line["adjoint"] = run_adjoint(dev, steps=2, warmup=1)
     if rank == 0:
         if (not args.no_cpu_baseline and args.arm == "both"
                 and int(os.environ.get("WORLD_SIZE", "1")) == 1):

@@ -110,6 +110,8 @@ typedef struct {
   int64_t kernel_launches; /* kernels run by the last setup + solve (graph
                               nodes counted once per replay)                 */
   int32_t refinements;    /* FP32_IR: outer FP64 refinement steps, else 0    */
+  double t_condense_ms;   /* device time of the element condensation kernel
+                             in the last hdgmg_setup (CUDA events around it) */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

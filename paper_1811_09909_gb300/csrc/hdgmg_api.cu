@@ -81,8 +81,8 @@ struct hdgmg_ctx {
   // host-call staging
   double *st_f = nullptr, *st_g = nullptr, *st_l = nullptr, *st_u = nullptr, *st_q = nullptr;
   bool setup_done = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double t_setup_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
+  double t_setup_ms = 0.0, t_condense_ms = 0.0;
   // PCG loop as one CUDA graph with a device-evaluated while condition
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t cg_graph = nullptr;
@@ -629,6 +629,8 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evk0) cudaEventDestroy(c->evk0);
+  if (c->evk1) cudaEventDestroy(c->evk1);
   delete c;
 }
 
@@ -810,6 +812,8 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     plan_tail<double>(c, 16);
   CTRY(cudaEventCreate(&c->ev0));
   CTRY(cudaEventCreate(&c->ev1));
+  CTRY(cudaEventCreate(&c->evk0));
+  CTRY(cudaEventCreate(&c->evk1));
   CTRY(cudaDeviceSynchronize());
 #undef CTRY
   *out = c;
@@ -826,8 +830,10 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
   Level& L0 = c->levels[0];
   launch_kappa(s, nE, c->logk, c->kap);
+  CUDA_TRY(cudaEventRecord(c->evk0, s));
   launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                   L0.d64.A, c->Lfac, c->err);
+  CUDA_TRY(cudaEventRecord(c->evk1, s));
   STATUS_TRY(check_launch("condensation"));
   if (c->opts.precision != HDGMG_PREC_FP64) {
     launch_convert<double, float>(s, (int64_t)L0.nsym * L0.nE, L0.d64.A, L0.d32.A);
@@ -841,6 +847,8 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->t_setup_ms = ms;
+  cudaEventElapsedTime(&ms, c->evk0, c->evk1);
+  c->t_condense_ms = ms;
   c->launches_setup = launch_count() - l0;
   if (c->err_h[0]) {
     c->setup_done = false;
@@ -877,6 +885,7 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     info->t_solve_ms = ms;
     info->t_setup_ms = c->t_setup_ms;
+    info->t_condense_ms = c->t_condense_ms;
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }
