@@ -97,6 +97,10 @@ typedef struct {
                              V-cycle on the normalised residual; FP64         */
   double inner_rtol;      /* FP32_IR only: inner PCG tolerance per refinement
                              step, in (0,1); 1e-5                             */
+  int32_t cluster_tail_n; /* > 0: the P1 levels with n <= this run fused in
+                             one thread-block cluster (distributed shared
+                             memory); <= 0: not used (the single-block tail
+                             and separate launches are faster on GB300); 0   */
 } hdgmg_opts;
 
 typedef struct {

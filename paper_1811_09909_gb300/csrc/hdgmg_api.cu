@@ -103,6 +103,10 @@ struct hdgmg_ctx {
   int refinements = 0;
   TailParams<float> tp32;
   TailParams<double> tp64;
+  // P1 tail run by one thread-block cluster (preferred when available)
+  int ctail_start = -1;
+  CTailParams<float> cp32;
+  CTailParams<double> cp64;
 
   template <typename T>
   cudaError_t alloc(T** p_, size_t count) {
@@ -122,6 +126,9 @@ namespace {
 template <typename T> LevelData<T>& ld(Level& L);
 template <> LevelData<double>& ld<double>(Level& L) { return L.d64; }
 template <> LevelData<float>& ld<float>(Level& L) { return L.d32; }
+template <typename T> CTailParams<T>& ctailp(hdgmg_ctx* c);
+template <> CTailParams<double>& ctailp<double>(hdgmg_ctx* c) { return c->cp64; }
+template <> CTailParams<float>& ctailp<float>(hdgmg_ctx* c) { return c->cp32; }
 template <typename T> TailParams<T>& tailp(hdgmg_ctx* c);
 template <> TailParams<double>& tailp<double>(hdgmg_ctx* c) { return c->tp64; }
 template <> TailParams<float>& tailp<float>(hdgmg_ctx* c) { return c->tp32; }
@@ -219,6 +226,105 @@ void plan_tail(hdgmg_ctx* c, int tail_n) {
   P.lc = c->opts.local_corr;
 }
 
+
+// Cluster tail: the P1 levels with n <= top_n down to the coarsest, split
+// over `cl` CTAs.  Vectors always live in distributed shared memory; level
+// operators are staged from the coarsest level upwards while they fit.
+template <typename T>
+size_t ctail_layout(hdgmg_ctx* c, int start, int cl, const std::vector<int>& staged,
+                    CTailParams<T>* P) {
+  const int last = (int)c->levels.size() - 1;
+  size_t off = 0;
+  auto take = [&](size_t count) {
+    size_t o = off;
+    off += (count + 3) / 4 * 4;
+    return o;
+  };
+  auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
+  for (int k = start; k <= last; ++k) {
+    const Level& L = c->levels[k];
+    CTailLevel<T> t;
+    t.n = L.n;
+    t.m = L.m;
+    t.nEdge = L.nEdge;
+    t.echunk = cdiv(L.nE, cl);
+    t.edchunk = cdiv(L.nEdge, cl);
+    t.cchunk = (k < last) ? cdiv(L.nE / 4, cl) : 1;
+    t.off_v = (int)take(6 * (size_t)t.edchunk);
+    if (k < last && staged[k]) {
+      t.off_A = (int)take(36 * (size_t)t.echunk);
+      t.off_D = (int)take(3 * (size_t)t.edchunk);
+      t.off_AII = (int)take(36 * (size_t)t.cchunk);
+      t.off_Y = (int)take(128 * (size_t)t.cchunk);
+      t.off_Pi = (int)take(64 * (size_t)t.cchunk);
+    }
+    if (P) P->lv[k - start] = t;
+  }
+  size_t bytes = (off * sizeof(T) + 15) / 16 * 16;
+  const size_t w_off = bytes;
+  bytes += sizeof(double) * (size_t)(c->nf + 2);
+  if (P) {
+    P->w_off = (int)w_off;
+    P->smem_bytes = (int)bytes;
+  }
+  return bytes;
+}
+
+template <typename T>
+void plan_ctail(hdgmg_ctx* c, int top_n) {
+  c->ctail_start = -1;
+  const int last = (int)c->levels.size() - 1;
+  if (last < 1) return;
+  int start = last;
+  while (start - 1 >= 0) {
+    const Level& L = c->levels[start - 1];
+    if (L.nd != 2 || L.transfer != 2 || L.n > top_n || last - (start - 1) + 1 > kMaxTail) break;
+    --start;
+  }
+  if (start == last) return;                 // nothing above the coarsest level to fuse
+  const size_t cap = (size_t)kTailMaxSmem;
+  for (int cl : {16, 8}) {
+    for (int s0 = start; s0 < last; ++s0) {
+      std::vector<int> staged(c->levels.size(), 0);
+      if (ctail_layout<T>(c, s0, cl, staged, nullptr) > cap) continue;
+      for (int k = last - 1; k >= s0; --k) {
+        staged[k] = 1;
+        if (ctail_layout<T>(c, s0, cl, staged, nullptr) > cap) {
+          staged[k] = 0;
+          break;
+        }
+      }
+      const size_t bytes = ctail_layout<T>(c, s0, cl, staged, nullptr);
+      if (ctail_max_clusters<T>(cl, (int)bytes) < 1) break;   // try a smaller cluster
+      CTailParams<T>& P = ctailp<T>(c);
+      P = CTailParams<T>();
+      P.nlev = last - s0 + 1;
+      P.cl = cl;
+      ctail_layout<T>(c, s0, cl, staged, &P);
+      for (int k = s0; k <= last; ++k) {
+        LevelData<T>& D = ld<T>(c->levels[k]);
+        CTailLevel<T>& t = P.lv[k - s0];
+        t.A = D.A;
+        t.Dinv = D.Dinv;
+        t.AIIinv = D.AIIinv;
+        t.Y = D.Y;
+        t.Pi = D.Pi;
+      }
+      P.r_in = ld<T>(c->levels[s0]).r;
+      P.e_out = ld<T>(c->levels[s0]).e;
+      P.Ainv = c->cinv;
+      P.fidx = c->freeidx;
+      P.fedge = c->fedge;
+      P.nf = c->nf;
+      P.omega = (T)c->opts.omega;
+      P.lc = c->opts.local_corr;
+      child_injection(P.Jc);
+      c->ctail_start = s0;
+      return;
+    }
+  }
+}
+
 hdgmg_status check_launch(const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(HDGMG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -232,6 +338,10 @@ void vcycle(hdgmg_ctx* c, int l) {
   Level& L = c->levels[l];
   LevelData<T>& D = ld<T>(L);
   const int last = (int)c->levels.size() - 1;
+  if (l == c->ctail_start) {                                // cluster-fused P1 tail
+    launch_ctail<T>(s, ctailp<T>(c));
+    return;
+  }
   if (l == c->tail_start) {                                 // fused P1 tail + B_1 = A_1^-1
     launch_vcycle_tail<T>(s, tailp<T>(c));
     return;
@@ -610,6 +720,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->rtol = 1e-10;
   o->precision = HDGMG_PREC_FP64;
   o->inner_rtol = 1e-5;
+  o->cluster_tail_n = 0;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -806,10 +917,19 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     CTRY(c->alloc(&c->clinv, (size_t)c->nf * c->nf));
     CTRY(c->alloc(&c->cinv, (size_t)c->nf * c->nf));
   }
-  if (fp32)
+  // The cluster tail is opt-in: measured on GB300 (256^2, p = 4) its
+  // distributed-shared-memory steps and cluster barriers cost more per step
+  // than the single-block tail plus separate launches of the larger levels.
+  const int ct = o.cluster_tail_n;
+  if (fp32) {
     plan_tail<float>(c, 32);
-  else
+    if (ct > 0) plan_ctail<float>(c, ct);
+  } else {
     plan_tail<double>(c, 16);
+    if (ct > 0) plan_ctail<double>(c, ct);
+  }
+  if (c->ctail_start >= 0 && c->tail_start >= 0 && c->tail_start < c->ctail_start)
+    c->ctail_start = -1;                     // keep whichever fuses more levels
   CTRY(cudaEventCreate(&c->ev0));
   CTRY(cudaEventCreate(&c->ev1));
   CTRY(cudaEventCreate(&c->evk0));

@@ -169,6 +169,41 @@ struct TailParams {
 template <typename T>
 void launch_vcycle_tail(cudaStream_t s, const TailParams<T>& P);
 
+// fused V-cycle over the P1 tail on one thread-block cluster (k_ctail.cu)
+template <typename T>
+struct CTailLevel {
+  int n = 0, m = 1, nEdge = 0;
+  int echunk = 0, edchunk = 0, cchunk = 0;   // elements / edges / macro-elements per CTA
+  // shared-memory offsets (T units): vectors [r|e|y] x [2][edchunk]; staged
+  // operators ([stride][chunk]) or -1 when they are read from global memory
+  int off_v = 0, off_A = -1, off_D = -1, off_AII = -1, off_Y = -1, off_Pi = -1;
+  const T* A = nullptr;
+  const T* Dinv = nullptr;
+  const T* AIIinv = nullptr;
+  const T* Y = nullptr;
+  const T* Pi = nullptr;
+};
+template <typename T>
+struct CTailParams {
+  int nlev = 0, cl = 0;
+  CTailLevel<T> lv[kMaxTail];
+  const T* r_in = nullptr;
+  T* e_out = nullptr;
+  const double* Ainv = nullptr;
+  const int* fidx = nullptr;
+  const int* fedge = nullptr;
+  int nf = 0;
+  int w_off = 0;                // byte offset of the coarse-solve workspace
+  T omega = T(1);
+  int lc = 0;
+  double Jc[2][2][2] = {};
+  int smem_bytes = 0;
+};
+template <typename T>
+int ctail_max_clusters(int cluster, int smem_bytes);
+template <typename T>
+void launch_ctail(cudaStream_t s, const CTailParams<T>& P);
+
 // coarsest level: dense FP64 Cholesky of the interior operator
 template <typename T>
 void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,

@@ -34,44 +34,6 @@ __global__ void pcoarsen_kernel(int nE, int ndf, const T* __restrict__ Af, T* __
     }
 }
 
-// ---------------------------------------------- 2x2 agglomeration geometry
-// Interior edges of macro-element C = (I, J) (fine mesh n = 2 nc):
-//   ie 0: v(2I+1, 2J)  1: v(2I+1, 2J+1)  2: h(2I, 2J+1)  3: h(2I+1, 2J+1)
-// Perimeter child edges (me, c): me 0 left v(2I, 2J+c), 1 right v(2I+2, 2J+c),
-//   2 bottom h(2I+c, 2J), 3 top h(2I+c, 2J+2); c = 0 is the half at the
-//   lower coordinate.  Local index: interior ie*2+k, boundary (me*2+c)*2+k.
-__device__ __forceinline__ int fine_v(int n, int i, int j) { return j * (n + 1) + i; }
-__device__ __forceinline__ int fine_h(int n, int i, int j) { return n * (n + 1) + j * n + i; }
-
-__device__ __forceinline__ int interior_edge(int n, int I, int J, int ie) {
-  switch (ie) {
-    case 0: return fine_v(n, 2 * I + 1, 2 * J);
-    case 1: return fine_v(n, 2 * I + 1, 2 * J + 1);
-    case 2: return fine_h(n, 2 * I, 2 * J + 1);
-    default: return fine_h(n, 2 * I + 1, 2 * J + 1);
-  }
-}
-
-__device__ __forceinline__ int perimeter_edge(int n, int I, int J, int me, int c) {
-  switch (me) {
-    case 0: return fine_v(n, 2 * I, 2 * J + c);
-    case 1: return fine_v(n, 2 * I + 2, 2 * J + c);
-    case 2: return fine_h(n, 2 * I + c, 2 * J);
-    default: return fine_h(n, 2 * I + c, 2 * J + 2);
-  }
-}
-
-// child ch = cj*2 + ci, local edge le -> (interior?, slot) with slot = ie or me*2+c
-__device__ __forceinline__ void child_map(int ch, int le, bool& interior, int& slot) {
-  const int ci = ch & 1, cj = ch >> 1;
-  switch (le) {
-    case 0: interior = (ci == 1); slot = interior ? cj : (0 * 2 + cj); break;
-    case 1: interior = (ci == 0); slot = interior ? cj : (1 * 2 + cj); break;
-    case 2: interior = (cj == 1); slot = interior ? 2 + ci : (2 * 2 + ci); break;
-    default: interior = (cj == 0); slot = interior ? 2 + ci : (3 * 2 + ci); break;
-  }
-}
-
 __constant__ double c_Jc[2][2][2];   // child injection [child][fine mode][coarse mode]
 
 // -------------------------------------------------- K4 agglomeration setup
@@ -263,8 +225,6 @@ __global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
   if (C < nc * nc) local_correction_item<T>(nc, AIIinv, Y, r, e, C);
 }
 
-__device__ __forceinline__ int coarse_v(int nc, int I, int J) { return J * (nc + 1) + I; }
-__device__ __forceinline__ int coarse_h(int nc, int I, int J) { return nc * (nc + 1) + J * nc + I; }
 
 // --------------------------------------------------------- K9 restriction
 // r_c = J^T s_B + Pi^T s_I (Q_{k-1} of eq. n_1_Qk with Pi^T = -J^T A_BI A_II^-1

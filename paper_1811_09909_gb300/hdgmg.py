@@ -41,7 +41,7 @@ class Opts(ctypes.Structure):
                 ("local_corr", ctypes.c_int32), ("omega", ctypes.c_double),
                 ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("inner_rtol", ctypes.c_double)]
+                ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
