@@ -63,7 +63,7 @@ typedef enum {
 
 enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min */
 enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
-enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1 };
+enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1, HDGMG_KRYLOV_GMRES = 2 };
 enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
@@ -86,7 +86,10 @@ typedef struct {
   int32_t m_max;          /* cap on m_k (0 = none); 0                        */
   int32_t local_corr;     /* HDGMG_LC_*: step 3 / steps 3+5 of Alg. 1; BOTH  */
   double omega;           /* block-Jacobi damping (1 = paper, undamped); 1   */
-  int32_t krylov;         /* NONE = MG as fixed-point solver, CG; CG         */
+  int32_t krylov;         /* NONE = MG as fixed-point solver, CG (symmetric
+                             cycle), GMRES = flexible GMRES(gmres_restart)
+                             right-preconditioned by the cycle (the paper's
+                             Krylov method, Sec. 4); CG                       */
   int32_t max_it;         /* outer iterations; 200                           */
   double rtol;            /* ||g - A lambda||_2 / ||g||_2 target; 1e-10      */
   int32_t precision;      /* FP64: PCG in FP64 with the FP64 V-cycle.
@@ -101,6 +104,7 @@ typedef struct {
                              one thread-block cluster (distributed shared
                              memory); <= 0: not used (the single-block tail
                              and separate launches are faster on GB300); 0   */
+  int32_t gmres_restart;  /* GMRES restart length m, 1..256; 30              */
 } hdgmg_opts;
 
 typedef struct {

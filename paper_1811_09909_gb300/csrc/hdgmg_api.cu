@@ -75,6 +75,14 @@ struct hdgmg_ctx {
   double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *b = nullptr;
   double *lam = nullptr, *partial = nullptr, *scal = nullptr, *scal_h = nullptr;
   unsigned* counter = nullptr;   // last-block counter of the fused reductions
+  // flexible GMRES (allocated on first use): V [(m+1)][len], Z [m][len]
+  double *gmV = nullptr, *gmZ = nullptr, *gmH = nullptr, *gmcs = nullptr, *gmsn = nullptr;
+  double *gmg = nullptr, *gmh = nullptr, *gmpart = nullptr, *gmtol = nullptr, *gmh_host = nullptr;
+  int* gmj = nullptr;
+  int* gmtot = nullptr;
+  cudaGraph_t gm_graph = nullptr;
+  cudaGraphExec_t gm_exec = nullptr;
+  long long gm_body_launches = 0;
   // adjoint buffers (allocated on first use)
   double *adj_f = nullptr, *adj_lam = nullptr, *adj_u = nullptr;
   double *fwd_lam = nullptr, *fwd_u = nullptr, *mis_d = nullptr, *mis_g = nullptr;
@@ -583,6 +591,101 @@ hdgmg_status refine_solve(hdgmg_ctx* c, double nb, int* iters, int* outer, doubl
   return HDGMG_OK;
 }
 
+// One Arnoldi step of right-preconditioned flexible GMRES (all on the
+// device; the index j is read from device memory by every kernel).
+void gm_body(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const int m = c->opts.gmres_restart;
+  launch_gm_select(s, len, c->gmV, c->gmj, 0, c->pv);          // v_j
+  apply_B(c, c->pv, c->z);                                     // z_j = B v_j
+  launch_gm_store(s, len, c->z, c->gmZ, c->gmj, 0);            // Z[j] = z_j
+  apply_A64(c, c->z, c->Ap);                                   // w = A z_j
+  launch_gm_orthogonalize(s, len, c->gmV, c->gmj, c->Ap, c->gmpart, m + 1, c->gmH, c->gmh, m + 1, 0);
+  launch_gm_orthogonalize(s, len, c->gmV, c->gmj, c->Ap, c->gmpart, m + 1, c->gmH, c->gmh, m + 1, 1);
+  launch_dot_fused<double>(s, len, c->Ap, c->Ap, c->partial, c->counter, c->scal, 2);
+  launch_gm_normalize(s, len, c->Ap, c->scal + 5, c->gmV, c->gmj);
+  launch_gm_givens(s, c->gmH, m + 1, c->gmcs, c->gmsn, c->gmg, c->gmj, m, c->gmtol, c->scal + 5, h,
+                   c->gmtot, c->opts.max_it);
+}
+
+hdgmg_status gmres_buffers(hdgmg_ctx* c) {
+  if (c->gmV) return HDGMG_OK;
+  const int m = c->opts.gmres_restart;
+  const int64_t len = c->fine_len();
+  CUDA_TRY(c->alloc(&c->gmV, (size_t)(m + 1) * len));
+  CUDA_TRY(c->alloc(&c->gmZ, (size_t)m * len));
+  CUDA_TRY(c->alloc(&c->gmH, (size_t)(m + 1) * m));
+  CUDA_TRY(c->alloc(&c->gmcs, (size_t)m));
+  CUDA_TRY(c->alloc(&c->gmsn, (size_t)m));
+  CUDA_TRY(c->alloc(&c->gmg, (size_t)m + 1));
+  CUDA_TRY(c->alloc(&c->gmh, (size_t)m + 1));
+  CUDA_TRY(c->alloc(&c->gmpart, (size_t)(m + 1) * gm_partial_blocks()));
+  CUDA_TRY(c->alloc(&c->gmtol, 2));
+  CUDA_TRY(c->alloc(&c->gmj, 2));
+  CUDA_TRY(c->alloc(&c->gmtot, 2));
+  CUDA_TRY(cudaMallocHost(&c->gmh_host, sizeof(double) * ((size_t)(m + 1) * m + 2 * (m + 1) + 8)));
+  return HDGMG_OK;
+}
+
+// FGMRES(m) with the V-cycle as right preconditioner; restarts recompute the
+// true FP64 residual.  Returns the total number of Arnoldi steps.
+hdgmg_status gmres_solve(hdgmg_ctx* c, double nb, int* iters, double* rel, bool* conv,
+                         bool* breakdown) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const hdgmg_opts& o = c->opts;
+  const int m = o.gmres_restart;
+  STATUS_TRY(gmres_buffers(c));
+  STATUS_TRY(build_loop_graph(c, gm_body, &c->gm_graph, &c->gm_exec, &c->gm_body_launches));
+  *iters = 0;
+  *conv = false;
+  *breakdown = false;
+  CUDA_TRY(cudaMemsetAsync(c->gmtot, 0, sizeof(int), s));
+  double* Hh = c->gmh_host;
+  double* gh = Hh + (size_t)(m + 1) * m;
+  double* yh = gh + (m + 1);
+  int* jh = reinterpret_cast<int*>(yh + (m + 1));
+  for (int cycle = 0; cycle < o.max_it; ++cycle) {
+    // r = b - A x, its norm, v_0 = r / ||r||
+    CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->x, c->r, -1.0);
+    const double rr = dot_sync(c, c->r, c->r);
+    *rel = std::sqrt(rr) / nb;
+    if (!std::isfinite(rr)) { *breakdown = true; return HDGMG_OK; }
+    if (*rel <= o.rtol) { *conv = true; return HDGMG_OK; }
+    if (*iters >= o.max_it) return HDGMG_OK;
+    const double beta = std::sqrt(rr);
+    launch_axpby(s, len, 1.0 / beta, c->r, 0.0, c->gmV);
+    CUDA_TRY(cudaMemsetAsync(c->gmH, 0, sizeof(double) * (size_t)(m + 1) * m, s));
+    CUDA_TRY(cudaMemsetAsync(c->gmg, 0, sizeof(double) * (size_t)(m + 1), s));
+    CUDA_TRY(cudaMemsetAsync(c->gmj, 0, sizeof(int), s));
+    c->init_h[4] = beta;
+    c->init_h[5] = o.rtol * nb;
+    CUDA_TRY(cudaMemcpyAsync(c->gmg, &c->init_h[4], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->gmtol, &c->init_h[5], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(c->gm_exec, s));
+    CUDA_TRY(cudaMemcpyAsync(jh, c->gmj, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(Hh, c->gmH, sizeof(double) * (size_t)(m + 1) * m, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(gh, c->gmg, sizeof(double) * (size_t)(m + 1), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int j = *jh;
+    *iters += j;
+    c->launches_solve += c->gm_body_launches * j;
+    // y = R^-1 g (upper triangular, column-major R = H[:, 0..j-1])
+    for (int i = j - 1; i >= 0; --i) {
+      double sacc = gh[i];
+      for (int k = i + 1; k < j; ++k) sacc -= Hh[(size_t)k * (m + 1) + i] * yh[k];
+      const double d = Hh[(size_t)i * (m + 1) + i];
+      yh[i] = d != 0.0 ? sacc / d : 0.0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->gmh, yh, sizeof(double) * (size_t)j, cudaMemcpyHostToDevice, s));
+    launch_gm_update(s, len, c->gmZ, j, c->gmh, c->x);
+    STATUS_TRY(check_launch("gmres update"));
+  }
+  return HDGMG_OK;
+}
+
 hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* lam_out,
                        double* u, double* q, hdgmg_info* info) {
   cudaStream_t s = c->stream;
@@ -599,6 +702,8 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   if (!(nb > 0.0)) {
     conv = true;
     if (!std::isfinite(bb)) breakdown = true;
+  } else if (o.krylov == HDGMG_KRYLOV_GMRES) {
+    STATUS_TRY(gmres_solve(c, nb, &it, &rel, &conv, &breakdown));
   } else if (o.krylov == HDGMG_KRYLOV_CG && o.precision == HDGMG_PREC_FP32_IR) {
     int outer = 0;
     STATUS_TRY(refine_solve(c, nb, &it, &outer, &rel, &conv, &breakdown));
@@ -721,6 +826,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->precision = HDGMG_PREC_FP64;
   o->inner_rtol = 1e-5;
   o->cluster_tail_n = 0;
+  o->gmres_restart = 30;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -736,6 +842,9 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
   if (c->cg_graph) cudaGraphDestroy(c->cg_graph);
   if (c->cg32_exec) cudaGraphExecDestroy(c->cg32_exec);
+  if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
+  if (c->gm_graph) cudaGraphDestroy(c->gm_graph);
+  if (c->gmh_host) cudaFreeHost(c->gmh_host);
   if (c->cg32_graph) cudaGraphDestroy(c->cg32_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -765,7 +874,9 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.coarsest_n < 2) return fail(HDGMG_EINVAL, "coarsest_n must be >= 2");
   if (o.m_fine < 1 || o.m_growth < 1 || o.m_max < 0) return fail(HDGMG_EINVAL, "bad smoothing schedule");
   if (o.local_corr < 0 || o.local_corr > 2) return fail(HDGMG_EINVAL, "unknown local_corr");
-  if (o.krylov < 0 || o.krylov > 1) return fail(HDGMG_EINVAL, "unknown krylov");
+  if (o.krylov < 0 || o.krylov > 2) return fail(HDGMG_EINVAL, "unknown krylov");
+  if (o.krylov == HDGMG_KRYLOV_GMRES && (o.gmres_restart < 1 || o.gmres_restart > 256))
+    return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
   if (o.precision < 0 || o.precision > 2) return fail(HDGMG_EINVAL, "unknown precision");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
   if (!(o.inner_rtol > 0.0) || !(o.inner_rtol < 1.0)) return fail(HDGMG_EINVAL, "inner_rtol must be in (0,1)");

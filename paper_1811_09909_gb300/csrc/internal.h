@@ -253,6 +253,23 @@ void launch_cg_scalars(cudaStream_t s, double* scal, int stage);
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y);
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam);
 
+// flexible GMRES (k_krylov.cu); jp: device Arnoldi index
+int gm_partial_blocks();
+void launch_gm_select(cudaStream_t s, int64_t len, const double* base, const int* jp, int shift,
+                      double* out);
+void launch_gm_store(cudaStream_t s, int64_t len, const double* in, double* base, const int* jp,
+                     int shift);
+void launch_gm_orthogonalize(cudaStream_t s, int64_t len, const double* V, const int* jp,
+                             double* w, double* partial, int ldh, double* H, double* h,
+                             int max_k, int accumulate);
+void launch_gm_normalize(cudaStream_t s, int64_t len, const double* w, const double* nrm2, double* V,
+                         const int* jp);
+void launch_gm_givens(cudaStream_t s, double* H, int ldh, double* cs, double* sn, double* g, int* jp,
+                      int m, const double* tolp, const double* nrm2, cudaGraphConditionalHandle hdl,
+                      int* total, int max_total);
+void launch_gm_update(cudaStream_t s, int64_t len, const double* Z, int nk, const double* y,
+                      double* x);
+
 // set the calling thread's hdgmg_last_error() message
 void set_last_error(const std::string& msg);
 

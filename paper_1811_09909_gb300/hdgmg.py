@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhdgmg.so")
 
 TAU_CONST, TAU_OVER_H = 0, 1
 LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
-KRYLOV_NONE, KRYLOV_CG = 0, 1
+KRYLOV_NONE, KRYLOV_CG, KRYLOV_GMRES = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_IR = 0, 1, 2
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("local_corr", ctypes.c_int32), ("omega", ctypes.c_double),
                 ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32)]
+                ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32),
+                ("gmres_restart", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

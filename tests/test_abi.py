@@ -46,18 +46,22 @@ def test_default_options(lib):
     assert o.local_corr == hdgmg.LC_BOTH and o.krylov == hdgmg.KRYLOV_CG
     assert o.omega == 1.0 and o.rtol == 1e-10 and o.max_it == 200
     assert o.precision == hdgmg.PREC_FP64 and o.inner_rtol == 1e-5
+    assert o.cluster_tail_n == 0 and o.gmres_restart == 30
 
 
 @pytest.mark.parametrize("kw,msg", [
     (dict(p=0), "p must"), (dict(p=9), "p must"), (dict(n=1), "n must"),
     (dict(n=12, coarsest=2), "halve"), (dict(tau_c=-1.0), "tau_c"),
+    (dict(krylov=2, restart=0), "gmres_restart"), (dict(krylov=2, restart=257), "gmres_restart"),
+    (dict(krylov=3), "krylov"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg
     n = kw.get("n", 16)
     p = kw.get("p", 2)
     prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0))
-    o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2))
+    o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2), krylov=kw.get("krylov", 1),
+                           gmres_restart=kw.get("restart", 30))
     ctx = ctypes.c_void_p()
     st = lib.hdgmg_create(ctypes.byref(ctx), ctypes.byref(prob), ctypes.byref(o), None)
     assert st == -1
