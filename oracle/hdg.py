@@ -33,10 +33,28 @@ n*(n+1) + j*n + i; element-local edges 0=left, 1=right, 2=bottom, 3=top.
 Trace vectors handed in and out use the mode-major layout [mode][edge]; the
 oracle works internally edge-major (dof = edge*(p+1) + mode).
 
+Convection-diffusion (not in the paper; the library's stated extension):
+-div(eps grad u) + div(beta u) = f with constant beta and eps = kappa per
+element.  The flux variable stays q = -eps grad u; HDG_local2 becomes
+  -(q + beta u, grad w)_K + <hhat.n, w>_dK = (f, w)_K,
+  hhat.n = q.n + (beta.n) lambda + tau_f (u - lambda),
+and the conservation condition sums <hhat.n, mu> over both sides of every
+interior edge.  tau_f = tau_e + max(beta.n_f, 0) on face f (upwinding: on
+outflow faces the total flux uses the interior u).  The local block is no
+longer symmetric; the same general LU condenses it into
+  A_e = C L^-1 R - T,  T = sum_f (beta.n_f - tau_f) El_f.
+With beta = 0 this is the diffusion element (T = -tau El).
+
 Pins (tests/test_oracle_hdg.py): polynomial patch test (exact to roundoff),
 O(h^{p+1}) rates for u and q, A_e 1 = 0, A_e symmetric PSD, homogeneity
 A_e(c kappa, c tau) = c A_e, SPD global trace operator, condensed solve equal
 to a dense uncondensed solve, closed-form 1x1 p=0 element.
+Convection-diffusion (tests/test_oracle_convdiff.py): the general path with
+beta = 0 equals the diffusion path; linear and quadratic patch tests with
+convection (exact to roundoff); the closed form A_e 1 = <beta.n, mu>;
+positive-definite symmetric part of the global trace operator (the upwind
+tau); O(h^{p+1}) rates for u; condensed solve equal to the dense uncondensed
+solve.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -109,6 +127,11 @@ class ElementForms:
         Cy = np.zeros((nv, nt))
         Fb = np.zeros((nv, nt))                     # <psi_k, phi_a>
         El = np.zeros((nt, nt))                     # <psi_l, psi_k>
+        # per-face pieces for face-dependent tau and the convective flux
+        self.Eb_f = np.zeros((4, nv, nv))
+        self.Fb_f = np.zeros((4, nv, nt))
+        self.El_f = np.zeros((4, nt, nt))
+        self.normals = np.zeros((4, 2))
         for edge in range(4):
             ph, psi, wds, (nx, ny) = rq.edge_tables(edge)
             sl = slice(edge * (p + 1), (edge + 1) * (p + 1))
@@ -121,6 +144,12 @@ class ElementForms:
             Cy[:, sl] += ny * mass_vt
             Fb[:, sl] += mass_vt
             El[sl, sl] += (psi * wds) @ psi.T
+            self.Eb_f[edge] = mass_vv
+            self.Fb_f[edge][:, sl] = mass_vt
+            self.El_f[edge][sl, sl] = (psi * wds) @ psi.T
+            self.normals[edge] = (nx, ny)
+        self.Dx, self.Dy = Dx, Dy
+        self.Cx, self.Cy = Cx, Cy
         Z = np.zeros((nv, nv))
         # rows: [HDG_local1 x-test, HDG_local1 y-test, HDG_local2]
         self.LM = np.block([[Mv, Z, Z], [Z, Mv, Z], [Z, Z, Z]])
@@ -142,6 +171,22 @@ class ElementForms:
         C = self.C0 + tau * self.Ct
         return L, R, C
 
+    def local_cd(self, kappa, tau_f, beta):
+        """Convection-diffusion local block with per-face tau_f [4]:
+        returns L, R, C, T (conservation rows C z + T lambda)."""
+        nv, nt = self.nv, self.nt
+        Z = np.zeros((nv, nv))
+        bn = self.normals @ np.asarray(beta, dtype=np.float64)        # beta.n_f
+        Euu = sum(tau_f[f] * self.Eb_f[f] for f in range(4))
+        conv = -(beta[0] * self.Dx + beta[1] * self.Dy)                # -(beta u, grad w)
+        L = self.L0 + self.LM / kappa + np.block([[Z, Z, Z], [Z, Z, Z], [Z, Z, Euu + conv]])
+        Rl = sum((bn[f] - tau_f[f]) * self.Fb_f[f] for f in range(4))  # <(beta.n - tau) lambda, w>
+        R = self.R0 + np.vstack([np.zeros((2 * nv, nt)), Rl])
+        Cu = sum(tau_f[f] * self.Fb_f[f] for f in range(4)).T         # <tau u, mu>
+        C = np.hstack([self.Cx.T, self.Cy.T, Cu])
+        T = sum((bn[f] - tau_f[f]) * self.El_f[f] for f in range(4))
+        return L, R, C, T
+
     def load(self, fnodal):
         """F = [0, 0, (f_h, phi_a)] for the Q_p interpolant of nodal f."""
         nv = self.nv
@@ -154,9 +199,12 @@ class HDGProblem:
     """HDG trace system on a uniform n x n rectangle mesh (oracle).
 
     kappa: per-element diffusivity [n*n] (K = kappa I); tau: scalar or [n*n].
+    beta: None (diffusion) or a constant convection velocity (bx, by); then
+    tau is the base value and face f of element e uses
+    tau_e + max(beta.n_f, 0).
     """
 
-    def __init__(self, n, p, kappa, tau, x0=0.0, x1=1.0, y0=0.0, y1=1.0, nq=None):
+    def __init__(self, n, p, kappa, tau, x0=0.0, x1=1.0, y0=0.0, y1=1.0, nq=None, beta=None):
         self.n, self.p = n, p
         self.E = n * n
         self.hx = (x1 - x0) / n
@@ -172,6 +220,32 @@ class HDGProblem:
         self.bmask = boundary_edge_mask(n)
         self._Ae = None
         self._ge_f = None
+        self.beta = None if beta is None else np.asarray(beta, dtype=np.float64)
+        self.symmetric = self.beta is None
+        if self.beta is not None:
+            bn = self.forms.normals @ self.beta
+            self.tau_f = self.tau[:, None] + np.maximum(bn, 0.0)[None, :]
+
+    def local(self, e):
+        """(L, R, C, T) of element e: conservation rows read C z + T lambda."""
+        fr = self.forms
+        if self.beta is None:
+            L, R, C = fr.local(self.kappa[e], self.tau[e])
+            return L, R, C, -self.tau[e] * fr.El
+        return fr.local_cd(self.kappa[e], self.tau_f[e], self.beta)
+
+    def _condense_general(self, f):
+        E, nv, nt = self.E, self.nv, self.nt
+        Ae = np.empty((E, nt, nt))
+        ge = np.zeros((E, nt)) if f is not None else None
+        for e in range(E):
+            L, R, C, T = self.local(e)
+            rhs = R if f is None else np.column_stack([R, self.forms.load(f[:, e])])
+            X = np.linalg.solve(L, rhs)                  # LU, partial pivoting
+            Ae[e] = C @ X[:, :nt] - T
+            if f is not None:
+                ge[e] = C @ X[:, nt]
+        return Ae, ge
 
     # -- per-element condensation (LU with partial pivoting) -------------
     def element_dofs(self):
@@ -183,6 +257,8 @@ class HDGProblem:
         """Return A_e [E, n_t, n_t] and g_e [E, n_t] (g_e only if f given).
 
         f: nodal forcing [n_v][E] (library layout)."""
+        if self.beta is not None:
+            return self._condense_general(f)
         E, nv, nt = self.E, self.nv, self.nt
         Ae = np.empty((E, nt, nt))
         ge = np.zeros((E, nt)) if f is not None else None
@@ -264,6 +340,12 @@ class HDGProblem:
         nv = self.nv
         u = np.empty((nv, self.E))
         q = np.empty((2, nv, self.E))
+        if self.beta is not None:
+            for e in range(self.E):
+                L, R, _, _ = self.local(e)
+                z = np.linalg.solve(L, fr.load(f[:, e]) - R @ lam[dofs[e]])
+                q[0][:, e], q[1][:, e], u[:, e] = z[:nv], z[nv:2 * nv], z[2 * nv:]
+            return u, q
         for s in range(0, self.E, 2048):
             idx = np.arange(s, min(self.E, s + 2048))
             k = self.kappa[idx][:, None, None]
@@ -302,7 +384,7 @@ class HDGProblem:
             lamD[dd] = full[dd]
         dofs = self.element_dofs()
         for e in range(E):
-            L, R, C = fr.local(self.kappa[e], self.tau[e])
+            L, R, C, T = self.local(e)
             zr = slice(3 * nv * e, 3 * nv * (e + 1))
             M[zr, zr] = L
             rhs[zr] = fr.load(f[:, e])
@@ -320,7 +402,7 @@ class HDGProblem:
                 M[row, zr] += C[r]
                 for c in range(nt):
                     dc = dofs[e, c]
-                    val = -self.tau[e] * fr.El[r, c]
+                    val = T[r, c]
                     if pos[dc] >= 0:
                         M[row, nz + pos[dc]] += val
                     else:

@@ -23,7 +23,8 @@ sparse matrix, in the order the paper defines them:
   capped); Sec. 4.1 block-Jacobi with one block per edge, undamped by default.
 * Sec. 3.4 local correction T_k = diag(A_II^-1, 0) (eq. localCorrection).
 * Sec. 3.6 Algorithm 1 (V-cycle) with B_1 = A_1^-1 by a dense Cholesky
-  factorisation, local correction in step 3 only ("pre", the paper's
+  factorisation (a dense LU with partial pivoting for the non-symmetric
+  convection-diffusion operator), local correction in step 3 only ("pre", the paper's
   choice), in steps 3 and 5 ("both", symmetric, for CG) or nowhere ("none").
 
 In the orthonormal trace bases used here the L2(E_k) adjoint J_k^* is the
@@ -168,8 +169,12 @@ class Hierarchy:
         for lev in levels:
             lev.Dinv = self._block_jacobi(lev) if dirichlet else None
         coarse = levels[-1]
-        coarse.chol = (sla.cho_factor(coarse.A.toarray())
-                       if coarse.A.shape[0] and dirichlet else None)
+        coarse.chol = coarse.lu = None
+        if coarse.A.shape[0] and dirichlet:
+            if problem.symmetric:
+                coarse.chol = sla.cho_factor(coarse.A.toarray())
+            else:
+                coarse.lu = sla.lu_factor(coarse.A.toarray())
         self.levels = levels
 
     # ------------------------------------------------------------------
@@ -247,7 +252,9 @@ class Hierarchy:
         """B_k r by Algorithm 1 (k = 0 is the finest level here)."""
         L = self.levels[k]
         if k == len(self.levels) - 1:
-            return sla.cho_solve(L.chol, r) if L.chol is not None else np.zeros_like(r)
+            if L.chol is not None:
+                return sla.cho_solve(L.chol, r)
+            return sla.lu_solve(L.lu, r) if L.lu is not None else np.zeros_like(r)
         A = L.A
         e = np.zeros_like(r)
         for _ in range(L.m):                                     # step 2

@@ -21,6 +21,10 @@ Workloads (paper: arXiv:1811.09909):
     g_D = 0 -- the synthetic stand-in for the heterogeneous permeability of
     Example V (SPE10 layer 75, a dataset that is not used here).
   * ``checkerboard``  : Example IV's two-block kappa in {1e6, 1}, f = 1, g_D = 0.
+  * ``convdiff``      : -eps lap u + beta.grad u = f with constant eps (given
+    per element as log eps) and beta, manufactured u = sin(pi x) sin(pi y)
+    (so g_D = 0), tau_e = eps/h on every face plus the upwind max(beta.n, 0)
+    the library adds.
 """
 import math
 
@@ -124,7 +128,7 @@ class Workload:
     """One synthetic problem: mesh size, order, coefficients and data."""
 
     def __init__(self, name, n, p, log_kappa, f, gD, tau_mode, tau_c,
-                 x0=0.0, x1=1.0, y0=0.0, y1=1.0, seed=None):
+                 x0=0.0, x1=1.0, y0=0.0, y1=1.0, seed=None, beta=None):
         self.name = name
         self.n, self.p = n, p
         self.log_kappa = np.ascontiguousarray(log_kappa, dtype=np.float64)
@@ -133,6 +137,7 @@ class Workload:
         self.tau_mode, self.tau_c = tau_mode, tau_c
         self.x0, self.x1, self.y0, self.y1 = x0, x1, y0, y1
         self.seed = seed
+        self.beta = beta          # None: diffusion; (bx, by): convection-diffusion
 
     @property
     def E(self):
@@ -180,6 +185,24 @@ def checkerboard(n, p, tau_mode="over_h", tau_c=1.0):
     f = np.ones((1, (p + 1) ** 2, n * n))
     gD = np.zeros((1, p + 1, n_edges(n)))
     return Workload(f"checkerboard_{n}_p{p}", n, p, logk, f, gD, tau_mode, tau_c)
+
+
+def convdiff_f(eps, beta):
+    """f = -eps lap u + beta.grad u for u = sin(pi x) sin(pi y)."""
+    def f(x, y):
+        return (2.0 * np.pi ** 2 * eps * np.sin(np.pi * x) * np.sin(np.pi * y)
+                + beta[0] * np.pi * np.cos(np.pi * x) * np.sin(np.pi * y)
+                + beta[1] * np.pi * np.sin(np.pi * x) * np.cos(np.pi * y))
+    return f
+
+
+def convdiff(n=512, p=6, eps=1e-3, beta=(1.0, 0.5), nrhs=1):
+    """Convection-diffusion with a manufactured smooth solution: eps = 1e-3,
+    beta = (1, 0.5) on 512 x 512 quads at p = 6 by default."""
+    f = np.repeat(nodal(convdiff_f(eps, beta), n, p)[None], nrhs, axis=0)
+    gD = np.zeros((nrhs, p + 1, n_edges(n)))
+    return Workload(f"convdiff_{n}_p{p}", n, p, np.full(n * n, math.log(eps)), f, gD,
+                    "over_h", eps, beta=tuple(float(b) for b in beta))
 
 
 def random_vectors(n, nd, count, seed):
