@@ -65,17 +65,31 @@ enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min
 enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
 enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1, HDGMG_KRYLOV_GMRES = 2 };
 enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2 };
+enum { HDGMG_PDE_DIFFUSION = 0, HDGMG_PDE_CONVDIFF = 1 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
 
 /* Problem statement (Sec. 2).  n must be a multiple of 2^L so that the mesh
- * halves down to opts.coarsest_n; 1 <= p <= 8. */
+ * halves down to opts.coarsest_n; 1 <= p <= 8.
+ *
+ * pde = HDGMG_PDE_DIFFUSION: -div(kappa grad u) = f (the paper's problem).
+ * pde = HDGMG_PDE_CONVDIFF (an extension, not in the paper):
+ *   -div(eps grad u) + div(beta u) = f with constant beta = (beta_x, beta_y)
+ *   and eps = exp(log_kappa) per element.  The HDG flux is
+ *   q.n + (beta.n) lambda + tau_f (u - lambda) with the upwind
+ *   tau_f = tau + max(beta.n_f, 0) on each element face.  The trace operator
+ *   is non-symmetric (full storage on every level, the restriction built from
+ *   A_BI); use krylov = GMRES or NONE (CG is rejected with EINVAL), and the
+ *   adjoint entry points reject it.  Zero-initialised fields (older callers)
+ *   select diffusion. */
 typedef struct {
   int32_t n;              /* elements per side                               */
   int32_t p;              /* polynomial order                                */
   double x0, x1, y0, y1;  /* domain                                          */
   int32_t tau_mode;       /* HDGMG_TAU_CONST or HDGMG_TAU_OVER_H (Sec. 4.1)  */
   double tau_c;           /* the constant c                                  */
+  int32_t pde;            /* HDGMG_PDE_DIFFUSION or HDGMG_PDE_CONVDIFF       */
+  double beta_x, beta_y;  /* convection velocity (CONVDIFF only)             */
 } hdgmg_problem;
 
 /* Solver options.  hdgmg_default_opts() fills the documented defaults. */

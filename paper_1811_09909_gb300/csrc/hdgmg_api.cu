@@ -52,6 +52,7 @@ namespace {
 struct hdgmg_ctx {
   hdgmg_problem prob{};
   hdgmg_opts opts{};
+  bool ns = false;             // convection-diffusion: non-symmetric operators (full storage)
   cudaStream_t stream = nullptr;
   double hx = 0, hy = 0, hmin = 0;
   int p = 0, n = 0, nv = 0, nt = 0;
@@ -61,7 +62,7 @@ struct hdgmg_ctx {
   std::vector<Level> levels;
   double* logk = nullptr;
   double* kap = nullptr;       // exp(log kappa) per element
-  double* Lfac = nullptr;
+  double* Lfac = nullptr;      // Cholesky (packed) or, when ns, LU (full) factors of S
   int* err = nullptr;
   int* err_h = nullptr;
   // coarsest level
@@ -163,11 +164,13 @@ size_t tail_layout(hdgmg_ctx* c, int start, const std::vector<int>& staged, bool
     t.staged = (k < last && staged[k]) ? 1 : 0;
     if (t.staged) {
       const size_t nC = (size_t)L.nE / 4;
-      t.a_off = (int)take(36 * (size_t)L.nE);
-      t.dinv_off = (int)take(3 * (size_t)L.nEdge);
-      t.aii_off = (int)take(36 * nC);
+      const size_t na = c->ns ? 64 : 36;
+      t.a_off = (int)take(na * (size_t)L.nE);
+      t.dinv_off = (int)take((c->ns ? 4 : 3) * (size_t)L.nEdge);
+      t.aii_off = (int)take(na * nC);
       t.y_off = (int)take(128 * nC);
       t.pi_off = (int)take(64 * nC);
+      if (c->ns) t.rt_off = (int)take(64 * nC);
     }
     if (P) P->lv[k - start] = t;
   }
@@ -223,6 +226,7 @@ void plan_tail(hdgmg_ctx* c, int tail_n) {
     t.AIIinv = D.AIIinv;
     t.Y = D.Y;
     t.Pi = D.Pi;
+    t.Rt = D.Rt;
   }
   P.r_in = ld<T>(c->levels[start]).r;
   P.e_out = ld<T>(c->levels[start]).e;
@@ -232,6 +236,7 @@ void plan_tail(hdgmg_ctx* c, int tail_n) {
   P.nf = c->nf;
   P.omega = (T)c->opts.omega;
   P.lc = c->opts.local_corr;
+  P.ns = c->ns ? 1 : 0;
 }
 
 
@@ -361,22 +366,23 @@ void vcycle(hdgmg_ctx* c, int l) {
   const T omega = (T)c->opts.omega;
   const int lc = c->opts.local_corr;
   // step 2: pre-smoothing (the first sweep starts from e = 0)
-  launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 1);
+  const bool ns = c->ns;
+  launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
   for (int i = 1; i < L.m; ++i) {
-    launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
-    launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 0);
+    launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
   }
   // step 3: local correction (interior edges of the next level's macro-elements)
   if (L.transfer == 2 && lc != HDGMG_LC_NONE)
-    launch_local_correction<T>(s, L.n / 2, D.AIIinv, D.Y, D.r, D.e);
+    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
   // step 4: coarse-grid correction
   Level& Lc = c->levels[l + 1];
   LevelData<T>& Dc = ld<T>(Lc);
-  launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
+  launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
   if (L.transfer == 1)
     launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
   else
-    launch_restrict_h<T>(s, Lc.n, D.Pi, D.r, D.y, Dc.r);
+    launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, D.y, Dc.r);
   vcycle<T>(c, l + 1);
   if (L.transfer == 1)
     launch_prolong_p<T>(s, L.n, L.nd, Dc.e, D.e);
@@ -384,11 +390,11 @@ void vcycle(hdgmg_ctx* c, int l) {
     launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y);
   // step 5: second local correction (symmetric cycle)
   if (L.transfer == 2 && lc == HDGMG_LC_BOTH)
-    launch_local_correction<T>(s, L.n / 2, D.AIIinv, D.Y, D.r, D.e);
+    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
   // step 6: post-smoothing
   for (int i = 0; i < L.m; ++i) {
-    launch_matvec<T>(s, L.n, L.nd, D.A, D.e, D.y, T(1));
-    launch_bj_update<T>(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, 0);
+    launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
   }
 }
 
@@ -411,7 +417,7 @@ void apply_B(hdgmg_ctx* c, const double* r, double* z) {
 // y = A_fine x (FP64, interior rows), y overwritten
 void apply_A64(hdgmg_ctx* c, const double* x, double* y) {
   cudaMemsetAsync(y, 0, sizeof(double) * c->fine_len(), c->stream);
-  launch_matvec<double>(c->stream, c->n, c->p + 1, c->levels[0].d64.A, x, y, 1.0);
+  launch_matvec<double>(c->stream, c->n, c->p + 1, c->ns, c->levels[0].d64.A, x, y, 1.0);
 }
 
 double dot_sync(hdgmg_ctx* c, const double* a, const double* b) {
@@ -425,8 +431,9 @@ template <typename T>
 hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
   LevelData<T>& D = ld<T>(L);
   (void)vec_only_fine;
+  const size_t nblk_ent = c->ns ? (size_t)L.nd * L.nd : (size_t)(L.nd * (L.nd + 1) / 2);
   CUDA_TRY(c->alloc(&D.A, (size_t)L.nsym * L.nE));
-  CUDA_TRY(c->alloc(&D.Dinv, (size_t)(L.nd * (L.nd + 1) / 2) * L.nEdge));
+  CUDA_TRY(c->alloc(&D.Dinv, nblk_ent * L.nEdge));
   CUDA_TRY(c->alloc(&D.r, (size_t)L.nd * L.nEdge));
   CUDA_TRY(c->alloc(&D.e, (size_t)L.nd * L.nEdge));
   CUDA_TRY(c->alloc(&D.y, (size_t)L.nd * L.nEdge));
@@ -435,9 +442,13 @@ hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
   CUDA_TRY(cudaMemset(D.e, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
   if (L.transfer == 2) {
     const size_t nC = (size_t)L.nE / 4;
-    CUDA_TRY(c->alloc(&D.AIIinv, 36 * nC));
+    CUDA_TRY(c->alloc(&D.AIIinv, (c->ns ? 64 : 36) * nC));
     CUDA_TRY(c->alloc(&D.Y, 128 * nC));
     CUDA_TRY(c->alloc(&D.Pi, 64 * nC));
+    if (c->ns)
+      CUDA_TRY(c->alloc(&D.Rt, 64 * nC));
+    else
+      D.Rt = D.Pi;                     // Q_{k-1} = I_k^T for symmetric A
   }
   return HDGMG_OK;
 }
@@ -451,17 +462,22 @@ hdgmg_status setup_hierarchy(hdgmg_ctx* c) {
     Level& Lc = c->levels[l + 1];
     LevelData<T>& D = ld<T>(L);
     LevelData<T>& Dc = ld<T>(Lc);
-    launch_bj_blocks<T>(s, L.n, L.nd, D.A, D.Dinv, c->err);
+    launch_bj_blocks<T>(s, L.n, L.nd, c->ns, D.A, D.Dinv, c->err);
     if (L.transfer == 1)
-      launch_pcoarsen<T>(s, L.nE, L.nd, D.A, Dc.A);
+      launch_pcoarsen<T>(s, L.nE, L.nd, c->ns, D.A, Dc.A);
     else
-      launch_agglomerate<T>(s, Lc.n, D.A, Dc.A, D.AIIinv, D.Y, D.Pi, c->err);
+      launch_agglomerate<T>(s, Lc.n, c->ns, D.A, Dc.A, D.AIIinv, D.Y, D.Pi, D.Rt, c->err);
   }
   Level& Lc = c->levels[nl - 1];
-  if (!launch_coarse_setup_smem<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->cinv, c->err)) {
-    launch_coarse_assemble<T>(s, Lc.n, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
-    launch_coarse_factor(s, c->nf, c->dense, c->err);
-    launch_coarse_inverse(s, c->nf, c->dense, c->clinv, c->cinv);
+  if (!launch_coarse_setup_smem<T>(s, Lc.n, c->ns, ld<T>(Lc).A, c->freeidx, c->nf, c->cinv,
+                                   c->err)) {
+    launch_coarse_assemble<T>(s, Lc.n, c->ns, ld<T>(Lc).A, c->freeidx, c->nf, c->dense);
+    if (c->ns) {
+      launch_coarse_gj(s, c->nf, c->dense, c->cinv, c->err);
+    } else {
+      launch_coarse_factor(s, c->nf, c->dense, c->err);
+      launch_coarse_inverse(s, c->nf, c->dense, c->clinv, c->cinv);
+    }
   }
   return check_launch("hierarchy set-up");
 }
@@ -470,10 +486,14 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
   CUDA_TRY(cudaMemsetAsync(c->b, 0, sizeof(double) * len, s));
-  launch_rhs(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
-             f, c->b);
+  if (c->ns)
+    launch_rhs_cd(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                  c->prob.beta_x, c->prob.beta_y, c->Lfac, f, c->b);
+  else
+    launch_rhs(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
+               f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
-  if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->lam, c->b, -1.0);
+  if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->b, -1.0);
   return check_launch("condensed right-hand side");
 }
 
@@ -489,7 +509,7 @@ void cg_body64(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   apply_B(c, c->r, c->z);
   launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);
   launch_cg_direction_zero<double>(s, len, c->scal, c->z, c->pv, c->Ap);
-  launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->pv, c->Ap, 1.0);
+  launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->pv, c->Ap, 1.0);
   launch_dot_fused<double>(s, len, c->pv, c->Ap, c->partial, c->counter, c->scal, 0);
   launch_cg_update_test<double>(s, len, c->scal, c->x, c->r, c->pv, c->Ap, c->partial, c->counter,
                                 h, c->it_dev, c->opts.max_it, c->opts.rtol * c->opts.rtol);
@@ -504,7 +524,7 @@ void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   vcycle<float>(c, 0);
   launch_dot_fused<float>(s, len, rs, zs, c->partial, c->counter, c->scal32, 1);
   launch_cg_direction_zero<float>(s, len, c->scal32, zs, c->ps, c->Aps);
-  launch_matvec<float>(s, c->n, c->p + 1, L0.d32.A, c->ps, c->Aps, 1.0f);
+  launch_matvec<float>(s, c->n, c->p + 1, c->ns, L0.d32.A, c->ps, c->Aps, 1.0f);
   launch_dot_fused<float>(s, len, c->ps, c->Aps, c->partial, c->counter, c->scal32, 0);
   launch_cg_update_test<float>(s, len, c->scal32, c->xs, rs, c->ps, c->Aps, c->partial, c->counter,
                                h, c->it_dev, c->opts.max_it,
@@ -562,7 +582,7 @@ hdgmg_status refine_solve(hdgmg_ctx* c, double nb, int* iters, int* outer, doubl
   *breakdown = false;
   for (;;) {
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    launch_matvec<double>(s, c->n, c->p + 1, L0.d64.A, c->x, c->r, -1.0);
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->x, c->r, -1.0);
     launch_dot<double>(s, len, c->r, c->r, c->partial, c->scal + 7);
     CUDA_TRY(cudaMemcpyAsync(c->scal_h + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -649,7 +669,7 @@ hdgmg_status gmres_solve(hdgmg_ctx* c, double nb, int* iters, double* rel, bool*
   for (int cycle = 0; cycle < o.max_it; ++cycle) {
     // r = b - A x, its norm, v_0 = r / ||r||
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    launch_matvec<double>(s, c->n, c->p + 1, c->levels[0].d64.A, c->x, c->r, -1.0);
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->x, c->r, -1.0);
     const double rr = dot_sync(c, c->r, c->r);
     *rel = std::sqrt(rr) / nb;
     if (!std::isfinite(rr)) { *breakdown = true; return HDGMG_OK; }
@@ -759,7 +779,10 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   // lambda = boundary data + interior solution
   CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
-  if (u || q)
+  if ((u || q) && c->ns)
+    launch_recover_cd(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                      c->prob.beta_x, c->prob.beta_y, c->Lfac, f, lam_out, u, q);
+  else if (u || q)
     launch_recover(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                    c->Lfac, f, lam_out, u, q);
   STATUS_TRY(check_launch("solve"));
@@ -871,6 +894,10 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (!(P.tau_c > 0.0)) return fail(HDGMG_EINVAL, "tau_c must be positive");
   if (P.tau_mode != HDGMG_TAU_CONST && P.tau_mode != HDGMG_TAU_OVER_H)
     return fail(HDGMG_EINVAL, "unknown tau_mode");
+  if (P.pde != HDGMG_PDE_DIFFUSION && P.pde != HDGMG_PDE_CONVDIFF)
+    return fail(HDGMG_EINVAL, "unknown pde");
+  if (P.pde == HDGMG_PDE_CONVDIFF && (!std::isfinite(P.beta_x) || !std::isfinite(P.beta_y)))
+    return fail(HDGMG_EINVAL, "beta must be finite");
   if (o.coarsest_n < 2) return fail(HDGMG_EINVAL, "coarsest_n must be >= 2");
   if (o.m_fine < 1 || o.m_growth < 1 || o.m_max < 0) return fail(HDGMG_EINVAL, "bad smoothing schedule");
   if (o.local_corr < 0 || o.local_corr > 2) return fail(HDGMG_EINVAL, "unknown local_corr");
@@ -878,6 +905,8 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.krylov == HDGMG_KRYLOV_GMRES && (o.gmres_restart < 1 || o.gmres_restart > 256))
     return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
   if (o.precision < 0 || o.precision > 2) return fail(HDGMG_EINVAL, "unknown precision");
+  if (P.pde == HDGMG_PDE_CONVDIFF && o.krylov == HDGMG_KRYLOV_CG)
+    return fail(HDGMG_EINVAL, "krylov CG needs a symmetric operator; use GMRES for convection-diffusion");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
   if (!(o.inner_rtol > 0.0) || !(o.inner_rtol < 1.0)) return fail(HDGMG_EINVAL, "inner_rtol must be in (0,1)");
   int nn = P.n;
@@ -891,6 +920,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   hdgmg_ctx* c = new hdgmg_ctx();
   c->prob = P;
   c->opts = o;
+  c->ns = P.pde == HDGMG_PDE_CONVDIFF;
   c->stream = (cudaStream_t)stream;
   c->n = P.n;
   c->p = P.p;
@@ -927,6 +957,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(upload(&c->refd.ByT, c->ref.ByT));
   CTRY(upload(&c->refd.Cx, c->ref.Cx));
   CTRY(upload(&c->refd.Cy, c->ref.Cy));
+  CTRY(upload(&c->refd.Ef, c->ref.Ef));
   // levels
   {
     Level L;
@@ -950,7 +981,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     int m = o.m_fine;
     for (Level& Lv : c->levels) {
       Lv.nl = 4 * Lv.nd;
-      Lv.nsym = Lv.nl * (Lv.nl + 1) / 2;
+      Lv.nsym = c->ns ? Lv.nl * Lv.nl : Lv.nl * (Lv.nl + 1) / 2;
       Lv.nE = Lv.n * Lv.n;
       Lv.nEdge = 2 * Lv.n * (Lv.n + 1);
       Lv.m = m;
@@ -975,7 +1006,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   const int64_t len = c->fine_len();
   CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
   CTRY(c->alloc(&c->kap, (size_t)P.n * P.n));
-  CTRY(c->alloc(&c->Lfac, (size_t)(c->nv * (c->nv + 1) / 2) * P.n * P.n));
+  CTRY(c->alloc(&c->Lfac, (size_t)(c->ns ? c->nv * c->nv : c->nv * (c->nv + 1) / 2) * P.n * P.n));
   CTRY(c->alloc(&c->err, 4));
   CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
   CTRY(c->alloc(&c->x, len));
@@ -1032,12 +1063,13 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   // distributed-shared-memory steps and cluster barriers cost more per step
   // than the single-block tail plus separate launches of the larger levels.
   const int ct = o.cluster_tail_n;
+  // (the cluster tail exists for symmetric operators only)
   if (fp32) {
     plan_tail<float>(c, 32);
-    if (ct > 0) plan_ctail<float>(c, ct);
+    if (ct > 0 && !c->ns) plan_ctail<float>(c, ct);
   } else {
     plan_tail<double>(c, 16);
-    if (ct > 0) plan_ctail<double>(c, ct);
+    if (ct > 0 && !c->ns) plan_ctail<double>(c, ct);
   }
   if (c->ctail_start >= 0 && c->tail_start >= 0 && c->tail_start < c->ctail_start)
     c->ctail_start = -1;                     // keep whichever fuses more levels
@@ -1062,8 +1094,12 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   Level& L0 = c->levels[0];
   launch_kappa(s, nE, c->logk, c->kap);
   CUDA_TRY(cudaEventRecord(c->evk0, s));
-  launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
-                  L0.d64.A, c->Lfac, c->err);
+  if (c->ns)
+    launch_condense_cd(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                       c->prob.beta_x, c->prob.beta_y, L0.d64.A, c->Lfac, c->err);
+  else
+    launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                    L0.d64.A, c->Lfac, c->err);
   CUDA_TRY(cudaEventRecord(c->evk1, s));
   STATUS_TRY(check_launch("condensation"));
   if (c->opts.precision != HDGMG_PREC_FP64) {
@@ -1158,6 +1194,7 @@ hdgmg_status hdgmg_run_host(hdgmg_ctx* c, const double* log_kappa, const double*
 hdgmg_status hdgmg_adjoint(hdgmg_ctx* c, const double* lambda, const double* u, const double* g_u,
                            double* dL_dlogk, double* dL_df, hdgmg_info* info) {
   if (!c || !lambda || !u || !g_u) return fail(HDGMG_EINVAL, "NULL argument");
+  if (c->ns) return fail(HDGMG_EINVAL, "the adjoint is for the symmetric diffusion operator");
   if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
   STATUS_TRY(adjoint_buffers(c));
   return adjoint_core(c, lambda, u, g_u, dL_dlogk, dL_df, info);
@@ -1166,6 +1203,7 @@ hdgmg_status hdgmg_adjoint(hdgmg_ctx* c, const double* lambda, const double* u, 
 hdgmg_status hdgmg_gradient(hdgmg_ctx* c, const double* f, const double* g_D, const double* u_obs,
                             double* J, double* dJ_dlogk, double* dJ_df, hdgmg_info* info) {
   if (!c || !f || !u_obs) return fail(HDGMG_EINVAL, "NULL argument");
+  if (c->ns) return fail(HDGMG_EINVAL, "the adjoint is for the symmetric diffusion operator");
   if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
   STATUS_TRY(adjoint_buffers(c));
   cudaStream_t s = c->stream;
@@ -1201,9 +1239,9 @@ hdgmg_status hdgmg_copy_element_matrices(hdgmg_ctx* c, int32_t level, double* ou
   if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
   Level& L = c->levels[level];
   if (level == 0 || c->opts.precision == HDGMG_PREC_FP64)
-    launch_unpack<double>(c->stream, L.nl, L.nE, L.d64.A, out);
+    launch_unpack<double>(c->stream, L.nl, L.nE, c->ns, L.d64.A, out);
   else
-    launch_unpack<float>(c->stream, L.nl, L.nE, L.d32.A, out);
+    launch_unpack<float>(c->stream, L.nl, L.nE, c->ns, L.d32.A, out);
   STATUS_TRY(check_launch("copy element matrices"));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return HDGMG_OK;
@@ -1223,7 +1261,7 @@ hdgmg_status hdgmg_apply_operator(hdgmg_ctx* c, int32_t level, const double* x, 
     cudaMemcpyAsync(xm, x, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
     launch_mask<double>(s, L.n, L.nd, xm);
     cudaMemsetAsync(ym, 0, sizeof(double) * len, s);
-    launch_matvec<double>(s, L.n, L.nd, L.d64.A, xm, ym, 1.0);
+    launch_matvec<double>(s, L.n, L.nd, c->ns, L.d64.A, xm, ym, 1.0);
     cudaMemcpyAsync(y, ym, sizeof(double) * len, cudaMemcpyDeviceToDevice, s);
     cudaStreamSynchronize(s);
     cudaFree(xm);
@@ -1235,7 +1273,7 @@ hdgmg_status hdgmg_apply_operator(hdgmg_ctx* c, int32_t level, const double* x, 
     launch_convert<double, float>(s, len, x, xm);
     launch_mask<float>(s, L.n, L.nd, xm);
     cudaMemsetAsync(ym, 0, sizeof(float) * len, s);
-    launch_matvec<float>(s, L.n, L.nd, L.d32.A, xm, ym, 1.0f);
+    launch_matvec<float>(s, L.n, L.nd, c->ns, L.d32.A, xm, ym, 1.0f);
     launch_convert<float, double>(s, len, ym, y);
     cudaStreamSynchronize(s);
     cudaFree(xm);
@@ -1332,14 +1370,14 @@ extern "C" hdgmg_status hdgmg_apply_operator_noalloc(hdgmg_ctx* c, int32_t level
     CUDA_TRY(cudaMemcpyAsync(xm, x, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     launch_mask<double>(s, L.n, L.nd, xm);
     CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * len, s));
-    launch_matvec<double>(s, L.n, L.nd, L.d64.A, xm, y, 1.0);
+    launch_matvec<double>(s, L.n, L.nd, c->ns, L.d64.A, xm, y, 1.0);
   } else {
     float* xm = reinterpret_cast<float*>(scratch);  // len floats, fully overwritten
     float* ym = xm + len;                          // len floats, cleared below
     launch_convert<double, float>(s, len, x, xm);
     launch_mask<float>(s, L.n, L.nd, xm);
     CUDA_TRY(cudaMemsetAsync(ym, 0, sizeof(float) * len, s));
-    launch_matvec<float>(s, L.n, L.nd, L.d32.A, xm, ym, 1.0f);
+    launch_matvec<float>(s, L.n, L.nd, c->ns, L.d32.A, xm, ym, 1.0f);
     launch_convert<float, double>(s, len, ym, y);
   }
   STATUS_TRY(check_launch("apply operator (no allocation)"));

@@ -24,13 +24,16 @@ namespace hdgmg {
 //   F      [nv][nt]    <psi_k, phi_a>_dK
 //   K      [nt][nt]    sum_d C_d^T M^-1 C_d
 //   BxT,ByT [nv][nv]   B_d^T  (BdT[a][b] = (phi_b, d_d phi_a)), recovery of q
+//                      and the convection term -(beta u, grad w)
 //   Cx, Cy [nv][nt]    <psi_k, phi_a n_d>, recovery of q
+//   Ef  [4][nv][nv]    <phi_a, phi_b> on face f alone (E = sum_f Ef), for
+//                      face-dependent tau (convection-diffusion)
 // ---------------------------------------------------------------------------
 struct RefElement {
   int p = 0, nv = 0, nt = 0;
   double hx = 0, hy = 0;
   std::vector<double> nodes, weights;
-  std::vector<double> M, G, E, H, F, K, BxT, ByT, Cx, Cy;
+  std::vector<double> M, G, E, H, F, K, BxT, ByT, Cx, Cy, Ef;
 };
 RefElement build_ref_element(int p, double hx, double hy);
 
@@ -57,6 +60,8 @@ struct LevelData {
   T* AIIinv = nullptr;   // [36][nC]   A_II^-1 (8x8, packed)
   T* Y = nullptr;        // [128][nC]  -A_II^-1 A_IB  (8x16, row-major)
   T* Pi = nullptr;       // [64][nC]   -A_II^-1 A_IB J (8x8, row-major)
+  T* Rt = nullptr;       // [64][nC]   (-J^T A_BI A_II^-1)^T, the interior part of
+                         //            Q_{k-1} transposed; aliases Pi when A is symmetric
   T* r = nullptr;        // level right-hand side   [nd][nEdge]
   T* e = nullptr;        // level correction        [nd][nEdge]
   T* y = nullptr;        // matvec accumulator      [nd][nEdge] (kept zero)
@@ -66,7 +71,7 @@ struct Level {
   int n = 0;       // macro-elements per side
   int nd = 0;      // trace modes per edge
   int nl = 0;      // 4*nd
-  int nsym = 0;    // nl(nl+1)/2
+  int nsym = 0;    // entries per element operator: nl(nl+1)/2 packed, nl*nl non-symmetric
   int nE = 0, nEdge = 0;
   int m = 1;       // smoothing steps
   int transfer = 0;   // 0 none (coarsest), 1 p-transfer, 2 h-transfer
@@ -78,7 +83,7 @@ struct Level {
 // kernel launchers (k_condense.cu, k_mg.cu, k_blas.cu)
 // ---------------------------------------------------------------------------
 struct RefDevice {     // device copies of RefElement tables (FP64)
-  double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy;
+  double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy, *Ef;
 };
 
 // kap = exp(log kappa) per element; the element kernels take kap
@@ -94,6 +99,18 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
                     const double* Lfac, const double* f, const double* lam,
                     double* u, double* q);
 
+// convection-diffusion element (non-symmetric A_e, full [nt*nt][nE]; LU
+// factors of the volume block, full [nv*nv][nE])
+void launch_condense_cd(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
+                        int tau_mode, double tau_c, double hmin, double bx, double by, double* A,
+                        double* LU, int* err);
+void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                   int tau_mode, double tau_c, double hmin, double bx, double by, const double* LU,
+                   const double* f, double* b);
+void launch_recover_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                       int tau_mode, double tau_c, double hmin, double bx, double by,
+                       const double* LU, const double* f, const double* lam, double* u, double* q);
+
 // adjoint: per-element derivative contraction (K13), adjoint source, misfit
 void launch_grad_contract(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
                           const double* lam, const double* u, const double* mu, const double* w,
@@ -103,28 +120,31 @@ void launch_adjoint_source(cudaStream_t s, const RefDevice& ref, int nv, int nE,
 void launch_misfit(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* u,
                    const double* uobs, double* d, double* gu);
 
+// ns: operators stored non-symmetric (full row-major) instead of packed
 template <typename T>
-void launch_matvec(cudaStream_t s, int n, int nd, const T* A, const T* x, T* y, T alpha);
+void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha);
 // per-ND instantiations (k_edge_inst.cu, one translation unit per type and ND)
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha);
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err);
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first);
 template <typename T>
-void launch_bj_blocks(cudaStream_t s, int n, int nd, const T* A, T* Dinv, int* err);
+void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err);
 template <typename T>
-void launch_bj_update(cudaStream_t s, int n, int nd, const T* Dinv, const T* r, T* y,
+void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
                       T* e, T omega, int first);
 template <typename T>
-void launch_pcoarsen(cudaStream_t s, int nE, int ndf, const T* Af, T* Ac);
+void launch_pcoarsen(cudaStream_t s, int nE, int ndf, bool ns, const T* Af, T* Ac);
+// ns: also writes Rt = Z^T J with Z = -A_BI A_II^-1 (the restriction block);
+// symmetric operators use Rt = Pi
 template <typename T>
-void launch_agglomerate(cudaStream_t s, int nc, const T* Af, T* Ac, T* AIIinv, T* Y,
-                        T* Pi, int* err);
+void launch_agglomerate(cudaStream_t s, int nc, bool ns, const T* Af, T* Ac, T* AIIinv, T* Y,
+                        T* Pi, T* Rt, int* err);
 template <typename T>
-void launch_local_correction(cudaStream_t s, int nc, const T* AIIinv, const T* Y,
+void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
                              const T* r, T* e);
 template <typename T>
 void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc);
@@ -142,13 +162,14 @@ template <typename T>
 struct TailLevel {
   int n = 0, m = 1, nEdge = 0;
   // shared-memory offsets (T units) of [r|e|y] and of the staged operators
-  int voff = 0, a_off = 0, dinv_off = 0, aii_off = 0, y_off = 0, pi_off = 0;
+  int voff = 0, a_off = 0, dinv_off = 0, aii_off = 0, y_off = 0, pi_off = 0, rt_off = 0;
   int staged = 0;              // operators copied to shared memory (else read from L2)
   const T* A = nullptr;
   const T* Dinv = nullptr;
   const T* AIIinv = nullptr;
   const T* Y = nullptr;
   const T* Pi = nullptr;
+  const T* Rt = nullptr;
 };
 template <typename T>
 struct TailParams {
@@ -162,6 +183,7 @@ struct TailParams {
   int nf = 0;
   T omega = T(1);
   int lc = 0;
+  int ns = 0;                   // non-symmetric (full) operators
   int ainv_off = 0, w_off = 0;  // byte offsets of the staged inverse (-1: read from global)
                                 // and of the workspace
   int smem_bytes = 0;
@@ -206,14 +228,17 @@ void launch_ctail(cudaStream_t s, const CTailParams<T>& P);
 
 // coarsest level: dense FP64 Cholesky of the interior operator
 template <typename T>
-void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
+void launch_coarse_assemble(cudaStream_t s, int n, bool ns, const T* A, const int* freeidx, int nf,
                             double* dense);
+// in-place Gauss-Jordan inverse of a dense matrix with positive-definite
+// symmetric part (one block, global memory): Ainv = M^-1
+void launch_coarse_gj(cudaStream_t s, int nf, double* M, double* Ainv, int* err);
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err);
 void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, double* Ainv);
 // assemble + invert in one block when A_1 fits in shared memory; false if not
 template <typename T>
-bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
-                              double* Ainv, int* err);
+bool launch_coarse_setup_smem(cudaStream_t s, int n, bool ns, const T* A, const int* freeidx,
+                              int nf, double* Ainv, int* err);
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
                          const double* Ainv, const T* r, T* e);
@@ -225,7 +250,7 @@ void launch_dot(cudaStream_t s, int64_t len, const T* a, const T* b, double* par
 template <typename T>
 void launch_mask(cudaStream_t s, int n, int nd, T* x);   // zero Dirichlet entries
 template <typename T>
-void launch_unpack(cudaStream_t s, int nl, int nE, const T* Ap, double* full);
+void launch_unpack(cudaStream_t s, int nl, int nE, bool ns, const T* Ap, double* full);
 template <typename A, typename B>
 void launch_convert(cudaStream_t s, int64_t len, const A* in, B* out);
 template <typename T>

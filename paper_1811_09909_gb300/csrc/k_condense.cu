@@ -116,6 +116,106 @@ __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
   }
 }
 
+// ------------------------------------------ convection-diffusion element
+// -div(eps grad u) + div(beta u) = f with the upwind flux
+// hhat.n = q.n + (beta.n) lambda + tau_f (u - lambda), tau_f = tau + max(beta.n_f, 0)
+// on local face f (normals 0: -x, 1: +x, 2: -y, 3: +y).  Eliminating q:
+//   S = eps G - beta_x BxT - beta_y ByT + sum_f tau_f E_f        (n_v x n_v)
+//   W = eps H + (tau_f - beta.n_f) F      (column c on face f(c))
+//   V = eps H + tau_f F
+//   A_e = eps K + diag(tau_f - beta.n_f) - V^T S^-1 W,  g_e = V^T S^-1 M f
+// S has a positive-definite symmetric part (tau_f - beta.n_f / 2 >= tau > 0),
+// so Gaussian elimination without pivoting never meets a zero pivot.
+__device__ __forceinline__ void face_terms(double tau, double bx, double by, double tf[4],
+                                           double bn[4]) {
+  bn[0] = -bx;
+  bn[1] = bx;
+  bn[2] = -by;
+  bn[3] = by;
+  for (int f = 0; f < 4; ++f) tf[f] = tau + (bn[f] > 0.0 ? bn[f] : 0.0);
+}
+
+// K1 (non-symmetric): one warp per element; S (LU in place) and W -> X =
+// S^-1 W in shared memory; the LU factors are kept for K5/K12 as
+// [nv*nv][nE] (unit lower part below the diagonal, U on and above it).
+__global__ void condense_cd_kernel(int nv, int nt, int nE, int warps_per_block,
+                                   const double* __restrict__ G, const double* __restrict__ Ef,
+                                   const double* __restrict__ BxT, const double* __restrict__ ByT,
+                                   const double* __restrict__ H, const double* __restrict__ F,
+                                   const double* __restrict__ K, const double* __restrict__ kapv,
+                                   int tau_mode, double tau_c, double hmin, double bx, double by,
+                                   double* __restrict__ A, double* __restrict__ LU,
+                                   int* __restrict__ err) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * warps_per_block + warp;
+  if (e >= nE) return;
+  double* S = smem + (size_t)warp * (nv * nv + nv * nt);
+  double* X = S + nv * nv;
+  const int p1 = nt / 4;
+  const double eps = kapv[e];
+  double tf[4], bn[4];
+  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
+  const int nvv = nv * nv;
+  for (int t = lane; t < nvv; t += 32) {
+    double s = eps * G[t] - bx * BxT[t] - by * ByT[t];
+    for (int f = 0; f < 4; ++f) s += tf[f] * Ef[(size_t)f * nvv + t];
+    S[t] = s;
+  }
+  for (int t = lane; t < nv * nt; t += 32) {
+    const int f = (t % nt) / p1;
+    X[t] = eps * H[t] + (tf[f] - bn[f]) * F[t];
+  }
+  __syncwarp();
+  bool bad = false;
+  // LU without pivoting; the forward sweep is applied to W on the fly
+  for (int k = 0; k < nv; ++k) {
+    double di = 0.0;
+    if (lane == 0) {
+      double d = S[k * nv + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = true;
+        d = 1.0;
+      }
+      di = 1.0 / d;
+    }
+    di = __shfl_sync(0xffffffffu, di, 0);
+    for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
+    __syncwarp();
+    const int m = nv - k - 1;
+    for (int t = lane; t < m * m; t += 32) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      S[i * nv + j] -= S[i * nv + k] * S[k * nv + j];
+    }
+    for (int t = lane; t < m * nt; t += 32) {
+      const int i = k + 1 + t / nt, c = t % nt;
+      X[i * nt + c] -= S[i * nv + k] * X[k * nt + c];
+    }
+    __syncwarp();
+  }
+  // back substitution U X = L^-1 W, one column per lane
+  for (int c = lane; c < nt; c += 32) {
+    for (int k = nv - 1; k >= 0; --k) {
+      double s = X[k * nt + c];
+      for (int j = k + 1; j < nv; ++j) s -= S[k * nv + j] * X[j * nt + c];
+      X[k * nt + c] = s / S[k * nv + k];
+    }
+  }
+  __syncwarp();
+  if (bad) atomicOr(err, 1);
+  for (int t = lane; t < nt * nt; t += 32) {
+    const int r = t / nt, c = t % nt;
+    const int fr = r / p1;
+    double s = 0.0;
+    for (int a = 0; a < nv; ++a) s += (eps * H[a * nt + r] + tf[fr] * F[a * nt + r]) * X[a * nt + c];
+    double v = eps * K[t] - s;
+    if (r == c) v += tf[fr] - bn[fr];
+    A[(size_t)t * nE + e] = v;
+  }
+  if (LU)
+    for (int t = lane; t < nvv; t += 32) LU[(size_t)t * nE + e] = S[t];
+}
+
 // kappa_e = exp(log kappa_e), once per element for all element kernels
 __global__ void kappa_kernel(int nE, const double* __restrict__ logk, double* __restrict__ kap) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -236,6 +336,102 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
     }
   }
 }
+// solve (LU) y = y in place with the full factors of condense_cd_kernel
+__device__ __forceinline__ void lu_solve(const double* __restrict__ LU, int nv, int nE, int e,
+                                         double* y) {
+  for (int i = 0; i < nv; ++i) {
+    double s = TV(y, i);
+    for (int j = 0; j < i; ++j) s -= LU[(size_t)(i * nv + j) * nE + e] * TV(y, j);
+    TV(y, i) = s;
+  }
+  for (int i = nv - 1; i >= 0; --i) {
+    double s = TV(y, i);
+    for (int j = i + 1; j < nv; ++j) s -= LU[(size_t)(i * nv + j) * nE + e] * TV(y, j);
+    TV(y, i) = s / LU[(size_t)(i * nv + i) * nE + e];
+  }
+}
+
+// K5 (convection-diffusion): g_e = V^T S^-1 M f_e
+__global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
+                              const double* __restrict__ H, const double* __restrict__ F,
+                              const double* __restrict__ kapv, int tau_mode, double tau_c,
+                              double hmin, double bx, double by, const double* __restrict__ LU,
+                              const double* __restrict__ f, double* __restrict__ b) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  const double eps = kapv[e];
+  double tf[4], bn[4];
+  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
+  for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
+  lu_solve(LU, nv, nE, e, y);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) {
+    const int edge = ed[c / p1];
+    if (is_boundary_edge(n, edge)) continue;
+    const double t = tf[c / p1];
+    double g = 0.0;
+    for (int a = 0; a < nv; ++a) g += (eps * H[a * nt + c] + t * F[a * nt + c]) * TV(y, a);
+    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
+  }
+}
+
+// K12 (convection-diffusion): u = S^-1 (M f + W lambda), q = eps M^-1 (B^T u - C lambda)
+__global__ void recover_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
+                                  const double* __restrict__ H, const double* __restrict__ F,
+                                  const double* __restrict__ BxT, const double* __restrict__ ByT,
+                                  const double* __restrict__ Cx, const double* __restrict__ Cy,
+                                  const double* __restrict__ kapv, int tau_mode, double tau_c,
+                                  double hmin, double bx, double by,
+                                  const double* __restrict__ LU, const double* __restrict__ f,
+                                  const double* __restrict__ lam, double* __restrict__ u,
+                                  double* __restrict__ q) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  double* le = smem + (size_t)nv * blockDim.x;
+  const double eps = kapv[e];
+  double tf[4], bn[4];
+  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
+  for (int a = 0; a < nv; ++a) {
+    double s = Mdiag[a] * f[(size_t)a * nE + e];
+    for (int c = 0; c < nt; ++c)
+      s += (eps * H[a * nt + c] + (tf[c / p1] - bn[c / p1]) * F[a * nt + c]) * TV(le, c);
+    TV(y, a) = s;
+  }
+  lu_solve(LU, nv, nE, e, y);
+  if (u)
+    for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
+  if (q) {
+    for (int a = 0; a < nv; ++a) {
+      double sx = 0.0, sy = 0.0;
+      for (int b2 = 0; b2 < nv; ++b2) {
+        sx += BxT[a * nv + b2] * TV(y, b2);
+        sy += ByT[a * nv + b2] * TV(y, b2);
+      }
+      for (int c = 0; c < nt; ++c) {
+        sx -= Cx[a * nt + c] * TV(le, c);
+        sy -= Cy[a * nt + c] * TV(le, c);
+      }
+      const double sc = eps / Mdiag[a];
+      q[(size_t)a * nE + e] = sc * sx;
+      q[(size_t)(nv + a) * nE + e] = sc * sy;
+    }
+  }
+}
+
 // ---------------------------------------------------------- adjoint (K13)
 // With the forward state (lambda, u) and the adjoint state (mu, w) -- the
 // solution of the same trace system with right-hand side built from g_u and
@@ -352,6 +548,60 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
   note_launch();
   condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
                                                  kap, tau_mode, tau_c, hmin, A, Lfac, err);
+}
+
+void launch_condense_cd(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
+                        int tau_mode, double tau_c, double hmin, double bx, double by, double* A,
+                        double* LU, int* err) {
+  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const size_t per_warp = sizeof(double) * (size_t)(nv * nv + nv * nt);
+  int wpb = (int)((200 * 1024) / per_warp);
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  const size_t shm = per_warp * wpb;
+  static const bool attr_set = [] {
+    cudaFuncSetAttribute(condense_cd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    return true;
+  }();
+  (void)attr_set;
+  const int blocks = (nE + wpb - 1) / wpb;
+  note_launch();
+  condense_cd_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.Ef, ref.BxT, ref.ByT,
+                                                    ref.H, ref.F, ref.K, kap, tau_mode, tau_c, hmin,
+                                                    bx, by, A, LU, err);
+}
+
+void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                   int tau_mode, double tau_c, double hmin, double bx, double by, const double* LU,
+                   const double* f, double* b) {
+  const int nE = n * n, nv = (p + 1) * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)nv * threads;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(rhs_cd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  rhs_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau_mode, tau_c, hmin,
+                                             bx, by, LU, f, b);
+}
+
+void launch_recover_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                       int tau_mode, double tau_c, double hmin, double bx, double by,
+                       const double* LU, const double* f, const double* lam, double* u, double* q) {
+  const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(recover_cd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  recover_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
+                                                 ref.Cy, kap, tau_mode, tau_c, hmin, bx, by, LU, f,
+                                                 lam, u, q);
 }
 
 void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,

@@ -1,9 +1,13 @@
-// Edge/element kernels templated on the number of trace modes per edge ND:
-//   K6  trace matvec y += alpha A x, one thread per element, packed symmetric
-//       A_e in structure-of-arrays layout, results added into the two edge
-//       owners with atomics (exactly two contributions per entry, so the
-//       sum does not depend on their order)
+// Edge/element kernels templated on the number of trace modes per edge ND
+// and on the storage of the element operators (NS = false: symmetric, packed
+// lower triangle; NS = true: non-symmetric, full row-major):
+//   K6  trace matvec y += alpha A x, one thread per element, A_e in
+//       structure-of-arrays layout, results added into the two edge owners
+//       with atomics (exactly two contributions per entry, so the sum does
+//       not depend on their order)
 //   K2  edge block-Jacobi blocks D = A_e0[edge] + A_e1[edge] and D^-1
+//       (Cholesky when symmetric; Gauss-Jordan without pivoting otherwise,
+//       D having a positive-definite symmetric part)
 //   K7  block-Jacobi update e += omega D^-1 (r - A e)  (Sec. 4.1)
 // Each (type, ND) pair is compiled in its own translation unit
 // (k_edge_inst.cu) so that the fully unrolled kernels build in parallel.
@@ -14,7 +18,7 @@
 namespace hdgmg {
 
 // ---------------------------------------------------------------- K6 matvec
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 __global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y,
                                                      T alpha) {
@@ -25,41 +29,60 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict_
   const int nedge = 2 * n * (n + 1);
   int ed[4];
   elem_edges(n, e, ed);
-  T xl[NL], yl[NL];
+  T xl[NL];
 #pragma unroll
-  for (int c = 0; c < NL; ++c) {
-    xl[c] = x[(size_t)(c % ND) * nedge + ed[c / ND]];
-    yl[c] = T(0);
-  }
+  for (int c = 0; c < NL; ++c) xl[c] = x[(size_t)(c % ND) * nedge + ed[c / ND]];
+  if constexpr (NS) {
+    // full storage: one row at a time (rows not unrolled, which keeps the
+    // NL^2-entry kernel small to compile), added straight into y
 #pragma unroll
-  for (int r = 0; r < NL; ++r) {
+    for (int le = 0; le < 4; ++le) {
+      if (bnd_edge(n, ed[le])) continue;
+#pragma unroll 1
+      for (int k = 0; k < ND; ++k) {
+        const T* Ar = A + (size_t)(le * ND + k) * NL * nE + e;
+        T s = T(0);
 #pragma unroll
-    for (int c = 0; c < r; ++c) {
-      const T a = A[(size_t)pk(r, c) * nE + e];
-      yl[r] += a * xl[c];
-      yl[c] += a * xl[r];
+        for (int c = 0; c < NL; ++c) s += Ar[(size_t)c * nE] * xl[c];
+        atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * s);
+      }
     }
-    yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
-  }
+  } else {
+    T yl[NL];
 #pragma unroll
-  for (int le = 0; le < 4; ++le) {
-    if (bnd_edge(n, ed[le])) continue;
+    for (int c = 0; c < NL; ++c) yl[c] = T(0);
 #pragma unroll
-    for (int k = 0; k < ND; ++k) atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * yl[le * ND + k]);
+    for (int r = 0; r < NL; ++r) {
+#pragma unroll
+      for (int c = 0; c < r; ++c) {
+        const T a = A[(size_t)pk(r, c) * nE + e];
+        yl[r] += a * xl[c];
+        yl[c] += a * xl[r];
+      }
+      yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
+    }
+#pragma unroll
+    for (int le = 0; le < 4; ++le) {
+      if (bnd_edge(n, ed[le])) continue;
+#pragma unroll
+      for (int k = 0; k < ND; ++k)
+        atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * yl[le * ND + k]);
+    }
   }
 }
 
 // ----------------------------------------------------- K2 block-Jacobi blocks
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__ Dinv,
                                  int* __restrict__ err) {
   const int nedge = 2 * n * (n + 1);
   const int edge = blockIdx.x * blockDim.x + threadIdx.x;
   if (edge >= nedge) return;
-  constexpr int NS = ND * (ND + 1) / 2;
+  constexpr int NENT = NS ? ND * ND : ND * (ND + 1) / 2;
+  constexpr int NL = 4 * ND;
   if (bnd_edge(n, edge)) {
 #pragma unroll
-    for (int t = 0; t < NS; ++t) Dinv[(size_t)t * nedge + edge] = T(0);
+    for (int t = 0; t < NENT; ++t) Dinv[(size_t)t * nedge + edge] = T(0);
     return;
   }
   const int nE = n * n;
@@ -75,6 +98,48 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
     e1 = j * n + i;       le1 = 2;  // element above, its bottom edge
   }
   T D[ND][ND];
+  if constexpr (NS) {
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int b = 0; b < ND; ++b)
+        D[a][b] = A[(size_t)((le0 * ND + a) * NL + le0 * ND + b) * nE + e0] +
+                  A[(size_t)((le1 * ND + a) * NL + le1 * ND + b) * nE + e1];
+    // Gauss-Jordan without pivoting: Inv = D^-1
+    T Inv[ND][ND];
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int b = 0; b < ND; ++b) Inv[a][b] = (a == b) ? T(1) : T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      T d = D[k][k];
+      if (!(d > T(0))) { bad = true; d = T(1); }
+      const T di = T(1) / d;
+#pragma unroll
+      for (int j = 0; j < ND; ++j) {
+        D[k][j] *= di;
+        Inv[k][j] *= di;
+      }
+#pragma unroll
+      for (int i = 0; i < ND; ++i) {
+        if (i == k) continue;
+        const T fct = D[i][k];
+#pragma unroll
+        for (int j = 0; j < ND; ++j) {
+          D[i][j] -= fct * D[k][j];
+          Inv[i][j] -= fct * Inv[k][j];
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < ND; ++a)
+#pragma unroll
+      for (int b = 0; b < ND; ++b) Dinv[(size_t)(a * ND + b) * nedge + edge] = Inv[a][b];
+    if (bad) atomicOr(err, 2);
+    return;
+  } else {
 #pragma unroll
   for (int a = 0; a < ND; ++a)
 #pragma unroll
@@ -128,10 +193,11 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
       Dinv[(size_t)pk(a, b) * nedge + edge] = s;
     }
   if (bad) atomicOr(err, 2);
+  }
 }
 
 // --------------------------------------------------- K7 block-Jacobi update
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __restrict__ r,
                                  T* __restrict__ y, T* __restrict__ e, T omega, int first) {
   const int nedge = 2 * n * (n + 1);
@@ -148,30 +214,32 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
   for (int a = 0; a < ND; ++a) {
     T s = T(0);
 #pragma unroll
-    for (int b = 0; b < ND; ++b) s += Dinv[(size_t)pk_any(a, b) * nedge + edge] * d[b];
+    for (int b = 0; b < ND; ++b)
+      s += Dinv[(size_t)(NS ? a * ND + b : pk_any(a, b)) * nedge + edge] * d[b];
     const size_t ix = (size_t)a * nedge + edge;
     e[ix] = first ? omega * s : e[ix] + omega * s;
   }
 }
 
 
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha) {
   note_launch();
-  matvec_kernel<T, ND><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
+  matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
 }
 
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err) {
   note_launch();
-  bj_blocks_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, A, Dinv, err);
+  bj_blocks_kernel<T, ND, NS><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, A, Dinv, err);
 }
 
-template <typename T, int ND>
+template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first) {
   note_launch();
-  bj_update_kernel<T, ND><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega, first);
+  bj_update_kernel<T, ND, NS><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega,
+                                                                         first);
 }
 
 }  // namespace hdgmg

@@ -10,11 +10,17 @@
 #endif
 
 namespace hdgmg {
-template void launch_matvec_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
-                                                     const HDGMG_REAL*, HDGMG_REAL*, HDGMG_REAL);
-template void launch_bj_blocks_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
-                                                        HDGMG_REAL*, int*);
-template void launch_bj_update_nd<HDGMG_REAL, HDGMG_ND>(cudaStream_t, int, const HDGMG_REAL*,
-                                                        const HDGMG_REAL*, HDGMG_REAL*,
-                                                        HDGMG_REAL*, HDGMG_REAL, int);
+#define HDGMG_INST(NS)                                                                          \
+  template void launch_matvec_nd<HDGMG_REAL, HDGMG_ND, NS>(cudaStream_t, int, const HDGMG_REAL*, \
+                                                           const HDGMG_REAL*, HDGMG_REAL*,      \
+                                                           HDGMG_REAL);                         \
+  template void launch_bj_blocks_nd<HDGMG_REAL, HDGMG_ND, NS>(cudaStream_t, int,                \
+                                                              const HDGMG_REAL*, HDGMG_REAL*,  \
+                                                              int*);                           \
+  template void launch_bj_update_nd<HDGMG_REAL, HDGMG_ND, NS>(                                  \
+      cudaStream_t, int, const HDGMG_REAL*, const HDGMG_REAL*, HDGMG_REAL*, HDGMG_REAL*,        \
+      HDGMG_REAL, int);
+HDGMG_INST(false)
+HDGMG_INST(true)
+#undef HDGMG_INST
 }  // namespace hdgmg

@@ -9,6 +9,11 @@
 //   K8  local correction, K9 restriction, K11 prolongation
 //   K10 coarsest level: dense Cholesky (assembly, factorisation, solve)
 //
+// Every kernel takes the operator storage: packed symmetric, or (ns, the
+// convection-diffusion operator) full row-major; the non-symmetric transfer
+// uses the restriction block Rt built from A_BI where the symmetric one
+// reuses Pi (Q_{k-1} = I_k^T).
+//
 // Vectors are [nd][n_edges] with Dirichlet (boundary) entries held at zero;
 // every level owns an accumulator y that is zero between kernels: the matvec
 // adds into it and the consumer of y resets it.
@@ -24,13 +29,18 @@ namespace {
 
 // ------------------------------------------------------- K3 p-coarsening
 template <typename T>
-__global__ void pcoarsen_kernel(int nE, int ndf, const T* __restrict__ Af, T* __restrict__ Ac) {
+__global__ void pcoarsen_kernel(int nE, int ndf, bool ns, const T* __restrict__ Af,
+                                T* __restrict__ Ac) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
+  const int nlf = 4 * ndf;
   for (int r = 0; r < 8; ++r)
-    for (int c = 0; c <= r; ++c) {
+    for (int c = 0; c < (ns ? 8 : r + 1); ++c) {
       const int rf = (r / 2) * ndf + (r % 2), cf = (c / 2) * ndf + (c % 2);
-      Ac[(size_t)pk(r, c) * nE + e] = Af[(size_t)pk(rf, cf) * nE + e];
+      if (ns)
+        Ac[(size_t)(r * 8 + c) * nE + e] = Af[(size_t)(rf * nlf + cf) * nE + e];
+      else
+        Ac[(size_t)pk(r, c) * nE + e] = Af[(size_t)pk(rf, cf) * nE + e];
     }
 }
 
@@ -182,10 +192,162 @@ __global__ void __launch_bounds__(32 * WPB) agglomerate_warp_kernel(
   for (int t = lane; t < 128; t += 32) Yout[(size_t)t * nC + C] = Yw[t];
 }
 
+// Non-symmetric variant (one warp per macro-element): A_BI is assembled on
+// its own, A_II = LU without pivoting (positive-definite symmetric part),
+//   A_II^-1, Y = -A_II^-1 A_IB, S = A_BB + A_BI Y, A_c = J^T S J (full),
+//   Pi = Y J, Z = -A_BI A_II^-1 and Rt = Z^T J (Q_{k-1} = [J^T Z, J^T]).
+template <typename T, int WPB>
+__global__ void __launch_bounds__(32 * WPB) agglomerate_ns_warp_kernel(
+    int nc, const T* __restrict__ Af, T* __restrict__ Ac, T* __restrict__ AIIinv,
+    T* __restrict__ Yout, T* __restrict__ Pi, T* __restrict__ Rt, int* __restrict__ err) {
+  constexpr int PER = 64 + 128 + 128 + 256 + 64 + 64 + 128 + 128 + 128;
+  __shared__ T sh[WPB * PER];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nC = nc * nc;
+  const int C = blockIdx.x * WPB + warp;
+  if (C >= nC) return;
+  const int J = C / nc, I = C - J * nc;
+  const int n = 2 * nc, nEf = n * n;
+  T* AII = sh + warp * PER;      // 8 x 8
+  T* AIB = AII + 64;             // 8 x 16
+  T* ABI = AIB + 128;            // 16 x 8
+  T* ABB = ABI + 128;            // 16 x 16, becomes S
+  T* LUm = ABB + 256;            // 8 x 8 LU factors of A_II
+  T* Ai = LUm + 64;              // 8 x 8 A_II^-1
+  T* Yw = Ai + 64;               // 8 x 16
+  T* SJ = Yw + 128;              // 16 x 8
+  T* Zw = SJ + 128;              // 16 x 8
+  for (int t = lane; t < PER; t += 32) AII[t] = T(0);
+  __syncwarp();
+  for (int ch = 0; ch < 4; ++ch) {
+    const int ef = (2 * J + (ch >> 1)) * n + 2 * I + (ch & 1);
+    for (int t = lane; t < 64; t += 32) {
+      const int r = t >> 3, c = t & 7;
+      bool ir, ic;
+      int sr, sc;
+      child_map(ch, r >> 1, ir, sr);
+      child_map(ch, c >> 1, ic, sc);
+      const int lr = sr * 2 + (r & 1), lc = sc * 2 + (c & 1);
+      const T a = Af[(size_t)(r * 8 + c) * nEf + ef];
+      if (ir && ic) AII[lr * 8 + lc] += a;
+      else if (ir && !ic) AIB[lr * 16 + lc] += a;
+      else if (!ir && ic) ABI[lr * 8 + lc] += a;
+      else ABB[lr * 16 + lc] += a;
+    }
+    __syncwarp();
+  }
+  // LU of A_II (unit lower part below the diagonal)
+  for (int t = lane; t < 64; t += 32) LUm[t] = AII[t];
+  __syncwarp();
+  bool bad = false;
+  for (int k = 0; k < 8; ++k) {
+    T di = T(0);
+    if (lane == 0) {
+      T d = LUm[k * 8 + k];
+      if (!(d > T(0))) {
+        bad = true;
+        d = T(1);
+      }
+      di = T(1) / d;
+    }
+    di = __shfl_sync(0xffffffffu, di, 0);
+    if (lane > k && lane < 8) LUm[lane * 8 + k] *= di;
+    __syncwarp();
+    const int m = 7 - k;
+    for (int t = lane; t < m * m; t += 32) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      LUm[i * 8 + j] -= LUm[i * 8 + k] * LUm[k * 8 + j];
+    }
+    __syncwarp();
+  }
+  if (bad) atomicOr(err, 4);
+  // A_II^-1 column by column (lanes 0..7)
+  if (lane < 8) {
+    const int j = lane;
+    T col[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      T s = (i == j) ? T(1) : T(0);
+#pragma unroll
+      for (int k = 0; k < i; ++k) s -= LUm[i * 8 + k] * col[k];
+      col[i] = s;
+    }
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+      T s = col[i];
+#pragma unroll
+      for (int k = i + 1; k < 8; ++k) s -= LUm[i * 8 + k] * col[k];
+      col[i] = s / LUm[i * 8 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Ai[i * 8 + j] = col[i];
+  }
+  __syncwarp();
+  // Y = -A_II^-1 A_IB, Z = -A_BI A_II^-1
+  for (int t = lane; t < 128; t += 32) {
+    const int a = t >> 4, b = t & 15;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s -= Ai[a * 8 + k] * AIB[k * 16 + b];
+    Yw[t] = s;
+    const int bz = t >> 3, az = t & 7;
+    T z = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) z -= ABI[bz * 8 + k] * Ai[k * 8 + az];
+    Zw[t] = z;
+  }
+  __syncwarp();
+  // S = A_BB + A_BI Y (in place)
+  for (int t = lane; t < 256; t += 32) {
+    const int a = t >> 4, b = t & 15;
+    T s = ABB[t];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += ABI[a * 8 + k] * Yw[k * 16 + b];
+    ABB[t] = s;
+  }
+  __syncwarp();
+  // SJ = S J (16 x 8)
+  for (int t = lane; t < 128; t += 32) {
+    const int a = t >> 3, cb = t & 7, me = cb >> 1, kc = cb & 1;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) s += ABB[a * 16 + (me * 2 + c) * 2 + kf] * (T)c_Jc[c][kf][kc];
+    SJ[t] = s;
+  }
+  __syncwarp();
+  // outputs: A_c = J^T S J, A_II^-1, Pi = Y J, Rt = Z^T J, Y
+  for (int t = lane; t < 64; t += 32) {
+    const int ca = t >> 3, cb = t & 7;
+    const int me = ca >> 1, kc = ca & 1;
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) s += (T)c_Jc[c][kf][kc] * SJ[((me * 2 + c) * 2 + kf) * 8 + cb];
+    Ac[(size_t)t * nC + C] = s;
+    AIIinv[(size_t)t * nC + C] = Ai[t];
+    const int a = t >> 3, mb = cb >> 1, kb = cb & 1;
+    T pi = T(0), rt = T(0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int kf = 0; kf < 2; ++kf) {
+        const int b = (mb * 2 + c) * 2 + kf;
+        pi += Yw[a * 16 + b] * (T)c_Jc[c][kf][kb];
+        rt += Zw[b * 8 + a] * (T)c_Jc[c][kf][kb];
+      }
+    Pi[(size_t)t * nC + C] = pi;
+    Rt[(size_t)t * nC + C] = rt;
+  }
+  for (int t = lane; t < 128; t += 32) Yout[(size_t)t * nC + C] = Yw[t];
+}
+
 // ------------------------------------------------- K8 local correction
 // e_I <- e_I + A_II^-1 (r - A e)_I = A_II^-1 r_I + Y e_B
 template <typename T>
-__device__ __forceinline__ void local_correction_item(int nc, const T* __restrict__ AIIinv,
+__device__ __forceinline__ void local_correction_item(int nc, bool ns, const T* __restrict__ AIIinv,
                                                       const T* __restrict__ Y, const T* r, T* e,
                                                       int C) {
   const int nC = nc * nc;
@@ -209,7 +371,7 @@ __device__ __forceinline__ void local_correction_item(int nc, const T* __restric
   for (int a = 0; a < 8; ++a) {
     T s = T(0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) s += AIIinv[(size_t)pk_any(a, k) * nC + C] * rI[k];
+    for (int k = 0; k < 8; ++k) s += AIIinv[(size_t)(ns ? a * 8 + k : pk_any(a, k)) * nC + C] * rI[k];
 #pragma unroll
     for (int b = 0; b < 16; ++b) s += Y[(size_t)(a * 16 + b) * nC + C] * eB[b];
     const int ed = interior_edge(n, I, J, a >> 1);
@@ -218,11 +380,11 @@ __device__ __forceinline__ void local_correction_item(int nc, const T* __restric
 }
 
 template <typename T>
-__global__ void local_correction_kernel(int nc, const T* __restrict__ AIIinv,
+__global__ void local_correction_kernel(int nc, bool ns, const T* __restrict__ AIIinv,
                                         const T* __restrict__ Y, const T* __restrict__ r,
                                         T* __restrict__ e) {
   const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C < nc * nc) local_correction_item<T>(nc, AIIinv, Y, r, e, C);
+  if (C < nc * nc) local_correction_item<T>(nc, ns, AIIinv, Y, r, e, C);
 }
 
 
@@ -373,8 +535,9 @@ __global__ void prolong_p_kernel(int n, const T* __restrict__ ec, T* __restrict_
 
 // ------------------------------------------------------ K10 coarsest level
 template <typename T>
-__global__ void coarse_assemble_kernel(int n, const T* __restrict__ A, const int* __restrict__ fidx,
-                                       int nf, double* __restrict__ dense) {
+__global__ void coarse_assemble_kernel(int n, bool ns, const T* __restrict__ A,
+                                       const int* __restrict__ fidx, int nf,
+                                       double* __restrict__ dense) {
   const int nE = n * n;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
@@ -387,9 +550,43 @@ __global__ void coarse_assemble_kernel(int n, const T* __restrict__ A, const int
       const int fc = fidx[ed[c / 2]];
       if (fc < 0) continue;
       atomicAdd(&dense[(size_t)(fr * 2 + (r & 1)) * nf + fc * 2 + (c & 1)],
-                (double)A[(size_t)pk_any(r, c) * nE + e]);
+                (double)A[(size_t)(ns ? r * 8 + c : pk_any(r, c)) * nE + e]);
     }
   }
+}
+
+// Gauss-Jordan inverse without pivoting of a dense matrix with positive-
+// definite symmetric part, in place in global memory (one block); the
+// inverse ends up in M and is copied to Ainv.
+__global__ void coarse_gj_kernel(int nf, double* __restrict__ M, double* __restrict__ Ainv,
+                                 int* __restrict__ err) {
+  extern __shared__ double colk[];
+  __shared__ double piv;
+  for (int k = 0; k < nf; ++k) {
+    if (threadIdx.x == 0) {
+      double d = M[(size_t)k * nf + k];
+      if (!(d > 0.0)) {
+        atomicOr(err, 8);
+        d = 1.0;
+      }
+      piv = 1.0 / d;
+      M[(size_t)k * nf + k] = 1.0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nf; j += blockDim.x) M[(size_t)k * nf + j] *= piv;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) colk[i] = (i == k) ? 0.0 : M[(size_t)i * nf + k];
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < (int64_t)nf * nf; t += blockDim.x) {
+      const int i = (int)(t / nf), j = (int)(t - (int64_t)i * nf);
+      if (i == k) continue;
+      if (j == k)
+        M[t] = -colk[i] * M[(size_t)k * nf + k];
+      else
+        M[t] -= colk[i] * M[(size_t)k * nf + j];
+    }
+    __syncthreads();
+  }
+  for (int64_t t = threadIdx.x; t < (int64_t)nf * nf; t += blockDim.x) Ainv[t] = M[t];
 }
 
 __global__ void coarse_factor_kernel(int nf, double* __restrict__ M, int* __restrict__ err) {
@@ -419,10 +616,12 @@ __global__ void coarse_factor_kernel(int nf, double* __restrict__ M, int* __rest
 
 // Coarsest level, small case (the whole matrix fits in shared memory): one
 // block assembles A_1 from the element matrices and inverts it in place by
-// Gauss-Jordan elimination without pivoting (A_1 is SPD), in FP64.
+// Gauss-Jordan elimination without pivoting (A_1 is SPD, or has a positive-
+// definite symmetric part), in FP64.
 template <typename T>
-__global__ void coarse_setup_smem_kernel(int n, const T* __restrict__ A, const int* __restrict__ fidx,
-                                         int nf, double* __restrict__ Ainv, int* __restrict__ err) {
+__global__ void coarse_setup_smem_kernel(int n, bool ns, const T* __restrict__ A,
+                                         const int* __restrict__ fidx, int nf,
+                                         double* __restrict__ Ainv, int* __restrict__ err) {
   extern __shared__ double M[];
   double* colk = M + (size_t)nf * nf;
   const int nE = n * n;
@@ -435,7 +634,7 @@ __global__ void coarse_setup_smem_kernel(int n, const T* __restrict__ A, const i
     const int fr = fidx[ed[r >> 1]], fc = fidx[ed[c >> 1]];
     if (fr < 0 || fc < 0) continue;
     atomicAdd(&M[(size_t)(fr * 2 + (r & 1)) * nf + fc * 2 + (c & 1)],
-              (double)A[(size_t)pk_any(r, c) * nE + e]);
+              (double)A[(size_t)(ns ? r * 8 + c : pk_any(r, c)) * nE + e]);
   }
   __syncthreads();
   __shared__ double piv;
@@ -527,8 +726,8 @@ __global__ void coarse_solve_kernel(int n, const int* __restrict__ fidx, const i
 // P1 (two modes per edge) element matvec y += A x for one element, and the
 // block-Jacobi update of one edge, for the single-block tail kernel.
 template <typename T>
-__device__ __forceinline__ void matvec_p1_item(int n, const T* __restrict__ A, const T* x, T* y,
-                                               int e) {
+__device__ __forceinline__ void matvec_p1_item(int n, bool ns, const T* __restrict__ A, const T* x,
+                                               T* y, int e) {
   const int nE = n * n, nedge = 2 * n * (n + 1);
   int ed[4];
   elem_edges(n, e, ed);
@@ -538,15 +737,22 @@ __device__ __forceinline__ void matvec_p1_item(int n, const T* __restrict__ A, c
     xl[c] = x[(size_t)(c & 1) * nedge + ed[c >> 1]];
     yl[c] = T(0);
   }
+  if (ns) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < r; ++c) {
-      const T a = A[(size_t)pk(r, c) * nE + e];
-      yl[r] += a * xl[c];
-      yl[c] += a * xl[r];
+      for (int c = 0; c < 8; ++c) yl[r] += A[(size_t)(r * 8 + c) * nE + e] * xl[c];
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int c = 0; c < r; ++c) {
+        const T a = A[(size_t)pk(r, c) * nE + e];
+        yl[r] += a * xl[c];
+        yl[c] += a * xl[r];
+      }
+      yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
     }
-    yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
   }
 #pragma unroll
   for (int le = 0; le < 4; ++le) {
@@ -557,8 +763,8 @@ __device__ __forceinline__ void matvec_p1_item(int n, const T* __restrict__ A, c
 }
 
 template <typename T>
-__device__ __forceinline__ void bj_p1_item(int n, const T* __restrict__ Dinv, const T* r, T* y,
-                                           T* e, T omega, bool first, int edge) {
+__device__ __forceinline__ void bj_p1_item(int n, bool ns, const T* __restrict__ Dinv, const T* r,
+                                           T* y, T* e, T omega, bool first, int edge) {
   const int nedge = 2 * n * (n + 1);
   if (bnd_edge(n, edge)) return;
   const T d0 = first ? r[edge] : r[edge] - y[edge];
@@ -567,8 +773,17 @@ __device__ __forceinline__ void bj_p1_item(int n, const T* __restrict__ Dinv, co
     y[edge] = T(0);
     y[nedge + edge] = T(0);
   }
+  // packed [d00, d10, d11] or full [d00, d01, d10, d11]
   const T a00 = Dinv[edge], a10 = Dinv[(size_t)nedge + edge], a11 = Dinv[(size_t)2 * nedge + edge];
-  const T s0 = a00 * d0 + a10 * d1, s1 = a10 * d0 + a11 * d1;
+  T s0, s1;
+  if (ns) {
+    const T b10 = a11, b11 = Dinv[(size_t)3 * nedge + edge];
+    s0 = a00 * d0 + a10 * d1;
+    s1 = b10 * d0 + b11 * d1;
+  } else {
+    s0 = a00 * d0 + a10 * d1;
+    s1 = a10 * d0 + a11 * d1;
+  }
   if (first) {
     e[edge] = omega * s0;
     e[nedge + edge] = omega * s1;
@@ -603,11 +818,13 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     for (int i = tid; i < 6 * L.nEdge; i += nth) base[i] = T(0);
     if (L.staged) {
       const int nE = L.n * L.n, nC = nE / 4;
-      stage_copy<T>(sm + L.a_off, L.A, 36 * nE);
-      stage_copy<T>(sm + L.dinv_off, L.Dinv, 3 * L.nEdge);
-      stage_copy<T>(sm + L.aii_off, L.AIIinv, 36 * nC);
+      const int na = P.ns ? 64 : 36, nd2 = P.ns ? 4 : 3;
+      stage_copy<T>(sm + L.a_off, L.A, na * nE);
+      stage_copy<T>(sm + L.dinv_off, L.Dinv, nd2 * L.nEdge);
+      stage_copy<T>(sm + L.aii_off, L.AIIinv, na * nC);
       stage_copy<T>(sm + L.y_off, L.Y, 128 * nC);
       stage_copy<T>(sm + L.pi_off, L.Pi, 64 * nC);
+      if (P.ns) stage_copy<T>(sm + L.rt_off, L.Rt, 64 * nC);
     }
   }
   if (staged_inv) stage_copy<double>(ainv_s, P.Ainv, P.nf * P.nf);
@@ -628,23 +845,24 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
     const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
     const T* Yb = L.staged ? sm + L.y_off : L.Y;
-    const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
-    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, true, i);
+    const T* Rt = P.ns ? (L.staged ? sm + L.rt_off : L.Rt) : (L.staged ? sm + L.pi_off : L.Pi);
+    const bool ns = P.ns != 0;
+    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, true, i);
     __syncthreads();
     for (int it = 1; it < L.m; ++it) {
-      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
       __syncthreads();
-      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, false, i);
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
       __syncthreads();
     }
     if (P.lc != HDGMG_LC_NONE) {
-      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
-    for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+    for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
     __syncthreads();
     T* rc = sm + P.lv[l + 1].voff;
-    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Pi, r, y, rc, i);
+    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, y, rc, i);
     __syncthreads();
   }
   {  // B_1 = A_1^-1
@@ -666,16 +884,17 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* Yb = L.staged ? sm + L.y_off : L.Y;
     const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
     const T* ec = sm + P.lv[l + 1].voff + 2 * P.lv[l + 1].nEdge;
+    const bool ns = P.ns != 0;
     for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
     __syncthreads();
     if (P.lc == HDGMG_LC_BOTH) {
-      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
     for (int it = 0; it < L.m; ++it) {
-      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, A, e, y, i);
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
       __syncthreads();
-      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, Dinv, r, y, e, P.omega, false, i);
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
       __syncthreads();
     }
   }
@@ -907,11 +1126,13 @@ __global__ void copy_boundary_kernel(int n, int nd, const double* __restrict__ g
 }
 
 template <typename T>
-__global__ void unpack_kernel(int nl, int nE, const T* __restrict__ Ap, double* __restrict__ full) {
+__global__ void unpack_kernel(int nl, int nE, bool ns, const T* __restrict__ Ap,
+                              double* __restrict__ full) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   for (int r = 0; r < nl; ++r)
-    for (int c = 0; c < nl; ++c) full[(size_t)(r * nl + c) * nE + e] = (double)Ap[(size_t)pk_any(r, c) * nE + e];
+    for (int c = 0; c < nl; ++c)
+      full[(size_t)(r * nl + c) * nE + e] = (double)Ap[(size_t)(ns ? r * nl + c : pk_any(r, c)) * nE + e];
 }
 
 
@@ -932,31 +1153,37 @@ __global__ void unpack_kernel(int nl, int nE, const T* __restrict__ Ap, double* 
   }
 
 template <typename T>
-void launch_matvec(cudaStream_t s, int n, int nd, const T* A, const T* x, T* y, T alpha) {
-#define MV(ND) launch_matvec_nd<T, ND>(s, n, A, x, y, alpha)
+void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha) {
+#define MV(ND)                                              \
+  if (ns) launch_matvec_nd<T, ND, true>(s, n, A, x, y, alpha); \
+  else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha)
   ND_DISPATCH(nd, MV)
 #undef MV
 }
 
 template <typename T>
-void launch_bj_blocks(cudaStream_t s, int n, int nd, const T* A, T* Dinv, int* err) {
-#define BJ(ND) launch_bj_blocks_nd<T, ND>(s, n, A, Dinv, err)
+void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err) {
+#define BJ(ND)                                                \
+  if (ns) launch_bj_blocks_nd<T, ND, true>(s, n, A, Dinv, err); \
+  else launch_bj_blocks_nd<T, ND, false>(s, n, A, Dinv, err)
   ND_DISPATCH(nd, BJ)
 #undef BJ
 }
 
 template <typename T>
-void launch_bj_update(cudaStream_t s, int n, int nd, const T* Dinv, const T* r, T* y, T* e,
-                      T omega, int first) {
-#define BU(ND) launch_bj_update_nd<T, ND>(s, n, Dinv, r, y, e, omega, first)
+void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
+                      T* e, T omega, int first) {
+#define BU(ND)                                                                  \
+  if (ns) launch_bj_update_nd<T, ND, true>(s, n, Dinv, r, y, e, omega, first);  \
+  else launch_bj_update_nd<T, ND, false>(s, n, Dinv, r, y, e, omega, first)
   ND_DISPATCH(nd, BU)
 #undef BU
 }
 
 template <typename T>
-void launch_pcoarsen(cudaStream_t s, int nE, int ndf, const T* Af, T* Ac) {
+void launch_pcoarsen(cudaStream_t s, int nE, int ndf, bool ns, const T* Af, T* Ac) {
   note_launch();
-  pcoarsen_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nE, ndf, Af, Ac);
+  pcoarsen_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nE, ndf, ns, Af, Ac);
 }
 
 static void upload_jc() {
@@ -972,18 +1199,22 @@ static void upload_jc() {
 }
 
 template <typename T>
-void launch_agglomerate(cudaStream_t s, int nc, const T* Af, T* Ac, T* AIIinv, T* Y, T* Pi,
-                        int* err) {
+void launch_agglomerate(cudaStream_t s, int nc, bool ns, const T* Af, T* Ac, T* AIIinv, T* Y,
+                        T* Pi, T* Rt, int* err) {
   upload_jc();
   note_launch();
-  agglomerate_warp_kernel<T, 4><<<nblk(nc * nc, 4), 128, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
+  if (ns)
+    agglomerate_ns_warp_kernel<T, 4><<<nblk(nc * nc, 4), 128, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, Rt,
+                                                                       err);
+  else
+    agglomerate_warp_kernel<T, 4><<<nblk(nc * nc, 4), 128, 0, s>>>(nc, Af, Ac, AIIinv, Y, Pi, err);
 }
 
 template <typename T>
-void launch_local_correction(cudaStream_t s, int nc, const T* AIIinv, const T* Y, const T* r,
-                             T* e) {
+void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
+                             const T* r, T* e) {
   note_launch();
-  local_correction_kernel<T><<<nblk(nc * nc, 128), 128, 0, s>>>(nc, AIIinv, Y, r, e);
+  local_correction_kernel<T><<<nblk(nc * nc, 128), 128, 0, s>>>(nc, ns, AIIinv, Y, r, e);
 }
 
 template <typename T>
@@ -1018,11 +1249,16 @@ void launch_prolong_p(cudaStream_t s, int n, int nd, const T* ec, T* e) {
 }
 
 template <typename T>
-void launch_coarse_assemble(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
+void launch_coarse_assemble(cudaStream_t s, int n, bool ns, const T* A, const int* freeidx, int nf,
                             double* dense) {
   cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)nf * nf, s);
   note_launch();
-  coarse_assemble_kernel<T><<<nblk(n * n, 64), 64, 0, s>>>(n, A, freeidx, nf, dense);
+  coarse_assemble_kernel<T><<<nblk(n * n, 64), 64, 0, s>>>(n, ns, A, freeidx, nf, dense);
+}
+
+void launch_coarse_gj(cudaStream_t s, int nf, double* M, double* Ainv, int* err) {
+  note_launch();
+  coarse_gj_kernel<<<1, 1024, sizeof(double) * (size_t)(nf > 0 ? nf : 1), s>>>(nf, M, Ainv, err);
 }
 
 void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
@@ -1031,8 +1267,8 @@ void launch_coarse_factor(cudaStream_t s, int nf, double* dense, int* err) {
 }
 
 template <typename T>
-bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* freeidx, int nf,
-                              double* Ainv, int* err) {
+bool launch_coarse_setup_smem(cudaStream_t s, int n, bool ns, const T* A, const int* freeidx,
+                              int nf, double* Ainv, int* err) {
   const size_t shm = sizeof(double) * ((size_t)nf * nf + nf);
   if (shm > 200 * 1024) return false;
   static const bool attr = [] {
@@ -1042,7 +1278,7 @@ bool launch_coarse_setup_smem(cudaStream_t s, int n, const T* A, const int* free
   }();
   (void)attr;
   note_launch();
-  coarse_setup_smem_kernel<T><<<1, 1024, shm, s>>>(n, A, freeidx, nf, Ainv, err);
+  coarse_setup_smem_kernel<T><<<1, 1024, shm, s>>>(n, ns, A, freeidx, nf, Ainv, err);
   return true;
 }
 
@@ -1091,9 +1327,9 @@ void launch_mask(cudaStream_t s, int n, int nd, T* x) {
 }
 
 template <typename T>
-void launch_unpack(cudaStream_t s, int nl, int nE, const T* Ap, double* full) {
+void launch_unpack(cudaStream_t s, int nl, int nE, bool ns, const T* Ap, double* full) {
   note_launch();
-  unpack_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nl, nE, Ap, full);
+  unpack_kernel<T><<<nblk(nE, 128), 128, 0, s>>>(nl, nE, ns, Ap, full);
 }
 
 template <typename A, typename B>
@@ -1181,29 +1417,33 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
 
 // explicit instantiations
 #define INST(T)                                                                                 \
-  template void launch_matvec<T>(cudaStream_t, int, int, const T*, const T*, T*, T);            \
-  template void launch_bj_blocks<T>(cudaStream_t, int, int, const T*, T*, int*);                \
-  template void launch_bj_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T, int); \
-  template void launch_pcoarsen<T>(cudaStream_t, int, int, const T*, T*);                       \
-  template void launch_agglomerate<T>(cudaStream_t, int, const T*, T*, T*, T*, T*, int*);       \
-  template void launch_local_correction<T>(cudaStream_t, int, const T*, const T*, const T*, T*); \
+  template void launch_matvec<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T);      \
+  template void launch_bj_blocks<T>(cudaStream_t, int, int, bool, const T*, T*, int*);          \
+  template void launch_bj_update<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T*, T, \
+                                    int);                                                       \
+  template void launch_pcoarsen<T>(cudaStream_t, int, int, bool, const T*, T*);                 \
+  template void launch_agglomerate<T>(cudaStream_t, int, bool, const T*, T*, T*, T*, T*, T*,    \
+                                      int*);                                                    \
+  template void launch_local_correction<T>(cudaStream_t, int, bool, const T*, const T*,         \
+                                           const T*, T*);                                       \
   template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);            \
   template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);             \
   template void launch_restrict_p<T>(cudaStream_t, int, int, const T*, T*, T*);                 \
   template void launch_prolong_p<T>(cudaStream_t, int, int, const T*, T*);                      \
-  template void launch_coarse_assemble<T>(cudaStream_t, int, const T*, const int*, int, double*); \
+  template void launch_coarse_assemble<T>(cudaStream_t, int, bool, const T*, const int*, int,   \
+                                          double*);                                             \
   template void launch_coarse_solve<T>(cudaStream_t, int, const int*, const int*, int,          \
                                        const double*, const T*, T*);                            \
   template void launch_mask<T>(cudaStream_t, int, int, T*);                                     \
-  template void launch_unpack<T>(cudaStream_t, int, int, const T*, double*);
+  template void launch_unpack<T>(cudaStream_t, int, int, bool, const T*, double*);
 INST(double)
 INST(float)
 #undef INST
 template void launch_convert<double, float>(cudaStream_t, int64_t, const double*, float*);
 template void launch_vcycle_tail<double>(cudaStream_t, const TailParams<double>&);
-template bool launch_coarse_setup_smem<double>(cudaStream_t, int, const double*, const int*, int,
-                                               double*, int*);
-template bool launch_coarse_setup_smem<float>(cudaStream_t, int, const float*, const int*, int,
+template bool launch_coarse_setup_smem<double>(cudaStream_t, int, bool, const double*, const int*,
+                                               int, double*, int*);
+template bool launch_coarse_setup_smem<float>(cudaStream_t, int, bool, const float*, const int*, int,
                                               double*, int*);
 template void launch_dot<double>(cudaStream_t, int64_t, const double*, const double*, double*, double*);
 template void launch_dot_fused<double>(cudaStream_t, int64_t, const double*, const double*, double*,

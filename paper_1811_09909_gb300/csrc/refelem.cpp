@@ -140,6 +140,7 @@ RefElement build_ref_element(int p, double hx, double hy) {
   // n=-y), 3 top.  Edge quadrature at the Gauss nodes of the tangential
   // direction, measure |e|/2.
   R.E.assign(nv * nv, 0.0);
+  R.Ef.assign(4 * nv * nv, 0.0);
   R.F.assign(nv * nt, 0.0);
   R.Cx.assign(nv * nt, 0.0);
   R.Cy.assign(nv * nt, 0.0);
@@ -156,6 +157,7 @@ RefElement build_ref_element(int p, double hx, double hy) {
         for (int nb = 0; nb < p1; ++nb) {
           const int b = vert ? (q * p1 + nb) : (nb * p1 + q);
           R.E[a * nv + b] += wq * phia * lend[nb];
+          R.Ef[(size_t)edge * nv * nv + a * nv + b] += wq * phia * lend[nb];
         }
         for (int k = 0; k < p1; ++k) {
           const double psi = std::sqrt((2.0 * k + 1.0) / len) * legendre_p(k, xi[q]);

@@ -15,6 +15,7 @@ TAU_CONST, TAU_OVER_H = 0, 1
 LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
 KRYLOV_NONE, KRYLOV_CG, KRYLOV_GMRES = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_IR = 0, 1, 2
+PDE_DIFFUSION, PDE_CONVDIFF = 0, 1
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
           -5: "EBREAKDOWN", -6: "ETIMEOUT"}
@@ -32,7 +33,8 @@ class Problem(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double),
-                ("tau_mode", ctypes.c_int32), ("tau_c", ctypes.c_double)]
+                ("tau_mode", ctypes.c_int32), ("tau_c", ctypes.c_double),
+                ("pde", ctypes.c_int32), ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -150,7 +152,7 @@ class Solver:
     krylov, max_it, rtol, precision)."""
 
     def __init__(self, n, p, tau_mode=TAU_OVER_H, tau_c=1.0, domain=(0.0, 1.0, 0.0, 1.0),
-                 stream=None, **opts):
+                 stream=None, beta=None, **opts):
         import torch
         lib = load()
         self.torch = torch
@@ -158,7 +160,9 @@ class Solver:
         self.nd = p + 1
         self.nv = (p + 1) ** 2
         self.n_edges = 2 * n * (n + 1)
-        prob = Problem(n, p, domain[0], domain[1], domain[2], domain[3], tau_mode, tau_c)
+        pde = PDE_DIFFUSION if beta is None else PDE_CONVDIFF
+        bx, by = (0.0, 0.0) if beta is None else (float(beta[0]), float(beta[1]))
+        prob = Problem(n, p, domain[0], domain[1], domain[2], domain[3], tau_mode, tau_c, pde, bx, by)
         self.opts = default_opts(**opts)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -309,8 +313,11 @@ class Batch:
         arr = (Problem * len(problems))()
         for i, pr in enumerate(problems):
             dom = pr.get("domain", (0.0, 1.0, 0.0, 1.0))
+            beta = pr.get("beta")
             arr[i] = Problem(pr["n"], pr["p"], dom[0], dom[1], dom[2], dom[3],
-                             pr.get("tau_mode", TAU_OVER_H), pr.get("tau_c", 1.0))
+                             pr.get("tau_mode", TAU_OVER_H), pr.get("tau_c", 1.0),
+                             PDE_DIFFUSION if beta is None else PDE_CONVDIFF,
+                             *((0.0, 0.0) if beta is None else (float(beta[0]), float(beta[1]))))
             self.problems.append((pr["n"], pr["p"]))
         self.opts = default_opts(**opts)
         if stream is None:

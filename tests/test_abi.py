@@ -54,12 +54,14 @@ def test_default_options(lib):
     (dict(n=12, coarsest=2), "halve"), (dict(tau_c=-1.0), "tau_c"),
     (dict(krylov=2, restart=0), "gmres_restart"), (dict(krylov=2, restart=257), "gmres_restart"),
     (dict(krylov=3), "krylov"),
+    (dict(pde=1, krylov=1), "symmetric"), (dict(pde=5), "unknown pde"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg
     n = kw.get("n", 16)
     p = kw.get("p", 2)
-    prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0))
+    prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0),
+                         kw.get("pde", 0), 1.0, 0.5)
     o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2), krylov=kw.get("krylov", 1),
                            gmres_restart=kw.get("restart", 30))
     ctx = ctypes.c_void_p()
