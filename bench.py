@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--arm", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the batched (64 problems x 16 RHS) and adjoint (1024^2) lines")
+                    help="skip the batched (64 problems x 16 RHS), adjoint (1024^2) and "
+                         "convection-diffusion (512^2, p=6) lines")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -418,6 +419,83 @@ def run_batched(dev, steps, warmup):
                         "16 N(0,1) right-hand sides each; mixed precision, one batch set-up + solve"}
 
 
+def condense_cd_flops(p, nE):
+    """Algorithmic FP64 flops of the convection-diffusion condensation per
+    launch: LU of S (2 n_v^3 / 3), X = S^-1 W (2 n_v^2 n_t), V^T X
+    (2 n_t^2 n_v) per element."""
+    nv, nt = (p + 1) ** 2, 4 * (p + 1)
+    return nE * (2.0 * nv ** 3 / 3.0 + 2.0 * nv * nv * nt + 2.0 * nt * nt * nv)
+
+
+def run_convdiff(dev, steps, warmup):
+    """Convection-diffusion, eps = 1e-3, beta = (1, 0.5), 512 x 512 quads,
+    p = 6, manufactured u = sin(pi x) sin(pi y): FP64 condensation, FGMRES(30)
+    right-preconditioned by the step-3 V-cycle in FP32 with the BF16 finest
+    operator (mixed) or in FP64; the error of the mixed solution against the
+    FP64 one and against the manufactured solution is reported."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1811_09909_gb300 import hdgmg
+    from paper_1811_09909_gb300 import workloads as W
+    n, p, eps, beta = 512, 6, 1e-3, (1.0, 0.5)
+    wl = W.convdiff(n, p, eps=eps, beta=beta)
+    logk = torch.as_tensor(wl.log_kappa, device=dev)
+    f = torch.as_tensor(wl.f[0], device=dev)
+    opts = dict(coarsest_n=4, m_fine=1, m_growth=2, m_max=4, rtol=1e-10,
+                krylov=hdgmg.KRYLOV_GMRES, gmres_restart=30, local_corr=hdgmg.LC_PRE,
+                tau_mode=hdgmg.TAU_OVER_H, tau_c=eps, beta=beta)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    sols = {}
+    for name, prec in (("mixed_bf16", hdgmg.PREC_BF16), ("mixed_fp32", hdgmg.PREC_FP32),
+                       ("fp64", hdgmg.PREC_FP64)):
+        s = hdgmg.Solver(n, p, precision=prec, stream=stream, **opts)
+        times, infos = [], []
+        for it in range(warmup + steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.setup(logk)
+            lam, u, _, info = s.solve(f, want_q=False)
+            e1.record(stream)
+            e1.synchronize()
+            if it >= warmup:
+                times.append(e0.elapsed_time(e1))
+                infos.append(info)
+        assert all(i.converged for i in infos)
+        ms = statistics.mean(times)
+        sols[name] = (lam, u)
+        cms = statistics.mean(i.t_condense_ms for i in infos)
+        out[name] = {"value": wl.interior_trace_dofs / (ms * 1e-3), "ms_per_step": ms,
+                     "setup_ms": infos[-1].t_setup_ms, "condense_ms": cms,
+                     "solve_ms": infos[-1].t_solve_ms, "iters": infos[-1].iters,
+                     "rel_res": max(i.rel_res for i in infos)}
+        s.close()
+    lam64, u64 = sols["fp64"]
+    for name in ("mixed_bf16", "mixed_fp32"):
+        lam, u = sols[name]
+        out[name]["lambda_rel_err_vs_fp64"] = float(torch.linalg.norm(lam - lam64) /
+                                                    torch.linalg.norm(lam64))
+    xi, _ = np.polynomial.legendre.leggauss(p + 1)
+    e = np.arange(n * n)
+    jj, ii = np.divmod(e, n)
+    a = np.arange((p + 1) ** 2)
+    Xn = (ii[None, :] + 0.5) / n + 0.5 / n * xi[a % (p + 1)][:, None]
+    Yn = (jj[None, :] + 0.5) / n + 0.5 / n * xi[a // (p + 1)][:, None]
+    u_ex = torch.as_tensor(np.sin(math.pi * Xn) * np.sin(math.pi * Yn), device=dev)
+    err = float((sols["mixed_bf16"][1] - u_ex).abs().max())
+    flops = condense_cd_flops(p, n * n)
+    return {"workload": "convection-diffusion eps=1e-3, beta=(1,0.5), 512x512 quads, p=6, "
+                        "u=sin(pi x)sin(pi y); FGMRES(30) + step-3 V-cycle (m_N=1 doubling to 4, "
+                        "coarsest 4x4); FP64 condensation",
+            "interior_trace_dofs": wl.interior_trace_dofs, "unit": UNIT, **out,
+            "u_nodal_max_err_vs_exact": err,
+            "condense_fp64_tflops": flops / (out["fp64"]["condense_ms"] * 1e-3) / 1e12,
+            "condense_fp64_frac": flops / (out["fp64"]["condense_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+
+
 def run_adjoint(dev, steps, warmup):
     """Misfit gradient at 1024 x 1024, p = 4: set-up, forward solve, misfit,
     transposed multigrid solve and per-element contraction."""
@@ -469,6 +547,7 @@ def main():
         dev = torch.device("cuda", 0)
         line["batched"] = run_batched(dev, steps=2, warmup=1)
         line["adjoint"] = run_adjoint(dev, steps=2, warmup=1)
+        line["convdiff"] = run_convdiff(dev, steps=2, warmup=1)
     if rank == 0:
         if (not args.no_cpu_baseline and args.arm == "both"
                 and int(os.environ.get("WORLD_SIZE", "1")) == 1):

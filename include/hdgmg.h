@@ -64,7 +64,7 @@ typedef enum {
 enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min */
 enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
 enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1, HDGMG_KRYLOV_GMRES = 2 };
-enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2 };
+enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2, HDGMG_PREC_BF16 = 3 };
 enum { HDGMG_PDE_DIFFUSION = 0, HDGMG_PDE_CONVDIFF = 1 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
@@ -111,7 +111,12 @@ typedef struct {
                              dot products) preconditioned by the FP32 V-cycle.
                              FP32_IR: iterative refinement -- FP64 residual of
                              the FP64 operator, inner FP32 PCG with the FP32
-                             V-cycle on the normalised residual; FP64         */
+                             V-cycle on the normalised residual.
+                             BF16: as FP32, but the finest level's V-cycle
+                             matvecs read a BF16 copy of the element
+                             operators (FP32 accumulation; block-Jacobi
+                             blocks and coarse levels from the FP64
+                             operator, rounded to FP32); FP64                */
   double inner_rtol;      /* FP32_IR only: inner PCG tolerance per refinement
                              step, in (0,1); 1e-5                             */
   int32_t cluster_tail_n; /* > 0: the P1 levels with n <= this run fused in

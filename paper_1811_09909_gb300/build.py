@@ -13,8 +13,9 @@ LIB = os.path.join(BUILD, "libhdgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["refelem.cpp", "k_condense.cu", "k_mg.cu", "k_ctail.cu", "k_krylov.cu", "hdgmg_api.cu",
            "hdgmg_batch.cpp"]
-# k_edge_inst.cu is built once per (real type, trace modes per edge)
-EDGE_UNITS = [(t, nd) for nd in range(2, 10) for t in ("double", "float")]
+# k_edge_inst.cu is built once per (real type, trace modes per edge), plus
+# once per ND for the BF16-storage matvec
+EDGE_UNITS = [(t, nd) for nd in range(2, 10) for t in ("double", "float", "bf16")]
 
 
 def nvcc():
@@ -32,7 +33,10 @@ def _compile(unit, extra):
         real, nd = unit
         src = "k_edge_inst.cu"
         obj = os.path.join(BUILD, f"k_edge_{real}_{nd}.o")
-        extra = [f"-DHDGMG_REAL={real}", f"-DHDGMG_ND={nd}", *extra]
+        if real == "bf16":
+            extra = ["-DHDGMG_BF16", "-DHDGMG_REAL=float", f"-DHDGMG_ND={nd}", *extra]
+        else:
+            extra = [f"-DHDGMG_REAL={real}", f"-DHDGMG_ND={nd}", *extra]
     else:
         src = unit
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -345,6 +346,19 @@ hdgmg_status check_launch(const char* where) {
 }
 
 // ----------------------------------------------------------- V-cycle (Alg. 1)
+// y += A_l e on level l (the finest level reads its BF16 copy when it has one)
+template <typename T>
+void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y) {
+  Level& L = c->levels[l];
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.A16) {
+      launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f);
+      return;
+    }
+  }
+  launch_matvec<T>(c->stream, L.n, L.nd, c->ns, ld<T>(L).A, x, y, T(1));
+}
+
 template <typename T>
 void vcycle(hdgmg_ctx* c, int l) {
   cudaStream_t s = c->stream;
@@ -369,7 +383,7 @@ void vcycle(hdgmg_ctx* c, int l) {
   const bool ns = c->ns;
   launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
   for (int i = 1; i < L.m; ++i) {
-    launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
+    level_matvec<T>(c, l, D.e, D.y);
     launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
   }
   // step 3: local correction (interior edges of the next level's macro-elements)
@@ -378,7 +392,7 @@ void vcycle(hdgmg_ctx* c, int l) {
   // step 4: coarse-grid correction
   Level& Lc = c->levels[l + 1];
   LevelData<T>& Dc = ld<T>(Lc);
-  launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
+  level_matvec<T>(c, l, D.e, D.y);
   if (L.transfer == 1)
     launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
   else
@@ -393,7 +407,7 @@ void vcycle(hdgmg_ctx* c, int l) {
     launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
   // step 6: post-smoothing
   for (int i = 0; i < L.m; ++i) {
-    launch_matvec<T>(s, L.n, L.nd, ns, D.A, D.e, D.y, T(1));
+    level_matvec<T>(c, l, D.e, D.y);
     launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
   }
 }
@@ -904,7 +918,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.krylov < 0 || o.krylov > 2) return fail(HDGMG_EINVAL, "unknown krylov");
   if (o.krylov == HDGMG_KRYLOV_GMRES && (o.gmres_restart < 1 || o.gmres_restart > 256))
     return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
-  if (o.precision < 0 || o.precision > 2) return fail(HDGMG_EINVAL, "unknown precision");
+  if (o.precision < 0 || o.precision > 3) return fail(HDGMG_EINVAL, "unknown precision");
   if (P.pde == HDGMG_PDE_CONVDIFF && o.krylov == HDGMG_KRYLOV_CG)
     return fail(HDGMG_EINVAL, "krylov CG needs a symmetric operator; use GMRES for convection-diffusion");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
@@ -997,6 +1011,9 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
       st = alloc_level<float>(c, L, false);
       if (st == HDGMG_OK && l == 0) {
         if (c->alloc(&L.d64.A, (size_t)L.nsym * L.nE) != cudaSuccess) st = fail(HDGMG_ENOMEM, "A64");
+        if (st == HDGMG_OK && o.precision == HDGMG_PREC_BF16 &&
+            c->alloc(&L.A16, (size_t)L.nsym * L.nE) != cudaSuccess)
+          st = fail(HDGMG_ENOMEM, "A16");
       }
     } else {
       st = alloc_level<double>(c, L, false);
@@ -1104,6 +1121,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   STATUS_TRY(check_launch("condensation"));
   if (c->opts.precision != HDGMG_PREC_FP64) {
     launch_convert<double, float>(s, (int64_t)L0.nsym * L0.nE, L0.d64.A, L0.d32.A);
+    if (L0.A16) launch_to_bf16(s, (int64_t)L0.nsym * L0.nE, L0.d64.A, L0.A16);
     STATUS_TRY(setup_hierarchy<float>(c));
   } else {
     STATUS_TRY(setup_hierarchy<double>(c));

@@ -1,6 +1,7 @@
 // Internal declarations of the hdgmg library (not part of the C ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,6 +78,7 @@ struct Level {
   int transfer = 0;   // 0 none (coarsest), 1 p-transfer, 2 h-transfer
   LevelData<double> d64;
   LevelData<float> d32;
+  __nv_bfloat16* A16 = nullptr;   // BF16 copy of A (finest level, PREC_BF16)
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +133,13 @@ void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err);
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first);
+// y += alpha A x with A stored in BF16, x, y and the accumulation in FP32
+void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
+                        const float* x, float* y, float alpha);
+template <int ND, bool NS>
+void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
+                           float alpha);
+void launch_to_bf16(cudaStream_t s, int64_t len, const double* in, __nv_bfloat16* out);
 template <typename T>
 void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err);
 template <typename T>

@@ -17,9 +17,16 @@
 
 namespace hdgmg {
 
+// element operator entries are read in their storage type TA and used in T
+template <typename T>
+static __device__ __forceinline__ T load_entry(const T* p) { return *p; }
+static __device__ __forceinline__ float load_entry(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
 // ---------------------------------------------------------------- K6 matvec
-template <typename T, int ND, bool NS>
-__global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict__ A,
+template <typename T, int ND, bool NS, typename TA = T>
+__global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y,
                                                      T alpha) {
   constexpr int NL = 4 * ND;
@@ -40,10 +47,10 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict_
       if (bnd_edge(n, ed[le])) continue;
 #pragma unroll 1
       for (int k = 0; k < ND; ++k) {
-        const T* Ar = A + (size_t)(le * ND + k) * NL * nE + e;
+        const TA* Ar = A + (size_t)(le * ND + k) * NL * nE + e;
         T s = T(0);
 #pragma unroll
-        for (int c = 0; c < NL; ++c) s += Ar[(size_t)c * nE] * xl[c];
+        for (int c = 0; c < NL; ++c) s += load_entry(Ar + (size_t)c * nE) * xl[c];
         atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * s);
       }
     }
@@ -55,11 +62,11 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const T* __restrict_
     for (int r = 0; r < NL; ++r) {
 #pragma unroll
       for (int c = 0; c < r; ++c) {
-        const T a = A[(size_t)pk(r, c) * nE + e];
+        const T a = load_entry(A + (size_t)pk(r, c) * nE + e);
         yl[r] += a * xl[c];
         yl[c] += a * xl[r];
       }
-      yl[r] += A[(size_t)pk(r, r) * nE + e] * xl[r];
+      yl[r] += load_entry(A + (size_t)pk(r, r) * nE + e) * xl[r];
     }
 #pragma unroll
     for (int le = 0; le < 4; ++le) {
@@ -226,6 +233,13 @@ template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha) {
   note_launch();
   matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
+}
+
+template <int ND, bool NS>
+void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
+                           float alpha) {
+  note_launch();
+  matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
 }
 
 template <typename T, int ND, bool NS>

@@ -1,5 +1,7 @@
 // One (type, ND) instantiation of the edge/element kernels of k_edge.cuh;
-// built once per pair with -DHDGMG_REAL=<double|float> -DHDGMG_ND=<2..9>.
+// built once per pair with -DHDGMG_REAL=<double|float> -DHDGMG_ND=<2..9>, and
+// once per ND with -DHDGMG_BF16 for the BF16-storage matvec alone (separate
+// units so that the widest ones compile in parallel).
 #include "k_edge.cuh"
 
 #ifndef HDGMG_REAL
@@ -10,6 +12,7 @@
 #endif
 
 namespace hdgmg {
+#ifndef HDGMG_BF16
 #define HDGMG_INST(NS)                                                                          \
   template void launch_matvec_nd<HDGMG_REAL, HDGMG_ND, NS>(cudaStream_t, int, const HDGMG_REAL*, \
                                                            const HDGMG_REAL*, HDGMG_REAL*,      \
@@ -23,4 +26,10 @@ namespace hdgmg {
 HDGMG_INST(false)
 HDGMG_INST(true)
 #undef HDGMG_INST
+#else
+template void launch_matvec_bf16_nd<HDGMG_ND, false>(cudaStream_t, int, const __nv_bfloat16*,
+                                                     const float*, float*, float);
+template void launch_matvec_bf16_nd<HDGMG_ND, true>(cudaStream_t, int, const __nv_bfloat16*,
+                                                    const float*, float*, float);
+#endif
 }  // namespace hdgmg

@@ -1161,6 +1161,29 @@ void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* 
 #undef MV
 }
 
+void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
+                        const float* x, float* y, float alpha) {
+#define MVB(ND)                                                        \
+  if (ns) launch_matvec_bf16_nd<ND, true>(s, n, A, x, y, alpha);       \
+  else launch_matvec_bf16_nd<ND, false>(s, n, A, x, y, alpha)
+  ND_DISPATCH(nd, MVB)
+#undef MVB
+}
+
+__global__ void to_bf16_kernel(int64_t len, const double* __restrict__ in,
+                               __nv_bfloat16* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __double2bfloat16(in[i]);
+}
+
+void launch_to_bf16(cudaStream_t s, int64_t len, const double* in, __nv_bfloat16* out) {
+  int blocks = nblk(len, 256);
+  if (blocks > 4 * 152 * 4) blocks = 4 * 152 * 4;
+  note_launch();
+  to_bf16_kernel<<<blocks, 256, 0, s>>>(len, in, out);
+}
+
 template <typename T>
 void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err) {
 #define BJ(ND)                                                \

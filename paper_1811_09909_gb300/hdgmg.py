@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libhdgmg.so")
 TAU_CONST, TAU_OVER_H = 0, 1
 LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
 KRYLOV_NONE, KRYLOV_CG, KRYLOV_GMRES = 0, 1, 2
-PREC_FP64, PREC_FP32, PREC_FP32_IR = 0, 1, 2
+PREC_FP64, PREC_FP32, PREC_FP32_IR, PREC_BF16 = 0, 1, 2, 3
 PDE_DIFFUSION, PDE_CONVDIFF = 0, 1
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",

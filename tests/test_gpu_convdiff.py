@@ -174,10 +174,11 @@ def test_dirichlet_data_and_fixed_point_iteration():
     _check_solution(wl, host(lam), host(u), host(q), 1e-10, gD=gD)
 
 
-@pytest.mark.parametrize("prec", [hdgmg.PREC_FP32, hdgmg.PREC_FP64])
+@pytest.mark.parametrize("prec", [hdgmg.PREC_FP32, hdgmg.PREC_FP64, hdgmg.PREC_BF16])
 def test_p6_gmres_reaches_fp64_residual(prec):
     """p = 6 (28 x 28 element operators), eps = 1e-3, FGMRES(30) with the
-    step-3 cycle: FP64 residual 1e-10 with the FP32 cycle too."""
+    step-3 cycle: FP64 residual 1e-10 with the FP32 cycle and with the BF16
+    fine-level operator too."""
     wl = workload(32, 6, 1e-3)
     s = solver(wl, coarsest_n=4, m_max=4, local_corr=hdgmg.LC_PRE, precision=prec, rtol=1e-10)
     lam, u, q, info = s.solve(cuda(wl.f[0]))

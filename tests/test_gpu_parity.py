@@ -130,6 +130,30 @@ def test_fp32_vcycle_close_to_oracle(n, p):
     assert rel_l2(e, ref) <= 1e-4
 
 
+def test_bf16_fine_operator():
+    """PREC_BF16: the finest level's V-cycle matvecs read BF16 operators
+    (FP32 accumulation).  One cycle stays within 2e-2 of the FP64 cycle and
+    is measurably less accurate than the FP32 cycle (the BF16 copy is what
+    runs); the FP64 PCG around it still reaches the FP64 residual."""
+    wl = random_kappa_workload(32, 4, 31)
+    s16 = make(wl, coarsest_n=4, m_fine=1, m_max=4, precision=hdgmg.PREC_BF16, rtol=1e-11)
+    s32 = make(wl, coarsest_n=4, m_fine=1, m_max=4, precision=hdgmg.PREC_FP32, rtol=1e-11)
+    H = mg.Hierarchy(oracle_problem(wl), coarsest_n=4, m_fine=1, m_max=4, local_corr="both")
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal((5, hdg.n_edges(32)))
+    ref = H.from_free(H.vcycle(H.to_free(r)))
+    err16 = rel_l2(host(s16.apply_vcycle(cuda(r))), ref)
+    err32 = rel_l2(host(s32.apply_vcycle(cuda(r))), ref)
+    print("V-cycle relative error: bf16 %.3e  fp32 %.3e" % (err16, err32))
+    assert err16 <= 2e-2 and err16 > 10 * err32
+    lam, u, q, i16 = s16.solve(cuda(wl.f[0]))
+    _, _, _, i32 = s32.solve(cuda(wl.f[0]))
+    print("PCG iterations: bf16 %d  fp32 %d" % (i16.iters, i32.iters))
+    assert i16.converged == 1 and i16.rel_res <= 1e-11
+    assert i16.iters <= i32.iters + 3
+    _check_solution(wl, host(lam), host(u), host(q), rtol_res=1e-11, tol_sol=1e-7)
+
+
 # ---------------------------------------------------------- end to end
 def _check_solution(wl, lam, u, q, rtol_res=1e-10, tol_sol=1e-8):
     pr = oracle_problem(wl)
