@@ -59,6 +59,7 @@ struct hdgmg_ctx {
   int p = 0, n = 0, nv = 0, nt = 0;
   RefElement ref;
   RefDevice refd{};
+  CdTables cd{};               // convection-diffusion tables (ns only)
   std::vector<void*> allocs;
   std::vector<Level> levels;
   double* logk = nullptr;
@@ -501,8 +502,7 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   const int64_t len = c->fine_len();
   CUDA_TRY(cudaMemsetAsync(c->b, 0, sizeof(double) * len, s));
   if (c->ns)
-    launch_rhs_cd(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
-                  c->prob.beta_x, c->prob.beta_y, c->Lfac, f, c->b);
+    launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
   else
     launch_rhs(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
                f, c->b);
@@ -794,8 +794,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
   if ((u || q) && c->ns)
-    launch_recover_cd(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
-                      c->prob.beta_x, c->prob.beta_y, c->Lfac, f, lam_out, u, q);
+    launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
   else if (u || q)
     launch_recover(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                    c->Lfac, f, lam_out, u, q);
@@ -972,6 +971,15 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(upload(&c->refd.Cx, c->ref.Cx));
   CTRY(upload(&c->refd.Cy, c->ref.Cy));
   CTRY(upload(&c->refd.Ef, c->ref.Ef));
+  if (c->ns) {
+    std::vector<double> S0, W0, V0, ad;
+    const double tau = P.tau_mode == HDGMG_TAU_OVER_H ? P.tau_c / c->hmin : P.tau_c;
+    build_cd_tables(c->ref, tau, P.beta_x, P.beta_y, S0, W0, V0, ad);
+    CTRY(upload(&c->cd.S0, S0));
+    CTRY(upload(&c->cd.W0, W0));
+    CTRY(upload(&c->cd.V0, V0));
+    CTRY(upload(&c->cd.adiag, ad));
+  }
   // levels
   {
     Level L;
@@ -1112,8 +1120,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   launch_kappa(s, nE, c->logk, c->kap);
   CUDA_TRY(cudaEventRecord(c->evk0, s));
   if (c->ns)
-    launch_condense_cd(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
-                       c->prob.beta_x, c->prob.beta_y, L0.d64.A, c->Lfac, c->err);
+    launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err);
   else
     launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
                     L0.d64.A, c->Lfac, c->err);

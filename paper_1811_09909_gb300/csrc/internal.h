@@ -102,16 +102,25 @@ void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
                     double* u, double* q);
 
 // convection-diffusion element (non-symmetric A_e, full [nt*nt][nE]; LU
-// factors of the volume block, full [nv*nv][nE])
-void launch_condense_cd(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
-                        int tau_mode, double tau_c, double hmin, double bx, double by, double* A,
-                        double* LU, int* err);
-void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                   int tau_mode, double tau_c, double hmin, double bx, double by, const double* LU,
-                   const double* f, double* b);
-void launch_recover_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                       int tau_mode, double tau_c, double hmin, double bx, double by,
-                       const double* LU, const double* f, const double* lam, double* u, double* q);
+// factors of the volume block, full [nv*nv][nE]).  The element-independent
+// tables (tau and beta are the same on every element):
+//   S0 [nv][nv] = -beta_x BxT - beta_y ByT + sum_f tau_f E_f
+//   W0 [nv][nt] = (tau_f - beta.n_f) F,   V0 [nv][nt] = tau_f F
+//   adiag [nt]  = tau_f - beta.n_f        (f = the face of trace dof c)
+// with tau_f = tau + max(beta.n_f, 0), normals 0: -x, 1: +x, 2: -y, 3: +y.
+struct CdTables {
+  double *S0 = nullptr, *W0 = nullptr, *V0 = nullptr, *adiag = nullptr;
+};
+void build_cd_tables(const RefElement& R, double tau, double bx, double by,
+                     std::vector<double>& S0, std::vector<double>& W0, std::vector<double>& V0,
+                     std::vector<double>& adiag);
+void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
+                        const double* kap, double* A, double* LU, int* err);
+void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
+                   const double* kap, const double* LU, const double* f, double* b);
+void launch_recover_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
+                       const double* kap, const double* LU, const double* f, const double* lam,
+                       double* u, double* q);
 
 // adjoint: per-element derivative contraction (K13), adjoint source, misfit
 void launch_grad_contract(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,

@@ -126,49 +126,51 @@ __global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
 //   A_e = eps K + diag(tau_f - beta.n_f) - V^T S^-1 W,  g_e = V^T S^-1 M f
 // S has a positive-definite symmetric part (tau_f - beta.n_f / 2 >= tau > 0),
 // so Gaussian elimination without pivoting never meets a zero pivot.
-__device__ __forceinline__ void face_terms(double tau, double bx, double by, double tf[4],
-                                           double bn[4]) {
-  bn[0] = -bx;
-  bn[1] = bx;
-  bn[2] = -by;
-  bn[3] = by;
-  for (int f = 0; f < 4; ++f) tf[f] = tau + (bn[f] > 0.0 ? bn[f] : 0.0);
+// 1/d for d > 0: FP32 reciprocal as the seed, then two Newton-Raphson steps
+// y <- y (2 - d y) in FP64 (relative error ~1e-7 -> ~1e-14 -> rounding).
+__device__ __forceinline__ double recip_newton(double d) {
+  const float df = (float)d;
+  double y = (df > 1e-30f && df < 1e30f) ? (double)__frcp_rn(df) : 1.0 / d;
+  y = y * (2.0 - d * y);
+  y = y * (2.0 - d * y);
+  return y;
 }
 
-// K1 (non-symmetric): one warp per element; S (LU in place) and W -> X =
-// S^-1 W in shared memory; the LU factors are kept for K5/K12 as
-// [nv*nv][nE] (unit lower part below the diagonal, U on and above it).
+// K1 (non-symmetric): one warp per element.  The element-independent parts
+// (tau is the same on every element of the uniform mesh, beta is constant)
+// come precomputed, so every entry of S, W and V costs one FMA:
+//   S = eps G + S0,  W = eps H + W0,  V = eps H + V0,
+//   A_e = eps K + diag(adiag) - V^T S^-1 W.
+// S is factored in shared memory (LU without pivoting, pivots inverted once
+// by a Newton reciprocal), the forward sweep applied to W on the fly, then
+// back substitution gives X = S^-1 W.  The factors are kept for K5/K12 as
+// [nv*nv][nE]: unit lower part below the diagonal, U above it and the
+// reciprocal pivots 1/u_kk on the diagonal.
 __global__ void condense_cd_kernel(int nv, int nt, int nE, int warps_per_block,
-                                   const double* __restrict__ G, const double* __restrict__ Ef,
-                                   const double* __restrict__ BxT, const double* __restrict__ ByT,
-                                   const double* __restrict__ H, const double* __restrict__ F,
-                                   const double* __restrict__ K, const double* __restrict__ kapv,
-                                   int tau_mode, double tau_c, double hmin, double bx, double by,
-                                   double* __restrict__ A, double* __restrict__ LU,
-                                   int* __restrict__ err) {
+                                   const double* __restrict__ G, const double* __restrict__ H,
+                                   const double* __restrict__ K, const double* __restrict__ S0,
+                                   const double* __restrict__ W0, const double* __restrict__ V0,
+                                   const double* __restrict__ adiag,
+                                   const double* __restrict__ kapv, double* __restrict__ A,
+                                   double* __restrict__ LU, int* __restrict__ err) {
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int e = blockIdx.x * warps_per_block + warp;
   if (e >= nE) return;
-  double* S = smem + (size_t)warp * (nv * nv + nv * nt);
-  double* X = S + nv * nv;
-  const int p1 = nt / 4;
+  const int nvv = nv * nv, nvt = nv * nt;
+  const int ns = nvv > nvt ? nvv : nvt;     // S, later V (n_v x n_t)
+  double* S = smem + (size_t)warp * (ns + nvt + nv);
+  double* X = S + ns;
+  double* dinv = X + nvt;
   const double eps = kapv[e];
-  double tf[4], bn[4];
-  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
-  const int nvv = nv * nv;
-  for (int t = lane; t < nvv; t += 32) {
-    double s = eps * G[t] - bx * BxT[t] - by * ByT[t];
-    for (int f = 0; f < 4; ++f) s += tf[f] * Ef[(size_t)f * nvv + t];
-    S[t] = s;
-  }
-  for (int t = lane; t < nv * nt; t += 32) {
-    const int f = (t % nt) / p1;
-    X[t] = eps * H[t] + (tf[f] - bn[f]) * F[t];
-  }
+  for (int t = lane; t < nvv; t += 32) S[t] = fma(eps, G[t], S0[t]);
+  for (int t = lane; t < nvt; t += 32) X[t] = fma(eps, H[t], W0[t]);
   __syncwarp();
   bool bad = false;
-  // LU without pivoting; the forward sweep is applied to W on the fly
+  // GB300 has one warp per scheduler here (shared memory bounds the
+  // occupancy), so every loop issues its shared-memory loads for four
+  // independent updates before the FMAs and stores: the loads of the next
+  // updates overlap the FP64 pipe instead of waiting behind each store.
   for (int k = 0; k < nv; ++k) {
     double di = 0.0;
     if (lane == 0) {
@@ -177,43 +179,97 @@ __global__ void condense_cd_kernel(int nv, int nt, int nE, int warps_per_block,
         bad = true;
         d = 1.0;
       }
-      di = 1.0 / d;
+      di = recip_newton(d);
+      dinv[k] = di;
     }
     di = __shfl_sync(0xffffffffu, di, 0);
     for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
     __syncwarp();
     const int m = nv - k - 1;
-    for (int t = lane; t < m * m; t += 32) {
-      const int i = k + 1 + t / m, j = k + 1 + t % m;
-      S[i * nv + j] -= S[i * nv + k] * S[k * nv + j];
+    const int mm = m * m;
+    for (int t0 = lane; t0 < mm; t0 += 128) {
+      double a[4], b[4], c[4];
+      int ix[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + 32 * u;
+        ix[u] = -1;
+        if (t < mm) {
+          const int i = k + 1 + t / m, j = k + 1 + t % m;
+          ix[u] = i * nv + j;
+          a[u] = S[i * nv + k];
+          b[u] = S[k * nv + j];
+          c[u] = S[ix[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ix[u] >= 0) S[ix[u]] = fma(-a[u], b[u], c[u]);
     }
-    for (int t = lane; t < m * nt; t += 32) {
-      const int i = k + 1 + t / nt, c = t % nt;
-      X[i * nt + c] -= S[i * nv + k] * X[k * nt + c];
+    const int mt = m * nt;
+    for (int t0 = lane; t0 < mt; t0 += 128) {
+      double a[4], b[4], c[4];
+      int ix[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int t = t0 + 32 * u;
+        ix[u] = -1;
+        if (t < mt) {
+          const int i = k + 1 + t / nt, cc = t % nt;
+          ix[u] = i * nt + cc;
+          a[u] = S[i * nv + k];
+          b[u] = X[k * nt + cc];
+          c[u] = X[ix[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (ix[u] >= 0) X[ix[u]] = fma(-a[u], b[u], c[u]);
     }
     __syncwarp();
   }
-  // back substitution U X = L^-1 W, one column per lane
+  // back substitution U X = L^-1 W, one column per lane, four partial sums
   for (int c = lane; c < nt; c += 32) {
     for (int k = nv - 1; k >= 0; --k) {
-      double s = X[k * nt + c];
-      for (int j = k + 1; j < nv; ++j) s -= S[k * nv + j] * X[j * nt + c];
-      X[k * nt + c] = s / S[k * nv + k];
+      double s0 = X[k * nt + c], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = k + 1;
+      for (; j + 3 < nv; j += 4) {
+        s0 = fma(-S[k * nv + j], X[j * nt + c], s0);
+        s1 = fma(-S[k * nv + j + 1], X[(j + 1) * nt + c], s1);
+        s2 = fma(-S[k * nv + j + 2], X[(j + 2) * nt + c], s2);
+        s3 = fma(-S[k * nv + j + 3], X[(j + 3) * nt + c], s3);
+      }
+      for (; j < nv; ++j) s0 = fma(-S[k * nv + j], X[j * nt + c], s0);
+      X[k * nt + c] = ((s0 + s1) + (s2 + s3)) * dinv[k];
     }
   }
   __syncwarp();
   if (bad) atomicOr(err, 1);
+  // the factors go out first; S's space then holds V = eps H + V0
+  if (LU)
+    for (int t = lane; t < nvv; t += 32) {
+      const int r = t / nv, c = t - r * nv;
+      LU[(size_t)t * nE + e] = (r == c) ? dinv[r] : S[t];
+    }
+  __syncwarp();
+  double* V = S;
+  for (int t = lane; t < nvt; t += 32) V[t] = fma(eps, H[t], V0[t]);
+  __syncwarp();
   for (int t = lane; t < nt * nt; t += 32) {
     const int r = t / nt, c = t % nt;
-    const int fr = r / p1;
-    double s = 0.0;
-    for (int a = 0; a < nv; ++a) s += (eps * H[a * nt + r] + tf[fr] * F[a * nt + r]) * X[a * nt + c];
-    double v = eps * K[t] - s;
-    if (r == c) v += tf[fr] - bn[fr];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int a = 0;
+    for (; a + 3 < nv; a += 4) {
+      s0 = fma(V[a * nt + r], X[a * nt + c], s0);
+      s1 = fma(V[(a + 1) * nt + r], X[(a + 1) * nt + c], s1);
+      s2 = fma(V[(a + 2) * nt + r], X[(a + 2) * nt + c], s2);
+      s3 = fma(V[(a + 3) * nt + r], X[(a + 3) * nt + c], s3);
+    }
+    for (; a < nv; ++a) s0 = fma(V[a * nt + r], X[a * nt + c], s0);
+    double v = fma(eps, K[t], -((s0 + s1) + (s2 + s3)));
+    if (r == c) v += adiag[r];
     A[(size_t)t * nE + e] = v;
   }
-  if (LU)
-    for (int t = lane; t < nvv; t += 32) LU[(size_t)t * nE + e] = S[t];
 }
 
 // kappa_e = exp(log kappa_e), once per element for all element kernels
@@ -347,15 +403,14 @@ __device__ __forceinline__ void lu_solve(const double* __restrict__ LU, int nv, 
   for (int i = nv - 1; i >= 0; --i) {
     double s = TV(y, i);
     for (int j = i + 1; j < nv; ++j) s -= LU[(size_t)(i * nv + j) * nE + e] * TV(y, j);
-    TV(y, i) = s / LU[(size_t)(i * nv + i) * nE + e];
+    TV(y, i) = s * LU[(size_t)(i * nv + i) * nE + e];      // reciprocal pivot
   }
 }
 
 // K5 (convection-diffusion): g_e = V^T S^-1 M f_e
 __global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
-                              const double* __restrict__ H, const double* __restrict__ F,
-                              const double* __restrict__ kapv, int tau_mode, double tau_c,
-                              double hmin, double bx, double by, const double* __restrict__ LU,
+                              const double* __restrict__ H, const double* __restrict__ V0,
+                              const double* __restrict__ kapv, const double* __restrict__ LU,
                               const double* __restrict__ f, double* __restrict__ b) {
   extern __shared__ double smem[];
   const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
@@ -364,8 +419,6 @@ __global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
   if (e >= nE) return;
   double* y = smem;
   const double eps = kapv[e];
-  double tf[4], bn[4];
-  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
   for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
   lu_solve(LU, nv, nE, e, y);
   int ed[4];
@@ -374,20 +427,18 @@ __global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
   for (int c = 0; c < nt; ++c) {
     const int edge = ed[c / p1];
     if (is_boundary_edge(n, edge)) continue;
-    const double t = tf[c / p1];
     double g = 0.0;
-    for (int a = 0; a < nv; ++a) g += (eps * H[a * nt + c] + t * F[a * nt + c]) * TV(y, a);
+    for (int a = 0; a < nv; ++a) g += fma(eps, H[a * nt + c], V0[a * nt + c]) * TV(y, a);
     atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
   }
 }
 
 // K12 (convection-diffusion): u = S^-1 (M f + W lambda), q = eps M^-1 (B^T u - C lambda)
 __global__ void recover_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
-                                  const double* __restrict__ H, const double* __restrict__ F,
+                                  const double* __restrict__ H, const double* __restrict__ W0,
                                   const double* __restrict__ BxT, const double* __restrict__ ByT,
                                   const double* __restrict__ Cx, const double* __restrict__ Cy,
-                                  const double* __restrict__ kapv, int tau_mode, double tau_c,
-                                  double hmin, double bx, double by,
+                                  const double* __restrict__ kapv,
                                   const double* __restrict__ LU, const double* __restrict__ f,
                                   const double* __restrict__ lam, double* __restrict__ u,
                                   double* __restrict__ q) {
@@ -399,16 +450,13 @@ __global__ void recover_cd_kernel(int p, int n, const double* __restrict__ Mdiag
   double* y = smem;
   double* le = smem + (size_t)nv * blockDim.x;
   const double eps = kapv[e];
-  double tf[4], bn[4];
-  face_terms(tau_of(tau_mode, tau_c, hmin), bx, by, tf, bn);
   int ed[4];
   element_edges(n, e, ed);
   const int nedge = 2 * n * (n + 1);
   for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
   for (int a = 0; a < nv; ++a) {
     double s = Mdiag[a] * f[(size_t)a * nE + e];
-    for (int c = 0; c < nt; ++c)
-      s += (eps * H[a * nt + c] + (tf[c / p1] - bn[c / p1]) * F[a * nt + c]) * TV(le, c);
+    for (int c = 0; c < nt; ++c) s += fma(eps, H[a * nt + c], W0[a * nt + c]) * TV(le, c);
     TV(y, a) = s;
   }
   lu_solve(LU, nv, nE, e, y);
@@ -550,11 +598,11 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
                                                  kap, tau_mode, tau_c, hmin, A, Lfac, err);
 }
 
-void launch_condense_cd(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
-                        int tau_mode, double tau_c, double hmin, double bx, double by, double* A,
-                        double* LU, int* err) {
+void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
+                        const double* kap, double* A, double* LU, int* err) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t per_warp = sizeof(double) * (size_t)(nv * nv + nv * nt);
+  const size_t per_warp =
+      sizeof(double) * (size_t)((nv * nv > nv * nt ? nv * nv : nv * nt) + nv * nt + nv);
   int wpb = (int)((200 * 1024) / per_warp);
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
@@ -566,14 +614,12 @@ void launch_condense_cd(cudaStream_t s, const RefDevice& ref, int p, int nE, con
   (void)attr_set;
   const int blocks = (nE + wpb - 1) / wpb;
   note_launch();
-  condense_cd_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.Ef, ref.BxT, ref.ByT,
-                                                    ref.H, ref.F, ref.K, kap, tau_mode, tau_c, hmin,
-                                                    bx, by, A, LU, err);
+  condense_cd_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.H, ref.K, cd.S0, cd.W0,
+                                                    cd.V0, cd.adiag, kap, A, LU, err);
 }
 
-void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                   int tau_mode, double tau_c, double hmin, double bx, double by, const double* LU,
-                   const double* f, double* b) {
+void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
+                   const double* kap, const double* LU, const double* f, double* b) {
   const int nE = n * n, nv = (p + 1) * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)nv * threads;
@@ -583,13 +629,12 @@ void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const dou
   }();
   (void)attr;
   note_launch();
-  rhs_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau_mode, tau_c, hmin,
-                                             bx, by, LU, f, b);
+  rhs_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, cd.V0, kap, LU, f, b);
 }
 
-void launch_recover_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                       int tau_mode, double tau_c, double hmin, double bx, double by,
-                       const double* LU, const double* f, const double* lam, double* u, double* q) {
+void launch_recover_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
+                       const double* kap, const double* LU, const double* f, const double* lam,
+                       double* u, double* q) {
   const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
   const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
@@ -599,9 +644,8 @@ void launch_recover_cd(cudaStream_t s, const RefDevice& ref, int p, int n, const
   }();
   (void)attr;
   note_launch();
-  recover_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
-                                                 ref.Cy, kap, tau_mode, tau_c, hmin, bx, by, LU, f,
-                                                 lam, u, q);
+  recover_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, cd.W0, ref.BxT, ref.ByT, ref.Cx,
+                                                 ref.Cy, kap, LU, f, lam, u, q);
 }
 
 void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,

@@ -192,4 +192,29 @@ RefElement build_ref_element(int p, double hx, double hy) {
   return R;
 }
 
+void build_cd_tables(const RefElement& R, double tau, double bx, double by,
+                     std::vector<double>& S0, std::vector<double>& W0, std::vector<double>& V0,
+                     std::vector<double>& adiag) {
+  const int nv = R.nv, nt = R.nt, p1 = R.p + 1;
+  const double bn[4] = {-bx, bx, -by, by};
+  double tf[4];
+  for (int f = 0; f < 4; ++f) tf[f] = tau + (bn[f] > 0.0 ? bn[f] : 0.0);
+  S0.assign((size_t)nv * nv, 0.0);
+  for (int t = 0; t < nv * nv; ++t) {
+    double s = -bx * R.BxT[t] - by * R.ByT[t];
+    for (int f = 0; f < 4; ++f) s += tf[f] * R.Ef[(size_t)f * nv * nv + t];
+    S0[t] = s;
+  }
+  W0.assign((size_t)nv * nt, 0.0);
+  V0.assign((size_t)nv * nt, 0.0);
+  for (int a = 0; a < nv; ++a)
+    for (int c = 0; c < nt; ++c) {
+      const int f = c / p1;
+      W0[(size_t)a * nt + c] = (tf[f] - bn[f]) * R.F[(size_t)a * nt + c];
+      V0[(size_t)a * nt + c] = tf[f] * R.F[(size_t)a * nt + c];
+    }
+  adiag.assign(nt, 0.0);
+  for (int c = 0; c < nt; ++c) adiag[c] = tf[c / p1] - bn[c / p1];
+}
+
 }  // namespace hdgmg
