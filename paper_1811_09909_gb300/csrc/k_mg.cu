@@ -345,52 +345,51 @@ __global__ void __launch_bounds__(32 * WPB) agglomerate_ns_warp_kernel(
 }
 
 // ------------------------------------------------- K8 local correction
-// e_I <- e_I + A_II^-1 (r - A e)_I = A_II^-1 r_I + Y e_B
+// e_I <- e_I + A_II^-1 (r - A e)_I = A_II^-1 r_I + Y e_B, one work item per
+// (macro-element C, interior dof a): t = a * nC + C, so that a warp reads one
+// row entry of 32 consecutive macro-elements' blocks.  The items of one C
+// write distinct interior entries and read only perimeter entries of e.
 template <typename T>
 __device__ __forceinline__ void local_correction_item(int nc, bool ns, const T* __restrict__ AIIinv,
                                                       const T* __restrict__ Y, const T* r, T* e,
-                                                      int C) {
+                                                      int t) {
   const int nC = nc * nc;
+  const int a = t / nC, C = t - a * nC;
   const int J = C / nc, I = C - J * nc;
   const int n = 2 * nc;
   const int nedge = 2 * n * (n + 1);
-  T rI[8], eB[16];
+  T s = T(0);
 #pragma unroll
   for (int ie = 0; ie < 4; ++ie) {
     const int ed = interior_edge(n, I, J, ie);
-    rI[ie * 2] = r[ed];
-    rI[ie * 2 + 1] = r[(size_t)nedge + ed];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int kk = ie * 2 + k;
+      s += AIIinv[(size_t)(ns ? a * 8 + kk : pk_any(a, kk)) * nC + C] * r[(size_t)k * nedge + ed];
+    }
   }
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     const int ed = perimeter_edge(n, I, J, b >> 1, b & 1);
-    eB[b * 2] = e[ed];
-    eB[b * 2 + 1] = e[(size_t)nedge + ed];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) s += Y[(size_t)(a * 16 + b * 2 + k) * nC + C] * e[(size_t)k * nedge + ed];
   }
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) s += AIIinv[(size_t)(ns ? a * 8 + k : pk_any(a, k)) * nC + C] * rI[k];
-#pragma unroll
-    for (int b = 0; b < 16; ++b) s += Y[(size_t)(a * 16 + b) * nC + C] * eB[b];
-    const int ed = interior_edge(n, I, J, a >> 1);
-    e[(size_t)(a & 1) * nedge + ed] = s;
-  }
+  e[(size_t)(a & 1) * nedge + interior_edge(n, I, J, a >> 1)] = s;
 }
 
 template <typename T>
 __global__ void local_correction_kernel(int nc, bool ns, const T* __restrict__ AIIinv,
                                         const T* __restrict__ Y, const T* __restrict__ r,
                                         T* __restrict__ e) {
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C < nc * nc) local_correction_item<T>(nc, ns, AIIinv, Y, r, e, C);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 8 * nc * nc) local_correction_item<T>(nc, ns, AIIinv, Y, r, e, t);
 }
 
 
 // --------------------------------------------------------- K9 restriction
-// r_c = J^T s_B + Pi^T s_I (Q_{k-1} of eq. n_1_Qk with Pi^T = -J^T A_BI A_II^-1
-// for symmetric A), s = r - y, y = A e.  One thread per coarse edge.
+// r_c = J^T s_B + Rt^T s_I (Q_{k-1} of eq. n_1_Qk: Rt^T = -J^T A_BI A_II^-1,
+// which is Pi^T for symmetric A), s = r - y, y = A e.  One thread per coarse
+// edge; the block argument (named Pi) is Rt.
 template <typename T>
 __device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi, const T* r,
                                                 const T* y, T* rc, int E) {
@@ -856,7 +855,7 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
       __syncthreads();
     }
     if (P.lc != HDGMG_LC_NONE) {
-      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
     for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
@@ -888,7 +887,7 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
     __syncthreads();
     if (P.lc == HDGMG_LC_BOTH) {
-      for (int i = tid; i < nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
     for (int it = 0; it < L.m; ++it) {
@@ -1237,7 +1236,7 @@ template <typename T>
 void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
                              const T* r, T* e) {
   note_launch();
-  local_correction_kernel<T><<<nblk(nc * nc, 128), 128, 0, s>>>(nc, ns, AIIinv, Y, r, e);
+  local_correction_kernel<T><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(nc, ns, AIIinv, Y, r, e);
 }
 
 template <typename T>
