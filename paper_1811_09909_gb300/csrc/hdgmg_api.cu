@@ -380,8 +380,35 @@ void vcycle(hdgmg_ctx* c, int l) {
   }
   const T omega = (T)c->opts.omega;
   const int lc = c->opts.local_corr;
-  // step 2: pre-smoothing (the first sweep starts from e = 0)
   const bool ns = c->ns;
+  if (L.nd == 2 && L.transfer == 2 && !L.A16) {
+    // P1 level: fused edge-centric sweeps, ping-ponging between e and y.  The
+    // first sweep (from e = 0) writes y; after the 2m - 1 sweeps of the level
+    // the correction is back in e.
+    Level& Lc = c->levels[l + 1];
+    LevelData<T>& Dc = ld<T>(Lc);
+    T* bufs[2] = {D.e, D.y};
+    int cur = 1;
+    launch_bj_update<T>(s, L.n, 2, ns, D.Dinv, D.r, bufs[0], bufs[1], omega, 1);
+    for (int i = 1; i < L.m; ++i) {
+      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true);
+      cur ^= 1;
+    }
+    if (lc != HDGMG_LC_NONE)
+      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur]);
+    launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, false);
+    launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, bufs[1 - cur], Dc.r);
+    vcycle<T>(c, l + 1);
+    launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, bufs[cur], bufs[1 - cur]);
+    if (lc == HDGMG_LC_BOTH)
+      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur]);
+    for (int i = 0; i < L.m; ++i) {
+      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true);
+      cur ^= 1;
+    }
+    return;                                    // cur == 0: the correction is in D.e
+  }
+  // step 2: pre-smoothing (the first sweep starts from e = 0)
   launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
   for (int i = 1; i < L.m; ++i) {
     level_matvec<T>(c, l, D.e, D.y);

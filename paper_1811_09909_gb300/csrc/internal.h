@@ -166,6 +166,11 @@ void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, c
                              const T* r, T* e);
 template <typename T>
 void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc);
+// P1 level, one thread per edge gathering both elements' rows (no atomics):
+// sweep: out = x + omega D^-1 (r - A x); else out = A x.  x != out.
+template <typename T>
+void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, const T* r, const T* x,
+                    T* out, T omega, bool sweep);
 template <typename T>
 void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y);
 template <typename T>

@@ -792,6 +792,79 @@ __device__ __forceinline__ void bj_p1_item(int n, bool ns, const T* __restrict__
   }
 }
 
+// Edge-centric P1 operator on interior edge E, from its two elements:
+// acc = (A x)_E (no atomics: the edge gathers both elements' rows).
+//   SWEEP: out_E = x_E + omega D_E^-1 (r_E - acc)   (one block-Jacobi sweep,
+//          x and out distinct buffers: Jacobi reads only old values)
+//   else:  out_E = acc
+// Boundary (Dirichlet) edges get out = 0.
+template <typename T, bool SWEEP>
+__device__ __forceinline__ void edge_p1_item(int n, bool ns, const T* __restrict__ A,
+                                             const T* __restrict__ Dinv, const T* r, const T* x,
+                                             T* out, T omega, int E) {
+  const int nedge = 2 * n * (n + 1);
+  if (bnd_edge(n, E)) {
+    out[E] = T(0);
+    out[nedge + E] = T(0);
+    return;
+  }
+  const int nE = n * n, nvert = n * (n + 1);
+  int el[2], le[2];
+  if (E < nvert) {
+    const int j = E / (n + 1), i = E - j * (n + 1);
+    el[0] = j * n + i - 1; le[0] = 1;
+    el[1] = j * n + i;     le[1] = 0;
+  } else {
+    const int j = (E - nvert) / n, i = (E - nvert) - j * n;
+    el[0] = (j - 1) * n + i; le[0] = 3;
+    el[1] = j * n + i;       le[1] = 2;
+  }
+  T s[2][2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int K = el[side], r0 = le[side] * 2;
+    int ed[4];
+    elem_edges(n, K, ed);
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const T xc = x[(size_t)(c & 1) * nedge + ed[c >> 1]];
+      const T a0 = A[(size_t)(ns ? r0 * 8 + c : pk_any(r0, c)) * nE + K];
+      const T a1 = A[(size_t)(ns ? (r0 + 1) * 8 + c : pk_any(r0 + 1, c)) * nE + K];
+      s0 += a0 * xc;
+      s1 += a1 * xc;
+    }
+    s[side][0] = s0;
+    s[side][1] = s1;
+  }
+  const T acc0 = s[0][0] + s[1][0], acc1 = s[0][1] + s[1][1];
+  if (SWEEP) {
+    const T d0 = r[E] - acc0, d1 = r[nedge + E] - acc1;
+    const T a00 = Dinv[E], a01 = Dinv[(size_t)nedge + E], a10 = Dinv[(size_t)2 * nedge + E];
+    T u0, u1;
+    if (ns) {          // full [d00, d01, d10, d11]
+      u0 = a00 * d0 + a01 * d1;
+      u1 = a10 * d0 + Dinv[(size_t)3 * nedge + E] * d1;
+    } else {           // packed [d00, d10, d11]
+      u0 = a00 * d0 + a01 * d1;
+      u1 = a01 * d0 + a10 * d1;
+    }
+    out[E] = x[E] + omega * u0;
+    out[nedge + E] = x[nedge + E] + omega * u1;
+  } else {
+    out[E] = acc0;
+    out[nedge + E] = acc1;
+  }
+}
+
+template <typename T, bool SWEEP>
+__global__ void edge_p1_kernel(int n, bool ns, const T* __restrict__ A, const T* __restrict__ Dinv,
+                               const T* __restrict__ r, const T* __restrict__ x,
+                               T* __restrict__ out, T omega) {
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E < 2 * n * (n + 1)) edge_p1_item<T, SWEEP>(n, ns, A, Dinv, r, x, out, omega, E);
+}
+
 template <typename T>
 __device__ __forceinline__ void stage_copy(T* dst, const T* __restrict__ src, int count) {
   for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = src[i];
@@ -833,35 +906,39 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     for (int i = tid; i < 2 * P.lv[0].nEdge; i += nth) r0[i] = P.r_in[i];
   }
   __syncthreads();
-  // down sweep: steps 2-4 of Algorithm 1
+  // down sweep: steps 2-4 of Algorithm 1.  Smoothing ping-pongs between the
+  // level's e and y regions with one fused edge sweep (one barrier) per
+  // Jacobi step; the first sweep (e = 0) writes y so that after the 2m - 1
+  // sweeps of the level the correction ends in e.
   for (int l = 0; l + 1 < P.nlev; ++l) {
     const TailLevel<T>& L = P.lv[l];
-    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
+    const int n = L.n, ned = L.nEdge, nc = n / 2;
     T* r = sm + L.voff;
-    T* e = r + 2 * ned;
-    T* y = e + 2 * ned;
+    T* bufs[2] = {r + 2 * ned, r + 4 * ned};
     const T* A = L.staged ? sm + L.a_off : L.A;
     const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
     const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
     const T* Yb = L.staged ? sm + L.y_off : L.Y;
     const T* Rt = P.ns ? (L.staged ? sm + L.rt_off : L.Rt) : (L.staged ? sm + L.pi_off : L.Pi);
     const bool ns = P.ns != 0;
-    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, true, i);
+    int cur = 1;
+    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, nullptr, bufs[cur], P.omega, true, i);
     __syncthreads();
     for (int it = 1; it < L.m; ++it) {
-      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
-      __syncthreads();
-      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
+      for (int i = tid; i < ned; i += nth)
+        edge_p1_item<T, true>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
+      cur ^= 1;
       __syncthreads();
     }
     if (P.lc != HDGMG_LC_NONE) {
-      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, bufs[cur], i);
       __syncthreads();
     }
-    for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
+    for (int i = tid; i < ned; i += nth)
+      edge_p1_item<T, false>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
     __syncthreads();
     T* rc = sm + P.lv[l + 1].voff;
-    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, y, rc, i);
+    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, bufs[1 - cur], rc, i);
     __syncthreads();
   }
   {  // B_1 = A_1^-1
@@ -870,13 +947,13 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     coarse_apply_block<T>(L.n, P.fidx, P.fedge, P.nf, ainv, r, r + 2 * L.nEdge, w);
     __syncthreads();
   }
-  // up sweep: steps 4-6
+  // up sweep: steps 4-6 (the level's current correction is in y after the
+  // down sweep's 2m - 1 ... m - 1 flips: it left cur = 1 - (m - 1) % 2)
   for (int l = P.nlev - 2; l >= 0; --l) {
     const TailLevel<T>& L = P.lv[l];
-    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
+    const int n = L.n, ned = L.nEdge, nc = n / 2;
     T* r = sm + L.voff;
-    T* e = r + 2 * ned;
-    T* y = e + 2 * ned;
+    T* bufs[2] = {r + 2 * ned, r + 4 * ned};
     const T* A = L.staged ? sm + L.a_off : L.A;
     const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
     const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
@@ -884,16 +961,18 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
     const T* ec = sm + P.lv[l + 1].voff + 2 * P.lv[l + 1].nEdge;
     const bool ns = P.ns != 0;
-    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
+    int cur = (L.m - 1) % 2 == 0 ? 1 : 0;
+    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth)
+      prolong_h_item<T>(nc, Pi, ec, bufs[cur], bufs[1 - cur], i);
     __syncthreads();
     if (P.lc == HDGMG_LC_BOTH) {
-      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, bufs[cur], i);
       __syncthreads();
     }
     for (int it = 0; it < L.m; ++it) {
-      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
-      __syncthreads();
-      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
+      for (int i = tid; i < ned; i += nth)
+        edge_p1_item<T, true>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
+      cur ^= 1;
       __syncthreads();
     }
   }
@@ -1240,6 +1319,17 @@ void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, c
 }
 
 template <typename T>
+void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, const T* r, const T* x,
+                    T* out, T omega, bool sweep) {
+  const int ne = 2 * n * (n + 1);
+  note_launch();
+  if (sweep)
+    edge_p1_kernel<T, true><<<nblk(ne, 128), 128, 0, s>>>(n, ns, A, Dinv, r, x, out, omega);
+  else
+    edge_p1_kernel<T, false><<<nblk(ne, 128), 128, 0, s>>>(n, ns, A, Dinv, r, x, out, omega);
+}
+
+template <typename T>
 void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc) {
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
@@ -1449,6 +1539,8 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
   template void launch_local_correction<T>(cudaStream_t, int, bool, const T*, const T*,         \
                                            const T*, T*);                                       \
   template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);            \
+  template void launch_edge_p1<T>(cudaStream_t, int, bool, const T*, const T*, const T*,       \
+                                  const T*, T*, T, bool);                                       \
   template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);             \
   template void launch_restrict_p<T>(cudaStream_t, int, int, const T*, T*, T*);                 \
   template void launch_prolong_p<T>(cudaStream_t, int, int, const T*, T*);                      \
