@@ -906,39 +906,35 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     for (int i = tid; i < 2 * P.lv[0].nEdge; i += nth) r0[i] = P.r_in[i];
   }
   __syncthreads();
-  // down sweep: steps 2-4 of Algorithm 1.  Smoothing ping-pongs between the
-  // level's e and y regions with one fused edge sweep (one barrier) per
-  // Jacobi step; the first sweep (e = 0) writes y so that after the 2m - 1
-  // sweeps of the level the correction ends in e.
+  // down sweep: steps 2-4 of Algorithm 1
   for (int l = 0; l + 1 < P.nlev; ++l) {
     const TailLevel<T>& L = P.lv[l];
-    const int n = L.n, ned = L.nEdge, nc = n / 2;
+    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
     T* r = sm + L.voff;
-    T* bufs[2] = {r + 2 * ned, r + 4 * ned};
+    T* e = r + 2 * ned;
+    T* y = e + 2 * ned;
     const T* A = L.staged ? sm + L.a_off : L.A;
     const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
     const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
     const T* Yb = L.staged ? sm + L.y_off : L.Y;
     const T* Rt = P.ns ? (L.staged ? sm + L.rt_off : L.Rt) : (L.staged ? sm + L.pi_off : L.Pi);
     const bool ns = P.ns != 0;
-    int cur = 1;
-    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, nullptr, bufs[cur], P.omega, true, i);
+    for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, true, i);
     __syncthreads();
     for (int it = 1; it < L.m; ++it) {
-      for (int i = tid; i < ned; i += nth)
-        edge_p1_item<T, true>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
-      cur ^= 1;
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
+      __syncthreads();
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
       __syncthreads();
     }
     if (P.lc != HDGMG_LC_NONE) {
-      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, bufs[cur], i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
-    for (int i = tid; i < ned; i += nth)
-      edge_p1_item<T, false>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
+    for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
     __syncthreads();
     T* rc = sm + P.lv[l + 1].voff;
-    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, bufs[1 - cur], rc, i);
+    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, y, rc, i);
     __syncthreads();
   }
   {  // B_1 = A_1^-1
@@ -947,13 +943,13 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     coarse_apply_block<T>(L.n, P.fidx, P.fedge, P.nf, ainv, r, r + 2 * L.nEdge, w);
     __syncthreads();
   }
-  // up sweep: steps 4-6 (the level's current correction is in y after the
-  // down sweep's 2m - 1 ... m - 1 flips: it left cur = 1 - (m - 1) % 2)
+  // up sweep: steps 4-6
   for (int l = P.nlev - 2; l >= 0; --l) {
     const TailLevel<T>& L = P.lv[l];
-    const int n = L.n, ned = L.nEdge, nc = n / 2;
+    const int n = L.n, nE = n * n, ned = L.nEdge, nc = n / 2;
     T* r = sm + L.voff;
-    T* bufs[2] = {r + 2 * ned, r + 4 * ned};
+    T* e = r + 2 * ned;
+    T* y = e + 2 * ned;
     const T* A = L.staged ? sm + L.a_off : L.A;
     const T* Dinv = L.staged ? sm + L.dinv_off : L.Dinv;
     const T* AIIinv = L.staged ? sm + L.aii_off : L.AIIinv;
@@ -961,18 +957,16 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
     const T* ec = sm + P.lv[l + 1].voff + 2 * P.lv[l + 1].nEdge;
     const bool ns = P.ns != 0;
-    int cur = (L.m - 1) % 2 == 0 ? 1 : 0;
-    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth)
-      prolong_h_item<T>(nc, Pi, ec, bufs[cur], bufs[1 - cur], i);
+    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
     __syncthreads();
     if (P.lc == HDGMG_LC_BOTH) {
-      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, bufs[cur], i);
+      for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
       __syncthreads();
     }
     for (int it = 0; it < L.m; ++it) {
-      for (int i = tid; i < ned; i += nth)
-        edge_p1_item<T, true>(n, ns, A, Dinv, r, bufs[cur], bufs[1 - cur], P.omega, i);
-      cur ^= 1;
+      for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
+      __syncthreads();
+      for (int i = tid; i < ned; i += nth) bj_p1_item<T>(n, ns, Dinv, r, y, e, P.omega, false, i);
       __syncthreads();
     }
   }
