@@ -388,15 +388,16 @@ __global__ void local_correction_kernel(int nc, bool ns, const T* __restrict__ A
 
 // --------------------------------------------------------- K9 restriction
 // r_c = J^T s_B + Rt^T s_I (Q_{k-1} of eq. n_1_Qk: Rt^T = -J^T A_BI A_II^-1,
-// which is Pi^T for symmetric A), s = r - y, y = A e.  One thread per coarse
-// edge; the block argument (named Pi) is Rt.
+// which is Pi^T for symmetric A), s = r - y, y = A e.  One work item per
+// (coarse edge E, coarse mode kc): t = kc * nedc + E.  The block argument
+// (named Pi) is Rt.
 template <typename T>
 __device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi, const T* r,
-                                                const T* y, T* rc, int E) {
+                                                const T* y, T* rc, int t) {
   const int nedc = 2 * nc * (nc + 1);
+  const int kc = t >= nedc ? 1 : 0, E = t - kc * nedc;
   if (bnd_edge(nc, E)) {
-    rc[E] = T(0);
-    rc[(size_t)nedc + E] = T(0);
+    rc[t] = T(0);
     return;
   }
   const int n = 2 * nc, nedge = 2 * n * (n + 1), nC = nc * nc;
@@ -415,14 +416,12 @@ __device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi
     Cs[0] = (J - 1) * nc + I; mes[0] = 3;  // macro-element below, its top edge
     Cs[1] = J * nc + I;       mes[1] = 2;
   }
-  T acc[2] = {T(0), T(0)};
+  T acc = T(0);
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const T s0 = r[ch[c]] - y[ch[c]];
     const T s1 = r[(size_t)nedge + ch[c]] - y[(size_t)nedge + ch[c]];
-#pragma unroll
-    for (int kc = 0; kc < 2; ++kc)
-      acc[kc] += (T)c_Jc[c][0][kc] * s0 + (T)c_Jc[c][1][kc] * s1;
+    acc += (T)c_Jc[c][0][kc] * s0 + (T)c_Jc[c][1][kc] * s1;
   }
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -434,73 +433,63 @@ __device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const T s = r[(size_t)k * nedge + ed] - y[(size_t)k * nedge + ed];
-        const int a = ie * 2 + k;
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc) acc[kc] += Pi[(size_t)(a * 8 + mes[side] * 2 + kc) * nC + C] * s;
+        acc += Pi[(size_t)((ie * 2 + k) * 8 + mes[side] * 2 + kc) * nC + C] * s;
       }
     }
   }
-  rc[E] = acc[0];
-  rc[(size_t)nedc + E] = acc[1];
+  rc[t] = acc;
 }
 
 template <typename T>
 __global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ r,
                                   const T* __restrict__ y, T* __restrict__ rc) {
-  const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E < 2 * nc * (nc + 1)) restrict_h_item<T>(nc, Pi, r, y, rc, E);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 4 * nc * (nc + 1)) restrict_h_item<T>(nc, Pi, r, y, rc, t);
 }
 
 // -------------------------------------------------------- K11 prolongation
-// e_B += J e_c (per coarse edge, its two halves), e_I += Pi e_c(C) (per
-// macro-element); every fine edge is touched exactly once, where y is reset.
+// e_I += Pi e_c(C): one item per (macro-element C, interior dof a),
+// t = a * nC + C; e_B += J e_c: one item per (coarse edge E, half c),
+// t = 8 nC + c * nedc + E.  Every fine edge is touched exactly once, where y
+// is reset.
 template <typename T>
 __device__ __forceinline__ void prolong_h_item(int nc, const T* __restrict__ Pi, const T* ec,
                                                T* e, T* y, int t) {
   const int nC = nc * nc, nedc = 2 * nc * (nc + 1), nvc = nc * (nc + 1);
   const int n = 2 * nc, nedge = 2 * n * (n + 1);
-  if (t < nC) {
-    const int C = t, J = C / nc, I = C - J * nc;
+  if (t < 8 * nC) {
+    const int a = t / nC, C = t - a * nC;
+    const int J = C / nc, I = C - J * nc;
     const int ce[4] = {coarse_v(nc, I, J), coarse_v(nc, I + 1, J), coarse_h(nc, I, J),
                        coarse_h(nc, I, J + 1)};
-    T xc[8];
+    T s = T(0);
 #pragma unroll
     for (int me = 0; me < 4; ++me) {
-      xc[me * 2] = ec[ce[me]];
-      xc[me * 2 + 1] = ec[(size_t)nedc + ce[me]];
+      s += Pi[(size_t)(a * 8 + me * 2) * nC + C] * ec[ce[me]];
+      s += Pi[(size_t)(a * 8 + me * 2 + 1) * nC + C] * ec[(size_t)nedc + ce[me]];
     }
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      T s = T(0);
-#pragma unroll
-      for (int b = 0; b < 8; ++b) s += Pi[(size_t)(a * 8 + b) * nC + C] * xc[b];
-      const size_t ix = (size_t)(a & 1) * nedge + interior_edge(n, I, J, a >> 1);
-      e[ix] += s;
-      y[ix] = T(0);
-    }
+    const size_t ix = (size_t)(a & 1) * nedge + interior_edge(n, I, J, a >> 1);
+    e[ix] += s;
+    y[ix] = T(0);
     return;
   }
-  const int E = t - nC;
-  if (E >= nedc) return;
-  int ch[2];
+  const int u = t - 8 * nC;
+  if (u >= 2 * nedc) return;
+  const int c = u >= nedc ? 1 : 0, E = u - c * nedc;
+  int ch;
   if (E < nvc) {
     const int J = E / (nc + 1), I = E % (nc + 1);
-    ch[0] = fine_v(n, 2 * I, 2 * J);
-    ch[1] = fine_v(n, 2 * I, 2 * J + 1);
+    ch = fine_v(n, 2 * I, 2 * J + c);
   } else {
     const int J = (E - nvc) / nc, I = (E - nvc) % nc;
-    ch[0] = fine_h(n, 2 * I, 2 * J);
-    ch[1] = fine_h(n, 2 * I + 1, 2 * J);
+    ch = fine_h(n, 2 * I + c, 2 * J);
   }
   const T x0 = ec[E], x1 = ec[(size_t)nedc + E];
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-#pragma unroll
-    for (int kf = 0; kf < 2; ++kf) {
-      const size_t ix = (size_t)kf * nedge + ch[c];
-      e[ix] += (T)c_Jc[c][kf][0] * x0 + (T)c_Jc[c][kf][1] * x1;
-      y[ix] = T(0);
-    }
+  for (int kf = 0; kf < 2; ++kf) {
+    const size_t ix = (size_t)kf * nedge + ch;
+    e[ix] += (T)c_Jc[c][kf][0] * x0 + (T)c_Jc[c][kf][1] * x1;
+    y[ix] = T(0);
   }
 }
 
@@ -508,7 +497,7 @@ template <typename T>
 __global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ ec,
                                  T* __restrict__ e, T* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < nc * nc + 2 * nc * (nc + 1)) prolong_h_item<T>(nc, Pi, ec, e, y, t);
+  if (t < 8 * nc * nc + 4 * nc * (nc + 1)) prolong_h_item<T>(nc, Pi, ec, e, y, t);
 }
 
 // ------------------------------------------------- p-transfer (J_N, J_N^T)
@@ -934,7 +923,7 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     for (int i = tid; i < nE; i += nth) matvec_p1_item<T>(n, ns, A, e, y, i);
     __syncthreads();
     T* rc = sm + P.lv[l + 1].voff;
-    for (int i = tid; i < P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, y, rc, i);
+    for (int i = tid; i < 2 * P.lv[l + 1].nEdge; i += nth) restrict_h_item<T>(nc, Rt, r, y, rc, i);
     __syncthreads();
   }
   {  // B_1 = A_1^-1
@@ -957,7 +946,8 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* Pi = L.staged ? sm + L.pi_off : L.Pi;
     const T* ec = sm + P.lv[l + 1].voff + 2 * P.lv[l + 1].nEdge;
     const bool ns = P.ns != 0;
-    for (int i = tid; i < nc * nc + P.lv[l + 1].nEdge; i += nth) prolong_h_item<T>(nc, Pi, ec, e, y, i);
+    for (int i = tid; i < 8 * nc * nc + 2 * P.lv[l + 1].nEdge; i += nth)
+      prolong_h_item<T>(nc, Pi, ec, e, y, i);
     __syncthreads();
     if (P.lc == HDGMG_LC_BOTH) {
       for (int i = tid; i < 8 * nc * nc; i += nth) local_correction_item<T>(nc, ns, AIIinv, Yb, r, e, i);
@@ -1328,13 +1318,13 @@ void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T*
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
   note_launch();
-  restrict_h_kernel<T><<<nblk(nedc, 128), 128, 0, s>>>(nc, Pi, r, y, rc);
+  restrict_h_kernel<T><<<nblk(2 * nedc, 128), 128, 0, s>>>(nc, Pi, r, y, rc);
 }
 
 template <typename T>
 void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y) {
   upload_jc();
-  const int tot = nc * nc + 2 * nc * (nc + 1);
+  const int tot = 8 * nc * nc + 4 * nc * (nc + 1);
   note_launch();
   prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(nc, Pi, ec, e, y);
 }
