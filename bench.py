@@ -31,9 +31,9 @@ UNIT = "trace DOFs/s"
 N_MESH, P_ORDER, SEED = 256, 4, 2
 SAMPLE_N = 128          # oracle sample: same recipe on a 128 x 128 mesh
 L2_FLUSH_BYTES = 512 << 20
-# symmetric V(1,1): m_N = 1 doubling per level up to 4, local correction in
-# steps 3 and 5, coarsest level 4 x 4 macro-elements (48 DOFs, dense Cholesky)
-SOLVER_OPTS = dict(coarsest_n=4, m_fine=1, m_growth=2, m_max=4, rtol=1e-10)
+# symmetric V(1,1): m_N = 1 doubling per level up to 2, local correction in
+# steps 3 and 5, coarsest level 4 x 4 macro-elements (48 DOFs, dense inverse)
+SOLVER_OPTS = dict(coarsest_n=4, m_fine=1, m_growth=2, m_max=2, rtol=1e-10)
 
 
 def parse():
@@ -57,7 +57,7 @@ def workload_config(n=N_MESH):
                         f"log kappa iid N(0,1) seed {SEED}, f=1, g_D=0, tau=1/h",
             "mesh": n, "p": P_ORDER, "interior_trace_dofs": 2 * n * (n - 1) * (P_ORDER + 1),
             "rtol": 1e-10, "krylov": "PCG with the symmetric V-cycle (m_N=1, m doubling per level "
-                                     "capped at 4, local correction steps 3+5, coarsest 4x4 dense)",
+                                     "capped at 2, local correction steps 3+5, coarsest 4x4 dense)",
             "l2": "flushed between steps (512 MiB write)"}
 
 

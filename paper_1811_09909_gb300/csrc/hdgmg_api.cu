@@ -349,19 +349,28 @@ hdgmg_status check_launch(const char* where) {
 // ----------------------------------------------------------- V-cycle (Alg. 1)
 // y += A_l e on level l (the finest level reads its BF16 copy when it has one)
 template <typename T>
-void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y) {
+void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y, const T* xadd = nullptr) {
   Level& L = c->levels[l];
   if constexpr (std::is_same<T, float>::value) {
     if (L.A16) {
-      launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f);
+      launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f, xadd);
       return;
     }
   }
-  launch_matvec<T>(c->stream, L.n, L.nd, c->ns, ld<T>(L).A, x, y, T(1));
+  launch_matvec<T>(c->stream, L.n, L.nd, c->ns, ld<T>(L).A, x, y, T(1), xadd);
 }
 
+// A P1 level run by separate launches with the fused edge sweeps (not in a
+// fused tail, not the coarsest level)
+bool p1_launched(hdgmg_ctx* c, int l) {
+  const Level& L = c->levels[l];
+  return L.nd == 2 && L.transfer == 2 && !L.A16 && l != c->tail_start && l != c->ctail_start;
+}
+
+// rp_r0/rp_y0/rp_nd0: the p-level above left its restriction J_N^T (r - A e)
+// pending; this level's first sweep applies it.
 template <typename T>
-void vcycle(hdgmg_ctx* c, int l) {
+void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, int rp_nd0 = 0) {
   cudaStream_t s = c->stream;
   Level& L = c->levels[l];
   LevelData<T>& D = ld<T>(L);
@@ -389,7 +398,10 @@ void vcycle(hdgmg_ctx* c, int l) {
     LevelData<T>& Dc = ld<T>(Lc);
     T* bufs[2] = {D.e, D.y};
     int cur = 1;
-    launch_bj_update<T>(s, L.n, 2, ns, D.Dinv, D.r, bufs[0], bufs[1], omega, 1);
+    if (rp_r0)
+      launch_bj_first_restrict_p<T>(s, L.n, rp_nd0, ns, D.Dinv, rp_r0, rp_y0, D.r, bufs[1], omega);
+    else
+      launch_bj_update<T>(s, L.n, 2, ns, D.Dinv, D.r, bufs[0], bufs[1], omega, 1);
     for (int i = 1; i < L.m; ++i) {
       launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true);
       cur ^= 1;
@@ -421,22 +433,31 @@ void vcycle(hdgmg_ctx* c, int l) {
   Level& Lc = c->levels[l + 1];
   LevelData<T>& Dc = ld<T>(Lc);
   level_matvec<T>(c, l, D.e, D.y);
-  if (L.transfer == 1)
-    launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
-  else
-    launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, D.y, Dc.r);
-  vcycle<T>(c, l + 1);
-  if (L.transfer == 1)
-    launch_prolong_p<T>(s, L.n, L.nd, Dc.e, D.e);
-  else
-    launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y);
+  // J_N^T and J_N fused into the neighbouring kernels when the P1 level
+  // below runs as separate launches
+  const bool fuse_p = L.transfer == 1 && p1_launched(c, l + 1);
+  const T* xadd = nullptr;
+  if (fuse_p) {
+    vcycle<T>(c, l + 1, D.r, D.y, L.nd);
+    xadd = Dc.e;
+  } else {
+    if (L.transfer == 1)
+      launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
+    else
+      launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, D.y, Dc.r);
+    vcycle<T>(c, l + 1);
+    if (L.transfer == 1)
+      launch_prolong_p<T>(s, L.n, L.nd, Dc.e, D.e);
+    else
+      launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y);
+  }
   // step 5: second local correction (symmetric cycle)
   if (L.transfer == 2 && lc == HDGMG_LC_BOTH)
     launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
-  // step 6: post-smoothing
+  // step 6: post-smoothing (the first step also adds the pending J_N e_c)
   for (int i = 0; i < L.m; ++i) {
-    level_matvec<T>(c, l, D.e, D.y);
-    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
+    level_matvec<T>(c, l, D.e, D.y, i == 0 ? xadd : nullptr);
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, i == 0 ? xadd : nullptr);
   }
 }
 
@@ -544,16 +565,28 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
 // FP64 form: A = the FP64 fine operator, B = the V-cycle.  FP32 form (inner
 // iteration of the refinement): A = the FP32 copy, vectors FP32, scalars and
 // dot products FP64; r and z are the V-cycle's own level-0 buffers.
+// With the FP32 V-cycle the level-0 FP32 residual is written by the update
+// kernel of the previous iteration (and once before the loop), and the
+// V-cycle output is read in FP32 by the two kernels that consume z.
 void cg_body64(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
-  apply_B(c, c->r, c->z);
-  launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);
-  launch_cg_direction_zero<double>(s, len, c->scal, c->z, c->pv, c->Ap);
-  launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->pv, c->Ap, 1.0);
+  Level& L0 = c->levels[0];
+  const bool mixed = c->opts.precision != HDGMG_PREC_FP64;
+  if (mixed) {
+    vcycle<float>(c, 0);
+    launch_dot_fused_mixed(s, len, c->r, L0.d32.e, c->partial, c->counter, c->scal, 1);
+    launch_cg_direction_zero_mixed(s, len, c->scal, L0.d32.e, c->pv, c->Ap);
+  } else {
+    apply_B(c, c->r, c->z);
+    launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);
+    launch_cg_direction_zero<double>(s, len, c->scal, c->z, c->pv, c->Ap);
+  }
+  launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->pv, c->Ap, 1.0);
   launch_dot_fused<double>(s, len, c->pv, c->Ap, c->partial, c->counter, c->scal, 0);
   launch_cg_update_test<double>(s, len, c->scal, c->x, c->r, c->pv, c->Ap, c->partial, c->counter,
-                                h, c->it_dev, c->opts.max_it, c->opts.rtol * c->opts.rtol);
+                                h, c->it_dev, c->opts.max_it, c->opts.rtol * c->opts.rtol,
+                                mixed ? L0.d32.r : nullptr);
 }
 
 void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
@@ -569,7 +602,7 @@ void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   launch_dot_fused<float>(s, len, c->ps, c->Aps, c->partial, c->counter, c->scal32, 0);
   launch_cg_update_test<float>(s, len, c->scal32, c->xs, rs, c->ps, c->Aps, c->partial, c->counter,
                                h, c->it_dev, c->opts.max_it,
-                               c->opts.inner_rtol * c->opts.inner_rtol);
+                               c->opts.inner_rtol * c->opts.inner_rtol, nullptr);
 }
 
 hdgmg_status build_loop_graph(hdgmg_ctx* c, void (*body)(hdgmg_ctx*, cudaGraphConditionalHandle),
@@ -774,6 +807,8 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     // whole iteration loop replayed as one CUDA graph
     STATUS_TRY(build_loop_graph(c, cg_body64, &c->cg_graph, &c->cg_exec, &c->cg_body_launches));
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    if (o.precision != HDGMG_PREC_FP64)
+      launch_convert<double, float>(s, len, c->r, c->levels[0].d32.r);
     CUDA_TRY(cudaMemsetAsync(c->pv, 0, sizeof(double) * len, s));
     CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int), s));
     c->init_h[0] = 1.0;      // rz of the previous iteration (p = 0 makes beta irrelevant)

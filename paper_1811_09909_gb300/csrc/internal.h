@@ -131,29 +131,39 @@ void launch_adjoint_source(cudaStream_t s, const RefDevice& ref, int nv, int nE,
 void launch_misfit(cudaStream_t s, const RefDevice& ref, int nv, int nE, const double* u,
                    const double* uobs, double* d, double* gu);
 
-// ns: operators stored non-symmetric (full row-major) instead of packed
+// ns: operators stored non-symmetric (full row-major) instead of packed.
+// xadd (nullable): the P1 correction of the next level, added to modes 0
+// and 1 of x (matvec) or of e (block-Jacobi update) on the fly -- the
+// p-prolongation J_N fused into the first post-smoothing step.
 template <typename T>
-void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha);
+void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha,
+                   const T* xadd = nullptr);
 // per-ND instantiations (k_edge_inst.cu, one translation unit per type and ND)
 template <typename T, int ND, bool NS>
-void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha);
+void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha, const T* xadd);
 template <typename T, int ND, bool NS>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err);
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
-                         int first);
+                         int first, const T* xadd);
 // y += alpha A x with A stored in BF16, x, y and the accumulation in FP32
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
-                        const float* x, float* y, float alpha);
+                        const float* x, float* y, float alpha, const float* xadd = nullptr);
 template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
-                           float alpha);
+                           float alpha, const float* xadd);
 void launch_to_bf16(cudaStream_t s, int64_t len, const double* in, __nv_bfloat16* out);
 template <typename T>
 void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err);
 template <typename T>
 void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
-                      T* e, T omega, int first);
+                      T* e, T omega, int first, const T* xadd = nullptr);
+// p-restriction fused into the first sweep of the P1 level below the
+// p-level: r1 = (r0 - y0) on modes 0, 1 (written), y0 := 0 on all nd0
+// modes, e1 = omega D1^-1 r1
+template <typename T>
+void launch_bj_first_restrict_p(cudaStream_t s, int n, int nd0, bool ns, const T* Dinv1,
+                                const T* r0, T* y0, T* r1, T* e1, T omega);
 template <typename T>
 void launch_pcoarsen(cudaStream_t s, int nE, int ndf, bool ns, const T* Af, T* Ac);
 // ns: also writes Rt = Z^T J with Z = -A_BI A_II^-1 (the restriction block);
@@ -289,10 +299,17 @@ void launch_dot_fused(cudaStream_t s, int64_t len, const T* a, const T* b, doubl
 template <typename T>
 void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p,
                               T* Ap);
+// r32 (nullable): also receives the updated r rounded to FP32
 template <typename T>
 void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r, const T* p,
                            const T* Ap, double* partial, unsigned* counter,
-                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2);
+                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2,
+                           float* r32);
+// FP64 CG vectors with the FP32 V-cycle output z read directly
+void launch_dot_fused_mixed(cudaStream_t s, int64_t len, const double* a, const float* b,
+                            double* partial, unsigned* counter, double* scal, int mode);
+void launch_cg_direction_zero_mixed(cudaStream_t s, int64_t len, const double* scal, const float* z,
+                                    double* p, double* Ap);
 // FP64 -> FP32 with 1/sqrt(*scale), and y += sqrt(*scale) x (FP32 -> FP64)
 void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
                          float* out);

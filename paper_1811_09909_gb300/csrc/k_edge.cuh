@@ -25,10 +25,12 @@ static __device__ __forceinline__ float load_entry(const __nv_bfloat16* p) {
 }
 
 // ---------------------------------------------------------------- K6 matvec
+// xadd (nullable, modes 0 and 1 only): x + J xadd is applied instead of x,
+// i.e. the P1 correction of the next level is prolonged on the fly
 template <typename T, int ND, bool NS, typename TA = T>
 __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y,
-                                                     T alpha) {
+                                                     T alpha, const T* __restrict__ xadd) {
   constexpr int NL = 4 * ND;
   const int nE = n * n;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,7 +40,11 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict
   elem_edges(n, e, ed);
   T xl[NL];
 #pragma unroll
-  for (int c = 0; c < NL; ++c) xl[c] = x[(size_t)(c % ND) * nedge + ed[c / ND]];
+  for (int c = 0; c < NL; ++c) {
+    const size_t ix = (size_t)(c % ND) * nedge + ed[c / ND];
+    xl[c] = x[ix];
+    if (xadd && c % ND < 2) xl[c] += xadd[ix];
+  }
   if constexpr (NS) {
     // full storage: one row at a time (rows not unrolled, which keeps the
     // NL^2-entry kernel small to compile), added straight into y
@@ -206,7 +212,8 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
 // --------------------------------------------------- K7 block-Jacobi update
 template <typename T, int ND, bool NS>
 __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __restrict__ r,
-                                 T* __restrict__ y, T* __restrict__ e, T omega, int first) {
+                                 T* __restrict__ y, T* __restrict__ e, T omega, int first,
+                                 const T* __restrict__ xadd) {
   const int nedge = 2 * n * (n + 1);
   const int edge = blockIdx.x * blockDim.x + threadIdx.x;
   if (edge >= nedge || bnd_edge(n, edge)) return;
@@ -224,22 +231,30 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
     for (int b = 0; b < ND; ++b)
       s += Dinv[(size_t)(NS ? a * ND + b : pk_any(a, b)) * nedge + edge] * d[b];
     const size_t ix = (size_t)a * nedge + edge;
-    e[ix] = first ? omega * s : e[ix] + omega * s;
+    if (first) {
+      e[ix] = omega * s;
+    } else {
+      T eo = e[ix];
+      if (xadd && a < 2) eo += xadd[ix];
+      e[ix] = eo + omega * s;
+    }
   }
 }
 
 
 template <typename T, int ND, bool NS>
-void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha) {
+void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha,
+                      const T* xadd) {
   note_launch();
-  matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
+  matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha, xadd);
 }
 
 template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
-                           float alpha) {
+                           float alpha, const float* xadd) {
   note_launch();
-  matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha);
+  matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha,
+                                                                              xadd);
 }
 
 template <typename T, int ND, bool NS>
@@ -250,10 +265,10 @@ void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err) {
 
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
-                         int first) {
+                         int first, const T* xadd) {
   note_launch();
   bj_update_kernel<T, ND, NS><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega,
-                                                                         first);
+                                                                         first, xadd);
 }
 
 }  // namespace hdgmg

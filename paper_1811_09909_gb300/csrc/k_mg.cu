@@ -501,6 +501,35 @@ __global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __re
 }
 
 // ------------------------------------------------- p-transfer (J_N, J_N^T)
+// J_N^T fused into the first block-Jacobi sweep of the P1 level below (same
+// mesh, one thread per edge): r1 = r0 - y0 on modes 0 and 1, y0 reset on
+// every mode, e1 = omega D1^-1 r1.
+template <typename T>
+__global__ void bj_first_restrict_p_kernel(int n, int nd0, bool ns, const T* __restrict__ Dinv1,
+                                           const T* __restrict__ r0, T* __restrict__ y0,
+                                           T* __restrict__ r1, T* __restrict__ e1, T omega) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge) return;
+  const T d0 = r0[E] - y0[E], d1 = r0[(size_t)nedge + E] - y0[(size_t)nedge + E];
+  for (int k = 0; k < nd0; ++k) y0[(size_t)k * nedge + E] = T(0);
+  r1[E] = d0;
+  r1[(size_t)nedge + E] = d1;
+  if (bnd_edge(n, E)) return;
+  const T a00 = Dinv1[E], a01 = Dinv1[(size_t)nedge + E], a10 = Dinv1[(size_t)2 * nedge + E];
+  T u0, u1;
+  if (ns) {
+    u0 = a00 * d0 + a01 * d1;
+    u1 = a10 * d0 + Dinv1[(size_t)3 * nedge + E] * d1;
+  } else {
+    u0 = a00 * d0 + a01 * d1;
+    u1 = a01 * d0 + a10 * d1;
+  }
+  e1[E] = omega * u0;
+  e1[(size_t)nedge + E] = omega * u1;
+}
+
+
 template <typename T>
 __global__ void restrict_p_kernel(int n, int nd, const T* __restrict__ r, T* __restrict__ y,
                                   T* __restrict__ rc) {
@@ -1044,9 +1073,9 @@ __device__ __forceinline__ double sum_partials(const double* partial, int n, dou
   return block_sum(s, sh);
 }
 
-template <typename T>
+template <typename T, typename TB = T>
 __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __restrict__ a,
-                                                        const T* __restrict__ b,
+                                                        const TB* __restrict__ b,
                                                         double* __restrict__ partial,
                                                         unsigned* __restrict__ counter,
                                                         double* __restrict__ scal, int mode) {
@@ -1076,14 +1105,14 @@ __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __
 }
 
 // p = z + beta p and Ap = 0
-template <typename T>
+template <typename T, typename TZ = T>
 __global__ void cg_direction_zero_kernel(int64_t len, const double* __restrict__ scal,
-                                         const T* __restrict__ z, T* __restrict__ p,
+                                         const TZ* __restrict__ z, T* __restrict__ p,
                                          T* __restrict__ Ap) {
   const T beta = (T)scal[4];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
-    p[i] = z[i] + beta * p[i];
+    p[i] = (T)z[i] + beta * p[i];
     Ap[i] = T(0);
   }
 }
@@ -1095,7 +1124,7 @@ __global__ void __launch_bounds__(256) cg_update_test_kernel(
     int64_t len, double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
     const T* __restrict__ p, const T* __restrict__ Ap, double* __restrict__ partial,
     unsigned* __restrict__ counter, cudaGraphConditionalHandle h, int* __restrict__ it,
-    int max_it, double tol2) {
+    int max_it, double tol2, float* __restrict__ r32) {
   __shared__ double sh[256];
   const T alpha = (T)scal[2];
   double s = 0.0;
@@ -1104,6 +1133,7 @@ __global__ void __launch_bounds__(256) cg_update_test_kernel(
     x[i] += alpha * p[i];
     const T ri = r[i] - alpha * Ap[i];
     r[i] = ri;
+    if (r32) r32[i] = (float)ri;
     s += (double)ri * (double)ri;
   }
   s = block_sum(s, sh);
@@ -1215,19 +1245,20 @@ __global__ void unpack_kernel(int nl, int nE, bool ns, const T* __restrict__ Ap,
   }
 
 template <typename T>
-void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha) {
-#define MV(ND)                                              \
-  if (ns) launch_matvec_nd<T, ND, true>(s, n, A, x, y, alpha); \
-  else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha)
+void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha,
+                   const T* xadd) {
+#define MV(ND)                                                        \
+  if (ns) launch_matvec_nd<T, ND, true>(s, n, A, x, y, alpha, xadd);   \
+  else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha, xadd)
   ND_DISPATCH(nd, MV)
 #undef MV
 }
 
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
-                        const float* x, float* y, float alpha) {
-#define MVB(ND)                                                        \
-  if (ns) launch_matvec_bf16_nd<ND, true>(s, n, A, x, y, alpha);       \
-  else launch_matvec_bf16_nd<ND, false>(s, n, A, x, y, alpha)
+                        const float* x, float* y, float alpha, const float* xadd) {
+#define MVB(ND)                                                              \
+  if (ns) launch_matvec_bf16_nd<ND, true>(s, n, A, x, y, alpha, xadd);       \
+  else launch_matvec_bf16_nd<ND, false>(s, n, A, x, y, alpha, xadd)
   ND_DISPATCH(nd, MVB)
 #undef MVB
 }
@@ -1257,10 +1288,10 @@ void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Din
 
 template <typename T>
 void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
-                      T* e, T omega, int first) {
-#define BU(ND)                                                                  \
-  if (ns) launch_bj_update_nd<T, ND, true>(s, n, Dinv, r, y, e, omega, first);  \
-  else launch_bj_update_nd<T, ND, false>(s, n, Dinv, r, y, e, omega, first)
+                      T* e, T omega, int first, const T* xadd) {
+#define BU(ND)                                                                        \
+  if (ns) launch_bj_update_nd<T, ND, true>(s, n, Dinv, r, y, e, omega, first, xadd);  \
+  else launch_bj_update_nd<T, ND, false>(s, n, Dinv, r, y, e, omega, first, xadd)
   ND_DISPATCH(nd, BU)
 #undef BU
 }
@@ -1327,6 +1358,15 @@ void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T*
   const int tot = 8 * nc * nc + 4 * nc * (nc + 1);
   note_launch();
   prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(nc, Pi, ec, e, y);
+}
+
+template <typename T>
+void launch_bj_first_restrict_p(cudaStream_t s, int n, int nd0, bool ns, const T* Dinv1,
+                                const T* r0, T* y0, T* r1, T* e1, T omega) {
+  const int ne = 2 * n * (n + 1);
+  note_launch();
+  bj_first_restrict_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd0, ns, Dinv1, r0, y0, r1, e1,
+                                                              omega);
 }
 
 template <typename T>
@@ -1472,10 +1512,25 @@ void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, c
 template <typename T>
 void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r, const T* p,
                            const T* Ap, double* partial, unsigned* counter,
-                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2) {
+                           cudaGraphConditionalHandle h, int* it, int max_it, double tol2,
+                           float* r32) {
   note_launch();
   cg_update_test_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, scal, x, r, p, Ap, partial, counter, h,
-                                                      it, max_it, tol2);
+                                                      it, max_it, tol2, r32);
+}
+
+void launch_dot_fused_mixed(cudaStream_t s, int64_t len, const double* a, const float* b,
+                            double* partial, unsigned* counter, double* scal, int mode) {
+  note_launch();
+  dot_fused_kernel<double, float><<<kDotBlocks, 256, 0, s>>>(len, a, b, partial, counter, scal, mode);
+}
+
+void launch_cg_direction_zero_mixed(cudaStream_t s, int64_t len, const double* scal, const float* z,
+                                    double* p, double* Ap) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  cg_direction_zero_kernel<double, float><<<blocks, 256, 0, s>>>(len, scal, z, p, Ap);
 }
 
 void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
@@ -1513,10 +1568,13 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
 
 // explicit instantiations
 #define INST(T)                                                                                 \
-  template void launch_matvec<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T);      \
+  template void launch_matvec<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T,       \
+                                 const T*);                                                     \
   template void launch_bj_blocks<T>(cudaStream_t, int, int, bool, const T*, T*, int*);          \
   template void launch_bj_update<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T*, T, \
-                                    int);                                                       \
+                                    int, const T*);                                             \
+  template void launch_bj_first_restrict_p<T>(cudaStream_t, int, int, bool, const T*, const T*, \
+                                              T*, T*, T*, T);                                   \
   template void launch_pcoarsen<T>(cudaStream_t, int, int, bool, const T*, T*);                 \
   template void launch_agglomerate<T>(cudaStream_t, int, bool, const T*, T*, T*, T*, T*, T*,    \
                                       int*);                                                    \
@@ -1554,10 +1612,10 @@ template void launch_cg_direction_zero<float>(cudaStream_t, int64_t, const doubl
                                               float*, float*);
 template void launch_cg_update_test<double>(cudaStream_t, int64_t, double*, double*, double*,
                                             const double*, const double*, double*, unsigned*,
-                                            cudaGraphConditionalHandle, int*, int, double);
+                                            cudaGraphConditionalHandle, int*, int, double, float*);
 template void launch_cg_update_test<float>(cudaStream_t, int64_t, double*, float*, float*,
                                            const float*, const float*, double*, unsigned*,
-                                           cudaGraphConditionalHandle, int*, int, double);
+                                           cudaGraphConditionalHandle, int*, int, double, float*);
 template void launch_dot<float>(cudaStream_t, int64_t, const float*, const float*, double*, double*);
 template void launch_cg_update<double>(cudaStream_t, int64_t, const double*, double*, double*,
                                        const double*, const double*);
