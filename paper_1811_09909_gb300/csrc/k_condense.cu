@@ -136,126 +136,93 @@ __device__ __forceinline__ double recip_newton(double d) {
   return y;
 }
 
-// K1 (non-symmetric): one warp per element.  The element-independent parts
-// (tau is the same on every element of the uniform mesh, beta is constant)
-// come precomputed, so every entry of S, W and V costs one FMA:
+// K1 (non-symmetric): one block of kCdThreads (two warps) per element.  The
+// element-independent parts (tau is the same on every element of the
+// uniform mesh, beta is constant) come precomputed, so every entry of S, W
+// and V costs one FMA:
 //   S = eps G + S0,  W = eps H + W0,  V = eps H + V0,
 //   A_e = eps K + diag(adiag) - V^T S^-1 W.
 // S is factored in shared memory (LU without pivoting, pivots inverted once
 // by a Newton reciprocal), the forward sweep applied to W on the fly, then
 // back substitution gives X = S^-1 W.  The factors are kept for K5/K12 as
 // [nv*nv][nE]: unit lower part below the diagonal, U above it and the
-// reciprocal pivots 1/u_kk on the diagonal.
-__global__ void condense_cd_kernel(int nv, int nt, int nE, int warps_per_block,
-                                   const double* __restrict__ G, const double* __restrict__ H,
-                                   const double* __restrict__ K, const double* __restrict__ S0,
-                                   const double* __restrict__ W0, const double* __restrict__ V0,
-                                   const double* __restrict__ adiag,
-                                   const double* __restrict__ kapv, double* __restrict__ A,
-                                   double* __restrict__ LU, int* __restrict__ err) {
+// reciprocal pivots 1/u_kk on the diagonal.  Shared memory per element bounds
+// the residency on GB300 (p = 6: 31 KB), so two warps share each element to
+// double the warps per SM that feed the FP64 pipe.
+constexpr int kCdThreads = 64;
+
+__global__ void __launch_bounds__(kCdThreads) condense_cd_kernel(
+    int nv, int nt, int nE, const double* __restrict__ G, const double* __restrict__ H,
+    const double* __restrict__ K, const double* __restrict__ S0, const double* __restrict__ W0,
+    const double* __restrict__ V0, const double* __restrict__ adiag,
+    const double* __restrict__ kapv, double* __restrict__ A, double* __restrict__ LU,
+    int* __restrict__ err) {
   extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * warps_per_block + warp;
+  const int tid = threadIdx.x;
+  constexpr int NT = kCdThreads;
+  const int e = blockIdx.x;
   if (e >= nE) return;
   const int nvv = nv * nv, nvt = nv * nt;
   const int ns = nvv > nvt ? nvv : nvt;     // S, later V (n_v x n_t)
-  double* S = smem + (size_t)warp * (ns + nvt + nv);
+  double* S = smem;
   double* X = S + ns;
   double* dinv = X + nvt;
   const double eps = kapv[e];
-  for (int t = lane; t < nvv; t += 32) S[t] = fma(eps, G[t], S0[t]);
-  for (int t = lane; t < nvt; t += 32) X[t] = fma(eps, H[t], W0[t]);
-  __syncwarp();
+  for (int t = tid; t < nvv; t += NT) S[t] = fma(eps, G[t], S0[t]);
+  for (int t = tid; t < nvt; t += NT) X[t] = fma(eps, H[t], W0[t]);
+  __syncthreads();
   bool bad = false;
-  // GB300 has one warp per scheduler here (shared memory bounds the
-  // occupancy), so every loop issues its shared-memory loads for four
-  // independent updates before the FMAs and stores: the loads of the next
-  // updates overlap the FP64 pipe instead of waiting behind each store.
   for (int k = 0; k < nv; ++k) {
-    double di = 0.0;
-    if (lane == 0) {
+    if (tid == 0) {
       double d = S[k * nv + k];
       if (!(d > 0.0) || !isfinite(d)) {
         bad = true;
         d = 1.0;
       }
-      di = recip_newton(d);
-      dinv[k] = di;
+      dinv[k] = recip_newton(d);
     }
-    di = __shfl_sync(0xffffffffu, di, 0);
-    for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
-    __syncwarp();
+    __syncthreads();
+    const double di = dinv[k];
+    for (int i = k + 1 + tid; i < nv; i += NT) S[i * nv + k] *= di;
+    __syncthreads();
     const int m = nv - k - 1;
     const int mm = m * m;
-    for (int t0 = lane; t0 < mm; t0 += 128) {
-      double a[4], b[4], c[4];
-      int ix[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int t = t0 + 32 * u;
-        ix[u] = -1;
-        if (t < mm) {
-          const int i = k + 1 + t / m, j = k + 1 + t % m;
-          ix[u] = i * nv + j;
-          a[u] = S[i * nv + k];
-          b[u] = S[k * nv + j];
-          c[u] = S[ix[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (ix[u] >= 0) S[ix[u]] = fma(-a[u], b[u], c[u]);
+    for (int t = tid; t < mm; t += NT) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      S[i * nv + j] = fma(-S[i * nv + k], S[k * nv + j], S[i * nv + j]);
     }
     const int mt = m * nt;
-    for (int t0 = lane; t0 < mt; t0 += 128) {
-      double a[4], b[4], c[4];
-      int ix[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int t = t0 + 32 * u;
-        ix[u] = -1;
-        if (t < mt) {
-          const int i = k + 1 + t / nt, cc = t % nt;
-          ix[u] = i * nt + cc;
-          a[u] = S[i * nv + k];
-          b[u] = X[k * nt + cc];
-          c[u] = X[ix[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (ix[u] >= 0) X[ix[u]] = fma(-a[u], b[u], c[u]);
+    for (int t = tid; t < mt; t += NT) {
+      const int i = k + 1 + t / nt, c = t % nt;
+      X[i * nt + c] = fma(-S[i * nv + k], X[k * nt + c], X[i * nt + c]);
     }
-    __syncwarp();
+    __syncthreads();
   }
-  // back substitution U X = L^-1 W, one column per lane, four partial sums
-  for (int c = lane; c < nt; c += 32) {
-    for (int k = nv - 1; k >= 0; --k) {
-      double s0 = X[k * nt + c], s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      int j = k + 1;
-      for (; j + 3 < nv; j += 4) {
-        s0 = fma(-S[k * nv + j], X[j * nt + c], s0);
-        s1 = fma(-S[k * nv + j + 1], X[(j + 1) * nt + c], s1);
-        s2 = fma(-S[k * nv + j + 2], X[(j + 2) * nt + c], s2);
-        s3 = fma(-S[k * nv + j + 3], X[(j + 3) * nt + c], s3);
-      }
-      for (; j < nv; ++j) s0 = fma(-S[k * nv + j], X[j * nt + c], s0);
-      X[k * nt + c] = ((s0 + s1) + (s2 + s3)) * dinv[k];
+  // back substitution U X = L^-1 W, right-looking: scale row k by the
+  // reciprocal pivot, then eliminate it from the rows above (all threads)
+  for (int k = nv - 1; k >= 0; --k) {
+    const double di = dinv[k];
+    for (int c = tid; c < nt; c += NT) X[k * nt + c] *= di;
+    __syncthreads();
+    const int kt = k * nt;
+    for (int t = tid; t < kt; t += NT) {
+      const int i = t / nt, c = t - i * nt;
+      X[t] = fma(-S[i * nv + k], X[k * nt + c], X[t]);
     }
+    __syncthreads();
   }
-  __syncwarp();
   if (bad) atomicOr(err, 1);
   // the factors go out first; S's space then holds V = eps H + V0
   if (LU)
-    for (int t = lane; t < nvv; t += 32) {
+    for (int t = tid; t < nvv; t += NT) {
       const int r = t / nv, c = t - r * nv;
       LU[(size_t)t * nE + e] = (r == c) ? dinv[r] : S[t];
     }
-  __syncwarp();
+  __syncthreads();
   double* V = S;
-  for (int t = lane; t < nvt; t += 32) V[t] = fma(eps, H[t], V0[t]);
-  __syncwarp();
-  for (int t = lane; t < nt * nt; t += 32) {
+  for (int t = tid; t < nvt; t += NT) V[t] = fma(eps, H[t], V0[t]);
+  __syncthreads();
+  for (int t = tid; t < nt * nt; t += NT) {
     const int r = t / nt, c = t % nt;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int a = 0;
@@ -601,21 +568,16 @@ void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const 
 void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
                         const double* kap, double* A, double* LU, int* err) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t per_warp =
+  const size_t shm =
       sizeof(double) * (size_t)((nv * nv > nv * nt ? nv * nv : nv * nt) + nv * nt + nv);
-  int wpb = (int)((200 * 1024) / per_warp);
-  if (wpb > 8) wpb = 8;
-  if (wpb < 1) wpb = 1;
-  const size_t shm = per_warp * wpb;
   static const bool attr_set = [] {
     cudaFuncSetAttribute(condense_cd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     return true;
   }();
   (void)attr_set;
-  const int blocks = (nE + wpb - 1) / wpb;
   note_launch();
-  condense_cd_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.H, ref.K, cd.S0, cd.W0,
-                                                    cd.V0, cd.adiag, kap, A, LU, err);
+  condense_cd_kernel<<<nE, kCdThreads, shm, s>>>(nv, nt, nE, ref.G, ref.H, ref.K, cd.S0, cd.W0, cd.V0,
+                                                 cd.adiag, kap, A, LU, err);
 }
 
 void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
