@@ -38,77 +38,84 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-// K1: one warp per element, the local matrices in shared memory.
-//   S: nv x nv (full square, lower part used), V: nv x nt.
+// K1: one block of kSymThreads (two warps) per element, the local matrices in
+// shared memory.  S: nv x nv (full square, lower part used), V: nv x nt.
 // The FP64 pipe is the bottleneck on GB300, so every pivot's square root and
-// reciprocal is computed by one lane and broadcast.
-__global__ void condense_kernel(int nv, int nt, int nE, int warps_per_block,
-                                const double* __restrict__ G, const double* __restrict__ Eb,
-                                const double* __restrict__ H, const double* __restrict__ F,
-                                const double* __restrict__ K, const double* __restrict__ kapv,
-                                int tau_mode, double tau_c, double hmin,
-                                double* __restrict__ A, double* __restrict__ Lfac,
-                                int* __restrict__ err) {
+// reciprocal is computed once (thread 0) and read by all threads.
+constexpr int kSymThreads = 64;
+
+__global__ void __launch_bounds__(kSymThreads) condense_kernel(
+    int nv, int nt, int nE, const double* __restrict__ G, const double* __restrict__ Eb,
+    const double* __restrict__ H, const double* __restrict__ F, const double* __restrict__ K,
+    const double* __restrict__ kapv, int tau_mode, double tau_c, double hmin,
+    double* __restrict__ A, double* __restrict__ Lfac, int* __restrict__ err) {
   extern __shared__ double smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int e = blockIdx.x * warps_per_block + warp;
+  constexpr int NT = kSymThreads;
+  const int tid = threadIdx.x;
+  const int e = blockIdx.x;
   if (e >= nE) return;
-  double* S = smem + (size_t)warp * (nv * nv + nv * nt);
+  double* S = smem;
   double* V = S + nv * nv;
+  double* dinv = V + nv * nt;
   const double kap = kapv[e];
   const double tau = tau_of(tau_mode, tau_c, hmin);
   const int nsv = nv * (nv + 1) / 2;
-  for (int t = lane; t < nsv; t += 32) {
+  for (int t = tid; t < nsv; t += NT) {
     int i, j;
     tri_index(t, i, j);
-    S[i * nv + j] = kap * G[i * nv + j] + tau * Eb[i * nv + j];
+    S[i * nv + j] = fma(kap, G[i * nv + j], tau * Eb[i * nv + j]);
   }
-  for (int t = lane; t < nv * nt; t += 32) V[t] = kap * H[t] + tau * F[t];
-  __syncwarp();
+  for (int t = tid; t < nv * nt; t += NT) V[t] = fma(kap, H[t], tau * F[t]);
+  __syncthreads();
   bool bad = false;
   for (int k = 0; k < nv; ++k) {
-    double di = 0.0;
-    if (lane == 0) {
+    if (tid == 0) {
       double d = S[k * nv + k];
       if (!(d > 0.0) || !isfinite(d)) {
         bad = true;
         d = 1.0;
       }
-      di = rsqrt_newton(d);
+      const double di = rsqrt_newton(d);
       S[k * nv + k] = d * di;
+      dinv[k] = di;
     }
-    di = __shfl_sync(0xffffffffu, di, 0);
-    for (int i = k + 1 + lane; i < nv; i += 32) S[i * nv + k] *= di;
-    for (int c = lane; c < nt; c += 32) V[k * nt + c] *= di;
-    __syncwarp();
+    __syncthreads();
+    const double di = dinv[k];
+    for (int i = k + 1 + tid; i < nv; i += NT) S[i * nv + k] *= di;
+    for (int c = tid; c < nt; c += NT) V[k * nt + c] *= di;
+    __syncthreads();
     const int m = nv - k - 1;
     const int ntri = m * (m + 1) / 2;
-    for (int t = lane; t < ntri; t += 32) {
+    for (int t = tid; t < ntri; t += NT) {
       int ii, jj;
       tri_index(t, ii, jj);
       const int i = k + 1 + ii, j = k + 1 + jj;
-      S[i * nv + j] -= S[i * nv + k] * S[j * nv + k];
+      S[i * nv + j] = fma(-S[i * nv + k], S[j * nv + k], S[i * nv + j]);
     }
-    for (int t = lane; t < m * nt; t += 32) {
+    for (int t = tid; t < m * nt; t += NT) {
       const int i = k + 1 + t / nt, c = t % nt;
-      V[i * nt + c] -= S[i * nv + k] * V[k * nt + c];
+      V[i * nt + c] = fma(-S[i * nv + k], V[k * nt + c], V[i * nt + c]);
     }
-    __syncwarp();
+    __syncthreads();
   }
   if (bad) atomicOr(err, 1);
   const int nsa = nt * (nt + 1) / 2;
-  for (int t = lane; t < nsa; t += 32) {
+  for (int t = tid; t < nsa; t += NT) {
     int r, c;
     tri_index(t, r, c);
-    double s = 0.0;
-    for (int i = 0; i < nv; ++i) s += V[i * nt + r] * V[i * nt + c];
-    double a = kap * K[r * nt + c] - s;
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      s0 = fma(V[i * nt + r], V[i * nt + c], s0);
+      s1 = fma(V[(i + 1) * nt + r], V[(i + 1) * nt + c], s1);
+    }
+    if (i < nv) s0 = fma(V[i * nt + r], V[i * nt + c], s0);
+    double a = fma(kap, K[r * nt + c], -(s0 + s1));
     if (r == c) a += tau;
     A[(size_t)t * nE + e] = a;
   }
   if (Lfac) {
-    const int nsl = nv * (nv + 1) / 2;
-    for (int t = lane; t < nsl; t += 32) {
+    for (int t = tid; t < nsv; t += NT) {
       int r, c;
       tri_index(t, r, c);
       Lfac[(size_t)t * nE + e] = S[r * nv + c];
@@ -549,20 +556,15 @@ void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap) {
 void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
                      int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t per_warp = sizeof(double) * (size_t)(nv * nv + nv * nt);
-  int wpb = (int)((200 * 1024) / per_warp);
-  if (wpb > 8) wpb = 8;
-  if (wpb < 1) wpb = 1;
-  const size_t shm = per_warp * wpb;
+  const size_t shm = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
   static const bool attr_set = [] {
     cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     return true;
   }();
   (void)attr_set;
-  const int blocks = (nE + wpb - 1) / wpb;
   note_launch();
-  condense_kernel<<<blocks, 32 * wpb, shm, s>>>(nv, nt, nE, wpb, ref.G, ref.E, ref.H, ref.F, ref.K,
-                                                 kap, tau_mode, tau_c, hmin, A, Lfac, err);
+  condense_kernel<<<nE, kSymThreads, shm, s>>>(nv, nt, nE, ref.G, ref.E, ref.H, ref.F, ref.K, kap,
+                                               tau_mode, tau_c, hmin, A, Lfac, err);
 }
 
 void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
