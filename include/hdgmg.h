@@ -139,6 +139,10 @@ typedef struct {
   int32_t refinements;    /* FP32_IR: outer FP64 refinement steps, else 0    */
   double t_condense_ms;   /* device time of the element condensation kernel
                              in the last hdgmg_setup (CUDA events around it) */
+  int32_t condense_threads; /* threads per element the condensation kernel
+                             ran with: picked once per (kernel, p, device) by
+                             timing 32/64/128/256 on the first set-up; the
+                             result does not depend on it                     */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

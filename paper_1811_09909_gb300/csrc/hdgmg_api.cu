@@ -94,6 +94,7 @@ struct hdgmg_ctx {
   bool setup_done = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   double t_setup_ms = 0.0, t_condense_ms = 0.0;
+  int condense_threads = 0;    // autotuned threads per element of the condensation kernel
   // PCG loop as one CUDA graph with a device-evaluated while condition
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t cg_graph = nullptr;
@@ -1180,12 +1181,19 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
   Level& L0 = c->levels[0];
   launch_kappa(s, nE, c->logk, c->kap);
-  CUDA_TRY(cudaEventRecord(c->evk0, s));
-  if (c->ns)
-    launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err);
-  else
-    launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
-                    L0.d64.A, c->Lfac, c->err);
+  // the first set-up of a (kernel, p) pair times the candidate block sizes
+  // before the condensation proper (outside the timed condensation events)
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool tune_only = pass == 0;
+    if (!tune_only) CUDA_TRY(cudaEventRecord(c->evk0, s));
+    if (c->ns)
+      c->condense_threads = launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A,
+                                               c->Lfac, c->err, tune_only);
+    else
+      c->condense_threads =
+          launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                          L0.d64.A, c->Lfac, c->err, tune_only);
+  }
   CUDA_TRY(cudaEventRecord(c->evk1, s));
   STATUS_TRY(check_launch("condensation"));
   if (c->opts.precision != HDGMG_PREC_FP64) {
@@ -1214,6 +1222,37 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   return HDGMG_OK;
 }
 
+}  // extern "C"
+
+namespace hdgmg {
+// Make the condensation autotuner's choice for this context's (kernel, p)
+// on its stream, synchronously; the batch set-up calls it for one problem of
+// each kind before running the set-ups concurrently, so that concurrent work
+// does not disturb the timings.
+hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa) {
+  cudaStream_t s = c->stream;
+  const int nE = c->n * c->n;
+  CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
+  launch_kappa(s, nE, c->logk, c->kap);
+  Level& L0 = c->levels[0];
+  if (c->ns)
+    launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
+  else
+    launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+                    L0.d64.A, c->Lfac, c->err, true);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return check_launch("condensation tuning");
+}
+bool condensation_kind(const hdgmg_ctx* c, int* p, int* ns) {
+  *p = c->p;
+  *ns = c->ns ? 1 : 0;
+  return true;
+}
+}  // namespace hdgmg
+
+extern "C" {
+
 hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const double* g_D,
                          double* lambda, double* u, double* q, hdgmg_info* info) {
   if (!c || !f || !lambda) return fail(HDGMG_EINVAL, "NULL argument");
@@ -1240,6 +1279,7 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     info->t_solve_ms = ms;
     info->t_setup_ms = c->t_setup_ms;
     info->t_condense_ms = c->t_condense_ms;
+    info->condense_threads = c->condense_threads;
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }

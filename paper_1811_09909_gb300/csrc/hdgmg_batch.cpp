@@ -135,6 +135,18 @@ hdgmg_status hdgmg_batch_create(hdgmg_batch** out, int32_t nprob, const hdgmg_pr
 
 hdgmg_status hdgmg_batch_setup(hdgmg_batch* b, const double* const* log_kappa) {
   if (!b || !log_kappa) return bfail(HDGMG_EINVAL, "NULL argument");
+  // one synchronous autotuning pass per distinct (p, operator kind) first, on
+  // an otherwise idle device, then the set-ups run concurrently
+  if (cudaStreamSynchronize(b->user) != cudaSuccess) return bfail(HDGMG_ECUDA, "stream sync");
+  std::vector<std::pair<int, int>> seen;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    int p = 0, ns = 0;
+    hdgmg::condensation_kind(b->ctx[i], &p, &ns);
+    if (std::find(seen.begin(), seen.end(), std::make_pair(p, ns)) != seen.end()) continue;
+    seen.emplace_back(p, ns);
+    hdgmg_status st = hdgmg::tune_condensation(b->ctx[i], log_kappa[i]);
+    if (st != HDGMG_OK) return st;
+  }
   return for_each_problem(b, [&](int i) { return hdgmg_setup(b->ctx[i], log_kappa[i]); });
 }
 

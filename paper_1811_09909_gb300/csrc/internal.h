@@ -90,9 +90,11 @@ struct RefDevice {     // device copies of RefElement tables (FP64)
 
 // kap = exp(log kappa) per element; the element kernels take kap
 void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap);
-void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE,
-                     const double* kap, int tau_mode, double tau_c, double hmin,
-                     double* A, double* Lfac, int* err);
+// returns the autotuned threads per element; tune_only: only make sure the
+// choice for this (kernel, p) is made (times the candidates on a sample)
+int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE,
+                    const double* kap, int tau_mode, double tau_c, double hmin,
+                    double* A, double* Lfac, int* err, bool tune_only = false);
 void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n,
                 const double* kap, int tau_mode, double tau_c, double hmin,
                 const double* Lfac, const double* f, double* b);
@@ -114,8 +116,8 @@ struct CdTables {
 void build_cd_tables(const RefElement& R, double tau, double bx, double by,
                      std::vector<double>& S0, std::vector<double>& W0, std::vector<double>& V0,
                      std::vector<double>& adiag);
-void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
-                        const double* kap, double* A, double* LU, int* err);
+int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
+                       const double* kap, double* A, double* LU, int* err, bool tune_only = false);
 void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
                    const double* kap, const double* LU, const double* f, double* b);
 void launch_recover_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
@@ -334,6 +336,10 @@ void launch_gm_givens(cudaStream_t s, double* H, int ldh, double* cs, double* sn
                       int* total, int max_total);
 void launch_gm_update(cudaStream_t s, int64_t len, const double* Z, int nk, const double* y,
                       double* x);
+
+// condensation autotuning of one context, synchronously (hdgmg_api.cu)
+hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa);
+bool condensation_kind(const hdgmg_ctx* c, int* p, int* ns);
 
 // set the calling thread's hdgmg_last_error() message
 void set_last_error(const std::string& msg);

@@ -8,6 +8,9 @@
 //   K5: g_e = W^T S^-1 (M f_e), assembled into the edge vector.
 //   K12: u_e = S^-1 (M f_e + W lambda_e),  q_d = kappa M^-1 (B_d^T u - C_d lambda_e).
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -38,21 +41,21 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-// K1: one block of kSymThreads (two warps) per element, the local matrices in
-// shared memory.  S: nv x nv (full square, lower part used), V: nv x nt.
-// The FP64 pipe is the bottleneck on GB300, so every pivot's square root and
-// reciprocal is computed once (thread 0) and read by all threads.
-constexpr int kSymThreads = 64;
-
-__global__ void __launch_bounds__(kSymThreads) condense_kernel(
-    int nv, int nt, int nE, const double* __restrict__ G, const double* __restrict__ Eb,
+// K1: one block of NT threads per element, the local matrices in shared
+// memory.  S: nv x nv (full square, lower part used), V: nv x nt.  The FP64
+// pipe is the bottleneck on GB300, so every pivot's square root and
+// reciprocal is computed once (thread 0) and read by all threads.  NT is
+// picked per (kernel, p) by a timing autotuner (tune_threads below); the
+// result does not depend on it.  Elements e_begin + blockIdx.x.
+template <int NT>
+__global__ void __launch_bounds__(NT) condense_kernel(
+    int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ Eb,
     const double* __restrict__ H, const double* __restrict__ F, const double* __restrict__ K,
     const double* __restrict__ kapv, int tau_mode, double tau_c, double hmin,
     double* __restrict__ A, double* __restrict__ Lfac, int* __restrict__ err) {
   extern __shared__ double smem[];
-  constexpr int NT = kSymThreads;
   const int tid = threadIdx.x;
-  const int e = blockIdx.x;
+  const int e = e_begin + blockIdx.x;
   if (e >= nE) return;
   double* S = smem;
   double* V = S + nv * nv;
@@ -143,7 +146,7 @@ __device__ __forceinline__ double recip_newton(double d) {
   return y;
 }
 
-// K1 (non-symmetric): one block of kCdThreads (two warps) per element.  The
+// K1 (non-symmetric): one block of NT threads per element (autotuned).  The
 // element-independent parts (tau is the same on every element of the
 // uniform mesh, beta is constant) come precomputed, so every entry of S, W
 // and V costs one FMA:
@@ -154,20 +157,18 @@ __device__ __forceinline__ double recip_newton(double d) {
 // back substitution gives X = S^-1 W.  The factors are kept for K5/K12 as
 // [nv*nv][nE]: unit lower part below the diagonal, U above it and the
 // reciprocal pivots 1/u_kk on the diagonal.  Shared memory per element bounds
-// the residency on GB300 (p = 6: 31 KB), so two warps share each element to
-// double the warps per SM that feed the FP64 pipe.
-constexpr int kCdThreads = 64;
-
-__global__ void __launch_bounds__(kCdThreads) condense_cd_kernel(
-    int nv, int nt, int nE, const double* __restrict__ G, const double* __restrict__ H,
+// the residency on GB300 (p = 6: 31 KB), so several warps share each element
+// to raise the warps per SM that feed the FP64 pipe.
+template <int NT>
+__global__ void __launch_bounds__(NT) condense_cd_kernel(
+    int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ H,
     const double* __restrict__ K, const double* __restrict__ S0, const double* __restrict__ W0,
     const double* __restrict__ V0, const double* __restrict__ adiag,
     const double* __restrict__ kapv, double* __restrict__ A, double* __restrict__ LU,
     int* __restrict__ err) {
   extern __shared__ double smem[];
   const int tid = threadIdx.x;
-  constexpr int NT = kCdThreads;
-  const int e = blockIdx.x;
+  const int e = e_begin + blockIdx.x;
   if (e >= nE) return;
   const int nvv = nv * nv, nvt = nv * nt;
   const int ns = nvv > nvt ? nvv : nvt;     // S, later V (n_v x n_t)
@@ -553,33 +554,117 @@ void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap) {
   kappa_kernel<<<(nE + 255) / 256, 256, 0, s>>>(nE, logk, kap);
 }
 
-void launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
-                     int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err) {
-  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t shm = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
-  static const bool attr_set = [] {
-    cudaFuncSetAttribute(condense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    return true;
-  }();
-  (void)attr_set;
-  note_launch();
-  condense_kernel<<<nE, kSymThreads, shm, s>>>(nv, nt, nE, ref.G, ref.E, ref.H, ref.F, ref.K, kap,
-                                               tau_mode, tau_c, hmin, A, Lfac, err);
+// ------------------------------------------------------------ autotuner
+// Threads per element of the condensation kernels: the candidates are timed
+// once per (kernel, p, ns, device) on the first elements of the first
+// problem that needs them (CUDA events on the caller's stream, outside any
+// capture) and the fastest is cached for the process.  The kernels give
+// bit-identical results for every candidate.
+namespace {
+constexpr int kTuneCandidates[4] = {32, 64, 128, 256};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+template <typename Launch>
+int tune_threads(cudaStream_t s, int kind, int p, int nE, size_t shm, Launch launch) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(kind, p, dev);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned.find(key);
+  if (it != g_tuned.end()) return it->second;
+  int best = 64;
+  if (shm <= 220 * 1024) {
+    const int sample = nE < 16384 ? nE : 16384;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    float best_ms = 1e30f;
+    for (int nt : kTuneCandidates) {
+      launch(nt, 0, sample);                       // warm-up
+      cudaEventRecord(t0, s);
+      launch(nt, 0, sample);
+      cudaEventRecord(t1, s);
+      if (cudaEventSynchronize(t1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = nt;
+      }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+  }
+  g_tuned[key] = best;
+  return best;
 }
 
-void launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
-                        const double* kap, double* A, double* LU, int* err) {
+template <int NT>
+void set_smem_attr_sym() {
+  static const bool done = [] {
+    cudaFuncSetAttribute(condense_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    return true;
+  }();
+  (void)done;
+}
+template <int NT>
+void set_smem_attr_cd() {
+  static const bool done = [] {
+    cudaFuncSetAttribute(condense_cd_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+    return true;
+  }();
+  (void)done;
+}
+}  // namespace
+
+int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
+                    int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err,
+                    bool tune_only) {
+  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const size_t shm = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
+  auto launch = [&](int threads, int e0, int count) {
+    note_launch();
+    switch (threads) {
+#define CASE(NT)                                                                              \
+  case NT:                                                                                    \
+    set_smem_attr_sym<NT>();                                                                  \
+    condense_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.E, ref.H, ref.F, ref.K, \
+                                               kap, tau_mode, tau_c, hmin, A, Lfac, err);     \
+    break;
+      CASE(32) CASE(64) CASE(128) CASE(256)
+#undef CASE
+      default: break;
+    }
+  };
+  const int threads = tune_threads(s, 0, p, nE, shm, launch);
+  if (!tune_only) launch(threads, 0, nE);
+  return threads;
+}
+
+int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
+                       const double* kap, double* A, double* LU, int* err, bool tune_only) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const size_t shm =
       sizeof(double) * (size_t)((nv * nv > nv * nt ? nv * nv : nv * nt) + nv * nt + nv);
-  static const bool attr_set = [] {
-    cudaFuncSetAttribute(condense_cd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    return true;
-  }();
-  (void)attr_set;
-  note_launch();
-  condense_cd_kernel<<<nE, kCdThreads, shm, s>>>(nv, nt, nE, ref.G, ref.H, ref.K, cd.S0, cd.W0, cd.V0,
-                                                 cd.adiag, kap, A, LU, err);
+  auto launch = [&](int threads, int e0, int count) {
+    note_launch();
+    switch (threads) {
+#define CASE(NT)                                                                                  \
+  case NT:                                                                                        \
+    set_smem_attr_cd<NT>();                                                                       \
+    condense_cd_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.H, ref.K, cd.S0,     \
+                                                  cd.W0, cd.V0, cd.adiag, kap, A, LU, err);       \
+    break;
+      CASE(32) CASE(64) CASE(128) CASE(256)
+#undef CASE
+      default: break;
+    }
+  };
+  const int threads = tune_threads(s, 1, p, nE, shm, launch);
+  if (!tune_only) launch(threads, 0, nE);
+  return threads;
 }
 
 void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,
