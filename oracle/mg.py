@@ -20,7 +20,14 @@ sparse matrix, in the order the paper defines them:
   A_II^-1 is found by splitting A_II into the connected components of its
   sparsity graph and inverting each dense component.
 * Sec. 3.3 smoothing steps m_{k-1} = beta m_k (beta = 2 in Sec. 4; optionally
-  capped); Sec. 4.1 block-Jacobi with one block per edge, undamped by default.
+  capped); Sec. 4.1 smoothers: block-Jacobi with one block per edge
+  (undamped by default), damped point-Jacobi (omega = 2/3 in the paper),
+  Chebyshev-accelerated point-Jacobi on [Lambda_max / 30, Lambda_max] with
+  Lambda_max from a power iteration on D^-1 A, and LU-SGS (one forward and
+  one backward point Gauss-Seidel sweep per step).  The Gauss-Seidel order is
+  multicolour by edge: vertical edges with even column, vertical odd,
+  horizontal with even row, horizontal odd (edges of one colour share no
+  element), then edge number, then mode; the paper does not state its order.
 * Sec. 3.4 local correction T_k = diag(A_II^-1, 0) (eq. localCorrection).
 * Sec. 3.6 Algorithm 1 (V-cycle) with B_1 = A_1^-1 by a dense Cholesky
   factorisation (a dense LU with partial pivoting for the non-symmetric
@@ -45,6 +52,7 @@ at p = 1 (Example I, table without local correction).
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 import scipy.sparse.csgraph as csgraph
 
 from . import hdg as H
@@ -108,6 +116,43 @@ class Level:
     pass
 
 
+SMOOTHERS = ("block_jacobi", "point_jacobi", "chebyshev", "lu_sgs")
+POWER_ITERS = 30          # power iterations for Lambda_max (Chebyshev)
+
+
+def power_start(n, nd, free):
+    """Deterministic start vector of the power iteration on the free dofs:
+    dof (edge e, mode k) of a mesh with E edges gets 1 + (h mod 1024) / 1024,
+    h = (i * 2654435761) mod 2^32 with i = k E + e (the library's layout
+    index).  Shared definition, so both sides start from the same vector."""
+    ne = H.n_edges(n)
+    e, k = np.divmod(free, nd)
+    i = (k * ne + e).astype(np.uint64)
+    h = (i * np.uint64(2654435761)) % np.uint64(1 << 32)
+    return 1.0 + (h % np.uint64(1024)).astype(np.float64) / 1024.0
+
+
+def lambda_max_power(A, dinv, x0, iters=POWER_ITERS):
+    """Largest eigenvalue of D^-1 A by power iteration: x <- y / |y|,
+    y = D^-1 A x, estimate |y| for the unit x of the last step."""
+    x = x0 / np.linalg.norm(x0)
+    lam = 0.0
+    for _ in range(iters):
+        y = dinv * (A @ x)
+        lam = np.linalg.norm(y)
+        x = y / lam
+    return lam
+
+
+def colour_order(n, nd, free):
+    """Positions of the free dofs in LU-SGS order (colour, edge, mode)."""
+    nvert = n * (n + 1)
+    e, k = np.divmod(free, nd)
+    vert = e < nvert
+    col = np.where(vert, (e % (n + 1)) % 2, 2 + ((e - nvert) // n) % 2)
+    return np.lexsort((k, e, col))
+
+
 class Hierarchy:
     """Multigrid hierarchy built from the fine trace system of an HDGProblem.
 
@@ -118,7 +163,10 @@ class Hierarchy:
     pure-Neumann operators, singular; used only to check the hierarchy)."""
 
     def __init__(self, problem, Ae=None, coarsest_n=2, m_fine=1, m_growth=2, m_max=None,
-                 local_corr="pre", omega=1.0, dirichlet=True):
+                 local_corr="pre", omega=1.0, dirichlet=True, smoother="block_jacobi"):
+        if smoother not in SMOOTHERS:
+            raise ValueError(f"unknown smoother {smoother}")
+        self.smoother = smoother
         self.problem = problem
         self.dirichlet = dirichlet
         self.local_corr = local_corr
@@ -168,6 +216,8 @@ class Hierarchy:
                 m = min(m, m_max)
         for lev in levels:
             lev.Dinv = self._block_jacobi(lev) if dirichlet else None
+            if dirichlet and lev.A.shape[0]:
+                self._smoother_setup(lev)
         coarse = levels[-1]
         coarse.chol = coarse.lu = None
         if coarse.A.shape[0] and dirichlet:
@@ -234,6 +284,49 @@ class Hierarchy:
         Lc.A = (L.Q @ A @ L.I).tocsr()                  # eq. coarse
         levels.append(Lc)
 
+    def _smoother_setup(self, L):
+        A = L.A.tocsr()
+        L.dpt = 1.0 / A.diagonal()
+        if self.smoother == "chebyshev":
+            L.lmax = lambda_max_power(A, L.dpt, power_start(L.n, L.nd, L.free))
+        if self.smoother == "lu_sgs":
+            order = colour_order(L.n, L.nd, L.free)
+            P = sp.csr_matrix((np.ones(len(order)), (np.arange(len(order)), order)),
+                              shape=(len(order), len(order)))
+            Ap = (P @ A @ P.T).tocsr()
+            L.gs_P = P
+            L.gs_lower = sp.tril(Ap, 0).tocsr()        # D + L in colour order
+            L.gs_upper = sp.triu(Ap, 0).tocsr()        # D + U
+
+    def smooth(self, L, r, e, steps):
+        """`steps` smoothing iterations on A e = r from e."""
+        A = L.A
+        for _ in range(steps) if self.smoother != "chebyshev" else range(1):
+            if self.smoother == "block_jacobi":
+                e = e + self.omega * (L.Dinv @ (r - A @ e))
+            elif self.smoother == "point_jacobi":
+                e = e + self.omega * L.dpt * (r - A @ e)
+            elif self.smoother == "lu_sgs":
+                P = L.gs_P
+                res = P @ (r - A @ e)
+                e = e + P.T @ spla.spsolve_triangular(L.gs_lower, res, lower=True)
+                res = P @ (r - A @ e)
+                e = e + P.T @ spla.spsolve_triangular(L.gs_upper, res, lower=False)
+        if self.smoother == "chebyshev":
+            lmax = L.lmax
+            lmin = lmax / 30.0
+            theta, delta = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+            sigma = theta / delta
+            rho = 1.0 / sigma
+            d = L.dpt * (r - A @ e) / theta
+            e = e + d
+            for _ in range(steps - 1):
+                rho_new = 1.0 / (2.0 * sigma - rho)
+                d = rho_new * rho * d + (2.0 * rho_new / delta) * L.dpt * (r - A @ e)
+                e = e + d
+                rho = rho_new
+        return e
+
     @staticmethod
     def _block_jacobi(L):
         nd = L.nd
@@ -256,18 +349,14 @@ class Hierarchy:
                 return sla.cho_solve(L.chol, r)
             return sla.lu_solve(L.lu, r) if L.lu is not None else np.zeros_like(r)
         A = L.A
-        e = np.zeros_like(r)
-        for _ in range(L.m):                                     # step 2
-            e = e + self.omega * (L.Dinv @ (r - A @ e))
+        e = self.smooth(L, r, np.zeros_like(r), L.m)             # step 2
         if L.T is not None and self.local_corr in ("pre", "both"):
             e = e + L.T @ (r - A @ e)                            # step 3
         rc = L.Q @ (r - A @ e)                                   # step 4
         e = e + L.I @ self.vcycle(rc, k + 1)
         if L.T is not None and self.local_corr == "both":
             e = e + L.T @ (r - A @ e)                            # step 5
-        for _ in range(L.m):                                     # step 6
-            e = e + self.omega * (L.Dinv @ (r - A @ e))
-        return e
+        return self.smooth(L, r, e, L.m)                         # step 6
 
     # ------------------------------------------------------------------
     # outer iterations (Sec. 3.6 and Sec. 4); b, x on the fine free dofs
