@@ -66,6 +66,9 @@ enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
 enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1, HDGMG_KRYLOV_GMRES = 2 };
 enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2, HDGMG_PREC_BF16 = 3 };
 enum { HDGMG_PDE_DIFFUSION = 0, HDGMG_PDE_CONVDIFF = 1 };
+/* smoothers of Sec. 4.1 */
+enum { HDGMG_SMOOTH_BLOCK_JACOBI = 0, HDGMG_SMOOTH_POINT_JACOBI = 1,
+       HDGMG_SMOOTH_CHEBYSHEV = 2, HDGMG_SMOOTH_LU_SGS = 3 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
 
@@ -124,6 +127,18 @@ typedef struct {
                              memory); <= 0: not used (the single-block tail
                              and separate launches are faster on GB300); 0   */
   int32_t gmres_restart;  /* GMRES restart length m, 1..256; 30              */
+  int32_t smoother;       /* HDGMG_SMOOTH_*, Sec. 4.1: BLOCK_JACOBI (one block
+                             per edge, damped by omega), POINT_JACOBI (damped
+                             by omega; the paper uses 2/3), CHEBYSHEV
+                             (point-Jacobi accelerated on [L/30, L], L the
+                             largest eigenvalue of D^-1 A from 30 power
+                             iterations at set-up), LU_SGS (one forward and
+                             one backward point Gauss-Seidel sweep per step,
+                             multicolour edge order: vertical edges of even,
+                             odd column, horizontal of even, odd row; then
+                             mode).  The fused single-block tail and the
+                             fused edge sweeps serve BLOCK_JACOBI only;
+                             BLOCK_JACOBI                                    */
 } hdgmg_opts;
 
 typedef struct {

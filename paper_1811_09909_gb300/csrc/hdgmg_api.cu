@@ -365,7 +365,53 @@ void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y, const T* xadd = nullptr
 // fused tail, not the coarsest level)
 bool p1_launched(hdgmg_ctx* c, int l) {
   const Level& L = c->levels[l];
-  return L.nd == 2 && L.transfer == 2 && !L.A16 && l != c->tail_start && l != c->ctail_start;
+  return c->opts.smoother == HDGMG_SMOOTH_BLOCK_JACOBI && L.nd == 2 && L.transfer == 2 && !L.A16 &&
+         l != c->tail_start && l != c->ctail_start;
+}
+
+// m smoothing steps of the point smoothers on level l (steps 2 and 6 of
+// Algorithm 1); from_zero: e is taken as zero (pre-smoothing)
+template <typename T>
+void smooth_point(hdgmg_ctx* c, int l, bool from_zero) {
+  cudaStream_t s = c->stream;
+  Level& L = c->levels[l];
+  LevelData<T>& D = ld<T>(L);
+  const T omega = (T)c->opts.omega;
+  switch (c->opts.smoother) {
+    case HDGMG_SMOOTH_POINT_JACOBI: {
+      int i = 0;
+      if (from_zero) {
+        launch_pj_update<T>(s, L.n, L.nd, D.Dpt, D.r, D.y, D.e, omega, 1);
+        i = 1;
+      }
+      for (; i < L.m; ++i) {
+        level_matvec<T>(c, l, D.e, D.y);
+        launch_pj_update<T>(s, L.n, L.nd, D.Dpt, D.r, D.y, D.e, omega, 0);
+      }
+      break;
+    }
+    case HDGMG_SMOOTH_CHEBYSHEV:
+      for (int k = 0; k < L.m; ++k) {
+        if (k == 0 && from_zero) {
+          launch_cheb_update<T>(s, L.n, L.nd, D.Dpt, D.r, D.y, D.e, D.cd, L.cheb, 0, 1, 1);
+        } else {
+          level_matvec<T>(c, l, D.e, D.y);
+          launch_cheb_update<T>(s, L.n, L.nd, D.Dpt, D.r, D.y, D.e, D.cd, L.cheb, k, 0, k == 0);
+        }
+      }
+      break;
+    case HDGMG_SMOOTH_LU_SGS:
+      if (from_zero) cudaMemsetAsync(D.e, 0, sizeof(T) * (size_t)L.nd * L.nEdge, s);
+      for (int i = 0; i < L.m; ++i) {
+        for (int col = 0; col < 4; ++col)
+          launch_gs_colour<T>(s, L.n, L.nd, c->ns, ld<T>(L).A, D.Dpt, D.r, D.e, col, 0);
+        for (int col = 3; col >= 0; --col)
+          launch_gs_colour<T>(s, L.n, L.nd, c->ns, ld<T>(L).A, D.Dpt, D.r, D.e, col, 1);
+      }
+      break;
+    default:
+      break;
+  }
 }
 
 // rp_r0/rp_y0/rp_nd0: the p-level above left its restriction J_N^T (r - A e)
@@ -391,7 +437,7 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   const T omega = (T)c->opts.omega;
   const int lc = c->opts.local_corr;
   const bool ns = c->ns;
-  if (L.nd == 2 && L.transfer == 2 && !L.A16) {
+  if (p1_launched(c, l)) {
     // P1 level: fused edge-centric sweeps, ping-ponging between e and y.  The
     // first sweep (from e = 0) writes y; after the 2m - 1 sweeps of the level
     // the correction is back in e.
@@ -421,11 +467,16 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
     }
     return;                                    // cur == 0: the correction is in D.e
   }
+  const bool bj = c->opts.smoother == HDGMG_SMOOTH_BLOCK_JACOBI;
   // step 2: pre-smoothing (the first sweep starts from e = 0)
-  launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
-  for (int i = 1; i < L.m; ++i) {
-    level_matvec<T>(c, l, D.e, D.y);
-    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
+  if (bj) {
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
+    for (int i = 1; i < L.m; ++i) {
+      level_matvec<T>(c, l, D.e, D.y);
+      launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
+    }
+  } else {
+    smooth_point<T>(c, l, true);
   }
   // step 3: local correction (interior edges of the next level's macro-elements)
   if (L.transfer == 2 && lc != HDGMG_LC_NONE)
@@ -456,6 +507,10 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   if (L.transfer == 2 && lc == HDGMG_LC_BOTH)
     launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
   // step 6: post-smoothing (the first step also adds the pending J_N e_c)
+  if (!bj) {
+    smooth_point<T>(c, l, false);
+    return;
+  }
   for (int i = 0; i < L.m; ++i) {
     level_matvec<T>(c, l, D.e, D.y, i == 0 ? xadd : nullptr);
     launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, i == 0 ? xadd : nullptr);
@@ -504,6 +559,14 @@ hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
   CUDA_TRY(cudaMemset(D.y, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
   CUDA_TRY(cudaMemset(D.r, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
   CUDA_TRY(cudaMemset(D.e, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+  if (c->opts.smoother != HDGMG_SMOOTH_BLOCK_JACOBI && L.transfer != 0) {
+    CUDA_TRY(c->alloc(&D.Dpt, (size_t)L.nd * L.nEdge));
+    if (c->opts.smoother == HDGMG_SMOOTH_CHEBYSHEV) {
+      CUDA_TRY(c->alloc(&D.cd, (size_t)L.nd * L.nEdge));
+      CUDA_TRY(cudaMemset(D.cd, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+      if (!L.cheb) CUDA_TRY(c->alloc(&L.cheb, 2 * (size_t)L.m));
+    }
+  }
   if (L.transfer == 2) {
     const size_t nC = (size_t)L.nE / 4;
     CUDA_TRY(c->alloc(&D.AIIinv, (c->ns ? 64 : 36) * nC));
@@ -515,6 +578,53 @@ hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
       D.Rt = D.Pi;                     // Q_{k-1} = I_k^T for symmetric A
   }
   return HDGMG_OK;
+}
+
+// Point smoothers: 1 / A_aa on every non-coarsest level; for Chebyshev also
+// Lambda_max of D^-1 A by 30 power iterations (from the deterministic start
+// vector, on the level's own vectors) and the step coefficients
+//   theta = (L + L/30)/2, delta = (L - L/30)/2, sigma = theta/delta,
+//   k = 0: d = D^-1 res / theta;  k >= 1: rho_k = 1/(2 sigma - rho_{k-1}),
+//   d = rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 res,   rho_0 = 1/sigma.
+constexpr int kPowerIters = 30;
+
+template <typename T>
+hdgmg_status setup_point_smoother(hdgmg_ctx* c) {
+  cudaStream_t s = c->stream;
+  const int nl = (int)c->levels.size();
+  for (int l = 0; l + 1 < nl; ++l) {
+    Level& L = c->levels[l];
+    LevelData<T>& D = ld<T>(L);
+    launch_point_diag<T>(s, L.n, L.nd, c->ns, D.A, D.Dpt);
+    if (c->opts.smoother != HDGMG_SMOOTH_CHEBYSHEV) continue;
+    const int64_t len = (int64_t)L.nd * L.nEdge;
+    launch_power_start<T>(s, L.n, L.nd, D.e);
+    for (int it = 0; it < kPowerIters; ++it) {
+      CUDA_TRY(cudaMemsetAsync(D.y, 0, sizeof(T) * len, s));
+      launch_matvec<T>(s, L.n, L.nd, c->ns, D.A, D.e, D.y, T(1));
+      launch_scale_by<T>(s, len, D.Dpt, D.y);
+      launch_dot<T>(s, len, D.y, D.y, c->partial, c->scal + 7);
+      launch_normalize<T>(s, len, D.y, c->scal + 7, D.e);
+    }
+    CUDA_TRY(cudaMemsetAsync(D.y, 0, sizeof(T) * len, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scal_h + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    L.lmax = std::sqrt(c->scal_h[7]);
+    const double lmin = L.lmax / 30.0;
+    const double theta = 0.5 * (L.lmax + lmin), delta = 0.5 * (L.lmax - lmin);
+    const double sigma = theta / delta;
+    std::vector<double> coef(2 * (size_t)L.m, 0.0);
+    double rho = 1.0 / sigma;
+    coef[1] = 1.0 / theta;
+    for (int k = 1; k < L.m; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      coef[2 * k] = rn * rho;
+      coef[2 * k + 1] = 2.0 * rn / delta;
+      rho = rn;
+    }
+    CUDA_TRY(cudaMemcpy(L.cheb, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+  }
+  return check_launch("point smoother set-up");
 }
 
 template <typename T>
@@ -532,6 +642,8 @@ hdgmg_status setup_hierarchy(hdgmg_ctx* c) {
     else
       launch_agglomerate<T>(s, Lc.n, c->ns, D.A, Dc.A, D.AIIinv, D.Y, D.Pi, D.Rt, c->err);
   }
+  if (c->opts.smoother != HDGMG_SMOOTH_BLOCK_JACOBI)
+    STATUS_TRY(setup_point_smoother<T>(c));
   Level& Lc = c->levels[nl - 1];
   if (!launch_coarse_setup_smem<T>(s, Lc.n, c->ns, ld<T>(Lc).A, c->freeidx, c->nf, c->cinv,
                                    c->err)) {
@@ -926,6 +1038,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->inner_rtol = 1e-5;
   o->cluster_tail_n = 0;
   o->gmres_restart = 30;
+  o->smoother = HDGMG_SMOOTH_BLOCK_JACOBI;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -981,6 +1094,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.krylov == HDGMG_KRYLOV_GMRES && (o.gmres_restart < 1 || o.gmres_restart > 256))
     return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
   if (o.precision < 0 || o.precision > 3) return fail(HDGMG_EINVAL, "unknown precision");
+  if (o.smoother < 0 || o.smoother > 3) return fail(HDGMG_EINVAL, "unknown smoother");
   if (P.pde == HDGMG_PDE_CONVDIFF && o.krylov == HDGMG_KRYLOV_CG)
     return fail(HDGMG_EINVAL, "krylov CG needs a symmetric operator; use GMRES for convection-diffusion");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
@@ -1161,6 +1275,10 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   }
   if (c->ctail_start >= 0 && c->tail_start >= 0 && c->tail_start < c->ctail_start)
     c->ctail_start = -1;                     // keep whichever fuses more levels
+  if (o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) {
+    c->tail_start = -1;                      // the fused tails implement block-Jacobi only
+    c->ctail_start = -1;
+  }
   CTRY(cudaEventCreate(&c->ev0));
   CTRY(cudaEventCreate(&c->ev1));
   CTRY(cudaEventCreate(&c->evk0));

@@ -66,6 +66,9 @@ struct LevelData {
   T* r = nullptr;        // level right-hand side   [nd][nEdge]
   T* e = nullptr;        // level correction        [nd][nEdge]
   T* y = nullptr;        // matvec accumulator      [nd][nEdge] (kept zero)
+  // point smoothers: 1 / A_aa per dof and the Chebyshev direction
+  T* Dpt = nullptr;      // [nd][nEdge]
+  T* cd = nullptr;       // [nd][nEdge]
 };
 
 struct Level {
@@ -79,6 +82,10 @@ struct Level {
   LevelData<double> d64;
   LevelData<float> d32;
   __nv_bfloat16* A16 = nullptr;   // BF16 copy of A (finest level, PREC_BF16)
+  // Chebyshev smoother: Lambda_max of D^-1 A and the step coefficients
+  // [c1_k, c2_k] of d_k = c1_k d_{k-1} + c2_k D^-1 (r - A e), k < m (device)
+  double lmax = 0.0;
+  double* cheb = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -340,6 +347,30 @@ void launch_gm_update(cudaStream_t s, int64_t len, const double* Z, int nk, cons
 // condensation autotuning of one context, synchronously (hdgmg_api.cu)
 hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa);
 bool condensation_kind(const hdgmg_ctx* c, int* p, int* ns);
+
+// point smoothers (k_mg.cu); generic in nd, element operators packed or full
+template <typename T>
+void launch_point_diag(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dpt);
+// e = omega Dpt r (first) or e += omega Dpt (r - y), y := 0
+template <typename T>
+void launch_pj_update(cudaStream_t s, int n, int nd, const T* Dpt, const T* r, T* y, T* e, T omega,
+                      int first);
+// d = c1_k d + c2_k Dpt (r - y) (first_d: d = c2_k Dpt (r - y)), e += d
+// (first_e: e = d; y is then not read), y := 0
+template <typename T>
+void launch_cheb_update(cudaStream_t s, int n, int nd, const T* Dpt, const T* r, T* y, T* e, T* d,
+                        const double* coef, int k, int first_e, int first_d);
+// one colour of a point Gauss-Seidel sweep, in place on e
+template <typename T>
+void launch_gs_colour(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* Dpt, const T* r,
+                      T* e, int colour, int backward);
+// power iteration helpers: x = start vector; y *= Dpt; x = y / sqrt(*nrm2)
+template <typename T>
+void launch_power_start(cudaStream_t s, int n, int nd, T* x);
+template <typename T>
+void launch_scale_by(cudaStream_t s, int64_t len, const T* Dpt, T* y);
+template <typename T>
+void launch_normalize(cudaStream_t s, int64_t len, const T* y, const double* nrm2, T* x);
 
 // set the calling thread's hdgmg_last_error() message
 void set_last_error(const std::string& msg);

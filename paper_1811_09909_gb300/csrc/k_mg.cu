@@ -995,6 +995,149 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
   }
 }
 
+// ------------------------------------------------ point smoothers (Sec. 4.1)
+// The two elements sharing interior edge E, and E's local edge in each.
+__device__ __forceinline__ void edge_owners(int n, int E, int el[2], int le[2]) {
+  const int nvert = n * (n + 1);
+  if (E < nvert) {
+    const int j = E / (n + 1), i = E - j * (n + 1);
+    el[0] = j * n + i - 1; le[0] = 1;
+    el[1] = j * n + i;     le[1] = 0;
+  } else {
+    const int j = (E - nvert) / n, i = (E - nvert) - j * n;
+    el[0] = (j - 1) * n + i; le[0] = 3;
+    el[1] = j * n + i;       le[1] = 2;
+  }
+}
+
+__device__ __forceinline__ int ent(bool ns, int nl, int r, int c) {
+  return ns ? r * nl + c : pk_any(r, c);
+}
+
+// Dpt[a][E] = 1 / A_{(E,a),(E,a)} (0 on Dirichlet edges)
+template <typename T>
+__global__ void point_diag_kernel(int n, int nd, bool ns, const T* __restrict__ A,
+                                  T* __restrict__ Dpt) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge) return;
+  if (bnd_edge(n, E)) {
+    for (int a = 0; a < nd; ++a) Dpt[(size_t)a * nedge + E] = T(0);
+    return;
+  }
+  const int nE = n * n, nl = 4 * nd;
+  int el[2], le[2];
+  edge_owners(n, E, el, le);
+  for (int a = 0; a < nd; ++a) {
+    T d = T(0);
+    for (int s = 0; s < 2; ++s) {
+      const int r = le[s] * nd + a;
+      d += A[(size_t)ent(ns, nl, r, r) * nE + el[s]];
+    }
+    Dpt[(size_t)a * nedge + E] = T(1) / d;
+  }
+}
+
+template <typename T>
+__global__ void pj_update_kernel(int n, int nd, const T* __restrict__ Dpt, const T* __restrict__ r,
+                                 T* __restrict__ y, T* __restrict__ e, T omega, int first) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge || bnd_edge(n, E)) return;
+  for (int a = 0; a < nd; ++a) {
+    const size_t ix = (size_t)a * nedge + E;
+    if (first) {
+      e[ix] = omega * Dpt[ix] * r[ix];
+    } else {
+      e[ix] += omega * Dpt[ix] * (r[ix] - y[ix]);
+      y[ix] = T(0);
+    }
+  }
+}
+
+template <typename T>
+__global__ void cheb_update_kernel(int n, int nd, const T* __restrict__ Dpt, const T* __restrict__ r,
+                                   T* __restrict__ y, T* __restrict__ e, T* __restrict__ d,
+                                   const double* __restrict__ coef, int k, int first_e,
+                                   int first_d) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge || bnd_edge(n, E)) return;
+  const T c1 = (T)coef[2 * k], c2 = (T)coef[2 * k + 1];
+  for (int a = 0; a < nd; ++a) {
+    const size_t ix = (size_t)a * nedge + E;
+    const T res = first_e ? r[ix] : r[ix] - y[ix];
+    if (!first_e) y[ix] = T(0);
+    const T dn = first_d ? c2 * Dpt[ix] * res : c1 * d[ix] + c2 * Dpt[ix] * res;
+    d[ix] = dn;
+    e[ix] = first_e ? dn : e[ix] + dn;
+  }
+}
+
+// One colour of the point Gauss-Seidel sweep: the edges of a colour share no
+// element, so they update in parallel exactly as in sequential order; inside
+// an edge the modes go in order (backward: reverse order).  e in place.
+template <typename T>
+__global__ void gs_colour_kernel(int n, int nd, bool ns, const T* __restrict__ A,
+                                 const T* __restrict__ Dpt, const T* __restrict__ r,
+                                 T* __restrict__ e, int colour, int backward) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge || bnd_edge(n, E)) return;
+  const int nvert = n * (n + 1);
+  const int col = E < nvert ? (E % (n + 1)) % 2 : 2 + ((E - nvert) / n) % 2;
+  if (col != colour) return;
+  const int nE = n * n, nl = 4 * nd;
+  int el[2], le[2];
+  edge_owners(n, E, el, le);
+  int ed[2][4];
+  elem_edges(n, el[0], ed[0]);
+  elem_edges(n, el[1], ed[1]);
+  for (int t = 0; t < nd; ++t) {
+    const int a = backward ? nd - 1 - t : t;
+    T s = T(0);
+    for (int side = 0; side < 2; ++side) {
+      const int rrow = le[side] * nd + a;
+      for (int c = 0; c < nl; ++c)
+        s += A[(size_t)ent(ns, nl, rrow, c) * nE + el[side]] *
+             e[(size_t)(c % nd) * nedge + ed[side][c / nd]];
+    }
+    const size_t ix = (size_t)a * nedge + E;
+    e[ix] += (r[ix] - s) * Dpt[ix];
+  }
+}
+
+// start vector of the power iteration: 1 + (h mod 1024) / 1024 with
+// h = (i * 2654435761) mod 2^32, i = mode * n_edges + edge; 0 on Dirichlet edges
+template <typename T>
+__global__ void power_start_kernel(int n, int nd, T* __restrict__ x) {
+  const int nedge = 2 * n * (n + 1);
+  const int E = blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= nedge) return;
+  const bool b = bnd_edge(n, E);
+  for (int a = 0; a < nd; ++a) {
+    const unsigned long long i = (unsigned long long)a * nedge + E;
+    const unsigned long long h = (i * 2654435761ull) & 0xffffffffull;
+    x[(size_t)a * nedge + E] = b ? T(0) : (T)(1.0 + (double)(h % 1024ull) / 1024.0);
+  }
+}
+
+template <typename T>
+__global__ void scale_by_kernel(int64_t len, const T* __restrict__ Dpt, T* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] *= Dpt[i];
+}
+
+template <typename T>
+__global__ void normalize_kernel(int64_t len, const T* __restrict__ y, const double* __restrict__ nrm2,
+                                 T* __restrict__ x) {
+  const double inv = 1.0 / sqrt(*nrm2);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = (T)((double)y[i] * inv);
+}
+
 // ------------------------------------------------------------ vector ops
 template <typename T>
 __global__ void dot_partial_kernel(int64_t len, const T* __restrict__ a,
@@ -1345,6 +1488,57 @@ void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, c
 }
 
 template <typename T>
+void launch_point_diag(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dpt) {
+  note_launch();
+  point_diag_kernel<T><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, nd, ns, A, Dpt);
+}
+
+template <typename T>
+void launch_pj_update(cudaStream_t s, int n, int nd, const T* Dpt, const T* r, T* y, T* e, T omega,
+                      int first) {
+  note_launch();
+  pj_update_kernel<T><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, nd, Dpt, r, y, e, omega, first);
+}
+
+template <typename T>
+void launch_cheb_update(cudaStream_t s, int n, int nd, const T* Dpt, const T* r, T* y, T* e, T* d,
+                        const double* coef, int k, int first_e, int first_d) {
+  note_launch();
+  cheb_update_kernel<T><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, nd, Dpt, r, y, e, d, coef, k,
+                                                                   first_e, first_d);
+}
+
+template <typename T>
+void launch_gs_colour(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* Dpt, const T* r,
+                      T* e, int colour, int backward) {
+  note_launch();
+  gs_colour_kernel<T><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, nd, ns, A, Dpt, r, e, colour,
+                                                                 backward);
+}
+
+template <typename T>
+void launch_power_start(cudaStream_t s, int n, int nd, T* x) {
+  note_launch();
+  power_start_kernel<T><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, nd, x);
+}
+
+template <typename T>
+void launch_scale_by(cudaStream_t s, int64_t len, const T* Dpt, T* y) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  scale_by_kernel<T><<<blocks, 256, 0, s>>>(len, Dpt, y);
+}
+
+template <typename T>
+void launch_normalize(cudaStream_t s, int64_t len, const T* y, const double* nrm2, T* x) {
+  int blocks = nblk(len, 256);
+  if (blocks > 2432) blocks = 2432;
+  note_launch();
+  normalize_kernel<T><<<blocks, 256, 0, s>>>(len, y, nrm2, x);
+}
+
+template <typename T>
 void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc) {
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
@@ -1581,6 +1775,15 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
   template void launch_local_correction<T>(cudaStream_t, int, bool, const T*, const T*,         \
                                            const T*, T*);                                       \
   template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);            \
+  template void launch_point_diag<T>(cudaStream_t, int, int, bool, const T*, T*);               \
+  template void launch_pj_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T, int); \
+  template void launch_cheb_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T*,   \
+                                      const double*, int, int, int);                            \
+  template void launch_gs_colour<T>(cudaStream_t, int, int, bool, const T*, const T*, const T*, \
+                                    T*, int, int);                                              \
+  template void launch_power_start<T>(cudaStream_t, int, int, T*);                              \
+  template void launch_scale_by<T>(cudaStream_t, int64_t, const T*, T*);                        \
+  template void launch_normalize<T>(cudaStream_t, int64_t, const T*, const double*, T*);        \
   template void launch_edge_p1<T>(cudaStream_t, int, bool, const T*, const T*, const T*,       \
                                   const T*, T*, T, bool);                                       \
   template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);             \

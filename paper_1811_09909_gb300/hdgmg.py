@@ -16,6 +16,7 @@ LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
 KRYLOV_NONE, KRYLOV_CG, KRYLOV_GMRES = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_IR, PREC_BF16 = 0, 1, 2, 3
 PDE_DIFFUSION, PDE_CONVDIFF = 0, 1
+SMOOTH_BLOCK_JACOBI, SMOOTH_POINT_JACOBI, SMOOTH_CHEBYSHEV, SMOOTH_LU_SGS = 0, 1, 2, 3
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
           -5: "EBREAKDOWN", -6: "ETIMEOUT"}
@@ -44,7 +45,7 @@ class Opts(ctypes.Structure):
                 ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32),
-                ("gmres_restart", ctypes.c_int32)]
+                ("gmres_restart", ctypes.c_int32), ("smoother", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -47,6 +47,7 @@ def test_default_options(lib):
     assert o.omega == 1.0 and o.rtol == 1e-10 and o.max_it == 200
     assert o.precision == hdgmg.PREC_FP64 and o.inner_rtol == 1e-5
     assert o.cluster_tail_n == 0 and o.gmres_restart == 30
+    assert o.smoother == hdgmg.SMOOTH_BLOCK_JACOBI
 
 
 @pytest.mark.parametrize("kw,msg", [
@@ -55,6 +56,7 @@ def test_default_options(lib):
     (dict(krylov=2, restart=0), "gmres_restart"), (dict(krylov=2, restart=257), "gmres_restart"),
     (dict(krylov=3), "krylov"),
     (dict(pde=1, krylov=1), "symmetric"), (dict(pde=5), "unknown pde"),
+    (dict(smoother=4), "unknown smoother"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg
@@ -63,7 +65,7 @@ def test_create_rejects_bad_arguments(lib, kw, msg):
     prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0),
                          kw.get("pde", 0), 1.0, 0.5)
     o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2), krylov=kw.get("krylov", 1),
-                           gmres_restart=kw.get("restart", 30))
+                           gmres_restart=kw.get("restart", 30), smoother=kw.get("smoother", 0))
     ctx = ctypes.c_void_p()
     st = lib.hdgmg_create(ctypes.byref(ctx), ctypes.byref(prob), ctypes.byref(o), None)
     assert st == -1
