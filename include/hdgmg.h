@@ -185,7 +185,9 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* ctx, const double* log_kappa);
  *   u       device, [nrhs][(p+1)^2][n*n] FP64 out, or NULL
  *   q       device, [nrhs][2][(p+1)^2][n*n] FP64 out, or NULL
  *   info    host, out (may be NULL); describes the last right-hand side.
- * Requires a prior hdgmg_setup.  ENOCONV still writes the last iterate. */
+ * Requires a prior hdgmg_setup.  ENOCONV still writes the last iterate.
+ * nrhs = 0 does nothing and returns OK (the array pointers may then be
+ * NULL). */
 hdgmg_status hdgmg_solve(hdgmg_ctx* ctx, int32_t nrhs, const double* f,
                          const double* g_D, double* lambda, double* u,
                          double* q, hdgmg_info* info);

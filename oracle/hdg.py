@@ -282,6 +282,25 @@ class HDGProblem:
                 ge[idx] = (C @ X[:, :, nt:])[:, :, 0]
         return Ae, ge
 
+    def element_operator(self, e, f=None):
+        """A_e (and g_e for nodal forcing f [n_v][E]) of one element by the
+        same general LU of the local block (for sampled checks at sizes where
+        condensing every element is too slow)."""
+        L, R, C, T = self.local(e)
+        rhs = R if f is None else np.column_stack([R, self.forms.load(f[:, e])])
+        X = np.linalg.solve(L, rhs)
+        Ae = C @ X[:, :self.nt] - T
+        return (Ae, C @ X[:, self.nt]) if f is not None else Ae
+
+    def recover_element(self, lam_api, f, e):
+        """(u_e, q_e) of one element from the full trace vector (library layout)."""
+        nd, nv = self.nd, self.nv
+        ne = self.ne
+        lam_e = np.concatenate([np.asarray(lam_api)[:, ed] for ed in self.edges[e]])
+        L, R, _, _ = self.local(e)
+        z = np.linalg.solve(L, self.forms.load(f[:, e]) - R @ lam_e)
+        return z[2 * nv:], np.stack([z[:nv], z[nv:2 * nv]])
+
     # -- global trace system ----------------------------------------------
     def assemble(self, Ae):
         """Sparse global trace matrix over all edges (edge-major dofs)."""

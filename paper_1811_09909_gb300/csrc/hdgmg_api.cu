@@ -1373,8 +1373,17 @@ extern "C" {
 
 hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const double* g_D,
                          double* lambda, double* u, double* q, hdgmg_info* info) {
-  if (!c || !f || !lambda) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c) return fail(HDGMG_EINVAL, "NULL argument");
   if (nrhs < 0) return fail(HDGMG_EINVAL, "nrhs < 0");
+  if (nrhs == 0) {                          // nothing to solve (the pointers may be NULL)
+    if (info) {
+      info->iters = 0;
+      info->converged = 1;
+      info->rel_res = 0.0;
+    }
+    return HDGMG_OK;
+  }
+  if (!f || !lambda) return fail(HDGMG_EINVAL, "NULL argument");
   if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
   const size_t nE = (size_t)c->n * c->n;
   const int64_t len = c->fine_len();

@@ -1,0 +1,229 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration that
+bench.py times, on outputs the oracle can compute one at a time (sampled
+element operators, local recoveries, residual rows) and on properties that
+hold at any size (residual against the oracle's operator, the manufactured
+solution, directional derivatives of the misfit).  Also the degenerate
+inputs: no right-hand side, the smallest mesh, a mesh that does not halve to
+2 x 2.
+
+Tolerances are those of test_gpu_parity.py / test_gpu_convdiff.py; a residual
+row is bounded by the whole residual, |res_E| <= ||g - A lambda||_2."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle import hdg  # noqa: E402
+from paper_1811_09909_gb300 import hdgmg  # noqa: E402
+from paper_1811_09909_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def full_residual(pr, lam, f):
+    """||g - A lambda||_2 / ||g||_2 on the interior traces with the oracle's
+    element operators (batched condensation of every element, scatter-add)."""
+    Ae, ge = pr.condense(f)
+    lam_em = hdg.api_to_edge_major(lam, pr.n, pr.nd)
+    dofs = pr.element_dofs()
+    Ax = np.zeros(pr.ne * pr.nd)
+    np.add.at(Ax, dofs.ravel(), np.einsum('erc,ec->er', Ae, lam_em[dofs]).ravel())
+    g = pr.assemble_rhs(ge)
+    fd = pr.free_dofs()
+    return np.linalg.norm(g[fd] - Ax[fd]) / np.linalg.norm(g[fd])
+
+
+def apply_elements(pr, Ae, lam):
+    """sum_e A_e lambda_e on the edge-major trace vector (scatter-add)."""
+    lam_em = hdg.api_to_edge_major(lam, pr.n, pr.nd)
+    dofs = pr.element_dofs()
+    Ax = np.zeros(pr.ne * pr.nd)
+    np.add.at(Ax, dofs.ravel(), np.einsum('erc,ec->er', Ae, lam_em[dofs]).ravel())
+    return Ax
+
+
+@pytest.mark.parametrize("prec", [hdgmg.PREC_FP32, hdgmg.PREC_FP64])
+def test_c2_256_p4_bench_configuration(prec):
+    """256 x 256, p = 4, log kappa ~ N(0, 1) seed 2, f = 1, tau = 1/h, the
+    bench's V-cycle and PCG options.  Every element operator and the condensed
+    right-hand side against the oracle; the solver's residual claim recomputed
+    on the host with the library's own operator; the residual with the
+    oracle's operator within that claim plus the measured operator difference
+    (at 652,800 DOFs ||A|| ||lambda|| / ||g|| amplifies the ~1e-12 difference
+    of two FP64 condensations to ~2e-10); sampled local recoveries."""
+    n, p = bench.N_MESH, bench.P_ORDER
+    wl = W.lognormal(n, p, seed=bench.SEED)
+    s = hdgmg.Solver(n, p, tau_mode=hdgmg.TAU_OVER_H, tau_c=1.0, precision=prec, **bench.SOLVER_OPTS)
+    s.setup(cuda(wl.log_kappa))
+    f = cuda(wl.f[0])
+    lam, u, q, info = s.solve(f)
+    assert info.converged == 1 and info.rel_res <= 1e-10
+    assert info.condense_threads in (32, 64, 128, 256)
+    pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau())
+    lam, u, q = host(lam), host(u), host(q)
+    Ao, go = pr.condense(wl.f[0])
+    Ag = np.transpose(host(s.element_matrices(0)), (2, 0, 1))
+    assert np.abs(Ag - Ao).max() <= 1e-11 * np.abs(Ao).max()
+    fd = pr.free_dofs()
+    bo = pr.assemble_rhs(go)[fd]
+    bg = hdg.api_to_edge_major(host(s.condensed_rhs(f)), n, p + 1)[fd]
+    assert np.abs(bg - bo).max() <= 1e-11 * np.abs(bo).max()
+    nbo = np.linalg.norm(bo)
+    res_g = np.linalg.norm(bg - apply_elements(pr, Ag, lam)[fd]) / np.linalg.norm(bg)
+    assert res_g <= 1.5e-10, res_g
+    res_o = np.linalg.norm(bo - apply_elements(pr, Ao, lam)[fd]) / nbo
+    dA = np.linalg.norm(apply_elements(pr, Ao - Ag, lam)[fd]) / nbo
+    assert res_o <= res_g * np.linalg.norm(bg) / nbo + dA + np.linalg.norm(bo - bg) / nbo + 1e-13
+    assert res_o <= 1e-9, (res_o, dA)
+    rng = np.random.default_rng(12)
+    for e in rng.choice(n * n, 24, replace=False):
+        ue, qe = pr.recover_element(lam, wl.f[0], e)
+        assert np.abs(u[:, e] - ue).max() <= 1e-9 * np.abs(ue).max(), e
+        assert np.abs(q[:, :, e] - qe).max() <= 1e-9 * np.abs(qe).max(), e
+
+
+def test_c3_512_p6_convection_diffusion():
+    """512 x 512, p = 6, eps = 1e-3, beta = (1, 0.5), the bench's FGMRES(30)
+    step-3 cycle with the BF16 finest operator.  Sampled element operators,
+    right-hand sides, residual rows and local recoveries against the oracle;
+    the manufactured solution at every node."""
+    n, p, eps = 512, 6, 1e-3
+    wl = W.convdiff(n, p, eps=eps)
+    s = hdgmg.Solver(n, p, tau_mode=hdgmg.TAU_OVER_H, tau_c=eps, beta=wl.beta,
+                     precision=hdgmg.PREC_BF16, krylov=hdgmg.KRYLOV_GMRES, gmres_restart=30,
+                     local_corr=hdgmg.LC_PRE, coarsest_n=4, m_fine=1, m_growth=2, m_max=4,
+                     rtol=1e-10)
+    s.setup(cuda(wl.log_kappa))
+    f = cuda(wl.f[0])
+    lam_t, u_t, _, info = s.solve(f, want_q=False)
+    assert info.converged == 1 and info.rel_res <= 1e-10
+    b = host(s.condensed_rhs(f))
+    lam, u = host(lam_t), host(u_t)
+    pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau(), beta=wl.beta)
+    X, Y = pr.node_coords()
+    assert np.abs(u - W.sine_u(X, Y)).max() <= 1e-9
+    rng = np.random.default_rng(13)
+    A = s.element_matrices(0)                      # [28][28][E] on the device
+    nb = np.linalg.norm(b)
+    nd = p + 1
+    for e in rng.choice(n * n, 8, replace=False):
+        ref, g_e = pr.element_operator(e, wl.f[0])
+        Ae = host(A[:, :, int(e)])
+        assert np.abs(Ae - ref).max() <= 1e-10 * np.abs(ref).max(), e
+        ue, _ = pr.recover_element(lam, wl.f[0], e)
+        assert np.abs(u[:, e] - ue).max() <= 1e-9 * np.abs(ue).max(), e
+    # residual rows of sampled interior edges from the two elements around them
+    for E in rng.choice(pr.ne, 24, replace=False):
+        if pr.bmask[E]:
+            continue
+        row = np.zeros(nd)
+        g = np.zeros(nd)
+        owners = np.nonzero((pr.edges == E).any(axis=1))[0]
+        for e in owners:
+            Ae, g_e = pr.element_operator(e, wl.f[0])
+            le = int(np.nonzero(pr.edges[e] == E)[0][0])
+            lam_e = np.concatenate([lam[:, ed] for ed in pr.edges[e]])
+            row += (Ae @ lam_e)[le * nd:(le + 1) * nd]
+            g += g_e[le * nd:(le + 1) * nd]
+        assert np.abs(b[:, E] - g).max() <= 1e-10 * np.abs(g).max() + 1e-14
+        assert np.abs(g - row).max() <= 1.5e-10 * nb, E
+
+
+def test_c4_batched_configuration():
+    """The bench's batch (64 problems, n in {32..256}, p in {2, 4, 8}, 16
+    right-hand sides): every solve converged; full oracle residual for a few
+    small problems and two right-hand sides each."""
+    rng = np.random.default_rng(4)
+    shapes = [(int(rng.choice((32, 64, 128, 256))), int(rng.choice((2, 4, 8)))) for _ in range(64)]
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    logks = [torch.randn(n * n, generator=gen, device="cuda", dtype=torch.float64) * 0.5
+             for n, p in shapes]
+    fs = [torch.randn((16, (p + 1) ** 2, n * n), generator=gen, device="cuda", dtype=torch.float64)
+          for n, p in shapes]
+    b = hdgmg.Batch([dict(n=n, p=p) for n, p in shapes], nthreads=16, precision=hdgmg.PREC_FP32,
+                    **bench.SOLVER_OPTS)
+    b.setup(logks)
+    lams, _, _, infos = b.solve(fs, want_u=False, want_q=False)
+    torch.cuda.synchronize()
+    assert all(i.converged == 1 and i.rel_res <= 1e-10 for i in infos)
+    small = [i for i, (n, p) in enumerate(shapes) if n <= 64][:3]
+    for i in small:
+        n, p = shapes[i]
+        pr = hdg.HDGProblem(n, p, np.exp(host(logks[i])), float(n))
+        for k in (0, 15):
+            res = full_residual(pr, host(lams[i][k]), host(fs[i][k]))
+            assert res <= 1.5e-10, (i, k, res)
+    b.close()
+
+
+def test_c5_1024_p4_adjoint_directional_derivatives():
+    """1024 x 1024, p = 4: the misfit gradient along one random direction of
+    log kappa and one of f against central differences of J (FP64 solves to
+    1e-12), at a point away from the data."""
+    n, p = 1024, 4
+    gen = torch.Generator(device="cuda").manual_seed(52)
+    logk = torch.randn(n * n, generator=gen, device="cuda", dtype=torch.float64)
+    f = torch.ones(((p + 1) ** 2, n * n), device="cuda", dtype=torch.float64)
+    s = hdgmg.Solver(n, p, precision=hdgmg.PREC_FP64, coarsest_n=4, m_fine=1, m_growth=2, m_max=2,
+                     rtol=1e-12)
+    s.setup(logk)
+    _, u_ref, _, _ = s.solve(f, want_q=False)
+    u_obs = u_ref * (1.0 + 0.01 * torch.randn(u_ref.shape, generator=gen, device="cuda",
+                                              dtype=torch.float64))
+    mk = logk + 0.1 * torch.randn(n * n, generator=gen, device="cuda", dtype=torch.float64)
+    dk = torch.randn(n * n, generator=gen, device="cuda", dtype=torch.float64)
+    df = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    s.setup(mk)
+    _, gk, gf, _ = s.gradient(f, u_obs)
+
+    def misfit(lk, ff):
+        s.setup(lk)
+        return s.gradient(ff, u_obs)[0]
+
+    t = 1e-4
+    fd = (misfit(mk + t * dk, f) - misfit(mk - t * dk, f)) / (2 * t)
+    an = float((gk * dk).sum())
+    assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+    fd = (misfit(mk, f + t * df) - misfit(mk, f - t * df)) / (2 * t)
+    an = float((gf * df).sum())
+    assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+
+
+def test_degenerate_inputs():
+    """No right-hand side (a no-op), the smallest mesh (2 x 2, one level),
+    and a mesh that halves only once (6 -> 3) with p = 8."""
+    wl = W.lognormal(8, 2, seed=1)
+    s = hdgmg.Solver(8, 2)
+    s.setup(cuda(wl.log_kappa))
+    empty = torch.empty((0, 9, 64), dtype=torch.float64, device="cuda")
+    lam, u, q, info = s.solve(empty)
+    assert lam.shape[0] == 0
+    for n, p, cn in ((2, 1, 2), (2, 3, 2), (6, 8, 3)):
+        wl = W.lognormal(n, p, seed=n + p)
+        rng = np.random.default_rng(p)
+        f = rng.standard_normal(((p + 1) ** 2, n * n))
+        s = hdgmg.Solver(n, p, coarsest_n=cn, rtol=1e-12)
+        s.setup(cuda(wl.log_kappa))
+        lam, u, q, info = s.solve(cuda(f))
+        assert info.converged == 1
+        pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau())
+        ref = pr.solve_direct(f)
+        assert np.linalg.norm(host(lam) - ref) <= 1e-9 * np.linalg.norm(ref), (n, p)
