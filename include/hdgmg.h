@@ -155,9 +155,11 @@ typedef struct {
   double t_condense_ms;   /* device time of the element condensation kernel
                              in the last hdgmg_setup (CUDA events around it) */
   int32_t condense_threads; /* threads per element the condensation kernel
-                             ran with: picked once per (kernel, p, device) by
-                             timing 32/64/128/256 on the first set-up; the
-                             result does not depend on it                     */
+                             ran with, and ...                                 */
+  int32_t condense_elements_per_block; /* ... elements per block: picked once
+                             per (kernel, p, device) by timing candidate
+                             shapes on the first set-up; the result does not
+                             depend on them                                   */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

@@ -94,7 +94,7 @@ struct hdgmg_ctx {
   bool setup_done = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   double t_setup_ms = 0.0, t_condense_ms = 0.0;
-  int condense_threads = 0;    // autotuned threads per element of the condensation kernel
+  int condense_threads = 0;    // autotuned launch shape of the condensation kernel (TPE * 16 + EPB)
   // PCG loop as one CUDA graph with a device-evaluated while condition
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t cg_graph = nullptr;
@@ -1406,7 +1406,8 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     info->t_solve_ms = ms;
     info->t_setup_ms = c->t_setup_ms;
     info->t_condense_ms = c->t_condense_ms;
-    info->condense_threads = c->condense_threads;
+    info->condense_threads = c->condense_threads / 16;
+    info->condense_elements_per_block = c->condense_threads % 16;
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }

@@ -97,8 +97,9 @@ struct RefDevice {     // device copies of RefElement tables (FP64)
 
 // kap = exp(log kappa) per element; the element kernels take kap
 void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap);
-// returns the autotuned threads per element; tune_only: only make sure the
-// choice for this (kernel, p) is made (times the candidates on a sample)
+// returns the autotuned launch shape, threads per element * 16 + elements per
+// block; tune_only: only make sure the choice for this (kernel, p) is made
+// (times the candidates on a sample)
 int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE,
                     const double* kap, int tau_mode, double tau_c, double hmin,
                     double* A, double* Lfac, int* err, bool tune_only = false);

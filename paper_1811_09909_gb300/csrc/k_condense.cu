@@ -41,34 +41,40 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-// K1: one block of NT threads per element, the local matrices in shared
-// memory.  S: nv x nv (full square, lower part used), V: nv x nt.  The FP64
-// pipe is the bottleneck on GB300, so every pivot's square root and
-// reciprocal is computed once (thread 0) and read by all threads.  NT is
-// picked per (kernel, p) by a timing autotuner (tune_threads below); the
-// result does not depend on it.  Elements e_begin + blockIdx.x.
-template <int NT>
-__global__ void __launch_bounds__(NT) condense_kernel(
+// K1: TPE threads per element and EPB elements per block, in lockstep (the
+// elements of a block run the same loops, so block barriers serve all of
+// them); the local matrices in shared memory, per element
+//   S: nv x nv (full square, lower part used), V: nv x nt, 1/sqrt pivots.
+// The FP64 pipe is the bottleneck on GB300: a pivot's square root and
+// reciprocal is computed once per element (one thread), so several elements
+// per warp share the cost of that single-lane step and of the partially
+// filled last pass of each loop.  (TPE, EPB) is picked per p by a timing
+// autotuner (tune_config below); the result does not depend on it.
+// Elements e_begin + blockIdx.x * EPB + (threadIdx.x / TPE); a block's
+// elements past nE recompute the last element and write nothing.
+template <int TPE, int EPB>
+__global__ void __launch_bounds__(TPE * EPB) condense_kernel(
     int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ Eb,
     const double* __restrict__ H, const double* __restrict__ F, const double* __restrict__ K,
     const double* __restrict__ kapv, int tau_mode, double tau_c, double hmin,
     double* __restrict__ A, double* __restrict__ Lfac, int* __restrict__ err) {
   extern __shared__ double smem[];
-  const int tid = threadIdx.x;
-  const int e = e_begin + blockIdx.x;
-  if (e >= nE) return;
-  double* S = smem;
+  const int tid = threadIdx.x % TPE, el = threadIdx.x / TPE;
+  const int e0 = e_begin + blockIdx.x * EPB + el;
+  const bool active = e0 < nE;
+  const int e = active ? e0 : nE - 1;
+  double* S = smem + (size_t)el * (nv * nv + nv * nt + nv);
   double* V = S + nv * nv;
   double* dinv = V + nv * nt;
   const double kap = kapv[e];
   const double tau = tau_of(tau_mode, tau_c, hmin);
   const int nsv = nv * (nv + 1) / 2;
-  for (int t = tid; t < nsv; t += NT) {
+  for (int t = tid; t < nsv; t += TPE) {
     int i, j;
     tri_index(t, i, j);
     S[i * nv + j] = fma(kap, G[i * nv + j], tau * Eb[i * nv + j]);
   }
-  for (int t = tid; t < nv * nt; t += NT) V[t] = fma(kap, H[t], tau * F[t]);
+  for (int t = tid; t < nv * nt; t += TPE) V[t] = fma(kap, H[t], tau * F[t]);
   __syncthreads();
   bool bad = false;
   for (int k = 0; k < nv; ++k) {
@@ -84,26 +90,26 @@ __global__ void __launch_bounds__(NT) condense_kernel(
     }
     __syncthreads();
     const double di = dinv[k];
-    for (int i = k + 1 + tid; i < nv; i += NT) S[i * nv + k] *= di;
-    for (int c = tid; c < nt; c += NT) V[k * nt + c] *= di;
+    for (int i = k + 1 + tid; i < nv; i += TPE) S[i * nv + k] *= di;
+    for (int c = tid; c < nt; c += TPE) V[k * nt + c] *= di;
     __syncthreads();
     const int m = nv - k - 1;
     const int ntri = m * (m + 1) / 2;
-    for (int t = tid; t < ntri; t += NT) {
+    for (int t = tid; t < ntri; t += TPE) {
       int ii, jj;
       tri_index(t, ii, jj);
       const int i = k + 1 + ii, j = k + 1 + jj;
       S[i * nv + j] = fma(-S[i * nv + k], S[j * nv + k], S[i * nv + j]);
     }
-    for (int t = tid; t < m * nt; t += NT) {
+    for (int t = tid; t < m * nt; t += TPE) {
       const int i = k + 1 + t / nt, c = t % nt;
       V[i * nt + c] = fma(-S[i * nv + k], V[k * nt + c], V[i * nt + c]);
     }
     __syncthreads();
   }
-  if (bad) atomicOr(err, 1);
+  if (bad && active) atomicOr(err, 1);
   const int nsa = nt * (nt + 1) / 2;
-  for (int t = tid; t < nsa; t += NT) {
+  for (int t = tid; t < nsa; t += TPE) {
     int r, c;
     tri_index(t, r, c);
     double s0 = 0.0, s1 = 0.0;
@@ -115,10 +121,10 @@ __global__ void __launch_bounds__(NT) condense_kernel(
     if (i < nv) s0 = fma(V[i * nt + r], V[i * nt + c], s0);
     double a = fma(kap, K[r * nt + c], -(s0 + s1));
     if (r == c) a += tau;
-    A[(size_t)t * nE + e] = a;
+    if (active) A[(size_t)t * nE + e] = a;
   }
-  if (Lfac) {
-    for (int t = tid; t < nsv; t += NT) {
+  if (Lfac && active) {
+    for (int t = tid; t < nsv; t += TPE) {
       int r, c;
       tri_index(t, r, c);
       Lfac[(size_t)t * nE + e] = S[r * nv + c];
@@ -555,55 +561,58 @@ void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap) {
 }
 
 // ------------------------------------------------------------ autotuner
-// Threads per element of the condensation kernels: the candidates are timed
-// once per (kernel, p, ns, device) on the first elements of the first
-// problem that needs them (CUDA events on the caller's stream, outside any
-// capture) and the fastest is cached for the process.  The kernels give
-// bit-identical results for every candidate.
+// Launch shapes of the condensation kernels, (threads per element TPE,
+// elements per block EPB), encoded as TPE * 16 + EPB: the candidates are
+// timed once per (kernel, p, ns, device) on the first elements of the first
+// problem that needs them (warm-up + CUDA events on the caller's stream,
+// outside any capture) and the fastest is cached for the process.  Every
+// shape gives bit-identical operators (each entry is formed by one thread in
+// a fixed order).
 namespace {
-constexpr int kTuneCandidates[4] = {32, 64, 128, 256};
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tuned;
 
 template <typename Launch>
-int tune_threads(cudaStream_t s, int kind, int p, int nE, size_t shm, Launch launch) {
+int tune_config(cudaStream_t s, int kind, int p, int nE, const int* cands, int ncand,
+                size_t shm_per_elem, Launch launch) {
   int dev = 0;
   cudaGetDevice(&dev);
   const auto key = std::make_tuple(kind, p, dev);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) return it->second;
-  int best = 64;
-  if (shm <= 220 * 1024) {
-    const int sample = nE < 16384 ? nE : 16384;
-    cudaEvent_t t0, t1;
-    cudaEventCreate(&t0);
-    cudaEventCreate(&t1);
-    float best_ms = 1e30f;
-    for (int nt : kTuneCandidates) {
-      launch(nt, 0, sample);                       // warm-up
-      cudaEventRecord(t0, s);
-      launch(nt, 0, sample);
-      cudaEventRecord(t1, s);
-      if (cudaEventSynchronize(t1) != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, t0, t1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = nt;
-      }
+  int best = cands[0];
+  const int sample = nE < 16384 ? nE : 16384;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  float best_ms = 1e30f;
+  for (int ci = 0; ci < ncand; ++ci) {
+    const int id = cands[ci];
+    if (shm_per_elem * (size_t)(id % 16) > 220 * 1024) continue;
+    launch(id, 0, sample);                         // warm-up
+    cudaEventRecord(t0, s);
+    launch(id, 0, sample);
+    cudaEventRecord(t1, s);
+    if (cudaEventSynchronize(t1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = id;
     }
-    cudaEventDestroy(t0);
-    cudaEventDestroy(t1);
   }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
   g_tuned[key] = best;
   return best;
 }
 
-template <int NT>
+template <int TPE, int EPB>
 void set_smem_attr_sym() {
   static const bool done = [] {
-    cudaFuncSetAttribute(condense_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(condense_kernel<TPE, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
     return true;
   }();
   (void)done;
@@ -617,30 +626,36 @@ void set_smem_attr_cd() {
   }();
   (void)done;
 }
+
+constexpr int kSymCands[] = {8 * 16 + 4, 16 * 16 + 2, 16 * 16 + 4, 32 * 16 + 1, 32 * 16 + 2,
+                             64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
+constexpr int kCdCands[] = {32 * 16 + 1, 64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
 }  // namespace
 
 int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
                     int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err,
                     bool tune_only) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t shm = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
-  auto launch = [&](int threads, int e0, int count) {
+  const size_t per_elem = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
+  auto launch = [&](int id, int e0, int count) {
     note_launch();
-    switch (threads) {
-#define CASE(NT)                                                                              \
-  case NT:                                                                                    \
-    set_smem_attr_sym<NT>();                                                                  \
-    condense_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.E, ref.H, ref.F, ref.K, \
-                                               kap, tau_mode, tau_c, hmin, A, Lfac, err);     \
+    switch (id) {
+#define CASE(TPE, EPB)                                                                        \
+  case TPE * 16 + EPB:                                                                        \
+    set_smem_attr_sym<TPE, EPB>();                                                            \
+    condense_kernel<TPE, EPB><<<(count + EPB - 1) / EPB, TPE * EPB, per_elem * EPB, s>>>(     \
+        nv, nt, nE, e0, ref.G, ref.E, ref.H, ref.F, ref.K, kap, tau_mode, tau_c, hmin, A,     \
+        Lfac, err);                                                                           \
     break;
-      CASE(32) CASE(64) CASE(128) CASE(256)
+      CASE(8, 4) CASE(16, 2) CASE(16, 4) CASE(32, 1) CASE(32, 2) CASE(64, 1) CASE(128, 1)
+      CASE(256, 1)
 #undef CASE
       default: break;
     }
   };
-  const int threads = tune_threads(s, 0, p, nE, shm, launch);
-  if (!tune_only) launch(threads, 0, nE);
-  return threads;
+  const int id = tune_config(s, 0, p, nE, kSymCands, 8, per_elem, launch);
+  if (!tune_only) launch(id, 0, nE);
+  return id;
 }
 
 int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,
@@ -648,11 +663,11 @@ int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const size_t shm =
       sizeof(double) * (size_t)((nv * nv > nv * nt ? nv * nv : nv * nt) + nv * nt + nv);
-  auto launch = [&](int threads, int e0, int count) {
+  auto launch = [&](int id, int e0, int count) {
     note_launch();
-    switch (threads) {
+    switch (id) {
 #define CASE(NT)                                                                                  \
-  case NT:                                                                                        \
+  case NT * 16 + 1:                                                                               \
     set_smem_attr_cd<NT>();                                                                       \
     condense_cd_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.H, ref.K, cd.S0,     \
                                                   cd.W0, cd.V0, cd.adiag, kap, A, LU, err);       \
@@ -662,9 +677,9 @@ int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
       default: break;
     }
   };
-  const int threads = tune_threads(s, 1, p, nE, shm, launch);
-  if (!tune_only) launch(threads, 0, nE);
-  return threads;
+  const int id = tune_config(s, 1, p, nE, kCdCands, 4, shm, launch);
+  if (!tune_only) launch(id, 0, nE);
+  return id;
 }
 
 void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,

@@ -54,7 +54,8 @@ class Info(ctypes.Structure):
                 ("t_solve_ms", ctypes.c_double), ("n_levels", ctypes.c_int32),
                 ("trace_dofs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("refinements", ctypes.c_int32), ("t_condense_ms", ctypes.c_double),
-                ("condense_threads", ctypes.c_int32)]
+                ("condense_threads", ctypes.c_int32),
+                ("condense_elements_per_block", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
