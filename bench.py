@@ -319,7 +319,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one condensation launch at 256^2, p = 4: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
 # (profiles/condense_256_p4.md).
-CONDENSE_TRAFFIC_BYTES = 1685248 + 223480320
+CONDENSE_TRAFFIC_BYTES = 8684032 + 228024320
 
 
 def condense_flops(p, nE):
