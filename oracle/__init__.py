@@ -16,7 +16,8 @@ hybridized high-order finite element methods" (arXiv:1811.09909):
   static condensation by a general LU with partial pivoting of the full
   (q_x, q_y, u) block, global assembly of the trace system of Sec. 3
   (eq. trace_linear_system), sparse direct solve, local recovery, and a
-  brute-force uncondensed solve.
+  brute-force uncondensed solve; the hybridized interior penalty schemes
+  SIPG-H, NIPG-H and IIPG-H of eq. IPG_H through the same condensation.
 * ``mg``       -- the multigrid of Sec. 3: p-coarsening (Sec. 3.1.1),
   h-agglomeration with the interior/boundary split (Sec. 3.1.2,
   eq. trace_partition), prolongation and restriction (eqs. n_1_Ik, n_g1_Ik,

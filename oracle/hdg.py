@@ -45,6 +45,16 @@ longer symmetric; the same general LU condenses it into
   A_e = C L^-1 R - T,  T = sum_f (beta.n_f - tau_f) El_f.
 With beta = 0 this is the diffusion element (T = -tau El).
 
+Hybridized interior penalty schemes (Sec. 2, eqs. IPDG_flux, SIPG_H,
+IPG_H): the primal local problem in u alone,
+  (kappa grad u, grad w)_K - s_f <u - lambda, kappa grad w.n>_dK
+      - <kappa grad u.n, w>_dK + <tau (u - lambda), w>_dK = (f, w)_K,
+with the flux uhat.n = -kappa grad u.n + tau (u - lambda) in the same
+conservation condition; s_f = 1 (SIPG-H), -1 (NIPG-H), 0 (IIPG-H).  The
+local block L (n_v x n_v) is condensed by the same general LU; the recovered
+flux is q = -kappa grad u_h at the volume nodes (reading: the primal schemes
+have no separate flux unknown).
+
 Pins (tests/test_oracle_hdg.py): polynomial patch test (exact to roundoff),
 O(h^{p+1}) rates for u and q, A_e 1 = 0, A_e symmetric PSD, homogeneity
 A_e(c kappa, c tau) = c A_e, SPD global trace operator, condensed solve equal
@@ -55,6 +65,11 @@ convection (exact to roundoff); the closed form A_e 1 = <beta.n, mu>;
 positive-definite symmetric part of the global trace operator (the upwind
 tau); O(h^{p+1}) rates for u; condensed solve equal to the dense uncondensed
 solve.
+IPDG-H (tests/test_oracle_ipdg.py): Q_p patch tests for the three schemes
+(exact to roundoff), SIPG-H symmetric and positive semi-definite with
+A_e 1 = 0, the NIPG-H energy identity (the s_f terms cancel), condensed equal
+to uncondensed solves, O(h^{p+1}) / O(h^p) rates, and the paper's NIPG-H
+iteration tables for Example I (tests/golden/paper_example1_iterations.txt).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -150,6 +165,19 @@ class ElementForms:
             self.normals[edge] = (nx, ny)
         self.Dx, self.Dy = Dx, Dy
         self.Cx, self.Cy = Cx, Cy
+        # primal (IPDG-H) pieces: stiffness (grad phi_b, grad phi_a), the
+        # boundary terms N[a, b] = <phi_b, grad phi_a.n> and
+        # Hn[a, k] = <psi_k, grad phi_a.n>
+        self.Kst = (dphidx * wJ) @ dphidx.T + (dphidy * wJ) @ dphidy.T
+        self.Nn = np.zeros((nv, nv))
+        self.Hn = np.zeros((nv, nt))
+        for edge in range(4):
+            ph, psi, wds, _ = rq.edge_tables(edge)
+            dn = rq.edge_normal_derivative(edge)
+            sl = slice(edge * (p + 1), (edge + 1) * (p + 1))
+            self.Nn += (dn * wds) @ ph.T
+            self.Hn[:, sl] += (dn * wds) @ psi.T
+        self.Gx, self.Gy = rq.nodal_gradient()
         Z = np.zeros((nv, nv))
         # rows: [HDG_local1 x-test, HDG_local1 y-test, HDG_local2]
         self.LM = np.block([[Mv, Z, Z], [Z, Mv, Z], [Z, Z, Z]])
@@ -187,6 +215,21 @@ class ElementForms:
         T = sum((bn[f] - tau_f[f]) * self.El_f[f] for f in range(4))
         return L, R, C, T
 
+    def local_ipdg(self, kappa, tau, sf):
+        """IPDG-H local block of eq. IPG_H (u only): L u + R lambda = M f and
+        conservation rows C u + T lambda."""
+        L = kappa * (self.Kst - sf * self.Nn - self.Nn.T) + tau * self.Eb_sum()
+        R = sf * kappa * self.Hn - tau * self.Fb_sum()
+        C = (-kappa * self.Hn + tau * self.Fb_sum()).T
+        T = -tau * self.El
+        return L, R, C, T
+
+    def Eb_sum(self):
+        return self.Eb_f.sum(axis=0)
+
+    def Fb_sum(self):
+        return self.Fb_f.sum(axis=0)
+
     def load(self, fnodal):
         """F = [0, 0, (f_h, phi_a)] for the Q_p interpolant of nodal f."""
         nv = self.nv
@@ -202,9 +245,15 @@ class HDGProblem:
     beta: None (diffusion) or a constant convection velocity (bx, by); then
     tau is the base value and face f of element e uses
     tau_e + max(beta.n_f, 0).
+    scheme: "hdg" (Sec. 2, eqs. HDG_local1/2) or one of the hybridized
+    interior penalty schemes "sipg", "nipg", "iipg" (eq. IPG_H with
+    s_f = 1, -1, 0; diffusion only).
     """
 
-    def __init__(self, n, p, kappa, tau, x0=0.0, x1=1.0, y0=0.0, y1=1.0, nq=None, beta=None):
+    SCHEMES = {"sipg": 1.0, "nipg": -1.0, "iipg": 0.0}
+
+    def __init__(self, n, p, kappa, tau, x0=0.0, x1=1.0, y0=0.0, y1=1.0, nq=None, beta=None,
+                 scheme="hdg"):
         self.n, self.p = n, p
         self.E = n * n
         self.hx = (x1 - x0) / n
@@ -221,7 +270,14 @@ class HDGProblem:
         self._Ae = None
         self._ge_f = None
         self.beta = None if beta is None else np.asarray(beta, dtype=np.float64)
-        self.symmetric = self.beta is None
+        if scheme != "hdg" and scheme not in self.SCHEMES:
+            raise ValueError(f"unknown scheme {scheme}")
+        if scheme != "hdg" and self.beta is not None:
+            raise ValueError("the interior penalty schemes are diffusion only")
+        self.scheme = scheme
+        self.ipdg = scheme != "hdg"
+        self.sf = self.SCHEMES.get(scheme)
+        self.symmetric = self.beta is None and scheme in ("hdg", "sipg")
         if self.beta is not None:
             bn = self.forms.normals @ self.beta
             self.tau_f = self.tau[:, None] + np.maximum(bn, 0.0)[None, :]
@@ -229,6 +285,8 @@ class HDGProblem:
     def local(self, e):
         """(L, R, C, T) of element e: conservation rows read C z + T lambda."""
         fr = self.forms
+        if self.ipdg:
+            return fr.local_ipdg(self.kappa[e], self.tau[e], self.sf)
         if self.beta is None:
             L, R, C = fr.local(self.kappa[e], self.tau[e])
             return L, R, C, -self.tau[e] * fr.El
@@ -240,12 +298,23 @@ class HDGProblem:
         ge = np.zeros((E, nt)) if f is not None else None
         for e in range(E):
             L, R, C, T = self.local(e)
-            rhs = R if f is None else np.column_stack([R, self.forms.load(f[:, e])])
+            rhs = R if f is None else np.column_stack([R, self.load(f, e)])
             X = np.linalg.solve(L, rhs)                  # LU, partial pivoting
             Ae[e] = C @ X[:, :nt] - T
             if f is not None:
                 ge[e] = C @ X[:, nt]
         return Ae, ge
+
+    def load(self, f, e):
+        """Right-hand side of element e's local block for nodal forcing f."""
+        if self.ipdg:
+            return self.forms.Mv @ f[:, e]
+        return self.forms.load(f[:, e])
+
+    def _flux_ipdg(self, u_e, e):
+        """q = -kappa grad u_h at the volume nodes (primal schemes)."""
+        fr = self.forms
+        return -self.kappa[e] * np.stack([fr.Gx @ u_e, fr.Gy @ u_e])
 
     # -- per-element condensation (LU with partial pivoting) -------------
     def element_dofs(self):
@@ -257,7 +326,7 @@ class HDGProblem:
         """Return A_e [E, n_t, n_t] and g_e [E, n_t] (g_e only if f given).
 
         f: nodal forcing [n_v][E] (library layout)."""
-        if self.beta is not None:
+        if self.beta is not None or self.ipdg:
             return self._condense_general(f)
         E, nv, nt = self.E, self.nv, self.nt
         Ae = np.empty((E, nt, nt))
@@ -287,7 +356,7 @@ class HDGProblem:
         same general LU of the local block (for sampled checks at sizes where
         condensing every element is too slow)."""
         L, R, C, T = self.local(e)
-        rhs = R if f is None else np.column_stack([R, self.forms.load(f[:, e])])
+        rhs = R if f is None else np.column_stack([R, self.load(f, e)])
         X = np.linalg.solve(L, rhs)
         Ae = C @ X[:, :self.nt] - T
         return (Ae, C @ X[:, self.nt]) if f is not None else Ae
@@ -298,7 +367,9 @@ class HDGProblem:
         ne = self.ne
         lam_e = np.concatenate([np.asarray(lam_api)[:, ed] for ed in self.edges[e]])
         L, R, _, _ = self.local(e)
-        z = np.linalg.solve(L, self.forms.load(f[:, e]) - R @ lam_e)
+        z = np.linalg.solve(L, self.load(f, e) - R @ lam_e)
+        if self.ipdg:
+            return z, self._flux_ipdg(z, e)
         return z[2 * nv:], np.stack([z[:nv], z[nv:2 * nv]])
 
     # -- global trace system ----------------------------------------------
@@ -359,6 +430,12 @@ class HDGProblem:
         nv = self.nv
         u = np.empty((nv, self.E))
         q = np.empty((2, nv, self.E))
+        if self.ipdg:
+            for e in range(self.E):
+                L, R, _, _ = self.local(e)
+                u[:, e] = np.linalg.solve(L, self.load(f, e) - R @ lam[dofs[e]])
+                q[:, :, e] = self._flux_ipdg(u[:, e], e)
+            return u, q
         if self.beta is not None:
             for e in range(self.E):
                 L, R, _, _ = self.local(e)
@@ -388,8 +465,8 @@ class HDGProblem:
         equations of every element, then the conservation equations of every
         interior edge.  Only for tiny meshes."""
         E, nv, nt = self.E, self.nv, self.nt
-        fr = self.forms
-        nz = 3 * nv * E
+        nzl = nv if self.ipdg else 3 * nv          # local unknowns per element
+        nz = nzl * E
         fd = self.free_dofs()
         pos = -np.ones(self.ne * self.nd, dtype=np.int64)
         pos[fd] = np.arange(len(fd))
@@ -404,9 +481,9 @@ class HDGProblem:
         dofs = self.element_dofs()
         for e in range(E):
             L, R, C, T = self.local(e)
-            zr = slice(3 * nv * e, 3 * nv * (e + 1))
+            zr = slice(nzl * e, nzl * (e + 1))
             M[zr, zr] = L
-            rhs[zr] = fr.load(f[:, e])
+            rhs[zr] = self.load(f, e)
             for c in range(nt):
                 d = dofs[e, c]
                 if pos[d] >= 0:
@@ -429,7 +506,11 @@ class HDGProblem:
         sol = np.linalg.solve(M, rhs)
         lam = lamD.copy()
         lam[fd] = sol[nz:]
-        z = sol[:nz].reshape(E, 3 * nv)
+        z = sol[:nz].reshape(E, nzl)
+        if self.ipdg:
+            u = z.T.copy()
+            q = np.stack([self._flux_ipdg(u[:, e], e) for e in range(E)], axis=2)
+            return edge_major_to_api(lam, self.n, self.nd), u, q
         u = z[:, 2 * nv:].T.copy()
         q = np.stack([z[:, :nv].T, z[:, nv:2 * nv].T])
         return edge_major_to_api(lam, self.n, self.nd), u, q

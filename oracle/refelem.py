@@ -96,6 +96,7 @@ class RefQuad:
         self.l_q = lagrange(self.nodes, self.xq)          # [nv1, nq]
         self.dl_q = lagrange_deriv(self.nodes, self.xq)   # [nv1, nq]
         self.l_end = lagrange(self.nodes, np.array([-1.0, 1.0]))  # [nv1, 2]
+        self.dl_end = lagrange_deriv(self.nodes, np.array([-1.0, 1.0]))
 
     # --- 2-D volume basis at the tensor quadrature grid ------------------
     def volume_tables(self):
@@ -144,3 +145,32 @@ class RefQuad:
         psi = trace_basis(self.p, self.xq, length)
         w_ds = self.wq * (length / 2.0)
         return phi, psi, w_ds, normal
+
+    def edge_normal_derivative(self, edge):
+        """dn[a, q] = (grad phi_a . n)(s_q) on local edge ``edge`` at the same
+        quadrature points as ``edge_tables`` (physical derivative)."""
+        p1 = self.p + 1
+        dn = np.zeros((self.nv, self.nq))
+        end = 0 if edge in (0, 2) else 1
+        sign = -1.0 if edge in (0, 2) else 1.0
+        for b in range(p1):
+            for a in range(p1):
+                if edge in (0, 1):      # n = -+x: d/dx of l_a(xi) at xi = -+1, times l_b(eta)
+                    dn[b * p1 + a] = sign * (2.0 / self.hx) * self.dl_end[a, end] * self.l_q[b]
+                else:                   # n = -+y
+                    dn[b * p1 + a] = sign * (2.0 / self.hy) * self.l_q[a] * self.dl_end[b, end]
+        return dn
+
+    def nodal_gradient(self):
+        """(Gx, Gy): [n_v, n_v] matrices taking nodal values of a Q_p function
+        to its physical x- and y-derivatives at the nodes."""
+        p1 = self.p + 1
+        D = lagrange_deriv(self.nodes, self.nodes)      # D[j, i] = l_j'(xi_i)
+        Gx = np.zeros((self.nv, self.nv))
+        Gy = np.zeros((self.nv, self.nv))
+        for a2 in range(p1):
+            for a1 in range(p1):
+                for b in range(p1):
+                    Gx[a2 * p1 + a1, a2 * p1 + b] = (2.0 / self.hx) * D[b, a1]
+                    Gy[a2 * p1 + a1, b * p1 + a1] = (2.0 / self.hy) * D[b, a2]
+        return Gx, Gy

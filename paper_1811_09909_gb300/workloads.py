@@ -148,9 +148,14 @@ class Workload:
         return 2 * self.n * (self.n - 1) * (self.p + 1)
 
     def tau(self):
-        """tau per element as the library computes it (TAU_CONST or c/h_min)."""
+        """tau per element as the library computes it (TAU_CONST, c/h_min or
+        c kappa_e/h_min)."""
         h = min((self.x1 - self.x0) / self.n, (self.y1 - self.y0) / self.n)
-        return self.tau_c if self.tau_mode == "const" else self.tau_c / h
+        if self.tau_mode == "const":
+            return self.tau_c
+        if self.tau_mode == "kappa_over_h":
+            return self.tau_c * np.exp(self.log_kappa) / h
+        return self.tau_c / h
 
 
 def poisson_sine(n=16, p=2, tau_mode="const", tau_c=1.0):

@@ -45,3 +45,31 @@ def test_legendre_closed_forms():
     assert np.allclose(P[1], s)
     assert np.allclose(P[2], 1.5 * s ** 2 - 0.5)
     assert np.allclose(P[3], 2.5 * s ** 3 - 1.5 * s)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_normal_derivative_and_nodal_gradient(p):
+    """For v = x^p y^(p-1) + 2x - y on a 0.3 x 0.2 element centred at the
+    origin: grad v . n on each edge and grad v at the nodes from its nodal
+    values match the analytic derivatives (IPDG-H boundary terms, Sec. 2)."""
+    hx, hy = 0.3, 0.2
+    rq = refelem.RefQuad(p, hx, hy)
+    v = lambda x, y: x ** p * y ** (p - 1) + 2 * x - y
+    vx = lambda x, y: p * x ** (p - 1) * y ** (p - 1) + 2
+    vy = lambda x, y: (p - 1) * x ** p * y ** max(p - 2, 0) - 1 if p > 1 else -1 + 0 * x
+    p1 = p + 1
+    a = np.arange(rq.nv) % p1
+    b = np.arange(rq.nv) // p1
+    X, Y = 0.5 * hx * rq.nodes[a], 0.5 * hy * rq.nodes[b]
+    coef = v(X, Y)
+    Gx, Gy = rq.nodal_gradient()
+    assert np.abs(Gx @ coef - vx(X, Y)).max() < 1e-11
+    assert np.abs(Gy @ coef - vy(X, Y)).max() < 1e-11
+    s = rq.xq
+    for edge, (x, y, n) in enumerate([(-hx / 2 + 0 * s, hy / 2 * s, (-1, 0)),
+                                      (hx / 2 + 0 * s, hy / 2 * s, (1, 0)),
+                                      (hx / 2 * s, -hy / 2 + 0 * s, (0, -1)),
+                                      (hx / 2 * s, hy / 2 + 0 * s, (0, 1))]):
+        dn = rq.edge_normal_derivative(edge)
+        exact = n[0] * vx(x, y) + n[1] * vy(x, y)
+        assert np.abs(coef @ dn - exact).max() < 1e-11, edge
