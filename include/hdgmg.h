@@ -61,11 +61,16 @@ typedef enum {
   HDGMG_ETIMEOUT = -6     /* a bounded device wait expired                 */
 } hdgmg_status;
 
-enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1 };  /* tau = c, tau = c / h_min */
+/* tau = c, tau = c / h_min, tau_e = c kappa_e / h_min (per element) */
+enum { HDGMG_TAU_CONST = 0, HDGMG_TAU_OVER_H = 1, HDGMG_TAU_KAPPA_OVER_H = 2 };
 enum { HDGMG_LC_NONE = 0, HDGMG_LC_PRE = 1, HDGMG_LC_BOTH = 2 };
 enum { HDGMG_KRYLOV_NONE = 0, HDGMG_KRYLOV_CG = 1, HDGMG_KRYLOV_GMRES = 2 };
 enum { HDGMG_PREC_FP64 = 0, HDGMG_PREC_FP32 = 1, HDGMG_PREC_FP32_IR = 2, HDGMG_PREC_BF16 = 3 };
 enum { HDGMG_PDE_DIFFUSION = 0, HDGMG_PDE_CONVDIFF = 1 };
+/* local discretisation (Sec. 2): HDG (eqs. HDG_local1/2, HDG_flux) or one of
+ * the hybridized interior penalty schemes of eq. IPG_H, s_f = 1, -1, 0 */
+enum { HDGMG_SCHEME_HDG = 0, HDGMG_SCHEME_SIPG = 1, HDGMG_SCHEME_NIPG = 2,
+       HDGMG_SCHEME_IIPG = 3 };
 /* smoothers of Sec. 4.1 */
 enum { HDGMG_SMOOTH_BLOCK_JACOBI = 0, HDGMG_SMOOTH_POINT_JACOBI = 1,
        HDGMG_SMOOTH_CHEBYSHEV = 2, HDGMG_SMOOTH_LU_SGS = 3 };
@@ -84,15 +89,30 @@ typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
  *   is non-symmetric (full storage on every level, the restriction built from
  *   A_BI); use krylov = GMRES or NONE (CG is rejected with EINVAL), and the
  *   adjoint entry points reject it.  Zero-initialised fields (older callers)
- *   select diffusion. */
+ *   select diffusion.
+ *
+ * scheme (diffusion only; EINVAL with CONVDIFF): HDGMG_SCHEME_HDG (default)
+ * or the primal hybridized interior penalty schemes of eq. IPG_H,
+ *   (kappa grad u, grad w)_K - s_f <u - lambda, kappa grad w.n>_dK
+ *     - <kappa grad u.n, w>_dK + <tau (u - lambda), w>_dK = (f, w)_K,
+ * flux uhat.n = -kappa grad u.n + tau (u - lambda) (eq. IPDG_flux) in the
+ * conservation condition.  SIPG-H (s_f = 1) is symmetric and runs the
+ * symmetric path (CG allowed; the adjoint too); NIPG-H (s_f = -1) and
+ * IIPG-H (s_f = 0) are non-symmetric and take the same path and limits as
+ * CONVDIFF (GMRES or NONE).  The recovered flux is q = -kappa grad u at the
+ * volume nodes.  The paper uses tau = (p+1)(p+2)/h_min (TAU_OVER_H with
+ * tau_c = (p+1)(p+2)); with a variable kappa, TAU_KAPPA_OVER_H keeps the
+ * penalty proportional to kappa_e.  A tau too small for the scheme makes the
+ * volume block indefinite: set-up then returns HDGMG_EBREAKDOWN. */
 typedef struct {
   int32_t n;              /* elements per side                               */
   int32_t p;              /* polynomial order                                */
   double x0, x1, y0, y1;  /* domain                                          */
-  int32_t tau_mode;       /* HDGMG_TAU_CONST or HDGMG_TAU_OVER_H (Sec. 4.1)  */
+  int32_t tau_mode;       /* HDGMG_TAU_* (Sec. 4.1)                          */
   double tau_c;           /* the constant c                                  */
   int32_t pde;            /* HDGMG_PDE_DIFFUSION or HDGMG_PDE_CONVDIFF       */
   double beta_x, beta_y;  /* convection velocity (CONVDIFF only)             */
+  int32_t scheme;         /* HDGMG_SCHEME_* (0 = HDG)                        */
 } hdgmg_problem;
 
 /* Solver options.  hdgmg_default_opts() fills the documented defaults. */

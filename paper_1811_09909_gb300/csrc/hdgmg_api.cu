@@ -53,7 +53,10 @@ namespace {
 struct hdgmg_ctx {
   hdgmg_problem prob{};
   hdgmg_opts opts{};
-  bool ns = false;             // convection-diffusion: non-symmetric operators (full storage)
+  bool ns = false;             // non-symmetric operators (full storage): convection-diffusion,
+                               // NIPG-H, IIPG-H
+  double ktau = 0.0;           // the element-independent tau the element kernels add (a
+                               // kappa-proportional tau is folded into the tables)
   cudaStream_t stream = nullptr;
   double hx = 0, hy = 0, hmin = 0;
   int p = 0, n = 0, nv = 0, nt = 0;
@@ -665,7 +668,7 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   if (c->ns)
     launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
   else
-    launch_rhs(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin, c->Lfac,
+    launch_rhs(s, c->refd, c->p, c->n, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin, c->Lfac,
                f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
   if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->b, -1.0);
@@ -971,7 +974,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   if ((u || q) && c->ns)
     launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
   else if (u || q)
-    launch_recover(s, c->refd, c->p, c->n, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+    launch_recover(s, c->refd, c->p, c->n, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
                    c->Lfac, f, lam_out, u, q);
   STATUS_TRY(check_launch("solve"));
   if (info) {
@@ -1081,8 +1084,13 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (P.n < 2) return fail(HDGMG_EINVAL, "n must be >= 2");
   if (!(P.x1 > P.x0) || !(P.y1 > P.y0)) return fail(HDGMG_EINVAL, "empty domain");
   if (!(P.tau_c > 0.0)) return fail(HDGMG_EINVAL, "tau_c must be positive");
-  if (P.tau_mode != HDGMG_TAU_CONST && P.tau_mode != HDGMG_TAU_OVER_H)
+  if (P.tau_mode != HDGMG_TAU_CONST && P.tau_mode != HDGMG_TAU_OVER_H &&
+      P.tau_mode != HDGMG_TAU_KAPPA_OVER_H)
     return fail(HDGMG_EINVAL, "unknown tau_mode");
+  if (P.scheme < HDGMG_SCHEME_HDG || P.scheme > HDGMG_SCHEME_IIPG)
+    return fail(HDGMG_EINVAL, "unknown scheme");
+  if (P.scheme != HDGMG_SCHEME_HDG && P.pde != HDGMG_PDE_DIFFUSION)
+    return fail(HDGMG_EINVAL, "the interior penalty schemes are for diffusion only");
   if (P.pde != HDGMG_PDE_DIFFUSION && P.pde != HDGMG_PDE_CONVDIFF)
     return fail(HDGMG_EINVAL, "unknown pde");
   if (P.pde == HDGMG_PDE_CONVDIFF && (!std::isfinite(P.beta_x) || !std::isfinite(P.beta_y)))
@@ -1095,8 +1103,11 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
   if (o.precision < 0 || o.precision > 3) return fail(HDGMG_EINVAL, "unknown precision");
   if (o.smoother < 0 || o.smoother > 3) return fail(HDGMG_EINVAL, "unknown smoother");
-  if (P.pde == HDGMG_PDE_CONVDIFF && o.krylov == HDGMG_KRYLOV_CG)
-    return fail(HDGMG_EINVAL, "krylov CG needs a symmetric operator; use GMRES for convection-diffusion");
+  const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
+                      P.scheme == HDGMG_SCHEME_IIPG;
+  if (nonsym && o.krylov == HDGMG_KRYLOV_CG)
+    return fail(HDGMG_EINVAL,
+                "krylov CG needs a symmetric operator; use GMRES for convection-diffusion, NIPG-H, IIPG-H");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
   if (!(o.inner_rtol > 0.0) || !(o.inner_rtol < 1.0)) return fail(HDGMG_EINVAL, "inner_rtol must be in (0,1)");
   int nn = P.n;
@@ -1110,7 +1121,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   hdgmg_ctx* c = new hdgmg_ctx();
   c->prob = P;
   c->opts = o;
-  c->ns = P.pde == HDGMG_PDE_CONVDIFF;
+  c->ns = nonsym;
   c->stream = (cudaStream_t)stream;
   c->n = P.n;
   c->p = P.p;
@@ -1118,6 +1129,12 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   c->hy = (P.y1 - P.y0) / P.n;
   c->hmin = c->hx < c->hy ? c->hx : c->hy;
   c->ref = build_ref_element(P.p, c->hx, c->hy);
+  if (P.scheme != HDGMG_SCHEME_HDG)
+    make_ipdg_tables(c->ref, P.scheme == HDGMG_SCHEME_SIPG ? 1.0 : P.scheme == HDGMG_SCHEME_NIPG ? -1.0 : 0.0);
+  if (P.tau_mode == HDGMG_TAU_KAPPA_OVER_H)
+    fold_kappa_tau(c->ref, P.tau_c / c->hmin);
+  else
+    c->ktau = P.tau_mode == HDGMG_TAU_OVER_H ? P.tau_c / c->hmin : P.tau_c;
   c->nv = c->ref.nv;
   c->nt = c->ref.nt;
   auto cleanup = [&](hdgmg_status st) {
@@ -1148,10 +1165,11 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(upload(&c->refd.Cx, c->ref.Cx));
   CTRY(upload(&c->refd.Cy, c->ref.Cy));
   CTRY(upload(&c->refd.Ef, c->ref.Ef));
+  CTRY(upload(&c->refd.Hv, c->ref.Hv));
   if (c->ns) {
     std::vector<double> S0, W0, V0, ad;
-    const double tau = P.tau_mode == HDGMG_TAU_OVER_H ? P.tau_c / c->hmin : P.tau_c;
-    build_cd_tables(c->ref, tau, P.beta_x, P.beta_y, S0, W0, V0, ad);
+    const bool conv = P.pde == HDGMG_PDE_CONVDIFF;
+    build_cd_tables(c->ref, c->ktau, conv ? P.beta_x : 0.0, conv ? P.beta_y : 0.0, S0, W0, V0, ad);
     CTRY(upload(&c->cd.S0, S0));
     CTRY(upload(&c->cd.W0, W0));
     CTRY(upload(&c->cd.V0, V0));
@@ -1309,7 +1327,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
                                                c->Lfac, c->err, tune_only);
     else
       c->condense_threads =
-          launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+          launch_condense(s, c->refd, c->p, nE, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
                           L0.d64.A, c->Lfac, c->err, tune_only);
   }
   CUDA_TRY(cudaEventRecord(c->evk1, s));
@@ -1357,7 +1375,7 @@ hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa) {
   if (c->ns)
     launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
   else
-    launch_condense(s, c->refd, c->p, nE, c->kap, c->prob.tau_mode, c->prob.tau_c, c->hmin,
+    launch_condense(s, c->refd, c->p, nE, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
                     L0.d64.A, c->Lfac, c->err, true);
   CUDA_TRY(cudaStreamSynchronize(s));
   return check_launch("condensation tuning");

@@ -35,8 +35,26 @@ struct RefElement {
   double hx = 0, hy = 0;
   std::vector<double> nodes, weights;
   std::vector<double> M, G, E, H, F, K, BxT, ByT, Cx, Cy, Ef;
+  // the kappa-proportional part of the left factor V of a non-symmetric
+  // element (A_e = ... - V^T S^-1 W); equal to H except for the primal schemes
+  std::vector<double> Hv;
 };
 RefElement build_ref_element(int p, double hx, double hy);
+
+// Replace the tables of R by those of the hybridized interior penalty element
+// of eq. IPG_H with the given s_f (1 SIPG-H, -1 NIPG-H, 0 IIPG-H):
+//   G = Kst - s_f N - N^T,  H = -s_f Hn,  Hv = -Hn,  K = 0,
+//   BxT[a][b] = -M_a d_x phi_b(x_a), ByT alike, Cx = Cy = 0,
+// with Kst[a][b] = (grad phi_b, grad phi_a), N[a][b] = <phi_b, grad phi_a.n>,
+// Hn[a][k] = <psi_k, grad phi_a.n>; E, F, M unchanged.  The element kernels
+// then compute S = kappa G + tau E, W = kappa H + tau F, V = kappa Hv + tau F,
+// A_e = kappa K + tau I - V^T S^-1 W and q = kappa M^-1 (B^T u - C lambda)
+// = -kappa grad u, i.e. exactly the primal scheme.
+void make_ipdg_tables(RefElement& R, double sf);
+
+// tau_e = t kappa_e: move tau into the kappa-proportional tables
+// (G += t E, H += t F, Hv += t F, K += t I); the kernels then add no tau.
+void fold_kappa_tau(RefElement& R, double t);
 
 // Gauss-Legendre rule on [-1, 1] (ascending nodes) by Newton iteration on P_m.
 void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w);
@@ -92,7 +110,7 @@ struct Level {
 // kernel launchers (k_condense.cu, k_mg.cu, k_blas.cu)
 // ---------------------------------------------------------------------------
 struct RefDevice {     // device copies of RefElement tables (FP64)
-  double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy, *Ef;
+  double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy, *Ef, *Hv;
 };
 
 // kap = exp(log kappa) per element; the element kernels take kap

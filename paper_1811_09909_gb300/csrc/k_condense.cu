@@ -142,6 +142,11 @@ __global__ void __launch_bounds__(TPE * EPB) condense_kernel(
 //   A_e = eps K + diag(tau_f - beta.n_f) - V^T S^-1 W,  g_e = V^T S^-1 M f
 // S has a positive-definite symmetric part (tau_f - beta.n_f / 2 >= tau > 0),
 // so Gaussian elimination without pivoting never meets a zero pivot.
+// The non-symmetric primal schemes NIPG-H and IIPG-H (eq. IPG_H) take the
+// same kernels with their own tables: V = eps Hv + V0 where Hv differs from
+// H, S's symmetric part eps (Kst - (1 + s_f)/2 (N + N^T)) + tau E is
+// positive definite for the penalties of Sec. 4.1 (the set-up flags a
+// non-positive pivot).
 // 1/d for d > 0: FP32 reciprocal as the seed, then two Newton-Raphson steps
 // y <- y (2 - d y) in FP64 (relative error ~1e-7 -> ~1e-14 -> rounding).
 __device__ __forceinline__ double recip_newton(double d) {
@@ -156,7 +161,7 @@ __device__ __forceinline__ double recip_newton(double d) {
 // element-independent parts (tau is the same on every element of the
 // uniform mesh, beta is constant) come precomputed, so every entry of S, W
 // and V costs one FMA:
-//   S = eps G + S0,  W = eps H + W0,  V = eps H + V0,
+//   S = eps G + S0,  W = eps H + W0,  V = eps Hv + V0,
 //   A_e = eps K + diag(adiag) - V^T S^-1 W.
 // S is factored in shared memory (LU without pivoting, pivots inverted once
 // by a Newton reciprocal), the forward sweep applied to W on the fly, then
@@ -168,7 +173,8 @@ __device__ __forceinline__ double recip_newton(double d) {
 template <int NT>
 __global__ void __launch_bounds__(NT) condense_cd_kernel(
     int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ H,
-    const double* __restrict__ K, const double* __restrict__ S0, const double* __restrict__ W0,
+    const double* __restrict__ Hv, const double* __restrict__ K, const double* __restrict__ S0,
+    const double* __restrict__ W0,
     const double* __restrict__ V0, const double* __restrict__ adiag,
     const double* __restrict__ kapv, double* __restrict__ A, double* __restrict__ LU,
     int* __restrict__ err) {
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(NT) condense_cd_kernel(
     __syncthreads();
   }
   if (bad) atomicOr(err, 1);
-  // the factors go out first; S's space then holds V = eps H + V0
+  // the factors go out first; S's space then holds V = eps Hv + V0
   if (LU)
     for (int t = tid; t < nvv; t += NT) {
       const int r = t / nv, c = t - r * nv;
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(NT) condense_cd_kernel(
     }
   __syncthreads();
   double* V = S;
-  for (int t = tid; t < nvt; t += NT) V[t] = fma(eps, H[t], V0[t]);
+  for (int t = tid; t < nvt; t += NT) V[t] = fma(eps, Hv[t], V0[t]);
   __syncthreads();
   for (int t = tid; t < nt * nt; t += NT) {
     const int r = t / nt, c = t % nt;
@@ -388,9 +394,9 @@ __device__ __forceinline__ void lu_solve(const double* __restrict__ LU, int nv, 
   }
 }
 
-// K5 (convection-diffusion): g_e = V^T S^-1 M f_e
+// K5 (convection-diffusion): g_e = V^T S^-1 M f_e, V = eps Hv + V0
 __global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
-                              const double* __restrict__ H, const double* __restrict__ V0,
+                              const double* __restrict__ Hv, const double* __restrict__ V0,
                               const double* __restrict__ kapv, const double* __restrict__ LU,
                               const double* __restrict__ f, double* __restrict__ b) {
   extern __shared__ double smem[];
@@ -409,7 +415,7 @@ __global__ void rhs_cd_kernel(int p, int n, const double* __restrict__ Mdiag,
     const int edge = ed[c / p1];
     if (is_boundary_edge(n, edge)) continue;
     double g = 0.0;
-    for (int a = 0; a < nv; ++a) g += fma(eps, H[a * nt + c], V0[a * nt + c]) * TV(y, a);
+    for (int a = 0; a < nv; ++a) g += fma(eps, Hv[a * nt + c], V0[a * nt + c]) * TV(y, a);
     atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
   }
 }
@@ -669,8 +675,8 @@ int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
 #define CASE(NT)                                                                                  \
   case NT * 16 + 1:                                                                               \
     set_smem_attr_cd<NT>();                                                                       \
-    condense_cd_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.H, ref.K, cd.S0,     \
-                                                  cd.W0, cd.V0, cd.adiag, kap, A, LU, err);       \
+    condense_cd_kernel<NT><<<count, NT, shm, s>>>(nv, nt, nE, e0, ref.G, ref.H, ref.Hv, ref.K,    \
+                                                  cd.S0, cd.W0, cd.V0, cd.adiag, kap, A, LU, err); \
     break;
       CASE(32) CASE(64) CASE(128) CASE(256)
 #undef CASE
@@ -693,7 +699,7 @@ void launch_rhs_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int
   }();
   (void)attr;
   note_launch();
-  rhs_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, cd.V0, kap, LU, f, b);
+  rhs_cd_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.Hv, cd.V0, kap, LU, f, b);
 }
 
 void launch_recover_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int n,

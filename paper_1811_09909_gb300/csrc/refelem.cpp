@@ -10,6 +10,7 @@
 // and the element contribution to the conservation condition gives the trace
 // operator  A_e = kappa K + tau I - W^T S^-1 W,  S = kappa G + tau E,
 // W = kappa H + tau F  (I = trace mass matrix in the orthonormal basis).
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -189,7 +190,116 @@ RefElement build_ref_element(int p, double hx, double hy) {
       for (int l = 0; l < nt; ++l) R.K[k * nt + l] += (cxk * R.Cx[a * nt + l] + cyk * R.Cy[a * nt + l]) * mi;
     }
   }
+  R.Hv = R.H;
   return R;
+}
+
+// Primal hybridized interior penalty element (Sec. 2, eqs. IPDG_flux, IPG_H).
+// Every integrand is a polynomial of degree <= 2p per direction, so the
+// (p+1)-point Gauss rule at the nodes integrates it exactly; at the nodes
+// l_a(xi_q) = delta_aq, which collapses the quadrature sums below.
+void make_ipdg_tables(RefElement& R, double sf) {
+  const int p1 = R.p + 1, nv = R.nv, nt = R.nt;
+  const std::vector<double>& xi = R.nodes;
+  const std::vector<double>& w = R.weights;
+  const double hx = R.hx, hy = R.hy, Jac = hx * hy / 4.0;
+  // D[i][j] = l_j'(xi_i) (barycentric), le[s][j] = l_j(-+1), dl[s][j] = l_j'(-+1)
+  std::vector<double> bw(p1, 1.0), D(p1 * p1, 0.0), le(2 * p1), dl(2 * p1);
+  for (int j = 0; j < p1; ++j)
+    for (int k = 0; k < p1; ++k)
+      if (k != j) bw[j] /= (xi[j] - xi[k]);
+  for (int i = 0; i < p1; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < p1; ++j)
+      if (j != i) {
+        D[i * p1 + j] = (bw[j] / bw[i]) / (xi[i] - xi[j]);
+        diag -= D[i * p1 + j];
+      }
+    D[i * p1 + i] = diag;
+  }
+  for (int s = 0; s < 2; ++s) {
+    const double x = s == 0 ? -1.0 : 1.0;     // not a Gauss node
+    for (int j = 0; j < p1; ++j) {
+      double l = 1.0, sum = 0.0;
+      for (int k = 0; k < p1; ++k)
+        if (k != j) {
+          l *= (x - xi[k]) / (xi[j] - xi[k]);
+          sum += 1.0 / (x - xi[k]);
+        }
+      le[s * p1 + j] = l;
+      dl[s * p1 + j] = l * sum;
+    }
+  }
+  auto idx = [p1](int a1, int a2) { return a2 * p1 + a1; };
+  // stiffness: x-part couples equal y indices, y-part equal x indices
+  std::vector<double> Kst(nv * nv, 0.0);
+  const double cx = Jac * (2.0 / hx) * (2.0 / hx), cy = Jac * (2.0 / hy) * (2.0 / hy);
+  for (int a2 = 0; a2 < p1; ++a2)
+    for (int a1 = 0; a1 < p1; ++a1)
+      for (int b1 = 0; b1 < p1; ++b1) {
+        double s = 0.0;
+        for (int q = 0; q < p1; ++q) s += w[q] * D[q * p1 + a1] * D[q * p1 + b1];
+        Kst[idx(a1, a2) * nv + idx(b1, a2)] += cx * w[a2] * s;
+      }
+  for (int a1 = 0; a1 < p1; ++a1)
+    for (int a2 = 0; a2 < p1; ++a2)
+      for (int b2 = 0; b2 < p1; ++b2) {
+        double s = 0.0;
+        for (int q = 0; q < p1; ++q) s += w[q] * D[q * p1 + a2] * D[q * p1 + b2];
+        Kst[idx(a1, a2) * nv + idx(a1, b2)] += cy * w[a1] * s;
+      }
+  // boundary terms, edge 0 left (n = -x), 1 right, 2 bottom (n = -y), 3 top;
+  // on a vertical edge the tangential node is a2, on a horizontal one a1
+  std::vector<double> N(nv * nv, 0.0), Hn(nv * nt, 0.0);
+  for (int edge = 0; edge < 4; ++edge) {
+    const bool vert = edge < 2;
+    const int s = (edge == 0 || edge == 2) ? 0 : 1;
+    const double sg = s == 0 ? -1.0 : 1.0;
+    const double len = vert ? hy : hx;
+    const double dnorm = sg * 2.0 / (vert ? hx : hy);   // d/dn of the normal coordinate
+    for (int t = 0; t < p1; ++t)            // tangential node (= quadrature point)
+      for (int na = 0; na < p1; ++na) {     // normal-direction index of phi_a
+        const int a = vert ? idx(na, t) : idx(t, na);
+        const double dna = w[t] * (len / 2.0) * dnorm * dl[s * p1 + na];
+        for (int nb = 0; nb < p1; ++nb) {
+          const int b = vert ? idx(nb, t) : idx(t, nb);
+          N[a * nv + b] += dna * le[s * p1 + nb];
+        }
+        for (int k = 0; k < p1; ++k) {
+          const double psi = std::sqrt((2.0 * k + 1.0) / len) * legendre_p(k, xi[t]);
+          Hn[a * nt + edge * p1 + k] += dna * psi;
+        }
+      }
+  }
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) R.G[a * nv + b] = Kst[a * nv + b] - sf * N[a * nv + b] - N[b * nv + a];
+  for (int t = 0; t < nv * nt; ++t) {
+    R.H[t] = -sf * Hn[t];
+    R.Hv[t] = -Hn[t];
+  }
+  std::fill(R.K.begin(), R.K.end(), 0.0);
+  std::fill(R.Cx.begin(), R.Cx.end(), 0.0);
+  std::fill(R.Cy.begin(), R.Cy.end(), 0.0);
+  std::fill(R.BxT.begin(), R.BxT.end(), 0.0);
+  std::fill(R.ByT.begin(), R.ByT.end(), 0.0);
+  for (int a2 = 0; a2 < p1; ++a2)
+    for (int a1 = 0; a1 < p1; ++a1) {
+      const int a = idx(a1, a2);
+      for (int b = 0; b < p1; ++b) {
+        R.BxT[a * nv + idx(b, a2)] = -R.M[a] * (2.0 / hx) * D[a1 * p1 + b];
+        R.ByT[a * nv + idx(a1, b)] = -R.M[a] * (2.0 / hy) * D[a2 * p1 + b];
+      }
+    }
+}
+
+void fold_kappa_tau(RefElement& R, double t) {
+  const int nv = R.nv, nt = R.nt;
+  for (int i = 0; i < nv * nv; ++i) R.G[i] += t * R.E[i];
+  for (int i = 0; i < nv * nt; ++i) {
+    R.H[i] += t * R.F[i];
+    R.Hv[i] += t * R.F[i];
+  }
+  for (int c = 0; c < nt; ++c) R.K[c * nt + c] += t;
 }
 
 void build_cd_tables(const RefElement& R, double tau, double bx, double by,

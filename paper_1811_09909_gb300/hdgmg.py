@@ -11,11 +11,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libhdgmg.so")
 
-TAU_CONST, TAU_OVER_H = 0, 1
+TAU_CONST, TAU_OVER_H, TAU_KAPPA_OVER_H = 0, 1, 2
 LC_NONE, LC_PRE, LC_BOTH = 0, 1, 2
 KRYLOV_NONE, KRYLOV_CG, KRYLOV_GMRES = 0, 1, 2
 PREC_FP64, PREC_FP32, PREC_FP32_IR, PREC_BF16 = 0, 1, 2, 3
 PDE_DIFFUSION, PDE_CONVDIFF = 0, 1
+SCHEME_HDG, SCHEME_SIPG, SCHEME_NIPG, SCHEME_IIPG = 0, 1, 2, 3
 SMOOTH_BLOCK_JACOBI, SMOOTH_POINT_JACOBI, SMOOTH_CHEBYSHEV, SMOOTH_LU_SGS = 0, 1, 2, 3
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
@@ -35,7 +36,8 @@ class Problem(ctypes.Structure):
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double),
                 ("tau_mode", ctypes.c_int32), ("tau_c", ctypes.c_double),
-                ("pde", ctypes.c_int32), ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double)]
+                ("pde", ctypes.c_int32), ("beta_x", ctypes.c_double), ("beta_y", ctypes.c_double),
+                ("scheme", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -150,12 +152,13 @@ def _hptr(a):
 class Solver:
     """One HDG trace problem on the GPU.
 
-    n, p, domain, tau as in hdgmg_problem; options as keyword arguments of
+    n, p, domain, tau, beta (convection velocity or None) and scheme
+    (SCHEME_*) as in hdgmg_problem; options as keyword arguments of
     hdgmg_opts (coarsest_n, m_fine, m_growth, m_max, local_corr, omega,
     krylov, max_it, rtol, precision)."""
 
     def __init__(self, n, p, tau_mode=TAU_OVER_H, tau_c=1.0, domain=(0.0, 1.0, 0.0, 1.0),
-                 stream=None, beta=None, **opts):
+                 stream=None, beta=None, scheme=SCHEME_HDG, **opts):
         import torch
         lib = load()
         self.torch = torch
@@ -165,7 +168,8 @@ class Solver:
         self.n_edges = 2 * n * (n + 1)
         pde = PDE_DIFFUSION if beta is None else PDE_CONVDIFF
         bx, by = (0.0, 0.0) if beta is None else (float(beta[0]), float(beta[1]))
-        prob = Problem(n, p, domain[0], domain[1], domain[2], domain[3], tau_mode, tau_c, pde, bx, by)
+        prob = Problem(n, p, domain[0], domain[1], domain[2], domain[3], tau_mode, tau_c, pde, bx, by,
+                       scheme)
         self.opts = default_opts(**opts)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -304,8 +308,8 @@ def _ptr_array(tensors):
 class Batch:
     """Many independent problems solved concurrently on one GPU.
 
-    problems: list of dicts with n, p and optionally tau_mode, tau_c, domain;
-    options as keyword arguments (one set for all problems)."""
+    problems: list of dicts with n, p and optionally tau_mode, tau_c, domain,
+    beta, scheme; options as keyword arguments (one set for all problems)."""
 
     def __init__(self, problems, nthreads=8, stream=None, **opts):
         import torch
@@ -320,7 +324,8 @@ class Batch:
             arr[i] = Problem(pr["n"], pr["p"], dom[0], dom[1], dom[2], dom[3],
                              pr.get("tau_mode", TAU_OVER_H), pr.get("tau_c", 1.0),
                              PDE_DIFFUSION if beta is None else PDE_CONVDIFF,
-                             *((0.0, 0.0) if beta is None else (float(beta[0]), float(beta[1]))))
+                             *((0.0, 0.0) if beta is None else (float(beta[0]), float(beta[1]))),
+                             pr.get("scheme", SCHEME_HDG))
             self.problems.append((pr["n"], pr["p"]))
         self.opts = default_opts(**opts)
         if stream is None:

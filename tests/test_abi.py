@@ -57,13 +57,17 @@ def test_default_options(lib):
     (dict(krylov=3), "krylov"),
     (dict(pde=1, krylov=1), "symmetric"), (dict(pde=5), "unknown pde"),
     (dict(smoother=4), "unknown smoother"),
+    (dict(scheme=4), "unknown scheme"), (dict(scheme=-1), "unknown scheme"),
+    (dict(scheme=2, pde=1, krylov=2), "diffusion only"),
+    (dict(scheme=2, krylov=1), "symmetric"), (dict(scheme=3, krylov=1), "symmetric"),
+    (dict(tau_mode=3), "tau_mode"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg
     n = kw.get("n", 16)
     p = kw.get("p", 2)
-    prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, hdgmg.TAU_CONST, kw.get("tau_c", 1.0),
-                         kw.get("pde", 0), 1.0, 0.5)
+    prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, kw.get("tau_mode", hdgmg.TAU_CONST),
+                         kw.get("tau_c", 1.0), kw.get("pde", 0), 1.0, 0.5, kw.get("scheme", 0))
     o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2), krylov=kw.get("krylov", 1),
                            gmres_restart=kw.get("restart", 30), smoother=kw.get("smoother", 0))
     ctx = ctypes.c_void_p()
