@@ -20,7 +20,12 @@ Workloads (paper: arXiv:1811.09909):
   * ``lognormal``     : log kappa iid N(0, sigma^2) per element (seeded), f = 1,
     g_D = 0 -- the synthetic stand-in for the heterogeneous permeability of
     Example V (SPE10 layer 75, a dataset that is not used here).
-  * ``checkerboard``  : Example IV's two-block kappa in {1e6, 1}, f = 1, g_D = 0.
+  * ``example3``      : Example III's smooth kappa = 1 + 0.5 sin(2 pi x) cos(3 pi y)
+    on the unit square (the paper's circle of triangles is not a quad mesh),
+    sampled at element centres, with u = x y exp(x^2 y^3) and
+    f = -div(kappa grad u) of the smooth kappa.
+  * ``checkerboard``  : Example IV's two-block kappa in {1e6, 1} (element
+    centres decide the block), f = 1, g_D = 0.
   * ``convdiff``      : -eps lap u + beta.grad u = f with constant eps (given
     per element as log eps) and beta, manufactured u = sin(pi x) sin(pi y)
     (so g_D = 0), tau_e = eps/h on every face plus the upwind max(beta.n, 0)
@@ -176,6 +181,27 @@ def lognormal(n=256, p=4, sigma=1.0, seed=2, tau_mode="over_h", tau_c=1.0, nrhs=
     f = np.ones((nrhs, (p + 1) ** 2, n * n))
     gD = np.zeros((nrhs, p + 1, n_edges(n)))
     return Workload(f"lognormal_{n}_p{p}_s{seed}", n, p, logk, f, gD, tau_mode, tau_c, seed=seed)
+
+
+def ex3_kappa(x, y):
+    return 1.0 + 0.5 * np.sin(2 * np.pi * x) * np.cos(3 * np.pi * y)
+
+
+def ex3_f(x, y):
+    """-div(kappa grad u) = kappa (-lap u) + grad kappa . q with q = -grad u."""
+    gx = np.pi * np.cos(2 * np.pi * x) * np.cos(3 * np.pi * y)
+    gy = -1.5 * np.pi * np.sin(2 * np.pi * x) * np.sin(3 * np.pi * y)
+    qx, qy = ex1_q(x, y)
+    return ex3_kappa(x, y) * ex1_f(x, y) + gx * qx + gy * qy
+
+
+def example3(n, p, tau_mode="over_h", tau_c=1.0):
+    """Example III on the unit square: kappa sampled at element centres."""
+    j, i = np.divmod(np.arange(n * n), n)
+    logk = np.log(ex3_kappa((i + 0.5) / n, (j + 0.5) / n))
+    f = nodal(ex3_f, n, p)[None]
+    gD = dirichlet(ex1_u, n, p)[None]
+    return Workload(f"example3_{n}_p{p}", n, p, logk, f, gD, tau_mode, tau_c)
 
 
 def checkerboard(n, p, tau_mode="over_h", tau_c=1.0):
