@@ -318,24 +318,24 @@ def run_ours(args):
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one condensation launch at 256^2, p = 4: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
-# (profiles/condense_256_p4.md).
-CONDENSE_TRAFFIC_BYTES = 8684032 + 228024320
+# (profiles/condense_256_p4.md); None until captured for this kernel.
+CONDENSE_TRAFFIC_BYTES = 576512 + 54012416
 
 
 def condense_flops(p, nE):
-    """Algorithmic flops of K1 per launch: Cholesky of S (n_v x n_v),
-    V = L^-1 W (n_t right-hand sides), V^T V (symmetric, n_t x n_t), as FMAs."""
+    """Algorithmic flops of K1 per launch in the basis that diagonalises every
+    volume block: s_i = kappa g_i + tau e_i (n_v FMAs), U = s^-1/2 (kappa P +
+    tau Q) (n_v n_t entries, 3 flops each), A_e = kappa K + tau I - U^T U
+    (n_t (n_t + 1) / 2 packed entries, n_v FMAs each, plus the kappa K term)."""
     nv, nt = (p + 1) ** 2, 4 * (p + 1)
-    chol = sum(m * (m + 1) // 2 for m in range(nv))
-    fwd = nt * nv * (nv - 1) // 2
-    schur = nt * (nt + 1) // 2 * nv
-    return 2.0 * (chol + fwd + schur) * nE
+    nsa = nt * (nt + 1) // 2
+    return (2.0 * nv + 3.0 * nv * nt + 2.0 * nsa * (nv + 1)) * nE
 
 
 def roofline_condense(ms):
     flops = condense_flops(P_ORDER, N_MESH * N_MESH)
     achieved = flops / (ms * 1e-3) / 1e12
-    return {"kernel": "condense_kernel (element condensation, FP64)", "bound": "alu",
+    return {"kernel": "condense_eig_kernel (element condensation, FP64)", "bound": "alu",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CONDENSE_TRAFFIC_BYTES,
             "algorithmic_flops_per_launch": flops, "launch_ms": ms,

@@ -193,10 +193,12 @@ hdgmg_status hdgmg_create(hdgmg_ctx** ctx, const hdgmg_problem* problem,
 
 /* Set-up (Sec. 2 static condensation; Sec. 3.1-3.2 hierarchy):
  *   log_kappa  device, [n*n] FP64, per-element log-diffusivity.
- * Runs element condensation (local Cholesky of the u-Schur complement of the
- * volume block), the edge block-Jacobi inverses, p-coarsening, every 2x2
- * agglomeration level and the dense Cholesky factorisation of the coarsest
- * operator.  EBREAKDOWN if a local pivot is not positive (e.g. kappa NaN). */
+ * Runs element condensation (symmetric volume blocks: in the basis that
+ * diagonalises every element's kappa G + tau E, built once at create;
+ * non-symmetric ones: local LU), the edge block-Jacobi inverses,
+ * p-coarsening, every 2x2 agglomeration level and the dense factorisation of
+ * the coarsest operator.  EBREAKDOWN if a volume block is not positive
+ * definite / a local pivot is not positive (e.g. kappa NaN). */
 hdgmg_status hdgmg_setup(hdgmg_ctx* ctx, const double* log_kappa);
 
 /* Solve (Sec. 2-3) for nrhs right-hand sides, one after another:
@@ -245,7 +247,7 @@ hdgmg_status hdgmg_run_host(hdgmg_ctx* ctx, const double* log_kappa,
  *   dJ_dlogk  device, [n*n] FP64 out (may be NULL)
  *   dJ_df     device, [(p+1)^2][n*n] FP64 out (may be NULL)
  *   info      host, out (may be NULL): the adjoint solve.
- * The local Cholesky factors of the set-up are reused (kept in memory). */
+ * The element data of the set-up are reused (kept in memory). */
 hdgmg_status hdgmg_gradient(hdgmg_ctx* ctx, const double* f, const double* g_D,
                             const double* u_obs, double* J, double* dJ_dlogk,
                             double* dJ_df, hdgmg_info* info);

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhdgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["refelem.cpp", "k_condense.cu", "k_mg.cu", "k_ctail.cu", "k_krylov.cu", "hdgmg_api.cu",
+SOURCES = ["refelem.cpp", "eigbasis.cpp", "k_condense.cu", "k_mg.cu", "k_ctail.cu", "k_krylov.cu", "hdgmg_api.cu",
            "hdgmg_batch.cpp"]
 # k_edge_inst.cu is built once per (real type, trace modes per edge), plus
 # once per ND for the BF16-storage matvec

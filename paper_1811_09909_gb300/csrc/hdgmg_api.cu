@@ -67,7 +67,7 @@ struct hdgmg_ctx {
   std::vector<Level> levels;
   double* logk = nullptr;
   double* kap = nullptr;       // exp(log kappa) per element
-  double* Lfac = nullptr;      // Cholesky (packed) or, when ns, LU (full) factors of S
+  double* Lfac = nullptr;      // LU factors of S (full), non-symmetric only
   int* err = nullptr;
   int* err_h = nullptr;
   // coarsest level
@@ -668,8 +668,7 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   if (c->ns)
     launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
   else
-    launch_rhs(s, c->refd, c->p, c->n, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin, c->Lfac,
-               f, c->b);
+    launch_rhs(s, c->refd, c->p, c->n, c->kap, c->ktau, f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
   if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->b, -1.0);
   return check_launch("condensed right-hand side");
@@ -974,8 +973,7 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   if ((u || q) && c->ns)
     launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
   else if (u || q)
-    launch_recover(s, c->refd, c->p, c->n, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
-                   c->Lfac, f, lam_out, u, q);
+    launch_recover(s, c->refd, c->p, c->n, c->kap, c->ktau, f, lam_out, u, q);
   STATUS_TRY(check_launch("solve"));
   if (info) {
     info->iters = it;
@@ -1166,6 +1164,19 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(upload(&c->refd.Cy, c->ref.Cy));
   CTRY(upload(&c->refd.Ef, c->ref.Ef));
   CTRY(upload(&c->refd.Hv, c->ref.Hv));
+  if (!c->ns) {
+    // the basis that diagonalises every element's volume block
+    EigBasis eb;
+    if (!build_eig_basis(c->ref, c->ktau, c->hmin, eb))
+      return cleanup(fail(HDGMG_EINVAL, "no positive-definite combination of the volume forms"));
+    for (double& v : eb.e) v *= c->ktau;    // the kernels take tau e and tau Q
+    for (double& v : eb.Q) v *= c->ktau;
+    CTRY(upload(&c->refd.Phi, eb.Phi));
+    CTRY(upload(&c->refd.eg, eb.g));
+    CTRY(upload(&c->refd.ee, eb.e));
+    CTRY(upload(&c->refd.P, eb.P));
+    CTRY(upload(&c->refd.Q, eb.Q));
+  }
   if (c->ns) {
     std::vector<double> S0, W0, V0, ad;
     const bool conv = P.pde == HDGMG_PDE_CONVDIFF;
@@ -1226,7 +1237,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   const int64_t len = c->fine_len();
   CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
   CTRY(c->alloc(&c->kap, (size_t)P.n * P.n));
-  CTRY(c->alloc(&c->Lfac, (size_t)(c->ns ? c->nv * c->nv : c->nv * (c->nv + 1) / 2) * P.n * P.n));
+  if (c->ns) CTRY(c->alloc(&c->Lfac, (size_t)c->nv * c->nv * P.n * P.n));
   CTRY(c->alloc(&c->err, 4));
   CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
   CTRY(c->alloc(&c->x, len));
@@ -1327,8 +1338,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
                                                c->Lfac, c->err, tune_only);
     else
       c->condense_threads =
-          launch_condense(s, c->refd, c->p, nE, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
-                          L0.d64.A, c->Lfac, c->err, tune_only);
+          launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, tune_only);
   }
   CUDA_TRY(cudaEventRecord(c->evk1, s));
   STATUS_TRY(check_launch("condensation"));
@@ -1375,8 +1385,7 @@ hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa) {
   if (c->ns)
     launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
   else
-    launch_condense(s, c->refd, c->p, nE, c->kap, HDGMG_TAU_CONST, c->ktau, c->hmin,
-                    L0.d64.A, c->Lfac, c->err, true);
+    launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, true);
   CUDA_TRY(cudaStreamSynchronize(s));
   return check_launch("condensation tuning");
 }

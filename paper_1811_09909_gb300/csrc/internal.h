@@ -52,6 +52,16 @@ RefElement build_ref_element(int p, double hx, double hy);
 // = -kappa grad u, i.e. exactly the primal scheme.
 void make_ipdg_tables(RefElement& R, double sf);
 
+// Basis of the volume space that diagonalises G and E together (eigbasis.cpp):
+// Phi^T (G + r0 E) Phi = I, Phi^T G Phi = diag(g), Phi^T E Phi = diag(e),
+// P = Phi^T H, Q = Phi^T F ([nv][nt], row i = basis vector i).  r0 >= the
+// given value, grown until G + r0 E is positive definite; false if it never is.
+struct EigBasis {
+  std::vector<double> Phi, g, e, P, Q;   // Phi [nv][nv], column i = phi_i
+  double r0 = 0.0;
+};
+bool build_eig_basis(const RefElement& R, double r0, double hmin, EigBasis& out);
+
 // tau_e = t kappa_e: move tau into the kappa-proportional tables
 // (G += t E, H += t F, Hv += t F, K += t I); the kernels then add no tau.
 void fold_kappa_tau(RefElement& R, double t);
@@ -111,6 +121,8 @@ struct Level {
 // ---------------------------------------------------------------------------
 struct RefDevice {     // device copies of RefElement tables (FP64)
   double *M, *G, *E, *H, *F, *K, *BxT, *ByT, *Cx, *Cy, *Ef, *Hv;
+  double *Phi, *eg, *ee, *P, *Q;   // EigBasis (symmetric volume blocks only), with the
+                                   // element-independent tau applied: ee = tau e, Q = tau Q
 };
 
 // kap = exp(log kappa) per element; the element kernels take kap
@@ -118,15 +130,15 @@ void launch_kappa(cudaStream_t s, int nE, const double* logk, double* kap);
 // returns the autotuned launch shape, threads per element * 16 + elements per
 // block; tune_only: only make sure the choice for this (kernel, p) is made
 // (times the candidates on a sample)
+// symmetric volume blocks S = kappa G + tau E through the EigBasis tables
+// (no stored factors): A_e = kappa K + tau I - U^T U,
+// U = diag(kappa g + tau e)^-1/2 (kappa P + tau Q)
 int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE,
-                    const double* kap, int tau_mode, double tau_c, double hmin,
-                    double* A, double* Lfac, int* err, bool tune_only = false);
+                    const double* kap, double tau, double* A, int* err, bool tune_only = false);
 void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n,
-                const double* kap, int tau_mode, double tau_c, double hmin,
-                const double* Lfac, const double* f, double* b);
+                const double* kap, double tau, const double* f, double* b);
 void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
-                    const double* kap, int tau_mode, double tau_c, double hmin,
-                    const double* Lfac, const double* f, const double* lam,
+                    const double* kap, double tau, const double* f, const double* lam,
                     double* u, double* q);
 
 // convection-diffusion element (non-symmetric A_e, full [nt*nt][nE]; LU

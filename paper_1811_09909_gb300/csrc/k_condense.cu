@@ -1,12 +1,17 @@
 // Element-local kernels: static condensation (K1), condensed right-hand side
 // (K5) and local recovery (K12) of the HDG scheme (arXiv:1811.09909, Sec. 2).
 //
-// Per element, with S = kappa G + tau E (SPD, n_v x n_v) and
-// W = kappa H + tau F (n_v x n_t):
-//   K1: S = L L^T (Cholesky: the LU of the volume block after the diagonal
-//       mass block of q is eliminated), V = L^-1 W, A_e = kappa K + tau I - V^T V.
-//   K5: g_e = W^T S^-1 (M f_e), assembled into the edge vector.
+// Per element, with S = kappa G + tau E (n_v x n_v) and W = kappa H + tau F
+// (n_v x n_t):
+//   K1: A_e = kappa K + tau I - W^T S^-1 W,
+//   K5: g_e = W^T S^-1 (M f_e), assembled into the edge vector,
 //   K12: u_e = S^-1 (M f_e + W lambda_e),  q_d = kappa M^-1 (B_d^T u - C_d lambda_e).
+// Symmetric S (diffusion, SIPG-H): every element's S is diagonal in one basis
+// Phi (eigbasis.cpp), S = Phi^-T diag(s) Phi^-1 with s_i = kappa g_i + tau e_i,
+// so no element is factored: W^T S^-1 W = U^T U with
+// U = diag(s)^-1/2 (kappa P + tau Q), P = Phi^T H, Q = Phi^T F, and
+// S^-1 y = Phi diag(1/s) Phi^T y.  Non-symmetric S (convection-diffusion,
+// NIPG-H, IIPG-H): LU without pivoting per element, factors kept for K5/K12.
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -17,10 +22,6 @@
 namespace hdgmg {
 
 namespace {
-
-__device__ __forceinline__ double tau_of(int tau_mode, double tau_c, double hmin) {
-  return tau_mode == HDGMG_TAU_OVER_H ? tau_c / hmin : tau_c;
-}
 
 __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
   // row-major packed lower triangle: t = i(i+1)/2 + j, 0 <= j <= i
@@ -35,101 +36,83 @@ __device__ __forceinline__ void tri_index(int t, int& i, int& j) {
 // inverse square root, y <- y (3 - d y^2) / 2, in FP64 (the error squares at
 // every step: ~1e-7 -> ~1e-14 -> FP64 rounding).
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  double y = (double)rsqrtf((float)d);
+  const float df = (float)d;
+  double y = (df > 1e-30f && df < 1e30f) ? (double)rsqrtf(df) : 1.0 / sqrt(d);
   y = y * (1.5 - 0.5 * d * y * y);
   y = y * (1.5 - 0.5 * d * y * y);
   return y;
 }
 
-// K1: TPE threads per element and EPB elements per block, in lockstep (the
-// elements of a block run the same loops, so block barriers serve all of
-// them); the local matrices in shared memory, per element
-//   S: nv x nv (full square, lower part used), V: nv x nt, 1/sqrt pivots.
-// The FP64 pipe is the bottleneck on GB300: a pivot's square root and
-// reciprocal is computed once per element (one thread), so several elements
-// per warp share the cost of that single-lane step and of the partially
-// filled last pass of each loop.  (TPE, EPB) is picked per p by a timing
-// autotuner (tune_config below); the result does not depend on it.
-// Elements e_begin + blockIdx.x * EPB + (threadIdx.x / TPE); a block's
-// elements past nE recompute the last element and write nothing.
-template <int TPE, int EPB>
-__global__ void __launch_bounds__(TPE * EPB) condense_kernel(
-    int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ Eb,
-    const double* __restrict__ H, const double* __restrict__ F, const double* __restrict__ K,
-    const double* __restrict__ kapv, int tau_mode, double tau_c, double hmin,
-    double* __restrict__ A, double* __restrict__ Lfac, int* __restrict__ err) {
+// 1/d for d > 0: FP32 reciprocal as the seed, then two Newton-Raphson steps
+// y <- y (2 - d y) in FP64 (relative error ~1e-7 -> ~1e-14 -> rounding).
+__device__ __forceinline__ double recip_newton(double d) {
+  const float df = (float)d;
+  double y = (df > 1e-30f && df < 1e30f) ? (double)__frcp_rn(df) : 1.0 / d;
+  y = y * (2.0 - d * y);
+  y = y * (2.0 - d * y);
+  return y;
+}
+
+// K1 (symmetric S): EPB elements per block of 128 threads, no factorisation:
+//   s_i = kappa g_i + tau e_i,  U[i][c] = s_i^-1/2 (kappa P[i][c] + tau Q[i][c]),
+//   A_e = kappa K + tau I - U^T U   (packed lower triangle, [entry][element]).
+// The tables come with tau applied (ev = tau e, Q = tau Q): tau is the same on
+// every element, so each entry of U costs one FMA and one multiplication.
+// Shared memory: kappa [EPB], s^-1/2 [nv][EPB] and U [nv][nt][EPB], the
+// element index fastest so that the threads of a warp, which take
+// consecutive elements of the same entry, read consecutive words.  S is
+// positive definite exactly when every s_i > 0; otherwise *err is set.
+// Elements [0, count) are formed; nE is the stride of A.
+template <int EPB>
+__global__ void __launch_bounds__(128) condense_eig_kernel(
+    int nv, int nt, int nE, int count, const double* __restrict__ g, const double* __restrict__ ev,
+    const double* __restrict__ P, const double* __restrict__ Q, const double* __restrict__ K,
+    const double* __restrict__ kapv, double tau, double* __restrict__ A, int* __restrict__ err) {
+  constexpr int NT = 128;
   extern __shared__ double smem[];
-  const int tid = threadIdx.x % TPE, el = threadIdx.x / TPE;
-  const int e0 = e_begin + blockIdx.x * EPB + el;
-  const bool active = e0 < nE;
-  const int e = active ? e0 : nE - 1;
-  double* S = smem + (size_t)el * (nv * nv + nv * nt + nv);
-  double* V = S + nv * nv;
-  double* dinv = V + nv * nt;
-  const double kap = kapv[e];
-  const double tau = tau_of(tau_mode, tau_c, hmin);
-  const int nsv = nv * (nv + 1) / 2;
-  for (int t = tid; t < nsv; t += TPE) {
-    int i, j;
-    tri_index(t, i, j);
-    S[i * nv + j] = fma(kap, G[i * nv + j], tau * Eb[i * nv + j]);
-  }
-  for (int t = tid; t < nv * nt; t += TPE) V[t] = fma(kap, H[t], tau * F[t]);
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  double* kp = smem;                  // [EPB]
+  double* rs = kp + EPB;              // [nv][EPB]
+  double* U = rs + nv * EPB;          // [nv * nt][EPB]
+  if (tid < EPB) kp[tid] = kapv[min(e0 + tid, count - 1)];
   __syncthreads();
   bool bad = false;
-  for (int k = 0; k < nv; ++k) {
-    if (tid == 0) {
-      double d = S[k * nv + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = true;
-        d = 1.0;
-      }
-      const double di = rsqrt_newton(d);
-      S[k * nv + k] = d * di;
-      dinv[k] = di;
+  for (int idx = tid; idx < nv * EPB; idx += NT) {
+    const int el = idx % EPB, i = idx / EPB;
+    double s = fma(kp[el], g[i], ev[i]);
+    if (!(s > 0.0) || !isfinite(s)) {
+      if (e0 + el < count) bad = true;
+      s = 1.0;
     }
-    __syncthreads();
-    const double di = dinv[k];
-    for (int i = k + 1 + tid; i < nv; i += TPE) S[i * nv + k] *= di;
-    for (int c = tid; c < nt; c += TPE) V[k * nt + c] *= di;
-    __syncthreads();
-    const int m = nv - k - 1;
-    const int ntri = m * (m + 1) / 2;
-    for (int t = tid; t < ntri; t += TPE) {
-      int ii, jj;
-      tri_index(t, ii, jj);
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      S[i * nv + j] = fma(-S[i * nv + k], S[j * nv + k], S[i * nv + j]);
-    }
-    for (int t = tid; t < m * nt; t += TPE) {
-      const int i = k + 1 + t / nt, c = t % nt;
-      V[i * nt + c] = fma(-S[i * nv + k], V[k * nt + c], V[i * nt + c]);
-    }
-    __syncthreads();
+    rs[idx] = rsqrt_newton(s);
   }
-  if (bad && active) atomicOr(err, 1);
-  const int nsa = nt * (nt + 1) / 2;
-  for (int t = tid; t < nsa; t += TPE) {
+  __syncthreads();
+  const int nvt = nv * nt;
+  for (int idx = tid; idx < nvt * EPB; idx += NT) {
+    const int el = idx % EPB, ic = idx / EPB;
+    U[idx] = rs[(ic / nt) * EPB + el] * fma(kp[el], P[ic], Q[ic]);
+  }
+  __syncthreads();
+  const int nsa = nt * (nt + 1) / 2, st = nt * EPB;
+  for (int idx = tid; idx < nsa * EPB; idx += NT) {
+    const int el = idx % EPB, t = idx / EPB;
     int r, c;
     tri_index(t, r, c);
+    const double* ur = U + r * EPB + el;
+    const double* uc = U + c * EPB + el;
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
     for (; i + 1 < nv; i += 2) {
-      s0 = fma(V[i * nt + r], V[i * nt + c], s0);
-      s1 = fma(V[(i + 1) * nt + r], V[(i + 1) * nt + c], s1);
+      s0 = fma(ur[i * st], uc[i * st], s0);
+      s1 = fma(ur[(i + 1) * st], uc[(i + 1) * st], s1);
     }
-    if (i < nv) s0 = fma(V[i * nt + r], V[i * nt + c], s0);
-    double a = fma(kap, K[r * nt + c], -(s0 + s1));
+    if (i < nv) s0 = fma(ur[i * st], uc[i * st], s0);
+    double a = fma(kp[el], K[r * nt + c], -(s0 + s1));
     if (r == c) a += tau;
-    if (active) A[(size_t)t * nE + e] = a;
+    if (e0 + el < count) A[(size_t)t * nE + e0 + el] = a;
   }
-  if (Lfac && active) {
-    for (int t = tid; t < nsv; t += TPE) {
-      int r, c;
-      tri_index(t, r, c);
-      Lfac[(size_t)t * nE + e] = S[r * nv + c];
-    }
-  }
+  if (bad) atomicOr(err, 1);
 }
 
 // ------------------------------------------ convection-diffusion element
@@ -147,15 +130,6 @@ __global__ void __launch_bounds__(TPE * EPB) condense_kernel(
 // H, S's symmetric part eps (Kst - (1 + s_f)/2 (N + N^T)) + tau E is
 // positive definite for the penalties of Sec. 4.1 (the set-up flags a
 // non-positive pivot).
-// 1/d for d > 0: FP32 reciprocal as the seed, then two Newton-Raphson steps
-// y <- y (2 - d y) in FP64 (relative error ~1e-7 -> ~1e-14 -> rounding).
-__device__ __forceinline__ double recip_newton(double d) {
-  const float df = (float)d;
-  double y = (df > 1e-30f && df < 1e30f) ? (double)__frcp_rn(df) : 1.0 / d;
-  y = y * (2.0 - d * y);
-  y = y * (2.0 - d * y);
-  return y;
-}
 
 // K1 (non-symmetric): one block of NT threads per element (autotuned).  The
 // element-independent parts (tau is the same on every element of the
@@ -269,22 +243,6 @@ __global__ void kappa_kernel(int nE, const double* __restrict__ logk, double* __
 // the 32 threads of a warp touch 32 consecutive words.
 #define TV(arr, i) arr[(size_t)(i) * blockDim.x + threadIdx.x]
 
-// solve L L^T y = y in place (L packed SoA, element e)
-__device__ __forceinline__ void chol_solve(const double* __restrict__ L, int nv, int nE, int e,
-                                           double* y) {
-  for (int i = 0; i < nv; ++i) {
-    double s = TV(y, i);
-    const int row = i * (i + 1) / 2;
-    for (int j = 0; j < i; ++j) s -= L[(size_t)(row + j) * nE + e] * TV(y, j);
-    TV(y, i) = s / L[(size_t)(row + i) * nE + e];
-  }
-  for (int i = nv - 1; i >= 0; --i) {
-    double s = TV(y, i);
-    for (int j = i + 1; j < nv; ++j) s -= L[(size_t)(j * (j + 1) / 2 + i) * nE + e] * TV(y, j);
-    TV(y, i) = s / L[(size_t)(i * (i + 1) / 2 + i) * nE + e];
-  }
-}
-
 __device__ __forceinline__ void element_edges(int n, int e, int ed[4]) {
   const int j = e / n, i = e - j * n;
   const int nvert = n * (n + 1);
@@ -304,11 +262,17 @@ __device__ __forceinline__ bool is_boundary_edge(int n, int edge) {
   return j == 0 || j == n;
 }
 
-// K5: thread per element; shared memory y[nv][blockDim]
+// s_i^-1 for element e (symmetric S)
+__device__ __forceinline__ double inv_s(const double* g, const double* ev, double kap, int i) {
+  return recip_newton(fma(kap, g[i], ev[i]));
+}
+
+// K5 (symmetric S): thread per element; shared memory y, z [nv][blockDim].
+//   z = diag(1/s) Phi^T (M f_e),  g_e = (kappa P + tau Q)^T z   (ev, Q scaled by tau)
 __global__ void rhs_kernel(int p, int n, const double* __restrict__ Mdiag,
-                           const double* __restrict__ H, const double* __restrict__ F,
-                           const double* __restrict__ kapv, int tau_mode, double tau_c,
-                           double hmin, const double* __restrict__ L,
+                           const double* __restrict__ Phi, const double* __restrict__ g,
+                           const double* __restrict__ ev, const double* __restrict__ P,
+                           const double* __restrict__ Q, const double* __restrict__ kapv,
                            const double* __restrict__ f, double* __restrict__ b) {
   extern __shared__ double smem[];
   const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
@@ -316,29 +280,38 @@ __global__ void rhs_kernel(int p, int n, const double* __restrict__ Mdiag,
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   double* y = smem;
+  double* z = smem + (size_t)nv * blockDim.x;
   const double kap = kapv[e];
-  const double tau = tau_of(tau_mode, tau_c, hmin);
   for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
-  chol_solve(L, nv, nE, e, y);
+  for (int i = 0; i < nv; ++i) {
+    double s = 0.0;
+    for (int a = 0; a < nv; ++a) s = fma(Phi[a * nv + i], TV(y, a), s);
+    TV(z, i) = s * inv_s(g, ev, kap, i);
+  }
   int ed[4];
   element_edges(n, e, ed);
   const int nedge = 2 * n * (n + 1);
   for (int c = 0; c < nt; ++c) {
     const int edge = ed[c / p1];
     if (is_boundary_edge(n, edge)) continue;
-    double g = 0.0;
-    for (int a = 0; a < nv; ++a) g += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(y, a);
-    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
+    double gp = 0.0, gq = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      gp = fma(P[i * nt + c], TV(z, i), gp);
+      gq = fma(Q[i * nt + c], TV(z, i), gq);
+    }
+    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], fma(kap, gp, gq));
   }
 }
 
-// K12: thread per element; shared memory y[nv][blockDim], le[nt][blockDim]
+// K12 (symmetric S): thread per element; shared memory y, z [nv][blockDim],
+// le [nt][blockDim].
+//   z = diag(1/s) (Phi^T M f_e + (kappa P + tau Q) lambda_e),  u = Phi z
 __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
-                               const double* __restrict__ H, const double* __restrict__ F,
-                               const double* __restrict__ BxT, const double* __restrict__ ByT,
-                               const double* __restrict__ Cx, const double* __restrict__ Cy,
-                               const double* __restrict__ kapv, int tau_mode, double tau_c,
-                               double hmin, const double* __restrict__ L,
+                               const double* __restrict__ Phi, const double* __restrict__ g,
+                               const double* __restrict__ ev, const double* __restrict__ P,
+                               const double* __restrict__ Q, const double* __restrict__ BxT,
+                               const double* __restrict__ ByT, const double* __restrict__ Cx,
+                               const double* __restrict__ Cy, const double* __restrict__ kapv,
                                const double* __restrict__ f, const double* __restrict__ lam,
                                double* __restrict__ u, double* __restrict__ q) {
   extern __shared__ double smem[];
@@ -347,19 +320,28 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   double* y = smem;
-  double* le = smem + (size_t)nv * blockDim.x;
+  double* z = smem + (size_t)nv * blockDim.x;
+  double* le = smem + (size_t)2 * nv * blockDim.x;
   const double kap = kapv[e];
-  const double tau = tau_of(tau_mode, tau_c, hmin);
   int ed[4];
   element_edges(n, e, ed);
   const int nedge = 2 * n * (n + 1);
   for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
+  for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
+  for (int i = 0; i < nv; ++i) {
+    double s = 0.0, sp = 0.0, sq = 0.0;
+    for (int a = 0; a < nv; ++a) s = fma(Phi[a * nv + i], TV(y, a), s);
+    for (int c = 0; c < nt; ++c) {
+      sp = fma(P[i * nt + c], TV(le, c), sp);
+      sq = fma(Q[i * nt + c], TV(le, c), sq);
+    }
+    TV(z, i) = (s + fma(kap, sp, sq)) * inv_s(g, ev, kap, i);
+  }
   for (int a = 0; a < nv; ++a) {
-    double s = Mdiag[a] * f[(size_t)a * nE + e];
-    for (int c = 0; c < nt; ++c) s += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(le, c);
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s = fma(Phi[a * nv + i], TV(z, i), s);
     TV(y, a) = s;
   }
-  chol_solve(L, nv, nE, e, y);
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
   if (q) {
@@ -614,10 +596,10 @@ int tune_config(cudaStream_t s, int kind, int p, int nE, const int* cands, int n
   return best;
 }
 
-template <int TPE, int EPB>
-void set_smem_attr_sym() {
+template <int EPB>
+void set_smem_attr_eig() {
   static const bool done = [] {
-    cudaFuncSetAttribute(condense_kernel<TPE, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(condense_eig_kernel<EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          220 * 1024);
     return true;
   }();
@@ -633,33 +615,31 @@ void set_smem_attr_cd() {
   (void)done;
 }
 
-constexpr int kSymCands[] = {8 * 16 + 4, 16 * 16 + 2, 16 * 16 + 4, 32 * 16 + 1, 32 * 16 + 2,
-                             64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
+// symmetric: 128 threads per block, EPB elements (encoded (128 / EPB) * 16 + EPB)
+constexpr int kSymCands[] = {64 * 16 + 2, 32 * 16 + 4, 16 * 16 + 8};
 constexpr int kCdCands[] = {32 * 16 + 1, 64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
 }  // namespace
 
 int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
-                    int tau_mode, double tau_c, double hmin, double* A, double* Lfac, int* err,
-                    bool tune_only) {
+                    double tau, double* A, int* err, bool tune_only) {
   const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
-  const size_t per_elem = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
+  const size_t per_elem = sizeof(double) * (size_t)(1 + nv + nv * nt);
   auto launch = [&](int id, int e0, int count) {
+    (void)e0;
     note_launch();
     switch (id) {
-#define CASE(TPE, EPB)                                                                        \
-  case TPE * 16 + EPB:                                                                        \
-    set_smem_attr_sym<TPE, EPB>();                                                            \
-    condense_kernel<TPE, EPB><<<(count + EPB - 1) / EPB, TPE * EPB, per_elem * EPB, s>>>(     \
-        nv, nt, nE, e0, ref.G, ref.E, ref.H, ref.F, ref.K, kap, tau_mode, tau_c, hmin, A,     \
-        Lfac, err);                                                                           \
+#define CASE(EPB)                                                                              \
+  case (128 / EPB) * 16 + EPB:                                                                 \
+    set_smem_attr_eig<EPB>();                                                                  \
+    condense_eig_kernel<EPB><<<(count + EPB - 1) / EPB, 128, per_elem * EPB, s>>>(             \
+        nv, nt, nE, count, ref.eg, ref.ee, ref.P, ref.Q, ref.K, kap, tau, A, err);             \
     break;
-      CASE(8, 4) CASE(16, 2) CASE(16, 4) CASE(32, 1) CASE(32, 2) CASE(64, 1) CASE(128, 1)
-      CASE(256, 1)
+      CASE(2) CASE(4) CASE(8)
 #undef CASE
       default: break;
     }
   };
-  const int id = tune_config(s, 0, p, nE, kSymCands, 8, per_elem, launch);
+  const int id = tune_config(s, 0, p, nE, kSymCands, 3, per_elem, launch);
   if (!tune_only) launch(id, 0, nE);
   return id;
 }
@@ -718,37 +698,36 @@ void launch_recover_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
                                                  ref.Cy, kap, LU, f, lam, u, q);
 }
 
-void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
-                double* b) {
+void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap, double tau,
+                const double* f, double* b) {
   const int nE = n * n, nv = (p + 1) * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
-  const size_t shm = sizeof(double) * (size_t)nv * threads;
+  const size_t shm = sizeof(double) * (size_t)(2 * nv) * threads;
   static const bool attr = [] {       // enough for p = 8
-    cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     return true;
   }();
   (void)attr;
   note_launch();
-  rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau_mode, tau_c, hmin,
-                                          Lfac, f, b);
+  (void)tau;                          // applied to the tables (RefDevice::ee, Q)
+  rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.Phi, ref.eg, ref.ee, ref.P, ref.Q, kap,
+                                          f, b);
 }
 
 void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
-                    int tau_mode, double tau_c, double hmin, const double* Lfac, const double* f,
-                    const double* lam, double* u, double* q) {
+                    double tau, const double* f, const double* lam, double* u, double* q) {
   const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
   const int threads = 64, blocks = (nE + threads - 1) / threads;
-  const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
+  const size_t shm = sizeof(double) * (size_t)(2 * nv + nt) * threads;
   static const bool attr = [] {       // enough for p = 8
-    cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(recover_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     return true;
   }();
   (void)attr;
   note_launch();
-  recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT, ref.Cx,
-                                              ref.Cy, kap, tau_mode, tau_c, hmin, Lfac, f, lam,
-                                              u, q);
+  (void)tau;                          // applied to the tables (RefDevice::ee, Q)
+  recover_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.Phi, ref.eg, ref.ee, ref.P, ref.Q,
+                                              ref.BxT, ref.ByT, ref.Cx, ref.Cy, kap, f, lam, u, q);
 }
 
 }  // namespace hdgmg

@@ -2,7 +2,7 @@
 SIPG-H, NIPG-H, IIPG-H) against the oracle's primal element and its
 multigrid, through the C ABI.
 
-SIPG-H runs the symmetric path (packed operators, Cholesky condensation, CG);
+SIPG-H runs the symmetric path (packed operators, eigenbasis condensation, CG);
 NIPG-H and IIPG-H the non-symmetric one (full storage, LU condensation,
 restriction from A_BI, GMRES), with the scheme's own reference tables.
 
@@ -222,8 +222,8 @@ def test_batch_mixes_schemes():
 
 def test_indefinite_penalty_is_reported():
     """SIPG-H with a penalty far below (p+1)(p+2)/h: the volume block
-    kappa (Kst - N - N^T) + tau E is indefinite, the Cholesky condensation
-    meets a non-positive pivot and set-up reports EBREAKDOWN."""
+    kappa (Kst - N - N^T) + tau E is indefinite, the condensation finds a
+    non-positive s_i = kappa g_i + tau e_i and set-up reports EBREAKDOWN."""
     wl = W.lognormal(8, 2, sigma=0.5, seed=2, tau_mode="const", tau_c=0.01)
     s = hdgmg.Solver(8, 2, tau_mode=hdgmg.TAU_CONST, tau_c=0.01, scheme=hdgmg.SCHEME_SIPG)
     with pytest.raises(hdgmg.HdgmgError) as ei:
