@@ -175,7 +175,8 @@ typedef struct {
   double t_condense_ms;   /* device time of the element condensation kernel
                              in the last hdgmg_setup (CUDA events around it) */
   int32_t condense_threads; /* threads per element the condensation kernel
-                             ran with, and ...                                 */
+                             ran with (symmetric blocks: 128 threads shared by
+                             the block's elements, i.e. 128 / EPB), and ...   */
   int32_t condense_elements_per_block; /* ... elements per block: picked once
                              per (kernel, p, device) by timing candidate
                              shapes on the first set-up; the result does not

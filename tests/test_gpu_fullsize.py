@@ -77,7 +77,7 @@ def test_c2_256_p4_bench_configuration(prec):
     lam, u, q, info = s.solve(f)
     assert info.converged == 1 and info.rel_res <= 1e-10
     assert info.condense_threads in (8, 16, 32, 64, 128, 256)
-    assert info.condense_elements_per_block in (1, 2, 4)
+    assert info.condense_elements_per_block in (1, 2, 4, 8)
     pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau())
     lam, u, q = host(lam), host(u), host(q)
     Ao, go = pr.condense(wl.f[0])
