@@ -74,6 +74,11 @@ enum { HDGMG_SCHEME_HDG = 0, HDGMG_SCHEME_SIPG = 1, HDGMG_SCHEME_NIPG = 2,
 /* smoothers of Sec. 4.1 */
 enum { HDGMG_SMOOTH_BLOCK_JACOBI = 0, HDGMG_SMOOTH_POINT_JACOBI = 1,
        HDGMG_SMOOTH_CHEBYSHEV = 2, HDGMG_SMOOTH_LU_SGS = 3 };
+/* element condensation (Sec. 2): BASIS uses one basis that diagonalises every
+ * element's volume block kappa G + tau E (symmetric blocks), FACTOR factors
+ * each element's volume block (Cholesky / LU), AUTO picks BASIS where it
+ * applies */
+enum { HDGMG_CONDENSE_AUTO = 0, HDGMG_CONDENSE_BASIS = 1, HDGMG_CONDENSE_FACTOR = 2 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
 
@@ -159,6 +164,10 @@ typedef struct {
                              mode).  The fused single-block tail and the
                              fused edge sweeps serve BLOCK_JACOBI only;
                              BLOCK_JACOBI                                    */
+  int32_t condensation;   /* HDGMG_CONDENSE_*: AUTO = BASIS for symmetric
+                             volume blocks (diffusion, SIPG-H), FACTOR (local
+                             LU) for the non-symmetric ones; BASIS on a
+                             non-symmetric problem is EINVAL; AUTO           */
 } hdgmg_opts;
 
 typedef struct {
@@ -181,6 +190,7 @@ typedef struct {
                              per (kernel, p, device) by timing candidate
                              shapes on the first set-up; the result does not
                              depend on them                                   */
+  int32_t condense_kind;  /* HDGMG_CONDENSE_BASIS or _FACTOR: what ran      */
 } hdgmg_info;
 
 void hdgmg_default_opts(hdgmg_opts* opts);

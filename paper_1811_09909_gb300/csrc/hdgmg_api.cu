@@ -67,7 +67,8 @@ struct hdgmg_ctx {
   std::vector<Level> levels;
   double* logk = nullptr;
   double* kap = nullptr;       // exp(log kappa) per element
-  double* Lfac = nullptr;      // LU factors of S (full), non-symmetric only
+  bool basis = false;          // symmetric S condensed through the shared eigenbasis
+  double* Lfac = nullptr;      // factors of S when not: LU (full, ns) or Cholesky (packed)
   int* err = nullptr;
   int* err_h = nullptr;
   // coarsest level
@@ -668,7 +669,8 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   if (c->ns)
     launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
   else
-    launch_rhs(s, c->refd, c->p, c->n, c->kap, c->ktau, f, c->b);
+    c->basis ? launch_rhs(s, c->refd, c->p, c->n, c->kap, c->ktau, f, c->b)
+             : launch_rhs_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
   if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->b, -1.0);
   return check_launch("condensed right-hand side");
@@ -973,7 +975,9 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   if ((u || q) && c->ns)
     launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
   else if (u || q)
-    launch_recover(s, c->refd, c->p, c->n, c->kap, c->ktau, f, lam_out, u, q);
+    c->basis ? launch_recover(s, c->refd, c->p, c->n, c->kap, c->ktau, f, lam_out, u, q)
+             : launch_recover_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f, lam_out,
+                                     u, q);
   STATUS_TRY(check_launch("solve"));
   if (info) {
     info->iters = it;
@@ -1040,6 +1044,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->cluster_tail_n = 0;
   o->gmres_restart = 30;
   o->smoother = HDGMG_SMOOTH_BLOCK_JACOBI;
+  o->condensation = HDGMG_CONDENSE_AUTO;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1101,8 +1106,12 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     return fail(HDGMG_EINVAL, "gmres_restart must be in 1..256");
   if (o.precision < 0 || o.precision > 3) return fail(HDGMG_EINVAL, "unknown precision");
   if (o.smoother < 0 || o.smoother > 3) return fail(HDGMG_EINVAL, "unknown smoother");
+  if (o.condensation < HDGMG_CONDENSE_AUTO || o.condensation > HDGMG_CONDENSE_FACTOR)
+    return fail(HDGMG_EINVAL, "unknown condensation");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
+  if (nonsym && o.condensation == HDGMG_CONDENSE_BASIS)
+    return fail(HDGMG_EINVAL, "condensation BASIS needs symmetric volume blocks");
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)
     return fail(HDGMG_EINVAL,
                 "krylov CG needs a symmetric operator; use GMRES for convection-diffusion, NIPG-H, IIPG-H");
@@ -1120,6 +1129,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   c->prob = P;
   c->opts = o;
   c->ns = nonsym;
+  c->basis = !nonsym && o.condensation != HDGMG_CONDENSE_FACTOR;
   c->stream = (cudaStream_t)stream;
   c->n = P.n;
   c->p = P.p;
@@ -1164,7 +1174,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(upload(&c->refd.Cy, c->ref.Cy));
   CTRY(upload(&c->refd.Ef, c->ref.Ef));
   CTRY(upload(&c->refd.Hv, c->ref.Hv));
-  if (!c->ns) {
+  if (c->basis) {
     // the basis that diagonalises every element's volume block
     EigBasis eb;
     if (!build_eig_basis(c->ref, c->ktau, c->hmin, eb))
@@ -1237,7 +1247,8 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   const int64_t len = c->fine_len();
   CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
   CTRY(c->alloc(&c->kap, (size_t)P.n * P.n));
-  if (c->ns) CTRY(c->alloc(&c->Lfac, (size_t)c->nv * c->nv * P.n * P.n));
+  if (!c->basis)
+    CTRY(c->alloc(&c->Lfac, (size_t)(c->ns ? c->nv * c->nv : c->nv * (c->nv + 1) / 2) * P.n * P.n));
   CTRY(c->alloc(&c->err, 4));
   CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
   CTRY(c->alloc(&c->x, len));
@@ -1338,7 +1349,9 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
                                                c->Lfac, c->err, tune_only);
     else
       c->condense_threads =
-          launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, tune_only);
+          c->basis ? launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, tune_only)
+                   : launch_condense_factor(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->Lfac,
+                                            c->err, tune_only);
   }
   CUDA_TRY(cudaEventRecord(c->evk1, s));
   STATUS_TRY(check_launch("condensation"));
@@ -1385,7 +1398,9 @@ hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa) {
   if (c->ns)
     launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
   else
-    launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, true);
+    c->basis ? launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, true)
+             : launch_condense_factor(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->Lfac,
+                                      c->err, true);
   CUDA_TRY(cudaStreamSynchronize(s));
   return check_launch("condensation tuning");
 }
@@ -1435,6 +1450,7 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     info->t_condense_ms = c->t_condense_ms;
     info->condense_threads = c->condense_threads / 16;
     info->condense_elements_per_block = c->condense_threads % 16;
+    info->condense_kind = c->basis ? HDGMG_CONDENSE_BASIS : HDGMG_CONDENSE_FACTOR;
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }

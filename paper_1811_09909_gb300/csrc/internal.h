@@ -140,6 +140,16 @@ void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n,
 void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n,
                     const double* kap, double tau, const double* f, const double* lam,
                     double* u, double* q);
+// symmetric S by local Cholesky (HDGMG_CONDENSE_FACTOR): packed factor
+// Lfac [nv(nv+1)/2][nE] kept for the right-hand side and recovery
+int launch_condense_factor(cudaStream_t s, const RefDevice& ref, int p, int nE,
+                           const double* kap, double tau, double* A, double* Lfac, int* err,
+                           bool tune_only = false);
+void launch_rhs_factor(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                       double tau, const double* Lfac, const double* f, double* b);
+void launch_recover_factor(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                           double tau, const double* Lfac, const double* f, const double* lam,
+                           double* u, double* q);
 
 // convection-diffusion element (non-symmetric A_e, full [nt*nt][nE]; LU
 // factors of the volume block, full [nv*nv][nE]).  The element-independent

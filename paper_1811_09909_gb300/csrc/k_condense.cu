@@ -115,6 +115,98 @@ __global__ void __launch_bounds__(128) condense_eig_kernel(
   if (bad) atomicOr(err, 1);
 }
 
+// K1 by local factorisation (HDGMG_CONDENSE_FACTOR, symmetric S): Cholesky
+// S = L L^T, V = L^-1 W, A_e = kappa K + tau I - V^T V; the packed factor is
+// kept for K5/K12.  TPE threads per element and EPB elements per block, in lockstep (the
+// elements of a block run the same loops, so block barriers serve all of
+// them); the local matrices in shared memory, per element
+//   S: nv x nv (full square, lower part used), V: nv x nt, 1/sqrt pivots.
+// The FP64 pipe is the bottleneck on GB300: a pivot's square root and
+// reciprocal is computed once per element (one thread), so several elements
+// per warp share the cost of that single-lane step and of the partially
+// filled last pass of each loop.  (TPE, EPB) is picked per p by a timing
+// autotuner (tune_config below); the result does not depend on it.
+// Elements e_begin + blockIdx.x * EPB + (threadIdx.x / TPE); a block's
+// elements past nE recompute the last element and write nothing.
+template <int TPE, int EPB>
+__global__ void __launch_bounds__(TPE * EPB) condense_chol_kernel(
+    int nv, int nt, int nE, int e_begin, const double* __restrict__ G, const double* __restrict__ Eb,
+    const double* __restrict__ H, const double* __restrict__ F, const double* __restrict__ K,
+    const double* __restrict__ kapv, double tau,
+    double* __restrict__ A, double* __restrict__ Lfac, int* __restrict__ err) {
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x % TPE, el = threadIdx.x / TPE;
+  const int e0 = e_begin + blockIdx.x * EPB + el;
+  const bool active = e0 < nE;
+  const int e = active ? e0 : nE - 1;
+  double* S = smem + (size_t)el * (nv * nv + nv * nt + nv);
+  double* V = S + nv * nv;
+  double* dinv = V + nv * nt;
+  const double kap = kapv[e];
+  const int nsv = nv * (nv + 1) / 2;
+  for (int t = tid; t < nsv; t += TPE) {
+    int i, j;
+    tri_index(t, i, j);
+    S[i * nv + j] = fma(kap, G[i * nv + j], tau * Eb[i * nv + j]);
+  }
+  for (int t = tid; t < nv * nt; t += TPE) V[t] = fma(kap, H[t], tau * F[t]);
+  __syncthreads();
+  bool bad = false;
+  for (int k = 0; k < nv; ++k) {
+    if (tid == 0) {
+      double d = S[k * nv + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = true;
+        d = 1.0;
+      }
+      const double di = rsqrt_newton(d);
+      S[k * nv + k] = d * di;
+      dinv[k] = di;
+    }
+    __syncthreads();
+    const double di = dinv[k];
+    for (int i = k + 1 + tid; i < nv; i += TPE) S[i * nv + k] *= di;
+    for (int c = tid; c < nt; c += TPE) V[k * nt + c] *= di;
+    __syncthreads();
+    const int m = nv - k - 1;
+    const int ntri = m * (m + 1) / 2;
+    for (int t = tid; t < ntri; t += TPE) {
+      int ii, jj;
+      tri_index(t, ii, jj);
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      S[i * nv + j] = fma(-S[i * nv + k], S[j * nv + k], S[i * nv + j]);
+    }
+    for (int t = tid; t < m * nt; t += TPE) {
+      const int i = k + 1 + t / nt, c = t % nt;
+      V[i * nt + c] = fma(-S[i * nv + k], V[k * nt + c], V[i * nt + c]);
+    }
+    __syncthreads();
+  }
+  if (bad && active) atomicOr(err, 1);
+  const int nsa = nt * (nt + 1) / 2;
+  for (int t = tid; t < nsa; t += TPE) {
+    int r, c;
+    tri_index(t, r, c);
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      s0 = fma(V[i * nt + r], V[i * nt + c], s0);
+      s1 = fma(V[(i + 1) * nt + r], V[(i + 1) * nt + c], s1);
+    }
+    if (i < nv) s0 = fma(V[i * nt + r], V[i * nt + c], s0);
+    double a = fma(kap, K[r * nt + c], -(s0 + s1));
+    if (r == c) a += tau;
+    if (active) A[(size_t)t * nE + e] = a;
+  }
+  if (Lfac && active) {
+    for (int t = tid; t < nsv; t += TPE) {
+      int r, c;
+      tri_index(t, r, c);
+      Lfac[(size_t)t * nE + e] = S[r * nv + c];
+    }
+  }
+}
+
 // ------------------------------------------ convection-diffusion element
 // -div(eps grad u) + div(beta u) = f with the upwind flux
 // hhat.n = q.n + (beta.n) lambda + tau_f (u - lambda), tau_f = tau + max(beta.n_f, 0)
@@ -243,6 +335,22 @@ __global__ void kappa_kernel(int nE, const double* __restrict__ logk, double* __
 // the 32 threads of a warp touch 32 consecutive words.
 #define TV(arr, i) arr[(size_t)(i) * blockDim.x + threadIdx.x]
 
+// solve L L^T y = y in place (L packed SoA, element e)
+__device__ __forceinline__ void chol_solve(const double* __restrict__ L, int nv, int nE, int e,
+                                           double* y) {
+  for (int i = 0; i < nv; ++i) {
+    double s = TV(y, i);
+    const int row = i * (i + 1) / 2;
+    for (int j = 0; j < i; ++j) s -= L[(size_t)(row + j) * nE + e] * TV(y, j);
+    TV(y, i) = s / L[(size_t)(row + i) * nE + e];
+  }
+  for (int i = nv - 1; i >= 0; --i) {
+    double s = TV(y, i);
+    for (int j = i + 1; j < nv; ++j) s -= L[(size_t)(j * (j + 1) / 2 + i) * nE + e] * TV(y, j);
+    TV(y, i) = s / L[(size_t)(i * (i + 1) / 2 + i) * nE + e];
+  }
+}
+
 __device__ __forceinline__ void element_edges(int n, int e, int ed[4]) {
   const int j = e / n, i = e - j * n;
   const int nvert = n * (n + 1);
@@ -342,6 +450,79 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
     for (int i = 0; i < nv; ++i) s = fma(Phi[a * nv + i], TV(z, i), s);
     TV(y, a) = s;
   }
+  if (u)
+    for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
+  if (q) {
+    for (int a = 0; a < nv; ++a) {
+      double sx = 0.0, sy = 0.0;
+      for (int b2 = 0; b2 < nv; ++b2) {
+        sx += BxT[a * nv + b2] * TV(y, b2);
+        sy += ByT[a * nv + b2] * TV(y, b2);
+      }
+      for (int c = 0; c < nt; ++c) {
+        sx -= Cx[a * nt + c] * TV(le, c);
+        sy -= Cy[a * nt + c] * TV(le, c);
+      }
+      const double sc = kap / Mdiag[a];
+      q[(size_t)a * nE + e] = sc * sx;
+      q[(size_t)(nv + a) * nE + e] = sc * sy;
+    }
+  }
+}
+// K5 (FACTOR, symmetric S): thread per element; shared memory y[nv][blockDim]
+__global__ void rhs_chol_kernel(int p, int n, const double* __restrict__ Mdiag,
+                           const double* __restrict__ H, const double* __restrict__ F,
+                           const double* __restrict__ kapv, double tau,
+                           const double* __restrict__ L,
+                           const double* __restrict__ f, double* __restrict__ b) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  const double kap = kapv[e];
+  for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
+  chol_solve(L, nv, nE, e, y);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) {
+    const int edge = ed[c / p1];
+    if (is_boundary_edge(n, edge)) continue;
+    double g = 0.0;
+    for (int a = 0; a < nv; ++a) g += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(y, a);
+    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], g);
+  }
+}
+
+// K12 (FACTOR, symmetric S): thread per element; shared memory y[nv][blockDim], le[nt][blockDim]
+__global__ void recover_chol_kernel(int p, int n, const double* __restrict__ Mdiag,
+                               const double* __restrict__ H, const double* __restrict__ F,
+                               const double* __restrict__ BxT, const double* __restrict__ ByT,
+                               const double* __restrict__ Cx, const double* __restrict__ Cy,
+                               const double* __restrict__ kapv, double tau,
+                               const double* __restrict__ L,
+                               const double* __restrict__ f, const double* __restrict__ lam,
+                               double* __restrict__ u, double* __restrict__ q) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  double* le = smem + (size_t)nv * blockDim.x;
+  const double kap = kapv[e];
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
+  for (int a = 0; a < nv; ++a) {
+    double s = Mdiag[a] * f[(size_t)a * nE + e];
+    for (int c = 0; c < nt; ++c) s += (kap * H[a * nt + c] + tau * F[a * nt + c]) * TV(le, c);
+    TV(y, a) = s;
+  }
+  chol_solve(L, nv, nE, e, y);
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
   if (q) {
@@ -596,6 +777,15 @@ int tune_config(cudaStream_t s, int kind, int p, int nE, const int* cands, int n
   return best;
 }
 
+template <int TPE, int EPB>
+void set_smem_attr_chol() {
+  static const bool done = [] {
+    cudaFuncSetAttribute(condense_chol_kernel<TPE, EPB>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    return true;
+  }();
+  (void)done;
+}
 template <int EPB>
 void set_smem_attr_eig() {
   static const bool done = [] {
@@ -618,6 +808,8 @@ void set_smem_attr_cd() {
 // symmetric: 128 threads per block, EPB elements (encoded (128 / EPB) * 16 + EPB)
 constexpr int kSymCands[] = {64 * 16 + 2, 32 * 16 + 4, 16 * 16 + 8};
 constexpr int kCdCands[] = {32 * 16 + 1, 64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
+constexpr int kCholCands[] = {8 * 16 + 4, 16 * 16 + 2, 16 * 16 + 4, 32 * 16 + 1, 32 * 16 + 2,
+                              64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
 }  // namespace
 
 int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
@@ -640,6 +832,30 @@ int launch_condense(cudaStream_t s, const RefDevice& ref, int p, int nE, const d
     }
   };
   const int id = tune_config(s, 0, p, nE, kSymCands, 3, per_elem, launch);
+  if (!tune_only) launch(id, 0, nE);
+  return id;
+}
+
+int launch_condense_factor(cudaStream_t s, const RefDevice& ref, int p, int nE, const double* kap,
+                           double tau, double* A, double* Lfac, int* err, bool tune_only) {
+  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const size_t per_elem = sizeof(double) * (size_t)(nv * nv + nv * nt + nv);
+  auto launch = [&](int id, int e0, int count) {
+    note_launch();
+    switch (id) {
+#define CASE(TPE, EPB)                                                                        \
+  case TPE * 16 + EPB:                                                                        \
+    set_smem_attr_chol<TPE, EPB>();                                                           \
+    condense_chol_kernel<TPE, EPB><<<(count + EPB - 1) / EPB, TPE * EPB, per_elem * EPB, s>>>( \
+        nv, nt, nE, e0, ref.G, ref.E, ref.H, ref.F, ref.K, kap, tau, A, Lfac, err);           \
+    break;
+      CASE(8, 4) CASE(16, 2) CASE(16, 4) CASE(32, 1) CASE(32, 2) CASE(64, 1) CASE(128, 1)
+      CASE(256, 1)
+#undef CASE
+      default: break;
+    }
+  };
+  const int id = tune_config(s, 2, p, nE, kCholCands, 8, per_elem, launch);
   if (!tune_only) launch(id, 0, nE);
   return id;
 }
@@ -712,6 +928,36 @@ void launch_rhs(cudaStream_t s, const RefDevice& ref, int p, int n, const double
   (void)tau;                          // applied to the tables (RefDevice::ee, Q)
   rhs_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.Phi, ref.eg, ref.ee, ref.P, ref.Q, kap,
                                           f, b);
+}
+
+void launch_rhs_factor(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                       double tau, const double* Lfac, const double* f, double* b) {
+  const int nE = n * n, nv = (p + 1) * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)nv * threads;
+  static const bool attr = [] {       // enough for p = 8
+    cudaFuncSetAttribute(rhs_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  rhs_chol_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, kap, tau, Lfac, f, b);
+}
+
+void launch_recover_factor(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,
+                           double tau, const double* Lfac, const double* f, const double* lam,
+                           double* u, double* q) {
+  const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(nv + nt) * threads;
+  static const bool attr = [] {       // enough for p = 8
+    cudaFuncSetAttribute(recover_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  recover_chol_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, ref.F, ref.BxT, ref.ByT,
+                                                   ref.Cx, ref.Cy, kap, tau, Lfac, f, lam, u, q);
 }
 
 void launch_recover(cudaStream_t s, const RefDevice& ref, int p, int n, const double* kap,

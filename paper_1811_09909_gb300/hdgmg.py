@@ -18,6 +18,7 @@ PREC_FP64, PREC_FP32, PREC_FP32_IR, PREC_BF16 = 0, 1, 2, 3
 PDE_DIFFUSION, PDE_CONVDIFF = 0, 1
 SCHEME_HDG, SCHEME_SIPG, SCHEME_NIPG, SCHEME_IIPG = 0, 1, 2, 3
 SMOOTH_BLOCK_JACOBI, SMOOTH_POINT_JACOBI, SMOOTH_CHEBYSHEV, SMOOTH_LU_SGS = 0, 1, 2, 3
+CONDENSE_AUTO, CONDENSE_BASIS, CONDENSE_FACTOR = 0, 1, 2
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV",
           -5: "EBREAKDOWN", -6: "ETIMEOUT"}
@@ -47,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("krylov", ctypes.c_int32), ("max_it", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32),
-                ("gmres_restart", ctypes.c_int32), ("smoother", ctypes.c_int32)]
+                ("gmres_restart", ctypes.c_int32), ("smoother", ctypes.c_int32),
+                ("condensation", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +59,8 @@ class Info(ctypes.Structure):
                 ("trace_dofs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("refinements", ctypes.c_int32), ("t_condense_ms", ctypes.c_double),
                 ("condense_threads", ctypes.c_int32),
-                ("condense_elements_per_block", ctypes.c_int32)]
+                ("condense_elements_per_block", ctypes.c_int32),
+                ("condense_kind", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

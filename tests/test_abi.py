@@ -48,6 +48,7 @@ def test_default_options(lib):
     assert o.precision == hdgmg.PREC_FP64 and o.inner_rtol == 1e-5
     assert o.cluster_tail_n == 0 and o.gmres_restart == 30
     assert o.smoother == hdgmg.SMOOTH_BLOCK_JACOBI
+    assert o.condensation == hdgmg.CONDENSE_AUTO
 
 
 @pytest.mark.parametrize("kw,msg", [
@@ -61,6 +62,8 @@ def test_default_options(lib):
     (dict(scheme=2, pde=1, krylov=2), "diffusion only"),
     (dict(scheme=2, krylov=1), "symmetric"), (dict(scheme=3, krylov=1), "symmetric"),
     (dict(tau_mode=3), "tau_mode"),
+    (dict(condensation=3), "unknown condensation"),
+    (dict(pde=1, krylov=2, condensation=1), "BASIS needs symmetric"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg
@@ -69,7 +72,8 @@ def test_create_rejects_bad_arguments(lib, kw, msg):
     prob = hdgmg.Problem(n, p, 0.0, 1.0, 0.0, 1.0, kw.get("tau_mode", hdgmg.TAU_CONST),
                          kw.get("tau_c", 1.0), kw.get("pde", 0), 1.0, 0.5, kw.get("scheme", 0))
     o = hdgmg.default_opts(coarsest_n=kw.get("coarsest", 2), krylov=kw.get("krylov", 1),
-                           gmres_restart=kw.get("restart", 30), smoother=kw.get("smoother", 0))
+                           gmres_restart=kw.get("restart", 30), smoother=kw.get("smoother", 0),
+                           condensation=kw.get("condensation", 0))
     ctx = ctypes.c_void_p()
     st = lib.hdgmg_create(ctypes.byref(ctx), ctypes.byref(prob), ctypes.byref(o), None)
     assert st == -1
