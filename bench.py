@@ -433,11 +433,15 @@ def run_batched(dev, steps, warmup):
                         "16 N(0,1) right-hand sides each; mixed precision, one batch set-up + solve"}
 
 
-def condense_cd_flops(p, nE):
+def condense_cd_flops(p, nE, basis=False):
     """Algorithmic FP64 flops of the convection-diffusion condensation per
-    launch: LU of S (2 n_v^3 / 3), X = S^-1 W (2 n_v^2 n_t), V^T X
-    (2 n_t^2 n_v) per element."""
+    launch.  Local LU: LU of S (2 n_v^3 / 3), X = S^-1 W (2 n_v^2 n_t), V^T X
+    (2 n_t^2 n_v) per element.  Pencil basis: Vt = eps Pv1 + Pv0 and
+    W~ = eps Pw1 + Pw0 (2 n_v n_t each), the 1 x 1 / 2 x 2 blocks on W~
+    (3 n_v n_t), Vt^T Y plus eps K (2 n_t^2 (n_v + 1))."""
     nv, nt = (p + 1) ** 2, 4 * (p + 1)
+    if basis:
+        return nE * (7.0 * nv * nt + 2.0 * nt * nt * (nv + 1))
     return nE * (2.0 * nv ** 3 / 3.0 + 2.0 * nv * nv * nt + 2.0 * nt * nt * nv)
 
 
@@ -485,8 +489,19 @@ def run_convdiff(dev, steps, warmup):
         out[name] = {"value": wl.interior_trace_dofs / (ms * 1e-3), "ms_per_step": ms,
                      "setup_ms": infos[-1].t_setup_ms, "condense_ms": cms,
                      "solve_ms": infos[-1].t_solve_ms, "iters": infos[-1].iters,
-                     "rel_res": max(i.rel_res for i in infos)}
+                     "rel_res": max(i.rel_res for i in infos),
+                     "condense_route": ("basis" if infos[-1].condense_kind == hdgmg.CONDENSE_BASIS
+                                        else "factor")}
         s.close()
+    # the same condensation by local LU (the factor route), for comparison
+    s = hdgmg.Solver(n, p, precision=hdgmg.PREC_FP64, stream=stream,
+                     condensation=hdgmg.CONDENSE_FACTOR, **opts)
+    fms = []
+    for it in range(2):
+        s.setup(logk)
+        _, _, _, info = s.solve(f, want_u=False, want_q=False)
+        fms.append(info.t_condense_ms)
+    s.close()
     lam64, u64 = sols["fp64"]
     for name in ("mixed_bf16", "mixed_fp32"):
         lam, u = sols[name]
@@ -500,14 +515,17 @@ def run_convdiff(dev, steps, warmup):
     Yn = (jj[None, :] + 0.5) / n + 0.5 / n * xi[a // (p + 1)][:, None]
     u_ex = torch.as_tensor(np.sin(math.pi * Xn) * np.sin(math.pi * Yn), device=dev)
     err = float((sols["mixed_bf16"][1] - u_ex).abs().max())
-    flops = condense_cd_flops(p, n * n)
+    flops = condense_cd_flops(p, n * n, basis=out["fp64"]["condense_route"] == "basis")
+    lu_flops = condense_cd_flops(p, n * n)
     return {"workload": "convection-diffusion eps=1e-3, beta=(1,0.5), 512x512 quads, p=6, "
                         "u=sin(pi x)sin(pi y); FGMRES(30) + step-3 V-cycle (m_N=1 doubling to 4, "
                         "coarsest 4x4); FP64 condensation",
             "interior_trace_dofs": wl.interior_trace_dofs, "unit": UNIT, **out,
             "u_nodal_max_err_vs_exact": err,
             "condense_fp64_tflops": flops / (out["fp64"]["condense_ms"] * 1e-3) / 1e12,
-            "condense_fp64_frac": flops / (out["fp64"]["condense_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+            "condense_fp64_frac": flops / (out["fp64"]["condense_ms"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+            "condense_factor_route_ms": fms[-1],
+            "condense_factor_route_frac": lu_flops / (fms[-1] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
 
 
 def run_adjoint(dev, steps, warmup):

@@ -74,10 +74,13 @@ enum { HDGMG_SCHEME_HDG = 0, HDGMG_SCHEME_SIPG = 1, HDGMG_SCHEME_NIPG = 2,
 /* smoothers of Sec. 4.1 */
 enum { HDGMG_SMOOTH_BLOCK_JACOBI = 0, HDGMG_SMOOTH_POINT_JACOBI = 1,
        HDGMG_SMOOTH_CHEBYSHEV = 2, HDGMG_SMOOTH_LU_SGS = 3 };
-/* element condensation (Sec. 2): BASIS uses one basis that diagonalises every
- * element's volume block kappa G + tau E (symmetric blocks), FACTOR factors
- * each element's volume block (Cholesky / LU), AUTO picks BASIS where it
- * applies */
+/* element condensation (Sec. 2): BASIS uses one basis in which every
+ * element's volume block kappa G + S0 is (block) diagonal -- for symmetric
+ * blocks the eigenbasis of the pencil (G, E), for non-symmetric ones that of
+ * B^-1 G with B the block at kappa's geometric mean, checked at every set-up
+ * against direct solves at the extreme kappa (1e-11) -- so no element is
+ * factored; FACTOR factors each element's volume block (Cholesky / LU) and
+ * keeps the factors; AUTO = BASIS where it is accurate, FACTOR otherwise */
 enum { HDGMG_CONDENSE_AUTO = 0, HDGMG_CONDENSE_BASIS = 1, HDGMG_CONDENSE_FACTOR = 2 };
 
 typedef struct hdgmg_ctx hdgmg_ctx;   /* opaque, library-owned */
@@ -164,10 +167,11 @@ typedef struct {
                              mode).  The fused single-block tail and the
                              fused edge sweeps serve BLOCK_JACOBI only;
                              BLOCK_JACOBI                                    */
-  int32_t condensation;   /* HDGMG_CONDENSE_*: AUTO = BASIS for symmetric
-                             volume blocks (diffusion, SIPG-H), FACTOR (local
-                             LU) for the non-symmetric ones; BASIS on a
-                             non-symmetric problem is EINVAL; AUTO           */
+  int32_t condensation;   /* HDGMG_CONDENSE_*: AUTO = BASIS where the basis
+                             is accurate (always for symmetric blocks), else
+                             FACTOR; BASIS when the non-symmetric basis fails
+                             its accuracy check: hdgmg_setup returns EINVAL;
+                             AUTO                                            */
 } hdgmg_opts;
 
 typedef struct {

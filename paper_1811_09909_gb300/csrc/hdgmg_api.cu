@@ -63,6 +63,11 @@ struct hdgmg_ctx {
   RefElement ref;
   RefDevice refd{};
   CdTables cd{};               // convection-diffusion tables (ns only)
+  std::vector<double> cdS0, cdW0, cdV0, cdad;   // host copies of the cd tables
+  PencilDevice pb{};           // non-symmetric pencil basis (ns), rebuilt when eps0 moves
+  EigBasisNS pb_host;          // its host copy (accuracy checks)
+  bool pb_valid = false;
+  bool cd_basis = false;       // ns: this set-up condenses through pb (else local LU)
   std::vector<void*> allocs;
   std::vector<Level> levels;
   double* logk = nullptr;
@@ -667,7 +672,8 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
   const int64_t len = c->fine_len();
   CUDA_TRY(cudaMemsetAsync(c->b, 0, sizeof(double) * len, s));
   if (c->ns)
-    launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
+    c->cd_basis ? launch_rhs_cdeig(s, c->refd, c->pb, c->p, c->n, c->kap, f, c->b)
+                : launch_rhs_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, c->b);
   else
     c->basis ? launch_rhs(s, c->refd, c->p, c->n, c->kap, c->ktau, f, c->b)
              : launch_rhs_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f, c->b);
@@ -973,7 +979,9 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
   if ((u || q) && c->ns)
-    launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
+    c->cd_basis
+        ? launch_recover_cdeig(s, c->refd, c->cd, c->pb, c->p, c->n, c->kap, f, lam_out, u, q)
+        : launch_recover_cd(s, c->refd, c->cd, c->p, c->n, c->kap, c->Lfac, f, lam_out, u, q);
   else if (u || q)
     c->basis ? launch_recover(s, c->refd, c->p, c->n, c->kap, c->ktau, f, lam_out, u, q)
              : launch_recover_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f, lam_out,
@@ -1110,8 +1118,6 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     return fail(HDGMG_EINVAL, "unknown condensation");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
-  if (nonsym && o.condensation == HDGMG_CONDENSE_BASIS)
-    return fail(HDGMG_EINVAL, "condensation BASIS needs symmetric volume blocks");
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)
     return fail(HDGMG_EINVAL,
                 "krylov CG needs a symmetric operator; use GMRES for convection-diffusion, NIPG-H, IIPG-H");
@@ -1191,6 +1197,10 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     std::vector<double> S0, W0, V0, ad;
     const bool conv = P.pde == HDGMG_PDE_CONVDIFF;
     build_cd_tables(c->ref, c->ktau, conv ? P.beta_x : 0.0, conv ? P.beta_y : 0.0, S0, W0, V0, ad);
+    c->cdS0 = S0;
+    c->cdW0 = W0;
+    c->cdV0 = V0;
+    c->cdad = ad;
     CTRY(upload(&c->cd.S0, S0));
     CTRY(upload(&c->cd.W0, W0));
     CTRY(upload(&c->cd.V0, V0));
@@ -1247,8 +1257,10 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   const int64_t len = c->fine_len();
   CTRY(c->alloc(&c->logk, (size_t)P.n * P.n));
   CTRY(c->alloc(&c->kap, (size_t)P.n * P.n));
-  if (!c->basis)
-    CTRY(c->alloc(&c->Lfac, (size_t)(c->ns ? c->nv * c->nv : c->nv * (c->nv + 1) / 2) * P.n * P.n));
+  if (!c->basis && !c->ns)
+    CTRY(c->alloc(&c->Lfac, (size_t)c->nv * (c->nv + 1) / 2 * P.n * P.n));
+  // ns: the LU factors (nv^2 doubles per element) are allocated by the first
+  // set-up that needs them (the pencil basis, when accurate, needs none)
   CTRY(c->alloc(&c->err, 4));
   CTRY(cudaMallocHost(&c->err_h, sizeof(int) * 4));
   CTRY(c->alloc(&c->x, len));
@@ -1329,6 +1341,66 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   return HDGMG_OK;
 }
 
+// Non-symmetric volume blocks: decide per set-up between the pencil basis
+// and local LU.  eps0 = kappa's geometric mean rounded to a quarter power of
+// two (so that repeated set-ups with similar kappa reuse the basis); the basis
+// is used when A_e through it agrees with a direct dense solve to 1e-11 at the
+// smallest and largest kappa of this set-up.
+hdgmg_status prepare_pencil(hdgmg_ctx* c, const double* log_kappa) {
+  c->cd_basis = false;
+  if (c->opts.condensation == HDGMG_CONDENSE_FACTOR) return HDGMG_OK;
+  const int nE = c->n * c->n;
+  std::vector<double> lk(nE);
+  CUDA_TRY(cudaMemcpyAsync(lk.data(), log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToHost,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  double lo = lk[0], hi = lk[0], sum = 0.0;
+  for (double v : lk) {
+    if (!std::isfinite(v)) return HDGMG_OK;          // the LU path reports it
+    lo = std::min(lo, v);
+    hi = std::max(hi, v);
+    sum += v;
+  }
+  const double l2 = sum / nE / std::log(2.0);
+  const double eps0 = std::exp2(std::round(4.0 * l2) / 4.0);
+  if (!c->pb_valid || c->pb.eps0 != eps0) {
+    EigBasisNS E;
+    c->pb_valid = false;
+    if (build_eig_basis_ns(c->ref, c->cdS0, c->cdW0, c->cdV0, eps0, E)) {
+      auto put = [&](double** dst, const std::vector<double>& v) -> cudaError_t {
+        if (!*dst) {
+          cudaError_t e = c->alloc(dst, v.size());
+          if (e != cudaSuccess) return e;
+        }
+        return cudaMemcpy(*dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+      };
+      CUDA_TRY(put(&c->pb.X, E.X));
+      CUDA_TRY(put(&c->pb.R, E.R));
+      CUDA_TRY(put(&c->pb.Pv1, E.Pv1));
+      CUDA_TRY(put(&c->pb.Pv0, E.Pv0));
+      CUDA_TRY(put(&c->pb.Pw1, E.Pw1));
+      CUDA_TRY(put(&c->pb.Pw0, E.Pw0));
+      CUDA_TRY(put(&c->pb.la, E.la));
+      CUDA_TRY(put(&c->pb.lb, E.lb));
+      if (!c->pb.kind) CUDA_TRY(c->alloc(&c->pb.kind, E.kind.size()));
+      CUDA_TRY(cudaMemcpy(c->pb.kind, E.kind.data(), sizeof(int) * E.kind.size(),
+                          cudaMemcpyHostToDevice));
+      c->pb.eps0 = eps0;
+      c->pb_valid = true;
+      c->pb_host = E;
+    }
+  }
+  if (c->pb_valid) {
+    const double err = std::max(
+        check_eig_basis_ns(c->ref, c->cdS0, c->cdW0, c->cdV0, c->cdad, c->pb_host, std::exp(lo)),
+        check_eig_basis_ns(c->ref, c->cdS0, c->cdW0, c->cdV0, c->cdad, c->pb_host, std::exp(hi)));
+    c->cd_basis = err <= 1e-11;
+  }
+  if (!c->cd_basis && c->opts.condensation == HDGMG_CONDENSE_BASIS)
+    return fail(HDGMG_EINVAL, "condensation BASIS: the pencil basis is not accurate for this kappa");
+  return HDGMG_OK;
+}
+
 hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   if (!c || !log_kappa) return fail(HDGMG_EINVAL, "NULL argument");
   cudaStream_t s = c->stream;
@@ -1338,6 +1410,10 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
   Level& L0 = c->levels[0];
+  if (c->ns) {
+    STATUS_TRY(prepare_pencil(c, log_kappa));
+    if (!c->cd_basis && !c->Lfac) CUDA_TRY(c->alloc(&c->Lfac, (size_t)c->nv * c->nv * nE));
+  }
   launch_kappa(s, nE, c->logk, c->kap);
   // the first set-up of a (kernel, p) pair times the candidate block sizes
   // before the condensation proper (outside the timed condensation events)
@@ -1345,8 +1421,11 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
     const bool tune_only = pass == 0;
     if (!tune_only) CUDA_TRY(cudaEventRecord(c->evk0, s));
     if (c->ns)
-      c->condense_threads = launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A,
-                                               c->Lfac, c->err, tune_only);
+      c->condense_threads =
+          c->cd_basis ? launch_condense_cdeig(s, c->refd, c->cd, c->pb, c->p, nE, c->kap, L0.d64.A,
+                                              c->err, tune_only)
+                      : launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac,
+                                           c->err, tune_only);
     else
       c->condense_threads =
           c->basis ? launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, tune_only)
@@ -1395,9 +1474,15 @@ hdgmg_status tune_condensation(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
   launch_kappa(s, nE, c->logk, c->kap);
   Level& L0 = c->levels[0];
-  if (c->ns)
-    launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
-  else
+  if (c->ns) {
+    STATUS_TRY(prepare_pencil(c, log_kappa));
+    if (c->cd_basis) {
+      launch_condense_cdeig(s, c->refd, c->cd, c->pb, c->p, nE, c->kap, L0.d64.A, c->err, true);
+    } else {
+      if (!c->Lfac) CUDA_TRY(c->alloc(&c->Lfac, (size_t)c->nv * c->nv * nE));
+      launch_condense_cd(s, c->refd, c->cd, c->p, nE, c->kap, L0.d64.A, c->Lfac, c->err, true);
+    }
+  } else
     c->basis ? launch_condense(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->err, true)
              : launch_condense_factor(s, c->refd, c->p, nE, c->kap, c->ktau, L0.d64.A, c->Lfac,
                                       c->err, true);
@@ -1450,7 +1535,8 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
     info->t_condense_ms = c->t_condense_ms;
     info->condense_threads = c->condense_threads / 16;
     info->condense_elements_per_block = c->condense_threads % 16;
-    info->condense_kind = c->basis ? HDGMG_CONDENSE_BASIS : HDGMG_CONDENSE_FACTOR;
+    info->condense_kind =
+        (c->ns ? c->cd_basis : c->basis) ? HDGMG_CONDENSE_BASIS : HDGMG_CONDENSE_FACTOR;
     info->n_levels = (int)c->levels.size();
     info->trace_dofs = (int64_t)2 * c->n * (c->n - 1) * (c->p + 1);
   }

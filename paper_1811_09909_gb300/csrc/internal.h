@@ -62,6 +62,28 @@ struct EigBasis {
 };
 bool build_eig_basis(const RefElement& R, double r0, double hmin, EigBasis& out);
 
+// Non-symmetric volume blocks S(eps) = eps G + S0 (eigbasis.cpp): with
+// B = S(eps0), B^-1 G = X Lambda X^-1 in real block form (kind 0: real
+// eigenvalue la; kind 1, 2: the two columns xr, xi of a pair la +- i lb), so
+// S(eps)^-1 = X (I + (eps - eps0) Lambda)^-1 R with R = X^-1 B^-1, and
+//   A_e = eps K + diag - (eps Pv1 + Pv0)^T (I + d Lambda)^-1 (eps Pw1 + Pw0),
+// Pv1 = X^T Hv, Pv0 = X^T V0, Pw1 = R H, Pw0 = R W0 ([nv][nt]).
+struct EigBasisNS {
+  std::vector<double> X, R, Pv1, Pv0, Pw1, Pw0, la, lb;
+  std::vector<int> kind;
+  double eps0 = 1.0;
+};
+bool real_eigen_decomposition(const std::vector<double>& M, int n, std::vector<double>& X,
+                              std::vector<double>& la, std::vector<double>& lb,
+                              std::vector<int>& kind);
+bool build_eig_basis_ns(const RefElement& R, const std::vector<double>& S0,
+                        const std::vector<double>& W0, const std::vector<double>& V0, double eps0,
+                        EigBasisNS& out);
+// relative difference of A_e(eps) through the basis against a direct solve
+double check_eig_basis_ns(const RefElement& R, const std::vector<double>& S0,
+                          const std::vector<double>& W0, const std::vector<double>& V0,
+                          const std::vector<double>& adiag, const EigBasisNS& E, double eps);
+
 // tau_e = t kappa_e: move tau into the kappa-proportional tables
 // (G += t E, H += t F, Hv += t F, K += t I); the kernels then add no tau.
 void fold_kappa_tau(RefElement& R, double t);
@@ -161,6 +183,22 @@ void launch_recover_factor(cudaStream_t s, const RefDevice& ref, int p, int n, c
 struct CdTables {
   double *S0 = nullptr, *W0 = nullptr, *V0 = nullptr, *adiag = nullptr;
 };
+// device copy of an EigBasisNS (X, R [nv][nv]; P* [nv][nt]; la, lb, kind [nv])
+struct PencilDevice {
+  double *X = nullptr, *R = nullptr, *Pv1 = nullptr, *Pv0 = nullptr, *Pw1 = nullptr,
+         *Pw0 = nullptr, *la = nullptr, *lb = nullptr;
+  int* kind = nullptr;
+  double eps0 = 0.0;
+};
+// non-symmetric S through the pencil basis (no stored factor)
+int launch_condense_cdeig(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
+                          const PencilDevice& pb, int p, int nE, const double* kap, double* A,
+                          int* err, bool tune_only = false);
+void launch_rhs_cdeig(cudaStream_t s, const RefDevice& ref, const PencilDevice& pb, int p, int n,
+                      const double* kap, const double* f, double* b);
+void launch_recover_cdeig(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
+                          const PencilDevice& pb, int p, int n, const double* kap, const double* f,
+                          const double* lam, double* u, double* q);
 void build_cd_tables(const RefElement& R, double tau, double bx, double by,
                      std::vector<double>& S0, std::vector<double>& W0, std::vector<double>& V0,
                      std::vector<double>& adiag);

@@ -115,6 +115,108 @@ __global__ void __launch_bounds__(128) condense_eig_kernel(
   if (bad) atomicOr(err, 1);
 }
 
+// K1 for non-symmetric S through the pencil basis (eigbasis.cpp): with
+// eps = kappa_e, d = eps - eps0 and B^-1 G = X Lambda X^-1 in real block form,
+//   Y = (I + d Lambda)^-1 (eps Pw1 + Pw0),   Vt = eps Pv1 + Pv0,
+//   A_e = eps K + diag(adiag) - Vt^T Y       (full n_t x n_t, [entry][element]),
+// i.e. V^T S^-1 W without a per-element factorisation.  (I + d Lambda) has
+// 1 x 1 blocks 1 + d la_i and 2 x 2 blocks [[1 + d a, d b], [-d b, 1 + d a]]
+// (kind 1, 2 = the two columns of a pair); a block whose determinant is not
+// positive and finite sets *err.  EPB elements per block of 128 threads;
+// shared memory kappa [EPB], block coefficients [2][nv][EPB], Vt and Y
+// [nv * nt][EPB], element index fastest.
+template <int EPB>
+__global__ void __launch_bounds__(128) condense_cdeig_kernel(
+    int nv, int nt, int nE, int count, const double* __restrict__ la, const double* __restrict__ lb,
+    const int* __restrict__ kind, const double* __restrict__ Pw1, const double* __restrict__ Pw0,
+    const double* __restrict__ Pv1, const double* __restrict__ Pv0, const double* __restrict__ K,
+    const double* __restrict__ adiag, const double* __restrict__ kapv, double eps0,
+    double* __restrict__ A, int* __restrict__ err) {
+  constexpr int NT = 128;
+  extern __shared__ double smem[];
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * EPB;
+  const int nvt = nv * nt;
+  double* kp = smem;                      // [EPB]
+  double* cf = kp + EPB;                  // [2][nv][EPB]
+  double* Vt = cf + 2 * nv * EPB;         // [nvt][EPB]
+  double* Y = Vt + (size_t)nvt * EPB;     // [nvt][EPB]
+  if (tid < EPB) kp[tid] = kapv[min(e0 + tid, count - 1)];
+  __syncthreads();
+  bool bad = false;
+  // block coefficients: kind 0 -> 1 / (1 + d la); kind 1 -> (c, s) of the
+  // inverse [[c, -s], [s, c]] of the pair block; kind 2 -> unused
+  for (int idx = tid; idx < nv * EPB; idx += NT) {
+    const int el = idx % EPB, i = idx / EPB;
+    const double d = kp[el] - eps0;
+    const int kd = kind[i];
+    double c = 0.0, s = 0.0;
+    if (kd == 0) {
+      const double a = fma(d, la[i], 1.0);
+      if (!(fabs(a) > 0.0) || !isfinite(a)) {
+        if (e0 + el < count) bad = true;
+        c = 1.0;
+      } else {
+        c = 1.0 / a;
+      }
+    } else if (kd == 1) {
+      const double a = fma(d, la[i], 1.0), b = d * lb[i];
+      const double det = fma(a, a, b * b);
+      if (!(det > 0.0) || !isfinite(det)) {
+        if (e0 + el < count) bad = true;
+        c = 1.0;
+      } else {
+        const double r = 1.0 / det;
+        c = a * r;
+        s = b * r;
+      }
+    }
+    cf[idx] = c;
+    cf[nv * EPB + idx] = s;
+  }
+  for (int idx = tid; idx < nvt * EPB; idx += NT) {
+    const int el = idx % EPB, ic = idx / EPB;
+    Vt[idx] = fma(kp[el], Pv1[ic], Pv0[ic]);
+  }
+  __syncthreads();
+  // Y = blocks (eps Pw1 + Pw0): one thread per (row i of kind 0 or 1, c, el)
+  for (int idx = tid; idx < nvt * EPB; idx += NT) {
+    const int el = idx % EPB, ic = idx / EPB, i = ic / nt, c = ic - i * nt;
+    const int kd = kind[i];
+    if (kd == 2) continue;
+    const double w0 = fma(kp[el], Pw1[ic], Pw0[ic]);
+    const double cc = cf[i * EPB + el];
+    if (kd == 0) {
+      Y[idx] = cc * w0;
+    } else {
+      const int ic1 = ic + nt;
+      const double w1 = fma(kp[el], Pw1[ic1], Pw0[ic1]);
+      const double ss = cf[nv * EPB + i * EPB + el];
+      Y[idx] = fma(cc, w0, -ss * w1);
+      Y[(size_t)ic1 * EPB + el] = fma(ss, w0, cc * w1);
+      (void)c;
+    }
+  }
+  __syncthreads();
+  const int nn = nt * nt, st = nt * EPB;
+  for (int idx = tid; idx < nn * EPB; idx += NT) {
+    const int el = idx % EPB, t = idx / EPB, r = t / nt, c = t - r * nt;
+    const double* vr = Vt + r * EPB + el;
+    const double* yc = Y + c * EPB + el;
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      s0 = fma(vr[i * st], yc[i * st], s0);
+      s1 = fma(vr[(i + 1) * st], yc[(i + 1) * st], s1);
+    }
+    if (i < nv) s0 = fma(vr[i * st], yc[i * st], s0);
+    double a = fma(kp[el], K[t], -(s0 + s1));
+    if (r == c) a += adiag[r];
+    if (e0 + el < count) A[(size_t)t * nE + e0 + el] = a;
+  }
+  if (bad) atomicOr(err, 1);
+}
+
 // K1 by local factorisation (HDGMG_CONDENSE_FACTOR, symmetric S): Cholesky
 // S = L L^T, V = L^-1 W, A_e = kappa K + tau I - V^T V; the packed factor is
 // kept for K5/K12.  TPE threads per element and EPB elements per block, in lockstep (the
@@ -542,6 +644,124 @@ __global__ void recover_chol_kernel(int p, int n, const double* __restrict__ Mdi
     }
   }
 }
+// apply (I + d Lambda)^-1 to the coefficient vector z [nv] (thread-local
+// shared-memory column) of the non-symmetric pencil basis
+__device__ __forceinline__ void apply_pencil_blocks(const double* __restrict__ la,
+                                                    const double* __restrict__ lb,
+                                                    const int* __restrict__ kind, double d, int nv,
+                                                    double* z) {
+  for (int i = 0; i < nv; ++i) {
+    const int kd = kind[i];
+    if (kd == 0) {
+      TV(z, i) = TV(z, i) / fma(d, la[i], 1.0);
+    } else if (kd == 1) {
+      const double a = fma(d, la[i], 1.0), b = d * lb[i];
+      const double r = 1.0 / fma(a, a, b * b);
+      const double z0 = TV(z, i), z1 = TV(z, i + 1);
+      TV(z, i) = (a * z0 - b * z1) * r;
+      TV(z, i + 1) = (b * z0 + a * z1) * r;
+    }
+  }
+}
+
+// K5 (non-symmetric S, pencil basis): g_e = (eps Pv1 + Pv0)^T (I + d Lambda)^-1 R (M f_e)
+__global__ void rhs_cdeig_kernel(int p, int n, const double* __restrict__ Mdiag,
+                                 const double* __restrict__ Rm, const double* __restrict__ la,
+                                 const double* __restrict__ lb, const int* __restrict__ kind,
+                                 const double* __restrict__ Pv1, const double* __restrict__ Pv0,
+                                 const double* __restrict__ kapv, double eps0,
+                                 const double* __restrict__ f, double* __restrict__ b) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  double* z = smem + (size_t)nv * blockDim.x;
+  const double eps = kapv[e];
+  for (int a = 0; a < nv; ++a) TV(y, a) = Mdiag[a] * f[(size_t)a * nE + e];
+  for (int i = 0; i < nv; ++i) {
+    double s = 0.0;
+    for (int a = 0; a < nv; ++a) s = fma(Rm[i * nv + a], TV(y, a), s);
+    TV(z, i) = s;
+  }
+  apply_pencil_blocks(la, lb, kind, eps - eps0, nv, z);
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) {
+    const int edge = ed[c / p1];
+    if (is_boundary_edge(n, edge)) continue;
+    double g1 = 0.0, g0 = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      g1 = fma(Pv1[i * nt + c], TV(z, i), g1);
+      g0 = fma(Pv0[i * nt + c], TV(z, i), g0);
+    }
+    atomicAdd(&b[(size_t)(c % p1) * nedge + edge], fma(eps, g1, g0));
+  }
+}
+
+// K12 (non-symmetric S, pencil basis): u = X (I + d Lambda)^-1 R (M f + W lambda_e),
+// W = eps H + W0; q = eps M^-1 (B^T u - C lambda)
+__global__ void recover_cdeig_kernel(int p, int n, const double* __restrict__ Mdiag,
+                                     const double* __restrict__ H, const double* __restrict__ W0,
+                                     const double* __restrict__ Xm, const double* __restrict__ Rm,
+                                     const double* __restrict__ la, const double* __restrict__ lb,
+                                     const int* __restrict__ kind, const double* __restrict__ BxT,
+                                     const double* __restrict__ ByT, const double* __restrict__ Cx,
+                                     const double* __restrict__ Cy, const double* __restrict__ kapv,
+                                     double eps0, const double* __restrict__ f,
+                                     const double* __restrict__ lam, double* __restrict__ u,
+                                     double* __restrict__ q) {
+  extern __shared__ double smem[];
+  const int p1 = p + 1, nv = p1 * p1, nt = 4 * p1;
+  const int nE = n * n;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nE) return;
+  double* y = smem;
+  double* z = smem + (size_t)nv * blockDim.x;
+  double* le = smem + (size_t)2 * nv * blockDim.x;
+  const double eps = kapv[e];
+  int ed[4];
+  element_edges(n, e, ed);
+  const int nedge = 2 * n * (n + 1);
+  for (int c = 0; c < nt; ++c) TV(le, c) = lam[(size_t)(c % p1) * nedge + ed[c / p1]];
+  for (int a = 0; a < nv; ++a) {
+    double s = Mdiag[a] * f[(size_t)a * nE + e];
+    for (int c = 0; c < nt; ++c) s += fma(eps, H[a * nt + c], W0[a * nt + c]) * TV(le, c);
+    TV(y, a) = s;
+  }
+  for (int i = 0; i < nv; ++i) {
+    double s = 0.0;
+    for (int a = 0; a < nv; ++a) s = fma(Rm[i * nv + a], TV(y, a), s);
+    TV(z, i) = s;
+  }
+  apply_pencil_blocks(la, lb, kind, eps - eps0, nv, z);
+  for (int a = 0; a < nv; ++a) {
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s = fma(Xm[a * nv + i], TV(z, i), s);
+    TV(y, a) = s;
+  }
+  if (u)
+    for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
+  if (q) {
+    for (int a = 0; a < nv; ++a) {
+      double sx = 0.0, sy = 0.0;
+      for (int b2 = 0; b2 < nv; ++b2) {
+        sx += BxT[a * nv + b2] * TV(y, b2);
+        sy += ByT[a * nv + b2] * TV(y, b2);
+      }
+      for (int c = 0; c < nt; ++c) {
+        sx -= Cx[a * nt + c] * TV(le, c);
+        sy -= Cy[a * nt + c] * TV(le, c);
+      }
+      const double sc = eps / Mdiag[a];
+      q[(size_t)a * nE + e] = sc * sx;
+      q[(size_t)(nv + a) * nE + e] = sc * sy;
+    }
+  }
+}
+
 // solve (LU) y = y in place with the full factors of condense_cd_kernel
 __device__ __forceinline__ void lu_solve(const double* __restrict__ LU, int nv, int nE, int e,
                                          double* y) {
@@ -787,6 +1007,15 @@ void set_smem_attr_chol() {
   (void)done;
 }
 template <int EPB>
+void set_smem_attr_cdeig() {
+  static const bool done = [] {
+    cudaFuncSetAttribute(condense_cdeig_kernel<EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         220 * 1024);
+    return true;
+  }();
+  (void)done;
+}
+template <int EPB>
 void set_smem_attr_eig() {
   static const bool done = [] {
     cudaFuncSetAttribute(condense_eig_kernel<EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -808,6 +1037,7 @@ void set_smem_attr_cd() {
 // symmetric: 128 threads per block, EPB elements (encoded (128 / EPB) * 16 + EPB)
 constexpr int kSymCands[] = {64 * 16 + 2, 32 * 16 + 4, 16 * 16 + 8};
 constexpr int kCdCands[] = {32 * 16 + 1, 64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
+constexpr int kCdEigCands[] = {128 * 16 + 1, 64 * 16 + 2, 32 * 16 + 4};
 constexpr int kCholCands[] = {8 * 16 + 4, 16 * 16 + 2, 16 * 16 + 4, 32 * 16 + 1, 32 * 16 + 2,
                               64 * 16 + 1, 128 * 16 + 1, 256 * 16 + 1};
 }  // namespace
@@ -858,6 +1088,65 @@ int launch_condense_factor(cudaStream_t s, const RefDevice& ref, int p, int nE, 
   const int id = tune_config(s, 2, p, nE, kCholCands, 8, per_elem, launch);
   if (!tune_only) launch(id, 0, nE);
   return id;
+}
+
+int launch_condense_cdeig(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
+                          const PencilDevice& pb, int p, int nE, const double* kap, double* A,
+                          int* err, bool tune_only) {
+  const int nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const size_t per_elem = sizeof(double) * (size_t)(1 + 2 * nv + 2 * nv * nt);
+  auto launch = [&](int id, int e0, int count) {
+    (void)e0;
+    note_launch();
+    switch (id) {
+#define CASE(EPB)                                                                              \
+  case (128 / EPB) * 16 + EPB:                                                                 \
+    set_smem_attr_cdeig<EPB>();                                                                \
+    condense_cdeig_kernel<EPB><<<(count + EPB - 1) / EPB, 128, per_elem * EPB, s>>>(           \
+        nv, nt, nE, count, pb.la, pb.lb, pb.kind, pb.Pw1, pb.Pw0, pb.Pv1, pb.Pv0, ref.K,       \
+        cd.adiag, kap, pb.eps0, A, err);                                                       \
+    break;
+      CASE(1) CASE(2) CASE(4)
+#undef CASE
+      default: break;
+    }
+  };
+  const int id = tune_config(s, 3, p, nE, kCdEigCands, 3, per_elem, launch);
+  if (!tune_only) launch(id, 0, nE);
+  return id;
+}
+
+void launch_rhs_cdeig(cudaStream_t s, const RefDevice& ref, const PencilDevice& pb, int p, int n,
+                      const double* kap, const double* f, double* b) {
+  const int nE = n * n, nv = (p + 1) * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(2 * nv) * threads;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(rhs_cdeig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  rhs_cdeig_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, pb.R, pb.la, pb.lb, pb.kind, pb.Pv1,
+                                                pb.Pv0, kap, pb.eps0, f, b);
+}
+
+void launch_recover_cdeig(cudaStream_t s, const RefDevice& ref, const CdTables& cd,
+                          const PencilDevice& pb, int p, int n, const double* kap, const double* f,
+                          const double* lam, double* u, double* q) {
+  const int nE = n * n, nv = (p + 1) * (p + 1), nt = 4 * (p + 1);
+  const int threads = 64, blocks = (nE + threads - 1) / threads;
+  const size_t shm = sizeof(double) * (size_t)(2 * nv + nt) * threads;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(recover_cdeig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         160 * 1024);
+    return true;
+  }();
+  (void)attr;
+  note_launch();
+  recover_cdeig_kernel<<<blocks, threads, shm, s>>>(p, n, ref.M, ref.H, cd.W0, pb.X, pb.R, pb.la,
+                                                    pb.lb, pb.kind, ref.BxT, ref.ByT, ref.Cx,
+                                                    ref.Cy, kap, pb.eps0, f, lam, u, q);
 }
 
 int launch_condense_cd(cudaStream_t s, const RefDevice& ref, const CdTables& cd, int p, int nE,

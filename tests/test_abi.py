@@ -63,7 +63,6 @@ def test_default_options(lib):
     (dict(scheme=2, krylov=1), "symmetric"), (dict(scheme=3, krylov=1), "symmetric"),
     (dict(tau_mode=3), "tau_mode"),
     (dict(condensation=3), "unknown condensation"),
-    (dict(pde=1, krylov=2, condensation=1), "BASIS needs symmetric"),
 ])
 def test_create_rejects_bad_arguments(lib, kw, msg):
     from paper_1811_09909_gb300 import hdgmg

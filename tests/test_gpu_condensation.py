@@ -84,7 +84,7 @@ def test_routes_agree_with_each_other_and_the_oracle(scheme, p, mode, c):
         assert rel_l2(out[route][3], q_ref) <= 1e-8
 
 
-def test_auto_picks_basis_for_symmetric_and_factor_for_nonsymmetric():
+def test_auto_picks_basis_where_accurate():
     wl = W.lognormal(8, 2, seed=3)
     s = hdgmg.Solver(8, 2, tau_c=1.0)
     s.setup(cuda(wl.log_kappa))
@@ -94,7 +94,71 @@ def test_auto_picks_basis_for_symmetric_and_factor_for_nonsymmetric():
     s = hdgmg.Solver(8, 2, tau_c=wl.tau_c, beta=wl.beta, krylov=hdgmg.KRYLOV_GMRES)
     s.setup(cuda(wl.log_kappa))
     _, _, _, info = s.solve(cuda(wl.f[0]))
-    assert info.condense_kind == hdgmg.CONDENSE_FACTOR
+    assert info.condense_kind == hdgmg.CONDENSE_BASIS
+
+
+@pytest.mark.parametrize("p,eps", [(2, 1e-2), (4, 1e-3), (6, 1e-3)])
+def test_nonsymmetric_routes_agree(p, eps):
+    """Convection-diffusion: the pencil basis (eps0 = kappa's geometric mean)
+    and the local LU give the oracle's element operators, right-hand sides and
+    solutions; kappa spread e^N(0, 0.3^2) around eps."""
+    n = 8
+    wl = W.convdiff(n, p, eps=eps)
+    rng = np.random.default_rng(p)
+    wl.log_kappa = wl.log_kappa + rng.normal(0.0, 0.3, n * n)
+    f = rng.standard_normal(wl.f[0].shape)
+    pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau(), beta=wl.beta)
+    Ae, _ = pr.condense()
+    ref = np.transpose(Ae, (1, 2, 0))
+    _, bf, *_ = pr.system(f)
+    lam_ref = pr.solve_direct(f)
+    u_ref, q_ref = pr.recover(lam_ref, f)
+    out = {}
+    for route in ROUTES:
+        s = hdgmg.Solver(n, p, tau_c=wl.tau_c, beta=wl.beta, krylov=hdgmg.KRYLOV_GMRES,
+                         condensation=ROUTES[route], coarsest_n=2, rtol=1e-12, max_it=300)
+        s.setup(cuda(wl.log_kappa))
+        A = host(s.element_matrices(0))
+        assert np.abs(A - ref).max() <= 1e-10 * np.abs(ref).max(), route
+        b = host(s.condensed_rhs(cuda(f)))
+        b_em = hdg.api_to_edge_major(b, n, p + 1)[pr.free_dofs()]
+        assert np.abs(b_em - bf).max() <= 1e-10 * np.abs(bf).max(), route
+        lam, u, q, info = s.solve(cuda(f))
+        assert info.converged == 1 and info.condense_kind == ROUTES[route], route
+        assert rel_l2(host(lam), lam_ref) <= 1e-8
+        assert rel_l2(host(u), u_ref) <= 1e-8
+        assert rel_l2(host(q), q_ref) <= 1e-8
+        out[route] = A
+    assert np.abs(out["basis"] - out["factor"]).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_inaccurate_pencil_basis_falls_back_to_lu():
+    """IIPG-H with a kappa-independent penalty at p = 4: the eigenvectors of
+    the pencil are nearly dependent (the element's symmetries make eigenvalues
+    coincide), the set-up's check fails, AUTO falls back to the local LU and
+    an explicit BASIS request is EINVAL."""
+    n, p = 8, 4
+    wl = W.lognormal(n, p, sigma=0.3, seed=5, tau_mode="over_h", tau_c=60.0)
+    s = hdgmg.Solver(n, p, tau_mode=hdgmg.TAU_OVER_H, tau_c=60.0, scheme=hdgmg.SCHEME_IIPG,
+                     krylov=hdgmg.KRYLOV_GMRES, coarsest_n=2, rtol=1e-12)
+    s.setup(cuda(wl.log_kappa))
+    lam, _, _, info = s.solve(cuda(wl.f[0]))
+    assert info.converged == 1
+    pr = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau(), scheme="iipg")
+    assert rel_l2(host(lam), pr.solve_direct(wl.f[0])) <= 1e-8
+    kind = info.condense_kind
+    s2 = hdgmg.Solver(n, p, tau_mode=hdgmg.TAU_OVER_H, tau_c=60.0, scheme=hdgmg.SCHEME_IIPG,
+                      krylov=hdgmg.KRYLOV_GMRES, condensation=hdgmg.CONDENSE_BASIS)
+    if kind == hdgmg.CONDENSE_FACTOR:
+        with pytest.raises(hdgmg.HdgmgError) as ei:
+            s2.setup(cuda(wl.log_kappa))
+        assert "EINVAL" in str(ei.value)
+    else:                                   # the basis passed its check: it must then be exact
+        s2.setup(cuda(wl.log_kappa))
+        A = host(s2.element_matrices(0))
+        Ae, _ = pr.condense()
+        ref = np.transpose(Ae, (1, 2, 0))
+        assert np.abs(A - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
 def test_factor_route_reports_indefinite_blocks():
