@@ -472,6 +472,34 @@ __device__ __forceinline__ bool is_boundary_edge(int n, int edge) {
   return j == 0 || j == n;
 }
 
+// q = kappa M^-1 (B^T u - C lambda) at every node from the nodal u (shared
+// column y) and the element's traces (le), using the tensor-product structure
+// of the tables: an x-derivative couples the nodes of one row (same a2), a
+// y-derivative those of one column (same a1); C_x lives on the vertical
+// edges (trace dofs 0 .. 2 p1 - 1), C_y on the horizontal ones.
+__device__ __forceinline__ void recover_q(int p1, const double* __restrict__ BxT,
+                                          const double* __restrict__ ByT,
+                                          const double* __restrict__ Cx,
+                                          const double* __restrict__ Cy,
+                                          const double* __restrict__ Mdiag, double kap,
+                                          const double* y, const double* le, double* __restrict__ q,
+                                          int nE, int e) {
+  const int nv = p1 * p1, nt = 4 * p1, hv = 2 * p1;
+  for (int a = 0; a < nv; ++a) {
+    const int a2 = a / p1, a1 = a - a2 * p1;
+    double sx = 0.0, sy = 0.0;
+    for (int b = 0; b < p1; ++b) {
+      sx += BxT[a * nv + a2 * p1 + b] * TV(y, a2 * p1 + b);
+      sy += ByT[a * nv + b * p1 + a1] * TV(y, b * p1 + a1);
+    }
+    for (int c = 0; c < hv; ++c) sx -= Cx[a * nt + c] * TV(le, c);
+    for (int c = hv; c < nt; ++c) sy -= Cy[a * nt + c] * TV(le, c);
+    const double sc = kap / Mdiag[a];
+    q[(size_t)a * nE + e] = sc * sx;
+    q[(size_t)(nv + a) * nE + e] = sc * sy;
+  }
+}
+
 // s_i^-1 for element e (symmetric S)
 __device__ __forceinline__ double inv_s(const double* g, const double* ev, double kap, int i) {
   return recip_newton(fma(kap, g[i], ev[i]));
@@ -554,22 +582,7 @@ __global__ void recover_kernel(int p, int n, const double* __restrict__ Mdiag,
   }
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
-  if (q) {
-    for (int a = 0; a < nv; ++a) {
-      double sx = 0.0, sy = 0.0;
-      for (int b2 = 0; b2 < nv; ++b2) {
-        sx += BxT[a * nv + b2] * TV(y, b2);
-        sy += ByT[a * nv + b2] * TV(y, b2);
-      }
-      for (int c = 0; c < nt; ++c) {
-        sx -= Cx[a * nt + c] * TV(le, c);
-        sy -= Cy[a * nt + c] * TV(le, c);
-      }
-      const double sc = kap / Mdiag[a];
-      q[(size_t)a * nE + e] = sc * sx;
-      q[(size_t)(nv + a) * nE + e] = sc * sy;
-    }
-  }
+  if (q) recover_q(p + 1, BxT, ByT, Cx, Cy, Mdiag, kap, y, le, q, nE, e);
 }
 // K5 (FACTOR, symmetric S): thread per element; shared memory y[nv][blockDim]
 __global__ void rhs_chol_kernel(int p, int n, const double* __restrict__ Mdiag,
@@ -627,22 +640,7 @@ __global__ void recover_chol_kernel(int p, int n, const double* __restrict__ Mdi
   chol_solve(L, nv, nE, e, y);
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
-  if (q) {
-    for (int a = 0; a < nv; ++a) {
-      double sx = 0.0, sy = 0.0;
-      for (int b2 = 0; b2 < nv; ++b2) {
-        sx += BxT[a * nv + b2] * TV(y, b2);
-        sy += ByT[a * nv + b2] * TV(y, b2);
-      }
-      for (int c = 0; c < nt; ++c) {
-        sx -= Cx[a * nt + c] * TV(le, c);
-        sy -= Cy[a * nt + c] * TV(le, c);
-      }
-      const double sc = kap / Mdiag[a];
-      q[(size_t)a * nE + e] = sc * sx;
-      q[(size_t)(nv + a) * nE + e] = sc * sy;
-    }
-  }
+  if (q) recover_q(p + 1, BxT, ByT, Cx, Cy, Mdiag, kap, y, le, q, nE, e);
 }
 // apply (I + d Lambda)^-1 to the coefficient vector z [nv] (thread-local
 // shared-memory column) of the non-symmetric pencil basis
@@ -744,22 +742,7 @@ __global__ void recover_cdeig_kernel(int p, int n, const double* __restrict__ Md
   }
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
-  if (q) {
-    for (int a = 0; a < nv; ++a) {
-      double sx = 0.0, sy = 0.0;
-      for (int b2 = 0; b2 < nv; ++b2) {
-        sx += BxT[a * nv + b2] * TV(y, b2);
-        sy += ByT[a * nv + b2] * TV(y, b2);
-      }
-      for (int c = 0; c < nt; ++c) {
-        sx -= Cx[a * nt + c] * TV(le, c);
-        sy -= Cy[a * nt + c] * TV(le, c);
-      }
-      const double sc = eps / Mdiag[a];
-      q[(size_t)a * nE + e] = sc * sx;
-      q[(size_t)(nv + a) * nE + e] = sc * sy;
-    }
-  }
+  if (q) recover_q(p + 1, BxT, ByT, Cx, Cy, Mdiag, eps, y, le, q, nE, e);
 }
 
 // solve (LU) y = y in place with the full factors of condense_cd_kernel
@@ -832,22 +815,7 @@ __global__ void recover_cd_kernel(int p, int n, const double* __restrict__ Mdiag
   lu_solve(LU, nv, nE, e, y);
   if (u)
     for (int a = 0; a < nv; ++a) u[(size_t)a * nE + e] = TV(y, a);
-  if (q) {
-    for (int a = 0; a < nv; ++a) {
-      double sx = 0.0, sy = 0.0;
-      for (int b2 = 0; b2 < nv; ++b2) {
-        sx += BxT[a * nv + b2] * TV(y, b2);
-        sy += ByT[a * nv + b2] * TV(y, b2);
-      }
-      for (int c = 0; c < nt; ++c) {
-        sx -= Cx[a * nt + c] * TV(le, c);
-        sy -= Cy[a * nt + c] * TV(le, c);
-      }
-      const double sc = eps / Mdiag[a];
-      q[(size_t)a * nE + e] = sc * sx;
-      q[(size_t)(nv + a) * nE + e] = sc * sy;
-    }
-  }
+  if (q) recover_q(p + 1, BxT, ByT, Cx, Cy, Mdiag, eps, y, le, q, nE, e);
 }
 
 // ---------------------------------------------------------- adjoint (K13)
