@@ -186,12 +186,10 @@ class ClockSampler:
 def run_ours(args):
     import numpy as np
     import torch
-    from paper_1811_09909_gb300 import hdgmg
+    from paper_1811_09909_gb300 import hdgmg, replicas
     from paper_1811_09909_gb300 import workloads as W
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.rank_info()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -200,7 +198,7 @@ def run_ours(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    wl = W.lognormal(N_MESH, P_ORDER, seed=SEED + 1000 * rank)
+    wl = W.lognormal(N_MESH, P_ORDER, seed=replicas.replica_seed(SEED, rank))
     logk = torch.as_tensor(wl.log_kappa, device=dev)
     f = torch.as_tensor(wl.f[0], device=dev)
     nd, ne, nv, E = P_ORDER + 1, 2 * N_MESH * (N_MESH + 1), (P_ORDER + 1) ** 2, N_MESH * N_MESH
@@ -248,10 +246,7 @@ def run_ours(args):
         if dist:
             dist.barrier()
         ck = clocks.stop() if clocks else None
-        tot = torch.tensor([sum(times)], device=dev, dtype=torch.float64)
-        if dist:
-            dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-        ms = float(tot.item()) / args.steps
+        ms = replicas.max_over_ranks(sum(times), dist, device=dev) / args.steps
         worst = max(i.rel_res for i in infos)
         assert all(i.converged for i in infos) and worst <= 1e-10, worst
         results[name] = {"ms": ms, "iters": infos[-1].iters, "rel_res": worst,
@@ -268,7 +263,7 @@ def run_ours(args):
                     "rel_res": r["rel_res"], "gpu_launches": r["launches"]}
         return None
     mixed, fp64 = results["mixed"], results["fp64"]
-    value = dofs * world / (mixed["ms"] * 1e-3)
+    value = replicas.whole_job_rate(dofs, world, mixed["ms"])
 
     # end to end through the C ABI on pinned host buffers (mixed arm)
     s = arms["mixed"]
@@ -291,7 +286,8 @@ def run_ours(args):
         assert st == 0 and info.rel_res <= 1e-10
     h2d = 8 * (E + nv * E)
     d2h = 8 * (nd * ne + nv * E + 2 * nv * E)
-    e2e = {"value": dofs * world / statistics.mean(e2e_t), "unit": UNIT,
+    e2e_s = replicas.max_over_ranks(statistics.mean(e2e_t), dist, device=dev)
+    e2e = {"value": dofs * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     line = None
@@ -301,7 +297,8 @@ def run_ours(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 condensation+outer CG, f32 V-cycle", "data": "synthetic",
                 "config": workload_config(),
-                "fp64": {"value": dofs * world / (fp64["ms"] * 1e-3), "ms_per_step": fp64["ms"],
+                "fp64": {"value": replicas.whole_job_rate(dofs, world, fp64["ms"]),
+                         "ms_per_step": fp64["ms"],
                          "iters": fp64["iters"], "rel_res": fp64["rel_res"],
                          "setup_ms": fp64["setup_ms"], "solve_ms": fp64["solve_ms"]},
                 "mixed": {"iters": mixed["iters"], "rel_res": mixed["rel_res"],
