@@ -302,7 +302,9 @@ def run_ours(args):
                          "iters": fp64["iters"], "rel_res": fp64["rel_res"],
                          "setup_ms": fp64["setup_ms"], "solve_ms": fp64["solve_ms"]},
                 "mixed": {"iters": mixed["iters"], "rel_res": mixed["rel_res"],
-                          "setup_ms": mixed["setup_ms"], "solve_ms": mixed["solve_ms"]},
+                          "setup_ms": mixed["setup_ms"], "solve_ms": mixed["solve_ms"],
+                          "solve_only_value": replicas.whole_job_rate(dofs, world,
+                                                                      mixed["solve_ms"])},
                 "clocks": mixed["clocks"], "e2e": e2e, "gpu_launches": mixed["launches"],
                 "roofline": roofline_condense(mixed["condense_ms"]),
                 "vcycle": vcycle_bandwidth(arms["mixed"], dev)}
