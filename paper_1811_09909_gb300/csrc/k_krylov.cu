@@ -30,26 +30,43 @@ __global__ void gm_store_kernel(int64_t len, const double* __restrict__ in, doub
     dst[i] = in[i];
 }
 
-// partial[k][block] = sum_i V[k][i] w[i] for k <= j
+// partial[k][block] = sum_i V[k][i] w[i] for k <= j: the dot products of up to
+// KC basis vectors per pass over the data (w read once per pass, the KC sums
+// in registers, reduced by warp shuffles and across the block's warps)
+constexpr int kMultidotChunk = 16;
 __global__ void __launch_bounds__(256) gm_multidot_kernel(int64_t len, const double* __restrict__ V,
                                                           const int* __restrict__ jp,
                                                           const double* __restrict__ w,
                                                           double* __restrict__ partial) {
-  __shared__ double sh[256];
+  constexpr int KC = kMultidotChunk;
+  __shared__ double sh[KC][8];
   const int nk = *jp + 1;
-  for (int k = 0; k < nk; ++k) {
-    const double* v = V + (int64_t)k * len;
-    double s = 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nk; k0 += KC) {
+    const int kc = nk - k0 < KC ? nk - k0 : KC;
+    const double* vb = V + (int64_t)k0 * len;
+    double s[KC];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) s[q] = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-         i += (int64_t)gridDim.x * blockDim.x)
-      s += v[i] * w[i];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < KC; ++q)
+        if (q < kc) s[q] = fma(vb[(int64_t)q * len + i], wi, s[q]);
     }
-    if (threadIdx.x == 0) partial[k * gridDim.x + blockIdx.x] = sh[0];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      double t = s[q];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) sh[q][warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < kc) {
+      double t = 0.0;
+      for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) t += sh[threadIdx.x][wv];
+      partial[(k0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+    }
     __syncthreads();
   }
 }
