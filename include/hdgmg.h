@@ -172,6 +172,14 @@ typedef struct {
                              FACTOR; BASIS when the non-symmetric basis fails
                              its accuracy check: hdgmg_setup returns EINVAL;
                              AUTO                                            */
+  int32_t l2_persist_mb;  /* > 0: the Krylov loop graphs mark the finest
+                             operator the V-cycle reads (its BF16, FP32 or
+                             FP64 copy) as persisting in L2, with a set-aside of
+                             this many MiB (capped by the device; the set-aside
+                             is a limit of the calling process's context, the
+                             persisting lines are reset by hdgmg_destroy); 0:
+                             off.  hdgmg_batch_create uses 0 for its contexts.
+                             64                                              */
 } hdgmg_opts;
 
 typedef struct {

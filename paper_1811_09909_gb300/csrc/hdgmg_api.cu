@@ -73,6 +73,7 @@ struct hdgmg_ctx {
   double* logk = nullptr;
   double* kap = nullptr;       // exp(log kappa) per element
   bool basis = false;          // symmetric S condensed through the shared eigenbasis
+  bool l2_window = false;      // an L2 persistence window was set on cap_stream
   double* Lfac = nullptr;      // factors of S when not: LU (full, ns) or Cholesky (packed)
   int* err = nullptr;
   int* err_h = nullptr;
@@ -728,11 +729,59 @@ void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
                                c->opts.inner_rtol * c->opts.inner_rtol, nullptr);
 }
 
+// Keep the finest operator the V-cycle reads (twice per cycle) in L2 across the
+// iterations of a Krylov loop: an access-policy window on the capture stream,
+// which the captured kernel nodes inherit.  The set-aside for persisting lines
+// is a limit of this process's context (capped by the device); hdgmg_destroy
+// resets the persisting lines.
+void set_l2_window(hdgmg_ctx* c) {
+  if (c->opts.l2_persist_mb <= 0) return;
+  int dev = 0, maxp = 0, maxw = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev);
+  cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+  if (maxp <= 0 || maxw <= 0) return;
+  Level& L0 = c->levels[0];
+  const size_t n = (size_t)L0.nsym * L0.nE;
+  void* base;
+  size_t bytes;
+  if (L0.A16) {
+    base = L0.A16;
+    bytes = n * sizeof(__nv_bfloat16);
+  } else if (c->opts.precision != HDGMG_PREC_FP64) {
+    base = L0.d32.A;
+    bytes = n * sizeof(float);
+  } else {
+    base = L0.d64.A;
+    bytes = n * sizeof(double);
+  }
+  size_t lim = (size_t)c->opts.l2_persist_mb << 20;
+  if (lim > (size_t)maxp) lim = (size_t)maxp;
+  if (bytes > (size_t)maxw) bytes = (size_t)maxw;
+  if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, lim) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaStreamAttrValue v = {};
+  v.accessPolicyWindow.base_ptr = base;
+  v.accessPolicyWindow.num_bytes = bytes;
+  v.accessPolicyWindow.hitRatio = lim >= bytes ? 1.0f : (float)((double)lim / (double)bytes);
+  v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+  v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+  if (cudaStreamSetAttribute(c->cap_stream, cudaStreamAttributeAccessPolicyWindow, &v) == cudaSuccess)
+    c->l2_window = true;
+  else
+    cudaGetLastError();
+}
+
 hdgmg_status build_loop_graph(hdgmg_ctx* c, void (*body)(hdgmg_ctx*, cudaGraphConditionalHandle),
                               cudaGraph_t* graph_out, cudaGraphExec_t* exec_out,
                               long long* body_launches) {
   if (*exec_out) return HDGMG_OK;
-  if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  if (!c->cap_stream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    set_l2_window(c);
+  }
   cudaGraph_t g = nullptr;
   CUDA_TRY(cudaGraphCreate(&g, 0));
   *graph_out = g;
@@ -1053,6 +1102,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->gmres_restart = 30;
   o->smoother = HDGMG_SMOOTH_BLOCK_JACOBI;
   o->condensation = HDGMG_CONDENSE_AUTO;
+  o->l2_persist_mb = 64;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1060,6 +1110,7 @@ const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
 void hdgmg_destroy(hdgmg_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->l2_window) cudaCtxResetPersistingL2Cache();   // demote this run's persisting lines
   for (void* p : c->allocs) cudaFree(p);
   if (c->err_h) cudaFreeHost(c->err_h);
   if (c->scal_h) cudaFreeHost(c->scal_h);
@@ -1116,6 +1167,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.smoother < 0 || o.smoother > 3) return fail(HDGMG_EINVAL, "unknown smoother");
   if (o.condensation < HDGMG_CONDENSE_AUTO || o.condensation > HDGMG_CONDENSE_FACTOR)
     return fail(HDGMG_EINVAL, "unknown condensation");
+  if (o.l2_persist_mb < 0) return fail(HDGMG_EINVAL, "l2_persist_mb must be >= 0");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)

@@ -102,6 +102,14 @@ hdgmg_status hdgmg_batch_create(hdgmg_batch** out, int32_t nprob, const hdgmg_pr
   if (!out) return bfail(HDGMG_EINVAL, "batch pointer is NULL");
   *out = nullptr;
   if (nprob < 1 || !problems) return bfail(HDGMG_EINVAL, "need nprob >= 1 problems");
+  // the contexts of a batch run concurrently: one L2 set-aside cannot hold all
+  // of their operators, so none of them asks for persisting lines
+  hdgmg_opts bo;
+  if (opts)
+    bo = *opts;
+  else
+    hdgmg_default_opts(&bo);
+  bo.l2_persist_mb = 0;
   hdgmg_batch* b = new hdgmg_batch();
   b->user = (cudaStream_t)stream;
   cudaGetDevice(&b->device);
@@ -121,7 +129,7 @@ hdgmg_status hdgmg_batch_create(hdgmg_batch** out, int32_t nprob, const hdgmg_pr
     b->streams.push_back(s);
     b->done.push_back(e);
     hdgmg_ctx* c = nullptr;
-    hdgmg_status st = hdgmg_create(&c, &problems[i], opts, s);
+    hdgmg_status st = hdgmg_create(&c, &problems[i], &bo, s);
     if (st != HDGMG_OK) {
       std::string m = "problem " + std::to_string(i) + ": " + hdgmg_last_error();
       hdgmg_batch_destroy(b);

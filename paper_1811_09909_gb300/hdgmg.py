@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("smoother", ctypes.c_int32),
-                ("condensation", ctypes.c_int32)]
+                ("condensation", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -48,7 +48,7 @@ def test_default_options(lib):
     assert o.precision == hdgmg.PREC_FP64 and o.inner_rtol == 1e-5
     assert o.cluster_tail_n == 0 and o.gmres_restart == 30
     assert o.smoother == hdgmg.SMOOTH_BLOCK_JACOBI
-    assert o.condensation == hdgmg.CONDENSE_AUTO
+    assert o.condensation == hdgmg.CONDENSE_AUTO and o.l2_persist_mb == 64
 
 
 @pytest.mark.parametrize("kw,msg", [
