@@ -124,9 +124,12 @@ class ElementForms:
     """Reference bilinear forms of one element (size hx x hy), split by how
     they depend on kappa^-1 and tau so that L = L0 + kappa^-1 LM + tau Lt."""
 
-    def __init__(self, p, hx, hy, nq=None):
+    def __init__(self, p, hx, hy, nq=None, quad=None):
+        """quad: an element with the RefQuad table interface (volume_tables,
+        edge_tables) in place of the hx x hy rectangle, e.g. a mapped
+        quadrilateral; the primal (IPDG-H) pieces are then not formed."""
         self.p = p
-        rq = refelem.RefQuad(p, hx, hy, nq)
+        rq = refelem.RefQuad(p, hx, hy, nq) if quad is None else quad
         self.rq = rq
         nv = rq.nv
         nt = 4 * (p + 1)
@@ -169,15 +172,16 @@ class ElementForms:
         # boundary terms N[a, b] = <phi_b, grad phi_a.n> and
         # Hn[a, k] = <psi_k, grad phi_a.n>
         self.Kst = (dphidx * wJ) @ dphidx.T + (dphidy * wJ) @ dphidy.T
-        self.Nn = np.zeros((nv, nv))
-        self.Hn = np.zeros((nv, nt))
-        for edge in range(4):
-            ph, psi, wds, _ = rq.edge_tables(edge)
-            dn = rq.edge_normal_derivative(edge)
-            sl = slice(edge * (p + 1), (edge + 1) * (p + 1))
-            self.Nn += (dn * wds) @ ph.T
-            self.Hn[:, sl] += (dn * wds) @ psi.T
-        self.Gx, self.Gy = rq.nodal_gradient()
+        if quad is None:
+            self.Nn = np.zeros((nv, nv))
+            self.Hn = np.zeros((nv, nt))
+            for edge in range(4):
+                ph, psi, wds, _ = rq.edge_tables(edge)
+                dn = rq.edge_normal_derivative(edge)
+                sl = slice(edge * (p + 1), (edge + 1) * (p + 1))
+                self.Nn += (dn * wds) @ ph.T
+                self.Hn[:, sl] += (dn * wds) @ psi.T
+            self.Gx, self.Gy = rq.nodal_gradient()
         Z = np.zeros((nv, nv))
         # rows: [HDG_local1 x-test, HDG_local1 y-test, HDG_local2]
         self.LM = np.block([[Mv, Z, Z], [Z, Mv, Z], [Z, Z, Z]])

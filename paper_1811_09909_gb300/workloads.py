@@ -256,3 +256,80 @@ def batched(nprob=64, nrhs=16, seed=4, sizes=(32, 64, 128, 256), orders=(2, 4, 8
         out.append(Workload(f"batch{k}_{n}_p{p}", n, p, logk, f,
                             np.zeros((nrhs, p + 1, n_edges(n))), "over_h", 1.0, seed=seed))
     return out
+
+
+# --------------------------------------------------------------------------
+# unstructured quadrilateral meshes
+# --------------------------------------------------------------------------
+def umesh(nx, ny, lx=1.0, ly=1.0, jitter=0.2, holes=(), seed=0):
+    """Seeded unstructured all-quadrilateral mesh of [0, lx] x [0, ly].
+
+    An nx x ny grid whose interior vertices are moved by up to
+    ``jitter`` x the cell size in each direction; every cell is cut into two
+    triangles along a randomly chosen diagonal; triangles whose centroid lies
+    in one of the ``holes`` (disks (cx, cy, r)) are removed; every remaining
+    triangle is split into three quadrilaterals through its edge midpoints and
+    centroid.  The result is conforming, with vertices of valence 3 to 8.
+    Returns verts [n_vert, 2] float64 and quads [E, 4] int32, each element
+    counter-clockwise."""
+    rng = np.random.default_rng(seed)
+    hx, hy = lx / nx, ly / ny
+    gx, gy = np.meshgrid(np.linspace(0.0, lx, nx + 1), np.linspace(0.0, ly, ny + 1))
+    P = np.stack([gx.ravel(), gy.ravel()], axis=1)
+    d = rng.uniform(-jitter, jitter, size=P.shape) * np.array([hx, hy])
+    inner = ((P[:, 0] > 0) & (P[:, 0] < lx) & (P[:, 1] > 0) & (P[:, 1] < ly))
+    P[inner] += d[inner]
+    diag = rng.integers(0, 2, size=(ny, nx))
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            v00 = j * (nx + 1) + i
+            v10, v01, v11 = v00 + 1, v00 + nx + 1, v00 + nx + 2
+            if diag[j, i]:
+                tris += [(v00, v10, v11), (v00, v11, v01)]
+            else:
+                tris += [(v00, v10, v01), (v10, v11, v01)]
+    keep = []
+    for t in tris:
+        c = P[list(t)].mean(axis=0)
+        if all((c[0] - hx0) ** 2 + (c[1] - hy0) ** 2 >= r * r for hx0, hy0, r in holes):
+            keep.append(t)
+    verts = [tuple(p) for p in P]
+    mid = {}
+
+    def midpoint(a, b):
+        k = (min(a, b), max(a, b))
+        if k not in mid:
+            mid[k] = len(verts)
+            verts.append(tuple(0.5 * (P[a] + P[b])))
+        return mid[k]
+
+    quads = []
+    for a, b, c in keep:
+        mab, mbc, mca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+        g = len(verts)
+        verts.append(tuple(P[[a, b, c]].mean(axis=0)))
+        quads += [(a, mab, g, mca), (b, mbc, g, mab), (c, mca, g, mbc)]
+    verts = np.array(verts, dtype=np.float64)
+    quads = np.array(quads, dtype=np.int64)
+    used = np.unique(quads)
+    remap = -np.ones(len(verts), dtype=np.int64)
+    remap[used] = np.arange(len(used))
+    return verts[used], remap[quads].astype(np.int32)
+
+
+EXAMPLE2_HOLES = tuple((0.25 + 0.5 * i, 0.25 + 0.5 * j, 0.1) for j in range(2) for i in range(4))
+EXAMPLE2_SEEDS_7 = ((0.2, 0.3), (0.5, 0.75), (0.75, 0.25), (1.0, 0.6), (1.3, 0.3),
+                    (1.5, 0.75), (1.8, 0.4))
+EXAMPLE2_SEEDS_4 = ((0.3, 0.5), (0.8, 0.3), (1.25, 0.7), (1.7, 0.45))
+
+
+def example2(n, p, seeds=7, seed=0):
+    """Stand-in for Example II (Sec. 4.2): a 2 x 1 box with eight circular
+    holes meshed by ``umesh`` (2n x n cells, about 12 n^2 quadrilaterals),
+    kappa = 1, f = 1, zero Dirichlet data, 7 or 4 seed points spread over the
+    box.  Returns (verts, quads, seeds, log_kappa [E], f [E][(p+1)^2])."""
+    verts, quads = umesh(2 * n, n, 2.0, 1.0, 0.2, EXAMPLE2_HOLES, seed)
+    sp = np.array(EXAMPLE2_SEEDS_7 if seeds == 7 else EXAMPLE2_SEEDS_4, dtype=np.float64)
+    E = len(quads)
+    return verts, quads, sp, np.zeros(E), np.ones((E, (p + 1) ** 2))

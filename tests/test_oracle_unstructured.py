@@ -1,0 +1,309 @@
+"""Pins of the unstructured-mesh oracle (oracle/unstructured.py) against the
+structured oracle it must reduce to, closed forms and exact properties."""
+import numpy as np
+import pytest
+
+from oracle import hdg, mg, unstructured as U
+from paper_1811_09909_gb300 import workloads as W
+
+
+def _grid(n):
+    """Uniform n x n mesh of the unit square as an unstructured mesh: vertex
+    j*(n+1)+i at (i/n, j/n), element (i, j) counter-clockwise from (i, j)."""
+    xs = np.arange(n + 1) / n
+    verts = np.array([(x, y) for y in xs for x in xs])
+    quads = []
+    for j in range(n):
+        for i in range(n):
+            v = j * (n + 1) + i
+            quads.append((v, v + 1, v + n + 2, v + n + 1))
+    return verts, np.array(quads)
+
+
+def _structured_edge_of(n, a, b):
+    """Structured edge number of the axis-aligned segment a -> b."""
+    (xa, ya), (xb, yb) = a, b
+    if abs(xa - xb) < 1e-12:                        # vertical, at x = xa
+        i = int(round(xa * n))
+        j = int(round(min(ya, yb) * n))
+        return j * (n + 1) + i
+    j = int(round(ya * n))
+    i = int(round(min(xa, xb) * n))
+    return n * (n + 1) + j * n + i
+
+
+def test_square_element_equals_structured_element():
+    """An axis-aligned square numbered so that every edge runs along +x / +y
+    gives hdg.ElementForms' element up to the local edge order."""
+    p = 3
+    verts = np.array([[0, 0], [0.5, 0], [0, 0.5], [0.5, 0.5]], float)
+    pr = U.UHDGProblem(verts, np.array([[0, 1, 3, 2]]), p, 2.0, 3.0)
+    A = pr.element_operator(0)
+    fr = hdg.ElementForms(p, 0.5, 0.5)
+    L, R, C = fr.local(2.0, 3.0)
+    As = C @ np.linalg.solve(L, R) + 3.0 * fr.El
+    nd = p + 1
+    # structured local edges left, right, bottom, top = unstructured 3, 1, 0, 2
+    perm = np.concatenate([np.arange(nd) + nd * u for u in (3, 1, 0, 2)])
+    assert np.abs(A[np.ix_(perm, perm)] - As).max() < 1e-12 * np.abs(As).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_linear_patch_test_on_jittered_mesh(p):
+    """Linear u is in the mapped Q_p space and q = -grad u constant: HDG
+    reproduces both to round-off on a bilinear (non-affine) mesh."""
+    v, q = W.umesh(5, 4, 1.0, 1.0, 0.25, (), 3)
+    pr = U.UHDGProblem(v, q, p, 1.7, 1.0)
+    uex = lambda x, y: 1 + 2 * x - 3 * y
+    f = np.zeros((pr.E, pr.nv))
+    lam = pr.solve_direct(f, uex)
+    u, qq = pr.recover(lam, f)
+    X = pr.node_coords()
+    assert np.abs(u - uex(X[..., 0], X[..., 1])).max() < 1e-11
+    assert np.abs(qq[:, 0] + 1.7 * 2).max() < 1e-9
+    assert np.abs(qq[:, 1] - 1.7 * 3).max() < 1e-9
+
+
+def _refine(verts, quads):
+    """Each quad into four through its edge midpoints and vertex average (the
+    children are the images of the reference quarters under the parent map)."""
+    verts = [tuple(x) for x in verts]
+    mid = {}
+
+    def m(a, b):
+        k = (min(a, b), max(a, b))
+        if k not in mid:
+            mid[k] = len(verts)
+            verts.append(tuple(0.5 * (np.array(verts[a]) + np.array(verts[b]))))
+        return mid[k]
+
+    out = []
+    for v0, v1, v2, v3 in quads:
+        c = len(verts)
+        verts.append(tuple(np.mean([verts[v0], verts[v1], verts[v2], verts[v3]], axis=0)))
+        m01, m12, m23, m30 = m(v0, v1), m(v1, v2), m(v2, v3), m(v3, v0)
+        out += [(v0, m01, c, m30), (m01, v1, m12, c), (c, m12, v2, m23), (m30, c, m23, v3)]
+    return np.array(verts), np.array(out)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_convergence_rate_on_refined_unstructured_meshes(p):
+    """u = sin(pi x) sin(pi y): ||u - u_h|| = O(h^{p+1}) (Sec. 2: HDG's
+    optimal order) under uniform refinement of a jittered mesh."""
+    v, q = W.umesh(2, 2, 1.0, 1.0, 0.2, (), 5)
+    errs = []
+    for _ in range(2):
+        v, q = _refine(v, q)
+        pr = U.UHDGProblem(v, q, p, 1.0, 1.0)
+        X = pr.node_coords()
+        f = 2 * np.pi ** 2 * W.sine_u(X[..., 0], X[..., 1])
+        lam = pr.solve_direct(f)
+        u, _ = pr.recover(lam, f)
+        errs.append(pr.l2_error(u, W.sine_u))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > p + 1 - 0.35, (errs, rate)
+
+
+def test_quadrature_is_exact_on_bilinear_elements():
+    """Every HDG form on a bilinear map is a polynomial of degree <= 2p+1 per
+    direction: p+1, p+3 and p+6 point rules give the same element."""
+    v, q = W.umesh(2, 2, 1.0, 1.0, 0.25, (), 7)
+    p = 3
+    ops = [U.UHDGProblem(v, q, p, 1.3, 2.0, nq=nq).element_operator(5) for nq in (p + 1, p + 3, p + 6)]
+    assert np.abs(ops[0] - ops[1]).max() < 1e-12 * np.abs(ops[1]).max()
+    assert np.abs(ops[2] - ops[1]).max() < 1e-12 * np.abs(ops[1]).max()
+
+
+def test_element_operator_annihilates_constants_and_is_spsd():
+    v, q = W.umesh(3, 3, 1.0, 1.0, 0.25, (), 2)
+    p = 2
+    pr = U.UHDGProblem(v, q, p, 0.7, 1.5)
+    for e in (0, 7, 20):
+        A = pr.element_operator(e)
+        c = np.zeros(pr.nt)
+        for j in range(4):
+            a, b = pr.verts[pr.quads[e][j]], pr.verts[pr.quads[e][(j + 1) % 4]]
+            c[j * (p + 1)] = np.sqrt(np.hypot(*(b - a)))    # <1, psi_0> = sqrt(|e|)
+        assert np.abs(A @ c).max() < 1e-12 * np.abs(A).max()
+        assert np.abs(A - A.T).max() < 1e-12 * np.abs(A).max()
+        assert np.linalg.eigvalsh(A).min() > -1e-12 * np.abs(A).max()
+
+
+def _match(n, pr, hier_u, hier_s, t_level, n_level):
+    """Permutation of the unstructured level's dofs onto the structured one's
+    (macro-edges matched by their end points)."""
+    chains = hier_u.chain_levels[t_level]["units"]
+    L = hier_u.levels[-(len(hier_u.chain_levels) - t_level)]
+    Ls = hier_s.levels[-(len(hier_u.chain_levels) - t_level)]
+    pos_s = {d: i for i, d in enumerate(Ls.free)}
+    perm = np.zeros(L.A.shape[0], dtype=np.int64)
+    for col, ci in enumerate(L.keep):
+        ch = chains[ci]
+        a, b = pr.verts[ch.start], pr.verts[ch.end]
+        se = _structured_edge_of(n_level, a, b)
+        for k in range(2):
+            perm[2 * col + k] = pos_s[se * 2 + k]
+    return L, Ls, perm
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_uniform_grid_reduces_to_structured_hierarchy(p):
+    """On a uniform 8 x 8 grid with the four seeds at the centres of its 4 x 4
+    blocks, the seed partition is the 2 x 2 block partition and the two
+    bisections give the 2 x 2 agglomeration of Sec. 3.1.2: every level's
+    operator and the V-cycle equal oracle.mg's structured ones up to the
+    numbering of the macro-edges."""
+    n = 8
+    verts, quads = _grid(n)
+    kappa = np.exp(np.random.default_rng(3).normal(0, 1, n * n))
+    pr = U.UHDGProblem(verts, quads, p, kappa, 1.0)
+    seeds = np.array([[0.25, 0.25], [0.75, 0.25], [0.25, 0.75], [0.75, 0.75]])
+    hu = U.UHierarchy(pr, seeds, local_corr="both")
+    ps = hdg.HDGProblem(n, p, kappa, 1.0)
+    hs = mg.Hierarchy(ps, coarsest_n=2, local_corr="both")
+    assert [L.A.shape[0] for L in hu.levels] == [L.A.shape[0] for L in hs.levels]
+    # P_0 is the 2 x 2 block partition, P_1 the 2 x 2 agglomerates of 4 x 4
+    c = U.centroids(verts, quads)
+    blk0 = (c[:, 0] > 0.5).astype(int) + 2 * (c[:, 1] > 0.5)
+    assert len(hu.parts) == 2
+    assert np.array_equal(hu.parts[0], blk0)
+    blk1 = np.floor(c[:, 0] * 4) + 4 * np.floor(c[:, 1] * 4)
+    _, inv = np.unique(hu.parts[1], return_inverse=True)
+    _, inv_s = np.unique(blk1, return_inverse=True)
+    pairs = set(zip(inv.tolist(), inv_s.tolist()))
+    assert len(pairs) == 16                           # one-to-one
+    # fine level(s): mesh edges matched to the structured numbering
+    free_u = pr.free_dofs()
+    nd = p + 1
+    pos_s = {d: i for i, d in enumerate(ps.free_dofs())}
+    perm = np.array([pos_s[_structured_edge_of(n, verts[pr.edge_vertices[d // nd][0]],
+                                               verts[pr.edge_vertices[d // nd][1]]) * nd + d % nd]
+                     for d in free_u])
+    A_s = hs.levels[0].A.toarray()
+    A_u = hu.levels[0].A.toarray()
+    assert np.abs(A_u - A_s[np.ix_(perm, perm)]).max() < 1e-11 * np.abs(A_s).max()
+    # h-levels
+    for t, nl in ((1, 4), (2, 2)):
+        L, Ls, pm = _match(n, pr, hu, hs, t, nl)
+        As = Ls.A.toarray()
+        assert np.abs(L.A.toarray() - As[np.ix_(pm, pm)]).max() < 1e-11 * np.abs(As).max()
+    # one V-cycle on a random residual
+    r_s = np.random.default_rng(1).normal(size=A_s.shape[0])
+    z_s = hs.vcycle(r_s)
+    z_u = hu.vcycle(r_s[perm])
+    assert np.abs(z_u - z_s[perm]).max() < 1e-10 * np.abs(z_s).max()
+
+
+def _closed_form_J(chains, units_fine, keep_f, keep_c, nfree):
+    """J (all fine dofs -> coarse dofs) from the closed form of the P_1
+    arc-length basis restricted to a unit of length l at offset s0:
+    coefficients sqrt(l)(a + b/2) and sqrt(3 l) b / 6 of a + b tau."""
+    fpos = {u: i for i, u in enumerate(keep_f)}
+    J = np.zeros((nfree, 2 * len(keep_c)))
+    for col, ci in enumerate(keep_c):
+        ch = chains[ci]
+        Lg = ch.length
+        s0 = 0.0
+        for u, d in zip(ch.units, ch.dirs):
+            l = units_fine[u].length
+            if u in fpos:
+                r = fpos[u]
+                c3 = np.sqrt(3 / Lg)
+                if d == 1:
+                    coef = [(1 / np.sqrt(Lg), 0.0), (c3 * (2 * s0 / Lg - 1), c3 * 2 * l / Lg)]
+                else:
+                    coef = [(1 / np.sqrt(Lg), 0.0), (c3 * (2 * (s0 + l) / Lg - 1), -c3 * 2 * l / Lg)]
+                for k, (a, b) in enumerate(coef):
+                    J[2 * r, 2 * col + k] = np.sqrt(l) * (a + b / 2)
+                    J[2 * r + 1, 2 * col + k] = np.sqrt(3 * l) * b / 6
+            s0 += l
+    return J
+
+
+def test_coarse_operators_are_schur_complements_on_holey_mesh():
+    """Eq. Akm1 / Proposition DtN on every h-level of the Example II stand-in
+    (curved, multi-unit macro-edges, cycles around the holes):
+    A_{k-1} = J^T (A_BB - A_BI A_II^-1 A_IB) J with a dense solve, J from the
+    closed form and I/B from the partitions directly."""
+    verts, quads, seeds, _, _ = W.example2(6, 1)
+    pr = U.UHDGProblem(verts, quads, 1, 1.0, 1.0)
+    hu = U.UHierarchy(pr, seeds)
+    assert hu.nested_residual < 1e-13
+    assert any(ch.closed for lev in hu.chain_levels for ch in lev["units"])
+    parts = [np.arange(pr.E)] + hu.parts[::-1]          # finest first
+    for t in range(1, len(hu.chain_levels)):
+        L, Lc = hu.levels[t - 1], hu.levels[t]
+        units_f = hu.chain_levels[t - 1]["units"]
+        # unit interior to a coarse macro-element: its two sides' elements
+        # lie in one macro of the coarse partition
+        fine_part, coarse_part = parts[t - 1], parts[t]
+        rep = {}
+        for e in range(pr.E):
+            rep.setdefault(fine_part[e], e)
+        inner = [coarse_part[rep[units_f[u].sides[0]]] == coarse_part[rep[units_f[u].sides[1]]]
+                 for u in L.keep]
+        Iset = np.array([2 * i + k for i, x in enumerate(inner) if x for k in range(2)])
+        Bset = np.array([2 * i + k for i, x in enumerate(inner) if not x for k in range(2)])
+        J = _closed_form_J(hu.chain_levels[t]["units"], units_f, L.keep, Lc.keep, L.A.shape[0])
+        A = L.A.toarray()
+        S = A[np.ix_(Bset, Bset)] - A[np.ix_(Bset, Iset)] @ np.linalg.solve(
+            A[np.ix_(Iset, Iset)], A[np.ix_(Iset, Bset)])
+        ref = J[Bset].T @ S @ J[Bset]
+        assert np.abs(J[Iset]).max() == 0.0
+        assert np.abs(Lc.A.toarray() - ref).max() < 1e-10 * np.abs(ref).max(), t
+
+
+def test_partitions_and_macro_edges_are_consistent():
+    verts, quads, seeds, _, _ = W.example2(4, 1)
+    E = len(quads)
+    c = U.centroids(verts, quads)
+    parts = U.partitions(verts, quads, seeds)
+    # P_0: brute-force nearest seed
+    d = ((c[:, None, :] - seeds[None]) ** 2).sum(-1)
+    assert np.array_equal(np.unique(np.argmin(d, 1), return_inverse=True)[1], parts[0])
+    for r in range(1, len(parts)):
+        # nested, at most four parts per parent, balanced sizes
+        for m in np.unique(parts[r - 1]):
+            kids = np.unique(parts[r][parts[r - 1] == m])
+            sizes = [np.sum(parts[r] == k) for k in kids]
+            assert 1 <= len(kids) <= 4 and max(sizes) - min(sizes) <= 1
+        assert 2 * (parts[r].max() + 1) <= E
+    ev, _, ee = U.mesh_edges(quads)
+    _, levels = U.hierarchy_chains(verts, quads, seeds)
+    allparts = [np.arange(E)] + parts[::-1]
+    for t, lev in enumerate(levels):
+        part = allparts[t]
+        covered = np.zeros(len(ev), dtype=int)
+        for ch in lev["units"]:
+            # consecutive mesh edges share the traversal vertex
+            cur = ch.start
+            for m, dd in zip(ch.edges, ch.edirs):
+                a, b = ev[m] if dd == 1 else ev[m][::-1]
+                assert a == cur
+                cur = b
+                covered[m] += 1
+                s = sorted(part[x] if x >= 0 else -1 for x in ee[m])
+                assert tuple(sorted(ch.sides, key=lambda z: (z < 0, z))) == \
+                    tuple(sorted(s, key=lambda z: (z < 0, z)))
+            assert cur == ch.end and (ch.closed == (ch.start == ch.end) or len(ch.units) == 1)
+            assert abs(ch.length - sum(np.hypot(*(verts[ev[m][1]] - verts[ev[m][0]]))
+                                       for m in ch.edges)) < 1e-12
+        skel = np.array([ee[m][1] < 0 or part[ee[m][0]] != part[ee[m][1]] for m in range(len(ev))])
+        assert np.array_equal(covered, skel.astype(int))
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_multigrid_converges_on_example2(p):
+    """Example II stand-in (kappa = 1, f = 1, zero Dirichlet data, tau = 1):
+    the V-cycle contracts and MG-preconditioned CG converges in a bounded
+    number of iterations (the paper's Table tab:HDG has 10-13 for GMRES on its
+    simplex mesh; this quadrilateral stand-in takes 15-25)."""
+    verts, quads, seeds, _, f = W.example2(5, p)
+    pr = U.UHDGProblem(verts, quads, p, 1.0, 1.0)
+    Ae, ge = pr.condense(f)
+    b = pr.assemble_rhs(ge)[pr.free_dofs()]
+    hu = U.UHierarchy(pr, seeds, Ae=Ae, local_corr="both", omega=0.8 if p == 1 else 1.0)
+    x, it, hist, ok = hu.solve_pcg(b, tol=1e-10)
+    assert ok and it <= 30, it
+    x_direct = pr.solve_direct(f)[pr.free_dofs()]
+    assert np.abs(x - x_direct).max() < 1e-8 * np.abs(x_direct).max()
