@@ -12,7 +12,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhdgmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["refelem.cpp", "eigbasis.cpp", "k_condense.cu", "k_mg.cu", "k_ctail.cu", "k_krylov.cu", "hdgmg_api.cu",
-           "hdgmg_batch.cpp"]
+           "hdgmg_batch.cpp", "umesh_plan.cpp", "umesh.cu"]
+# the unstructured plan takes integer decisions from fp64 comparisons: no
+# floating-point contraction, so that every host decides alike
+FILE_FLAGS = {"umesh_plan.cpp": ["-Xcompiler", "-ffp-contract=off"]}
 # k_edge_inst.cu is built once per (real type, trace modes per edge), plus
 # once per ND for the BF16-storage matvec
 EDGE_UNITS = [(t, nd) for nd in range(2, 10) for t in ("double", "float", "bf16")]
@@ -40,6 +43,7 @@ def _compile(unit, extra):
     else:
         src = unit
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+        extra = [*FILE_FLAGS.get(src, []), *extra]
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-O3", "-I", os.path.join(HERE, "..", "include"), *extra,
            "-c", os.path.join(CSRC, src), "-o", obj]

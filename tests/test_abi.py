@@ -11,8 +11,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "hdgmg.h")
 
 
-def _declared():
-    txt = open(HEADER).read()
+def _declared(header=HEADER):
+    txt = open(header).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(hdgmg_[a-z_]+)\s*\(", txt)))
 
@@ -37,6 +37,14 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
     from paper_1811_09909_gb300 import hdgmg
     assert sorted(hdgmg.EXPORTED) == sorted(n for n in _declared())
+
+
+def test_library_exports_every_unstructured_symbol(lib):
+    from paper_1811_09909_gb300 import umesh
+    names = _declared(os.path.join(ROOT, "include", "hdgmg_umesh.h"))
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(umesh.EXPORTED) == names
 
 
 def test_default_options(lib):

@@ -1,0 +1,142 @@
+"""GPU parity of the unstructured-mesh path (hdgmg_umesh_*) against the
+oracle (oracle/unstructured.py): element operators, every coarse level, the
+V-cycle, PCG and fixed-point iteration counts, the solution and its
+recovery, at sizes spanning several macro-elements and ragged ones (holes,
+cycles, single-element macro-elements)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import unstructured as U
+from paper_1811_09909_gb300 import hdgmg, umesh as um, workloads as W
+
+TOL = 1e-10          # FP64, different summation orders: relative to the operator's scale
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _setup(n, p, seeds=7, kappa_sigma=0.0, **opts):
+    v, q, sp, logk, f = W.example2(n, p, seeds=seeds)
+    if kappa_sigma:
+        logk = np.random.default_rng(11).normal(0, kappa_sigma, len(q))
+    s = um.USolver(v, q, p, 1.0, sp, **opts)
+    s.setup(_dev(logk))
+    pr = U.UHDGProblem(v, q, p, np.exp(logk), 1.0)
+    return s, pr, sp, f
+
+
+def _dense(s, level):
+    A, dofs = s.element_matrices(level)
+    A = A.cpu().numpy()
+    n = s.level_sizes(level)[0]
+    M = np.zeros((n, n))
+    for e in range(A.shape[0]):
+        d = dofs[e]
+        ok = d >= 0
+        M[np.ix_(d[ok], d[ok])] += A[e][np.ix_(ok, ok)]
+    return M
+
+
+@pytest.mark.parametrize("p", [1, 2, 4])
+def test_element_operators_and_levels_match_oracle(p):
+    s, pr, sp, _ = _setup(4, p, kappa_sigma=1.0)
+    Ae, _ = pr.condense()
+    A, dofs = s.element_matrices(0)
+    A = A.cpu().numpy()
+    scale = np.abs(Ae).max()
+    assert np.abs(A - Ae).max() < TOL * scale
+    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="both")
+    assert s.n_levels == len(hu.levels)
+    for k, L in enumerate(hu.levels):
+        M = _dense(s, k)
+        ref = L.A.toarray()
+        assert M.shape == ref.shape, k
+        assert np.abs(M - ref).max() < TOL * np.abs(ref).max(), k
+
+
+@pytest.mark.parametrize("p,lc", [(2, "both"), (3, "pre"), (1, "both")])
+def test_vcycle_matches_oracle(p, lc):
+    om = 0.8 if p == 1 else 1.0
+    s, pr, sp, _ = _setup(4, p, kappa_sigma=0.5, omega=om, local_corr=hdgmg.LC_BOTH if lc == "both" else hdgmg.LC_PRE,
+                          m_fine=1, m_growth=2, m_max=4)
+    hu = U.UHierarchy(pr, sp, local_corr=lc, omega=om, m_fine=1, m_growth=2, m_max=4)
+    r = np.random.default_rng(5).normal(size=hu.levels[0].A.shape[0])
+    z = s.vcycle(_dev(r)).cpu().numpy()
+    zo = hu.vcycle(r)
+    assert np.abs(z - zo).max() < 1e-9 * np.abs(zo).max()
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_pcg_solve_and_recovery_match_oracle(p):
+    om = 0.8 if p == 1 else 1.0
+    s, pr, sp, f = _setup(5, p, kappa_sigma=1.0, omega=om, rtol=1e-11)
+    lam, u, q, info = s.solve(_dev(f))
+    assert info.converged and info.rel_res <= 1e-11
+    lam_o = pr.solve_direct(f)
+    lam = lam.cpu().numpy().ravel()
+    assert np.abs(lam - lam_o).max() < 1e-8 * np.abs(lam_o).max()
+    u_o, q_o = pr.recover(lam_o, f)
+    assert np.abs(u.cpu().numpy() - u_o).max() < 1e-8 * np.abs(u_o).max()
+    assert np.abs(q.cpu().numpy() - q_o).max() < 1e-7 * np.abs(q_o).max()
+    Ae, ge = pr.condense(f)
+    b = pr.assemble_rhs(ge)[pr.free_dofs()]
+    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="both", omega=om)
+    _, it, _, ok = hu.solve_pcg(b, tol=1e-11)
+    assert ok and abs(info.iters - it) <= 1, (info.iters, it)
+
+
+def test_fixed_point_iterations_match_oracle():
+    s, pr, sp, f = _setup(4, 2, krylov=hdgmg.KRYLOV_NONE, local_corr=hdgmg.LC_PRE, rtol=1e-9)
+    lam, _, _, info = s.solve(_dev(f), want_u=False, want_q=False)
+    Ae, ge = pr.condense(f)
+    b = pr.assemble_rhs(ge)[pr.free_dofs()]
+    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="pre")
+    _, it, _, ok = hu.solve_fixed_point(b, tol=1e-9)
+    assert ok and info.converged and abs(info.iters - it) <= 1, (info.iters, it)
+
+
+def test_four_seed_strategy_and_single_seed():
+    for seeds in (4,):
+        s, pr, sp, f = _setup(4, 2, seeds=seeds)
+        lam, _, _, info = s.solve(_dev(f), want_u=False, want_q=False)
+        assert info.converged
+        assert np.abs(lam.cpu().numpy().ravel() - pr.solve_direct(f)).max() < 1e-8
+    v, q = W.umesh(3, 3, 1.0, 1.0, 0.2, (), 2)
+    s = um.USolver(v, q, 2, 1.0, np.array([[0.5, 0.5]]))
+    s.setup(_dev(np.zeros(len(q))))
+    f = np.ones((len(q), 9))
+    lam, _, _, info = s.solve(_dev(f))
+    pr = U.UHDGProblem(v, q, 2, 1.0, 1.0)
+    assert info.converged
+    assert np.abs(lam.cpu().numpy().ravel() - pr.solve_direct(f)).max() < 1e-8
+
+
+def test_large_mesh_sampled_elements_and_convergence():
+    """About 27k elements (n = 48): sampled element operators against the
+    oracle one by one, and PCG convergence with the true residual."""
+    v, q, sp, _, f = W.example2(48, 3)
+    logk = np.random.default_rng(2).normal(0, 1.0, len(q))
+    s = um.USolver(v, q, 3, 1.0, sp, rtol=1e-10)
+    s.setup(_dev(logk))
+    pr = U.UHDGProblem(v, q, 3, np.exp(logk), 1.0)
+    A = s.element_matrices(0)[0]
+    for e in np.random.default_rng(0).choice(len(q), 12, replace=False):
+        Ao = pr.element_operator(int(e))
+        assert np.abs(A[int(e)].cpu().numpy() - Ao).max() < TOL * np.abs(Ao).max()
+    lam, u, qq, info = s.solve(_dev(f))
+    assert info.converged and info.rel_res <= 1e-10 and info.iters <= 40
+    assert torch.isfinite(u).all() and torch.isfinite(qq).all()
+
+
+def test_breakdown_on_nan_kappa():
+    v, q, sp, logk, f = W.example2(3, 2)
+    s = um.USolver(v, q, 2, 1.0, sp)
+    logk = logk.copy()
+    logk[5] = np.nan
+    with pytest.raises(hdgmg.HdgmgError) as ei:
+        s.setup(_dev(logk))
+    assert ei.value.status == -5
