@@ -875,6 +875,7 @@ void launch_recover_p(hdgmg_umesh* c, const double* lam, const double* f, double
 
 void level_matvec(hdgmg_umesh* c, int k, const double* x, double* y, int mode, const double* r) {
   ULevelDev& L = c->L[k];
+  if (L.n_blk == 0) return;
   note_launch();
   u_elem_matvec_kernel<<<nblk((long long)L.n_el * L.ndm, 128), 128, 0, c->s>>>(L.n_el, L.nu, L.nd, L.el_slot, L.A,
                                                                               x, L.t);
@@ -888,11 +889,13 @@ void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
   ULevelDev& L = c->L[k];
   const int nl = (int)c->L.size();
   if (k == nl - 1) {
+    if (c->n_coarse == 0) return;
     note_launch();
     u_dense_matvec_kernel<<<nblk(c->n_coarse, 128), 128, 0, c->s>>>(c->n_coarse, c->cInv, r, e);
     return;
   }
   const double om = c->opts.omega;
+  if (L.n_blk == 0) return;
   // step 2: pre-smoothing from zero
   note_launch();
   u_bj_first_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.Dinv, r, om, e);
@@ -910,9 +913,11 @@ void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
   if (hlev) {
     note_launch();
     u_restrict_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, C.t);
-    note_launch();
-    u_unit_kernel<<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, C.t, nullptr, nullptr,
-                                                        0.0, U_SUM, C.r);
+    if (C.n_blk > 0) {
+      note_launch();
+      u_unit_kernel<<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, C.t, nullptr, nullptr,
+                                                          0.0, U_SUM, C.r);
+    }
   } else {
     note_launch();
     u_prestrict_kernel<<<nblk(2LL * L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.res, C.r);
@@ -1116,13 +1121,15 @@ hdgmg_status hdgmg_umesh_setup(hdgmg_umesh* c, const double* log_kappa) {
   }
   for (size_t k = 0; k + 1 < c->L.size(); ++k) {
     ULevelDev& L = c->L[k];
+    if (L.n_blk == 0) continue;
     note_launch();
     u_bjinv_kernel<<<nblk(L.n_blk, 64), 64, 0, c->s>>>(L.n_blk, L.nu, L.nd, L.blk_t0, L.blk_t1, L.A, L.Dinv,
                                                        c->err);
   }
   ULevelDev& C = c->L.back();
-  note_launch();
-  u_coarse_setup_kernel<<<1, 1024, 0, c->s>>>(c->n_coarse, C.n_el, C.nu, C.el_slot, C.A, c->cD, c->cInv, c->err);
+  if (c->n_coarse > 0) note_launch();
+  if (c->n_coarse > 0)
+    u_coarse_setup_kernel<<<1, 1024, 0, c->s>>>(c->n_coarse, C.n_el, C.nu, C.el_slot, C.A, c->cD, c->cInv, c->err);
   cudaEventRecord(c->ev1, c->s);
   hdgmg_status st = cuda_status("set-up");
   if (st != HDGMG_OK) return st;
@@ -1194,9 +1201,11 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
   cudaEventRecord(c->ev0, c->s);
   // b = sum_e g_e on the interior edges
   U_DISPATCH(c->p, launch_rhs_p, c, f, L0.t);
-  note_launch();
-  u_unit_kernel<<<nblk(L0.n_blk, 128), 128, 0, c->s>>>(L0.n_blk, L0.nd, L0.blk_t0, L0.blk_t1, L0.t, nullptr,
-                                                       nullptr, 0.0, U_SUM, c->b);
+  if (L0.n_blk > 0) {
+    note_launch();
+    u_unit_kernel<<<nblk(L0.n_blk, 128), 128, 0, c->s>>>(L0.n_blk, L0.nd, L0.blk_t0, L0.blk_t1, L0.t, nullptr,
+                                                         nullptr, 0.0, U_SUM, c->b);
+  }
   launch_dot(c->s, n, c->b, c->b, c->partial, c->scal + 6);
   const double bb = read_scalar(c, c->scal + 6);
   cudaMemsetAsync(c->x, 0, n * sizeof(double), c->s);
