@@ -121,12 +121,21 @@ hdgmg_status hdgmg_umesh_plan_macro_edges(const hdgmg_umesh_plan* plan, int32_t 
 
 typedef struct hdgmg_umesh hdgmg_umesh;
 
+/* The options hdgmg_umesh_create uses when given NULL: hdgmg_default_opts
+ * with omega = 0.8, m_fine = 2, m_max = 8.  On meshes with irregular
+ * elements the undamped edge block-Jacobi smoother is not convergent on its
+ * own (more smoothing steps make the V-cycle worse), so it is damped and
+ * applied twice on the finest level, doubling per level up to 8. */
+void hdgmg_umesh_default_opts(hdgmg_opts* opts);
+
 /* Create a context on the current device: builds the plan, uploads it and
  * allocates every buffer.  Options used: m_fine, m_growth, m_max,
- * local_corr, omega, krylov (NONE or CG; GMRES: EINVAL), max_it, rtol.
+ * local_corr, omega, krylov (NONE or CG; GMRES: EINVAL), max_it, rtol
+ * (opts NULL: hdgmg_umesh_default_opts).
  * precision must be FP64 and smoother BLOCK_JACOBI (EINVAL otherwise).
- * EINVAL also when a macro-element's local system exceeds 160 unknowns or
- * the coarsest level exceeds 4096 unknowns.  stream: a cudaStream_t (NULL =
+ * EINVAL also when a macro-element's local system exceeds 160 unknowns, a
+ * macro-element has more than 64 macro-edges, or the coarsest level exceeds
+ * 1024 unknowns.  stream: a cudaStream_t (NULL =
  * legacy default stream). */
 hdgmg_status hdgmg_umesh_create(hdgmg_umesh** ctx,
                                 const hdgmg_umesh_problem* problem,

@@ -805,8 +805,13 @@ struct hdgmg_umesh {
   double *scal = nullptr, *partial = nullptr, *hbuf = nullptr;
   int* err = nullptr;
   bool ready = false;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
   size_t condense_smem = 0, agg_smem = 0;
+  // one outer iteration (PCG or fixed point) captured as a CUDA graph on a
+  // private stream at the first solve; replayed per iteration
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g_iter[2] = {nullptr, nullptr};
+  long long g_nodes[2] = {0, 0};
 };
 
 namespace {
@@ -956,17 +961,74 @@ double read_scalar(hdgmg_umesh* c, const double* d) {
   return *c->hbuf;
 }
 
+// one PCG iteration: alpha, x, r, |r|^2 (scal[5]), z = B r, beta, p
+void pcg_body(hdgmg_umesh* c) {
+  const long long n = c->L[0].n();
+  level_matvec(c, 0, c->pd, c->Ap, U_SUM, nullptr);
+  launch_dot(c->s, n, c->pd, c->Ap, c->partial, c->scal + 1);
+  launch_cg_scalars(c->s, c->scal, 0);
+  launch_cg_update(c->s, n, c->scal, c->x, c->rr, c->pd, c->Ap);
+  launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
+  vcycle(c, 0, c->rr, c->z);
+  launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 3);
+  launch_cg_scalars(c->s, c->scal, 1);
+  launch_cg_direction(c->s, n, c->scal, c->z, c->pd);
+}
+
+// one fixed-point iteration x += B (b - A x), then |b - A x|^2 (scal[5])
+void fp_body(hdgmg_umesh* c) {
+  const long long n = c->L[0].n();
+  level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
+  vcycle(c, 0, c->rr, c->z);
+  launch_axpby(c->s, n, 1.0, c->z, 1.0, c->x);
+  level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
+  launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
+}
+
+// captures body k (0 PCG, 1 fixed point) once; false if capture failed
+bool ensure_graph(hdgmg_umesh* c, int k) {
+  if (c->g_iter[k]) return true;
+  cudaStream_t saved = c->s;
+  c->s = c->cap;
+  const long long l0 = launch_count();
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    c->s = saved;
+    return false;
+  }
+  if (k == 0) pcg_body(c);
+  else fp_body(c);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  c->s = saved;
+  c->g_nodes[k] = launch_count() - l0;
+  if (e != cudaSuccess || !g) return false;
+  const bool ok = cudaGraphInstantiate(&c->g_iter[k], g, 0) == cudaSuccess;
+  cudaGraphDestroy(g);
+  return ok;
+}
+
 }  // namespace
 
 extern "C" {
+
+void hdgmg_umesh_default_opts(hdgmg_opts* o) {
+  if (!o) return;
+  hdgmg_default_opts(o);
+  o->omega = 0.8;
+  o->m_fine = 2;
+  o->m_max = 8;
+}
 
 hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr, const hdgmg_opts* opts,
                                 void* stream) {
   if (!out || !pr) return fail_u(HDGMG_EINVAL, "null argument");
   *out = nullptr;
   hdgmg_opts o;
-  if (opts) o = *opts;
-  else hdgmg_default_opts(&o);
+  if (opts) {
+    o = *opts;
+  } else {
+    hdgmg_umesh_default_opts(&o);
+  }
   if (o.precision != HDGMG_PREC_FP64) return fail_u(HDGMG_EINVAL, "the unstructured path runs in FP64 only");
   if (o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) return fail_u(HDGMG_EINVAL, "the unstructured path smooths by block-Jacobi");
   if (o.krylov != HDGMG_KRYLOV_NONE && o.krylov != HDGMG_KRYLOV_CG)
@@ -1096,7 +1158,10 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
     attr = attr && cudaFuncSetAttribute(u_agglomerate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)c->agg_smem) == cudaSuccess;
   if (!attr) return bail(HDGMG_ECUDA, "shared-memory attribute refused");
-  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(HDGMG_ECUDA, "stream creation failed");
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+      cudaEventCreate(&c->ev2) != cudaSuccess || cudaEventCreate(&c->ev3) != cudaSuccess)
     return bail(HDGMG_ECUDA, "event creation failed");
   *out = c;
   return HDGMG_OK;
@@ -1106,7 +1171,9 @@ hdgmg_status hdgmg_umesh_setup(hdgmg_umesh* c, const double* log_kappa) {
   if (!c || !log_kappa) return fail_u(HDGMG_EINVAL, "null argument");
   cudaMemcpyAsync(c->logk, log_kappa, (size_t)c->E * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
   cudaEventRecord(c->ev0, c->s);
+  cudaEventRecord(c->ev2, c->s);
   U_DISPATCH(c->p, launch_condense_p, c);
+  cudaEventRecord(c->ev3, c->s);
   UPlan& P = c->plan;
   if (P.p > 1) {
     note_launch();
@@ -1195,8 +1262,9 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
   if (!c->ready) return fail_u(HDGMG_EINVAL, "set-up required");
   ULevelDev& L0 = c->L[0];
   const long long n = L0.n();
-  float t_setup = 0.0f;
+  float t_setup = 0.0f, t_cond = 0.0f;
   cudaEventElapsedTime(&t_setup, c->ev0, c->ev1);
+  cudaEventElapsedTime(&t_cond, c->ev2, c->ev3);
   const long long launches0 = launch_count();
   cudaEventRecord(c->ev0, c->s);
   // b = sum_e g_e on the interior edges
@@ -1213,37 +1281,31 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
   bool conv = bb == 0.0;
   double rel = 0.0;
   bool broke = false;
-  if (!conv && c->opts.krylov == HDGMG_KRYLOV_CG) {
-    cudaMemcpyAsync(c->rr, c->b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);   // r = b
-    vcycle(c, 0, c->rr, c->z);
-    cudaMemcpyAsync(c->pd, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
-    launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 0);
-    while (it < c->opts.max_it) {
-      level_matvec(c, 0, c->pd, c->Ap, U_SUM, nullptr);
-      launch_dot(c->s, n, c->pd, c->Ap, c->partial, c->scal + 1);
-      launch_cg_scalars(c->s, c->scal, 0);
-      launch_cg_update(c->s, n, c->scal, c->x, c->rr, c->pd, c->Ap);
-      launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
-      ++it;
-      const double r2 = read_scalar(c, c->scal + 5);
-      rel = std::sqrt(r2 / bb);
-      if (!std::isfinite(rel)) { broke = true; break; }
-      if (rel <= c->opts.rtol) { conv = true; break; }
+  const int gk = c->opts.krylov == HDGMG_KRYLOV_CG ? 0 : 1;
+  long long captured = 0, replayed = 0;
+  if (!conv) {
+    // the iteration body as one graph (captured at the first solve)
+    const bool had = c->g_iter[gk] != nullptr;
+    const bool use_graph = ensure_graph(c, gk);
+    if (!had) captured = c->g_nodes[gk];
+    if (gk == 0) {
+      cudaMemcpyAsync(c->rr, c->b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);   // r = b
       vcycle(c, 0, c->rr, c->z);
-      launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 3);
-      launch_cg_scalars(c->s, c->scal, 1);
-      launch_cg_direction(c->s, n, c->scal, c->z, c->pd);
+      cudaMemcpyAsync(c->pd, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+      launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 0);
     }
-  } else if (!conv) {                                   // MG as a fixed-point solver
     while (it < c->opts.max_it) {
-      level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
-      vcycle(c, 0, c->rr, c->z);
-      launch_axpby(c->s, n, 1.0, c->z, 1.0, c->x);
+      if (use_graph) {
+        cudaGraphLaunch(c->g_iter[gk], c->s);
+        replayed += c->g_nodes[gk];
+      } else if (gk == 0) {
+        pcg_body(c);
+      } else {
+        fp_body(c);
+      }
       ++it;
-      level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
-      launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
       rel = std::sqrt(read_scalar(c, c->scal + 5) / bb);
-      if (!std::isfinite(rel) || rel > 1e8) { broke = true; break; }
+      if (!std::isfinite(rel) || (gk == 1 && rel > 1e8)) { broke = true; break; }
       if (rel <= c->opts.rtol) { conv = true; break; }
     }
   }
@@ -1270,7 +1332,11 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
     info->t_solve_ms = t_solve;
     info->n_levels = (int32_t)c->L.size();
     info->trace_dofs = c->plan.trace_dofs;
-    info->kernel_launches = launch_count() - launches0;
+    info->kernel_launches = launch_count() - launches0 - captured + replayed;
+    info->t_condense_ms = t_cond;
+    info->condense_threads = 128;
+    info->condense_elements_per_block = 1;
+    info->condense_kind = HDGMG_CONDENSE_FACTOR;
   }
   if (broke) return fail_u(HDGMG_EBREAKDOWN, "the iteration broke down (NaN/Inf or divergence)");
   if (!conv) return fail_u(HDGMG_ENOCONV, "max_it reached");
@@ -1284,6 +1350,11 @@ void hdgmg_umesh_destroy(hdgmg_umesh* c) {
   if (c->hbuf) cudaFreeHost(c->hbuf);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev2) cudaEventDestroy(c->ev2);
+  for (auto& g : c->g_iter)
+    if (g) cudaGraphExecDestroy(g);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev3) cudaEventDestroy(c->ev3);
   delete c;
 }
 

@@ -10,7 +10,7 @@ import numpy as np
 
 from . import hdgmg as _h
 
-EXPORTED = ["hdgmg_umesh_plan_create", "hdgmg_umesh_plan_destroy", "hdgmg_umesh_plan_sizes",
+EXPORTED = ["hdgmg_umesh_default_opts", "hdgmg_umesh_plan_create", "hdgmg_umesh_plan_destroy", "hdgmg_umesh_plan_sizes",
             "hdgmg_umesh_plan_edges", "hdgmg_umesh_plan_partition", "hdgmg_umesh_plan_macro_edges",
             "hdgmg_umesh_create", "hdgmg_umesh_setup", "hdgmg_umesh_solve",
             "hdgmg_umesh_level_sizes", "hdgmg_umesh_element_matrices", "hdgmg_umesh_apply",
@@ -41,6 +41,8 @@ def load():
     lib.hdgmg_umesh_plan_edges.argtypes = [P, P]
     lib.hdgmg_umesh_plan_partition.argtypes = [P, I32, P]
     lib.hdgmg_umesh_plan_macro_edges.argtypes = [P, I32, P, P, P]
+    lib.hdgmg_umesh_default_opts.argtypes = [ctypes.POINTER(_h.Opts)]
+    lib.hdgmg_umesh_default_opts.restype = None
     lib.hdgmg_umesh_create.argtypes = [PP, ctypes.POINTER(UProblem), ctypes.POINTER(_h.Opts), P]
     lib.hdgmg_umesh_setup.argtypes = [P, P]
     lib.hdgmg_umesh_solve.argtypes = [P, P, P, P, P, ctypes.POINTER(_h.Info)]
@@ -51,7 +53,7 @@ def load():
     lib.hdgmg_umesh_destroy.argtypes = [P]
     lib.hdgmg_umesh_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("hdgmg_umesh_plan_destroy", "hdgmg_umesh_destroy"):
+        if name not in ("hdgmg_umesh_plan_destroy", "hdgmg_umesh_destroy", "hdgmg_umesh_default_opts"):
             getattr(lib, name).restype = ctypes.c_int
     _ready = True
     return lib
@@ -138,7 +140,7 @@ class USolver:
         self.p = int(p)
         self._pr = _Problem(verts, quads, p, tau, seeds)
         o = _h.Opts()
-        lib.hdgmg_default_opts(ctypes.byref(o))
+        lib.hdgmg_umesh_default_opts(ctypes.byref(o))
         for k, v in opts.items():
             setattr(o, k, v)
         self.opts = o

@@ -333,3 +333,12 @@ def example2(n, p, seeds=7, seed=0):
     sp = np.array(EXAMPLE2_SEEDS_7 if seeds == 7 else EXAMPLE2_SEEDS_4, dtype=np.float64)
     E = len(quads)
     return verts, quads, sp, np.zeros(E), np.ones((E, (p + 1) ** 2))
+
+
+def seed_grid(nx, ny, lx=2.0, ly=1.0):
+    """nx x ny seed points at the centres of a regular grid of the box, so
+    that every level-1 macro-element holds about the same number of elements
+    (the paper's criterion for placing seeds)."""
+    xs = (np.arange(nx) + 0.5) * lx / nx
+    ys = (np.arange(ny) + 0.5) * ly / ny
+    return np.array([(x, y) for y in ys for x in xs], dtype=np.float64)

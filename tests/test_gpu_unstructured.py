@@ -13,6 +13,8 @@ from oracle import unstructured as U
 from paper_1811_09909_gb300 import hdgmg, umesh as um, workloads as W
 
 TOL = 1e-10          # FP64, different summation orders: relative to the operator's scale
+# the unstructured defaults (hdgmg_umesh_default_opts), passed to the oracle
+SMOOTH = dict(omega=0.8, m_fine=2, m_max=8)
 
 
 def _dev(a):
@@ -72,8 +74,7 @@ def test_vcycle_matches_oracle(p, lc):
 
 @pytest.mark.parametrize("p", [1, 3])
 def test_pcg_solve_and_recovery_match_oracle(p):
-    om = 0.8 if p == 1 else 1.0
-    s, pr, sp, f = _setup(5, p, kappa_sigma=1.0, omega=om, rtol=1e-11)
+    s, pr, sp, f = _setup(5, p, kappa_sigma=1.0, rtol=1e-11)
     lam, u, q, info = s.solve(_dev(f))
     assert info.converged and info.rel_res <= 1e-11
     lam_o = pr.solve_direct(f)
@@ -84,7 +85,7 @@ def test_pcg_solve_and_recovery_match_oracle(p):
     assert np.abs(q.cpu().numpy() - q_o).max() < 1e-7 * np.abs(q_o).max()
     Ae, ge = pr.condense(f)
     b = pr.assemble_rhs(ge)[pr.free_dofs()]
-    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="both", omega=om)
+    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="both", **SMOOTH)
     _, it, _, ok = hu.solve_pcg(b, tol=1e-11)
     assert ok and abs(info.iters - it) <= 1, (info.iters, it)
 
@@ -94,7 +95,7 @@ def test_fixed_point_iterations_match_oracle():
     lam, _, _, info = s.solve(_dev(f), want_u=False, want_q=False)
     Ae, ge = pr.condense(f)
     b = pr.assemble_rhs(ge)[pr.free_dofs()]
-    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="pre")
+    hu = U.UHierarchy(pr, sp, Ae=Ae, local_corr="pre", **SMOOTH)
     _, it, _, ok = hu.solve_fixed_point(b, tol=1e-9)
     assert ok and info.converged and abs(info.iters - it) <= 1, (info.iters, it)
 
