@@ -144,21 +144,48 @@ __device__ __forceinline__ double eval_E(const UTab& T, const Geo<P>& g, int a, 
 }
 
 // ---------------------------------------------------------------------------
-// condensation: one element per block
+// condensation: one element per block.  The kernel is bound by the FP64 pipe,
+// so every FP64 quantity used more than once is formed once: 1/m_i, the
+// trace-basis scales, and D_d[i][a] for the 2p+1 nodes i on the row and
+// column of a (the only non-zeros), stored by (a, t) with
+//   t < p+1:  i = (t, a2)            (the row of a)
+//   t >= p+1: i = (a1, t-p-1 skipping a2)   (the column of a).
 // ---------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ int line_node(int a, int t) {
+  constexpr int P1 = P + 1;
+  const int a1 = a % P1, a2 = a / P1;
+  if (t < P1) return a2 * P1 + t;
+  const int r = t - P1;
+  return (r < a2 ? r : r + 1) * P1 + a1;
+}
+
+// position of node i in the line list of b, or -1
+template <int P>
+__device__ __forceinline__ int line_pos(int b, int i) {
+  constexpr int P1 = P + 1;
+  const int b1 = b % P1, b2 = b / P1, i1 = i % P1, i2 = i / P1;
+  if (i2 == b2) return i1;
+  if (i1 == b1) return P1 + (i2 < b2 ? i2 : i2 - 1);
+  return -1;
+}
+
 template <int P>
 __global__ void __launch_bounds__(128) u_condense_kernel(
     UTab T, const double* __restrict__ xy, const int* __restrict__ quads,
     const double* __restrict__ logk, double tau, int E, double* __restrict__ Aout,
     double* __restrict__ Lout, double* __restrict__ Zout, double* __restrict__ Mout,
     int* __restrict__ err) {
-  constexpr int P1 = P + 1, NV = P1 * P1, NT = 4 * P1;
+  constexpr int P1 = P + 1, NV = P1 * P1, NT = 4 * P1, NL = 2 * P1 - 1;
   extern __shared__ double sm[];
   double* S = sm;                 // [NV][NV]
   double* W = S + NV * NV;        // [NV][NT]
   double* F = W + NV * NT;        // [NV][NT], later Z
   double* Am = F + NV * NT;       // [NT][NT]
+  double* Dx = Am + NT * NT;      // [NV][NL]  D_x[line_node(a,t)][a]
+  double* Dy = Dx + NV * NL;      // [NV][NL]
   __shared__ Geo<P> g;
+  __shared__ double invm[NV], escale[4][P1], rdiag[NV];
   __shared__ int bad;
   const int e = blockIdx.x;
   const int tid = threadIdx.x;
@@ -166,57 +193,83 @@ __global__ void __launch_bounds__(128) u_condense_kernel(
   element_geometry<P>(T, xy, quads, e, g);
   __syncthreads();
   const double kap = exp(logk[e]);
-  for (int x = tid; x < NV * NT; x += blockDim.x) {
-    const int i = x / NT, jk = x % NT;
-    F[x] = fval<P>(T, g, i, jk / P1, jk % P1);
+  for (int a = tid; a < NV; a += blockDim.x) {
+    invm[a] = 1.0 / g.m[a];
+    Mout[(size_t)e * NV + a] = g.m[a];
   }
-  for (int a = tid; a < NV; a += blockDim.x) Mout[(size_t)e * NV + a] = g.m[a];
+  for (int x = tid; x < 4 * P1; x += blockDim.x) {
+    const int j = x / P1, k = x % P1;
+    escale[j][k] = 0.5 * sqrt(g.len[j] * (2.0 * k + 1.0));
+  }
+  for (int x = tid; x < NV * NL; x += blockDim.x) {
+    const int a = x / NL, t = x % NL;
+    const int i = line_node<P>(a, t);
+    Dx[x] = dval<P>(T, g, 0, i, a);
+    Dy[x] = dval<P>(T, g, 1, i, a);
+  }
   __syncthreads();
-  // S = kappa G + tau E
+  // F[i][(j,k)] = <psi_jk, phi_i>_{edge j}
+  for (int x = tid; x < NV * NT; x += blockDim.x) {
+    const int i = x / NT, jk = x % NT, j = jk / P1, k = jk % P1;
+    const int i1 = i % P1, i2 = i / P1;
+    int al, rev;
+    double endv;
+    switch (j) {
+      case 0: al = i1; endv = T.le[i2]; rev = 0; break;
+      case 1: al = i2; endv = T.re[i1]; rev = 0; break;
+      case 2: al = i1; endv = T.re[i2]; rev = 1; break;
+      default: al = i2; endv = T.le[i1]; rev = 1; break;
+    }
+    const double v = escale[j][k] * T.w[al] * endv * T.Pk[k][al];
+    F[x] = (((rev ^ g.flip[j]) & k) & 1) ? -v : v;
+  }
+  __syncthreads();
+  // S = kappa G + tau E,  G[a][b] = sum_i sum_d D_d[i][a] D_d[i][b] / m_i
   for (int x = tid; x < NV * NV; x += blockDim.x) {
     const int a = x / NV, b = x % NV;
-    const int a1 = a % P1, a2 = a / P1;
     double gsum = 0.0;
-    for (int t = 0; t < 2 * P1 - 1; ++t) {        // i on the row and column of a
-      const int i = t < P1 ? a2 * P1 + t : (t - P1 < a2 ? t - P1 : t - P1 + 1) * P1 + a1;
-      const double dxa = dval<P>(T, g, 0, i, a), dya = dval<P>(T, g, 1, i, a);
-      const double dxb = dval<P>(T, g, 0, i, b), dyb = dval<P>(T, g, 1, i, b);
-      gsum += (dxa * dxb + dya * dyb) / g.m[i];
+    for (int t = 0; t < NL; ++t) {
+      const int i = line_node<P>(a, t);
+      const int tb = line_pos<P>(b, i);
+      if (tb < 0) continue;
+      const double pr = Dx[a * NL + t] * Dx[b * NL + tb] + Dy[a * NL + t] * Dy[b * NL + tb];
+      gsum += pr * invm[i];
     }
     S[x] = kap * gsum + tau * eval_E<P>(T, g, a, b);
   }
-  // W = kappa H + tau F
+  // W = kappa H + tau F,  H[a][(j,k)] = sum_i (D_x n_jx + D_y n_jy)[i][a] F[i][(j,k)] / m_i
   for (int x = tid; x < NV * NT; x += blockDim.x) {
     const int a = x / NT, jk = x % NT, j = jk / P1;
-    const int a1 = a % P1, a2 = a / P1;
     double h = 0.0;
-    for (int t = 0; t < 2 * P1 - 1; ++t) {
-      const int i = t < P1 ? a2 * P1 + t : (t - P1 < a2 ? t - P1 : t - P1 + 1) * P1 + a1;
-      const double dn = dval<P>(T, g, 0, i, a) * g.nx[j] + dval<P>(T, g, 1, i, a) * g.ny[j];
-      h += dn * F[i * NT + jk] / g.m[i];
+    for (int t = 0; t < NL; ++t) {
+      const int i = line_node<P>(a, t);
+      const double dn = (Dx[a * NL + t] * g.nx[j] + Dy[a * NL + t] * g.ny[j]) * invm[i];
+      h += dn * F[i * NT + jk];
     }
     W[x] = kap * h + tau * F[x];
   }
-  // kappa K + tau I
+  // kappa K + tau I,  K[r][c] = n_r . n_c sum_i F[i][r] F[i][c] / m_i
   for (int x = tid; x < NT * NT; x += blockDim.x) {
     const int r = x / NT, c = x % NT;
     const int jr = r / P1, jc = c / P1;
     const double nn = g.nx[jr] * g.nx[jc] + g.ny[jr] * g.ny[jc];
     double ks = 0.0;
-    for (int i = 0; i < NV; ++i) ks += F[i * NT + r] * F[i * NT + c] / g.m[i];
+    for (int i = 0; i < NV; ++i) ks += F[i * NT + r] * (F[i * NT + c] * invm[i]);
     Am[x] = kap * nn * ks + (r == c ? tau : 0.0);
   }
   __syncthreads();
-  // Cholesky of S (lower, in place)
+  // Cholesky of S (lower, in place); rdiag = 1 / L_kk
   for (int k = 0; k < NV; ++k) {
     if (tid == 0) {
       double d = S[k * NV + k];
       if (!(d > 0.0)) { bad = 1; d = 1.0; }
-      S[k * NV + k] = sqrt(d);
+      const double l = sqrt(d);
+      S[k * NV + k] = l;
+      rdiag[k] = 1.0 / l;
     }
     __syncthreads();
-    const double piv = S[k * NV + k];
-    for (int r = k + 1 + tid; r < NV; r += blockDim.x) S[r * NV + k] /= piv;
+    const double rp = rdiag[k];
+    for (int r = k + 1 + tid; r < NV; r += blockDim.x) S[r * NV + k] *= rp;
     __syncthreads();
     const int m = NV - k - 1;
     for (int x = tid; x < m * m; x += blockDim.x) {
@@ -230,12 +283,12 @@ __global__ void __launch_bounds__(128) u_condense_kernel(
     for (int r = 0; r < NV; ++r) {
       double v = W[r * NT + c];
       for (int q = 0; q < r; ++q) v -= S[r * NV + q] * F[q * NT + c];
-      F[r * NT + c] = v / S[r * NV + r];
+      F[r * NT + c] = v * rdiag[r];
     }
     for (int r = NV - 1; r >= 0; --r) {
       double v = F[r * NT + c];
       for (int q = r + 1; q < NV; ++q) v -= S[q * NV + r] * F[q * NT + c];
-      F[r * NT + c] = v / S[r * NV + r];
+      F[r * NT + c] = v * rdiag[r];
     }
   }
   __syncthreads();
@@ -346,6 +399,33 @@ __global__ void u_elem_matvec_kernel(int n_el, int nu, int nd, const int* __rest
     if (b >= 0) s += Ae[(size_t)j * ndm + i] * x[(size_t)b * nd + j % nd];
   }
   t[id] = s;
+}
+
+// the same for the mesh levels (4 edges of ND modes per element), fully
+// unrolled so that every load of a thread is in flight at once
+template <int ND>
+__global__ void __launch_bounds__(128) u_elem_matvec_mesh_kernel(int n_el, const int* __restrict__ el_slot,
+                                                                 const double* __restrict__ A,
+                                                                 const double* __restrict__ x,
+                                                                 double* __restrict__ t) {
+  constexpr int NDM = 4 * ND;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)n_el * NDM) return;
+  const int e = (int)(id / NDM), i = (int)(id % NDM);
+  const double* Ae = A + (size_t)e * NDM * NDM + i;
+  int b[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) b[s] = __ldg(el_slot + 4 * e + s);
+  double xv[NDM];
+#pragma unroll
+  for (int j = 0; j < NDM; ++j) xv[j] = b[j / ND] >= 0 ? __ldg(x + (size_t)b[j / ND] * ND + j % ND) : 0.0;
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+  for (int j = 0; j < NDM; j += 2) {
+    s0 += __ldg(Ae + (size_t)j * NDM) * xv[j];
+    if (j + 1 < NDM) s1 += __ldg(Ae + (size_t)(j + 1) * NDM) * xv[j + 1];
+  }
+  t[id] = s0 + s1;
 }
 
 enum { U_SUM = 0, U_RES = 1, U_SMOOTH = 2 };
@@ -878,12 +958,31 @@ void launch_recover_p(hdgmg_umesh* c, const double* lam, const double* f, double
                                                lam, u, q);
 }
 
+template <int ND>
+void mesh_matvec(hdgmg_umesh* c, const ULevelDev& L, const double* x) {
+  u_elem_matvec_mesh_kernel<ND><<<nblk((long long)L.n_el * 4 * ND, 128), 128, 0, c->s>>>(L.n_el, L.el_slot, L.A, x,
+                                                                                       L.t);
+}
+
 void level_matvec(hdgmg_umesh* c, int k, const double* x, double* y, int mode, const double* r) {
   ULevelDev& L = c->L[k];
   if (L.n_blk == 0) return;
   note_launch();
-  u_elem_matvec_kernel<<<nblk((long long)L.n_el * L.ndm, 128), 128, 0, c->s>>>(L.n_el, L.nu, L.nd, L.el_slot, L.A,
-                                                                              x, L.t);
+  if (k < c->plan.first_h + 1 && L.nu == 4) {       // a mesh level
+    switch (L.nd) {
+      case 2: mesh_matvec<2>(c, L, x); break;
+      case 3: mesh_matvec<3>(c, L, x); break;
+      case 4: mesh_matvec<4>(c, L, x); break;
+      case 5: mesh_matvec<5>(c, L, x); break;
+      case 6: mesh_matvec<6>(c, L, x); break;
+      case 7: mesh_matvec<7>(c, L, x); break;
+      case 8: mesh_matvec<8>(c, L, x); break;
+      default: mesh_matvec<9>(c, L, x); break;
+    }
+  } else {
+    u_elem_matvec_kernel<<<nblk((long long)L.n_el * L.ndm, 128), 128, 0, c->s>>>(L.n_el, L.nu, L.nd, L.el_slot,
+                                                                                L.A, x, L.t);
+  }
   note_launch();
   u_unit_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.blk_t0, L.blk_t1, L.t, r, L.Dinv,
                                                       c->opts.omega, mode, y);
@@ -1142,7 +1241,7 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
   if (cudaMallocHost((void**)&c->hbuf, 64) != cudaSuccess) return bail(HDGMG_ENOMEM, "pinned allocation failed");
   cudaMemset(c->err, 0, sizeof(int));
   const int nv = c->nv, nt = c->nt;
-  c->condense_smem = (size_t)(nv * nv + 2 * nv * nt + nt * nt) * sizeof(double);
+  c->condense_smem = (size_t)(nv * nv + 2 * nv * nt + nt * nt + 2 * nv * (2 * c->p + 1)) * sizeof(double);
   bool attr = true;
   switch (c->p) {
     case 1: attr = set_condense_attr<1>(c->condense_smem); break;
