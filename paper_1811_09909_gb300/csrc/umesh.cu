@@ -383,26 +383,9 @@ __global__ void __launch_bounds__(128) u_recover_kernel(
 // ---------------------------------------------------------------------------
 // level operators
 // ---------------------------------------------------------------------------
-// t[e][i] = sum_j A[e][j][i] x(dof of slot j)
-__global__ void u_elem_matvec_kernel(int n_el, int nu, int nd, const int* __restrict__ el_slot,
-                                     const double* __restrict__ A, const double* __restrict__ x,
-                                     double* __restrict__ t) {
-  const int ndm = nu * nd;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (long long)n_el * ndm) return;
-  const int e = (int)(id / ndm), i = (int)(id % ndm);
-  const double* Ae = A + (size_t)e * ndm * ndm;
-  const int* sl = el_slot + (size_t)e * nu;
-  double s = 0.0;
-  for (int j = 0; j < ndm; ++j) {
-    const int b = sl[j / nd];
-    if (b >= 0) s += Ae[(size_t)j * ndm + i] * x[(size_t)b * nd + j % nd];
-  }
-  t[id] = s;
-}
-
-// the same for the mesh levels (4 edges of ND modes per element), fully
-// unrolled so that every load of a thread is in flight at once
+// t[e][i] = sum_j A_e[j][i] x(slot j) on a mesh level (4 edges of ND modes per
+// element), one thread per row, fully unrolled so that every load of a thread
+// is in flight at once (consecutive threads read consecutive entries)
 template <int ND>
 __global__ void __launch_bounds__(128) u_elem_matvec_mesh_kernel(int n_el, const int* __restrict__ el_slot,
                                                                  const double* __restrict__ A,
@@ -428,22 +411,20 @@ __global__ void __launch_bounds__(128) u_elem_matvec_mesh_kernel(int n_el, const
   t[id] = s0 + s1;
 }
 
-enum { U_SUM = 0, U_RES = 1, U_SMOOTH = 2 };
-
-// per unknown block: y = t(side 0) + t(side 1); SUM: out = y; RES: out = r - y;
-// SMOOTH: e += omega Dinv (r - y)
-__global__ void u_unit_kernel(int n_blk, int nd, const int* __restrict__ t0, const int* __restrict__ t1,
-                              const double* __restrict__ t, const double* __restrict__ r,
-                              const double* __restrict__ Dinv, double omega, int mode,
-                              double* __restrict__ out) {
+// mesh levels, second half: per edge block y = t(side 0) + t(side 1); SUM:
+// out = y; RES: out = r - y; SMOOTH: out = x + omega Dinv (r - y)
+__global__ void u_edge_kernel(int n_blk, int nd, const int* __restrict__ t0, const int* __restrict__ t1,
+                              const double* __restrict__ t, const double* __restrict__ x,
+                              const double* __restrict__ r, const double* __restrict__ Dinv, double omega,
+                              int mode, double* __restrict__ out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blk) return;
   double y[9];
   const size_t o0 = (size_t)t0[b] * nd, o1 = (size_t)t1[b] * nd;
   for (int k = 0; k < nd; ++k) y[k] = t[o0 + k] + t[o1 + k];
-  if (mode == U_SUM) {
+  if (mode == 0) {
     for (int k = 0; k < nd; ++k) out[(size_t)b * nd + k] = y[k];
-  } else if (mode == U_RES) {
+  } else if (mode == 1) {
     for (int k = 0; k < nd; ++k) out[(size_t)b * nd + k] = r[(size_t)b * nd + k] - y[k];
   } else {
     for (int k = 0; k < nd; ++k) y[k] = r[(size_t)b * nd + k] - y[k];
@@ -451,9 +432,84 @@ __global__ void u_unit_kernel(int n_blk, int nd, const int* __restrict__ t0, con
     for (int k = 0; k < nd; ++k) {
       double s = 0.0;
       for (int l = 0; l < nd; ++l) s += D[k * nd + l] * y[l];
-      out[(size_t)b * nd + k] += omega * s;
+      out[(size_t)b * nd + k] = x[(size_t)b * nd + k] + omega * s;
     }
   }
+}
+
+enum { U_SUM = 0, U_RES = 1, U_SMOOTH = 2 };
+
+// y = A x for one level in one pass, pulled per macro-edge: thread (b, k)
+// forms row k of macro-edge b from its two sides, y_bk = sum over the sides
+// of the element rows (A_e symmetric, stored column by column, so row i is
+// contiguous across k) against the element's gathered x; every element row is
+// read once.  Then SUM: out = y; RES: out = r - y; SMOOTH: out = x + omega
+// Dinv (r - y) on the block (the block's rows meet in shared memory).  out
+// never aliases x: a smoothing step reads every neighbour's old value.
+template <int ND, int NU>
+__global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const int* __restrict__ el_slot,
+                                                     const int* __restrict__ t0, const int* __restrict__ t1,
+                                                     const double* __restrict__ A, const double* __restrict__ x,
+                                                     const double* __restrict__ r, const double* __restrict__ Dinv,
+                                                     double omega, int mode, double* __restrict__ out) {
+  constexpr int UPB = 128 / ND;
+  __shared__ double ys[UPB * ND];
+  const int nu = NU > 0 ? NU : nu_rt;
+  const int ndm = nu * ND;
+  const int lu = threadIdx.x / ND, k = threadIdx.x % ND;
+  const int b = blockIdx.x * UPB + lu;
+  const bool act = lu < UPB && b < n_blk;
+  double y = 0.0;
+  if (act) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int ts = side == 0 ? __ldg(t0 + b) : __ldg(t1 + b);
+      const int el = ts / nu, sl = ts % nu;
+      const double* Ae = A + (size_t)el * ndm * ndm + sl * ND + k;
+      const int* sls = el_slot + (size_t)el * nu;
+      double s = 0.0;
+      if (NU > 0) {
+#pragma unroll
+        for (int j = 0; j < NU * ND; ++j) {
+          const int bj = __ldg(sls + j / ND);
+          if (bj >= 0) s += __ldg(Ae + (size_t)j * ndm) * __ldg(x + (size_t)bj * ND + j % ND);
+        }
+      } else {
+        for (int j = 0; j < ndm; ++j) {
+          const int bj = __ldg(sls + j / ND);
+          if (bj >= 0) s += __ldg(Ae + (size_t)j * ndm) * __ldg(x + (size_t)bj * ND + j % ND);
+        }
+      }
+      y += s;
+    }
+  }
+  if (mode == U_SUM) {
+    if (act) out[(size_t)b * ND + k] = y;
+    return;
+  }
+  if (mode == U_RES) {
+    if (act) out[(size_t)b * ND + k] = r[(size_t)b * ND + k] - y;
+    return;
+  }
+  if (lu < UPB) ys[lu * ND + k] = act ? r[(size_t)b * ND + k] - y : 0.0;
+  __syncthreads();
+  if (act) {
+    const double* D = Dinv + (size_t)b * ND * ND + k * ND;
+    double s = 0.0;
+#pragma unroll
+    for (int l = 0; l < ND; ++l) s += D[l] * ys[lu * ND + l];
+    out[(size_t)b * ND + k] = x[(size_t)b * ND + k] + omega * s;
+  }
+}
+
+// per unknown block: out = t(side 0) + t(side 1) (the element-slot sums of
+// the right-hand side and of the restriction)
+__global__ void u_unit_kernel(int n_blk, int nd, const int* __restrict__ t0, const int* __restrict__ t1,
+                              const double* __restrict__ t, double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_blk) return;
+  const size_t o0 = (size_t)t0[b] * nd, o1 = (size_t)t1[b] * nd;
+  for (int k = 0; k < nd; ++k) out[(size_t)b * nd + k] = t[o0 + k] + t[o1 + k];
 }
 
 // e = omega Dinv r (first smoothing step from zero)
@@ -849,7 +905,7 @@ struct ULevelDev {
   int nd = 0, n_el = 0, nu = 0, ndm = 0, n_blk = 0, m = 1;
   int *el_slot = nullptr, *blk_t0 = nullptr, *blk_t1 = nullptr;
   double *A = nullptr, *Dinv = nullptr;
-  double *r = nullptr, *e = nullptr, *res = nullptr, *t = nullptr;
+  double *r = nullptr, *e = nullptr, *res = nullptr, *t = nullptr, *tmp = nullptr;
   long long n() const { return (long long)n_blk * nd; }
 };
 
@@ -958,17 +1014,29 @@ void launch_recover_p(hdgmg_umesh* c, const double* lam, const double* f, double
                                                lam, u, q);
 }
 
+template <int ND, int NU>
+void pull(hdgmg_umesh* c, const ULevelDev& L, const double* x, double* y, int mode, const double* r) {
+  constexpr int UPB = 128 / ND;
+  u_pull_kernel<ND, NU><<<nblk(L.n_blk, UPB), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1, L.A,
+                                                               x, r, L.Dinv, c->opts.omega, mode, y);
+}
+
 template <int ND>
 void mesh_matvec(hdgmg_umesh* c, const ULevelDev& L, const double* x) {
   u_elem_matvec_mesh_kernel<ND><<<nblk((long long)L.n_el * 4 * ND, 128), 128, 0, c->s>>>(L.n_el, L.el_slot, L.A, x,
                                                                                        L.t);
 }
 
+// y = A_k x (SUM), y = r - A_k x (RES) or y = x + omega Dinv (r - A_k x)
+// (SMOOTH; y never aliases x).  Mesh levels stream their element operators
+// from HBM: one thread per element row (coalesced) into the slot buffer, then
+// the edge sums.  Macro-element levels are small and latency-bound: one pass
+// pulled per macro-edge.
 void level_matvec(hdgmg_umesh* c, int k, const double* x, double* y, int mode, const double* r) {
   ULevelDev& L = c->L[k];
   if (L.n_blk == 0) return;
-  note_launch();
-  if (k < c->plan.first_h + 1 && L.nu == 4) {       // a mesh level
+  if (k <= c->plan.first_h && L.nu == 4) {
+    note_launch();
     switch (L.nd) {
       case 2: mesh_matvec<2>(c, L, x); break;
       case 3: mesh_matvec<3>(c, L, x); break;
@@ -979,13 +1047,13 @@ void level_matvec(hdgmg_umesh* c, int k, const double* x, double* y, int mode, c
       case 8: mesh_matvec<8>(c, L, x); break;
       default: mesh_matvec<9>(c, L, x); break;
     }
+    note_launch();
+    u_edge_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.blk_t0, L.blk_t1, L.t, x, r, L.Dinv,
+                                                        c->opts.omega, mode, y);
   } else {
-    u_elem_matvec_kernel<<<nblk((long long)L.n_el * L.ndm, 128), 128, 0, c->s>>>(L.n_el, L.nu, L.nd, L.el_slot,
-                                                                                L.A, x, L.t);
+    note_launch();
+    pull<2, 0>(c, L, x, y, mode, r);
   }
-  note_launch();
-  u_unit_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.blk_t0, L.blk_t1, L.t, r, L.Dinv,
-                                                      c->opts.omega, mode, y);
 }
 
 // e = B_k r (Algorithm 1)
@@ -1000,10 +1068,16 @@ void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
   }
   const double om = c->opts.omega;
   if (L.n_blk == 0) return;
-  // step 2: pre-smoothing from zero
+  // step 2: pre-smoothing from zero; the steps alternate between e and tmp
+  // and end in e
+  double* cur = ((L.m - 1) % 2 == 1) ? L.tmp : e;
   note_launch();
-  u_bj_first_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.Dinv, r, om, e);
-  for (int it = 1; it < L.m; ++it) level_matvec(c, k, e, e, U_SMOOTH, r);
+  u_bj_first_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.Dinv, r, om, cur);
+  for (int it = 1; it < L.m; ++it) {
+    double* nxt = cur == e ? L.tmp : e;
+    level_matvec(c, k, cur, nxt, U_SMOOTH, r);
+    cur = nxt;
+  }
   const bool hlev = k >= c->plan.first_h;
   const int lc = c->opts.local_corr;
   UHDev* H = hlev ? &c->H[k - c->plan.first_h] : nullptr;
@@ -1019,8 +1093,7 @@ void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
     u_restrict_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, C.t);
     if (C.n_blk > 0) {
       note_launch();
-      u_unit_kernel<<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, C.t, nullptr, nullptr,
-                                                          0.0, U_SUM, C.r);
+      u_unit_kernel<<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, C.t, C.r);
     }
   } else {
     note_launch();
@@ -1039,7 +1112,16 @@ void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
     note_launch();
     u_localcorr_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, e);
   }
-  for (int it = 0; it < L.m; ++it) level_matvec(c, k, e, e, U_SMOOTH, r);   // step 6
+  cur = e;                                                        // step 6
+  if (L.m % 2 == 1) {
+    cudaMemcpyAsync(L.tmp, e, (size_t)L.n() * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
+    cur = L.tmp;
+  }
+  for (int it = 0; it < L.m; ++it) {
+    double* nxt = cur == e ? L.tmp : e;
+    level_matvec(c, k, cur, nxt, U_SMOOTH, r);
+    cur = nxt;
+  }
 }
 
 hdgmg_status read_err(hdgmg_umesh* c, const char* what) {
@@ -1185,6 +1267,7 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
     ok = upload(c, &d.el_slot, pl.el_slot) && upload(c, &d.blk_t0, pl.blk_t0) && upload(c, &d.blk_t1, pl.blk_t1) &&
          dalloc(c, &d.A, (size_t)d.n_el * d.ndm * d.ndm) && dalloc(c, &d.Dinv, (size_t)d.n_blk * d.nd * d.nd) &&
          dalloc(c, &d.r, (size_t)d.n()) && dalloc(c, &d.e, (size_t)d.n()) && dalloc(c, &d.res, (size_t)d.n()) &&
+         dalloc(c, &d.tmp, (size_t)d.n()) &&
          dalloc(c, &d.t, (size_t)d.n_el * d.ndm);
     c->L.push_back(d);
   }
@@ -1370,8 +1453,7 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
   U_DISPATCH(c->p, launch_rhs_p, c, f, L0.t);
   if (L0.n_blk > 0) {
     note_launch();
-    u_unit_kernel<<<nblk(L0.n_blk, 128), 128, 0, c->s>>>(L0.n_blk, L0.nd, L0.blk_t0, L0.blk_t1, L0.t, nullptr,
-                                                         nullptr, 0.0, U_SUM, c->b);
+    u_unit_kernel<<<nblk(L0.n_blk, 128), 128, 0, c->s>>>(L0.n_blk, L0.nd, L0.blk_t0, L0.blk_t1, L0.t, c->b);
   }
   launch_dot(c->s, n, c->b, c->b, c->partial, c->scal + 6);
   const double bb = read_scalar(c, c->scal + 6);
