@@ -163,8 +163,9 @@ hdgmg_status hdgmg_umesh_level_sizes(const hdgmg_umesh* ctx, int32_t level,
                                      int64_t* out);
 
 /* Element operators of a level after set-up: A device [n_el][nd_max][nd_max]
- * FP64 out (symmetric, zero padding), dofs host [n_el][nd_max] out: the
- * level-vector index of every row (-1: padding or a boundary edge). */
+ * FP64 out (symmetric, zero padding; EINVAL before the first set-up), dofs
+ * host [n_el][nd_max] out: the level-vector index of every row (-1: padding
+ * or a boundary edge).  Either pointer may be NULL. */
 hdgmg_status hdgmg_umesh_element_matrices(const hdgmg_umesh* ctx, int32_t level,
                                           double* A, int32_t* dofs);
 

@@ -25,6 +25,11 @@ hybridized high-order finite element methods" (arXiv:1811.09909):
   edge block-Jacobi smoothing (Sec. 4.1), local correction (eq.
   localCorrection) and the V-cycle of Algorithm 1, all on global sparse
   matrices; outer fixed-point iteration, PCG and right-preconditioned GMRES.
+* ``unstructured`` -- the same HDG element on bilinearly mapped quadrilaterals
+  of an unstructured mesh, the seed-point agglomeration of Sec. 3.1.2 with
+  recursive cuts into four, macro-edges parameterised by arc length (the
+  remark in Sec. 3.1), J as an L2 projection by quadrature, and the hierarchy
+  and V-cycle of ``mg`` on those levels.
 
 Naming follows the usual HDG convention rather than the paper's: u is the
 scalar, q = -kappa grad u the flux, lambda the trace of u.

@@ -1420,6 +1420,7 @@ hdgmg_status hdgmg_umesh_level_sizes(const hdgmg_umesh* c, int32_t level, int64_
 
 hdgmg_status hdgmg_umesh_element_matrices(const hdgmg_umesh* c, int32_t level, double* A, int32_t* dofs) {
   if (!c) return fail_u(HDGMG_EINVAL, "null argument");
+  if (A && !c->ready) return fail_u(HDGMG_EINVAL, "set-up required");
   if (level < 0 || level >= (int32_t)c->L.size()) return fail_u(HDGMG_EINVAL, "level out of range");
   const ULevelDev& L = c->L[level];
   const UPlanLevel& pl = c->plan.levels[level];
