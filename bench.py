@@ -579,7 +579,7 @@ def run_unstructured(dev, steps, warmup, n=96, p=3):
     last = infos[-1]
     out = {"workload": f"Example II stand-in: 2x1 box, 8 holes, {nel} quads (bilinear), p={p}, "
                        f"{len(sp)} seeds, kappa=1, f=1; set-up + PCG (V-cycle, damped edge "
-                       "block-Jacobi 0.8, m=2 doubling to 8) to 1e-10 + recovery, FP64",
+                       "block-Jacobi 0.8, m=2 doubling to 4) to 1e-10 + recovery, FP64",
            "elements": nel, "trace_dofs": s.trace_dofs, "levels": s.n_levels,
            "value": s.trace_dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
            "setup_ms": last.t_setup_ms, "condense_ms": last.t_condense_ms,

@@ -122,10 +122,10 @@ hdgmg_status hdgmg_umesh_plan_macro_edges(const hdgmg_umesh_plan* plan, int32_t 
 typedef struct hdgmg_umesh hdgmg_umesh;
 
 /* The options hdgmg_umesh_create uses when given NULL: hdgmg_default_opts
- * with omega = 0.8, m_fine = 2, m_max = 8.  On meshes with irregular
+ * with omega = 0.8, m_fine = 2, m_max = 4.  On meshes with irregular
  * elements the undamped edge block-Jacobi smoother is not convergent on its
  * own (more smoothing steps make the V-cycle worse), so it is damped and
- * applied twice on the finest level, doubling per level up to 8. */
+ * applied twice on the finest level, doubling per level up to 4. */
 void hdgmg_umesh_default_opts(hdgmg_opts* opts);
 
 /* Create a context on the current device: builds the plan, uploads it and

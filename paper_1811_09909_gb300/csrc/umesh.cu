@@ -1197,7 +1197,7 @@ void hdgmg_umesh_default_opts(hdgmg_opts* o) {
   hdgmg_default_opts(o);
   o->omega = 0.8;
   o->m_fine = 2;
-  o->m_max = 8;
+  o->m_max = 4;
 }
 
 hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr, const hdgmg_opts* opts,

@@ -14,7 +14,7 @@ from paper_1811_09909_gb300 import hdgmg, umesh as um, workloads as W
 
 TOL = 1e-10          # FP64, different summation orders: relative to the operator's scale
 # the unstructured defaults (hdgmg_umesh_default_opts), passed to the oracle
-SMOOTH = dict(omega=0.8, m_fine=2, m_max=8)
+SMOOTH = dict(omega=0.8, m_fine=2, m_max=4)
 
 
 def _dev(a):
