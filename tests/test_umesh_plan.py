@@ -84,3 +84,48 @@ def test_plan_rejects_invalid_problems(bad):
     with pytest.raises(hdgmg.HdgmgError) as ei:
         um.Plan(v, q, p, tau, seeds)
     assert ei.value.status == -1
+
+
+def test_plan_edge_cases():
+    """One element (no interior edge), one seed, and four elements around one
+    vertex: sizes, partitions and macro-edges as worked by hand."""
+    verts = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    pl = um.Plan(verts, np.array([[0, 1, 2, 3]]), 2, 1.0, np.array([[0.5, 0.5]]))
+    assert (pl.n_edges, pl.n_parts, pl.trace_dofs) == (4, 1, 0)
+    info, items = pl.macro_edges(1)                 # P_0 = the element: one cycle around it
+    assert len(info) == 1 and info[0, 1] == -1 and info[0, 4] == 1 and len(items) == 4
+    # 2 x 2 elements, one seed: P_0 holds all four; no cut partition has <= 2 macro-elements
+    xs = np.array([0.0, 0.5, 1.0])
+    v = np.array([(x, y) for y in xs for x in xs])
+    q = np.array([(0, 1, 4, 3), (1, 2, 5, 4), (3, 4, 7, 6), (4, 5, 8, 7)])
+    pl = um.Plan(v, q, 1, 1.0, np.array([[0.3, 0.3]]))
+    assert pl.n_parts == 1 and np.all(pl.partition(0) == 0)
+    assert pl.trace_dofs == 4 * 2                  # the four interior edges, P_1
+    info, _ = pl.macro_edges(1)
+    assert len(info) == 1 and info[0, 1] == -1     # only the outer boundary
+    # two seeds splitting the square left / right: one interior macro-edge of two mesh edges
+    pl = um.Plan(v, q, 1, 1.0, np.array([[0.25, 0.5], [0.75, 0.5]]))
+    info, items = pl.macro_edges(1)
+    inner = info[info[:, 1] >= 0]
+    assert len(inner) == 1 and not inner[0, 4]
+    o = inner[0, 5]
+    assert sorted(items[o:o + 2, 0].tolist()) == sorted(
+        [i for i, (a, b) in enumerate(pl.edges().tolist()) if {a, b} in ({1, 4}, {4, 7})])
+    assert inner[0, 2] == 1 and inner[0, 3] == 7    # starts at the lower free end
+
+
+@pytest.mark.parametrize("field,value", [("krylov", 2), ("precision", 1), ("smoother", 1), ("m_fine", 0),
+                                         ("omega", 0.0), ("local_corr", 7)])
+def test_create_rejects_unsupported_options_before_touching_the_gpu(field, value):
+    import ctypes
+    from paper_1811_09909_gb300 import hdgmg
+    lib = um.load()
+    v, q = W.umesh(2, 2, 1.0, 1.0, 0.2, (), 1)
+    pr = um._Problem(v, q, 2, 1.0, np.array([[0.5, 0.5]]))
+    o = hdgmg.Opts()
+    lib.hdgmg_umesh_default_opts(ctypes.byref(o))
+    assert (o.omega, o.m_fine, o.m_max) == (0.8, 2, 4)
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    st = lib.hdgmg_umesh_create(ctypes.byref(h), ctypes.byref(pr.s), ctypes.byref(o), None)
+    assert st == -1 and not h
