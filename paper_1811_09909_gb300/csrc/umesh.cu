@@ -225,8 +225,10 @@ __global__ void __launch_bounds__(128) u_condense_kernel(
   }
   __syncthreads();
   // S = kappa G + tau E,  G[a][b] = sum_i sum_d D_d[i][a] D_d[i][b] / m_i
+  // (lower triangle: the Cholesky factorisation reads no other entry)
   for (int x = tid; x < NV * NV; x += blockDim.x) {
     const int a = x / NV, b = x % NV;
+    if (b > a) continue;
     double gsum = 0.0;
     for (int t = 0; t < NL; ++t) {
       const int i = line_node<P>(a, t);
@@ -248,9 +250,11 @@ __global__ void __launch_bounds__(128) u_condense_kernel(
     }
     W[x] = kap * h + tau * F[x];
   }
-  // kappa K + tau I,  K[r][c] = n_r . n_c sum_i F[i][r] F[i][c] / m_i
+  // kappa K + tau I,  K[r][c] = n_r . n_c sum_i F[i][r] F[i][c] / m_i (lower
+  // triangle; A_e is symmetric)
   for (int x = tid; x < NT * NT; x += blockDim.x) {
     const int r = x / NT, c = x % NT;
+    if (c > r) continue;
     const int jr = r / P1, jc = c / P1;
     const double nn = g.nx[jr] * g.nx[jc] + g.ny[jr] * g.ny[jc];
     double ks = 0.0;
@@ -292,13 +296,16 @@ __global__ void __launch_bounds__(128) u_condense_kernel(
     }
   }
   __syncthreads();
-  // A_e = kappa K + tau I - W^T Z
+  // A_e = kappa K + tau I - W^T Z, symmetric: the lower triangle, mirrored
   double* Ag = Aout + (size_t)e * NT * NT;
   for (int x = tid; x < NT * NT; x += blockDim.x) {
     const int r = x / NT, c = x % NT;
+    if (c > r) continue;
     double s = 0.0;
     for (int a = 0; a < NV; ++a) s += W[a * NT + r] * F[a * NT + c];
-    Ag[x] = Am[x] - s;
+    const double v = Am[x] - s;
+    Ag[x] = v;
+    Ag[c * NT + r] = v;
   }
   double* Lg = Lout + (size_t)e * NV * NV;
   for (int x = tid; x < NV * NV; x += blockDim.x) Lg[x] = S[x];
