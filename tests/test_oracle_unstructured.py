@@ -307,3 +307,78 @@ def test_multigrid_converges_on_example2(p):
     assert ok and it <= 30, it
     x_direct = pr.solve_direct(f)[pr.free_dofs()]
     assert np.abs(x - x_direct).max() < 1e-8 * np.abs(x_direct).max()
+
+
+def test_symmetric_cycle_is_symmetric_positive():
+    """With the local correction in steps 3 and 5 the V-cycle is a symmetric
+    positive definite preconditioner (what PCG needs): r1^T B r2 = r2^T B r1
+    and r^T B r > 0 on the holey mesh."""
+    verts, quads, seeds, _, _ = W.example2(4, 2)
+    pr = U.UHDGProblem(verts, quads, 2, 1.0, 1.0)
+    hu = U.UHierarchy(pr, seeds, local_corr="both", omega=0.8, m_fine=2, m_max=4)
+    rng = np.random.default_rng(4)
+    n = hu.levels[0].A.shape[0]
+    r1, r2 = rng.normal(size=n), rng.normal(size=n)
+    a, b = r1 @ hu.vcycle(r2), r2 @ hu.vcycle(r1)
+    assert abs(a - b) < 1e-10 * abs(a)
+    assert r1 @ hu.vcycle(r1) > 0 and r2 @ hu.vcycle(r2) > 0
+
+
+def test_planted_orientation_mistake_is_caught(monkeypatch):
+    """Dropping the global orientation of the trace basis (an element reading
+    its edges counter-clockwise regardless of the vertex order) breaks the
+    linear patch test: the pins see that mistake."""
+    orig = U.MappedQuad.__init__
+
+    def no_flip(self, p, xy, flips, nq=None):
+        orig(self, p, xy, [False] * 4, nq)
+
+    monkeypatch.setattr(U.MappedQuad, "__init__", no_flip)
+    v, q = W.umesh(3, 3, 1.0, 1.0, 0.25, (), 3)
+    pr = U.UHDGProblem(v, q, 2, 1.0, 1.0)
+    uex = lambda x, y: 1 + 2 * x - 3 * y
+    f = np.zeros((pr.E, pr.nv))
+    lam = pr.solve_direct(f, uex)
+    u, _ = pr.recover(lam, f)
+    X = pr.node_coords()
+    assert np.abs(u - uex(X[..., 0], X[..., 1])).max() > 1e-3
+
+
+def _arc_continuous(levels, ev):
+    """Every macro-edge's mesh edges, in arc-length order, form one walk from
+    its start vertex to its end vertex."""
+    for lev in levels:
+        for ch in lev["units"]:
+            cur = ch.start
+            for m, d in zip(ch.edges, ch.edirs):
+                a, b = ev[m] if d == 1 else ev[m][::-1]
+                if a != cur:
+                    return False
+                cur = b
+            if cur != ch.end:
+                return False
+    return True
+
+
+def test_planted_parameterisation_mistake_is_caught(monkeypatch):
+    """Traversing every unit forwards inside its macro-edge (dropping the
+    directions of the parameterisation) makes the arc length jump: the
+    continuity pin of the macro-edges sees it (nestedness alone does not --
+    each unit stays a contiguous piece of the coarse parameter)."""
+    verts, quads, seeds, _, _ = W.example2(4, 1)
+    ev = U.mesh_edges(quads)[0]
+    assert _arc_continuous(U.hierarchy_chains(verts, quads, seeds)[1], ev)
+    orig = U._order_chain
+
+    def forwards(comp, units, links, sides):
+        ch = orig(comp, units, links, sides)
+        ch.dirs = [1] * len(ch.dirs)
+        edges, edirs = [], []
+        for x in ch.units:
+            edges += units[x].edges
+            edirs += units[x].edirs
+        ch.edges, ch.edirs = edges, edirs
+        return ch
+
+    monkeypatch.setattr(U, "_order_chain", forwards)
+    assert not _arc_continuous(U.hierarchy_chains(verts, quads, seeds)[1], ev)
