@@ -130,9 +130,13 @@ void hdgmg_umesh_default_opts(hdgmg_opts* opts);
 
 /* Create a context on the current device: builds the plan, uploads it and
  * allocates every buffer.  Options used: m_fine, m_growth, m_max,
- * local_corr, omega, krylov (NONE or CG; GMRES: EINVAL), max_it, rtol
- * (opts NULL: hdgmg_umesh_default_opts).
- * precision must be FP64 and smoother BLOCK_JACOBI (EINVAL otherwise).
+ * local_corr, omega, krylov (NONE or CG; GMRES: EINVAL), max_it, rtol,
+ * precision (opts NULL: hdgmg_umesh_default_opts).  precision FP64: the
+ * whole path in FP64; FP32: the V-cycle on FP32 copies of every level
+ * operator, block-Jacobi inverse, transfer block and the coarsest inverse,
+ * inside the FP64 outer iteration (FP64 operator, residual, dot products);
+ * FP32_IR and BF16: EINVAL.  smoother must be BLOCK_JACOBI (EINVAL
+ * otherwise).
  * EINVAL also when a macro-element's local system exceeds 160 unknowns, a
  * macro-element has more than 64 macro-edges, or the coarsest level exceeds
  * 1024 unknowns.  stream: a cudaStream_t (NULL =
@@ -173,7 +177,8 @@ hdgmg_status hdgmg_umesh_element_matrices(const hdgmg_umesh* ctx, int32_t level,
 hdgmg_status hdgmg_umesh_apply(hdgmg_umesh* ctx, int32_t level, const double* x,
                                double* y);
 
-/* z = B r: one V-cycle of Algorithm 1 on the finest level (device). */
+/* z = B r: one V-cycle of Algorithm 1 on the finest level (device, FP64 in
+ * and out; the cycle itself in the context's precision). */
 hdgmg_status hdgmg_umesh_vcycle(hdgmg_umesh* ctx, const double* r, double* z);
 
 void hdgmg_umesh_destroy(hdgmg_umesh* ctx);

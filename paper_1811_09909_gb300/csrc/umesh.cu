@@ -393,23 +393,23 @@ __global__ void __launch_bounds__(128) u_recover_kernel(
 // t[e][i] = sum_j A_e[j][i] x(slot j) on a mesh level (4 edges of ND modes per
 // element), one thread per row, fully unrolled so that every load of a thread
 // is in flight at once (consecutive threads read consecutive entries)
-template <int ND>
+template <typename T, int ND>
 __global__ void __launch_bounds__(128) u_elem_matvec_mesh_kernel(int n_el, const int* __restrict__ el_slot,
-                                                                 const double* __restrict__ A,
-                                                                 const double* __restrict__ x,
-                                                                 double* __restrict__ t) {
+                                                                 const T* __restrict__ A,
+                                                                 const T* __restrict__ x,
+                                                                 T* __restrict__ t) {
   constexpr int NDM = 4 * ND;
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (long long)n_el * NDM) return;
   const int e = (int)(id / NDM), i = (int)(id % NDM);
-  const double* Ae = A + (size_t)e * NDM * NDM + i;
+  const T* Ae = A + (size_t)e * NDM * NDM + i;
   int b[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) b[s] = __ldg(el_slot + 4 * e + s);
-  double xv[NDM];
+  T xv[NDM];
 #pragma unroll
-  for (int j = 0; j < NDM; ++j) xv[j] = b[j / ND] >= 0 ? __ldg(x + (size_t)b[j / ND] * ND + j % ND) : 0.0;
-  double s0 = 0.0, s1 = 0.0;
+  for (int j = 0; j < NDM; ++j) xv[j] = b[j / ND] >= 0 ? __ldg(x + (size_t)b[j / ND] * ND + j % ND) : T(0);
+  T s0 = 0, s1 = 0;
 #pragma unroll
   for (int j = 0; j < NDM; j += 2) {
     s0 += __ldg(Ae + (size_t)j * NDM) * xv[j];
@@ -420,13 +420,14 @@ __global__ void __launch_bounds__(128) u_elem_matvec_mesh_kernel(int n_el, const
 
 // mesh levels, second half: per edge block y = t(side 0) + t(side 1); SUM:
 // out = y; RES: out = r - y; SMOOTH: out = x + omega Dinv (r - y)
+template <typename T>
 __global__ void u_edge_kernel(int n_blk, int nd, const int* __restrict__ t0, const int* __restrict__ t1,
-                              const double* __restrict__ t, const double* __restrict__ x,
-                              const double* __restrict__ r, const double* __restrict__ Dinv, double omega,
-                              int mode, double* __restrict__ out) {
+                              const T* __restrict__ t, const T* __restrict__ x,
+                              const T* __restrict__ r, const T* __restrict__ Dinv, double omega,
+                              int mode, T* __restrict__ out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blk) return;
-  double y[9];
+  T y[9];
   const size_t o0 = (size_t)t0[b] * nd, o1 = (size_t)t1[b] * nd;
   for (int k = 0; k < nd; ++k) y[k] = t[o0 + k] + t[o1 + k];
   if (mode == 0) {
@@ -435,11 +436,11 @@ __global__ void u_edge_kernel(int n_blk, int nd, const int* __restrict__ t0, con
     for (int k = 0; k < nd; ++k) out[(size_t)b * nd + k] = r[(size_t)b * nd + k] - y[k];
   } else {
     for (int k = 0; k < nd; ++k) y[k] = r[(size_t)b * nd + k] - y[k];
-    const double* D = Dinv + (size_t)b * nd * nd;
+    const T* D = Dinv + (size_t)b * nd * nd;
     for (int k = 0; k < nd; ++k) {
-      double s = 0.0;
+      T s = 0;
       for (int l = 0; l < nd; ++l) s += D[k * nd + l] * y[l];
-      out[(size_t)b * nd + k] = x[(size_t)b * nd + k] + omega * s;
+      out[(size_t)b * nd + k] = x[(size_t)b * nd + k] + (T)omega * s;
     }
   }
 }
@@ -453,28 +454,28 @@ enum { U_SUM = 0, U_RES = 1, U_SMOOTH = 2 };
 // read once.  Then SUM: out = y; RES: out = r - y; SMOOTH: out = x + omega
 // Dinv (r - y) on the block (the block's rows meet in shared memory).  out
 // never aliases x: a smoothing step reads every neighbour's old value.
-template <int ND, int NU>
+template <typename T, int ND, int NU>
 __global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const int* __restrict__ el_slot,
                                                      const int* __restrict__ t0, const int* __restrict__ t1,
-                                                     const double* __restrict__ A, const double* __restrict__ x,
-                                                     const double* __restrict__ r, const double* __restrict__ Dinv,
-                                                     double omega, int mode, double* __restrict__ out) {
+                                                     const T* __restrict__ A, const T* __restrict__ x,
+                                                     const T* __restrict__ r, const T* __restrict__ Dinv,
+                                                     double omega, int mode, T* __restrict__ out) {
   constexpr int UPB = 128 / ND;
-  __shared__ double ys[UPB * ND];
+  __shared__ T ys[UPB * ND];
   const int nu = NU > 0 ? NU : nu_rt;
   const int ndm = nu * ND;
   const int lu = threadIdx.x / ND, k = threadIdx.x % ND;
   const int b = blockIdx.x * UPB + lu;
   const bool act = lu < UPB && b < n_blk;
-  double y = 0.0;
+  T y = 0;
   if (act) {
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int ts = side == 0 ? __ldg(t0 + b) : __ldg(t1 + b);
       const int el = ts / nu, sl = ts % nu;
-      const double* Ae = A + (size_t)el * ndm * ndm + sl * ND + k;
+      const T* Ae = A + (size_t)el * ndm * ndm + sl * ND + k;
       const int* sls = el_slot + (size_t)el * nu;
-      double s = 0.0;
+      T s = 0;
       if (NU > 0) {
 #pragma unroll
         for (int j = 0; j < NU * ND; ++j) {
@@ -498,21 +499,22 @@ __global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const
     if (act) out[(size_t)b * ND + k] = r[(size_t)b * ND + k] - y;
     return;
   }
-  if (lu < UPB) ys[lu * ND + k] = act ? r[(size_t)b * ND + k] - y : 0.0;
+  if (lu < UPB) ys[lu * ND + k] = act ? r[(size_t)b * ND + k] - y : T(0);
   __syncthreads();
   if (act) {
-    const double* D = Dinv + (size_t)b * ND * ND + k * ND;
-    double s = 0.0;
+    const T* D = Dinv + (size_t)b * ND * ND + k * ND;
+    T s = 0;
 #pragma unroll
     for (int l = 0; l < ND; ++l) s += D[l] * ys[lu * ND + l];
-    out[(size_t)b * ND + k] = x[(size_t)b * ND + k] + omega * s;
+    out[(size_t)b * ND + k] = x[(size_t)b * ND + k] + (T)omega * s;
   }
 }
 
 // per unknown block: out = t(side 0) + t(side 1) (the element-slot sums of
 // the right-hand side and of the restriction)
+template <typename T>
 __global__ void u_unit_kernel(int n_blk, int nd, const int* __restrict__ t0, const int* __restrict__ t1,
-                              const double* __restrict__ t, double* __restrict__ out) {
+                              const T* __restrict__ t, T* __restrict__ out) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blk) return;
   const size_t o0 = (size_t)t0[b] * nd, o1 = (size_t)t1[b] * nd;
@@ -520,15 +522,16 @@ __global__ void u_unit_kernel(int n_blk, int nd, const int* __restrict__ t0, con
 }
 
 // e = omega Dinv r (first smoothing step from zero)
-__global__ void u_bj_first_kernel(int n_blk, int nd, const double* __restrict__ Dinv,
-                                  const double* __restrict__ r, double omega, double* __restrict__ e) {
+template <typename T>
+__global__ void u_bj_first_kernel(int n_blk, int nd, const T* __restrict__ Dinv,
+                                  const T* __restrict__ r, double omega, T* __restrict__ e) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= n_blk) return;
-  const double* D = Dinv + (size_t)b * nd * nd;
+  const T* D = Dinv + (size_t)b * nd * nd;
   for (int k = 0; k < nd; ++k) {
-    double s = 0.0;
+    T s = 0;
     for (int l = 0; l < nd; ++l) s += D[k * nd + l] * r[(size_t)b * nd + l];
-    e[(size_t)b * nd + k] = omega * s;
+    e[(size_t)b * nd + k] = (T)omega * s;
   }
 }
 
@@ -574,13 +577,15 @@ __global__ void u_pcoarsen_kernel(int E, int P1, const double* __restrict__ A, d
   A1[id] = A[(size_t)e * NT * NT + (size_t)rf * NT + cf];
 }
 
-__global__ void u_prestrict_kernel(int n_blk, int P1, const double* __restrict__ res, double* __restrict__ r1) {
+template <typename T>
+__global__ void u_prestrict_kernel(int n_blk, int P1, const T* __restrict__ res, T* __restrict__ r1) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= 2 * n_blk) return;
   r1[id] = res[(size_t)(id / 2) * P1 + id % 2];
 }
 
-__global__ void u_pprolong_kernel(int n_blk, int P1, const double* __restrict__ e1, double* __restrict__ e) {
+template <typename T>
+__global__ void u_pprolong_kernel(int n_blk, int P1, const T* __restrict__ e1, T* __restrict__ e) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= 2 * n_blk) return;
   e[(size_t)(id / 2) * P1 + id % 2] += e1[id];
@@ -589,15 +594,16 @@ __global__ void u_pprolong_kernel(int n_blk, int P1, const double* __restrict__ 
 // ---------------------------------------------------------------------------
 // h-coarsening (one block per coarse macro-element)
 // ---------------------------------------------------------------------------
+template <typename T>
 struct UHArgs {
   int n_E, nu_f, nd_f, nu_c;
   const int *loc_ptr, *loc_blk, *nI, *own, *ch_ptr, *ch_el, *ch_map, *bs_ptr;
   const long long *J_off, *AI_off, *Y_off;
-  const double* J;
-  double *AIinv, *Y;
+  const T* J;
+  T *AIinv, *Y;
 };
 
-__global__ void __launch_bounds__(256) u_agglomerate_kernel(UHArgs h, const double* __restrict__ Af,
+__global__ void __launch_bounds__(256) u_agglomerate_kernel(UHArgs<double> h, const double* __restrict__ Af,
                                                             double* __restrict__ Ac, int* __restrict__ err) {
   extern __shared__ double A[];                     // [n][n], n = 2 nloc
   const int E = blockIdx.x, tid = threadIdx.x;
@@ -707,32 +713,34 @@ __global__ void __launch_bounds__(256) u_agglomerate_kernel(UHArgs h, const doub
 }
 
 // e_I += A_II^-1 res_I (local correction, eq. localCorrection)
-__global__ void u_localcorr_kernel(UHArgs h, const double* __restrict__ res, double* __restrict__ e) {
-  __shared__ double rI[kMaxLoc];
+template <typename T>
+__global__ void u_localcorr_kernel(UHArgs<T> h, const T* __restrict__ res, T* __restrict__ e) {
+  __shared__ T rI[kMaxLoc];
   const int E = blockIdx.x, tid = threadIdx.x;
   const int l0 = h.loc_ptr[E], nI2 = 2 * h.nI[E];
   for (int i = tid; i < nI2; i += blockDim.x) rI[i] = res[(size_t)h.loc_blk[l0 + i / 2] * 2 + i % 2];
   __syncthreads();
-  const double* AI = h.AIinv + h.AI_off[E];
+  const T* AI = h.AIinv + h.AI_off[E];
   for (int i = tid; i < nI2; i += blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     for (int j = 0; j < nI2; ++j) s += AI[(size_t)j * nI2 + i] * rI[j];
     e[(size_t)h.loc_blk[l0 + i / 2] * 2 + i % 2] += s;
   }
 }
 
 // tc[E][c] = (J_E^T (Y^T res_I + own res_B))_c: E's share of Q_{k-1} res
-__global__ void u_restrict_kernel(UHArgs h, const double* __restrict__ res, double* __restrict__ tc) {
-  __shared__ double rI[kMaxLoc], vB[kMaxLoc];
+template <typename T>
+__global__ void u_restrict_kernel(UHArgs<T> h, const T* __restrict__ res, T* __restrict__ tc) {
+  __shared__ T rI[kMaxLoc], vB[kMaxLoc];
   const int E = blockIdx.x, tid = threadIdx.x;
   const int l0 = h.loc_ptr[E], nloc = h.loc_ptr[E + 1] - l0;
   const int nI2 = 2 * h.nI[E], nB2 = 2 * nloc - nI2;
   for (int i = tid; i < nI2; i += blockDim.x) rI[i] = res[(size_t)h.loc_blk[l0 + i / 2] * 2 + i % 2];
   __syncthreads();
-  const double* Y = h.Y + h.Y_off[E];
+  const T* Y = h.Y + h.Y_off[E];
   for (int b = tid; b < nB2; b += blockDim.x) {
     const int lb = h.nI[E] + b / 2;
-    double s = h.own[l0 + lb] ? res[(size_t)h.loc_blk[l0 + lb] * 2 + b % 2] : 0.0;
+    T s = h.own[l0 + lb] ? res[(size_t)h.loc_blk[l0 + lb] * 2 + b % 2] : T(0);
     for (int i = 0; i < nI2; ++i) s += Y[(size_t)i * nB2 + b] * rI[i];
     vB[b] = s;
   }
@@ -741,9 +749,9 @@ __global__ void u_restrict_kernel(UHArgs h, const double* __restrict__ res, doub
   int nc = 0;
   while (nc < h.nu_c && bs[nc + 1] > bs[nc]) ++nc;
   const int nc2 = 2 * nc, ndm_c = 2 * h.nu_c;
-  const double* J = h.J + h.J_off[E];
+  const T* J = h.J + h.J_off[E];
   for (int c = tid; c < ndm_c; c += blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     if (c < nc2)
       for (int b = 2 * bs[c / 2]; b < 2 * bs[c / 2 + 1]; ++b) s += J[(size_t)b * nc2 + c] * vB[b];
     tc[(size_t)E * ndm_c + c] = s;
@@ -751,9 +759,10 @@ __global__ void u_restrict_kernel(UHArgs h, const double* __restrict__ res, doub
 }
 
 // w = J_E e_c;  e_I += Y w;  e_B += w on the blocks E owns (eq. n_1_Ik)
-__global__ void u_prolong_kernel(UHArgs h, const int* __restrict__ el_slot_c, const double* __restrict__ ec,
-                                 double* __restrict__ e) {
-  __shared__ double ecl[2 * 64], w[kMaxLoc];
+template <typename T>
+__global__ void u_prolong_kernel(UHArgs<T> h, const int* __restrict__ el_slot_c, const T* __restrict__ ec,
+                                 T* __restrict__ e) {
+  __shared__ T ecl[2 * 64], w[kMaxLoc];
   const int E = blockIdx.x, tid = threadIdx.x;
   const int l0 = h.loc_ptr[E], nloc = h.loc_ptr[E + 1] - l0;
   const int nI2 = 2 * h.nI[E], nB2 = 2 * nloc - nI2;
@@ -764,20 +773,20 @@ __global__ void u_prolong_kernel(UHArgs h, const int* __restrict__ el_slot_c, co
   for (int c = tid; c < nc2; c += blockDim.x)
     ecl[c] = ec[(size_t)el_slot_c[(size_t)E * h.nu_c + c / 2] * 2 + c % 2];
   __syncthreads();
-  const double* J = h.J + h.J_off[E];
+  const T* J = h.J + h.J_off[E];
   for (int b = tid; b < nB2; b += blockDim.x) {
     int s = 0;
     while (b >= 2 * bs[s + 1]) ++s;
-    double v = 0.0;
+    T v = 0;
     for (int c = 2 * s; c < 2 * s + 2; ++c) v += J[(size_t)b * nc2 + c] * ecl[c];
     w[b] = v;
     const int lb = h.nI[E] + b / 2;
     if (h.own[l0 + lb]) e[(size_t)h.loc_blk[l0 + lb] * 2 + b % 2] += v;
   }
   __syncthreads();
-  const double* Y = h.Y + h.Y_off[E];
+  const T* Y = h.Y + h.Y_off[E];
   for (int i = tid; i < nI2; i += blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     for (int b = 0; b < nB2; ++b) s += Y[(size_t)i * nB2 + b] * w[b];
     e[(size_t)h.loc_blk[l0 + i / 2] * 2 + i % 2] += s;
   }
@@ -835,11 +844,12 @@ __global__ void __launch_bounds__(1024) u_coarse_setup_kernel(int n, int n_el, i
   if (tid == 0 && bad) atomicExch(err, 1);
 }
 
-__global__ void u_dense_matvec_kernel(int n, const double* __restrict__ M, const double* __restrict__ x,
-                                      double* __restrict__ y) {
+template <typename T>
+__global__ void u_dense_matvec_kernel(int n, const T* __restrict__ M, const T* __restrict__ x,
+                                      T* __restrict__ y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
+  T s = 0;
   for (int j = 0; j < n; ++j) s += M[(size_t)j * n + i] * x[j];
   y[i] = s;
 }
@@ -913,14 +923,36 @@ struct ULevelDev {
   int *el_slot = nullptr, *blk_t0 = nullptr, *blk_t1 = nullptr;
   double *A = nullptr, *Dinv = nullptr;
   double *r = nullptr, *e = nullptr, *res = nullptr, *t = nullptr, *tmp = nullptr;
+  // FP32 copies for the FP32 V-cycle (PREC_FP32 only)
+  float *A32 = nullptr, *Dinv32 = nullptr;
+  float *r32 = nullptr, *e32 = nullptr, *res32 = nullptr, *t32 = nullptr, *tmp32 = nullptr;
   long long n() const { return (long long)n_blk * nd; }
 };
 
-struct UHDev {
-  UHArgs a{};
-  int nloc_max = 0;
-  std::vector<void*> bufs;
+// the buffers of one level in the V-cycle's precision
+template <typename T>
+struct LV {
+  T *A, *Dinv, *r, *e, *res, *t, *tmp;
 };
+template <typename T>
+LV<T> lv(ULevelDev& L);
+template <>
+LV<double> lv<double>(ULevelDev& L) { return {L.A, L.Dinv, L.r, L.e, L.res, L.t, L.tmp}; }
+template <>
+LV<float> lv<float>(ULevelDev& L) { return {L.A32, L.Dinv32, L.r32, L.e32, L.res32, L.t32, L.tmp32}; }
+
+struct UHDev {
+  UHArgs<double> a{};
+  UHArgs<float> a32{};
+  int nloc_max = 0;
+  size_t jn = 0, ain = 0, yn = 0;
+};
+template <typename T>
+UHArgs<T>& ha(UHDev& h);
+template <>
+UHArgs<double>& ha<double>(UHDev& h) { return h.a; }
+template <>
+UHArgs<float>& ha<float>(UHDev& h) { return h.a32; }
 
 hdgmg_status fail_u(hdgmg_status st, const std::string& msg) {
   set_last_error(msg);
@@ -943,6 +975,7 @@ struct hdgmg_umesh {
   std::vector<ULevelDev> L;
   std::vector<UHDev> H;
   double *cD = nullptr, *cInv = nullptr;
+  float* cInv32 = nullptr;
   int n_coarse = 0;
   double *x = nullptr, *b = nullptr, *pd = nullptr, *Ap = nullptr, *z = nullptr, *rr = nullptr;
   double *scal = nullptr, *partial = nullptr, *hbuf = nullptr;
@@ -1021,113 +1054,133 @@ void launch_recover_p(hdgmg_umesh* c, const double* lam, const double* f, double
                                                lam, u, q);
 }
 
-template <int ND, int NU>
-void pull(hdgmg_umesh* c, const ULevelDev& L, const double* x, double* y, int mode, const double* r) {
-  constexpr int UPB = 128 / ND;
-  u_pull_kernel<ND, NU><<<nblk(L.n_blk, UPB), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1, L.A,
-                                                               x, r, L.Dinv, c->opts.omega, mode, y);
-}
+template <typename T>
+T* coarse_inverse(hdgmg_umesh* c);
+template <>
+double* coarse_inverse<double>(hdgmg_umesh* c) { return c->cInv; }
+template <>
+float* coarse_inverse<float>(hdgmg_umesh* c) { return c->cInv32; }
 
-template <int ND>
-void mesh_matvec(hdgmg_umesh* c, const ULevelDev& L, const double* x) {
-  u_elem_matvec_mesh_kernel<ND><<<nblk((long long)L.n_el * 4 * ND, 128), 128, 0, c->s>>>(L.n_el, L.el_slot, L.A, x,
-                                                                                       L.t);
+template <typename T, int ND>
+void mesh_matvec(hdgmg_umesh* c, ULevelDev& L, const T* x) {
+  const LV<T> v = lv<T>(L);
+  u_elem_matvec_mesh_kernel<T, ND><<<nblk((long long)L.n_el * 4 * ND, 128), 128, 0, c->s>>>(L.n_el, L.el_slot, v.A,
+                                                                                          x, v.t);
 }
 
 // y = A_k x (SUM), y = r - A_k x (RES) or y = x + omega Dinv (r - A_k x)
-// (SMOOTH; y never aliases x).  Mesh levels stream their element operators
-// from HBM: one thread per element row (coalesced) into the slot buffer, then
-// the edge sums.  Macro-element levels are small and latency-bound: one pass
-// pulled per macro-edge.
-void level_matvec(hdgmg_umesh* c, int k, const double* x, double* y, int mode, const double* r) {
+// (SMOOTH; y never aliases x), in precision T.  Mesh levels stream their
+// element operators from HBM: one thread per element row (coalesced) into the
+// slot buffer, then the edge sums.  Macro-element levels are small and
+// latency-bound: one pass pulled per macro-edge.
+template <typename T>
+void level_matvec(hdgmg_umesh* c, int k, const T* x, T* y, int mode, const T* r) {
   ULevelDev& L = c->L[k];
   if (L.n_blk == 0) return;
+  const LV<T> v = lv<T>(L);
   if (k <= c->plan.first_h && L.nu == 4) {
     note_launch();
     switch (L.nd) {
-      case 2: mesh_matvec<2>(c, L, x); break;
-      case 3: mesh_matvec<3>(c, L, x); break;
-      case 4: mesh_matvec<4>(c, L, x); break;
-      case 5: mesh_matvec<5>(c, L, x); break;
-      case 6: mesh_matvec<6>(c, L, x); break;
-      case 7: mesh_matvec<7>(c, L, x); break;
-      case 8: mesh_matvec<8>(c, L, x); break;
-      default: mesh_matvec<9>(c, L, x); break;
+      case 2: mesh_matvec<T, 2>(c, L, x); break;
+      case 3: mesh_matvec<T, 3>(c, L, x); break;
+      case 4: mesh_matvec<T, 4>(c, L, x); break;
+      case 5: mesh_matvec<T, 5>(c, L, x); break;
+      case 6: mesh_matvec<T, 6>(c, L, x); break;
+      case 7: mesh_matvec<T, 7>(c, L, x); break;
+      case 8: mesh_matvec<T, 8>(c, L, x); break;
+      default: mesh_matvec<T, 9>(c, L, x); break;
     }
     note_launch();
-    u_edge_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.blk_t0, L.blk_t1, L.t, x, r, L.Dinv,
-                                                        c->opts.omega, mode, y);
+    u_edge_kernel<T><<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.blk_t0, L.blk_t1, v.t, x, r, v.Dinv,
+                                                           c->opts.omega, mode, y);
   } else {
     note_launch();
-    pull<2, 0>(c, L, x, y, mode, r);
+    u_pull_kernel<T, 2, 0><<<nblk(L.n_blk, 64), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1, v.A,
+                                                                x, r, v.Dinv, c->opts.omega, mode, y);
   }
 }
 
-// e = B_k r (Algorithm 1)
-void vcycle(hdgmg_umesh* c, int k, const double* r, double* e) {
+// e = B_k r (Algorithm 1) in precision T
+template <typename T>
+void vcycle(hdgmg_umesh* c, int k, const T* r, T* e) {
   ULevelDev& L = c->L[k];
   const int nl = (int)c->L.size();
   if (k == nl - 1) {
     if (c->n_coarse == 0) return;
     note_launch();
-    u_dense_matvec_kernel<<<nblk(c->n_coarse, 128), 128, 0, c->s>>>(c->n_coarse, c->cInv, r, e);
+    u_dense_matvec_kernel<T><<<nblk(c->n_coarse, 128), 128, 0, c->s>>>(c->n_coarse, coarse_inverse<T>(c), r, e);
     return;
   }
   const double om = c->opts.omega;
   if (L.n_blk == 0) return;
+  const LV<T> v = lv<T>(L);
   // step 2: pre-smoothing from zero; the steps alternate between e and tmp
   // and end in e
-  double* cur = ((L.m - 1) % 2 == 1) ? L.tmp : e;
+  T* cur = ((L.m - 1) % 2 == 1) ? v.tmp : e;
   note_launch();
-  u_bj_first_kernel<<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.Dinv, r, om, cur);
+  u_bj_first_kernel<T><<<nblk(L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, v.Dinv, r, om, cur);
   for (int it = 1; it < L.m; ++it) {
-    double* nxt = cur == e ? L.tmp : e;
-    level_matvec(c, k, cur, nxt, U_SMOOTH, r);
+    T* nxt = cur == e ? v.tmp : e;
+    level_matvec<T>(c, k, cur, nxt, U_SMOOTH, r);
     cur = nxt;
   }
   const bool hlev = k >= c->plan.first_h;
   const int lc = c->opts.local_corr;
   UHDev* H = hlev ? &c->H[k - c->plan.first_h] : nullptr;
   if (hlev && (lc == HDGMG_LC_PRE || lc == HDGMG_LC_BOTH)) {      // step 3
-    level_matvec(c, k, e, L.res, U_RES, r);
+    level_matvec<T>(c, k, e, v.res, U_RES, r);
     note_launch();
-    u_localcorr_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, e);
+    u_localcorr_kernel<T><<<H->a.n_E, 64, 0, c->s>>>(ha<T>(*H), v.res, e);
   }
-  level_matvec(c, k, e, L.res, U_RES, r);                         // step 4
+  level_matvec<T>(c, k, e, v.res, U_RES, r);                      // step 4
   ULevelDev& C = c->L[k + 1];
+  const LV<T> cv = lv<T>(C);
   if (hlev) {
     note_launch();
-    u_restrict_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, C.t);
+    u_restrict_kernel<T><<<H->a.n_E, 64, 0, c->s>>>(ha<T>(*H), v.res, cv.t);
     if (C.n_blk > 0) {
       note_launch();
-      u_unit_kernel<<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, C.t, C.r);
+      u_unit_kernel<T><<<nblk(C.n_blk, 128), 128, 0, c->s>>>(C.n_blk, 2, C.blk_t0, C.blk_t1, cv.t, cv.r);
     }
   } else {
     note_launch();
-    u_prestrict_kernel<<<nblk(2LL * L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, L.res, C.r);
+    u_prestrict_kernel<T><<<nblk(2LL * L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, v.res, cv.r);
   }
-  vcycle(c, k + 1, C.r, C.e);
+  vcycle<T>(c, k + 1, cv.r, cv.e);
   if (hlev) {
     note_launch();
-    u_prolong_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, C.el_slot, C.e, e);
+    u_prolong_kernel<T><<<H->a.n_E, 64, 0, c->s>>>(ha<T>(*H), C.el_slot, cv.e, e);
   } else {
     note_launch();
-    u_pprolong_kernel<<<nblk(2LL * L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, C.e, e);
+    u_pprolong_kernel<T><<<nblk(2LL * L.n_blk, 128), 128, 0, c->s>>>(L.n_blk, L.nd, cv.e, e);
   }
   if (hlev && lc == HDGMG_LC_BOTH) {                              // step 5
-    level_matvec(c, k, e, L.res, U_RES, r);
+    level_matvec<T>(c, k, e, v.res, U_RES, r);
     note_launch();
-    u_localcorr_kernel<<<H->a.n_E, 64, 0, c->s>>>(H->a, L.res, e);
+    u_localcorr_kernel<T><<<H->a.n_E, 64, 0, c->s>>>(ha<T>(*H), v.res, e);
   }
   cur = e;                                                        // step 6
   if (L.m % 2 == 1) {
-    cudaMemcpyAsync(L.tmp, e, (size_t)L.n() * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
-    cur = L.tmp;
+    cudaMemcpyAsync(v.tmp, e, (size_t)L.n() * sizeof(T), cudaMemcpyDeviceToDevice, c->s);
+    cur = v.tmp;
   }
   for (int it = 0; it < L.m; ++it) {
-    double* nxt = cur == e ? L.tmp : e;
-    level_matvec(c, k, cur, nxt, U_SMOOTH, r);
+    T* nxt = cur == e ? v.tmp : e;
+    level_matvec<T>(c, k, cur, nxt, U_SMOOTH, r);
     cur = nxt;
+  }
+}
+
+// z = B r on the finest level (FP64 in and out), the cycle in the context's
+// precision: FP32 levels behind an FP64 -> FP32 -> FP64 hand-over
+void apply_B(hdgmg_umesh* c, const double* r, double* z) {
+  if (c->opts.precision == HDGMG_PREC_FP32) {
+    ULevelDev& L0 = c->L[0];
+    launch_convert<double, float>(c->s, L0.n(), r, L0.r32);
+    vcycle<float>(c, 0, L0.r32, L0.e32);
+    launch_convert<float, double>(c->s, L0.n(), L0.e32, z);
+  } else {
+    vcycle<double>(c, 0, r, z);
   }
 }
 
@@ -1152,12 +1205,12 @@ double read_scalar(hdgmg_umesh* c, const double* d) {
 // one PCG iteration: alpha, x, r, |r|^2 (scal[5]), z = B r, beta, p
 void pcg_body(hdgmg_umesh* c) {
   const long long n = c->L[0].n();
-  level_matvec(c, 0, c->pd, c->Ap, U_SUM, nullptr);
+  level_matvec<double>(c, 0, c->pd, c->Ap, U_SUM, nullptr);
   launch_dot(c->s, n, c->pd, c->Ap, c->partial, c->scal + 1);
   launch_cg_scalars(c->s, c->scal, 0);
   launch_cg_update(c->s, n, c->scal, c->x, c->rr, c->pd, c->Ap);
   launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
-  vcycle(c, 0, c->rr, c->z);
+  apply_B(c, c->rr, c->z);
   launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 3);
   launch_cg_scalars(c->s, c->scal, 1);
   launch_cg_direction(c->s, n, c->scal, c->z, c->pd);
@@ -1166,10 +1219,10 @@ void pcg_body(hdgmg_umesh* c) {
 // one fixed-point iteration x += B (b - A x), then |b - A x|^2 (scal[5])
 void fp_body(hdgmg_umesh* c) {
   const long long n = c->L[0].n();
-  level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
-  vcycle(c, 0, c->rr, c->z);
+  level_matvec<double>(c, 0, c->x, c->rr, U_RES, c->b);
+  apply_B(c, c->rr, c->z);
   launch_axpby(c->s, n, 1.0, c->z, 1.0, c->x);
-  level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
+  level_matvec<double>(c, 0, c->x, c->rr, U_RES, c->b);
   launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
 }
 
@@ -1217,7 +1270,8 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
   } else {
     hdgmg_umesh_default_opts(&o);
   }
-  if (o.precision != HDGMG_PREC_FP64) return fail_u(HDGMG_EINVAL, "the unstructured path runs in FP64 only");
+  if (o.precision != HDGMG_PREC_FP64 && o.precision != HDGMG_PREC_FP32)
+    return fail_u(HDGMG_EINVAL, "the unstructured path runs the V-cycle in FP64 or FP32");
   if (o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) return fail_u(HDGMG_EINVAL, "the unstructured path smooths by block-Jacobi");
   if (o.krylov != HDGMG_KRYLOV_NONE && o.krylov != HDGMG_KRYLOV_CG)
     return fail_u(HDGMG_EINVAL, "the unstructured path supports krylov NONE or CG");
@@ -1276,6 +1330,11 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
          dalloc(c, &d.r, (size_t)d.n()) && dalloc(c, &d.e, (size_t)d.n()) && dalloc(c, &d.res, (size_t)d.n()) &&
          dalloc(c, &d.tmp, (size_t)d.n()) &&
          dalloc(c, &d.t, (size_t)d.n_el * d.ndm);
+    if (ok && o.precision == HDGMG_PREC_FP32)
+      ok = dalloc(c, &d.A32, (size_t)d.n_el * d.ndm * d.ndm) && dalloc(c, &d.Dinv32, (size_t)d.n_blk * d.nd * d.nd) &&
+           dalloc(c, &d.r32, (size_t)d.n()) && dalloc(c, &d.e32, (size_t)d.n()) &&
+           dalloc(c, &d.res32, (size_t)d.n()) && dalloc(c, &d.tmp32, (size_t)d.n()) &&
+           dalloc(c, &d.t32, (size_t)d.n_el * d.ndm);
     c->L.push_back(d);
   }
   ok = ok && upload(c, &c->unit_blk0, P.levels[0].unit_blk);
@@ -1319,10 +1378,23 @@ hdgmg_status hdgmg_umesh_create(hdgmg_umesh** out, const hdgmg_umesh_problem* pr
     d.a.loc_ptr = lp; d.a.loc_blk = lb; d.a.nI = nI; d.a.own = own; d.a.ch_ptr = cp; d.a.ch_el = ce;
     d.a.ch_map = cm; d.a.bs_ptr = bsp; d.a.J_off = jo; d.a.AI_off = ao; d.a.Y_off = yo; d.a.J = J;
     d.a.AIinv = AI; d.a.Y = Y;
+    d.jn = h.J.size();
+    d.ain = (size_t)h.AI_off.back();
+    d.yn = (size_t)h.Y_off.back();
+    d.a32.n_E = d.a.n_E; d.a32.nu_f = d.a.nu_f; d.a32.nd_f = d.a.nd_f; d.a32.nu_c = d.a.nu_c;
+    d.a32.loc_ptr = lp; d.a32.loc_blk = lb; d.a32.nI = nI; d.a32.own = own; d.a32.ch_ptr = cp; d.a32.ch_el = ce;
+    d.a32.ch_map = cm; d.a32.bs_ptr = bsp; d.a32.J_off = jo; d.a32.AI_off = ao; d.a32.Y_off = yo;
+    if (o.precision == HDGMG_PREC_FP32) {
+      float *J32, *AI32, *Y32;
+      ok = dalloc(c, &J32, d.jn) && dalloc(c, &AI32, d.ain) && dalloc(c, &Y32, d.yn);
+      if (!ok) break;
+      d.a32.J = J32; d.a32.AIinv = AI32; d.a32.Y = Y32;
+    }
     c->H.push_back(d);
     c->agg_smem = std::max(c->agg_smem, (size_t)4 * h.nloc_max * h.nloc_max * sizeof(double));
   }
   const long long nf = c->L[0].n();
+  if (ok && o.precision == HDGMG_PREC_FP32) ok = dalloc(c, &c->cInv32, (size_t)c->n_coarse * c->n_coarse);
   ok = ok && dalloc(c, &c->cD, (size_t)c->n_coarse * c->n_coarse) &&
        dalloc(c, &c->cInv, (size_t)c->n_coarse * c->n_coarse) && dalloc(c, &c->x, nf) && dalloc(c, &c->b, nf) &&
        dalloc(c, &c->pd, nf) && dalloc(c, &c->Ap, nf) && dalloc(c, &c->z, nf) && dalloc(c, &c->rr, nf) &&
@@ -1386,6 +1458,21 @@ hdgmg_status hdgmg_umesh_setup(hdgmg_umesh* c, const double* log_kappa) {
   if (c->n_coarse > 0) note_launch();
   if (c->n_coarse > 0)
     u_coarse_setup_kernel<<<1, 1024, 0, c->s>>>(c->n_coarse, C.n_el, C.nu, C.el_slot, C.A, c->cD, c->cInv, c->err);
+  if (c->opts.precision == HDGMG_PREC_FP32) {     // the FP32 V-cycle's copies
+    for (size_t k = 0; k < c->L.size(); ++k) {
+      ULevelDev& L = c->L[k];
+      launch_convert<double, float>(c->s, (int64_t)L.n_el * L.ndm * L.ndm, L.A, L.A32);
+      if (k + 1 < c->L.size() && L.n_blk > 0)
+        launch_convert<double, float>(c->s, (int64_t)L.n_blk * L.nd * L.nd, L.Dinv, L.Dinv32);
+    }
+    for (UHDev& h : c->H) {
+      if (h.jn) launch_convert<double, float>(c->s, (int64_t)h.jn, h.a.J, const_cast<float*>(h.a32.J));
+      if (h.ain) launch_convert<double, float>(c->s, (int64_t)h.ain, h.a.AIinv, h.a32.AIinv);
+      if (h.yn) launch_convert<double, float>(c->s, (int64_t)h.yn, h.a.Y, h.a32.Y);
+    }
+    if (c->n_coarse > 0)
+      launch_convert<double, float>(c->s, (int64_t)c->n_coarse * c->n_coarse, c->cInv, c->cInv32);
+  }
   cudaEventRecord(c->ev1, c->s);
   hdgmg_status st = cuda_status("set-up");
   if (st != HDGMG_OK) return st;
@@ -1398,7 +1485,7 @@ hdgmg_status hdgmg_umesh_setup(hdgmg_umesh* c, const double* log_kappa) {
 hdgmg_status hdgmg_umesh_vcycle(hdgmg_umesh* c, const double* r, double* z) {
   if (!c || !r || !z) return fail_u(HDGMG_EINVAL, "null argument");
   if (!c->ready) return fail_u(HDGMG_EINVAL, "set-up required");
-  vcycle(c, 0, r, z);
+  apply_B(c, r, z);
   hdgmg_status st = cuda_status("vcycle");
   if (st == HDGMG_OK && cudaStreamSynchronize(c->s) != cudaSuccess) st = cuda_status("vcycle");
   return st;
@@ -1408,7 +1495,7 @@ hdgmg_status hdgmg_umesh_apply(hdgmg_umesh* c, int32_t level, const double* x, d
   if (!c || !x || !y) return fail_u(HDGMG_EINVAL, "null argument");
   if (!c->ready) return fail_u(HDGMG_EINVAL, "set-up required");
   if (level < 0 || level >= (int32_t)c->L.size()) return fail_u(HDGMG_EINVAL, "level out of range");
-  level_matvec(c, level, x, y, U_SUM, nullptr);
+  level_matvec<double>(c, level, x, y, U_SUM, nullptr);
   hdgmg_status st = cuda_status("apply");
   if (st == HDGMG_OK && cudaStreamSynchronize(c->s) != cudaSuccess) st = cuda_status("apply");
   return st;
@@ -1479,7 +1566,7 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
     if (!had) captured = c->g_nodes[gk];
     if (gk == 0) {
       cudaMemcpyAsync(c->rr, c->b, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);   // r = b
-      vcycle(c, 0, c->rr, c->z);
+      apply_B(c, c->rr, c->z);
       cudaMemcpyAsync(c->pd, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, c->s);
       launch_dot(c->s, n, c->rr, c->z, c->partial, c->scal + 0);
     }
@@ -1499,7 +1586,7 @@ hdgmg_status hdgmg_umesh_solve(hdgmg_umesh* c, const double* f, double* lam, dou
     }
   }
   // true residual
-  level_matvec(c, 0, c->x, c->rr, U_RES, c->b);
+  level_matvec<double>(c, 0, c->x, c->rr, U_RES, c->b);
   launch_dot(c->s, n, c->rr, c->rr, c->partial, c->scal + 5);
   rel = bb > 0 ? std::sqrt(read_scalar(c, c->scal + 5) / bb) : 0.0;
   note_launch();

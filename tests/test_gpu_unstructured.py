@@ -164,8 +164,8 @@ def test_large_mesh_sampled_elements_and_convergence():
 
 def test_invalid_options_are_rejected():
     v, q, sp, _, _ = W.example2(3, 2)
-    for kw in ({"krylov": hdgmg.KRYLOV_GMRES}, {"precision": hdgmg.PREC_FP32},
-               {"smoother": hdgmg.SMOOTH_POINT_JACOBI}):
+    for kw in ({"krylov": hdgmg.KRYLOV_GMRES}, {"precision": hdgmg.PREC_BF16},
+               {"precision": hdgmg.PREC_FP32_IR}, {"smoother": hdgmg.SMOOTH_POINT_JACOBI}):
         with pytest.raises(hdgmg.HdgmgError) as ei:
             um.USolver(v, q, 2, 1.0, sp, **kw)
         assert ei.value.status == -1
@@ -179,3 +179,26 @@ def test_breakdown_on_nan_kappa():
     with pytest.raises(hdgmg.HdgmgError) as ei:
         s.setup(_dev(logk))
     assert ei.value.status == -5
+
+
+def test_fp32_cycle_inside_fp64_pcg():
+    """PREC_FP32: the V-cycle on FP32 copies of every level, inside the FP64
+    PCG.  One cycle within 1e-4 of the FP64 cycle (FP32 rounding amplified by
+    the level conditioning); the solve reaches the same FP64 residual target
+    with at most two more iterations and the oracle's solution."""
+    v, q, sp, logk, f = W.example2(5, 3)
+    s64 = um.USolver(v, q, 3, 1.0, sp, rtol=1e-10)
+    s32 = um.USolver(v, q, 3, 1.0, sp, rtol=1e-10, precision=hdgmg.PREC_FP32)
+    for s in (s64, s32):
+        s.setup(_dev(logk))
+    r = _dev(np.random.default_rng(8).normal(size=s64.level_sizes(0)[0]))
+    z64, z32 = s64.vcycle(r), s32.vcycle(r)
+    rel = float(torch.linalg.norm(z32 - z64) / torch.linalg.norm(z64))
+    assert 0.0 < rel < 1e-4, rel
+    lam64, _, _, i64 = s64.solve(_dev(f), want_u=False, want_q=False)
+    lam32, _, _, i32 = s32.solve(_dev(f), want_u=False, want_q=False)
+    assert i64.converged and i32.converged and i32.rel_res <= 1e-10
+    assert i32.iters <= i64.iters + 2, (i32.iters, i64.iters)
+    pr = U.UHDGProblem(v, q, 3, 1.0, 1.0)
+    lam_o = pr.solve_direct(f)
+    assert np.abs(lam32.cpu().numpy().ravel() - lam_o).max() < 1e-8 * np.abs(lam_o).max()

@@ -114,7 +114,7 @@ def test_plan_edge_cases():
     assert inner[0, 2] == 1 and inner[0, 3] == 7    # starts at the lower free end
 
 
-@pytest.mark.parametrize("field,value", [("krylov", 2), ("precision", 1), ("smoother", 1), ("m_fine", 0),
+@pytest.mark.parametrize("field,value", [("krylov", 2), ("precision", 3), ("precision", 2), ("smoother", 1), ("m_fine", 0),
                                          ("omega", 0.0), ("local_corr", 7)])
 def test_create_rejects_unsupported_options_before_touching_the_gpu(field, value):
     import ctypes
