@@ -17,13 +17,16 @@
 // recovery.
 //
 // Levels are element-based: level vectors hold the macro-edges that carry
-// unknowns; y = A x is a gather-multiply per element (t = A_el x_el) and a
-// sum of the two sides of every macro-edge.  h-coarsening per coarse
+// unknowns, and y = A x sums the element products of the two sides of every
+// macro-edge.  Mesh levels compute the element products row by row into a
+// slot buffer and then sum per edge; macro-element levels pull each
+// macro-edge's rows from its two sides in one pass.  h-coarsening per coarse
 // macro-element E: assemble its children's operators, Cholesky of A_II,
 // Y = -A_II^-1 A_IB, S_B = A_BB + A_BI Y, A_E = J_E^T S_B J_E (eqs. n_1_Ik,
 // coarse).  The V-cycle is Algorithm 1 with block-Jacobi smoothing, the
 // local correction of eq. localCorrection, Q = [J^T Y^T, J^T] and
-// I = [Y J; J].
+// I = [Y J; J]; it runs in FP64 or on FP32 copies of every level (the outer
+// PCG, its operator and residual stay FP64).
 #include <cuda_runtime.h>
 
 #include <algorithm>
