@@ -129,3 +129,28 @@ def test_create_rejects_unsupported_options_before_touching_the_gpu(field, value
     h = ctypes.c_void_p()
     st = lib.hdgmg_umesh_create(ctypes.byref(h), ctypes.byref(pr.s), ctypes.byref(o), None)
     assert st == -1 and not h
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_plan_matches_oracle_on_random_meshes(case):
+    """Random jittered meshes (with and without holes) and random seed sets:
+    the library's partitions and macro-edges equal the oracle's exactly."""
+    rng = np.random.default_rng(100 + case)
+    nx, ny = int(rng.integers(3, 9)), int(rng.integers(3, 7))
+    holes = ((0.5, 0.5, 0.15),) if case % 2 else ()
+    v, q = W.umesh(nx, ny, 1.0, 1.0, 0.25, holes, int(rng.integers(0, 1000)))
+    seeds = rng.uniform(0.0, 1.0, size=(int(rng.integers(1, 9)), 2))
+    pl = um.Plan(v, q, 1 + case % 3, 1.0, seeds)
+    parts, levels = U.hierarchy_chains(v, q, seeds)
+    assert pl.n_parts == len(parts)
+    for r, part in enumerate(parts):
+        assert np.array_equal(pl.partition(r), part)
+    for t, lev in enumerate(levels):
+        info, items = pl.macro_edges(t)
+        ch = lev["units"]
+        assert len(info) == len(ch)
+        for c, x in enumerate(ch):
+            assert tuple(info[c, :5]) == (x.sides[0], x.sides[1], x.start, x.end, int(x.closed))
+            o, m = info[c, 5], len(x.edges)
+            assert np.array_equal(items[o:o + m, 0], x.edges)
+            assert np.array_equal(items[o:o + m, 1], x.edirs)
