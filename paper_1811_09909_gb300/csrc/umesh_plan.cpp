@@ -6,7 +6,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <map>
 #include <new>
 #include <numeric>
 #include <utility>
@@ -137,52 +136,78 @@ std::vector<int> split_partition(const std::vector<int>& part, const std::vector
 // Links the units of the finer level into the macro-edges of the coarser
 // partition (parent: finer macro-element -> coarser one).  interior receives
 // (unit, coarse macro) of the units inside one coarse macro-element.
+// Groups are formed by sorting (pair of coarse sides, unit); inside a group
+// the unit ends are sorted by vertex, and two units are linked at a vertex
+// where exactly two unit ends of the group meet.  Every decision depends only
+// on the indices, so the order of the work does not change the result.
 void link_units(const std::vector<UChain>& units, const std::vector<int>& parent,
                 std::vector<UChain>& chains, std::vector<std::pair<int, int>>& interior) {
-  std::map<std::pair<int, int>, std::vector<int>> groups;
+  struct KU { int a, b, u; };
+  std::vector<KU> sk;
+  sk.reserve(units.size());
   interior.clear();
   for (int ui = 0; ui < (int)units.size(); ++ui) {
     const UChain& u = units[ui];
     const int pa = parent[u.s0];
     const int pb = u.s1 >= 0 ? parent[u.s1] : -1;
     if (pa == pb) { interior.push_back({ui, pa}); continue; }
-    const std::pair<int, int> key = pb >= 0 ? std::make_pair(std::min(pa, pb), std::max(pa, pb))
-                                            : std::make_pair(pa, -1);
-    groups[key].push_back(ui);
+    if (pb >= 0) sk.push_back({std::min(pa, pb), std::max(pa, pb), ui});
+    else sk.push_back({pa, -1, ui});
   }
+  std::sort(sk.begin(), sk.end(), [](const KU& x, const KU& y) {
+    return x.a < y.a || (x.a == y.a && (x.b < y.b || (x.b == y.b && x.u < y.u)));
+  });
   chains.clear();
-  for (const auto& g : groups) {
-    const std::vector<int>& ulist = g.second;       // ascending
-    std::map<int, std::vector<int>> at;
-    for (int ui : ulist) {
-      at[units[ui].start].push_back(ui);
-      at[units[ui].end].push_back(ui);
+  std::vector<std::pair<int, int>> inc;          // (vertex, local unit) per unit end
+  std::vector<int> nlink, comp, stack;
+  std::vector<std::pair<int, int>> lk;           // [local][2]: (vertex, other local unit)
+  std::vector<char> seen;
+  for (size_t g0 = 0; g0 < sk.size();) {
+    size_t g1 = g0;
+    while (g1 < sk.size() && sk[g1].a == sk[g0].a && sk[g1].b == sk[g0].b) ++g1;
+    const int n = (int)(g1 - g0);
+    auto U = [&](int li) -> const UChain& { return units[sk[g0 + li].u]; };
+    auto uid = [&](int li) { return sk[g0 + li].u; };
+    inc.clear();
+    for (int li = 0; li < n; ++li) {
+      inc.push_back({U(li).start, li});
+      inc.push_back({U(li).end, li});
     }
-    std::map<int, std::vector<std::pair<int, int>>> links;   // unit -> (vertex, other)
-    for (const auto& kv : at)
-      if (kv.second.size() == 2 && kv.second[0] != kv.second[1]) {
-        links[kv.second[0]].push_back({kv.first, kv.second[1]});
-        links[kv.second[1]].push_back({kv.first, kv.second[0]});
+    std::sort(inc.begin(), inc.end());
+    nlink.assign(n, 0);
+    lk.assign(2 * (size_t)n, {-1, -1});
+    for (size_t k0 = 0; k0 < inc.size();) {
+      size_t k1 = k0;
+      while (k1 < inc.size() && inc[k1].first == inc[k0].first) ++k1;
+      if (k1 - k0 == 2 && inc[k0].second != inc[k0 + 1].second) {
+        const int x = inc[k0].second, y = inc[k0 + 1].second, v = inc[k0].first;
+        lk[2 * x + nlink[x]++] = {v, y};
+        lk[2 * y + nlink[y]++] = {v, x};
       }
-    std::map<int, bool> seen;
-    for (int u0 : ulist) {
-      if (seen[u0]) continue;
-      std::vector<int> comp, stack{u0};
-      seen[u0] = true;
+      k0 = k1;
+    }
+    seen.assign(n, 0);
+    for (int l0 = 0; l0 < n; ++l0) {              // ascending unit index
+      if (seen[l0]) continue;
+      comp.clear();
+      stack.assign(1, l0);
+      seen[l0] = 1;
       while (!stack.empty()) {
         const int x = stack.back();
         stack.pop_back();
         comp.push_back(x);
-        for (const auto& l : links[x])
-          if (!seen[l.second]) { seen[l.second] = true; stack.push_back(l.second); }
+        for (int q = 0; q < nlink[x]; ++q) {
+          const int y = lk[2 * x + q].second;
+          if (!seen[y]) { seen[y] = 1; stack.push_back(y); }
+        }
       }
-      std::sort(comp.begin(), comp.end());
+      std::sort(comp.begin(), comp.end());        // local order = unit order
       UChain ch;
-      ch.s0 = g.first.first;
-      ch.s1 = g.first.second;
+      ch.s0 = sk[g0].a;
+      ch.s1 = sk[g0].b;
       if (comp.size() == 1) {
-        const UChain& u = units[comp[0]];
-        ch.units = {comp[0]};
+        const UChain& u = U(comp[0]);
+        ch.units = {uid(comp[0])};
         ch.dirs = {1};
         ch.start = u.start;
         ch.end = u.end;
@@ -195,13 +220,13 @@ void link_units(const std::vector<UChain>& units, const std::vector<int>& parent
       }
       std::vector<int> ends;
       for (int x : comp)
-        if (links[x].size() == 1) ends.push_back(x);
+        if (nlink[x] == 1) ends.push_back(x);
       int first, v;
       bool closed;
       if (!ends.empty()) {
         auto free_vertex = [&](int x) {
-          const int w = links[x][0].first;
-          return units[x].start == w ? units[x].end : units[x].start;
+          const int w = lk[2 * x].first;
+          return U(x).start == w ? U(x).end : U(x).start;
         };
         const int fa = free_vertex(ends[0]), fb = free_vertex(ends[1]);
         if (fa != fb) {
@@ -214,26 +239,27 @@ void link_units(const std::vector<UChain>& units, const std::vector<int>& parent
       } else {
         v = -1;
         for (int x : comp)
-          for (const auto& l : links[x])
-            if (v < 0 || l.first < v) v = l.first;
+          for (int q = 0; q < nlink[x]; ++q)
+            if (v < 0 || lk[2 * x + q].first < v) v = lk[2 * x + q].first;
         first = -1;
         for (int x : comp)
-          for (const auto& l : links[x])
-            if (l.first == v && (first < 0 || l.second < first)) first = l.second;
+          for (int q = 0; q < nlink[x]; ++q)
+            if (lk[2 * x + q].first == v && (first < 0 || lk[2 * x + q].second < first)) first = lk[2 * x + q].second;
         closed = true;
       }
       int x = first, cur = v, prev = -1;
       ch.start = v;
+      std::vector<int> order;
       while (true) {
-        const UChain& u = units[x];
+        const UChain& u = U(x);
         const int d = u.start == cur ? 1 : -1;
-        ch.units.push_back(x);
+        order.push_back(x);
         ch.dirs.push_back(d);
         cur = d == 1 ? u.end : u.start;
         int nxt = -1;
-        for (const auto& l : links[x])
-          if (l.first == cur && l.second != prev) { nxt = l.second; break; }
-        if (closed && ch.units.size() == comp.size()) break;
+        for (int q = 0; q < nlink[x]; ++q)
+          if (lk[2 * x + q].first == cur && lk[2 * x + q].second != prev) { nxt = lk[2 * x + q].second; break; }
+        if (closed && order.size() == comp.size()) break;
         if (nxt < 0) break;
         prev = x;
         x = nxt;
@@ -242,8 +268,9 @@ void link_units(const std::vector<UChain>& units, const std::vector<int>& parent
       ch.end = cur;
       ch.closed = closed;
       double length = 0.0;
-      for (size_t i = 0; i < ch.units.size(); ++i) {
-        const UChain& u = units[ch.units[i]];
+      for (size_t i = 0; i < order.size(); ++i) {
+        const UChain& u = U(order[i]);
+        ch.units.push_back(uid(order[i]));
         if (ch.dirs[i] == 1) {
           ch.edges.insert(ch.edges.end(), u.edges.begin(), u.edges.end());
           ch.edirs.insert(ch.edirs.end(), u.edirs.begin(), u.edirs.end());
@@ -258,6 +285,7 @@ void link_units(const std::vector<UChain>& units, const std::vector<int>& parent
       ch.length = length;
       chains.push_back(std::move(ch));
     }
+    g0 = g1;
   }
   std::sort(chains.begin(), chains.end(), [](const UChain& a, const UChain& b) {
     return *std::min_element(a.units.begin(), a.units.end()) <
@@ -440,13 +468,13 @@ bool build_uplan(const hdgmg_umesh_problem& pr, UPlan& P, std::string& err) {
     std::vector<std::vector<int>> kids(n_el), inner(n_el);
     for (int f = 0; f < Lf.n_el; ++f) kids[parent[f]].push_back(f);
     for (const auto& iu : interior[t]) inner[iu.second].push_back(iu.first);
+    std::vector<int> local(Lf.n_blk, -1);   // fine block -> local index in the current E
     h.loc_ptr.push_back(0);
     h.ch_ptr.push_back(0);
     h.J_off.push_back(0);
     h.AI_off.push_back(0);
     h.Y_off.push_back(0);
     for (int E = 0; E < n_el; ++E) {
-      std::map<int, int> local;        // fine block -> local index
       const int base = (int)h.loc_blk.size();
       for (int u : inner[E]) {
         const int b = Lf.unit_blk[u];
@@ -484,7 +512,7 @@ bool build_uplan(const hdgmg_umesh_problem& pr, UPlan& P, std::string& err) {
       for (int r = 0; r < nB; ++r) {
         const int s = bref[r].first, pos = bref[r].second;
         const UChain& ch = chains_c[blk_chain[Lc.el_slot[(size_t)E * Lc.nu + s]]];
-        double s0 = 0.0;
+        double s0 = 0.0;                 // arc offset of the unit (summed in chain order)
         for (int i = 0; i < pos; ++i) s0 += units_f[ch.units[i]].length;
         double blk[2][2];
         j_block(ch.length, units_f[ch.units[pos]].length, s0, ch.dirs[pos], blk);
@@ -500,10 +528,11 @@ bool build_uplan(const hdgmg_umesh_problem& pr, UPlan& P, std::string& err) {
         h.ch_el.push_back(f);
         for (int s = 0; s < Lf.nu; ++s) {
           const int b = Lf.el_slot[(size_t)f * Lf.nu + s];
-          h.ch_map.push_back(b < 0 ? -1 : local.at(b));
+          h.ch_map.push_back(b < 0 ? -1 : local[b]);
         }
       }
       h.ch_ptr.push_back((int)h.ch_el.size());
+      for (size_t q = base; q < h.loc_blk.size(); ++q) local[h.loc_blk[q]] = -1;
     }
     P.hc.push_back(std::move(h));
   }
