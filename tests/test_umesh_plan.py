@@ -64,7 +64,8 @@ def test_plan_on_uniform_grid_is_the_block_agglomeration():
     assert np.all(sizes[info[:, 1] >= 0] == 4)
 
 
-@pytest.mark.parametrize("bad", ["clockwise", "index", "p", "tau", "seeds"])
+@pytest.mark.parametrize("bad", ["clockwise", "index", "p", "tau", "seeds", "empty", "nonconforming",
+                                 "degenerate"])
 def test_plan_rejects_invalid_problems(bad):
     from paper_1811_09909_gb300 import hdgmg
     v, q = W.umesh(3, 3, 1.0, 1.0, 0.2, (), 1)
@@ -79,6 +80,13 @@ def test_plan_rejects_invalid_problems(bad):
         p = 9
     elif bad == "tau":
         tau = 0.0
+    elif bad == "empty":
+        q = q[:0]
+    elif bad == "nonconforming":
+        q = np.concatenate([q, q[:1]])               # a second copy of element 0: three sides per edge
+    elif bad == "degenerate":
+        v = v.copy()
+        v[q[2, 1]] = v[q[2, 0]]                     # a zero-length edge
     else:
         seeds = np.zeros((0, 2))
     with pytest.raises(hdgmg.HdgmgError) as ei:
