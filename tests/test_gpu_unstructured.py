@@ -202,3 +202,35 @@ def test_fp32_cycle_inside_fp64_pcg():
     pr = U.UHDGProblem(v, q, 3, 1.0, 1.0)
     lam_o = pr.solve_direct(f)
     assert np.abs(lam32.cpu().numpy().ravel() - lam_o).max() < 1e-8 * np.abs(lam_o).max()
+
+
+@pytest.mark.parametrize("p", [5, 6])
+def test_higher_orders_element_operators_and_solve(p):
+    """p = 5, 6: element operators against the oracle and a PCG solve against
+    its direct solve on the Example II stand-in at n = 3."""
+    s, pr, sp, f = _setup(3, p, kappa_sigma=0.5, rtol=1e-11)
+    A = s.element_matrices(0)[0].cpu().numpy()
+    for e in (0, 17, len(pr.quads) - 1):
+        Ao = pr.element_operator(e)
+        assert np.abs(A[e] - Ao).max() < TOL * np.abs(Ao).max()
+    lam, _, _, info = s.solve(_dev(f), want_u=False, want_q=False)
+    assert info.converged
+    lam_o = pr.solve_direct(f)
+    assert np.abs(lam.cpu().numpy().ravel() - lam_o).max() < 1e-8 * np.abs(lam_o).max()
+
+
+def test_mesh_without_interior_edges():
+    """One element: no trace unknowns; the solve is the local solve with
+    lambda = 0 on the boundary, recovered u equal to the oracle's."""
+    verts = np.array([[0, 0], [1, 0], [1.2, 1], [0, 0.8]], float)
+    quads = np.array([[0, 1, 2, 3]])
+    s = um.USolver(verts, quads, 2, 1.0, np.array([[0.5, 0.5]]))
+    s.setup(_dev(np.zeros(1)))
+    f = np.ones((1, 9))
+    lam, u, q, info = s.solve(_dev(f))
+    assert info.converged and info.iters == 0
+    assert float(lam.abs().max()) == 0.0
+    pr = U.UHDGProblem(verts, quads, 2, 1.0, 1.0)
+    u_o, q_o = pr.recover(np.zeros(pr.ne * 3), f)
+    assert np.abs(u.cpu().numpy() - u_o).max() < 1e-10 * np.abs(u_o).max()
+    assert np.abs(q.cpu().numpy() - q_o).max() < 1e-9 * np.abs(q_o).max()
