@@ -180,6 +180,20 @@ typedef struct {
                              persisting lines are reset by hdgmg_destroy); 0:
                              off.  hdgmg_batch_create uses 0 for its contexts.
                              64                                              */
+  int32_t pcycle;         /* 1: with BLOCK_JACOBI, the P1 levels of every
+                             V-cycle (from the first P1 level down to the
+                             coarsest and back) run as ONE cooperative
+                             kernel launch, the steps separated by grid
+                             barriers whose waits are bounded (a wait that
+                             runs out makes the solve return HDGMG_ETIMEOUT
+                             and leaves the context usable); 0: separate
+                             launches per step plus the single-block tail.
+                             Needs a coarsest level with at most 4096
+                             unknowns; otherwise the launched form runs.  1 */
+  int32_t pcycle_tail_n;  /* pcycle = 1: the levels with n <= this run on
+                             one thread block of the launch (block barriers)
+                             while the others wait at one grid barrier; 0:
+                             every level on the whole grid.  16             */
 } hdgmg_opts;
 
 typedef struct {
@@ -345,9 +359,11 @@ hdgmg_status hdgmg_apply_operator(hdgmg_ctx* ctx, int32_t level,
                                   const double* x, double* y);
 
 /* Same result as hdgmg_apply_operator, for callers that cannot allocate
- * device memory when they call it: code running while a stream is being
- * captured into a CUDA graph (cudaMalloc is not allowed there), or programs
- * whose device memory belongs to another allocator.  The paper has no
+ * device memory when they call it: programs whose device memory is owned by
+ * another allocator (a caching allocator that has already reserved the free
+ * memory, so a cudaMalloc would fail or fragment it), and latency-critical
+ * loops that must not call cudaMalloc/cudaFree (both can synchronise the
+ * device and take far longer than the operator itself).  The paper has no
  * counterpart; this is an interface convenience.
  *   Instead of cudaMalloc'd temporaries it uses one static device array of
  *   2^20 doubles (8 MiB) that every GPU loading the library reserves until
@@ -358,7 +374,8 @@ hdgmg_status hdgmg_apply_operator(hdgmg_ctx* ctx, int32_t level,
  *   before any stream capture begins.
  *   All calls share the array: calls whose work overlaps on the GPU (other
  *   streams, other host threads) race on it.  x, y: as in
- *   hdgmg_apply_operator.  Returns after the work is complete. */
+ *   hdgmg_apply_operator.  Returns after the work is complete on the
+ *   context's stream (the call synchronises that stream). */
 hdgmg_status hdgmg_apply_operator_noalloc(hdgmg_ctx* ctx, int32_t level,
                                           const double* x, double* y);
 
@@ -366,6 +383,17 @@ hdgmg_status hdgmg_apply_operator_noalloc(hdgmg_ctx* ctx, int32_t level,
  * precision; r, e device, [p+1][n_edges] FP64 (Dirichlet entries ignored /
  * zero). */
 hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* ctx, const double* r, double* e);
+
+/* Check of the bounded waits of the persistent V-cycle (opts.pcycle): runs
+ * its kernel once on the context's level vectors with every thread block
+ * withholding its arrival at the first grid barrier, so that each block's
+ * wait runs out after wait_us (1 ... 10^6) microseconds.  Returns
+ * HDGMG_ETIMEOUT when the limit works: the kernel returns by itself, the
+ * barrier and the flag are reset, and the context stays usable for further
+ * solves.  HDGMG_EINVAL when the context does not run the persistent cycle
+ * or before hdgmg_setup.  (A test entry point; the paper has no
+ * counterpart.) */
+hdgmg_status hdgmg_check_cycle_timeout(hdgmg_ctx* ctx, int32_t wait_us);
 
 /* The condensed right-hand side b = sum_e g_e - A lambda_D on interior
  * edges (Sec. 2; Dirichlet data applied strongly): f, g_D as in hdgmg_solve

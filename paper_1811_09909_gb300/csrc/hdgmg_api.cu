@@ -129,6 +129,14 @@ struct hdgmg_ctx {
   int ctail_start = -1;
   CTailParams<float> cp32;
   CTailParams<double> cp64;
+  // persistent P1 cycle: the levels from pc_start down run as one cooperative
+  // launch of pc_blocks blocks; pc_bar is its grid barrier's arrival count,
+  // err[2] its expired-wait flag
+  int pc_start = -1;
+  int pc_blocks = 0;
+  unsigned long long* pc_bar = nullptr;
+  PCycleParams<float> pc32;
+  PCycleParams<double> pc64;
 
   template <typename T>
   cudaError_t alloc(T** p_, size_t count) {
@@ -151,6 +159,9 @@ template <> LevelData<float>& ld<float>(Level& L) { return L.d32; }
 template <typename T> CTailParams<T>& ctailp(hdgmg_ctx* c);
 template <> CTailParams<double>& ctailp<double>(hdgmg_ctx* c) { return c->cp64; }
 template <> CTailParams<float>& ctailp<float>(hdgmg_ctx* c) { return c->cp32; }
+template <typename T> PCycleParams<T>& pcyclep(hdgmg_ctx* c);
+template <> PCycleParams<double>& pcyclep<double>(hdgmg_ctx* c) { return c->pc64; }
+template <> PCycleParams<float>& pcyclep<float>(hdgmg_ctx* c) { return c->pc32; }
 template <typename T> TailParams<T>& tailp(hdgmg_ctx* c);
 template <> TailParams<double>& tailp<double>(hdgmg_ctx* c) { return c->tp64; }
 template <> TailParams<float>& tailp<float>(hdgmg_ctx* c) { return c->tp32; }
@@ -218,7 +229,8 @@ void plan_tail(hdgmg_ctx* c, int tail_n) {
   while (start - 1 >= 0) {
     const int k = start - 1;
     const Level& L = c->levels[k];
-    if (L.nd != 2 || L.transfer != 2 || L.n > tail_n) break;
+    // a finest level with a BF16 operator copy keeps its launched BF16 matvecs
+    if (L.nd != 2 || L.transfer != 2 || L.n > tail_n || L.A16) break;
     if (last - k + 1 > kMaxTail) break;
     staged[k] = 1;
     if (tail_layout<T>(c, k, staged, stage_inv, nullptr) > cap) {
@@ -304,7 +316,8 @@ void plan_ctail(hdgmg_ctx* c, int top_n) {
   int start = last;
   while (start - 1 >= 0) {
     const Level& L = c->levels[start - 1];
-    if (L.nd != 2 || L.transfer != 2 || L.n > top_n || last - (start - 1) + 1 > kMaxTail) break;
+    if (L.nd != 2 || L.transfer != 2 || L.n > top_n || L.A16 || last - (start - 1) + 1 > kMaxTail)
+      break;
     --start;
   }
   if (start == last) return;                 // nothing above the coarsest level to fuse
@@ -349,6 +362,149 @@ void plan_ctail(hdgmg_ctx* c, int top_n) {
       return;
     }
   }
+}
+
+// Persistent P1 cycle: from the first P1 level that the launched path runs by
+// fused edge sweeps (below the p-level, or level 0 when p = 1) down to the
+// coarsest.  The levels with n <= tail_n (and the coarsest) run on block 0:
+// staged in its shared memory when they fit (operators, inverse, vectors),
+// from L2 otherwise.  The grid is sized to the first level's edges (one item
+// per thread), at most one block per SM; a tail from the first level is one
+// block.
+constexpr size_t kPcSmemBudget = 200 * 1024;
+
+// shared-memory layout of levels [k, last] of the block-0 tail; returns bytes
+template <typename T>
+size_t pcycle_tail_layout(hdgmg_ctx* c, int ls, int k, PCycleParams<T>* P) {
+  const int last = (int)c->levels.size() - 1;
+  const size_t sz = sizeof(T);
+  const size_t na = c->ns ? 64 : 36, nd2 = c->ns ? 4 : 3;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 15) / 16 * 16;
+    return (int)o;
+  };
+  for (int l = k; l <= last; ++l) {
+    const Level& L = c->levels[l];
+    const size_t nE = L.nE, ned = L.nEdge, nC = nE / 4;
+    PLevel<T> q;
+    q.so_v = take(6 * ned * sz);
+    if (l < last) {
+      q.so_A = take(na * nE * sz);
+      q.so_D = take(nd2 * ned * sz);
+      q.so_AII = take(na * nC * sz);
+      q.so_Y = take(128 * nC * sz);
+      q.so_Pi = take(64 * nC * sz);
+      q.so_Rt = c->ns ? take(64 * nC * sz) : q.so_Pi;
+    }
+    if (P) {
+      PLevel<T>& d = P->lv[l - ls];
+      d.so_v = q.so_v;
+      d.so_A = q.so_A;
+      d.so_D = q.so_D;
+      d.so_AII = q.so_AII;
+      d.so_Y = q.so_Y;
+      d.so_Pi = q.so_Pi;
+      d.so_Rt = q.so_Rt;
+    }
+  }
+  const int so_Ainv = take(sizeof(double) * (size_t)c->nf * c->nf);
+  const int so_w = take(sizeof(double) * (size_t)(c->nf > 0 ? c->nf : 1));
+  if (P) {
+    // bytes moved by the bulk copies: every operator array of the staged
+    // levels and the coarsest inverse
+    size_t tx = sizeof(double) * (size_t)c->nf * c->nf;
+    for (int l = k; l < last; ++l) {
+      const Level& L = c->levels[l];
+      const size_t nE = L.nE, ned = L.nEdge, nC = nE / 4;
+      tx += sz * (na * nE + nd2 * ned + na * nC + 128 * nC + 64 * nC + (c->ns ? 64 * nC : 0));
+    }
+    P->stage_bytes = (int)tx;
+    P->so_Ainv = so_Ainv;
+    P->so_w = so_w;
+    P->smem_bytes = (int)off;
+  }
+  return off;
+}
+
+template <typename T>
+void plan_pcycle(hdgmg_ctx* c) {
+  c->pc_start = -1;
+  const hdgmg_opts& o = c->opts;
+  if (o.pcycle <= 0 || o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) return;
+  const int last = (int)c->levels.size() - 1;
+  int ls = -1;
+  for (int l = 0; l < last; ++l) {
+    const Level& L = c->levels[l];
+    if (L.nd == 2 && L.transfer == 2 && !L.A16) {
+      ls = l;
+      break;
+    }
+  }
+  if (ls < 0 || last - ls + 1 > kMaxPLev || c->nf > 4096) return;
+  PCycleParams<T>& P = pcyclep<T>(c);
+  P = PCycleParams<T>();
+  P.nlev = last - ls + 1;
+  P.tail = P.nlev;
+  for (int k = ls; k <= last; ++k) {
+    Level& L = c->levels[k];
+    LevelData<T>& D = ld<T>(L);
+    PLevel<T>& q = P.lv[k - ls];
+    q.n = L.n;
+    q.m = L.m;
+    q.g = make_p1geom(L.n);
+    q.A = D.A;
+    q.Dinv = D.Dinv;
+    q.AIIinv = D.AIIinv;
+    q.Y = D.Y;
+    q.Pi = D.Pi;
+    q.Rt = c->ns ? D.Rt : D.Pi;
+    q.r = D.r;
+    q.e = D.e;
+    q.y = D.y;
+    if (P.tail == P.nlev && L.n <= o.pcycle_tail_n) P.tail = k - ls;
+  }
+  P.so_w = 0;
+  P.smem_bytes = (int)(sizeof(double) * (size_t)(c->nf > 0 ? c->nf : 1));
+  if (P.tail < P.nlev) {
+    // stage the tail in shared memory from the highest level that fits
+    for (int k = ls + P.tail; k <= last; ++k) {
+      if (pcycle_tail_layout<T>(c, ls, k, nullptr) <= kPcSmemBudget) {
+        P.tail = k - ls;
+        P.staged = 1;
+        pcycle_tail_layout<T>(c, ls, k, &P);
+        break;
+      }
+    }
+  }
+  P.Ainv = c->cinv;
+  P.fidx = c->freeidx;
+  P.fedge = c->fedge;
+  P.nf = c->nf;
+  P.omega = (T)o.omega;
+  P.lc = o.local_corr;
+  P.ns = c->ns ? 1 : 0;
+  P.bar = c->pc_bar;
+  P.err = c->err + 2;
+  const int maxb = pcycle_max_blocks<T>(P.smem_bytes);
+  if (maxb < 1) return;
+  const int nthr = pcycle_threads<T>();
+  const int want = (c->levels[ls].nEdge + nthr - 1) / nthr;
+  c->pc_blocks = P.tail == 0 ? 1 : (want < maxb ? want : maxb);
+  c->pc_start = ls;
+}
+
+// A bounded grid-barrier wait of the persistent cycle ran out on the device
+// (err[2] set; its copy in err_h[2] must be current): reset the barrier and the
+// flag so that the context stays usable, and report it.
+hdgmg_status cycle_wait_status(hdgmg_ctx* c) {
+  if (c->pc_start < 0 || c->err_h[2] == 0) return HDGMG_OK;
+  c->err_h[2] = 0;
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->err + 2, 0, sizeof(int), c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return fail(HDGMG_ETIMEOUT, "a grid-barrier wait of the persistent V-cycle ran out");
 }
 
 hdgmg_status check_launch(const char* where) {
@@ -432,6 +588,14 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   Level& L = c->levels[l];
   LevelData<T>& D = ld<T>(L);
   const int last = (int)c->levels.size() - 1;
+  if (l == c->pc_start) {                                   // persistent P1 cycle
+    PCycleParams<T> P = pcyclep<T>(c);
+    P.rp_r0 = rp_r0;
+    P.rp_y0 = rp_y0;
+    P.rp_nd0 = rp_nd0;
+    launch_pcycle<T>(s, P, c->pc_blocks);
+    return;
+  }
   if (l == c->ctail_start) {                                // cluster-fused P1 tail
     launch_ctail<T>(s, ctailp<T>(c));
     return;
@@ -1016,6 +1180,10 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     if (conv) it = it - 1;
     if (it > o.max_it) it = o.max_it;
   }
+  // the persistent cycle's expired-wait flag is read back with the final
+  // residual
+  if (c->pc_start >= 0)
+    CUDA_TRY(cudaMemcpyAsync(c->err_h + 2, c->err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   // true FP64 residual of the final iterate
   if (nb > 0.0) {
     apply_A64(c, c->x, c->Ap);
@@ -1023,7 +1191,10 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     launch_axpby(s, len, -1.0, c->Ap, 1.0, c->r);
     rel = std::sqrt(dot_sync(c, c->r, c->r)) / nb;
     conv = conv && rel <= o.rtol * 10.0;
+  } else if (c->pc_start >= 0) {
+    CUDA_TRY(cudaStreamSynchronize(s));
   }
+  STATUS_TRY(cycle_wait_status(c));
   // lambda = boundary data + interior solution
   CUDA_TRY(cudaMemcpyAsync(lam_out, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
   launch_axpby(s, len, 1.0, c->x, 1.0, lam_out);
@@ -1103,6 +1274,8 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->smoother = HDGMG_SMOOTH_BLOCK_JACOBI;
   o->condensation = HDGMG_CONDENSE_AUTO;
   o->l2_persist_mb = 64;
+  o->pcycle = 1;
+  o->pcycle_tail_n = 16;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1383,6 +1556,16 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     c->tail_start = -1;                      // the fused tails implement block-Jacobi only
     c->ctail_start = -1;
   }
+  CTRY(c->alloc(&c->pc_bar, 1));
+  CTRY(cudaMemset(c->pc_bar, 0, sizeof(unsigned long long)));
+  if (fp32)
+    plan_pcycle<float>(c);
+  else
+    plan_pcycle<double>(c);
+  if (c->pc_start >= 0) {                    // the persistent cycle replaces both tails
+    c->tail_start = -1;
+    c->ctail_start = -1;
+  }
   CTRY(cudaEventCreate(&c->ev0));
   CTRY(cudaEventCreate(&c->ev1));
   CTRY(cudaEventCreate(&c->evk0));
@@ -1461,6 +1644,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaEventRecord(c->ev0, s));
   CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned long long), s));
   Level& L0 = c->levels[0];
   if (c->ns) {
     STATUS_TRY(prepare_pencil(c, log_kappa));
@@ -1727,8 +1911,36 @@ hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* c, const double* r, double* e) {
   launch_mask<double>(s, c->n, c->p + 1, c->r);
   apply_B(c, c->r, e);
   STATUS_TRY(check_launch("apply vcycle"));
+  if (c->pc_start >= 0)
+    CUDA_TRY(cudaMemcpyAsync(c->err_h + 2, c->err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
-  return HDGMG_OK;
+  return cycle_wait_status(c);
+}
+
+hdgmg_status hdgmg_check_cycle_timeout(hdgmg_ctx* c, int32_t wait_us) {
+  if (!c) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  if (c->pc_start < 0) return fail(HDGMG_EINVAL, "this context does not run the persistent cycle");
+  const int tail = c->opts.precision != HDGMG_PREC_FP64 ? c->pc32.tail : c->pc64.tail;
+  if (tail == 0) return fail(HDGMG_EINVAL, "this context's cycle runs on one block (no grid barrier)");
+  if (wait_us < 1 || wait_us > 1000000) return fail(HDGMG_EINVAL, "wait_us must be in [1, 1e6]");
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  if (c->opts.precision != HDGMG_PREC_FP64) {
+    PCycleParams<float> P = c->pc32;
+    P.withhold = 1;
+    P.wait_ns = (unsigned long long)wait_us * 1000ull;
+    e = launch_pcycle<float>(s, P, c->pc_blocks);
+  } else {
+    PCycleParams<double> P = c->pc64;
+    P.withhold = 1;
+    P.wait_ns = (unsigned long long)wait_us * 1000ull;
+    e = launch_pcycle<double>(s, P, c->pc_blocks);
+  }
+  if (e != cudaSuccess) return fail(HDGMG_ECUDA, std::string("persistent cycle: ") + cudaGetErrorString(e));
+  CUDA_TRY(cudaMemcpyAsync(c->err_h + 2, c->err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return cycle_wait_status(c);
 }
 
 hdgmg_status hdgmg_condensed_rhs(hdgmg_ctx* c, const double* f, const double* g_D, double* b) {
@@ -1748,11 +1960,11 @@ hdgmg_status hdgmg_condensed_rhs(hdgmg_ctx* c, const double* f, const double* g_
 // hdgmg_apply_operator takes its temporaries (the copy of x with the
 // Dirichlet entries zeroed, and the FP32 accumulator on FP32 levels) from
 // cudaMalloc on every call.  Some callers cannot allocate device memory at
-// the point where they need the operator: code running while a stream is
-// being captured into a CUDA graph (cudaMalloc is not permitted there), or
-// integrations whose device memory is fully owned by another allocator.  For
-// them the temporaries live in one fixed array that the library reserves in
-// device memory when it is loaded.
+// the point where they need the operator: integrations whose device memory
+// is owned by another allocator (a cudaMalloc would fail or fragment it), and
+// latency-critical loops that must not call cudaMalloc/cudaFree (both can
+// synchronise the device).  For them the temporaries live in one fixed array
+// that the library reserves in device memory when it is loaded.
 // ---------------------------------------------------------------------------
 namespace {
 

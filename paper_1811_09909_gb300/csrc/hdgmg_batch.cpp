@@ -110,6 +110,10 @@ hdgmg_status hdgmg_batch_create(hdgmg_batch** out, int32_t nprob, const hdgmg_pr
   else
     hdgmg_default_opts(&bo);
   bo.l2_persist_mb = 0;
+  // the persistent cycle is one cooperative grid per context; the batch's
+  // contexts run concurrently on their own streams, so they use the launched
+  // cycle
+  bo.pcycle = 0;
   hdgmg_batch* b = new hdgmg_batch();
   b->user = (cudaStream_t)stream;
   cudaGetDevice(&b->device);

@@ -347,6 +347,108 @@ int ctail_max_clusters(int cluster, int smem_bytes);
 template <typename T>
 void launch_ctail(cudaStream_t s, const CTailParams<T>& P);
 
+// Persistent V-cycle over the P1 levels (k_mg.cu): one cooperative launch
+// runs Algorithm 1 from the first P1 level to the coarsest and back, every
+// step a grid-stride loop over its work items, the steps separated by grid
+// barriers (bounded waits) instead of kernel launches.  Levels from `tail`
+// on run on block 0 alone (block barriers), while the other blocks wait at
+// one grid barrier.  Vectors stay in global memory (L2-resident).
+constexpr int kMaxPLev = 14;
+// floor(x / d) for 0 <= x < 2^31 by a multiply-high and a shift (the
+// round-up method of Granlund and Montgomery): s = ceil(log2 d),
+// m = floor(2^(32+s) / d) + 1 - 2^32, floor(x / d) = (mulhi(x, m) + x) >> s.
+// m / 2^(32+s) exceeds 1/d by less than 2^-(32+s), so for x < 2^31 the
+// error stays below 2^-(s+1) <= 1/(2d) and never reaches the next integer.
+struct FastDiv {
+  unsigned m = 1, s = 0;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  unsigned s = 0;
+  while ((1ull << s) < (unsigned long long)d) ++s;
+  f.s = s;
+  f.m = (unsigned)(((1ull << (32 + s)) / (unsigned long long)d) + 1ull - (1ull << 32));
+  return f;
+}
+// Sizes of a P1 level with n macro-elements per side and, when n is even, of
+// the next coarser level nc = n / 2, with the divisors the work items need.
+struct P1Geom {
+  int n = 0, nE = 0, nvert = 0, nedge = 0;
+  int nc = 0, nC = 0, nvc = 0, nedc = 0;
+  FastDiv dn, dn1, dnc, dnc1, dnC;
+};
+inline P1Geom make_p1geom(int n) {
+  P1Geom g;
+  g.n = n;
+  g.nE = n * n;
+  g.nvert = n * (n + 1);
+  g.nedge = 2 * n * (n + 1);
+  g.dn = make_fastdiv(n);
+  g.dn1 = make_fastdiv(n + 1);
+  g.nc = n / 2;
+  if (g.nc > 0) {
+    g.nC = g.nc * g.nc;
+    g.nvc = g.nc * (g.nc + 1);
+    g.nedc = 2 * g.nc * (g.nc + 1);
+    g.dnc = make_fastdiv(g.nc);
+    g.dnc1 = make_fastdiv(g.nc + 1);
+    g.dnC = make_fastdiv(g.nC);
+  }
+  return g;
+}
+template <typename T>
+struct PLevel {
+  int n = 0, m = 1;
+  P1Geom g;
+  const T* A = nullptr;
+  const T* Dinv = nullptr;
+  const T* AIIinv = nullptr;
+  const T* Y = nullptr;
+  const T* Pi = nullptr;
+  const T* Rt = nullptr;        // restriction block (= Pi when symmetric)
+  T* r = nullptr;
+  T* e = nullptr;
+  T* y = nullptr;
+  // levels of the block-0 tail: byte offsets of their shared-memory copies
+  // (operators, and the vectors [r | e | y]); -1 when not staged
+  int so_A = -1, so_D = -1, so_AII = -1, so_Y = -1, so_Pi = -1, so_Rt = -1, so_v = -1;
+};
+template <typename T>
+struct PCycleParams {
+  int nlev = 0;                 // lv[0] first P1 level ... lv[nlev-1] coarsest
+  int tail = 0;                 // first level run by block 0 alone (nlev: none)
+  PLevel<T> lv[kMaxPLev];
+  // pending p-restriction J_N^T (r0 - y0) of the level above lv[0] (r0 null:
+  // lv[0].r is the given right-hand side)
+  const T* rp_r0 = nullptr;
+  T* rp_y0 = nullptr;
+  int rp_nd0 = 0;
+  const double* Ainv = nullptr; // coarsest dense inverse (FP64)
+  const int* fidx = nullptr;
+  const int* fedge = nullptr;
+  int nf = 0;
+  T omega = T(1);
+  int lc = 0;
+  int ns = 0;
+  unsigned long long* bar = nullptr;   // grid barrier: monotonic arrival count
+  int* err = nullptr;           // bit 0: a barrier wait expired, bit 1: the wait for the
+                                // tail's bulk copies expired (both HDGMG_ETIMEOUT)
+  unsigned long long wait_ns = 1000000000ull;   // limit of one barrier wait
+  int withhold = 0;             // testing: no block arrives at the first barrier
+  // dynamic shared memory: the block-0 tail's staged levels (staged = 1), the
+  // coarsest inverse at so_Ainv and the coarse workspace at so_w (bytes)
+  int staged = 0;
+  int stage_bytes = 0;          // bytes of the staged operators and inverse (bulk copies)
+  int so_Ainv = -1, so_w = 0;
+  int smem_bytes = 0;
+};
+template <typename T>
+int pcycle_max_blocks(int smem_bytes);   // co-resident blocks of the kernel on this device
+template <typename T>
+int pcycle_threads();
+template <typename T>
+cudaError_t launch_pcycle(cudaStream_t s, const PCycleParams<T>& P, int blocks);
+
 // coarsest level: dense FP64 Cholesky of the interior operator
 template <typename T>
 void launch_coarse_assemble(cudaStream_t s, int n, bool ns, const T* A, const int* freeidx, int nf,

@@ -45,6 +45,15 @@ __global__ void pcoarsen_kernel(int nE, int ndf, bool ns, const T* __restrict__ 
 }
 
 __constant__ double c_Jc[2][2][2];   // child injection [child][fine mode][coarse mode]
+// the same in FP32: the FP32 cycle reads these (a per-use FP64 -> FP32
+// conversion runs on GB300's narrow FP64 pipe)
+__constant__ float c_Jcf[2][2][2];
+
+}  // namespace
+}  // namespace hdgmg
+#include "k_p1.cuh"
+namespace hdgmg {
+namespace {
 
 // -------------------------------------------------- K4 agglomeration setup
 // One warp per macro-element C: the 24 x 24 local block assembled from the
@@ -377,12 +386,12 @@ __device__ __forceinline__ void local_correction_item(int nc, bool ns, const T* 
   e[(size_t)(a & 1) * nedge + interior_edge(n, I, J, a >> 1)] = s;
 }
 
-template <typename T>
-__global__ void local_correction_kernel(int nc, bool ns, const T* __restrict__ AIIinv,
+template <typename T, bool NS>
+__global__ void local_correction_kernel(const P1Geom g, const T* __restrict__ AIIinv,
                                         const T* __restrict__ Y, const T* __restrict__ r,
                                         T* __restrict__ e) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 8 * nc * nc) local_correction_item<T>(nc, ns, AIIinv, Y, r, e, t);
+  if (t < 8 * g.nC) p1_lc<T, NS>(g, AIIinv, Y, r, e, t);
 }
 
 
@@ -441,10 +450,10 @@ __device__ __forceinline__ void restrict_h_item(int nc, const T* __restrict__ Pi
 }
 
 template <typename T>
-__global__ void restrict_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ r,
+__global__ void restrict_h_kernel(const P1Geom g, const T* __restrict__ Pi, const T* __restrict__ r,
                                   const T* __restrict__ y, T* __restrict__ rc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 4 * nc * (nc + 1)) restrict_h_item<T>(nc, Pi, r, y, rc, t);
+  if (t < 2 * g.nedc) p1_restrict<T>(g, Pi, r, y, rc, t);
 }
 
 // -------------------------------------------------------- K11 prolongation
@@ -494,41 +503,23 @@ __device__ __forceinline__ void prolong_h_item(int nc, const T* __restrict__ Pi,
 }
 
 template <typename T>
-__global__ void prolong_h_kernel(int nc, const T* __restrict__ Pi, const T* __restrict__ ec,
+__global__ void prolong_h_kernel(const P1Geom g, const T* __restrict__ Pi, const T* __restrict__ ec,
                                  T* __restrict__ e, T* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 8 * nc * nc + 4 * nc * (nc + 1)) prolong_h_item<T>(nc, Pi, ec, e, y, t);
+  if (t < 8 * g.nC + 2 * g.nedc) p1_prolong<T>(g, Pi, ec, e, y, t);
 }
 
 // ------------------------------------------------- p-transfer (J_N, J_N^T)
 // J_N^T fused into the first block-Jacobi sweep of the P1 level below (same
 // mesh, one thread per edge): r1 = r0 - y0 on modes 0 and 1, y0 reset on
 // every mode, e1 = omega D1^-1 r1.
-template <typename T>
-__global__ void bj_first_restrict_p_kernel(int n, int nd0, bool ns, const T* __restrict__ Dinv1,
+template <typename T, bool NS>
+__global__ void bj_first_restrict_p_kernel(const P1Geom g, int nd0, const T* __restrict__ Dinv1,
                                            const T* __restrict__ r0, T* __restrict__ y0,
                                            T* __restrict__ r1, T* __restrict__ e1, T omega) {
-  const int nedge = 2 * n * (n + 1);
   const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E >= nedge) return;
-  const T d0 = r0[E] - y0[E], d1 = r0[(size_t)nedge + E] - y0[(size_t)nedge + E];
-  for (int k = 0; k < nd0; ++k) y0[(size_t)k * nedge + E] = T(0);
-  r1[E] = d0;
-  r1[(size_t)nedge + E] = d1;
-  if (bnd_edge(n, E)) return;
-  const T a00 = Dinv1[E], a01 = Dinv1[(size_t)nedge + E], a10 = Dinv1[(size_t)2 * nedge + E];
-  T u0, u1;
-  if (ns) {
-    u0 = a00 * d0 + a01 * d1;
-    u1 = a10 * d0 + Dinv1[(size_t)3 * nedge + E] * d1;
-  } else {
-    u0 = a00 * d0 + a01 * d1;
-    u1 = a01 * d0 + a10 * d1;
-  }
-  e1[E] = omega * u0;
-  e1[(size_t)nedge + E] = omega * u1;
+  if (E < g.nedge) p1_first_restrict_p<T, NS>(g, nd0, Dinv1, r0, y0, r1, e1, omega, E);
 }
-
 
 template <typename T>
 __global__ void restrict_p_kernel(int n, int nd, const T* __restrict__ r, T* __restrict__ y,
@@ -810,77 +801,14 @@ __device__ __forceinline__ void bj_p1_item(int n, bool ns, const T* __restrict__
   }
 }
 
-// Edge-centric P1 operator on interior edge E, from its two elements:
-// acc = (A x)_E (no atomics: the edge gathers both elements' rows).
-//   SWEEP: out_E = x_E + omega D_E^-1 (r_E - acc)   (one block-Jacobi sweep,
-//          x and out distinct buffers: Jacobi reads only old values)
-//   else:  out_E = acc
-// Boundary (Dirichlet) edges get out = 0.
-template <typename T, bool SWEEP>
-__device__ __forceinline__ void edge_p1_item(int n, bool ns, const T* __restrict__ A,
-                                             const T* __restrict__ Dinv, const T* r, const T* x,
-                                             T* out, T omega, int E) {
-  const int nedge = 2 * n * (n + 1);
-  if (bnd_edge(n, E)) {
-    out[E] = T(0);
-    out[nedge + E] = T(0);
-    return;
-  }
-  const int nE = n * n, nvert = n * (n + 1);
-  int el[2], le[2];
-  if (E < nvert) {
-    const int j = E / (n + 1), i = E - j * (n + 1);
-    el[0] = j * n + i - 1; le[0] = 1;
-    el[1] = j * n + i;     le[1] = 0;
-  } else {
-    const int j = (E - nvert) / n, i = (E - nvert) - j * n;
-    el[0] = (j - 1) * n + i; le[0] = 3;
-    el[1] = j * n + i;       le[1] = 2;
-  }
-  T s[2][2];
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const int K = el[side], r0 = le[side] * 2;
-    int ed[4];
-    elem_edges(n, K, ed);
-    T s0 = T(0), s1 = T(0);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const T xc = x[(size_t)(c & 1) * nedge + ed[c >> 1]];
-      const T a0 = A[(size_t)(ns ? r0 * 8 + c : pk_any(r0, c)) * nE + K];
-      const T a1 = A[(size_t)(ns ? (r0 + 1) * 8 + c : pk_any(r0 + 1, c)) * nE + K];
-      s0 += a0 * xc;
-      s1 += a1 * xc;
-    }
-    s[side][0] = s0;
-    s[side][1] = s1;
-  }
-  const T acc0 = s[0][0] + s[1][0], acc1 = s[0][1] + s[1][1];
-  if (SWEEP) {
-    const T d0 = r[E] - acc0, d1 = r[nedge + E] - acc1;
-    const T a00 = Dinv[E], a01 = Dinv[(size_t)nedge + E], a10 = Dinv[(size_t)2 * nedge + E];
-    T u0, u1;
-    if (ns) {          // full [d00, d01, d10, d11]
-      u0 = a00 * d0 + a01 * d1;
-      u1 = a10 * d0 + Dinv[(size_t)3 * nedge + E] * d1;
-    } else {           // packed [d00, d10, d11]
-      u0 = a00 * d0 + a01 * d1;
-      u1 = a01 * d0 + a10 * d1;
-    }
-    out[E] = x[E] + omega * u0;
-    out[nedge + E] = x[nedge + E] + omega * u1;
-  } else {
-    out[E] = acc0;
-    out[nedge + E] = acc1;
-  }
-}
-
-template <typename T, bool SWEEP>
-__global__ void edge_p1_kernel(int n, bool ns, const T* __restrict__ A, const T* __restrict__ Dinv,
+// Edge-centric P1 operator, one thread per edge gathering both elements'
+// rows (no atomics): SWEEP out = x + omega D^-1 (r - A x), else out = A x.
+template <typename T, bool NS, bool SWEEP>
+__global__ void edge_p1_kernel(const P1Geom g, const T* __restrict__ A, const T* __restrict__ Dinv,
                                const T* __restrict__ r, const T* __restrict__ x,
                                T* __restrict__ out, T omega) {
   const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E < 2 * n * (n + 1)) edge_p1_item<T, SWEEP>(n, ns, A, Dinv, r, x, out, omega, E);
+  if (E < g.nedge) p1_edge<T, NS, SWEEP>(g, A, Dinv, r, x, out, omega, E);
 }
 
 template <typename T>
@@ -993,6 +921,409 @@ __global__ void __launch_bounds__(NTHR) vcycle_tail_kernel(const TailParams<T> P
     const T* e0 = sm + P.lv[0].voff + 2 * P.lv[0].nEdge;
     for (int i = tid; i < 2 * P.lv[0].nEdge; i += nth) P.e_out[i] = e0[i];
   }
+}
+
+// ------------------------------------ persistent V-cycle over the P1 levels
+// Algorithm 1 from the first P1 level down to B_1 = A_1^-1 and back, in one
+// cooperative launch: each step is a grid-stride loop over the work items of
+// the launched kernels (the same item functions, so the same arithmetic), and
+// a grid barrier replaces each kernel boundary.  Levels from P.tail on run on
+// block 0 alone with block barriers while the other blocks wait at a single
+// grid barrier.
+
+__device__ __forceinline__ unsigned long long pc_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long pc_ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void pc_red_release(unsigned long long* p) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+
+// one-dimensional bulk copies (TMA) global -> shared, completing on an mbarrier
+__device__ __forceinline__ unsigned pc_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void pc_mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pc_smem_addr(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void pc_mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(pc_smem_addr(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void pc_bulk_copy(void* dst, const void* src, unsigned bytes,
+                                             unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          pc_smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(pc_smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool pc_mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(pc_smem_addr(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// wait for phase 0 of bar, at most wait_ns; false when the limit ran out
+__device__ __forceinline__ bool pc_mbar_wait(unsigned long long* bar, unsigned long long wait_ns) {
+  if (pc_mbar_test(bar, 0)) return true;
+  const unsigned long long t0 = pc_now_ns();
+  while (!pc_mbar_test(bar, 0))
+    if (pc_now_ns() - t0 > wait_ns) return false;
+  return true;
+}
+
+struct PcSync {
+  unsigned long long target = 0;   // thread 0: arrivals that end the current barrier
+  int first = 1;                   // no barrier passed yet
+};
+
+// Grid barrier on a monotonic arrival count: thread 0 of every block adds one
+// with release semantics (after the block barrier, so the block's writes are
+// published) and waits, with acquire loads, until the count reaches the next
+// multiple of the grid size -- no reset, no second round trip.  The count is a
+// multiple of the grid size between launches, so each launch starts from the
+// multiple below the value it reads.  A wait longer than P.wait_ns sets bit 0
+// of *P.err; an error set by any block ends every later wait at once (a block
+// that gave up never arrives again, so no later barrier can complete).
+// Returns false in every thread of the block once the wait failed.
+template <typename T>
+__device__ bool pc_grid_sync(const PCycleParams<T>& P, PcSync& st, volatile int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    st.target += gridDim.x;
+    if (!(P.withhold && st.first)) pc_red_release(P.bar);
+    st.first = 0;
+    if (pc_ld_acquire(P.bar) < st.target) {
+      const unsigned long long t0 = pc_now_ns();
+      unsigned spin = 0;
+      while (pc_ld_acquire(P.bar) < st.target) {
+        if ((++spin & 15u) == 0) {
+          if (*(volatile int*)P.err != 0) {
+            ok = 0;
+            break;
+          }
+          if (pc_now_ns() - t0 > P.wait_ns) {
+            atomicOr(P.err, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool pc_sync(const PCycleParams<T>& P, bool grid, PcSync& st,
+                                        volatile int* s_ok) {
+  if (grid) return pc_grid_sync<T>(P, st, s_ok);
+  __syncthreads();
+  return true;
+}
+
+// The two buffers a P1 level's sweeps ping-pong between, ordered so that the
+// correction ends in L.e: the first sweep writes bufs[1]; with the fused
+// prolongation + second local correction (LC_BOTH) the up sweep has one more
+// buffer swap.
+template <typename T>
+__device__ __forceinline__ void pc_bufs(const PCycleParams<T>& P, int l, T* bufs[2]) {
+  const PLevel<T>& L = P.lv[l];
+  if (P.lc == HDGMG_LC_BOTH) {
+    bufs[0] = L.y;
+    bufs[1] = L.e;
+  } else {
+    bufs[0] = L.e;
+    bufs[1] = L.y;
+  }
+}
+
+// Steps 2-4 on P1 level l down to the restriction into level l + 1.  The
+// first sweep from e = 0 of a level other than lv[0] and the first level of
+// a staged block-0 tail is fused into the restriction above it; after a
+// local correction the residual and the restriction are one step
+// (p1_resid_restrict).
+template <typename T, bool NS>
+__device__ bool pc_down(const PCycleParams<T>& P, int l, int i0, int di, bool grid, PcSync& st,
+                        volatile int* s_ok) {
+  const PLevel<T>& L = P.lv[l];
+  const P1Geom& g = L.g;
+  const int ned = g.nedge;
+  T* bufs[2];
+  pc_bufs<T>(P, l, bufs);
+  int cur = 1;
+  if (l == 0 || (P.staged && l == P.tail)) {
+    if (l == 0 && P.rp_r0) {
+      for (int i = i0; i < ned; i += di)
+        p1_first_restrict_p<T, NS>(g, P.rp_nd0, L.Dinv, P.rp_r0, P.rp_y0, L.r, bufs[1], P.omega, i);
+    } else {
+      for (int i = i0; i < ned; i += di) p1_first<T, NS>(g, L.Dinv, L.r, bufs[1], P.omega, i);
+    }
+    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  }
+  for (int it = 1; it < L.m; ++it) {
+    for (int i = i0; i < ned; i += di)
+      p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+    cur ^= 1;
+    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  }
+  // the next level's first sweep joins its restriction unless it is the
+  // coarsest level (no smoothing) or the first, staged level of the tail
+  const bool fuse_next = l + 1 < P.nlev - 1 && !(P.staged && l + 1 == P.tail);
+  T* rc = P.lv[l + 1].r;
+  T* cb[2];
+  pc_bufs<T>(P, l + 1, cb);
+  T* ec = fuse_next ? cb[1] : nullptr;
+  const T* Dc = P.lv[l + 1].Dinv;
+  if (P.lc != HDGMG_LC_NONE) {
+    for (int i = i0; i < 8 * g.nC; i += di) p1_lc<T, NS>(g, L.AIIinv, L.Y, L.r, bufs[cur], i);
+    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+    for (int i = i0; i < 2 * g.nedc; i += di)
+      p1_resid_restrict2<T, NS>(g, L.A, L.r, bufs[cur], rc, Dc, ec, P.omega, i);
+    return pc_sync<T>(P, grid, st, s_ok);
+  }
+  for (int i = i0; i < ned; i += di)
+    p1_edge<T, NS, false>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+  if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  for (int i = i0; i < g.nedc; i += di)
+    p1_restrict_first<T, NS>(g, L.Rt, L.r, bufs[1 - cur], rc, Dc, ec, P.omega, i);
+  return pc_sync<T>(P, grid, st, s_ok);
+}
+
+// B_1 = A_1^-1 on the coarsest level: every participating block gathers the
+// interior right-hand side into w (shared memory), then one item per row.
+template <typename T>
+__device__ bool pc_coarse(const PCycleParams<T>& P, int i0, int di, bool grid, PcSync& st,
+                          volatile int* s_ok, double* w) {
+  const PLevel<T>& L = P.lv[P.nlev - 1];
+  const int ned = L.g.nedge, nf = P.nf;
+  for (int j = threadIdx.x; j < nf; j += blockDim.x)
+    w[j] = (double)L.r[(j & 1) * ned + P.fedge[j >> 1]];
+  __syncthreads();
+  for (int i = i0; i < ned + nf; i += di) {
+    if (i < ned) {
+      if (P.fidx[i] < 0) {
+        L.e[i] = T(0);
+        L.e[ned + i] = T(0);
+      }
+    } else {
+      const int row = i - ned;
+      const double* Ar = P.Ainv + (size_t)row * nf;
+      double s = 0.0;
+      for (int j = 0; j < nf; ++j) s += Ar[j] * w[j];
+      L.e[(row & 1) * ned + P.fedge[row >> 1]] = (T)s;
+    }
+  }
+  return pc_sync<T>(P, grid, st, s_ok);
+}
+
+// Steps 4-6 on P1 level l: prolongation from level l + 1 (fused with the
+// second local correction under LC_BOTH), post-smoothing; the correction ends
+// in L.e.  `final`: the last step of the kernel (no barrier after it).
+template <typename T, bool NS>
+__device__ bool pc_up(const PCycleParams<T>& P, int l, int i0, int di, bool grid, PcSync& st,
+                      volatile int* s_ok, bool final) {
+  const PLevel<T>& L = P.lv[l];
+  const P1Geom& g = L.g;
+  const int ned = g.nedge;
+  T* bufs[2];
+  pc_bufs<T>(P, l, bufs);
+  int cur = L.m & 1;                   // where the down sweep left the correction
+  const T* ec = P.lv[l + 1].e;
+  const int items = 8 * g.nC + 2 * g.nedc;
+  if (P.lc == HDGMG_LC_BOTH) {
+    for (int i = i0; i < items; i += di)
+      p1_prolong_lc<T, NS>(g, L.AIIinv, L.Y, L.r, ec, bufs[cur], bufs[1 - cur], i);
+    cur ^= 1;
+  } else {
+    for (int i = i0; i < items; i += di) p1_prolong<T>(g, L.Pi, ec, bufs[cur], bufs[1 - cur], i);
+  }
+  if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  for (int it = 0; it < L.m; ++it) {
+    for (int i = i0; i < ned; i += di)
+      p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+    cur ^= 1;
+    if (final && it + 1 == L.m) return true;
+    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  }
+  return true;
+}
+
+// block copy of `count` elements; 16-byte vectors when both ends allow it,
+// several loads in flight per thread
+template <typename T>
+__device__ __forceinline__ void pc_copy(T* dst, const T* src, int count) {
+  constexpr int V = 16 / sizeof(T);
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const int nv = count / V;
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    int i = threadIdx.x;
+    for (; i + 3 * (int)blockDim.x < nv; i += 4 * blockDim.x) {
+      const float4 a = s4[i], b = s4[i + blockDim.x], c = s4[i + 2 * blockDim.x],
+                   d = s4[i + 3 * blockDim.x];
+      d4[i] = a;
+      d4[i + blockDim.x] = b;
+      d4[i + 2 * blockDim.x] = c;
+      d4[i + 3 * blockDim.x] = d;
+    }
+    for (; i < nv; i += blockDim.x) d4[i] = s4[i];
+    for (int j = nv * V + threadIdx.x; j < count; j += blockDim.x) dst[j] = src[j];
+  } else {
+    for (int j = threadIdx.x; j < count; j += blockDim.x) dst[j] = src[j];
+  }
+}
+
+// Block 0 runs levels P.tail ... coarsest.  Staged: their operators, the
+// coarsest inverse and all their vectors are first copied into shared memory
+// (a copy of the parameters points there), lv[tail].r is taken from global
+// memory (where the grid's restriction put it) and lv[tail].e is written back.
+// Block 0 of a staged tail: thread 0 requests the tail's operators and the
+// coarsest inverse into shared memory by bulk copies on one mbarrier, before
+// the grid levels start, so that the copies overlap their work.  Every
+// array is a whole device allocation (16-byte aligned, its size a multiple
+// of 16 bytes by construction of the level sizes).
+template <typename T, bool NS>
+__device__ void pc_prefetch(const PCycleParams<T>& P, unsigned char* smem, unsigned long long* mbar) {
+  const int last = P.nlev - 1;
+  const int na = NS ? 64 : 36;
+  pc_mbar_init(mbar);
+  pc_mbar_expect(mbar, (unsigned)P.stage_bytes);
+  for (int l = P.tail; l < last; ++l) {
+    const PLevel<T>& gl = P.lv[l];
+    const unsigned nE = gl.g.nE, ned = gl.g.nedge, nC = nE / 4, sz = sizeof(T);
+    pc_bulk_copy(smem + gl.so_A, gl.A, na * nE * sz, mbar);
+    pc_bulk_copy(smem + gl.so_D, gl.Dinv, (NS ? 4 : 3) * ned * sz, mbar);
+    pc_bulk_copy(smem + gl.so_AII, gl.AIIinv, na * nC * sz, mbar);
+    pc_bulk_copy(smem + gl.so_Y, gl.Y, 128 * nC * sz, mbar);
+    pc_bulk_copy(smem + gl.so_Pi, gl.Pi, 64 * nC * sz, mbar);
+    if (gl.so_Rt != gl.so_Pi) pc_bulk_copy(smem + gl.so_Rt, gl.Rt, 64 * nC * sz, mbar);
+  }
+  pc_bulk_copy(smem + P.so_Ainv, P.Ainv, (unsigned)(sizeof(double) * P.nf * P.nf), mbar);
+}
+
+template <typename T, bool NS>
+__device__ void pc_tail(const PCycleParams<T>& P, PCycleParams<T>& sP, unsigned char* smem,
+                        unsigned long long* mbar, PcSync& st, volatile int* s_ok) {
+  const int last = P.nlev - 1, t0 = P.tail;
+  const int ti = threadIdx.x, td = blockDim.x;
+  const PCycleParams<T>* Q = &P;
+  double* w = reinterpret_cast<double*>(smem + P.so_w);
+  if (P.staged) {
+    {   // sP = P by the whole block, then thread 0 points the tail levels at shared memory
+      static_assert(sizeof(PCycleParams<T>) % 8 == 0, "parameter block copied as 8-byte words");
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&P);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sP);
+      for (int i = threadIdx.x; i < (int)(sizeof(PCycleParams<T>) / 8); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int l = t0; l <= last; ++l) {
+        PLevel<T>& q = sP.lv[l];
+        const int ned = q.g.nedge;
+        T* v = reinterpret_cast<T*>(smem + q.so_v);
+        q.r = v;
+        q.e = v + 2 * ned;
+        q.y = v + 4 * ned;
+        if (l < last) {
+          q.A = reinterpret_cast<const T*>(smem + q.so_A);
+          q.Dinv = reinterpret_cast<const T*>(smem + q.so_D);
+          q.AIIinv = reinterpret_cast<const T*>(smem + q.so_AII);
+          q.Y = reinterpret_cast<const T*>(smem + q.so_Y);
+          q.Pi = reinterpret_cast<const T*>(smem + q.so_Pi);
+          q.Rt = reinterpret_cast<const T*>(smem + q.so_Rt);
+        }
+      }
+      sP.Ainv = reinterpret_cast<const double*>(smem + P.so_Ainv);
+    }
+    for (int l = t0; l <= last; ++l) {
+      const PLevel<T>& gl = P.lv[l];
+      T* v = reinterpret_cast<T*>(smem + gl.so_v);
+      for (int i = threadIdx.x; i < 6 * gl.g.nedge; i += blockDim.x) v[i] = T(0);
+    }
+    __syncthreads();
+    if (!(t0 == 0 && P.rp_r0)) {
+      const int ned = P.lv[t0].g.nedge;
+      pc_copy<T>(reinterpret_cast<T*>(smem + P.lv[t0].so_v), P.lv[t0].r, 2 * ned);
+    }
+    // the operators were requested at the start of the kernel (pc_prefetch)
+    if (!pc_mbar_wait(mbar, P.wait_ns)) {
+      atomicOr(P.err, 2);
+      pc_mbar_wait(mbar, P.wait_ns);   // let copies still in flight land before leaving
+      *s_ok = 0;
+    }
+    __syncthreads();
+    if (!*s_ok) return;
+    Q = &sP;
+  }
+  for (int l = t0; l < last; ++l) pc_down<T, NS>(*Q, l, ti, td, false, st, s_ok);
+  pc_coarse<T>(*Q, ti, td, false, st, s_ok, w);
+  for (int l = last - 1; l >= t0; --l)
+    pc_up<T, NS>(*Q, l, ti, td, false, st, s_ok, l == 0 && !P.staged);
+  if (P.staged) {
+    __syncthreads();
+    const int ned = P.lv[t0].g.nedge;
+    pc_copy<T>(P.lv[t0].e, reinterpret_cast<const T*>(smem + P.lv[t0].so_v) + 2 * ned, 2 * ned);
+  }
+}
+
+template <typename T, bool NS, int NTHR>
+__device__ void pc_body(const PCycleParams<T>& P, PCycleParams<T>& sP, unsigned char* smem,
+                        unsigned long long* mbar, PcSync& st, volatile int* s_ok, int* s_tail) {
+  const int last = P.nlev - 1;
+  const int top = P.tail < last ? P.tail : last;   // levels [0, top) run on the whole grid
+  const int gi = blockIdx.x * NTHR + threadIdx.x, gd = gridDim.x * NTHR;
+  for (int l = 0; l < top; ++l)
+    if (!pc_down<T, NS>(P, l, gi, gd, true, st, s_ok)) return;
+  if (P.tail <= last) {
+    if (blockIdx.x == 0) {
+      *s_tail = 1;
+      pc_tail<T, NS>(P, sP, smem, mbar, st, s_ok);
+    }
+    if (top > 0 && !pc_grid_sync<T>(P, st, s_ok)) return;
+  } else {
+    if (!pc_coarse<T>(P, gi, gd, true, st, s_ok, reinterpret_cast<double*>(smem + P.so_w))) return;
+  }
+  for (int l = top - 1; l >= 0; --l)
+    if (!pc_up<T, NS>(P, l, gi, gd, true, st, s_ok, l == 0)) return;
+}
+
+template <typename T, bool NS, int NTHR>
+__global__ void __launch_bounds__(NTHR, 1) pcycle_kernel(const __grid_constant__ PCycleParams<T> P) {
+  extern __shared__ __align__(16) unsigned char pc_smem[];
+  __shared__ int s_ok, s_tail;
+  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ PCycleParams<T> sP;
+  PcSync st;
+  const bool prefetch = P.staged && blockIdx.x == 0;
+  if (threadIdx.x == 0) {
+    const unsigned long long c0 = *(volatile unsigned long long*)P.bar;
+    st.target = c0 - c0 % gridDim.x;
+    s_ok = *(volatile int*)P.err == 0;   // a wait of an earlier launch expired: do nothing
+    s_tail = 0;
+    if (s_ok && prefetch) pc_prefetch<T, NS>(P, pc_smem, &s_mbar);
+  }
+  __syncthreads();
+  if (!s_ok) return;
+  pc_body<T, NS, NTHR>(P, sP, pc_smem, &s_mbar, st, &s_ok, &s_tail);
+  // block 0 leaves no bulk copy into its shared memory in flight: when the
+  // tail was not reached (a barrier wait ran out), wait for the prefetch
+  // (bounded) before returning
+  if (prefetch && !s_tail && !pc_mbar_wait(&s_mbar, P.wait_ns)) atomicOr(P.err, 2);
 }
 
 // ------------------------------------------------ point smoothers (Sec. 4.1)
@@ -1454,6 +1785,9 @@ static void upload_jc() {
     double J[2][2][2];
     child_injection(J);
     cudaMemcpyToSymbol(c_Jc, J, sizeof(J));
+    float Jf[2][2][2];
+    for (int a = 0; a < 8; ++a) (&Jf[0][0][0])[a] = (float)(&J[0][0][0])[a];
+    cudaMemcpyToSymbol(c_Jcf, Jf, sizeof(Jf));
   });
 }
 
@@ -1472,19 +1806,31 @@ void launch_agglomerate(cudaStream_t s, int nc, bool ns, const T* Af, T* Ac, T* 
 template <typename T>
 void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
                              const T* r, T* e) {
+  const P1Geom g = make_p1geom(2 * nc);
   note_launch();
-  local_correction_kernel<T><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(nc, ns, AIIinv, Y, r, e);
+  if (ns)
+    local_correction_kernel<T, true><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(g, AIIinv, Y, r, e);
+  else
+    local_correction_kernel<T, false><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(g, AIIinv, Y, r, e);
 }
 
 template <typename T>
 void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, const T* r, const T* x,
                     T* out, T omega, bool sweep) {
-  const int ne = 2 * n * (n + 1);
+  const P1Geom g = make_p1geom(n);
+  const int nb = nblk(g.nedge, 128);
   note_launch();
-  if (sweep)
-    edge_p1_kernel<T, true><<<nblk(ne, 128), 128, 0, s>>>(n, ns, A, Dinv, r, x, out, omega);
-  else
-    edge_p1_kernel<T, false><<<nblk(ne, 128), 128, 0, s>>>(n, ns, A, Dinv, r, x, out, omega);
+  if (ns) {
+    if (sweep)
+      edge_p1_kernel<T, true, true><<<nb, 128, 0, s>>>(g, A, Dinv, r, x, out, omega);
+    else
+      edge_p1_kernel<T, true, false><<<nb, 128, 0, s>>>(g, A, Dinv, r, x, out, omega);
+  } else {
+    if (sweep)
+      edge_p1_kernel<T, false, true><<<nb, 128, 0, s>>>(g, A, Dinv, r, x, out, omega);
+    else
+      edge_p1_kernel<T, false, false><<<nb, 128, 0, s>>>(g, A, Dinv, r, x, out, omega);
+  }
 }
 
 template <typename T>
@@ -1543,7 +1889,7 @@ void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T*
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
   note_launch();
-  restrict_h_kernel<T><<<nblk(2 * nedc, 128), 128, 0, s>>>(nc, Pi, r, y, rc);
+  restrict_h_kernel<T><<<nblk(2 * nedc, 128), 128, 0, s>>>(make_p1geom(2 * nc), Pi, r, y, rc);
 }
 
 template <typename T>
@@ -1551,16 +1897,20 @@ void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T*
   upload_jc();
   const int tot = 8 * nc * nc + 4 * nc * (nc + 1);
   note_launch();
-  prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(nc, Pi, ec, e, y);
+  prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(make_p1geom(2 * nc), Pi, ec, e, y);
 }
 
 template <typename T>
 void launch_bj_first_restrict_p(cudaStream_t s, int n, int nd0, bool ns, const T* Dinv1,
                                 const T* r0, T* y0, T* r1, T* e1, T omega) {
-  const int ne = 2 * n * (n + 1);
+  const P1Geom g = make_p1geom(n);
   note_launch();
-  bj_first_restrict_p_kernel<T><<<nblk(ne, 128), 128, 0, s>>>(n, nd0, ns, Dinv1, r0, y0, r1, e1,
-                                                              omega);
+  if (ns)
+    bj_first_restrict_p_kernel<T, true><<<nblk(g.nedge, 128), 128, 0, s>>>(g, nd0, Dinv1, r0, y0,
+                                                                            r1, e1, omega);
+  else
+    bj_first_restrict_p_kernel<T, false><<<nblk(g.nedge, 128), 128, 0, s>>>(g, nd0, Dinv1, r0, y0,
+                                                                             r1, e1, omega);
 }
 
 template <typename T>
@@ -1638,6 +1988,70 @@ void launch_vcycle_tail(cudaStream_t s, const TailParams<T>& P) {
   (void)attr;
   note_launch();
   vcycle_tail_kernel<T, NTHR><<<1, NTHR, P.smem_bytes, s>>>(P);
+}
+
+// the persistent cycle: 1024 threads per block in FP32 (at most 64 registers
+// a thread), 512 in FP64; one block per SM; shared memory for the coarsest
+// right-hand side (nf <= kPcMaxNf doubles)
+constexpr int kPcMaxNf = 4096;
+constexpr int kPcMaxSmem = 200 * 1024;
+template <typename T>
+constexpr int pc_nthr() {
+  return sizeof(T) == 8 ? 512 : 1024;
+}
+
+template <typename T>
+int pcycle_threads() {
+  return pc_nthr<T>();
+}
+
+template <typename T>
+static void pc_attributes() {
+  static std::once_flag flags[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(flags[dev & 63], [] {
+    cudaFuncSetAttribute(pcycle_kernel<T, false, pc_nthr<T>()>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPcMaxSmem);
+    cudaFuncSetAttribute(pcycle_kernel<T, true, pc_nthr<T>()>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPcMaxSmem);
+  });
+}
+
+template <typename T>
+int pcycle_max_blocks(int smem_bytes) {
+  int dev = 0, sms = 0, per_sm = 0, per_sm_ns = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  pc_attributes<T>();
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcycle_kernel<T, false, pc_nthr<T>()>,
+                                                    pc_nthr<T>(), smem_bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_ns, pcycle_kernel<T, true, pc_nthr<T>()>,
+                                                    pc_nthr<T>(), smem_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (per_sm < per_sm_ns ? per_sm : per_sm_ns) * sms;
+}
+
+template <typename T>
+cudaError_t launch_pcycle(cudaStream_t s, const PCycleParams<T>& P, int blocks) {
+  if (P.nf > kPcMaxNf || blocks < 1 || P.smem_bytes > kPcMaxSmem) return cudaErrorInvalidValue;
+  upload_jc();
+  pc_attributes<T>();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+  cfg.blockDim = dim3(pc_nthr<T>(), 1, 1);
+  cfg.dynamicSmemBytes = (size_t)P.smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  if (P.ns) return cudaLaunchKernelEx(&cfg, pcycle_kernel<T, true, pc_nthr<T>()>, P);
+  return cudaLaunchKernelEx(&cfg, pcycle_kernel<T, false, pc_nthr<T>()>, P);
 }
 
 template <typename T>
@@ -1827,6 +2241,12 @@ template void launch_cg_update<float>(cudaStream_t, int64_t, const double*, floa
 template void launch_cg_direction<double>(cudaStream_t, int64_t, const double*, const double*, double*);
 template void launch_cg_direction<float>(cudaStream_t, int64_t, const double*, const float*, float*);
 template void launch_vcycle_tail<float>(cudaStream_t, const TailParams<float>&);
+template int pcycle_threads<float>();
+template int pcycle_threads<double>();
+template int pcycle_max_blocks<float>(int);
+template int pcycle_max_blocks<double>(int);
+template cudaError_t launch_pcycle<float>(cudaStream_t, const PCycleParams<float>&, int);
+template cudaError_t launch_pcycle<double>(cudaStream_t, const PCycleParams<double>&, int);
 template void launch_convert<float, double>(cudaStream_t, int64_t, const float*, double*);
 template void launch_convert<double, double>(cudaStream_t, int64_t, const double*, double*);
 

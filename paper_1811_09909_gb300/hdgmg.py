@@ -29,7 +29,7 @@ EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
             "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy",
             "hdgmg_apply_operator_noalloc", "hdgmg_gradient", "hdgmg_adjoint",
             "hdgmg_batch_create", "hdgmg_batch_setup", "hdgmg_batch_solve",
-            "hdgmg_batch_context", "hdgmg_batch_destroy"]
+            "hdgmg_batch_context", "hdgmg_batch_destroy", "hdgmg_check_cycle_timeout"]
 
 
 class Problem(ctypes.Structure):
@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("cluster_tail_n", ctypes.c_int32),
                 ("gmres_restart", ctypes.c_int32), ("smoother", ctypes.c_int32),
-                ("condensation", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32)]
+                ("condensation", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32),
+                ("pcycle", ctypes.c_int32), ("pcycle_tail_n", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -107,6 +108,7 @@ def load():
     lib.hdgmg_batch_destroy.argtypes = [P]
     lib.hdgmg_batch_destroy.restype = None
     lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
+    lib.hdgmg_check_cycle_timeout.argtypes = [P, I32]
     lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
     lib.hdgmg_last_error.argtypes = []
     lib.hdgmg_last_error.restype = ctypes.c_char_p

@@ -1,6 +1,6 @@
 """GPU parity of the CUDA path against the CPU FP64 oracle, through the C ABI.
 
-Tolerances (derived in DESIGN.md, "Parity tolerances"):
+Tolerances, from the arithmetic:
   * FP64 element operators and level operators: |gpu - oracle| <= 1e-11 max|A|
     (two different FP64 factorisations of local blocks whose condition
     numbers stay below ~1e4);

@@ -1,8 +1,9 @@
 """hdgmg_apply_operator_noalloc: the allocation-free variant of
 hdgmg_apply_operator for callers that cannot allocate device memory when they
-apply the operator (for example while a stream is being captured into a CUDA
-graph).  It keeps its temporaries in one static device array of 2^20 doubles
-instead of cudaMalloc'd buffers.
+apply the operator (their device memory belongs to another allocator, or their
+loop must not pay for cudaMalloc/cudaFree, which can synchronise the device).
+It keeps its temporaries in one static device array of 2^20 doubles instead of
+cudaMalloc'd buffers.
 
 Checked through the C ABI against hdgmg_apply_operator, on two calls in a row
 (the array keeps the previous call's contents), on an FP64 level and on an
