@@ -117,7 +117,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(), "cpu_baseline": cb,
+            "data": "synthetic", "config": workload_config(SAMPLE_N), "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -306,26 +306,46 @@ def run_ours(args):
                           "solve_only_value": replicas.whole_job_rate(dofs, world,
                                                                       mixed["solve_ms"])},
                 "clocks": mixed["clocks"], "e2e": e2e, "gpu_launches": mixed["launches"],
-                "roofline": roofline_condense(mixed["condense_ms"]),
+                "roofline": roofline_pcg(arms["mixed"], mixed),
+                "roofline_condense": roofline_condense(mixed["condense_ms"]),
                 "vcycle": vcycle_bandwidth(arms["mixed"], dev)}
     return line
 
 
 # ------------------------------------------------------------- roofline
+def hbm_peak():
+    """HBM copy bandwidth measured on this machine's GPUs (the driver writes it
+    next to this file); the recipe's earlier single measurement otherwise."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
 # FP64 peak of GB300 from unit counts and clock: 152 SMs x 2 FP64 FMA/clk
-# x 2 flop x 2.07 GHz (a standalone FMA-throughput probe measured 1.18).
+# x 2 flop x 2.07 GHz; a throughput probe on the box measured 1.20 TFLOP/s
+# for FP64 FMA and 1.06 for FP64 MMA (mma.sync m8n8k4), so the FP64 set-up
+# runs on the FMA pipe (paper_1811_09909_gb300/probes/mma_rate.cu).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one condensation launch at 256^2, p = 4: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of the current kernel
-# (profiles/condense_256_p4.md); None until captured for this kernel.
+# (576 KB read, 54.0 MB written); None until captured for this kernel.
 CONDENSE_TRAFFIC_BYTES = 576512 + 54012416
+# DRAM traffic of one PCG iteration at 256^2, p = 4, mixed form: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels of one
+# iteration (host-driven loop, warm L2); None until captured for these kernels.
+PCG_ITER_TRAFFIC_BYTES = None
 
 
 def condense_flops(p, nE):
     """Algorithmic flops of K1 per launch in the basis that diagonalises every
     volume block: s_i = kappa g_i + tau e_i (n_v FMAs), U = s^-1/2 (kappa P +
     tau Q) (n_v n_t entries, 3 flops each), A_e = kappa K + tau I - U^T U
-    (n_t (n_t + 1) / 2 packed entries, n_v FMAs each, plus the kappa K term)."""
+    (n_t (n_t + 1) / 2 packed entries, n_v FMAs each, plus the kappa K term).
+    At p = 4 this is 12.5 kflop per element, 3.2x fewer than the block
+    elimination count n_v^3/3 + 2 n_v^2 n_t + n_t^2 n_v = 40.2 kflop that the
+    per-element factorisation route needs."""
     nv, nt = (p + 1) ** 2, 4 * (p + 1)
     nsa = nt * (nt + 1) // 2
     return (2.0 * nv + 3.0 * nv * nt + 2.0 * nsa * (nv + 1)) * nE
@@ -334,12 +354,48 @@ def condense_flops(p, nE):
 def roofline_condense(ms):
     flops = condense_flops(P_ORDER, N_MESH * N_MESH)
     achieved = flops / (ms * 1e-3) / 1e12
+    nv, nt = (P_ORDER + 1) ** 2, 4 * (P_ORDER + 1)
+    elim = (nv ** 3 / 3 + 2 * nv * nv * nt + nt * nt * nv) * N_MESH * N_MESH
     return {"kernel": "condense_eig_kernel (element condensation, FP64)", "bound": "alu",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": CONDENSE_TRAFFIC_BYTES,
             "algorithmic_flops_per_launch": flops, "launch_ms": ms,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz "
-                           "(FMA probe on the box: 1.18 TFLOP/s)"}
+            "flop_count": "eigenbasis route, 12.5 kflop per element at p=4; the block-elimination "
+                          "count of the factorisation route (40.2 kflop per element) would read "
+                          f"{elim / (ms * 1e-3) / 1e12:.2f} TFLOP/s for the same launch",
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz (probe on the box: "
+                           "1.20 TFLOP/s FP64 FMA, 1.06 FP64 MMA)"}
+
+
+def pcg_iteration_bytes(solver):
+    """Algorithmic HBM bytes of one mixed PCG iteration: the FP32 V-cycle
+    (vcycle_bytes), the FP64 outer matvec (packed operator once, p read, A p
+    read and written) and the CG vector passes of the fused kernels (r.z,
+    p = z + beta p, p.Ap, x += alpha p with r -= alpha Ap and the FP32 copy of r):
+    108 bytes per trace value."""
+    n, nd = solver.level_shape(0)
+    nE, ned = n * n, 2 * n * (n + 1)
+    nsym = 4 * nd * (4 * nd + 1) // 2
+    vals = nd * ned
+    matvec64 = nsym * nE * 8 + 3 * vals * 8
+    cg = 108 * vals
+    return vcycle_bytes(solver) + matvec64 + cg, matvec64, cg
+
+
+def roofline_pcg(solver, info):
+    peak, src = hbm_peak()
+    b, mv, cg = pcg_iteration_bytes(solver)
+    it_ms = info["solve_ms"] / max(info["iters"], 1)
+    achieved = b / (it_ms * 1e-3) / 1e9
+    return {"kernel": "PCG iteration: FP32 V-cycle (pcycle_kernel over the P1 levels, fine-level "
+                      "matvec and block-Jacobi kernels) + FP64 outer matvec + fused CG updates",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": PCG_ITER_TRAFFIC_BYTES,
+            "algorithmic_bytes_per_iteration": b, "fp64_matvec_bytes": mv, "cg_vector_bytes": cg,
+            "iteration_ms": it_ms,
+            "peak_source": f"{src} HBM copy bandwidth",
+            "note": "iteration time = CUDA-event solve time of the library / iterations (the solve "
+                    "also holds the right-hand side, the final FP64 residual and the recovery)"}
 
 
 def vcycle_bytes(solver):
@@ -386,10 +442,12 @@ def vcycle_bandwidth(solver, dev, reps=20):
     ms = e0.elapsed_time(e1) / reps
     b = vcycle_bytes(solver)
     gbs = b / (ms * 1e-3) / 1e9
+    peak, src = hbm_peak()
     return {"ms": ms, "algorithmic_bytes": b, "achieved_gbs": gbs,
-            "hbm_peak_gbs": 6797.9, "frac": gbs / 6797.9,
-            "note": "FP32 V-cycle launched kernel by kernel (hdgmg_apply_vcycle); L2-resident "
-                    "coarse levels make this latency-bound"}
+            "hbm_peak_gbs": peak, "peak_source": src, "frac": gbs / peak,
+            "note": "one FP32 V-cycle through hdgmg_apply_vcycle (fine level launched, the P1 levels "
+                    "in one persistent cooperative launch; FP64<->FP32 conversions of r and e "
+                    "included); the L2-resident coarse levels keep it latency-bound"}
 
 
 # ------------------------------------------------------- extra workloads
@@ -608,7 +666,8 @@ def run_unstructured(dev, steps, warmup, n=96, p=3):
                           "solve_ms": i32[-1].t_solve_ms, "iters": i32[-1].iters,
                           "rel_res": max(i.rel_res for i in i32)},
            "apply_roofline": {"bound": "hbm", "kernel": "u_elem_matvec_mesh_kernel + u_edge_kernel",
-                              "achieved": gbs, "peak": 6797.9, "unit": "GB/s", "frac": gbs / 6797.9,
+                              "achieved": gbs, "peak": hbm_peak()[0], "unit": "GB/s",
+                              "frac": gbs / hbm_peak()[0],
                               "ms": ams, "algorithmic_bytes": abytes}}
     s.close()
     return out

@@ -194,6 +194,12 @@ typedef struct {
                              one thread block of the launch (block barriers)
                              while the others wait at one grid barrier; 0:
                              every level on the whole grid.  16             */
+  int32_t pcg_graph;      /* 1: the PCG loop (krylov = CG, precision FP64,
+                             FP32 or BF16) runs as one CUDA graph with a
+                             device-side while node; 0: every iteration's
+                             kernels are launched from the host, which reads
+                             the stop test back after each iteration (same
+                             arithmetic; for per-kernel profiling).  1       */
 } hdgmg_opts;
 
 typedef struct {

@@ -415,12 +415,17 @@ class HDGProblem:
         b = g - A @ lamD
         return A[fd][:, fd].tocsc(), b[fd], A, g, lamD
 
-    def solve_direct(self, f, gD=None):
+    def solve_direct(self, f, gD=None, ordering="COLAMD"):
         """Sparse direct solve (SuperLU) of the trace system; returns the full
-        trace vector in the library layout [nd][n_edges]."""
+        trace vector in the library layout [nd][n_edges].  ordering: SuperLU's
+        column ordering (permc_spec); "MMD_AT_PLUS_A" (minimum degree on
+        A^T + A) fills far less on these 2-D trace systems at large n."""
         Aff, bf, A, g, lamD = self.system(f, gD)
         lam = lamD.copy()
-        lam[self.free_dofs()] = spla.spsolve(Aff, bf)
+        if ordering == "COLAMD":
+            lam[self.free_dofs()] = spla.spsolve(Aff, bf)
+        else:
+            lam[self.free_dofs()] = spla.splu(Aff.tocsc(), permc_spec=ordering).solve(bf)
         return edge_major_to_api(lam, self.n, self.nd)
 
     # -- recovery ---------------------------------------------------------

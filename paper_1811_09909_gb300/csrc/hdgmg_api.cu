@@ -1138,6 +1138,33 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     int outer = 0;
     STATUS_TRY(refine_solve(c, nb, &it, &outer, &rel, &conv, &breakdown));
     c->refinements = outer;
+  } else if (o.krylov == HDGMG_KRYLOV_CG && o.pcg_graph == 0) {
+    // the same PCG, each iteration's kernels launched from the host, which
+    // reads the stop flag back after every iteration (for per-kernel
+    // profiling: the kernels are not hidden inside a graph)
+    CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    if (o.precision != HDGMG_PREC_FP64)
+      launch_convert<double, float>(s, len, c->r, c->levels[0].d32.r);
+    CUDA_TRY(cudaMemsetAsync(c->pv, 0, sizeof(double) * len, s));
+    CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int) * 2, s));
+    c->init_h[0] = 1.0;
+    c->init_h[1] = bb;
+    CUDA_TRY(cudaMemcpyAsync(c->scal + 0, &c->init_h[0], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->scal + 6, &c->init_h[1], sizeof(double), cudaMemcpyHostToDevice, s));
+    for (;;) {
+      cg_body64(c, 0);
+      STATUS_TRY(check_launch("PCG iteration"));
+      CUDA_TRY(cudaMemcpyAsync(c->it_h, c->it_dev, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (c->it_h[1] || c->it_h[0] >= o.max_it) break;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->scal_h + 5, c->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    it = *c->it_h;
+    const double rr = c->scal_h[5];
+    rel = std::sqrt(rr) / nb;
+    breakdown = !std::isfinite(rr);
+    conv = !breakdown && rel <= o.rtol;
   } else if (o.krylov == HDGMG_KRYLOV_CG) {
     // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle), the
     // whole iteration loop replayed as one CUDA graph
@@ -1276,6 +1303,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->l2_persist_mb = 64;
   o->pcycle = 1;
   o->pcycle_tail_n = 16;
+  o->pcg_graph = 1;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }

@@ -210,6 +210,8 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
 }
 
 // --------------------------------------------------- K7 block-Jacobi update
+// every load of an edge (r, y, e, xadd, D^-1) is issued before its stores, so
+// the edge's 5 ND-mode round trips overlap
 template <typename T, int ND, bool NS>
 __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __restrict__ r,
                                  T* __restrict__ y, T* __restrict__ e, T omega, int first,
@@ -217,27 +219,36 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
   const int nedge = 2 * n * (n + 1);
   const int edge = blockIdx.x * blockDim.x + threadIdx.x;
   if (edge >= nedge || bnd_edge(n, edge)) return;
-  T d[ND];
+  T d[ND], eo[ND], Dv[NS ? ND * ND : ND * (ND + 1) / 2];
 #pragma unroll
-  for (int k = 0; k < ND; ++k) {
-    const size_t ix = (size_t)k * nedge + edge;
-    d[k] = first ? r[ix] : r[ix] - y[ix];
-    if (!first) y[ix] = T(0);
+  for (int t = 0; t < (NS ? ND * ND : ND * (ND + 1) / 2); ++t) Dv[t] = Dinv[(size_t)t * nedge + edge];
+  if (first) {
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      d[k] = r[(size_t)k * nedge + edge];
+      eo[k] = T(0);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const size_t ix = (size_t)k * nedge + edge;
+      d[k] = r[ix] - y[ix];
+      eo[k] = e[ix];
+    }
+    if (xadd) {
+      eo[0] += xadd[edge];
+      eo[1] += xadd[(size_t)nedge + edge];
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) y[(size_t)k * nedge + edge] = T(0);
   }
 #pragma unroll
   for (int a = 0; a < ND; ++a) {
     T s = T(0);
 #pragma unroll
-    for (int b = 0; b < ND; ++b)
-      s += Dinv[(size_t)(NS ? a * ND + b : pk_any(a, b)) * nedge + edge] * d[b];
+    for (int b = 0; b < ND; ++b) s += Dv[NS ? a * ND + b : pk_any(a, b)] * d[b];
     const size_t ix = (size_t)a * nedge + edge;
-    if (first) {
-      e[ix] = omega * s;
-    } else {
-      T eo = e[ix];
-      if (xadd && a < 2) eo += xadd[ix];
-      e[ix] = eo + omega * s;
-    }
+    e[ix] = first ? omega * s : eo[a] + omega * s;
   }
 }
 

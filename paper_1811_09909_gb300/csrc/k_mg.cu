@@ -1521,29 +1521,47 @@ __global__ void convert_kernel(int64_t len, const A* __restrict__ in, B* __restr
 //   mode 0: scal[1] = p.Ap,     scal[2] = alpha = scal[0] / scal[1]
 //   mode 1: scal[3] = r.z,      scal[4] = beta = scal[3] / scal[0], scal[0] = scal[3]
 //   mode 2: scal[5] = r.r
+// block reduction by warp shuffles then one warp over the warp sums (a fixed
+// order for a fixed block size); sh holds at least blockDim / 32 doubles
 __device__ __forceinline__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+  __syncthreads();                         // sh may still be read by an earlier call
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (l == 0) sh[32] = v;
   }
-  return sh[0];
+  __syncthreads();
+  return sh[32];
 }
 
-// returns true in the last block to finish, after all partials are visible
+// returns true in the last block to finish, after all partials are visible;
+// thread 0 published this block's partial before calling
 __device__ __forceinline__ bool last_block(unsigned* counter) {
   __shared__ bool is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();                       // release the partial
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    if (is_last) __threadfence();          // acquire every other block's partial
+  }
   __syncthreads();
   return is_last;
 }
 
+// sum of n partials in a fixed order: thread t adds partial[t], partial[t + B],
+// ... (loads issued together), then block_sum
 __device__ __forceinline__ double sum_partials(const double* partial, int n, double* sh) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += ((volatile const double*)partial)[i];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int B = blockDim.x;
+  int i = threadIdx.x, k = 0;
+  for (; i < n && k < 4; i += B, ++k) v[k] = __ldcg(partial + i);
+  double s = ((v[0] + v[1]) + v[2]) + v[3];
+  for (; i < n; i += B) s += __ldcg(partial + i);
   return block_sum(s, sh);
 }
 
@@ -1553,11 +1571,21 @@ __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __
                                                         double* __restrict__ partial,
                                                         unsigned* __restrict__ counter,
                                                         double* __restrict__ scal, int mode) {
-  __shared__ double sh[256];
+  __shared__ double sh[33];
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x)
-    s += (double)a[i] * (double)b[i];
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * G < len; i += 4 * G) {      // four independent loads in flight, summed in order
+    const double a0 = (double)a[i], a1 = (double)a[i + G], a2 = (double)a[i + 2 * G],
+                 a3 = (double)a[i + 3 * G];
+    const double b0 = (double)b[i], b1 = (double)b[i + G], b2 = (double)b[i + 2 * G],
+                 b3 = (double)b[i + 3 * G];
+    s += a0 * b0;
+    s += a1 * b1;
+    s += a2 * b2;
+    s += a3 * b3;
+  }
+  for (; i < len; i += G) s += (double)a[i] * (double)b[i];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
   if (!last_block(counter)) return;
@@ -1593,17 +1621,34 @@ __global__ void cg_direction_zero_kernel(int64_t len, const double* __restrict__
 
 // x += alpha p, r -= alpha Ap, scal[5] = r.r, then the loop test of the
 // graph: stop when r.r <= tol2 * scal[6], on NaN, or after max_it iterations
+// (h == 0: no graph; it[1] = 1 tells the host loop to stop)
 template <typename T>
 __global__ void __launch_bounds__(256) cg_update_test_kernel(
     int64_t len, double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
     const T* __restrict__ p, const T* __restrict__ Ap, double* __restrict__ partial,
     unsigned* __restrict__ counter, cudaGraphConditionalHandle h, int* __restrict__ it,
     int max_it, double tol2, float* __restrict__ r32) {
-  __shared__ double sh[256];
+  __shared__ double sh[33];
   const T alpha = (T)scal[2];
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + G < len; i += 2 * G) {          // two values per pass, loads first
+    const T p0 = p[i], p1 = p[i + G], q0 = Ap[i], q1 = Ap[i + G];
+    const T x0 = x[i], x1 = x[i + G], s0 = r[i], s1 = r[i + G];
+    x[i] = x0 + alpha * p0;
+    x[i + G] = x1 + alpha * p1;
+    const T r0 = s0 - alpha * q0, r1 = s1 - alpha * q1;
+    r[i] = r0;
+    r[i + G] = r1;
+    if (r32) {
+      r32[i] = (float)r0;
+      r32[i + G] = (float)r1;
+    }
+    s += (double)r0 * (double)r0;
+    s += (double)r1 * (double)r1;
+  }
+  for (; i < len; i += G) {
     x[i] += alpha * p[i];
     const T ri = r[i] - alpha * Ap[i];
     r[i] = ri;
@@ -1619,7 +1664,12 @@ __global__ void __launch_bounds__(256) cg_update_test_kernel(
     scal[5] = rr;
     *counter = 0u;
     const int k = ++(*it);
-    if (!(rr > tol2 * scal[6]) || k >= max_it) cudaGraphSetConditional(h, 0);
+    if (!(rr > tol2 * scal[6]) || k >= max_it) {
+      if (h)
+        cudaGraphSetConditional(h, 0);
+      else
+        it[1] = 1;                // host-driven loop: the stop flag it reads back
+    }
   }
 }
 

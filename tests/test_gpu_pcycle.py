@@ -142,3 +142,18 @@ def test_pcycle_expired_wait_reports_timeout(precision):
     # a context without the persistent cycle rejects the check
     t = make(wl, coarsest_n=4, pcycle=0)
     assert t.lib.hdgmg_check_cycle_timeout(t.ctx, 2000) == -1
+
+
+def test_host_driven_pcg_equals_graph_pcg():
+    """pcg_graph = 0 launches each PCG iteration from the host (for per-kernel
+    profiling): the same kernels in the same order, so the same iterate."""
+    n, p = 32, 3
+    wl = workload(n, p, 90)
+    kw = dict(coarsest_n=4, m_fine=1, m_max=2, precision=hdgmg.PREC_FP32)
+    a = make(wl, pcg_graph=1, **kw)
+    b = make(wl, pcg_graph=0, **kw)
+    f = cuda(wl.f[0])
+    la, _, _, ia = a.solve(f, want_u=False, want_q=False)
+    lb, _, _, ib = b.solve(f, want_u=False, want_q=False)
+    assert ia.iters == ib.iters and ib.converged == 1
+    assert np.array_equal(host(la), host(lb))

@@ -158,3 +158,20 @@ def test_example1_forcing_matches_finite_differences():
     lap = (-u(x + 2 * d, y) + 16 * u(x + d, y) - 30 * u(x, y) + 16 * u(x - d, y) - u(x - 2 * d, y)) / (12 * d * d) \
         + (-u(x, y + 2 * d) + 16 * u(x, y + d) - 30 * u(x, y) + 16 * u(x, y - d) - u(x, y - 2 * d)) / (12 * d * d)
     assert np.allclose(W.ex1_f(x, y), -lap, rtol=1e-7)
+
+
+def test_direct_solve_orderings_agree():
+    """The minimum-degree column ordering used at full size gives the same
+    direct solution as SuperLU's default ordering (symmetric HDG and the
+    non-symmetric convection-diffusion system)."""
+    from paper_1811_09909_gb300 import workloads as W
+    wl = W.lognormal(8, 3, seed=5)
+    pr = hdg.HDGProblem(8, 3, np.exp(wl.log_kappa), wl.tau())
+    a = pr.solve_direct(wl.f[0])
+    b = pr.solve_direct(wl.f[0], ordering="MMD_AT_PLUS_A")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    wc = W.convdiff(8, 2, eps=1e-2)
+    pc = hdg.HDGProblem(8, 2, np.exp(wc.log_kappa), wc.tau(), beta=wc.beta)
+    a = pc.solve_direct(wc.f[0])
+    b = pc.solve_direct(wc.f[0], ordering="MMD_AT_PLUS_A")
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
