@@ -200,6 +200,18 @@ typedef struct {
                              kernels are launched from the host, which reads
                              the stop test back after each iteration (same
                              arithmetic; for per-kernel profiling).  1       */
+  int32_t rhs_block;      /* > 1: hdgmg_solve with nrhs > 1 solves blocks of
+                             up to rhs_block (<= 16) right-hand sides
+                             together: FP64 iterative refinement (residual of
+                             the FP64 operator per right-hand side) around
+                             k simultaneous FP32 PCGs that share every
+                             V-cycle, FP32 matvec and vector pass (each
+                             level operator is read once for all k).  Needs
+                             a symmetric operator, krylov CG, BLOCK_JACOBI
+                             and precision FP32 or FP32_IR (EINVAL
+                             otherwise); info then describes the last block
+                             (iters: inner iterations, rel_res: the worst
+                             right-hand side).  0 or 1: one at a time.  0    */
 } hdgmg_opts;
 
 typedef struct {

@@ -50,6 +50,8 @@ namespace {
   } while (0)
 }  // namespace
 
+constexpr int kMaxRhsBlock = 16;
+
 struct hdgmg_ctx {
   hdgmg_problem prob{};
   hdgmg_opts opts{};
@@ -137,6 +139,18 @@ struct hdgmg_ctx {
   unsigned long long* pc_bar = nullptr;
   PCycleParams<float> pc32;
   PCycleParams<double> pc64;
+  // blocked solves of up to kb right-hand sides (opts.rhs_block): FP32 level
+  // vectors hold kb copies [kb][...]; kr is the count the V-cycle launches
+  // run with (1 outside a blocked solve)
+  int kb = 1, kr = 1;
+  PCycleParams<float> pc32b;   // the persistent cycle for kr > 1 (no block-0 tail)
+  int pc_blocks_b = 0;
+  double *Xb = nullptr, *Rb = nullptr, *Bb = nullptr, *Lb = nullptr;   // FP64 [kb][len]
+  double *scal64b = nullptr, *scal32b = nullptr, *partial_b = nullptr, *scal_hb = nullptr;
+  unsigned* counter_b = nullptr;                                         // [kb + 1]
+  cudaGraph_t cgb_graph[kMaxRhsBlock + 1] = {};
+  cudaGraphExec_t cgb_exec[kMaxRhsBlock + 1] = {};
+  long long cgb_body_launches[kMaxRhsBlock + 1] = {};
 
   template <typename T>
   cudaError_t alloc(T** p_, size_t count) {
@@ -162,6 +176,9 @@ template <> CTailParams<float>& ctailp<float>(hdgmg_ctx* c) { return c->cp32; }
 template <typename T> PCycleParams<T>& pcyclep(hdgmg_ctx* c);
 template <> PCycleParams<double>& pcyclep<double>(hdgmg_ctx* c) { return c->pc64; }
 template <> PCycleParams<float>& pcyclep<float>(hdgmg_ctx* c) { return c->pc32; }
+template <typename T> PCycleParams<T>& pcycleb(hdgmg_ctx* c);
+template <> PCycleParams<double>& pcycleb<double>(hdgmg_ctx* c) { return c->pc64; }   // FP64: unblocked
+template <> PCycleParams<float>& pcycleb<float>(hdgmg_ctx* c) { return c->pc32b; }
 template <typename T> TailParams<T>& tailp(hdgmg_ctx* c);
 template <> TailParams<double>& tailp<double>(hdgmg_ctx* c) { return c->tp64; }
 template <> TailParams<float>& tailp<float>(hdgmg_ctx* c) { return c->tp32; }
@@ -482,6 +499,7 @@ void plan_pcycle(hdgmg_ctx* c) {
   P.fidx = c->freeidx;
   P.fedge = c->fedge;
   P.nf = c->nf;
+  P.dco = make_fastdiv(c->levels[last].nEdge + c->nf);
   P.omega = (T)o.omega;
   P.lc = o.local_corr;
   P.ns = c->ns ? 1 : 0;
@@ -492,6 +510,21 @@ void plan_pcycle(hdgmg_ctx* c) {
   const int nthr = pcycle_threads<T>();
   const int want = (c->levels[ls].nEdge + nthr - 1) / nthr;
   c->pc_blocks = P.tail == 0 ? 1 : (want < maxb ? want : maxb);
+  if (std::is_same<T, float>::value && c->kb > 1) {
+    // blocked solves: the same levels for up to kb right-hand sides, every
+    // level on the whole grid (no block-0 tail: k vector sets do not fit in
+    // one block's shared memory), shared memory for the k coarse right-hand sides
+    PCycleParams<T>& B = pcycleb<T>(c);
+    B = P;
+    B.tail = B.nlev;
+    B.staged = 0;
+    B.so_w = 0;
+    B.smem_bytes = (int)(sizeof(double) * (size_t)c->kb * (c->nf > 0 ? c->nf : 1));
+    const int maxbb = pcycle_max_blocks<T>(B.smem_bytes);
+    const int wantb = (c->kb * c->levels[ls].nEdge + nthr - 1) / nthr;
+    c->pc_blocks_b = wantb < maxbb ? wantb : maxbb;
+    if (c->pc_blocks_b < 1) return;
+  }
   c->pc_start = ls;
 }
 
@@ -520,11 +553,11 @@ void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y, const T* xadd = nullptr
   Level& L = c->levels[l];
   if constexpr (std::is_same<T, float>::value) {
     if (L.A16) {
-      launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f, xadd);
+      launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f, xadd, c->kr);
       return;
     }
   }
-  launch_matvec<T>(c->stream, L.n, L.nd, c->ns, ld<T>(L).A, x, y, T(1), xadd);
+  launch_matvec<T>(c->stream, L.n, L.nd, c->ns, ld<T>(L).A, x, y, T(1), xadd, c->kr);
 }
 
 // A P1 level run by separate launches with the fused edge sweeps (not in a
@@ -589,11 +622,13 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   LevelData<T>& D = ld<T>(L);
   const int last = (int)c->levels.size() - 1;
   if (l == c->pc_start) {                                   // persistent P1 cycle
-    PCycleParams<T> P = pcyclep<T>(c);
+    const bool blocked = std::is_same<T, float>::value && c->kr > 1;
+    PCycleParams<T> P = blocked ? pcycleb<T>(c) : pcyclep<T>(c);
     P.rp_r0 = rp_r0;
     P.rp_y0 = rp_y0;
     P.rp_nd0 = rp_nd0;
-    launch_pcycle<T>(s, P, c->pc_blocks);
+    P.nrhs = c->kr;
+    launch_pcycle<T>(s, P, blocked ? c->pc_blocks_b : c->pc_blocks);
     return;
   }
   if (l == c->ctail_start) {                                // cluster-fused P1 tail
@@ -605,12 +640,13 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
     return;
   }
   if (l == last) {                                          // B_1 = A_1^-1
-    launch_coarse_solve<T>(s, L.n, c->freeidx, c->fedge, c->nf, c->cinv, D.r, D.e);
+    launch_coarse_solve<T>(s, L.n, c->freeidx, c->fedge, c->nf, c->cinv, D.r, D.e, c->kr);
     return;
   }
   const T omega = (T)c->opts.omega;
   const int lc = c->opts.local_corr;
   const bool ns = c->ns;
+  const int k = c->kr;
   if (p1_launched(c, l)) {
     // P1 level: fused edge-centric sweeps, ping-ponging between e and y.  The
     // first sweep (from e = 0) writes y; after the 2m - 1 sweeps of the level
@@ -620,23 +656,23 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
     T* bufs[2] = {D.e, D.y};
     int cur = 1;
     if (rp_r0)
-      launch_bj_first_restrict_p<T>(s, L.n, rp_nd0, ns, D.Dinv, rp_r0, rp_y0, D.r, bufs[1], omega);
+      launch_bj_first_restrict_p<T>(s, L.n, rp_nd0, ns, D.Dinv, rp_r0, rp_y0, D.r, bufs[1], omega, k);
     else
-      launch_bj_update<T>(s, L.n, 2, ns, D.Dinv, D.r, bufs[0], bufs[1], omega, 1);
+      launch_bj_update<T>(s, L.n, 2, ns, D.Dinv, D.r, bufs[0], bufs[1], omega, 1, nullptr, k);
     for (int i = 1; i < L.m; ++i) {
-      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true);
+      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true, k);
       cur ^= 1;
     }
     if (lc != HDGMG_LC_NONE)
-      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur]);
-    launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, false);
-    launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, bufs[1 - cur], Dc.r);
+      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur], k);
+    launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, false, k);
+    launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, bufs[1 - cur], Dc.r, k);
     vcycle<T>(c, l + 1);
-    launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, bufs[cur], bufs[1 - cur]);
+    launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, bufs[cur], bufs[1 - cur], k);
     if (lc == HDGMG_LC_BOTH)
-      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur]);
+      launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, bufs[cur], k);
     for (int i = 0; i < L.m; ++i) {
-      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true);
+      launch_edge_p1<T>(s, L.n, ns, D.A, D.Dinv, D.r, bufs[cur], bufs[1 - cur], omega, true, k);
       cur ^= 1;
     }
     return;                                    // cur == 0: the correction is in D.e
@@ -644,17 +680,17 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   const bool bj = c->opts.smoother == HDGMG_SMOOTH_BLOCK_JACOBI;
   // step 2: pre-smoothing (the first sweep starts from e = 0)
   if (bj) {
-    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1);
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 1, nullptr, k);
     for (int i = 1; i < L.m; ++i) {
       level_matvec<T>(c, l, D.e, D.y);
-      launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0);
+      launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, nullptr, k);
     }
   } else {
     smooth_point<T>(c, l, true);
   }
   // step 3: local correction (interior edges of the next level's macro-elements)
   if (L.transfer == 2 && lc != HDGMG_LC_NONE)
-    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
+    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e, k);
   // step 4: coarse-grid correction
   Level& Lc = c->levels[l + 1];
   LevelData<T>& Dc = ld<T>(Lc);
@@ -670,16 +706,16 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
     if (L.transfer == 1)
       launch_restrict_p<T>(s, L.n, L.nd, D.r, D.y, Dc.r);
     else
-      launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, D.y, Dc.r);
+      launch_restrict_h<T>(s, Lc.n, D.Rt, D.r, D.y, Dc.r, k);
     vcycle<T>(c, l + 1);
     if (L.transfer == 1)
       launch_prolong_p<T>(s, L.n, L.nd, Dc.e, D.e);
     else
-      launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y);
+      launch_prolong_h<T>(s, Lc.n, D.Pi, Dc.e, D.e, D.y, k);
   }
   // step 5: second local correction (symmetric cycle)
   if (L.transfer == 2 && lc == HDGMG_LC_BOTH)
-    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e);
+    launch_local_correction<T>(s, L.n / 2, ns, D.AIIinv, D.Y, D.r, D.e, k);
   // step 6: post-smoothing (the first step also adds the pending J_N e_c)
   if (!bj) {
     smooth_point<T>(c, l, false);
@@ -687,7 +723,8 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   }
   for (int i = 0; i < L.m; ++i) {
     level_matvec<T>(c, l, D.e, D.y, i == 0 ? xadd : nullptr);
-    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, i == 0 ? xadd : nullptr);
+    launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, i == 0 ? xadd : nullptr,
+                        k);
   }
 }
 
@@ -727,12 +764,14 @@ hdgmg_status alloc_level(hdgmg_ctx* c, Level& L, bool vec_only_fine) {
   const size_t nblk_ent = c->ns ? (size_t)L.nd * L.nd : (size_t)(L.nd * (L.nd + 1) / 2);
   CUDA_TRY(c->alloc(&D.A, (size_t)L.nsym * L.nE));
   CUDA_TRY(c->alloc(&D.Dinv, nblk_ent * L.nEdge));
-  CUDA_TRY(c->alloc(&D.r, (size_t)L.nd * L.nEdge));
-  CUDA_TRY(c->alloc(&D.e, (size_t)L.nd * L.nEdge));
-  CUDA_TRY(c->alloc(&D.y, (size_t)L.nd * L.nEdge));
-  CUDA_TRY(cudaMemset(D.y, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
-  CUDA_TRY(cudaMemset(D.r, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
-  CUDA_TRY(cudaMemset(D.e, 0, sizeof(T) * (size_t)L.nd * L.nEdge));
+  // blocked solves run the FP32 cycle on kb right-hand sides at once
+  const size_t nvec = (size_t)L.nd * L.nEdge * (std::is_same<T, float>::value ? c->kb : 1);
+  CUDA_TRY(c->alloc(&D.r, nvec));
+  CUDA_TRY(c->alloc(&D.e, nvec));
+  CUDA_TRY(c->alloc(&D.y, nvec));
+  CUDA_TRY(cudaMemset(D.y, 0, sizeof(T) * nvec));
+  CUDA_TRY(cudaMemset(D.r, 0, sizeof(T) * nvec));
+  CUDA_TRY(cudaMemset(D.e, 0, sizeof(T) * nvec));
   if (c->opts.smoother != HDGMG_SMOOTH_BLOCK_JACOBI && L.transfer != 0) {
     CUDA_TRY(c->alloc(&D.Dpt, (size_t)L.nd * L.nEdge));
     if (c->opts.smoother == HDGMG_SMOOTH_CHEBYSHEV) {
@@ -1021,6 +1060,159 @@ hdgmg_status refine_solve(hdgmg_ctx* c, double nb, int* iters, int* outer, doubl
   return HDGMG_OK;
 }
 
+// ------------------------------------------- blocked right-hand sides
+// One iteration of k = c->kr simultaneous FP32 PCGs (the inner solver of the
+// blocked refinement): one V-cycle, FP32 matvec and vector pass serve every
+// right-hand side, each with its own scalars (scal32b[8 j ...]); a right-hand
+// side that has reached the inner tolerance is frozen; the loop stops when
+// all have (cg_update_test_block).
+void cg_body_block(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const int k = c->kr;
+  Level& L0 = c->levels[0];
+  float* rs = L0.d32.r;
+  float* zs = L0.d32.e;
+  vcycle<float>(c, 0);
+  launch_dot_fused<float>(s, len, rs, zs, c->partial_b, c->counter_b, c->scal32b, 1, k);
+  launch_cg_direction_zero<float>(s, len, c->scal32b, zs, c->ps, c->Aps, k);
+  launch_matvec<float>(s, c->n, c->p + 1, c->ns, L0.d32.A, c->ps, c->Aps, 1.0f, nullptr, k);
+  launch_dot_fused<float>(s, len, c->ps, c->Aps, c->partial_b, c->counter_b, c->scal32b, 0, k);
+  launch_cg_update_test_block<float>(s, len, k, c->scal32b, c->xs, rs, c->ps, c->Aps, c->partial_b,
+                                     c->counter_b, h, c->it_dev, c->opts.max_it,
+                                     c->opts.inner_rtol * c->opts.inner_rtol);
+}
+
+// FP64 iterative refinement around the blocked FP32 PCG for k right-hand
+// sides (b_j in Bb, solutions accumulated in Xb): r_j = b_j - A x_j in FP64,
+// stop when every ||r_j|| <= rtol ||b_j|| (or breakdown / max_it inner
+// iterations), else solve A d_j = r_j / ||r_j|| in FP32 to inner_rtol for all
+// j at once and x_j += ||r_j|| d_j.  rel[j]: final relative residuals.
+hdgmg_status refine_solve_block(hdgmg_ctx* c, int k, const double* nb, int* iters, int* outer,
+                                double* rel, bool* conv, bool* breakdown) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const hdgmg_opts& o = c->opts;
+  Level& L0 = c->levels[0];
+  if (!c->cgb_exec[k]) {
+    const int saved = c->kr;
+    c->kr = k;
+    const hdgmg_status st = build_loop_graph(c, cg_body_block, &c->cgb_graph[k], &c->cgb_exec[k],
+                                             &c->cgb_body_launches[k]);
+    c->kr = saved;
+    STATUS_TRY(st);
+  }
+  *iters = 0;
+  *outer = 0;
+  *conv = false;
+  *breakdown = false;
+  for (;;) {
+    CUDA_TRY(cudaMemcpyAsync(c->Rb, c->Bb, sizeof(double) * len * k, cudaMemcpyDeviceToDevice, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->Xb, c->Rb, -1.0, nullptr, k);
+    launch_dot_fused<double>(s, len, c->Rb, c->Rb, c->partial_b, c->counter_b, c->scal64b, 2, k);
+    CUDA_TRY(cudaMemcpyAsync(c->scal_hb, c->scal64b, sizeof(double) * 8 * k, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int j = 0; j < k; ++j) {
+      const double rr = c->scal_hb[8 * j + 5];
+      rel[j] = nb[j] > 0.0 ? std::sqrt(rr) / nb[j] : 0.0;
+      if (!std::isfinite(rr)) *breakdown = true;
+      // a solved right-hand side (or a zero one) gets a zero inner right-hand side
+      if (!(rel[j] > o.rtol)) c->scal_hb[8 * j + 5] = 0.0;
+      else all = false;
+    }
+    if (*breakdown) break;
+    if (all) {
+      *conv = true;
+      break;
+    }
+    if (*iters >= o.max_it) break;
+    // inner blocked FP32 PCG on the normalised residuals
+    CUDA_TRY(cudaMemcpyAsync(c->scal64b, c->scal_hb, sizeof(double) * 8 * k, cudaMemcpyHostToDevice, s));
+    launch_scale_to_f32(s, len, c->Rb, c->scal64b + 5, L0.d32.r, k, 8);
+    CUDA_TRY(cudaMemsetAsync(c->xs, 0, sizeof(float) * len * k, s));
+    CUDA_TRY(cudaMemsetAsync(c->ps, 0, sizeof(float) * len * k, s));
+    CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int) * 2, s));
+    // inner scalars in the second half of the staging buffer (the first half
+    // may still be in flight to scal64b)
+    double* q0 = c->scal_hb + 8 * c->kb;
+    for (int j = 0; j < k; ++j) {
+      double* q = q0 + 8 * j;              // rz = 1 (p = 0 makes beta irrelevant), ref norm^2 = 1
+      const bool solved = c->scal_hb[8 * j + 5] == 0.0;
+      for (int t = 0; t < 8; ++t) q[t] = 0.0;
+      q[0] = 1.0;
+      q[6] = 1.0;
+      q[7] = solved ? 1.0 : 0.0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->scal32b, q0, sizeof(double) * 8 * k, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaGraphLaunch(c->cgb_exec[k], s));
+    launch_add_f32(s, len, c->scal64b + 5, c->xs, c->Xb, k, 8);
+    CUDA_TRY(cudaMemcpyAsync(c->it_h, c->it_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *iters += *c->it_h;
+    c->launches_solve += c->cgb_body_launches[k] * (*c->it_h);
+    ++*outer;
+    STATUS_TRY(check_launch("blocked refinement"));
+  }
+  return HDGMG_OK;
+}
+
+// Solve k <= kb right-hand sides together: condensed right-hand sides one by
+// one (into Bb, boundary traces into Lb), the blocked refinement, then
+// lambda_j = boundary + x_j and the local recovery of each.
+hdgmg_status solve_block(hdgmg_ctx* c, int k, const double* f, const double* gD, double* lam,
+                         double* u, double* q, hdgmg_info* info) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  const size_t nvE = (size_t)c->nv * c->n * c->n;
+  double nb[kMaxRhsBlock], rel[kMaxRhsBlock];
+  for (int j = 0; j < k; ++j) {
+    STATUS_TRY(build_rhs(c, f + j * nvE, gD ? gD + j * len : nullptr));
+    CUDA_TRY(cudaMemcpyAsync(c->Bb + j * len, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->Lb + j * len, c->lam, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+  }
+  launch_dot_fused<double>(s, len, c->Bb, c->Bb, c->partial_b, c->counter_b, c->scal64b, 2, k);
+  CUDA_TRY(cudaMemcpyAsync(c->scal_hb, c->scal64b, sizeof(double) * 8 * k, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemsetAsync(c->Xb, 0, sizeof(double) * len * k, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  bool bad_b = false;
+  for (int j = 0; j < k; ++j) {
+    nb[j] = std::sqrt(c->scal_hb[8 * j + 5]);
+    if (!std::isfinite(nb[j])) bad_b = true;
+  }
+  int it = 0, outer = 0;
+  bool conv = true, breakdown = bad_b;
+  if (!bad_b) STATUS_TRY(refine_solve_block(c, k, nb, &it, &outer, rel, &conv, &breakdown));
+  double worst = 0.0;
+  for (int j = 0; j < k; ++j) worst = rel[j] > worst || !(rel[j] == rel[j]) ? rel[j] : worst;
+  for (int j = 0; j < k; ++j) {
+    double* lj = lam + j * len;
+    CUDA_TRY(cudaMemcpyAsync(lj, c->Lb + j * len, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
+    launch_axpby(s, len, 1.0, c->Xb + j * len, 1.0, lj);
+    double* uj = u ? u + j * nvE : nullptr;
+    double* qj = q ? q + 2 * j * nvE : nullptr;
+    if (uj || qj)
+      c->basis ? launch_recover(s, c->refd, c->p, c->n, c->kap, c->ktau, f + j * nvE, lj, uj, qj)
+               : launch_recover_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f + j * nvE,
+                                       lj, uj, qj);
+  }
+  STATUS_TRY(check_launch("blocked solve"));
+  if (c->pc_start >= 0)
+    CUDA_TRY(cudaMemcpyAsync(c->err_h + 2, c->err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  STATUS_TRY(cycle_wait_status(c));
+  c->refinements = outer;
+  if (info) {
+    info->iters = it;
+    info->converged = conv ? 1 : 0;
+    info->rel_res = worst;
+    info->refinements = outer;
+  }
+  if (breakdown) return fail(HDGMG_EBREAKDOWN, "NaN/Inf in the blocked outer iteration");
+  if (!conv) return fail(HDGMG_ENOCONV, "blocked refinement did not reach rtol");
+  return HDGMG_OK;
+}
+
 // One Arnoldi step of right-preconditioned flexible GMRES (all on the
 // device; the index j is read from device memory by every kernel).
 void gm_body(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
@@ -1304,6 +1496,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->pcycle = 1;
   o->pcycle_tail_n = 16;
   o->pcg_graph = 1;
+  o->rhs_block = 0;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1323,6 +1516,11 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   if (c->gm_exec) cudaGraphExecDestroy(c->gm_exec);
   if (c->gm_graph) cudaGraphDestroy(c->gm_graph);
   if (c->gmh_host) cudaFreeHost(c->gmh_host);
+  if (c->scal_hb) cudaFreeHost(c->scal_hb);
+  for (int k = 0; k <= kMaxRhsBlock; ++k) {
+    if (c->cgb_exec[k]) cudaGraphExecDestroy(c->cgb_exec[k]);
+    if (c->cgb_graph[k]) cudaGraphDestroy(c->cgb_graph[k]);
+  }
   if (c->cg32_graph) cudaGraphDestroy(c->cg32_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1369,6 +1567,8 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.condensation < HDGMG_CONDENSE_AUTO || o.condensation > HDGMG_CONDENSE_FACTOR)
     return fail(HDGMG_EINVAL, "unknown condensation");
   if (o.l2_persist_mb < 0) return fail(HDGMG_EINVAL, "l2_persist_mb must be >= 0");
+  if (o.rhs_block < 0 || o.rhs_block > kMaxRhsBlock)
+    return fail(HDGMG_EINVAL, "rhs_block must be in 0..16");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)
@@ -1376,6 +1576,12 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
                 "krylov CG needs a symmetric operator; use GMRES for convection-diffusion, NIPG-H, IIPG-H");
   if (!(o.omega > 0.0) || !(o.rtol > 0.0) || o.max_it < 1) return fail(HDGMG_EINVAL, "bad omega/rtol/max_it");
   if (!(o.inner_rtol > 0.0) || !(o.inner_rtol < 1.0)) return fail(HDGMG_EINVAL, "inner_rtol must be in (0,1)");
+  if (o.rhs_block > 1 &&
+      (nonsym || o.krylov != HDGMG_KRYLOV_CG || o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI ||
+       (o.precision != HDGMG_PREC_FP32 && o.precision != HDGMG_PREC_FP32_IR)))
+    return fail(HDGMG_EINVAL,
+                "rhs_block > 1 needs a symmetric operator, krylov CG, block-Jacobi and the FP32 "
+                "cycle (precision FP32 or FP32_IR)");
   int nn = P.n;
   while (nn > o.coarsest_n) {
     if (nn % 2) return fail(HDGMG_EINVAL, "n must halve evenly down to coarsest_n");
@@ -1387,6 +1593,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   hdgmg_ctx* c = new hdgmg_ctx();
   c->prob = P;
   c->opts = o;
+  c->kb = o.rhs_block > 1 ? o.rhs_block : 1;
   c->ns = nonsym;
   c->basis = !nonsym && o.condensation != HDGMG_CONDENSE_FACTOR;
   c->stream = (cudaStream_t)stream;
@@ -1529,9 +1736,22 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   CTRY(c->alloc(&c->scal, 8));
   CTRY(c->alloc(&c->scal32, 8));
   if (fp32) {
-    CTRY(c->alloc(&c->xs, len));
-    CTRY(c->alloc(&c->ps, len));
-    CTRY(c->alloc(&c->Aps, len));
+    CTRY(c->alloc(&c->xs, len * c->kb));
+    CTRY(c->alloc(&c->ps, len * c->kb));
+    CTRY(c->alloc(&c->Aps, len * c->kb));
+  }
+  if (c->kb > 1) {
+    const size_t kb = (size_t)c->kb;
+    CTRY(c->alloc(&c->Xb, len * kb));
+    CTRY(c->alloc(&c->Rb, len * kb));
+    CTRY(c->alloc(&c->Bb, len * kb));
+    CTRY(c->alloc(&c->Lb, len * kb));
+    CTRY(c->alloc(&c->scal64b, 8 * kb));
+    CTRY(c->alloc(&c->scal32b, 8 * kb));
+    CTRY(c->alloc(&c->partial_b, (size_t)kDotBlocks * kb));
+    CTRY(c->alloc(&c->counter_b, kb + 1));
+    CTRY(cudaMemset(c->counter_b, 0, sizeof(unsigned) * (kb + 1)));
+    CTRY(cudaMallocHost(&c->scal_hb, sizeof(double) * 16 * kb));   // two halves: 64b, 32b
   }
   CTRY(cudaMallocHost(&c->scal_h, sizeof(double) * 8));
   CTRY(cudaMallocHost(&c->init_h, sizeof(double) * 8));
@@ -1580,9 +1800,9 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   }
   if (c->ctail_start >= 0 && c->tail_start >= 0 && c->tail_start < c->ctail_start)
     c->ctail_start = -1;                     // keep whichever fuses more levels
-  if (o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) {
-    c->tail_start = -1;                      // the fused tails implement block-Jacobi only
-    c->ctail_start = -1;
+  if (o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI || c->kb > 1) {
+    c->tail_start = -1;                      // the fused tails implement block-Jacobi only, and
+    c->ctail_start = -1;                     // one right-hand side at a time
   }
   CTRY(c->alloc(&c->pc_bar, 1));
   CTRY(cudaMemset(c->pc_bar, 0, sizeof(unsigned long long)));
@@ -1782,12 +2002,26 @@ hdgmg_status hdgmg_solve(hdgmg_ctx* c, int32_t nrhs, const double* f, const doub
   const long long l0 = launch_count(), cap0 = c->capture_launches;
   c->launches_solve = 0;
   CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-  for (int k = 0; k < nrhs; ++k) {
-    hdgmg_status st = solve_one(c, f + (size_t)k * c->nv * nE, g_D ? g_D + (size_t)k * len : nullptr,
-                                lambda + (size_t)k * len, u ? u + (size_t)k * c->nv * nE : nullptr,
-                                q ? q + (size_t)k * 2 * c->nv * nE : nullptr, info);
-    if (st == HDGMG_ECUDA || st == HDGMG_EINVAL || st == HDGMG_ENOMEM) return st;
-    if (st != HDGMG_OK) last = st;
+  if (c->kb > 1 && nrhs > 1) {
+    // blocks of up to kb right-hand sides solved together
+    for (int k0 = 0; k0 < nrhs; k0 += c->kb) {
+      const int k = nrhs - k0 < c->kb ? nrhs - k0 : c->kb;
+      hdgmg_status st = solve_block(c, k, f + (size_t)k0 * c->nv * nE,
+                                    g_D ? g_D + (size_t)k0 * len : nullptr, lambda + (size_t)k0 * len,
+                                    u ? u + (size_t)k0 * c->nv * nE : nullptr,
+                                    q ? q + (size_t)k0 * 2 * c->nv * nE : nullptr, info);
+      if (st == HDGMG_ECUDA || st == HDGMG_EINVAL || st == HDGMG_ENOMEM || st == HDGMG_ETIMEOUT)
+        return st;
+      if (st != HDGMG_OK) last = st;
+    }
+  } else {
+    for (int k = 0; k < nrhs; ++k) {
+      hdgmg_status st = solve_one(c, f + (size_t)k * c->nv * nE, g_D ? g_D + (size_t)k * len : nullptr,
+                                  lambda + (size_t)k * len, u ? u + (size_t)k * c->nv * nE : nullptr,
+                                  q ? q + (size_t)k * 2 * c->nv * nE : nullptr, info);
+      if (st == HDGMG_ECUDA || st == HDGMG_EINVAL || st == HDGMG_ENOMEM) return st;
+      if (st != HDGMG_OK) last = st;
+    }
   }
   CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));

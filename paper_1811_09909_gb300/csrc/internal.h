@@ -223,35 +223,39 @@ void launch_misfit(cudaStream_t s, const RefDevice& ref, int nv, int nE, const d
 // xadd (nullable): the P1 correction of the next level, added to modes 0
 // and 1 of x (matvec) or of e (block-Jacobi update) on the fly -- the
 // p-prolongation J_N fused into the first post-smoothing step.
+// k: right-hand sides of a blocked solve, vectors [k][...] contiguous per
+// right-hand side (every V-cycle launcher below takes it, default 1)
 template <typename T>
 void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha,
-                   const T* xadd = nullptr);
+                   const T* xadd = nullptr, int k = 1);
 // per-ND instantiations (k_edge_inst.cu, one translation unit per type and ND)
 template <typename T, int ND, bool NS>
-void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha, const T* xadd);
+void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha, const T* xadd,
+                      int k);
 template <typename T, int ND, bool NS>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err);
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
-                         int first, const T* xadd);
+                         int first, const T* xadd, int k);
 // y += alpha A x with A stored in BF16, x, y and the accumulation in FP32
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
-                        const float* x, float* y, float alpha, const float* xadd = nullptr);
+                        const float* x, float* y, float alpha, const float* xadd = nullptr,
+                        int k = 1);
 template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
-                           float alpha, const float* xadd);
+                           float alpha, const float* xadd, int k);
 void launch_to_bf16(cudaStream_t s, int64_t len, const double* in, __nv_bfloat16* out);
 template <typename T>
 void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Dinv, int* err);
 template <typename T>
 void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
-                      T* e, T omega, int first, const T* xadd = nullptr);
+                      T* e, T omega, int first, const T* xadd = nullptr, int k = 1);
 // p-restriction fused into the first sweep of the P1 level below the
 // p-level: r1 = (r0 - y0) on modes 0, 1 (written), y0 := 0 on all nd0
 // modes, e1 = omega D1^-1 r1
 template <typename T>
 void launch_bj_first_restrict_p(cudaStream_t s, int n, int nd0, bool ns, const T* Dinv1,
-                                const T* r0, T* y0, T* r1, T* e1, T omega);
+                                const T* r0, T* y0, T* r1, T* e1, T omega, int k = 1);
 template <typename T>
 void launch_pcoarsen(cudaStream_t s, int nE, int ndf, bool ns, const T* Af, T* Ac);
 // ns: also writes Rt = Z^T J with Z = -A_BI A_II^-1 (the restriction block);
@@ -261,16 +265,16 @@ void launch_agglomerate(cudaStream_t s, int nc, bool ns, const T* Af, T* Ac, T* 
                         T* Pi, T* Rt, int* err);
 template <typename T>
 void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
-                             const T* r, T* e);
+                             const T* r, T* e, int k = 1);
 template <typename T>
-void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc);
+void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc, int k = 1);
 // P1 level, one thread per edge gathering both elements' rows (no atomics):
 // sweep: out = x + omega D^-1 (r - A x); else out = A x.  x != out.
 template <typename T>
 void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, const T* r, const T* x,
-                    T* out, T omega, bool sweep);
+                    T* out, T omega, bool sweep, int k = 1);
 template <typename T>
-void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y);
+void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y, int k = 1);
 template <typename T>
 void launch_restrict_p(cudaStream_t s, int n, int nd, const T* r, T* y, T* rc);
 template <typename T>
@@ -376,6 +380,8 @@ struct P1Geom {
   int n = 0, nE = 0, nvert = 0, nedge = 0;
   int nc = 0, nC = 0, nvc = 0, nedc = 0;
   FastDiv dn, dn1, dnc, dnc1, dnC;
+  // item counts of the cycle's steps (blocked solves: item j = rhs * count + t)
+  FastDiv dne, dlc, dc1, dc2, dpro;   // nedge, 8 nC, nedc, 2 nedc, 8 nC + 2 nedc
 };
 inline P1Geom make_p1geom(int n) {
   P1Geom g;
@@ -393,7 +399,12 @@ inline P1Geom make_p1geom(int n) {
     g.dnc = make_fastdiv(g.nc);
     g.dnc1 = make_fastdiv(g.nc + 1);
     g.dnC = make_fastdiv(g.nC);
+    g.dlc = make_fastdiv(8 * g.nC);
+    g.dc1 = make_fastdiv(g.nedc);
+    g.dc2 = make_fastdiv(2 * g.nedc);
+    g.dpro = make_fastdiv(8 * g.nC + 2 * g.nedc);
   }
+  g.dne = make_fastdiv(g.nedge);
   return g;
 }
 template <typename T>
@@ -427,6 +438,8 @@ struct PCycleParams {
   const int* fidx = nullptr;
   const int* fedge = nullptr;
   int nf = 0;
+  FastDiv dco;                  // n_edges(coarsest) + nf: items of the coarse step
+  int nrhs = 1;                 // right-hand sides of a blocked solve (vectors [k][...])
   T omega = T(1);
   int lc = 0;
   int ns = 0;
@@ -464,7 +477,7 @@ bool launch_coarse_setup_smem(cudaStream_t s, int n, bool ns, const T* A, const 
                               int nf, double* Ainv, int* err);
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
-                         const double* Ainv, const T* r, T* e);
+                         const double* Ainv, const T* r, T* e, int k = 1);
 
 // vector kernels (FP64 unless templated)
 template <typename T>
@@ -483,12 +496,19 @@ template <typename T>
 void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p);
 // fused PCG kernels (scal layout: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 beta,
 // 5 rr, 6 reference norm^2); counter: a zeroed unsigned reset by the kernel
+// k > 1: blocked over k right-hand sides (vectors [k][len], scalars
+// scal[8 j ...], partials [k][blocks], counters [k])
 template <typename T>
 void launch_dot_fused(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
-                      unsigned* counter, double* scal, int mode);
+                      unsigned* counter, double* scal, int mode, int k = 1);
 template <typename T>
 void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p,
-                              T* Ap);
+                              T* Ap, int k = 1);
+// blocked PCG update and loop test (see k_mg.cu): counters [k + 1]
+template <typename T>
+void launch_cg_update_test_block(cudaStream_t s, int64_t len, int k, double* scal, T* x, T* r,
+                                 const T* p, const T* Ap, double* partial, unsigned* counter,
+                                 cudaGraphConditionalHandle h, int* it, int max_it, double tol2);
 // r32 (nullable): also receives the updated r rounded to FP32
 template <typename T>
 void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r, const T* p,
@@ -501,9 +521,11 @@ void launch_dot_fused_mixed(cudaStream_t s, int64_t len, const double* a, const 
 void launch_cg_direction_zero_mixed(cudaStream_t s, int64_t len, const double* scal, const float* z,
                                     double* p, double* Ap);
 // FP64 -> FP32 with 1/sqrt(*scale), and y += sqrt(*scale) x (FP32 -> FP64)
+// k right-hand sides, the scale of j at scale[j * sstride]
 void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
-                         float* out);
-void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y);
+                         float* out, int k = 1, int sstride = 0);
+void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y,
+                    int k = 1, int sstride = 0);
 void launch_cg_scalars(cudaStream_t s, double* scal, int stage);
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y);
 void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, double* lam);

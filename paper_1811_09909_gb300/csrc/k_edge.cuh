@@ -27,6 +27,8 @@ static __device__ __forceinline__ float load_entry(const __nv_bfloat16* p) {
 // ---------------------------------------------------------------- K6 matvec
 // xadd (nullable, modes 0 and 1 only): x + J xadd is applied instead of x,
 // i.e. the P1 correction of the next level is prolonged on the fly
+// blockIdx.y: right-hand side of a blocked solve (x, y with stride ND
+// n_edges, xadd with the P1 stride 2 n_edges)
 template <typename T, int ND, bool NS, typename TA = T>
 __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y,
@@ -36,6 +38,11 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   const int nedge = 2 * n * (n + 1);
+  if (blockIdx.y) {
+    x += (size_t)blockIdx.y * ND * nedge;
+    y += (size_t)blockIdx.y * ND * nedge;
+    if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
+  }
   int ed[4];
   elem_edges(n, e, ed);
   T xl[NL];
@@ -219,6 +226,13 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
   const int nedge = 2 * n * (n + 1);
   const int edge = blockIdx.x * blockDim.x + threadIdx.x;
   if (edge >= nedge || bnd_edge(n, edge)) return;
+  if (blockIdx.y) {                         // right-hand side of a blocked solve
+    const size_t o = (size_t)blockIdx.y * ND * nedge;
+    r += o;
+    y += o;
+    e += o;
+    if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
+  }
   T d[ND], eo[ND], Dv[NS ? ND * ND : ND * (ND + 1) / 2];
 #pragma unroll
   for (int t = 0; t < (NS ? ND * ND : ND * (ND + 1) / 2); ++t) Dv[t] = Dinv[(size_t)t * nedge + edge];
@@ -255,17 +269,17 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
 
 template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha,
-                      const T* xadd) {
+                      const T* xadd, int k) {
   note_launch();
-  matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha, xadd);
+  matvec_kernel<T, ND, NS><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(n, A, x, y, alpha, xadd);
 }
 
 template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
-                           float alpha, const float* xadd) {
+                           float alpha, const float* xadd, int k) {
   note_launch();
-  matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha,
-                                                                              xadd);
+  matvec_kernel<float, ND, NS, __nv_bfloat16><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(
+      n, A, x, y, alpha, xadd);
 }
 
 template <typename T, int ND, bool NS>
@@ -276,10 +290,10 @@ void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err) {
 
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
-                         int first, const T* xadd) {
+                         int first, const T* xadd, int k) {
   note_launch();
-  bj_update_kernel<T, ND, NS><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega,
-                                                                         first, xadd);
+  bj_update_kernel<T, ND, NS><<<dim3(nblk(2 * n * (n + 1), 128), k), 128, 0, s>>>(
+      n, Dinv, r, y, e, omega, first, xadd);
 }
 
 }  // namespace hdgmg

@@ -16,20 +16,20 @@ namespace hdgmg {
 #define HDGMG_INST(NS)                                                                          \
   template void launch_matvec_nd<HDGMG_REAL, HDGMG_ND, NS>(cudaStream_t, int, const HDGMG_REAL*, \
                                                            const HDGMG_REAL*, HDGMG_REAL*,      \
-                                                           HDGMG_REAL, const HDGMG_REAL*);      \
+                                                           HDGMG_REAL, const HDGMG_REAL*, int); \
   template void launch_bj_blocks_nd<HDGMG_REAL, HDGMG_ND, NS>(cudaStream_t, int,                \
                                                               const HDGMG_REAL*, HDGMG_REAL*,  \
                                                               int*);                           \
   template void launch_bj_update_nd<HDGMG_REAL, HDGMG_ND, NS>(                                  \
       cudaStream_t, int, const HDGMG_REAL*, const HDGMG_REAL*, HDGMG_REAL*, HDGMG_REAL*,        \
-      HDGMG_REAL, int, const HDGMG_REAL*);
+      HDGMG_REAL, int, const HDGMG_REAL*, int);
 HDGMG_INST(false)
 HDGMG_INST(true)
 #undef HDGMG_INST
 #else
 template void launch_matvec_bf16_nd<HDGMG_ND, false>(cudaStream_t, int, const __nv_bfloat16*,
-                                                     const float*, float*, float, const float*);
+                                                     const float*, float*, float, const float*, int);
 template void launch_matvec_bf16_nd<HDGMG_ND, true>(cudaStream_t, int, const __nv_bfloat16*,
-                                                    const float*, float*, float, const float*);
+                                                    const float*, float*, float, const float*, int);
 #endif
 }  // namespace hdgmg

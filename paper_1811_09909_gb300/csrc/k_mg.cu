@@ -391,7 +391,8 @@ __global__ void local_correction_kernel(const P1Geom g, const T* __restrict__ AI
                                         const T* __restrict__ Y, const T* __restrict__ r,
                                         T* __restrict__ e) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 8 * g.nC) p1_lc<T, NS>(g, AIIinv, Y, r, e, t);
+  const size_t o = (size_t)blockIdx.y * 2 * g.nedge;        // right-hand side of a blocked solve
+  if (t < 8 * g.nC) p1_lc<T, NS>(g, AIIinv, Y, r + o, e + o, t);
 }
 
 
@@ -453,7 +454,8 @@ template <typename T>
 __global__ void restrict_h_kernel(const P1Geom g, const T* __restrict__ Pi, const T* __restrict__ r,
                                   const T* __restrict__ y, T* __restrict__ rc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 2 * g.nedc) p1_restrict<T>(g, Pi, r, y, rc, t);
+  const size_t o = (size_t)blockIdx.y * 2 * g.nedge, oc = (size_t)blockIdx.y * 2 * g.nedc;
+  if (t < 2 * g.nedc) p1_restrict<T>(g, Pi, r + o, y + o, rc + oc, t);
 }
 
 // -------------------------------------------------------- K11 prolongation
@@ -506,7 +508,8 @@ template <typename T>
 __global__ void prolong_h_kernel(const P1Geom g, const T* __restrict__ Pi, const T* __restrict__ ec,
                                  T* __restrict__ e, T* __restrict__ y) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 8 * g.nC + 2 * g.nedc) p1_prolong<T>(g, Pi, ec, e, y, t);
+  const size_t o = (size_t)blockIdx.y * 2 * g.nedge, oc = (size_t)blockIdx.y * 2 * g.nedc;
+  if (t < 8 * g.nC + 2 * g.nedc) p1_prolong<T>(g, Pi, ec + oc, e + o, y + o, t);
 }
 
 // ------------------------------------------------- p-transfer (J_N, J_N^T)
@@ -518,7 +521,9 @@ __global__ void bj_first_restrict_p_kernel(const P1Geom g, int nd0, const T* __r
                                            const T* __restrict__ r0, T* __restrict__ y0,
                                            T* __restrict__ r1, T* __restrict__ e1, T omega) {
   const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E < g.nedge) p1_first_restrict_p<T, NS>(g, nd0, Dinv1, r0, y0, r1, e1, omega, E);
+  const size_t o0 = (size_t)blockIdx.y * nd0 * g.nedge, o1 = (size_t)blockIdx.y * 2 * g.nedge;
+  if (E < g.nedge)
+    p1_first_restrict_p<T, NS>(g, nd0, Dinv1, r0 + o0, y0 + o0, r1 + o1, e1 + o1, omega, E);
 }
 
 template <typename T>
@@ -727,7 +732,8 @@ __global__ void coarse_solve_kernel(int n, const int* __restrict__ fidx, const i
                                     int nf, const double* __restrict__ Ainv, const T* __restrict__ r,
                                     T* __restrict__ e) {
   extern __shared__ double cw[];
-  coarse_apply_block<T>(n, fidx, fedge, nf, Ainv, r, e, cw);
+  const size_t o = (size_t)blockIdx.y * 4 * n * (n + 1);   // right-hand side of a blocked solve
+  coarse_apply_block<T>(n, fidx, fedge, nf, Ainv, r + o, e + o, cw);
 }
 
 // ------------------------------------------- fused V-cycle on the P1 tail
@@ -808,7 +814,8 @@ __global__ void edge_p1_kernel(const P1Geom g, const T* __restrict__ A, const T*
                                const T* __restrict__ r, const T* __restrict__ x,
                                T* __restrict__ out, T omega) {
   const int E = blockIdx.x * blockDim.x + threadIdx.x;
-  if (E < g.nedge) p1_edge<T, NS, SWEEP>(g, A, Dinv, r, x, out, omega, E);
+  const size_t o = (size_t)blockIdx.y * 2 * g.nedge;        // right-hand side of a blocked solve
+  if (E < g.nedge) p1_edge<T, NS, SWEEP>(g, A, Dinv, r + o, x + o, out + o, omega, E);
 }
 
 template <typename T>
@@ -1052,32 +1059,42 @@ __device__ __forceinline__ void pc_bufs(const PCycleParams<T>& P, int l, T* bufs
   }
 }
 
+// Grid-stride loop over the k x COUNT items of one step (k = P.nrhs right-hand
+// sides of a blocked solve): j = rhs * COUNT + t; the body sees rhs and t.
+#define PC_FOR(COUNT, FD)                                                         \
+  for (int j_ = i0, cnt_ = (COUNT); j_ < P.nrhs * cnt_; j_ += di)                 \
+    if (const int rhs = P.nrhs == 1 ? 0 : fdiv(j_, (FD)), t = j_ - rhs * cnt_; true)
+
 // Steps 2-4 on P1 level l down to the restriction into level l + 1.  The
 // first sweep from e = 0 of a level other than lv[0] and the first level of
 // a staged block-0 tail is fused into the restriction above it; after a
 // local correction the residual and the restriction are one step
-// (p1_resid_restrict).
+// (p1_resid_restrict2).  Vectors of right-hand side rhs are offset by
+// rhs * 2 n_edges (coarse level: rhs * 2 n_edges(coarse)).
 template <typename T, bool NS>
 __device__ bool pc_down(const PCycleParams<T>& P, int l, int i0, int di, bool grid, PcSync& st,
                         volatile int* s_ok) {
   const PLevel<T>& L = P.lv[l];
   const P1Geom& g = L.g;
-  const int ned = g.nedge;
+  const int ned = g.nedge, V = 2 * g.nedge, Vc = 2 * g.nedc;
   T* bufs[2];
   pc_bufs<T>(P, l, bufs);
   int cur = 1;
   if (l == 0 || (P.staged && l == P.tail)) {
     if (l == 0 && P.rp_r0) {
-      for (int i = i0; i < ned; i += di)
-        p1_first_restrict_p<T, NS>(g, P.rp_nd0, L.Dinv, P.rp_r0, P.rp_y0, L.r, bufs[1], P.omega, i);
+      const int V0 = P.rp_nd0 * ned;
+      PC_FOR(ned, g.dne)
+      p1_first_restrict_p<T, NS>(g, P.rp_nd0, L.Dinv, P.rp_r0 + rhs * V0, P.rp_y0 + rhs * V0,
+                                 L.r + rhs * V, bufs[1] + rhs * V, P.omega, t);
     } else {
-      for (int i = i0; i < ned; i += di) p1_first<T, NS>(g, L.Dinv, L.r, bufs[1], P.omega, i);
+      PC_FOR(ned, g.dne) p1_first<T, NS>(g, L.Dinv, L.r + rhs * V, bufs[1] + rhs * V, P.omega, t);
     }
     if (!pc_sync<T>(P, grid, st, s_ok)) return false;
   }
   for (int it = 1; it < L.m; ++it) {
-    for (int i = i0; i < ned; i += di)
-      p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+    PC_FOR(ned, g.dne)
+    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
+                         bufs[1 - cur] + rhs * V, P.omega, t);
     cur ^= 1;
     if (!pc_sync<T>(P, grid, st, s_ok)) return false;
   }
@@ -1090,42 +1107,50 @@ __device__ bool pc_down(const PCycleParams<T>& P, int l, int i0, int di, bool gr
   T* ec = fuse_next ? cb[1] : nullptr;
   const T* Dc = P.lv[l + 1].Dinv;
   if (P.lc != HDGMG_LC_NONE) {
-    for (int i = i0; i < 8 * g.nC; i += di) p1_lc<T, NS>(g, L.AIIinv, L.Y, L.r, bufs[cur], i);
+    PC_FOR(8 * g.nC, g.dlc)
+    p1_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, bufs[cur] + rhs * V, t);
     if (!pc_sync<T>(P, grid, st, s_ok)) return false;
-    for (int i = i0; i < 2 * g.nedc; i += di)
-      p1_resid_restrict2<T, NS>(g, L.A, L.r, bufs[cur], rc, Dc, ec, P.omega, i);
+    PC_FOR(2 * g.nedc, g.dc2)
+    p1_resid_restrict2<T, NS>(g, L.A, L.r + rhs * V, bufs[cur] + rhs * V, rc + rhs * Vc, Dc,
+                              ec ? ec + rhs * Vc : nullptr, P.omega, t);
     return pc_sync<T>(P, grid, st, s_ok);
   }
-  for (int i = i0; i < ned; i += di)
-    p1_edge<T, NS, false>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+  PC_FOR(ned, g.dne)
+  p1_edge<T, NS, false>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
+                        bufs[1 - cur] + rhs * V, P.omega, t);
   if (!pc_sync<T>(P, grid, st, s_ok)) return false;
-  for (int i = i0; i < g.nedc; i += di)
-    p1_restrict_first<T, NS>(g, L.Rt, L.r, bufs[1 - cur], rc, Dc, ec, P.omega, i);
+  PC_FOR(g.nedc, g.dc1)
+  p1_restrict_first<T, NS>(g, L.Rt, L.r + rhs * V, bufs[1 - cur] + rhs * V, rc + rhs * Vc, Dc,
+                           ec ? ec + rhs * Vc : nullptr, P.omega, t);
   return pc_sync<T>(P, grid, st, s_ok);
 }
 
 // B_1 = A_1^-1 on the coarsest level: every participating block gathers the
-// interior right-hand side into w (shared memory), then one item per row.
+// interior right-hand sides into w (shared memory, [k][nf]), then one item per
+// (right-hand side, row).
 template <typename T>
 __device__ bool pc_coarse(const PCycleParams<T>& P, int i0, int di, bool grid, PcSync& st,
                           volatile int* s_ok, double* w) {
   const PLevel<T>& L = P.lv[P.nlev - 1];
-  const int ned = L.g.nedge, nf = P.nf;
-  for (int j = threadIdx.x; j < nf; j += blockDim.x)
-    w[j] = (double)L.r[(j & 1) * ned + P.fedge[j >> 1]];
+  const int ned = L.g.nedge, nf = P.nf, V = 2 * ned;
+  for (int q = threadIdx.x; q < P.nrhs * nf; q += blockDim.x) {
+    const int rq = q / nf, jq = q - rq * nf;
+    w[q] = (double)L.r[rq * V + (jq & 1) * ned + P.fedge[jq >> 1]];
+  }
   __syncthreads();
-  for (int i = i0; i < ned + nf; i += di) {
-    if (i < ned) {
-      if (P.fidx[i] < 0) {
-        L.e[i] = T(0);
-        L.e[ned + i] = T(0);
+  PC_FOR(ned + nf, P.dco) {
+    if (t < ned) {
+      if (P.fidx[t] < 0) {
+        L.e[rhs * V + t] = T(0);
+        L.e[rhs * V + ned + t] = T(0);
       }
     } else {
-      const int row = i - ned;
+      const int row = t - ned;
       const double* Ar = P.Ainv + (size_t)row * nf;
+      const double* wr = w + rhs * nf;
       double s = 0.0;
-      for (int j = 0; j < nf; ++j) s += Ar[j] * w[j];
-      L.e[(row & 1) * ned + P.fedge[row >> 1]] = (T)s;
+      for (int j = 0; j < nf; ++j) s += Ar[j] * wr[j];
+      L.e[rhs * V + (row & 1) * ned + P.fedge[row >> 1]] = (T)s;
     }
   }
   return pc_sync<T>(P, grid, st, s_ok);
@@ -1139,23 +1164,25 @@ __device__ bool pc_up(const PCycleParams<T>& P, int l, int i0, int di, bool grid
                       volatile int* s_ok, bool final) {
   const PLevel<T>& L = P.lv[l];
   const P1Geom& g = L.g;
-  const int ned = g.nedge;
+  const int ned = g.nedge, V = 2 * g.nedge, Vc = 2 * g.nedc;
   T* bufs[2];
   pc_bufs<T>(P, l, bufs);
   int cur = L.m & 1;                   // where the down sweep left the correction
   const T* ec = P.lv[l + 1].e;
-  const int items = 8 * g.nC + 2 * g.nedc;
   if (P.lc == HDGMG_LC_BOTH) {
-    for (int i = i0; i < items; i += di)
-      p1_prolong_lc<T, NS>(g, L.AIIinv, L.Y, L.r, ec, bufs[cur], bufs[1 - cur], i);
+    PC_FOR(8 * g.nC + 2 * g.nedc, g.dpro)
+    p1_prolong_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, ec + rhs * Vc, bufs[cur] + rhs * V,
+                         bufs[1 - cur] + rhs * V, t);
     cur ^= 1;
   } else {
-    for (int i = i0; i < items; i += di) p1_prolong<T>(g, L.Pi, ec, bufs[cur], bufs[1 - cur], i);
+    PC_FOR(8 * g.nC + 2 * g.nedc, g.dpro)
+    p1_prolong<T>(g, L.Pi, ec + rhs * Vc, bufs[cur] + rhs * V, bufs[1 - cur] + rhs * V, t);
   }
   if (!pc_sync<T>(P, grid, st, s_ok)) return false;
   for (int it = 0; it < L.m; ++it) {
-    for (int i = i0; i < ned; i += di)
-      p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r, bufs[cur], bufs[1 - cur], P.omega, i);
+    PC_FOR(ned, g.dne)
+    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
+                         bufs[1 - cur] + rhs * V, P.omega, t);
     cur ^= 1;
     if (final && it + 1 == L.m) return true;
     if (!pc_sync<T>(P, grid, st, s_ok)) return false;
@@ -1572,6 +1599,13 @@ __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __
                                                         unsigned* __restrict__ counter,
                                                         double* __restrict__ scal, int mode) {
   __shared__ double sh[33];
+  if (blockIdx.y) {          // right-hand side of a blocked solve: its vectors, partials, scalars
+    a += (size_t)blockIdx.y * len;
+    b += (size_t)blockIdx.y * len;
+    partial += (size_t)blockIdx.y * gridDim.x;
+    counter += blockIdx.y;
+    scal += 8 * blockIdx.y;
+  }
   double s = 0.0;
   const int64_t G = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1606,16 +1640,81 @@ __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __
   }
 }
 
-// p = z + beta p and Ap = 0
+// p = z + beta p and Ap = 0; blockIdx.y: right-hand side of a blocked solve,
+// whose p is held at zero once it has converged (scal[7] != 0)
 template <typename T, typename TZ = T>
 __global__ void cg_direction_zero_kernel(int64_t len, const double* __restrict__ scal,
                                          const TZ* __restrict__ z, T* __restrict__ p,
                                          T* __restrict__ Ap) {
+  if (blockIdx.y) {
+    const size_t o = (size_t)blockIdx.y * len;
+    z += o;
+    p += o;
+    Ap += o;
+    scal += 8 * blockIdx.y;
+  }
+  const bool done = gridDim.y > 1 && scal[7] != 0.0;
   const T beta = (T)scal[4];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x) {
-    p[i] = (T)z[i] + beta * p[i];
+    p[i] = done ? T(0) : (T)z[i] + beta * p[i];
     Ap[i] = T(0);
+  }
+}
+
+// Blocked form of cg_update_test_kernel, blockIdx.y = right-hand side j with
+// scalars scal[8 j ...] (7: converged), partials partial[j][gridDim.x] and
+// counters counter[j]: x += alpha p and r -= alpha A p unless j has converged,
+// r.r; the last block of j tests r.r <= tol2 scal[6] (or NaN) and marks j
+// converged; the last of those (counter[k]) counts the iteration and stops
+// the loop once every right-hand side has converged or after max_it.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_test_block_kernel(
+    int64_t len, double* __restrict__ scal, T* __restrict__ x, T* __restrict__ r,
+    const T* __restrict__ p, const T* __restrict__ Ap, double* __restrict__ partial,
+    unsigned* __restrict__ counter, cudaGraphConditionalHandle h, int* __restrict__ it,
+    int max_it, double tol2) {
+  __shared__ double sh[33];
+  __shared__ bool last_all;
+  const int j = blockIdx.y, k = gridDim.y;
+  const size_t o = (size_t)j * len;
+  double* sc = scal + 8 * j;
+  const bool done = sc[7] != 0.0;
+  const T alpha = done ? T(0) : (T)sc[2];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T ri = r[o + i];
+    if (!done) {
+      x[o + i] += alpha * p[o + i];
+      ri -= alpha * Ap[o + i];
+      r[o + i] = ri;
+    }
+    s += (double)ri * (double)ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[(size_t)j * gridDim.x + blockIdx.x] = s;
+  if (!last_block(counter + j)) return;
+  const double rr = sum_partials(partial + (size_t)j * gridDim.x, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    sc[5] = rr;
+    counter[j] = 0u;
+    if (!(rr > tol2 * sc[6])) sc[7] = 1.0;
+    __threadfence();
+    last_all = atomicAdd(counter + k, 1u) == (unsigned)(k - 1);
+    if (last_all) {
+      __threadfence();
+      bool all = true;
+      for (int q = 0; q < k; ++q) all = all && ((volatile double*)scal)[8 * q + 7] != 0.0;
+      counter[k] = 0u;
+      const int kk = ++(*it);
+      if (all || kk >= max_it) {
+        if (h)
+          cudaGraphSetConditional(h, 0);
+        else
+          it[1] = 1;
+      }
+    }
   }
 }
 
@@ -1697,20 +1796,27 @@ __global__ void cg_direction_kernel(int64_t len, const double* __restrict__ scal
 
 // out = scale * in (FP64 -> FP32), and y += alpha * x (FP32 -> FP64): the
 // hand-over between the FP64 outer and the FP32 inner iteration
+// blockIdx.y: right-hand side j of a blocked solve, its scale at
+// scale[j * sstride]; a zero scale (a right-hand side already solved)
+// gives a zero vector
 __global__ void scale_to_f32_kernel(int64_t len, const double* __restrict__ in,
-                                    const double* __restrict__ scale, float* __restrict__ out) {
-  const double sc = 1.0 / sqrt(*scale);
+                                    const double* __restrict__ scale, float* __restrict__ out,
+                                    int sstride) {
+  const size_t o = (size_t)blockIdx.y * len;
+  const double v = scale[(size_t)blockIdx.y * sstride];
+  const double sc = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)(in[i] * sc);
+    out[o + i] = (float)(in[o + i] * sc);
 }
 
 __global__ void add_f32_kernel(int64_t len, const double* __restrict__ scale,
-                               const float* __restrict__ x, double* __restrict__ y) {
-  const double sc = sqrt(*scale);
+                               const float* __restrict__ x, double* __restrict__ y, int sstride) {
+  const size_t o = (size_t)blockIdx.y * len;
+  const double sc = sqrt(scale[(size_t)blockIdx.y * sstride]);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += sc * (double)x[i];
+    y[o + i] += sc * (double)x[o + i];
 }
 
 __global__ void axpby_kernel(int64_t len, double a, const double* __restrict__ x, double b,
@@ -1770,19 +1876,19 @@ __global__ void unpack_kernel(int nl, int nE, bool ns, const T* __restrict__ Ap,
 
 template <typename T>
 void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* x, T* y, T alpha,
-                   const T* xadd) {
-#define MV(ND)                                                        \
-  if (ns) launch_matvec_nd<T, ND, true>(s, n, A, x, y, alpha, xadd);   \
-  else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha, xadd)
+                   const T* xadd, int k) {
+#define MV(ND)                                                           \
+  if (ns) launch_matvec_nd<T, ND, true>(s, n, A, x, y, alpha, xadd, k);   \
+  else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha, xadd, k)
   ND_DISPATCH(nd, MV)
 #undef MV
 }
 
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
-                        const float* x, float* y, float alpha, const float* xadd) {
-#define MVB(ND)                                                              \
-  if (ns) launch_matvec_bf16_nd<ND, true>(s, n, A, x, y, alpha, xadd);       \
-  else launch_matvec_bf16_nd<ND, false>(s, n, A, x, y, alpha, xadd)
+                        const float* x, float* y, float alpha, const float* xadd, int k) {
+#define MVB(ND)                                                                 \
+  if (ns) launch_matvec_bf16_nd<ND, true>(s, n, A, x, y, alpha, xadd, k);       \
+  else launch_matvec_bf16_nd<ND, false>(s, n, A, x, y, alpha, xadd, k)
   ND_DISPATCH(nd, MVB)
 #undef MVB
 }
@@ -1812,10 +1918,10 @@ void launch_bj_blocks(cudaStream_t s, int n, int nd, bool ns, const T* A, T* Din
 
 template <typename T>
 void launch_bj_update(cudaStream_t s, int n, int nd, bool ns, const T* Dinv, const T* r, T* y,
-                      T* e, T omega, int first, const T* xadd) {
-#define BU(ND)                                                                        \
-  if (ns) launch_bj_update_nd<T, ND, true>(s, n, Dinv, r, y, e, omega, first, xadd);  \
-  else launch_bj_update_nd<T, ND, false>(s, n, Dinv, r, y, e, omega, first, xadd)
+                      T* e, T omega, int first, const T* xadd, int k) {
+#define BU(ND)                                                                           \
+  if (ns) launch_bj_update_nd<T, ND, true>(s, n, Dinv, r, y, e, omega, first, xadd, k);  \
+  else launch_bj_update_nd<T, ND, false>(s, n, Dinv, r, y, e, omega, first, xadd, k)
   ND_DISPATCH(nd, BU)
 #undef BU
 }
@@ -1855,20 +1961,21 @@ void launch_agglomerate(cudaStream_t s, int nc, bool ns, const T* Af, T* Ac, T* 
 
 template <typename T>
 void launch_local_correction(cudaStream_t s, int nc, bool ns, const T* AIIinv, const T* Y,
-                             const T* r, T* e) {
+                             const T* r, T* e, int k) {
   const P1Geom g = make_p1geom(2 * nc);
+  const dim3 grid(nblk(8 * nc * nc, 128), k);
   note_launch();
   if (ns)
-    local_correction_kernel<T, true><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(g, AIIinv, Y, r, e);
+    local_correction_kernel<T, true><<<grid, 128, 0, s>>>(g, AIIinv, Y, r, e);
   else
-    local_correction_kernel<T, false><<<nblk(8 * nc * nc, 128), 128, 0, s>>>(g, AIIinv, Y, r, e);
+    local_correction_kernel<T, false><<<grid, 128, 0, s>>>(g, AIIinv, Y, r, e);
 }
 
 template <typename T>
 void launch_edge_p1(cudaStream_t s, int n, bool ns, const T* A, const T* Dinv, const T* r, const T* x,
-                    T* out, T omega, bool sweep) {
+                    T* out, T omega, bool sweep, int k) {
   const P1Geom g = make_p1geom(n);
-  const int nb = nblk(g.nedge, 128);
+  const dim3 nb(nblk(g.nedge, 128), k);
   note_launch();
   if (ns) {
     if (sweep)
@@ -1935,32 +2042,32 @@ void launch_normalize(cudaStream_t s, int64_t len, const T* y, const double* nrm
 }
 
 template <typename T>
-void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc) {
+void launch_restrict_h(cudaStream_t s, int nc, const T* Pi, const T* r, T* y, T* rc, int k) {
   upload_jc();
   const int nedc = 2 * nc * (nc + 1);
   note_launch();
-  restrict_h_kernel<T><<<nblk(2 * nedc, 128), 128, 0, s>>>(make_p1geom(2 * nc), Pi, r, y, rc);
+  restrict_h_kernel<T><<<dim3(nblk(2 * nedc, 128), k), 128, 0, s>>>(make_p1geom(2 * nc), Pi, r, y,
+                                                                    rc);
 }
 
 template <typename T>
-void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y) {
+void launch_prolong_h(cudaStream_t s, int nc, const T* Pi, const T* ec, T* e, T* y, int k) {
   upload_jc();
   const int tot = 8 * nc * nc + 4 * nc * (nc + 1);
   note_launch();
-  prolong_h_kernel<T><<<nblk(tot, 128), 128, 0, s>>>(make_p1geom(2 * nc), Pi, ec, e, y);
+  prolong_h_kernel<T><<<dim3(nblk(tot, 128), k), 128, 0, s>>>(make_p1geom(2 * nc), Pi, ec, e, y);
 }
 
 template <typename T>
 void launch_bj_first_restrict_p(cudaStream_t s, int n, int nd0, bool ns, const T* Dinv1,
-                                const T* r0, T* y0, T* r1, T* e1, T omega) {
+                                const T* r0, T* y0, T* r1, T* e1, T omega, int k) {
   const P1Geom g = make_p1geom(n);
+  const dim3 grid(nblk(g.nedge, 128), k);
   note_launch();
   if (ns)
-    bj_first_restrict_p_kernel<T, true><<<nblk(g.nedge, 128), 128, 0, s>>>(g, nd0, Dinv1, r0, y0,
-                                                                            r1, e1, omega);
+    bj_first_restrict_p_kernel<T, true><<<grid, 128, 0, s>>>(g, nd0, Dinv1, r0, y0, r1, e1, omega);
   else
-    bj_first_restrict_p_kernel<T, false><<<nblk(g.nedge, 128), 128, 0, s>>>(g, nd0, Dinv1, r0, y0,
-                                                                             r1, e1, omega);
+    bj_first_restrict_p_kernel<T, false><<<grid, 128, 0, s>>>(g, nd0, Dinv1, r0, y0, r1, e1, omega);
 }
 
 template <typename T>
@@ -2021,9 +2128,10 @@ void launch_coarse_inverse(cudaStream_t s, int nf, const double* L, double* Li, 
 
 template <typename T>
 void launch_coarse_solve(cudaStream_t s, int n, const int* freeidx, const int* fedge, int nf,
-                         const double* Ainv, const T* r, T* e) {
+                         const double* Ainv, const T* r, T* e, int k) {
   note_launch();
-  coarse_solve_kernel<T><<<1, 256, sizeof(double) * (nf + 1), s>>>(n, freeidx, fedge, nf, Ainv, r, e);
+  coarse_solve_kernel<T><<<dim3(1, k), 256, sizeof(double) * (nf + 1), s>>>(n, freeidx, fedge, nf,
+                                                                             Ainv, r, e);
 }
 
 template <typename T>
@@ -2153,18 +2261,18 @@ void launch_cg_direction(cudaStream_t s, int64_t len, const double* scal, const 
 
 template <typename T>
 void launch_dot_fused(cudaStream_t s, int64_t len, const T* a, const T* b, double* partial,
-                      unsigned* counter, double* scal, int mode) {
+                      unsigned* counter, double* scal, int mode, int k) {
   note_launch();
-  dot_fused_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, a, b, partial, counter, scal, mode);
+  dot_fused_kernel<T><<<dim3(kDotBlocks, k), 256, 0, s>>>(len, a, b, partial, counter, scal, mode);
 }
 
 template <typename T>
 void launch_cg_direction_zero(cudaStream_t s, int64_t len, const double* scal, const T* z, T* p,
-                              T* Ap) {
+                              T* Ap, int k) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
   note_launch();
-  cg_direction_zero_kernel<T><<<blocks, 256, 0, s>>>(len, scal, z, p, Ap);
+  cg_direction_zero_kernel<T><<<dim3(blocks, k), 256, 0, s>>>(len, scal, z, p, Ap);
 }
 
 template <typename T>
@@ -2192,19 +2300,33 @@ void launch_cg_direction_zero_mixed(cudaStream_t s, int64_t len, const double* s
 }
 
 void launch_scale_to_f32(cudaStream_t s, int64_t len, const double* in, const double* scale,
-                         float* out) {
+                         float* out, int k, int sstride) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
   note_launch();
-  scale_to_f32_kernel<<<blocks, 256, 0, s>>>(len, in, scale, out);
+  scale_to_f32_kernel<<<dim3(blocks, k), 256, 0, s>>>(len, in, scale, out, sstride);
 }
 
-void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y) {
+void launch_add_f32(cudaStream_t s, int64_t len, const double* scale, const float* x, double* y,
+                    int k, int sstride) {
   int blocks = nblk(len, 256);
   if (blocks > 2432) blocks = 2432;
   note_launch();
-  add_f32_kernel<<<blocks, 256, 0, s>>>(len, scale, x, y);
+  add_f32_kernel<<<dim3(blocks, k), 256, 0, s>>>(len, scale, x, y, sstride);
 }
+
+template <typename T>
+void launch_cg_update_test_block(cudaStream_t s, int64_t len, int k, double* scal, T* x, T* r,
+                                 const T* p, const T* Ap, double* partial, unsigned* counter,
+                                 cudaGraphConditionalHandle h, int* it, int max_it, double tol2) {
+  note_launch();
+  cg_update_test_block_kernel<T><<<dim3(kDotBlocks, k), 256, 0, s>>>(len, scal, x, r, p, Ap, partial,
+                                                                     counter, h, it, max_it, tol2);
+}
+template void launch_cg_update_test_block<float>(cudaStream_t, int64_t, int, double*, float*,
+                                                 float*, const float*, const float*, double*,
+                                                 unsigned*, cudaGraphConditionalHandle, int*, int,
+                                                 double);
 
 void launch_axpby(cudaStream_t s, int64_t len, double a, const double* x, double b, double* y) {
   int blocks = nblk(len, 256);
@@ -2227,18 +2349,18 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
 // explicit instantiations
 #define INST(T)                                                                                 \
   template void launch_matvec<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T,       \
-                                 const T*);                                                     \
+                                 const T*, int);                                                \
   template void launch_bj_blocks<T>(cudaStream_t, int, int, bool, const T*, T*, int*);          \
   template void launch_bj_update<T>(cudaStream_t, int, int, bool, const T*, const T*, T*, T*, T, \
-                                    int, const T*);                                             \
+                                    int, const T*, int);                                        \
   template void launch_bj_first_restrict_p<T>(cudaStream_t, int, int, bool, const T*, const T*, \
-                                              T*, T*, T*, T);                                   \
+                                              T*, T*, T*, T, int);                              \
   template void launch_pcoarsen<T>(cudaStream_t, int, int, bool, const T*, T*);                 \
   template void launch_agglomerate<T>(cudaStream_t, int, bool, const T*, T*, T*, T*, T*, T*,    \
                                       int*);                                                    \
   template void launch_local_correction<T>(cudaStream_t, int, bool, const T*, const T*,         \
-                                           const T*, T*);                                       \
-  template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);            \
+                                           const T*, T*, int);                                  \
+  template void launch_restrict_h<T>(cudaStream_t, int, const T*, const T*, T*, T*, int);       \
   template void launch_point_diag<T>(cudaStream_t, int, int, bool, const T*, T*);               \
   template void launch_pj_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T, int); \
   template void launch_cheb_update<T>(cudaStream_t, int, int, const T*, const T*, T*, T*, T*,   \
@@ -2249,14 +2371,14 @@ void launch_copy_boundary(cudaStream_t s, int n, int nd, const double* gD, doubl
   template void launch_scale_by<T>(cudaStream_t, int64_t, const T*, T*);                        \
   template void launch_normalize<T>(cudaStream_t, int64_t, const T*, const double*, T*);        \
   template void launch_edge_p1<T>(cudaStream_t, int, bool, const T*, const T*, const T*,       \
-                                  const T*, T*, T, bool);                                       \
-  template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*);             \
+                                  const T*, T*, T, bool, int);                                  \
+  template void launch_prolong_h<T>(cudaStream_t, int, const T*, const T*, T*, T*, int);        \
   template void launch_restrict_p<T>(cudaStream_t, int, int, const T*, T*, T*);                 \
   template void launch_prolong_p<T>(cudaStream_t, int, int, const T*, T*);                      \
   template void launch_coarse_assemble<T>(cudaStream_t, int, bool, const T*, const int*, int,   \
                                           double*);                                             \
   template void launch_coarse_solve<T>(cudaStream_t, int, const int*, const int*, int,          \
-                                       const double*, const T*, T*);                            \
+                                       const double*, const T*, T*, int);                       \
   template void launch_mask<T>(cudaStream_t, int, int, T*);                                     \
   template void launch_unpack<T>(cudaStream_t, int, int, bool, const T*, double*);
 INST(double)
@@ -2270,13 +2392,13 @@ template bool launch_coarse_setup_smem<float>(cudaStream_t, int, bool, const flo
                                               double*, int*);
 template void launch_dot<double>(cudaStream_t, int64_t, const double*, const double*, double*, double*);
 template void launch_dot_fused<double>(cudaStream_t, int64_t, const double*, const double*, double*,
-                                       unsigned*, double*, int);
+                                       unsigned*, double*, int, int);
 template void launch_dot_fused<float>(cudaStream_t, int64_t, const float*, const float*, double*,
-                                      unsigned*, double*, int);
+                                      unsigned*, double*, int, int);
 template void launch_cg_direction_zero<double>(cudaStream_t, int64_t, const double*, const double*,
-                                               double*, double*);
+                                               double*, double*, int);
 template void launch_cg_direction_zero<float>(cudaStream_t, int64_t, const double*, const float*,
-                                              float*, float*);
+                                              float*, float*, int);
 template void launch_cg_update_test<double>(cudaStream_t, int64_t, double*, double*, double*,
                                             const double*, const double*, double*, unsigned*,
                                             cudaGraphConditionalHandle, int*, int, double, float*);
