@@ -181,15 +181,17 @@ typedef struct {
                              off.  hdgmg_batch_create uses 0 for its contexts.
                              64                                              */
   int32_t pcycle;         /* 1: with BLOCK_JACOBI, the P1 levels of every
-                             V-cycle (from the first P1 level down to the
-                             coarsest and back) run as ONE cooperative
+                             FP32 V-cycle (from the first P1 level down to
+                             the coarsest and back) run as ONE cooperative
                              kernel launch, the steps separated by grid
                              barriers whose waits are bounded (a wait that
                              runs out makes the solve return HDGMG_ETIMEOUT
-                             and leaves the context usable); 0: separate
-                             launches per step plus the single-block tail.
-                             Needs a coarsest level with at most 4096
-                             unknowns; otherwise the launched form runs.  1 */
+                             and leaves the context usable); the FP64 cycle
+                             stays launched (faster on GB300); 2: the FP64
+                             cycle too; 0: separate launches per step plus
+                             the single-block tail.  Needs a coarsest level
+                             with at most 4096 unknowns; otherwise the
+                             launched form runs.  1                         */
   int32_t pcycle_tail_n;  /* pcycle = 1: the levels with n <= this run on
                              one thread block of the launch (block barriers)
                              while the others wait at one grid barrier; 0:

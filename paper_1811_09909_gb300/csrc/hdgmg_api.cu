@@ -450,6 +450,10 @@ void plan_pcycle(hdgmg_ctx* c) {
   c->pc_start = -1;
   const hdgmg_opts& o = c->opts;
   if (o.pcycle <= 0 || o.smoother != HDGMG_SMOOTH_BLOCK_JACOBI) return;
+  // the FP64 cycle's steps are FP64-pipe bound and run faster as launched
+  // kernels with more threads per SM (measured at 256^2, p = 4: 17.8 ms per
+  // step launched, 18.9 persistent); pcycle = 2 forces the persistent form
+  if (std::is_same<T, double>::value && o.pcycle < 2) return;
   const int last = (int)c->levels.size() - 1;
   int ls = -1;
   for (int l = 0; l < last; ++l) {
@@ -882,7 +886,13 @@ hdgmg_status build_rhs(hdgmg_ctx* c, const double* f, const double* gD) {
     c->basis ? launch_rhs(s, c->refd, c->p, c->n, c->kap, c->ktau, f, c->b)
              : launch_rhs_factor(s, c->refd, c->p, c->n, c->kap, c->ktau, c->Lfac, f, c->b);
   launch_copy_boundary(s, c->n, c->p + 1, gD, c->lam);
-  if (gD) launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->b, -1.0);
+  if (gD) {
+    // the lift -A lambda_D formed in a zeroed buffer (two contributions per
+    // entry, so their order cannot change the sum), then subtracted
+    CUDA_TRY(cudaMemsetAsync(c->Ap, 0, sizeof(double) * len, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->lam, c->Ap, 1.0);
+    launch_axpby(s, len, -1.0, c->Ap, 1.0, c->b);
+  }
   return check_launch("condensed right-hand side");
 }
 
@@ -1030,8 +1040,11 @@ hdgmg_status refine_solve(hdgmg_ctx* c, double nb, int* iters, int* outer, doubl
   *conv = false;
   *breakdown = false;
   for (;;) {
+    // r = b - A x with A x formed in a zeroed buffer (deterministic sum)
+    CUDA_TRY(cudaMemsetAsync(c->Ap, 0, sizeof(double) * len, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->x, c->Ap, 1.0);
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->x, c->r, -1.0);
+    launch_axpby(s, len, -1.0, c->Ap, 1.0, c->r);
     launch_dot<double>(s, len, c->r, c->r, c->partial, c->scal + 7);
     CUDA_TRY(cudaMemcpyAsync(c->scal_h + 7, c->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1107,8 +1120,10 @@ hdgmg_status refine_solve_block(hdgmg_ctx* c, int k, const double* nb, int* iter
   *conv = false;
   *breakdown = false;
   for (;;) {
-    CUDA_TRY(cudaMemcpyAsync(c->Rb, c->Bb, sizeof(double) * len * k, cudaMemcpyDeviceToDevice, s));
-    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->Xb, c->Rb, -1.0, nullptr, k);
+    // R = B - A X with A X formed in the zeroed R (deterministic sums)
+    CUDA_TRY(cudaMemsetAsync(c->Rb, 0, sizeof(double) * len * k, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, L0.d64.A, c->Xb, c->Rb, 1.0, nullptr, k);
+    launch_axpby(s, len * k, 1.0, c->Bb, -1.0, c->Rb);
     launch_dot_fused<double>(s, len, c->Rb, c->Rb, c->partial_b, c->counter_b, c->scal64b, 2, k);
     CUDA_TRY(cudaMemcpyAsync(c->scal_hb, c->scal64b, sizeof(double) * 8 * k, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -1270,8 +1285,10 @@ hdgmg_status gmres_solve(hdgmg_ctx* c, double nb, int* iters, double* rel, bool*
   int* jh = reinterpret_cast<int*>(yh + (m + 1));
   for (int cycle = 0; cycle < o.max_it; ++cycle) {
     // r = b - A x, its norm, v_0 = r / ||r||
+    CUDA_TRY(cudaMemsetAsync(c->Ap, 0, sizeof(double) * len, s));
+    launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->x, c->Ap, 1.0);
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
-    launch_matvec<double>(s, c->n, c->p + 1, c->ns, c->levels[0].d64.A, c->x, c->r, -1.0);
+    launch_axpby(s, len, -1.0, c->Ap, 1.0, c->r);
     const double rr = dot_sync(c, c->r, c->r);
     *rel = std::sqrt(rr) / nb;
     if (!std::isfinite(rr)) { *breakdown = true; return HDGMG_OK; }

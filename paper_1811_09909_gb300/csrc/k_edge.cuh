@@ -27,9 +27,10 @@ static __device__ __forceinline__ float load_entry(const __nv_bfloat16* p) {
 // ---------------------------------------------------------------- K6 matvec
 // xadd (nullable, modes 0 and 1 only): x + J xadd is applied instead of x,
 // i.e. the P1 correction of the next level is prolonged on the fly
-// blockIdx.y: right-hand side of a blocked solve (x, y with stride ND
-// n_edges, xadd with the P1 stride 2 n_edges)
-template <typename T, int ND, bool NS, typename TA = T>
+// MULTI: blockIdx.y is the right-hand side of a blocked solve (x, y with
+// stride ND n_edges, xadd with the P1 stride 2 n_edges); the one-right-hand-
+// side instantiation carries no offset code
+template <typename T, int ND, bool NS, typename TA = T, bool MULTI = false>
 __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict__ A,
                                                      const T* __restrict__ x, T* __restrict__ y,
                                                      T alpha, const T* __restrict__ xadd) {
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nE) return;
   const int nedge = 2 * n * (n + 1);
-  if (blockIdx.y) {
+  if (MULTI) {
     x += (size_t)blockIdx.y * ND * nedge;
     y += (size_t)blockIdx.y * ND * nedge;
     if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
@@ -217,25 +218,24 @@ __global__ void bj_blocks_kernel(int n, const T* __restrict__ A, T* __restrict__
 }
 
 // --------------------------------------------------- K7 block-Jacobi update
-// every load of an edge (r, y, e, xadd, D^-1) is issued before its stores, so
-// the edge's 5 ND-mode round trips overlap
-template <typename T, int ND, bool NS>
+// every vector load of an edge (r, y, e, xadd) is issued before its stores,
+// so that the edge's ND round trips overlap (D^-1 is read in the product:
+// holding all its ND^2 entries would cost registers at large ND)
+template <typename T, int ND, bool NS, bool MULTI = false>
 __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __restrict__ r,
                                  T* __restrict__ y, T* __restrict__ e, T omega, int first,
                                  const T* __restrict__ xadd) {
   const int nedge = 2 * n * (n + 1);
   const int edge = blockIdx.x * blockDim.x + threadIdx.x;
   if (edge >= nedge || bnd_edge(n, edge)) return;
-  if (blockIdx.y) {                         // right-hand side of a blocked solve
+  if (MULTI) {                              // right-hand side blockIdx.y of a blocked solve
     const size_t o = (size_t)blockIdx.y * ND * nedge;
     r += o;
     y += o;
     e += o;
     if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
   }
-  T d[ND], eo[ND], Dv[NS ? ND * ND : ND * (ND + 1) / 2];
-#pragma unroll
-  for (int t = 0; t < (NS ? ND * ND : ND * (ND + 1) / 2); ++t) Dv[t] = Dinv[(size_t)t * nedge + edge];
+  T d[ND], eo[ND];
   if (first) {
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
@@ -260,26 +260,37 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
   for (int a = 0; a < ND; ++a) {
     T s = T(0);
 #pragma unroll
-    for (int b = 0; b < ND; ++b) s += Dv[NS ? a * ND + b : pk_any(a, b)] * d[b];
+    for (int b = 0; b < ND; ++b)
+      s += Dinv[(size_t)(NS ? a * ND + b : pk_any(a, b)) * nedge + edge] * d[b];
     const size_t ix = (size_t)a * nedge + edge;
     e[ix] = first ? omega * s : eo[a] + omega * s;
   }
 }
 
 
+// k > 1 right-hand sides of a blocked solve: one launch over gridDim.y = k
+// (the right-hand sides' blocks read the operator from L2 together)
 template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha,
                       const T* xadd, int k) {
   note_launch();
-  matvec_kernel<T, ND, NS><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(n, A, x, y, alpha, xadd);
+  if (k > 1)
+    matvec_kernel<T, ND, NS, T, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(n, A, x, y, alpha,
+                                                                                 xadd);
+  else
+    matvec_kernel<T, ND, NS><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha, xadd);
 }
 
 template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
                            float alpha, const float* xadd, int k) {
   note_launch();
-  matvec_kernel<float, ND, NS, __nv_bfloat16><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(
-      n, A, x, y, alpha, xadd);
+  if (k > 1)
+    matvec_kernel<float, ND, NS, __nv_bfloat16, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(
+        n, A, x, y, alpha, xadd);
+  else
+    matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha,
+                                                                                xadd);
 }
 
 template <typename T, int ND, bool NS>
@@ -292,8 +303,12 @@ template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first, const T* xadd, int k) {
   note_launch();
-  bj_update_kernel<T, ND, NS><<<dim3(nblk(2 * n * (n + 1), 128), k), 128, 0, s>>>(
-      n, Dinv, r, y, e, omega, first, xadd);
+  if (k > 1)
+    bj_update_kernel<T, ND, NS, true><<<dim3(nblk(2 * n * (n + 1), 128), k), 128, 0, s>>>(
+        n, Dinv, r, y, e, omega, first, xadd);
+  else
+    bj_update_kernel<T, ND, NS><<<nblk(2 * n * (n + 1), 128), 128, 0, s>>>(n, Dinv, r, y, e, omega,
+                                                                           first, xadd);
 }
 
 }  // namespace hdgmg

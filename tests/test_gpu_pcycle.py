@@ -1,4 +1,5 @@
-"""GPU tests of the persistent V-cycle over the P1 levels (opts.pcycle = 1):
+"""GPU tests of the persistent V-cycle over the P1 levels (opts.pcycle = 2:
+in the FP32 and the FP64 cycle; the default 1 keeps the FP64 cycle launched):
 Algorithm 1 from the first P1 level to the coarsest and back in one
 cooperative launch, the steps separated by grid barriers with bounded waits.
 
@@ -62,7 +63,7 @@ def rel_max(a, b):
                                               (8, 2, "none", 2, 0)])
 def test_pcycle_vcycle_matches_oracle(n, p, lc, m, tail_n):
     wl = workload(n, p, 41 + p)
-    s = make(wl, coarsest_n=2, m_fine=m, local_corr=LC[lc], pcycle=1, pcycle_tail_n=tail_n)
+    s = make(wl, coarsest_n=2, m_fine=m, local_corr=LC[lc], pcycle=2, pcycle_tail_n=tail_n)
     H = mg.Hierarchy(hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau()), coarsest_n=2, m_fine=m,
                      local_corr=lc)
     rng = np.random.default_rng(9)
@@ -84,7 +85,7 @@ def test_pcycle_matches_launched_cycle(precision, n, p, tol):
     below from the restricted residual."""
     wl = workload(n, p, 60 + p)
     kw = dict(coarsest_n=4, m_fine=1, m_max=2, precision=precision)
-    a = make(wl, pcycle=1, **kw)
+    a = make(wl, pcycle=2, **kw)
     b = make(wl, pcycle=0, **kw)
     rng = np.random.default_rng(10)
     r = cuda(rng.standard_normal((p + 1, hdg.n_edges(n))))
@@ -99,7 +100,7 @@ def test_pcycle_nonsymmetric_matches_launched_cycle():
     kw = dict(coarsest_n=4, m_fine=1, m_max=2, krylov=hdgmg.KRYLOV_GMRES, local_corr=hdgmg.LC_PRE)
     r = cuda(np.random.default_rng(13).standard_normal((p + 1, hdg.n_edges(n))))
     out = []
-    for pc in (1, 0):
+    for pc in (2, 0):
         s = hdgmg.Solver(n, p, tau_mode=hdgmg.TAU_OVER_H, tau_c=wl.tau_c, beta=wl.beta, pcycle=pc, **kw)
         s.setup(cuda(wl.log_kappa))
         out.append(host(s.apply_vcycle(r)))
@@ -111,7 +112,7 @@ def test_pcycle_pcg_solution(precision):
     n, p = 32, 3
     wl = workload(n, p, 70)
     kw = dict(coarsest_n=4, m_fine=1, m_max=2, precision=precision, rtol=1e-13)
-    a = make(wl, pcycle=1, **kw)
+    a = make(wl, pcycle=2, **kw)
     b = make(wl, pcycle=0, **kw)
     f = cuda(wl.f[0])
     la, _, _, ia = a.solve(f, want_u=False, want_q=False)
@@ -130,7 +131,7 @@ def test_pcycle_expired_wait_reports_timeout(precision):
     next solve gives the same answer as before (barrier and flag reset)."""
     n, p = 64, 2
     wl = workload(n, p, 80)
-    s = make(wl, coarsest_n=4, m_fine=1, m_max=2, precision=precision)
+    s = make(wl, coarsest_n=4, m_fine=1, m_max=2, precision=precision, pcycle=2)
     f = cuda(wl.f[0])
     lam0, _, _, i0 = s.solve(f, want_u=False, want_q=False)
     st = s.lib.hdgmg_check_cycle_timeout(s.ctx, 2000)
