@@ -415,6 +415,22 @@ hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* ctx, const double* r, double* e);
  * counterpart.) */
 hdgmg_status hdgmg_check_cycle_timeout(hdgmg_ctx* ctx, int32_t wait_us);
 
+/* Step trace of the persistent V-cycle (opts.pcycle): applies one V-cycle
+ * exactly as hdgmg_apply_vcycle (same r, e), and thread 0 of block 0 of the
+ * persistent kernel records, after each barrier, the device's global timer
+ * (ns) and the tag of the step the barrier ended.  stamps: host int64 array
+ * of 2 * cap entries, written as (time_ns, tag) pairs; *count: pairs
+ * written (at most cap, 1 <= cap <= 4096).  tag = level * 16 + kind, level
+ * counted from the first P1 level of the persistent cycle, kind: 0 kernel
+ * start, 1 first sweep, 2 down sweep, 3 local correction, 4 residual +
+ * restriction, 5 residual, 6 restriction, 7 coarsest solve, 8 prolongation,
+ * 9 up sweep, 10 end of the block-0 tail, 11 kernel end (block 0).  The
+ * steps of the block-0 tail are stamped after its block barriers.
+ * HDGMG_EINVAL when the context does not run the persistent cycle.  (A
+ * profiling entry point; the paper has no counterpart.) */
+hdgmg_status hdgmg_trace_vcycle(hdgmg_ctx* ctx, const double* r, double* e, int64_t* stamps,
+                                int32_t cap, int32_t* count);
+
 /* The condensed right-hand side b = sum_e g_e - A lambda_D on interior
  * edges (Sec. 2; Dirichlet data applied strongly): f, g_D as in hdgmg_solve
  * (one right-hand side), b device [p+1][n_edges] FP64 out. */

@@ -139,6 +139,11 @@ struct hdgmg_ctx {
   unsigned long long* pc_bar = nullptr;
   PCycleParams<float> pc32;
   PCycleParams<double> pc64;
+  // step trace of the persistent cycle (hdgmg_trace_vcycle): device buffer of
+  // pc_trace_cap (time, tag) pairs, armed for one call only
+  unsigned long long* pc_trace = nullptr;
+  int pc_trace_cap = 0;
+  bool pc_trace_armed = false;
   // blocked solves of up to kb right-hand sides (opts.rhs_block): FP32 level
   // vectors hold kb copies [kb][...]; kr is the count the V-cycle launches
   // run with (1 outside a blocked solve)
@@ -632,6 +637,10 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
     P.rp_y0 = rp_y0;
     P.rp_nd0 = rp_nd0;
     P.nrhs = c->kr;
+    if (c->pc_trace_armed) {
+      P.trace = c->pc_trace;
+      P.trace_cap = c->pc_trace_cap;
+    }
     launch_pcycle<T>(s, P, blocked ? c->pc_blocks_b : c->pc_blocks);
     return;
   }
@@ -1524,6 +1533,7 @@ void hdgmg_destroy(hdgmg_ctx* c) {
   if (c->l2_window) cudaCtxResetPersistingL2Cache();   // demote this run's persisting lines
   for (void* p : c->allocs) cudaFree(p);
   if (c->err_h) cudaFreeHost(c->err_h);
+  if (c->pc_trace) cudaFree(c->pc_trace);
   if (c->scal_h) cudaFreeHost(c->scal_h);
   if (c->init_h) cudaFreeHost(c->init_h);
   if (c->it_h) cudaFreeHost(c->it_h);
@@ -2194,6 +2204,38 @@ hdgmg_status hdgmg_apply_vcycle(hdgmg_ctx* c, const double* r, double* e) {
     CUDA_TRY(cudaMemcpyAsync(c->err_h + 2, c->err + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   return cycle_wait_status(c);
+}
+
+hdgmg_status hdgmg_trace_vcycle(hdgmg_ctx* c, const double* r, double* e, int64_t* stamps,
+                                int32_t cap, int32_t* count) {
+  if (!c || !r || !e || !stamps || !count) return fail(HDGMG_EINVAL, "NULL argument");
+  if (!c->setup_done) return fail(HDGMG_EINVAL, "hdgmg_setup has not succeeded");
+  if (c->pc_start < 0) return fail(HDGMG_EINVAL, "this context does not run the persistent cycle");
+  if (cap < 1 || cap > 4096) return fail(HDGMG_EINVAL, "cap must be in [1, 4096]");
+  cudaStream_t s = c->stream;
+  if (c->pc_trace_cap < cap) {
+    if (c->pc_trace) cudaFree(c->pc_trace);
+    c->pc_trace = nullptr;
+    c->pc_trace_cap = 0;
+    CUDA_TRY(cudaMalloc(&c->pc_trace, sizeof(unsigned long long) * 2 * (size_t)cap));
+    c->pc_trace_cap = cap;
+  }
+  CUDA_TRY(cudaMemsetAsync(c->pc_trace, 0xff, sizeof(unsigned long long) * 2 * (size_t)cap, s));
+  const int saved = c->pc_trace_cap;
+  c->pc_trace_cap = cap;
+  c->pc_trace_armed = true;
+  const hdgmg_status st = hdgmg_apply_vcycle(c, r, e);
+  c->pc_trace_armed = false;
+  c->pc_trace_cap = saved;
+  if (st != HDGMG_OK) return st;
+  std::vector<unsigned long long> h(2 * (size_t)cap);
+  CUDA_TRY(cudaMemcpy(h.data(), c->pc_trace, sizeof(unsigned long long) * h.size(),
+                      cudaMemcpyDeviceToHost));
+  int k = 0;
+  while (k < cap && h[2 * k] != ~0ull) ++k;
+  for (int i = 0; i < 2 * k; ++i) stamps[i] = (int64_t)h[i];
+  *count = k;
+  return HDGMG_OK;
 }
 
 hdgmg_status hdgmg_check_cycle_timeout(hdgmg_ctx* c, int32_t wait_us) {

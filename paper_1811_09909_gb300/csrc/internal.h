@@ -448,6 +448,10 @@ struct PCycleParams {
                                 // tail's bulk copies expired (both HDGMG_ETIMEOUT)
   unsigned long long wait_ns = 1000000000ull;   // limit of one barrier wait
   int withhold = 0;             // testing: no block arrives at the first barrier
+  // profiling: (global timer ns, step tag) pairs written by block 0 after each
+  // barrier, at most trace_cap pairs (null: no trace)
+  unsigned long long* trace = nullptr;
+  int trace_cap = 0;
   // dynamic shared memory: the block-0 tail's staged levels (staged = 1), the
   // coarsest inverse at so_Ainv and the coarse workspace at so_w (bytes)
   int staged = 0;

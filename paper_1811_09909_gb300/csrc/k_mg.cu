@@ -993,7 +993,25 @@ __device__ __forceinline__ bool pc_mbar_wait(unsigned long long* bar, unsigned l
 struct PcSync {
   unsigned long long target = 0;   // thread 0: arrivals that end the current barrier
   int first = 1;                   // no barrier passed yet
+  int nstep = 0;                   // thread 0 of block 0: trace records written
 };
+
+// Step trace (P.trace non-null): thread 0 of block 0 records, after each
+// barrier, the global timer and the tag of the step that barrier ended
+// (level * 16 + kind, the PcStep values), up to P.trace_cap records.
+enum PcStep {
+  kPcStart = 0, kPcFirst = 1, kPcSweepDown = 2, kPcLc = 3, kPcResidRestrict = 4, kPcResid = 5,
+  kPcRestrict = 6, kPcCoarse = 7, kPcProlong = 8, kPcSweepUp = 9, kPcTail = 10, kPcEnd = 11
+};
+
+template <typename T>
+__device__ __forceinline__ void pc_stamp(const PCycleParams<T>& P, PcSync& st, int tag) {
+  if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && st.nstep < P.trace_cap) {
+    P.trace[2 * st.nstep] = pc_now_ns();
+    P.trace[2 * st.nstep + 1] = (unsigned long long)tag;
+    ++st.nstep;
+  }
+}
 
 // Grid barrier on a monotonic arrival count: thread 0 of every block adds one
 // with release semantics (after the block barrier, so the block's writes are
@@ -1037,9 +1055,10 @@ __device__ bool pc_grid_sync(const PCycleParams<T>& P, PcSync& st, volatile int*
 
 template <typename T>
 __device__ __forceinline__ bool pc_sync(const PCycleParams<T>& P, bool grid, PcSync& st,
-                                        volatile int* s_ok) {
-  if (grid) return pc_grid_sync<T>(P, st, s_ok);
-  __syncthreads();
+                                        volatile int* s_ok, int tag) {
+  if (grid && !pc_grid_sync<T>(P, st, s_ok)) return false;
+  if (!grid) __syncthreads();
+  pc_stamp<T>(P, st, tag);
   return true;
 }
 
@@ -1089,14 +1108,14 @@ __device__ bool pc_down(const PCycleParams<T>& P, int l, int i0, int di, bool gr
     } else {
       PC_FOR(ned, g.dne) p1_first<T, NS>(g, L.Dinv, L.r + rhs * V, bufs[1] + rhs * V, P.omega, t);
     }
-    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+    if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcFirst)) return false;
   }
   for (int it = 1; it < L.m; ++it) {
     PC_FOR(ned, g.dne)
-    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
-                         bufs[1 - cur] + rhs * V, P.omega, t);
+    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, (cur ? bufs[1] : bufs[0]) + rhs * V,
+                         (cur ? bufs[0] : bufs[1]) + rhs * V, P.omega, t);
     cur ^= 1;
-    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+    if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcSweepDown)) return false;
   }
   // the next level's first sweep joins its restriction unless it is the
   // coarsest level (no smoothing) or the first, staged level of the tail
@@ -1108,21 +1127,21 @@ __device__ bool pc_down(const PCycleParams<T>& P, int l, int i0, int di, bool gr
   const T* Dc = P.lv[l + 1].Dinv;
   if (P.lc != HDGMG_LC_NONE) {
     PC_FOR(8 * g.nC, g.dlc)
-    p1_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, bufs[cur] + rhs * V, t);
-    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+    p1_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, (cur ? bufs[1] : bufs[0]) + rhs * V, t);
+    if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcLc)) return false;
     PC_FOR(2 * g.nedc, g.dc2)
-    p1_resid_restrict2<T, NS>(g, L.A, L.r + rhs * V, bufs[cur] + rhs * V, rc + rhs * Vc, Dc,
+    p1_resid_restrict2<T, NS>(g, L.A, L.r + rhs * V, (cur ? bufs[1] : bufs[0]) + rhs * V, rc + rhs * Vc, Dc,
                               ec ? ec + rhs * Vc : nullptr, P.omega, t);
-    return pc_sync<T>(P, grid, st, s_ok);
+    return pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcResidRestrict);
   }
   PC_FOR(ned, g.dne)
-  p1_edge<T, NS, false>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
-                        bufs[1 - cur] + rhs * V, P.omega, t);
-  if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  p1_edge<T, NS, false>(g, L.A, L.Dinv, L.r + rhs * V, (cur ? bufs[1] : bufs[0]) + rhs * V,
+                        (cur ? bufs[0] : bufs[1]) + rhs * V, P.omega, t);
+  if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcResid)) return false;
   PC_FOR(g.nedc, g.dc1)
-  p1_restrict_first<T, NS>(g, L.Rt, L.r + rhs * V, bufs[1 - cur] + rhs * V, rc + rhs * Vc, Dc,
+  p1_restrict_first<T, NS>(g, L.Rt, L.r + rhs * V, (cur ? bufs[0] : bufs[1]) + rhs * V, rc + rhs * Vc, Dc,
                            ec ? ec + rhs * Vc : nullptr, P.omega, t);
-  return pc_sync<T>(P, grid, st, s_ok);
+  return pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcRestrict);
 }
 
 // B_1 = A_1^-1 on the coarsest level: every participating block gathers the
@@ -1153,7 +1172,7 @@ __device__ bool pc_coarse(const PCycleParams<T>& P, int i0, int di, bool grid, P
       L.e[rhs * V + (row & 1) * ned + P.fedge[row >> 1]] = (T)s;
     }
   }
-  return pc_sync<T>(P, grid, st, s_ok);
+  return pc_sync<T>(P, grid, st, s_ok, (P.nlev - 1) * 16 + kPcCoarse);
 }
 
 // Steps 4-6 on P1 level l: prolongation from level l + 1 (fused with the
@@ -1171,21 +1190,21 @@ __device__ bool pc_up(const PCycleParams<T>& P, int l, int i0, int di, bool grid
   const T* ec = P.lv[l + 1].e;
   if (P.lc == HDGMG_LC_BOTH) {
     PC_FOR(8 * g.nC + 2 * g.nedc, g.dpro)
-    p1_prolong_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, ec + rhs * Vc, bufs[cur] + rhs * V,
-                         bufs[1 - cur] + rhs * V, t);
+    p1_prolong_lc<T, NS>(g, L.AIIinv, L.Y, L.r + rhs * V, ec + rhs * Vc, (cur ? bufs[1] : bufs[0]) + rhs * V,
+                         (cur ? bufs[0] : bufs[1]) + rhs * V, t);
     cur ^= 1;
   } else {
     PC_FOR(8 * g.nC + 2 * g.nedc, g.dpro)
-    p1_prolong<T>(g, L.Pi, ec + rhs * Vc, bufs[cur] + rhs * V, bufs[1 - cur] + rhs * V, t);
+    p1_prolong<T>(g, L.Pi, ec + rhs * Vc, (cur ? bufs[1] : bufs[0]) + rhs * V, (cur ? bufs[0] : bufs[1]) + rhs * V, t);
   }
-  if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+  if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcProlong)) return false;
   for (int it = 0; it < L.m; ++it) {
     PC_FOR(ned, g.dne)
-    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, bufs[cur] + rhs * V,
-                         bufs[1 - cur] + rhs * V, P.omega, t);
+    p1_edge<T, NS, true>(g, L.A, L.Dinv, L.r + rhs * V, (cur ? bufs[1] : bufs[0]) + rhs * V,
+                         (cur ? bufs[0] : bufs[1]) + rhs * V, P.omega, t);
     cur ^= 1;
     if (final && it + 1 == L.m) return true;
-    if (!pc_sync<T>(P, grid, st, s_ok)) return false;
+    if (!pc_sync<T>(P, grid, st, s_ok, l * 16 + kPcSweepUp)) return false;
   }
   return true;
 }
@@ -1313,7 +1332,12 @@ __device__ void pc_body(const PCycleParams<T>& P, PCycleParams<T>& sP, unsigned 
                         unsigned long long* mbar, PcSync& st, volatile int* s_ok, int* s_tail) {
   const int last = P.nlev - 1;
   const int top = P.tail < last ? P.tail : last;   // levels [0, top) run on the whole grid
-  const int gi = blockIdx.x * NTHR + threadIdx.x, gd = gridDim.x * NTHR;
+  // item j of a grid step goes to warp j / 32 mod (blocks x warps), warps
+  // numbered across the blocks first: a level with fewer items than threads
+  // spreads over every SM (its loads use all L1s) instead of filling the
+  // first blocks; lane pairs (j, j ^ 1) stay in one warp
+  const int gi = (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) << 5) + (threadIdx.x & 31);
+  const int gd = gridDim.x * NTHR;
   for (int l = 0; l < top; ++l)
     if (!pc_down<T, NS>(P, l, gi, gd, true, st, s_ok)) return;
   if (P.tail <= last) {
@@ -1321,7 +1345,7 @@ __device__ void pc_body(const PCycleParams<T>& P, PCycleParams<T>& sP, unsigned 
       *s_tail = 1;
       pc_tail<T, NS>(P, sP, smem, mbar, st, s_ok);
     }
-    if (top > 0 && !pc_grid_sync<T>(P, st, s_ok)) return;
+    if (top > 0 && !pc_sync<T>(P, true, st, s_ok, P.tail * 16 + kPcTail)) return;
   } else {
     if (!pc_coarse<T>(P, gi, gd, true, st, s_ok, reinterpret_cast<double*>(smem + P.so_w))) return;
   }
@@ -1346,7 +1370,9 @@ __global__ void __launch_bounds__(NTHR, 1) pcycle_kernel(const __grid_constant__
   }
   __syncthreads();
   if (!s_ok) return;
+  pc_stamp<T>(P, st, kPcStart);
   pc_body<T, NS, NTHR>(P, sP, pc_smem, &s_mbar, st, &s_ok, &s_tail);
+  pc_stamp<T>(P, st, kPcEnd);
   // block 0 leaves no bulk copy into its shared memory in flight: when the
   // tail was not reached (a barrier wait ran out), wait for the prefetch
   // (bounded) before returning

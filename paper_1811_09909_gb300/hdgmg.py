@@ -29,7 +29,8 @@ EXPORTED = ["hdgmg_default_opts", "hdgmg_create", "hdgmg_setup", "hdgmg_solve",
             "hdgmg_condensed_rhs", "hdgmg_last_error", "hdgmg_destroy",
             "hdgmg_apply_operator_noalloc", "hdgmg_gradient", "hdgmg_adjoint",
             "hdgmg_batch_create", "hdgmg_batch_setup", "hdgmg_batch_solve",
-            "hdgmg_batch_context", "hdgmg_batch_destroy", "hdgmg_check_cycle_timeout"]
+            "hdgmg_batch_context", "hdgmg_batch_destroy", "hdgmg_check_cycle_timeout",
+            "hdgmg_trace_vcycle"]
 
 
 class Problem(ctypes.Structure):
@@ -110,6 +111,7 @@ def load():
     lib.hdgmg_batch_destroy.restype = None
     lib.hdgmg_apply_vcycle.argtypes = [P, P, P]
     lib.hdgmg_check_cycle_timeout.argtypes = [P, I32]
+    lib.hdgmg_trace_vcycle.argtypes = [P, P, P, P, I32, P]
     lib.hdgmg_condensed_rhs.argtypes = [P, P, P, P]
     lib.hdgmg_last_error.argtypes = []
     lib.hdgmg_last_error.restype = ctypes.c_char_p
@@ -297,6 +299,17 @@ class Solver:
         e = self.torch.empty_like(r)
         _check(self.lib.hdgmg_apply_vcycle(self.ctx, _ptr(r), _ptr(e)))
         return e
+
+    def trace_vcycle(self, r, cap=512):
+        """One V-cycle as apply_vcycle, with the persistent kernel's step
+        trace: returns (e, [(time_ns, tag), ...]) (see hdgmg_trace_vcycle)."""
+        import numpy as np
+        e = self.torch.empty_like(r)
+        stamps = np.zeros(2 * cap, dtype=np.int64)
+        count = ctypes.c_int32(0)
+        _check(self.lib.hdgmg_trace_vcycle(self.ctx, _ptr(r), _ptr(e), _hptr(stamps), cap,
+                                           ctypes.byref(count)))
+        return e, [(int(stamps[2 * i]), int(stamps[2 * i + 1])) for i in range(count.value)]
 
     def condensed_rhs(self, f, gD=None):
         b = self.torch.empty((self.nd, self.n_edges), dtype=self.torch.float64, device="cuda")

@@ -158,3 +158,26 @@ def test_host_driven_pcg_equals_graph_pcg():
     lb, _, _, ib = b.solve(f, want_u=False, want_q=False)
     assert ia.iters == ib.iters and ib.converged == 1
     assert np.array_equal(host(la), host(lb))
+
+
+def test_trace_vcycle_records_every_step():
+    """hdgmg_trace_vcycle: the same correction as apply_vcycle, and one
+    (time, tag) record per barrier in step order: kernel start first, kernel
+    end last, times non-decreasing, one coarsest solve."""
+    n, p = 64, 2
+    wl = workload(n, p, 95)
+    s = make(wl, coarsest_n=4, m_fine=1, m_max=2, precision=hdgmg.PREC_FP32, pcycle=1,
+             local_corr=hdgmg.LC_BOTH)
+    r = cuda(np.random.default_rng(14).standard_normal((p + 1, hdg.n_edges(n))))
+    e0 = host(s.apply_vcycle(r))
+    e1, rec = s.trace_vcycle(r)
+    assert np.array_equal(e0, host(e1))
+    tags = [t for _, t in rec]
+    times = [t for t, _ in rec]
+    assert tags[0] == 0 and tags[-1] == 11 and len(rec) > 4
+    assert all(b >= a for a, b in zip(times, times[1:]))
+    assert sum(1 for t in tags if t % 16 == 7) == 1
+    # a context without the persistent cycle rejects the call
+    t = make(wl, coarsest_n=4, pcycle=0)
+    with pytest.raises(hdgmg.HdgmgError):
+        t.trace_vcycle(r)
