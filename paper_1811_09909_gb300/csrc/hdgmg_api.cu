@@ -132,7 +132,9 @@ struct hdgmg_ctx {
   CTailParams<float> cp32;
   CTailParams<double> cp64;
   // persistent P1 cycle: the levels from pc_start down run as one cooperative
-  // launch of pc_blocks blocks; pc_bar is its grid barrier's arrival count,
+  // launch of pc_blocks blocks; pc_bar[0] is its grid barrier's arrival count
+  // (pc_bar[1] that of the blocked form, which launches pc_blocks_b blocks:
+  // each count stays a multiple of its own grid size between launches),
   // err[2] its expired-wait flag
   int pc_start = -1;
   int pc_blocks = 0;
@@ -527,6 +529,7 @@ void plan_pcycle(hdgmg_ctx* c) {
     B = P;
     B.tail = B.nlev;
     B.staged = 0;
+    B.bar = c->pc_bar + 1;   // its own count: the two launch different grid sizes
     B.so_w = 0;
     B.smem_bytes = (int)(sizeof(double) * (size_t)c->kb * (c->nf > 0 ? c->nf : 1));
     const int maxbb = pcycle_max_blocks<T>(B.smem_bytes);
@@ -543,7 +546,7 @@ void plan_pcycle(hdgmg_ctx* c) {
 hdgmg_status cycle_wait_status(hdgmg_ctx* c) {
   if (c->pc_start < 0 || c->err_h[2] == 0) return HDGMG_OK;
   c->err_h[2] = 0;
-  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned long long), c->stream));
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 2 * sizeof(unsigned long long), c->stream));
   CUDA_TRY(cudaMemsetAsync(c->err + 2, 0, sizeof(int), c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return fail(HDGMG_ETIMEOUT, "a grid-barrier wait of the persistent V-cycle ran out");
@@ -1831,8 +1834,8 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
     c->tail_start = -1;                      // the fused tails implement block-Jacobi only, and
     c->ctail_start = -1;                     // one right-hand side at a time
   }
-  CTRY(c->alloc(&c->pc_bar, 1));
-  CTRY(cudaMemset(c->pc_bar, 0, sizeof(unsigned long long)));
+  CTRY(c->alloc(&c->pc_bar, 2));
+  CTRY(cudaMemset(c->pc_bar, 0, 2 * sizeof(unsigned long long)));
   if (fp32)
     plan_pcycle<float>(c);
   else
@@ -1919,7 +1922,7 @@ hdgmg_status hdgmg_setup(hdgmg_ctx* c, const double* log_kappa) {
   CUDA_TRY(cudaEventRecord(c->ev0, s));
   CUDA_TRY(cudaMemcpyAsync(c->logk, log_kappa, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
   CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
-  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned long long), s));
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 2 * sizeof(unsigned long long), s));
   Level& L0 = c->levels[0];
   if (c->ns) {
     STATUS_TRY(prepare_pencil(c, log_kappa));

@@ -132,3 +132,25 @@ def test_blocked_batch_problem_equals_alone():
         s.setup(logks[i])
         lam, _, _, _ = s.solve(fs[i], want_u=False, want_q=False)
         assert np.array_equal(host(lams[i]), host(lam)), i
+
+
+def test_single_solve_after_blocked_solve_is_unchanged():
+    """The blocked and the single-right-hand-side persistent cycles launch
+    different grid sizes; each keeps its own barrier count, so a single solve
+    after a blocked one in the same context repeats its earlier result bit for
+    bit."""
+    n, p = 64, 2
+    wl = W.lognormal(n, p, seed=23)
+    F = forcing(n, p, 4, 24)
+    s = hdgmg.Solver(n, p, coarsest_n=4, m_fine=1, m_max=2, rtol=1e-10, precision=hdgmg.PREC_FP32,
+                     pcycle=1, rhs_block=4, tau_mode=hdgmg.TAU_OVER_H)
+    s.setup(cuda(wl.log_kappa))
+    f0 = cuda(F[0])
+    la, _, _, ia = s.solve(f0, want_u=False, want_q=False)
+    la = host(la).copy()
+    for _ in range(3):
+        _, _, _, ib = s.solve(cuda(F[:3]), want_u=False, want_q=False)
+        assert ib.converged == 1
+        lc, _, _, ic = s.solve(f0, want_u=False, want_q=False)
+        assert ic.iters == ia.iters
+        assert np.array_equal(host(lc), la)
