@@ -214,6 +214,14 @@ typedef struct {
                              otherwise); info then describes the last block
                              (iters: inner iterations, rel_res: the worst
                              right-hand side).  0 or 1: one at a time.  0    */
+  int32_t pcg_fuse;       /* 1: each FP64 PCG iteration (krylov = CG, one
+                             right-hand side) forms the direction update, the
+                             FP64 matvec and p.Ap in one kernel and x, r, p in
+                             one more (the matvec gathers p + beta z where the
+                             elements read it; p.Ap summed element by element,
+                             sum_e p_e^T A_e p_e); 0: separate direction,
+                             matvec, dot and update kernels.  Same iteration,
+                             different summation order.  1                   */
 } hdgmg_opts;
 
 typedef struct {

@@ -39,7 +39,8 @@ def _compile(unit, extra):
         if real == "bf16":
             extra = ["-DHDGMG_BF16", "-DHDGMG_REAL=float", f"-DHDGMG_ND={nd}", *extra]
         else:
-            extra = [f"-DHDGMG_REAL={real}", f"-DHDGMG_ND={nd}", *extra]
+            extra = [f"-DHDGMG_REAL={real}", f"-DHDGMG_ND={nd}",
+                     f"-DHDGMG_REAL_IS_DOUBLE={int(real == 'double')}", *extra]
     else:
         src = unit
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

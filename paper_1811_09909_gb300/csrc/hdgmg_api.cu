@@ -938,6 +938,34 @@ void cg_body64(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
                                 mixed ? L0.d32.r : nullptr);
 }
 
+// The same iteration in three launches after the V-cycle (opts.pcg_fuse,
+// symmetric operator): r.z and beta; then p+ = z + beta p, Ap = A p+ and
+// alpha = (r.z)/(p+.Ap) in the matvec kernel (p+ formed where the elements
+// gather it); then x, r, p and the test.  Ap is zero on entry (zeroed before
+// the loop and by every update).
+void cg_body64_fused(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
+  cudaStream_t s = c->stream;
+  const int64_t len = c->fine_len();
+  Level& L0 = c->levels[0];
+  const bool mixed = c->opts.precision != HDGMG_PREC_FP64;
+  const float* z32 = mixed ? L0.d32.e : nullptr;
+  const double* z64 = mixed ? nullptr : c->z;
+  if (mixed) {
+    vcycle<float>(c, 0);
+    launch_dot_fused_mixed(s, len, c->r, z32, c->partial, c->counter, c->scal, 1);
+  } else {
+    apply_B(c, c->r, c->z);
+    launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);
+  }
+  launch_cg_matvec(s, c->n, c->p + 1, L0.d64.A, z32, z64, c->pv, c->Ap, c->scal, c->partial,
+                   c->counter);
+  launch_cg_update_dir_test(s, len, c->scal, c->x, c->r, c->pv, c->Ap, z32, z64, c->partial,
+                            c->counter, h, c->it_dev, c->opts.max_it, c->opts.rtol * c->opts.rtol,
+                            mixed ? L0.d32.r : nullptr);
+}
+
+bool pcg_fused(const hdgmg_ctx* c) { return c->opts.pcg_fuse && !c->ns; }
+
 void cg_body32(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   cudaStream_t s = c->stream;
   const int64_t len = c->fine_len();
@@ -1372,8 +1400,9 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
     c->init_h[1] = bb;
     CUDA_TRY(cudaMemcpyAsync(c->scal + 0, &c->init_h[0], sizeof(double), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->scal + 6, &c->init_h[1], sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(c->Ap, 0, sizeof(double) * len, s));
     for (;;) {
-      cg_body64(c, 0);
+      pcg_fused(c) ? cg_body64_fused(c, 0) : cg_body64(c, 0);
       STATUS_TRY(check_launch("PCG iteration"));
       CUDA_TRY(cudaMemcpyAsync(c->it_h, c->it_dev, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
       CUDA_TRY(cudaStreamSynchronize(s));
@@ -1389,11 +1418,13 @@ hdgmg_status solve_one(hdgmg_ctx* c, const double* f, const double* gD, double* 
   } else if (o.krylov == HDGMG_KRYLOV_CG) {
     // preconditioned CG with the V-cycle B_N (Sec. 3.6; symmetric cycle), the
     // whole iteration loop replayed as one CUDA graph
-    STATUS_TRY(build_loop_graph(c, cg_body64, &c->cg_graph, &c->cg_exec, &c->cg_body_launches));
+    STATUS_TRY(build_loop_graph(c, pcg_fused(c) ? cg_body64_fused : cg_body64, &c->cg_graph,
+                                &c->cg_exec, &c->cg_body_launches));
     CUDA_TRY(cudaMemcpyAsync(c->r, c->b, sizeof(double) * len, cudaMemcpyDeviceToDevice, s));
     if (o.precision != HDGMG_PREC_FP64)
       launch_convert<double, float>(s, len, c->r, c->levels[0].d32.r);
     CUDA_TRY(cudaMemsetAsync(c->pv, 0, sizeof(double) * len, s));
+    CUDA_TRY(cudaMemsetAsync(c->Ap, 0, sizeof(double) * len, s));
     CUDA_TRY(cudaMemsetAsync(c->it_dev, 0, sizeof(int), s));
     c->init_h[0] = 1.0;      // rz of the previous iteration (p = 0 makes beta irrelevant)
     c->init_h[1] = bb;
@@ -1526,6 +1557,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->pcycle_tail_n = 16;
   o->pcg_graph = 1;
   o->rhs_block = 0;
+  o->pcg_fuse = 1;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1599,6 +1631,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.l2_persist_mb < 0) return fail(HDGMG_EINVAL, "l2_persist_mb must be >= 0");
   if (o.rhs_block < 0 || o.rhs_block > kMaxRhsBlock)
     return fail(HDGMG_EINVAL, "rhs_block must be in 0..16");
+  if (o.pcg_fuse < 0 || o.pcg_fuse > 1) return fail(HDGMG_EINVAL, "pcg_fuse must be 0 or 1");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)

@@ -234,6 +234,22 @@ void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alp
                       int k);
 template <typename T, int ND, bool NS>
 void launch_bj_blocks_nd(cudaStream_t s, int n, const T* A, T* Dinv, int* err);
+// the PCG iteration's direction update, FP64 matvec and p.Ap in one launch
+// (symmetric storage; z32 or z64 is the preconditioned residual, the other
+// null); partial holds kDotBlocks doubles
+void launch_cg_matvec(cudaStream_t s, int n, int nd, const double* A, const float* z32,
+                      const double* z64, const double* p, double* Ap, double* scal,
+                      double* partial, unsigned* counter);
+template <int ND>
+void launch_cg_matvec_nd(cudaStream_t s, int n, const double* A, const float* z32,
+                         const double* z64, const double* p, double* Ap, double* scal,
+                         double* partial, unsigned* counter);
+// x += alpha p+, r -= alpha Ap, Ap = 0, p = p+ (= fma(beta, p, z)), r.r and
+// the loop test of cg_update_test (r32: FP32 copy of r, nullable)
+void launch_cg_update_dir_test(cudaStream_t s, int64_t len, double* scal, double* x, double* r,
+                               double* p, double* Ap, const float* z32, const double* z64,
+                               double* partial, unsigned* counter, cudaGraphConditionalHandle h,
+                               int* it, int max_it, double tol2, float* r32);
 template <typename T, int ND, bool NS>
 void launch_bj_update_nd(cudaStream_t s, int n, const T* Dinv, const T* r, T* y, T* e, T omega,
                          int first, const T* xadd, int k);

@@ -31,6 +31,52 @@ static __host__ __device__ __forceinline__ int pk(int r, int c) {   // packed in
 
 static __device__ __forceinline__ int pk_any(int r, int c) { return r >= c ? pk(r, c) : pk(c, r); }
 
+// ------------------------------------ deterministic block reductions
+// block reduction by warp shuffles then one warp over the warp sums (a fixed
+// order for a fixed block size); sh holds at least blockDim / 32 doubles
+static __device__ __forceinline__ double block_sum(double v, double* sh) {
+  __syncthreads();                         // sh may still be read by an earlier call
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (l == 0) sh[32] = v;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// returns true in the last block to finish, after all partials are visible;
+// thread 0 published this block's partial before calling
+static __device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    __threadfence();                       // release the partial
+    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    if (is_last) __threadfence();          // acquire every other block's partial
+  }
+  __syncthreads();
+  return is_last;
+}
+
+// sum of n partials in a fixed order: thread t adds partial[t], partial[t + B],
+// ... (loads issued together), then block_sum
+static __device__ __forceinline__ double sum_partials(const double* partial, int n, double* sh) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int B = blockDim.x;
+  int i = threadIdx.x, k = 0;
+  for (; i < n && k < 4; i += B, ++k) v[k] = __ldcg(partial + i);
+  double s = ((v[0] + v[1]) + v[2]) + v[3];
+  for (; i < n; i += B) s += __ldcg(partial + i);
+  return block_sum(s, sh);
+}
+
+
 
 // ---------------------------------------------- 2x2 agglomeration geometry
 // Interior edges of macro-element C = (I, J) (fine mesh n = 2 nc):

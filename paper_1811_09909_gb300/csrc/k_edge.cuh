@@ -1,8 +1,9 @@
 // Edge/element kernels templated on the number of trace modes per edge ND
 // and on the storage of the element operators (NS = false: symmetric, packed
 // lower triangle; NS = true: non-symmetric, full row-major):
-//   K6  trace matvec y += alpha A x, one thread per element, A_e in
-//       structure-of-arrays layout, results added into the two edge owners
+//   K6  trace matvec y += alpha A x, A_e in structure-of-arrays layout, one
+//       thread per (element, row block) for symmetric storage and per
+//       element for full storage; results added into the two edge owners
 //       with atomics (exactly two contributions per entry, so the sum does
 //       not depend on their order)
 //   K2  edge block-Jacobi blocks D = A_e0[edge] + A_e1[edge] and D^-1
@@ -89,6 +90,153 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict
       for (int k = 0; k < ND; ++k)
         atomicAdd(&y[(size_t)k * nedge + ed[le]], alpha * yl[le * ND + k]);
     }
+  }
+}
+
+// K6 for symmetric (packed) storage, one thread per (element, row block):
+// a block of four warps covers 32 consecutive elements; warp w forms the ND
+// rows of local edge w (rows w ND ... w ND + ND - 1) over all 4 ND columns,
+// in column order, and lane l works on element 32 blockIdx.x + l.  Every
+// warp load is one contiguous 32-element run of an entry row, and a block
+// has four times the warps of the one-thread-per-element form in flight; an
+// off-diagonal entry is read by the two warps whose rows it couples (the
+// second read is served by L1 or L2).  Same arguments as matvec_kernel.
+template <typename T, int ND, typename TA, int LE>
+__device__ __forceinline__ void matvec_rows(const TA* __restrict__ Ae, int nE, const T* xl,
+                                            T* yE, int nedge, T alpha) {
+  constexpr int NL = 4 * ND;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < NL; ++c) s += load_entry(Ae + (size_t)pk_any(LE * ND + k, c) * nE) * xl[c];
+    atomicAdd(yE + (size_t)k * nedge, alpha * s);
+  }
+}
+
+template <typename T, int ND, typename TA = T, bool MULTI = false>
+__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) matvec_rb_kernel(int n, const TA* __restrict__ A,
+                                                           const T* __restrict__ x,
+                                                           T* __restrict__ y, T alpha,
+                                                           const T* __restrict__ xadd) {
+  constexpr int NL = 4 * ND;
+  const int nE = n * n;
+  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int le = threadIdx.x >> 5;
+  if (e >= nE) return;
+  const int nedge = 2 * n * (n + 1);
+  if (MULTI) {
+    x += (size_t)blockIdx.y * ND * nedge;
+    y += (size_t)blockIdx.y * ND * nedge;
+    if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
+  }
+  int ed[4];
+  elem_edges(n, e, ed);
+  const int E = le == 0 ? ed[0] : le == 1 ? ed[1] : le == 2 ? ed[2] : ed[3];
+  if (bnd_edge(n, E)) return;
+  T xl[NL];
+#pragma unroll
+  for (int c = 0; c < NL; ++c) {
+    const size_t ix = (size_t)(c % ND) * nedge + ed[c / ND];
+    xl[c] = x[ix];
+    if (xadd && c % ND < 2) xl[c] += xadd[ix];
+  }
+  const TA* Ae = A + e;
+  T* yE = y + E;
+  switch (le) {   // warp-uniform
+    case 0: matvec_rows<T, ND, TA, 0>(Ae, nE, xl, yE, nedge, alpha); break;
+    case 1: matvec_rows<T, ND, TA, 1>(Ae, nE, xl, yE, nedge, alpha); break;
+    case 2: matvec_rows<T, ND, TA, 2>(Ae, nE, xl, yE, nedge, alpha); break;
+    default: matvec_rows<T, ND, TA, 3>(Ae, nE, xl, yE, nedge, alpha); break;
+  }
+}
+
+// rows LE ND ... LE ND + ND - 1 of A_e times xl added into y (as
+// matvec_rows, FP64), returning their part of xl^T A_e xl
+template <int ND, int LE>
+__device__ __forceinline__ double matvec_rows_q(const double* __restrict__ Ae, int nE,
+                                                const double* xl, double* yE, int nedge) {
+  constexpr int NL = 4 * ND;
+  double q = 0.0;
+#pragma unroll
+  for (int k = 0; k < ND; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < NL; ++c) s += Ae[(size_t)pk_any(LE * ND + k, c) * nE] * xl[c];
+    atomicAdd(yE + (size_t)k * nedge, s);
+    q = fma(xl[LE * ND + k], s, q);
+  }
+  return q;
+}
+
+// K6 fused into the PCG iteration (FP64 operator in symmetric storage, one
+// right-hand side): the new search direction p+ = z + beta p (beta =
+// scal[4], z the preconditioned residual in TZ), Ap += A p+ (Ap zeroed by the
+// previous update), and the quadratic form p+ . A p+ = sum_e p+_e^T A_e p+_e
+// summed element by element (each thread over its rows and element groups,
+// then block_sum, then the last block over the block partials in block
+// order) into scal[1], with alpha = scal[0] / scal[1] in scal[2].  Thread
+// layout of matvec_rb_kernel over groups of 32 elements, a fixed grid
+// striding over the groups: warp w forms p+ on local edge w of the group's
+// elements (one fma per value, the same as cg_update_dir_test_kernel's) into
+// shared memory, then every warp reads the element's 4 ND values from there.
+// Rows of Dirichlet edges are skipped, where p+ is zero.
+template <int ND, typename TZ>
+__global__ void __launch_bounds__(128, 4) cg_matvec_kernel(int n, const double* __restrict__ A,
+                                                           const TZ* __restrict__ z,
+                                                           const double* __restrict__ p,
+                                                           double* __restrict__ Ap,
+                                                           double* __restrict__ scal,
+                                                           double* __restrict__ partial,
+                                                           unsigned* __restrict__ counter) {
+  constexpr int NL = 4 * ND;
+  __shared__ double sh[33];
+  __shared__ double xs[NL][32];
+  const int nE = n * n;
+  const int lane = threadIdx.x & 31, le = threadIdx.x >> 5;
+  const int nedge = 2 * n * (n + 1);
+  const int ngroups = (nE + 31) >> 5;
+  const double beta = scal[4];
+  double q = 0.0;
+  for (int gi = blockIdx.x; gi < ngroups; gi += gridDim.x) {
+    const int e = gi * 32 + lane;
+    int ed[4] = {0, 0, 0, 0};
+    if (e < nE) {
+      elem_edges(n, e, ed);
+      const int E = le == 0 ? ed[0] : le == 1 ? ed[1] : le == 2 ? ed[2] : ed[3];
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        const size_t ix = (size_t)k * nedge + E;
+        xs[le * ND + k][lane] = fma(beta, p[ix], (double)z[ix]);
+      }
+    }
+    __syncthreads();
+    if (e < nE) {
+      const int E = le == 0 ? ed[0] : le == 1 ? ed[1] : le == 2 ? ed[2] : ed[3];
+      if (!bnd_edge(n, E)) {
+        double xl[NL];
+#pragma unroll
+        for (int c = 0; c < NL; ++c) xl[c] = xs[c][lane];
+        const double* Ae = A + e;
+        double* yE = Ap + E;
+        switch (le) {   // warp-uniform
+          case 0: q += matvec_rows_q<ND, 0>(Ae, nE, xl, yE, nedge); break;
+          case 1: q += matvec_rows_q<ND, 1>(Ae, nE, xl, yE, nedge); break;
+          case 2: q += matvec_rows_q<ND, 2>(Ae, nE, xl, yE, nedge); break;
+          default: q += matvec_rows_q<ND, 3>(Ae, nE, xl, yE, nedge); break;
+        }
+      }
+    }
+    __syncthreads();   // xs is rewritten by the next group
+  }
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = q;
+  if (!last_block(counter)) return;
+  const double pap = sum_partials(partial, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    scal[1] = pap;
+    scal[2] = scal[0] / pap;
+    *counter = 0u;
   }
 }
 
@@ -274,6 +422,14 @@ template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha,
                       const T* xadd, int k) {
   note_launch();
+  if (!NS) {
+    if (k > 1)
+      matvec_rb_kernel<T, ND, T, true><<<dim3(nblk(n * n, 32), k), 128, 0, s>>>(n, A, x, y, alpha,
+                                                                              xadd);
+    else
+      matvec_rb_kernel<T, ND><<<nblk(n * n, 32), 128, 0, s>>>(n, A, x, y, alpha, xadd);
+    return;
+  }
   if (k > 1)
     matvec_kernel<T, ND, NS, T, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(n, A, x, y, alpha,
                                                                                  xadd);
@@ -285,12 +441,35 @@ template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
                            float alpha, const float* xadd, int k) {
   note_launch();
+  if (!NS) {
+    if (k > 1)
+      matvec_rb_kernel<float, ND, __nv_bfloat16, true><<<dim3(nblk(n * n, 32), k), 128, 0, s>>>(
+          n, A, x, y, alpha, xadd);
+    else
+      matvec_rb_kernel<float, ND, __nv_bfloat16><<<nblk(n * n, 32), 128, 0, s>>>(n, A, x, y, alpha,
+                                                                                 xadd);
+    return;
+  }
   if (k > 1)
     matvec_kernel<float, ND, NS, __nv_bfloat16, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(
         n, A, x, y, alpha, xadd);
   else
     matvec_kernel<float, ND, NS, __nv_bfloat16><<<nblk(n * n, 128), 128, 0, s>>>(n, A, x, y, alpha,
                                                                                 xadd);
+}
+
+// grid: at most kDotBlocks blocks striding over the groups of 32 elements
+// (fixed for a given mesh, so the reduction order is too)
+template <int ND>
+void launch_cg_matvec_nd(cudaStream_t s, int n, const double* A, const float* z32,
+                         const double* z64, const double* p, double* Ap, double* scal,
+                         double* partial, unsigned* counter) {
+  note_launch();
+  const int g = nblk(n * n, 32), blocks = g < kDotBlocks ? g : kDotBlocks;
+  if (z32)
+    cg_matvec_kernel<ND, float><<<blocks, 128, 0, s>>>(n, A, z32, p, Ap, scal, partial, counter);
+  else
+    cg_matvec_kernel<ND, double><<<blocks, 128, 0, s>>>(n, A, z64, p, Ap, scal, partial, counter);
 }
 
 template <typename T, int ND, bool NS>

@@ -10,6 +10,9 @@
 #ifndef HDGMG_ND
 #define HDGMG_ND 2
 #endif
+#ifndef HDGMG_REAL_IS_DOUBLE
+#define HDGMG_REAL_IS_DOUBLE 0
+#endif
 
 namespace hdgmg {
 #ifndef HDGMG_BF16
@@ -26,6 +29,11 @@ namespace hdgmg {
 HDGMG_INST(false)
 HDGMG_INST(true)
 #undef HDGMG_INST
+#if HDGMG_REAL_IS_DOUBLE
+template void launch_cg_matvec_nd<HDGMG_ND>(cudaStream_t, int, const double*, const float*,
+                                            const double*, const double*, double*, double*,
+                                            double*, unsigned*);
+#endif
 #else
 template void launch_matvec_bf16_nd<HDGMG_ND, false>(cudaStream_t, int, const __nv_bfloat16*,
                                                      const float*, float*, float, const float*, int);

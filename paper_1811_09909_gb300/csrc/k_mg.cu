@@ -1574,50 +1574,6 @@ __global__ void convert_kernel(int64_t len, const A* __restrict__ in, B* __restr
 //   mode 0: scal[1] = p.Ap,     scal[2] = alpha = scal[0] / scal[1]
 //   mode 1: scal[3] = r.z,      scal[4] = beta = scal[3] / scal[0], scal[0] = scal[3]
 //   mode 2: scal[5] = r.r
-// block reduction by warp shuffles then one warp over the warp sums (a fixed
-// order for a fixed block size); sh holds at least blockDim / 32 doubles
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  __syncthreads();                         // sh may still be read by an earlier call
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (l == 0) sh[32] = v;
-  }
-  __syncthreads();
-  return sh[32];
-}
-
-// returns true in the last block to finish, after all partials are visible;
-// thread 0 published this block's partial before calling
-__device__ __forceinline__ bool last_block(unsigned* counter) {
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) {
-    __threadfence();                       // release the partial
-    is_last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    if (is_last) __threadfence();          // acquire every other block's partial
-  }
-  __syncthreads();
-  return is_last;
-}
-
-// sum of n partials in a fixed order: thread t adds partial[t], partial[t + B],
-// ... (loads issued together), then block_sum
-__device__ __forceinline__ double sum_partials(const double* partial, int n, double* sh) {
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  const int B = blockDim.x;
-  int i = threadIdx.x, k = 0;
-  for (; i < n && k < 4; i += B, ++k) v[k] = __ldcg(partial + i);
-  double s = ((v[0] + v[1]) + v[2]) + v[3];
-  for (; i < n; i += B) s += __ldcg(partial + i);
-  return block_sum(s, sh);
-}
-
 template <typename T, typename TB = T>
 __global__ void __launch_bounds__(256) dot_fused_kernel(int64_t len, const T* __restrict__ a,
                                                         const TB* __restrict__ b,
@@ -1798,6 +1754,71 @@ __global__ void __launch_bounds__(256) cg_update_test_kernel(
   }
 }
 
+// The update that closes the fused PCG iteration (after cg_matvec_kernel):
+// p+ = fma(beta, p, z) -- the direction cg_matvec_kernel applied A to --,
+// x += alpha p+, r -= alpha Ap, p = p+, Ap = 0 for the next matvec, the FP32
+// copy of r (r32, nullable) and r.r with the loop test of
+// cg_update_test_kernel.
+template <typename TZ>
+__global__ void __launch_bounds__(256) cg_update_dir_test_kernel(
+    int64_t len, double* __restrict__ scal, double* __restrict__ x, double* __restrict__ r,
+    double* __restrict__ p, double* __restrict__ Ap, const TZ* __restrict__ z,
+    double* __restrict__ partial, unsigned* __restrict__ counter, cudaGraphConditionalHandle h,
+    int* __restrict__ it, int max_it, double tol2, float* __restrict__ r32) {
+  __shared__ double sh[33];
+  const double alpha = scal[2], beta = scal[4];
+  double s = 0.0;
+  const int64_t G = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + G < len; i += 2 * G) {          // two values per pass, loads first
+    const double z0 = (double)z[i], z1 = (double)z[i + G], p0 = p[i], p1 = p[i + G];
+    const double q0 = Ap[i], q1 = Ap[i + G], x0 = x[i], x1 = x[i + G];
+    const double s0 = r[i], s1 = r[i + G];
+    const double d0 = fma(beta, p0, z0), d1 = fma(beta, p1, z1);
+    p[i] = d0;
+    p[i + G] = d1;
+    Ap[i] = 0.0;
+    Ap[i + G] = 0.0;
+    x[i] = x0 + alpha * d0;
+    x[i + G] = x1 + alpha * d1;
+    const double r0 = s0 - alpha * q0, r1 = s1 - alpha * q1;
+    r[i] = r0;
+    r[i + G] = r1;
+    if (r32) {
+      r32[i] = (float)r0;
+      r32[i + G] = (float)r1;
+    }
+    s += r0 * r0;
+    s += r1 * r1;
+  }
+  for (; i < len; i += G) {
+    const double d = fma(beta, p[i], (double)z[i]);
+    p[i] = d;
+    x[i] += alpha * d;
+    const double ri = r[i] - alpha * Ap[i];
+    Ap[i] = 0.0;
+    r[i] = ri;
+    if (r32) r32[i] = (float)ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (!last_block(counter)) return;
+  __syncthreads();
+  const double rr = sum_partials(partial, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    scal[5] = rr;
+    *counter = 0u;
+    const int k = ++(*it);
+    if (!(rr > tol2 * scal[6]) || k >= max_it) {
+      if (h)
+        cudaGraphSetConditional(h, 0);
+      else
+        it[1] = 1;
+    }
+  }
+}
+
 // scal layout: 0 rz, 1 pAp, 2 alpha, 3 rz_new, 4 beta, 5 rr
 template <typename T>
 __global__ void cg_update_kernel(int64_t len, const double* __restrict__ scal, T* __restrict__ x,
@@ -1908,6 +1929,14 @@ void launch_matvec(cudaStream_t s, int n, int nd, bool ns, const T* A, const T* 
   else launch_matvec_nd<T, ND, false>(s, n, A, x, y, alpha, xadd, k)
   ND_DISPATCH(nd, MV)
 #undef MV
+}
+
+void launch_cg_matvec(cudaStream_t s, int n, int nd, const double* A, const float* z32,
+                      const double* z64, const double* p, double* Ap, double* scal,
+                      double* partial, unsigned* counter) {
+#define CGM(ND) launch_cg_matvec_nd<ND>(s, n, A, z32, z64, p, Ap, scal, partial, counter)
+  ND_DISPATCH(nd, CGM)
+#undef CGM
 }
 
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
@@ -2309,6 +2338,19 @@ void launch_cg_update_test(cudaStream_t s, int64_t len, double* scal, T* x, T* r
   note_launch();
   cg_update_test_kernel<T><<<kDotBlocks, 256, 0, s>>>(len, scal, x, r, p, Ap, partial, counter, h,
                                                       it, max_it, tol2, r32);
+}
+
+void launch_cg_update_dir_test(cudaStream_t s, int64_t len, double* scal, double* x, double* r,
+                               double* p, double* Ap, const float* z32, const double* z64,
+                               double* partial, unsigned* counter, cudaGraphConditionalHandle h,
+                               int* it, int max_it, double tol2, float* r32) {
+  note_launch();
+  if (z32)
+    cg_update_dir_test_kernel<float><<<kDotBlocks, 256, 0, s>>>(len, scal, x, r, p, Ap, z32, partial,
+                                                                counter, h, it, max_it, tol2, r32);
+  else
+    cg_update_dir_test_kernel<double><<<kDotBlocks, 256, 0, s>>>(len, scal, x, r, p, Ap, z64, partial,
+                                                                 counter, h, it, max_it, tol2, r32);
 }
 
 void launch_dot_fused_mixed(cudaStream_t s, int64_t len, const double* a, const float* b,
