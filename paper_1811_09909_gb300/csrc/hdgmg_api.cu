@@ -146,6 +146,9 @@ struct hdgmg_ctx {
   unsigned long long* pc_trace = nullptr;
   int pc_trace_cap = 0;
   bool pc_trace_armed = false;
+  // fused PCG body: the finest level's last post-smoothing step also forms the
+  // PCG's r.z (rz_fuse set while the body is recorded; rz_done: it was)
+  bool rz_fuse = false, rz_done = false;
   // blocked solves of up to kb right-hand sides (opts.rhs_block): FP32 level
   // vectors hold kb copies [kb][...]; kr is the count the V-cycle launches
   // run with (1 outside a blocked solve)
@@ -739,6 +742,15 @@ void vcycle(hdgmg_ctx* c, int l, const T* rp_r0 = nullptr, T* rp_y0 = nullptr, i
   }
   for (int i = 0; i < L.m; ++i) {
     level_matvec<T>(c, l, D.e, D.y, i == 0 ? xadd : nullptr);
+    if constexpr (std::is_same<T, float>::value) {
+      // the PCG's r.z joins the last step of the finest level (cg_body64_fused)
+      if (l == 0 && i + 1 == L.m && c->rz_fuse && k == 1 && !ns) {
+        launch_bj_update_dot(s, L.n, L.nd, D.Dinv, D.r, D.y, D.e, omega, i == 0 ? xadd : nullptr,
+                             c->r, c->scal, c->partial, c->counter);
+        c->rz_done = true;
+        continue;
+      }
+    }
     launch_bj_update<T>(s, L.n, L.nd, ns, D.Dinv, D.r, D.y, D.e, omega, 0, i == 0 ? xadd : nullptr,
                         k);
   }
@@ -951,8 +963,11 @@ void cg_body64_fused(hdgmg_ctx* c, cudaGraphConditionalHandle h) {
   const float* z32 = mixed ? L0.d32.e : nullptr;
   const double* z64 = mixed ? nullptr : c->z;
   if (mixed) {
+    c->rz_fuse = true;
+    c->rz_done = false;
     vcycle<float>(c, 0);
-    launch_dot_fused_mixed(s, len, c->r, z32, c->partial, c->counter, c->scal, 1);
+    c->rz_fuse = false;
+    if (!c->rz_done) launch_dot_fused_mixed(s, len, c->r, z32, c->partial, c->counter, c->scal, 1);
   } else {
     apply_B(c, c->r, c->z);
     launch_dot_fused<double>(s, len, c->r, c->z, c->partial, c->counter, c->scal, 1);

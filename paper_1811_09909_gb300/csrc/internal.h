@@ -244,6 +244,16 @@ template <int ND>
 void launch_cg_matvec_nd(cudaStream_t s, int n, const double* A, const float* z32,
                          const double* z64, const double* p, double* Ap, double* scal,
                          double* partial, unsigned* counter);
+// the finest FP32 level's last post-smoothing step with r64 . z (z the new
+// e) and the beta recurrence of the FP64 PCG (symmetric storage, one
+// right-hand side); partial holds kDotBlocks doubles
+void launch_bj_update_dot(cudaStream_t s, int n, int nd, const float* Dinv, const float* r,
+                          float* y, float* e, float omega, const float* xadd, const double* r64,
+                          double* scal, double* partial, unsigned* counter);
+template <int ND>
+void launch_bj_update_dot_nd(cudaStream_t s, int n, const float* Dinv, const float* r, float* y,
+                             float* e, float omega, const float* xadd, const double* r64,
+                             double* scal, double* partial, unsigned* counter);
 // x += alpha p+, r -= alpha Ap, Ap = 0, p = p+ (= fma(beta, p, z)), r.r and
 // the loop test of cg_update_test (r32: FP32 copy of r, nullable)
 void launch_cg_update_dir_test(cudaStream_t s, int64_t len, double* scal, double* x, double* r,

@@ -416,6 +416,72 @@ __global__ void bj_update_kernel(int n, const T* __restrict__ Dinv, const T* __r
 }
 
 
+// The last post-smoothing step of the finest FP32 level when it closes the
+// preconditioner of the FP64 PCG (symmetric storage, one right-hand side):
+// the update of bj_update_kernel (first = 0) and r.z with z the new e and r
+// the FP64 residual r64, over the interior edges (r is zero on Dirichlet
+// edges), summed per thread over its edges, then block_sum, then the last
+// block over the block partials in block order: scal[3] = r.z, scal[4] =
+// beta = scal[3] / scal[0], scal[0] = scal[3].  A fixed grid strides over the
+// edges (a fixed reduction order for a given mesh).
+template <int ND>
+__global__ void __launch_bounds__(256) bj_update_dot_kernel(
+    int n, const float* __restrict__ Dinv, const float* __restrict__ r, float* __restrict__ y,
+    float* __restrict__ e, float omega, const float* __restrict__ xadd,
+    const double* __restrict__ r64, double* __restrict__ scal, double* __restrict__ partial,
+    unsigned* __restrict__ counter) {
+  __shared__ double sh[33];
+  const int nedge = 2 * n * (n + 1);
+  double q = 0.0;
+  for (int edge = blockIdx.x * blockDim.x + threadIdx.x; edge < nedge;
+       edge += gridDim.x * blockDim.x) {
+    if (bnd_edge(n, edge)) continue;
+    float d[ND], eo[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      const size_t ix = (size_t)k * nedge + edge;
+      d[k] = r[ix] - y[ix];
+      eo[k] = e[ix];
+    }
+    if (xadd) {
+      eo[0] += xadd[edge];
+      eo[1] += xadd[(size_t)nedge + edge];
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) y[(size_t)k * nedge + edge] = 0.f;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+      float sa = 0.f;
+#pragma unroll
+      for (int b = 0; b < ND; ++b) sa += Dinv[(size_t)pk_any(a, b) * nedge + edge] * d[b];
+      const size_t ix = (size_t)a * nedge + edge;
+      const float ea = eo[a] + omega * sa;
+      e[ix] = ea;
+      q += r64[ix] * (double)ea;
+    }
+  }
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = q;
+  if (!last_block(counter)) return;
+  const double rz = sum_partials(partial, gridDim.x, sh);
+  if (threadIdx.x == 0) {
+    scal[3] = rz;
+    scal[4] = rz / scal[0];
+    scal[0] = rz;
+    *counter = 0u;
+  }
+}
+
+template <int ND>
+void launch_bj_update_dot_nd(cudaStream_t s, int n, const float* Dinv, const float* r, float* y,
+                             float* e, float omega, const float* xadd, const double* r64,
+                             double* scal, double* partial, unsigned* counter) {
+  note_launch();
+  const int g = nblk(2 * n * (n + 1), 256), blocks = g < kDotBlocks ? g : kDotBlocks;
+  bj_update_dot_kernel<ND><<<blocks, 256, 0, s>>>(n, Dinv, r, y, e, omega, xadd, r64, scal, partial,
+                                                  counter);
+}
+
 // k > 1 right-hand sides of a blocked solve: one launch over gridDim.y = k
 // (the right-hand sides' blocks read the operator from L2 together)
 template <typename T, int ND, bool NS>

@@ -29,6 +29,11 @@ namespace hdgmg {
 HDGMG_INST(false)
 HDGMG_INST(true)
 #undef HDGMG_INST
+#if !HDGMG_REAL_IS_DOUBLE
+template void launch_bj_update_dot_nd<HDGMG_ND>(cudaStream_t, int, const float*, const float*,
+                                                float*, float*, float, const float*,
+                                                const double*, double*, double*, unsigned*);
+#endif
 #if HDGMG_REAL_IS_DOUBLE
 template void launch_cg_matvec_nd<HDGMG_ND>(cudaStream_t, int, const double*, const float*,
                                             const double*, const double*, double*, double*,

@@ -1939,6 +1939,14 @@ void launch_cg_matvec(cudaStream_t s, int n, int nd, const double* A, const floa
 #undef CGM
 }
 
+void launch_bj_update_dot(cudaStream_t s, int n, int nd, const float* Dinv, const float* r,
+                          float* y, float* e, float omega, const float* xadd, const double* r64,
+                          double* scal, double* partial, unsigned* counter) {
+#define BJD(ND) launch_bj_update_dot_nd<ND>(s, n, Dinv, r, y, e, omega, xadd, r64, scal, partial, counter)
+  ND_DISPATCH(nd, BJD)
+#undef BJD
+}
+
 void launch_matvec_bf16(cudaStream_t s, int n, int nd, bool ns, const __nv_bfloat16* A,
                         const float* x, float* y, float alpha, const float* xadd, int k) {
 #define MVB(ND)                                                                 \
