@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--arm", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--arm", default="both", choices=["both", "mixed", "fp64", "mixed_matrix_free"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched (64 problems x 16 RHS), adjoint (1024^2) and "
@@ -210,7 +210,9 @@ def run_ours(args):
 
     common = dict(tau_mode=hdgmg.TAU_OVER_H, tau_c=1.0, stream=stream, **SOLVER_OPTS)
     arms = {"mixed": hdgmg.Solver(N_MESH, P_ORDER, precision=hdgmg.PREC_FP32, **common),
-            "fp64": hdgmg.Solver(N_MESH, P_ORDER, precision=hdgmg.PREC_FP64, **common)}
+            "fp64": hdgmg.Solver(N_MESH, P_ORDER, precision=hdgmg.PREC_FP64, **common),
+            "mixed_matrix_free": hdgmg.Solver(N_MESH, P_ORDER, precision=hdgmg.PREC_FP32,
+                                              matrix_free=1, **common)}
     if args.arm != "both":
         arms = {args.arm: arms[args.arm]}
 
@@ -262,7 +264,7 @@ def run_ours(args):
             return {"arm": args.arm, "ms_per_step": r["ms"], "iters": r["iters"],
                     "rel_res": r["rel_res"], "gpu_launches": r["launches"]}
         return None
-    mixed, fp64 = results["mixed"], results["fp64"]
+    mixed, fp64, mfree = results["mixed"], results["fp64"], results["mixed_matrix_free"]
     value = replicas.whole_job_rate(dofs, world, mixed["ms"])
 
     # end to end through the C ABI on pinned host buffers (mixed arm)
@@ -301,6 +303,11 @@ def run_ours(args):
                          "ms_per_step": fp64["ms"],
                          "iters": fp64["iters"], "rel_res": fp64["rel_res"],
                          "setup_ms": fp64["setup_ms"], "solve_ms": fp64["solve_ms"]},
+                "mixed_matrix_free": {
+                    "value": replicas.whole_job_rate(dofs, world, mfree["ms"]),
+                    "ms_per_step": mfree["ms"], "iters": mfree["iters"], "rel_res": mfree["rel_res"],
+                    "note": "the mixed arm with the V-cycle's FP32 finest-level matvecs applied "
+                            "matrix-free through the eigenbasis (opts.matrix_free)"},
                 "mixed": {"iters": mixed["iters"], "rel_res": mixed["rel_res"],
                           "setup_ms": mixed["setup_ms"], "solve_ms": mixed["solve_ms"],
                           "solve_only_value": replicas.whole_job_rate(dofs, world,

@@ -222,6 +222,15 @@ typedef struct {
                              sum_e p_e^T A_e p_e); 0: separate direction,
                              matvec, dot and update kernels.  Same iteration,
                              different summation order.  1                   */
+  int32_t matrix_free;    /* 1: the V-cycle applies the finest operator
+                             matrix-free in FP32 through the shared
+                             eigenbasis, A_e x = kappa K x + tau x -
+                             sum_i (kappa P_i + tau Q_i)^T (...) x / s_i
+                             (nt^2 + 4 nv nt FMA per element, no stored
+                             entries read); the FP64 operator of the Krylov
+                             iteration stays stored.  Needs the symmetric
+                             basis condensation, p <= 6 and precision FP32
+                             or FP32_IR (EINVAL otherwise).  0: stored.  0   */
 } hdgmg_opts;
 
 typedef struct {

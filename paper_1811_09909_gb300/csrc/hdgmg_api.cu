@@ -149,6 +149,9 @@ struct hdgmg_ctx {
   // fused PCG body: the finest level's last post-smoothing step also forms the
   // PCG's r.z (rz_fuse set while the body is recorded; rz_done: it was)
   bool rz_fuse = false, rz_done = false;
+  // opts.matrix_free: the FP32 tables of the matrix-free finest-level apply
+  // (laid out as MfTables<p + 1>)
+  std::vector<float> mf_tab;
   // blocked solves of up to kb right-hand sides (opts.rhs_block): FP32 level
   // vectors hold kb copies [kb][...]; kr is the count the V-cycle launches
   // run with (1 outside a blocked solve)
@@ -569,6 +572,10 @@ void level_matvec(hdgmg_ctx* c, int l, const T* x, T* y, const T* xadd = nullptr
   if constexpr (std::is_same<T, float>::value) {
     if (L.A16) {
       launch_matvec_bf16(c->stream, L.n, L.nd, c->ns, L.A16, x, y, 1.0f, xadd, c->kr);
+      return;
+    }
+    if (l == 0 && c->opts.matrix_free) {
+      launch_matvec_mf(c->stream, L.n, L.nd, c->mf_tab.data(), c->kap, x, y, 1.0f, xadd, c->kr);
       return;
     }
   }
@@ -1573,6 +1580,7 @@ void hdgmg_default_opts(hdgmg_opts* o) {
   o->pcg_graph = 1;
   o->rhs_block = 0;
   o->pcg_fuse = 1;
+  o->matrix_free = 0;
 }
 
 const char* hdgmg_last_error(void) { return g_last_error.c_str(); }
@@ -1647,6 +1655,7 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (o.rhs_block < 0 || o.rhs_block > kMaxRhsBlock)
     return fail(HDGMG_EINVAL, "rhs_block must be in 0..16");
   if (o.pcg_fuse < 0 || o.pcg_fuse > 1) return fail(HDGMG_EINVAL, "pcg_fuse must be 0 or 1");
+  if (o.matrix_free < 0 || o.matrix_free > 1) return fail(HDGMG_EINVAL, "matrix_free must be 0 or 1");
   const bool nonsym = P.pde == HDGMG_PDE_CONVDIFF || P.scheme == HDGMG_SCHEME_NIPG ||
                       P.scheme == HDGMG_SCHEME_IIPG;
   if (nonsym && o.krylov == HDGMG_KRYLOV_CG)
@@ -1668,6 +1677,11 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
   if (nn < 2) return fail(HDGMG_EINVAL, "coarsest mesh would be smaller than 2 x 2");
   if ((int64_t)P.n * P.n > (1ll << 26)) return fail(HDGMG_EINVAL, "n too large");
 
+  if (o.matrix_free &&
+      (nonsym || o.condensation == HDGMG_CONDENSE_FACTOR || P.p + 1 > kMfMaxNd ||
+       (o.precision != HDGMG_PREC_FP32 && o.precision != HDGMG_PREC_FP32_IR)))
+    return fail(HDGMG_EINVAL, "matrix_free needs the symmetric basis condensation, p <= 6 and "
+                              "precision FP32 or FP32_IR");
   hdgmg_ctx* c = new hdgmg_ctx();
   c->prob = P;
   c->opts = o;
@@ -1725,6 +1739,19 @@ hdgmg_status hdgmg_create(hdgmg_ctx** out, const hdgmg_problem* prob, const hdgm
       return cleanup(fail(HDGMG_EINVAL, "no positive-definite combination of the volume forms"));
     for (double& v : eb.e) v *= c->ktau;    // the kernels take tau e and tau Q
     for (double& v : eb.Q) v *= c->ktau;
+    if (o.matrix_free) {
+      const int nd = c->p + 1, nt = 4 * nd, nv = nd * nd;
+      c->mf_tab.clear();
+      for (double v : c->ref.K) c->mf_tab.push_back((float)v);
+      for (double v : eb.P) c->mf_tab.push_back((float)v);
+      for (double v : eb.Q) c->mf_tab.push_back((float)v);   // tau Q
+      for (double v : eb.g) c->mf_tab.push_back((float)v);
+      for (double v : eb.e) c->mf_tab.push_back((float)v);   // tau e
+      c->mf_tab.push_back((float)c->ktau);
+      if ((int)c->mf_tab.size() != mf_table_size(nd) || (int)c->ref.K.size() != nt * nt ||
+          (int)eb.P.size() != nv * nt)
+        return cleanup(fail(HDGMG_EINVAL, "matrix-free tables: unexpected basis sizes"));
+    }
     CTRY(upload(&c->refd.Phi, eb.Phi));
     CTRY(upload(&c->refd.eg, eb.g));
     CTRY(upload(&c->refd.ee, eb.e));

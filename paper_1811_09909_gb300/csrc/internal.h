@@ -244,6 +244,17 @@ template <int ND>
 void launch_cg_matvec_nd(cudaStream_t s, int n, const double* A, const float* z32,
                          const double* z64, const double* p, double* Ap, double* scal,
                          double* partial, unsigned* counter);
+// matrix-free FP32 finest-level apply through the eigenbasis (k_mf.cuh;
+// symmetric basis route, nd <= 7): tables is a host array of
+// mf_table_size(nd) floats (K [nt][nt], P [nv][nt], tau Q, g [nv], tau e,
+// tau), kap the FP64 element coefficients
+constexpr int mf_table_size(int nd) { return 16 * nd * nd + 8 * nd * nd * nd + 2 * nd * nd + 1; }
+constexpr int kMfMaxNd = 7;
+void launch_matvec_mf(cudaStream_t s, int n, int nd, const float* tables, const double* kap,
+                      const float* x, float* y, float alpha, const float* xadd, int k);
+template <int ND>
+void launch_matvec_mf_nd(cudaStream_t s, int n, const float* tables, const double* kap,
+                         const float* x, float* y, float alpha, const float* xadd, int k);
 // the finest FP32 level's last post-smoothing step with r64 . z (z the new
 // e) and the beta recurrence of the FP64 PCG (symmetric storage, one
 // right-hand side); partial holds kDotBlocks doubles

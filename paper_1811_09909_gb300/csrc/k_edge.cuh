@@ -1,9 +1,8 @@
 // Edge/element kernels templated on the number of trace modes per edge ND
 // and on the storage of the element operators (NS = false: symmetric, packed
 // lower triangle; NS = true: non-symmetric, full row-major):
-//   K6  trace matvec y += alpha A x, A_e in structure-of-arrays layout, one
-//       thread per (element, row block) for symmetric storage and per
-//       element for full storage; results added into the two edge owners
+//   K6  trace matvec y += alpha A x, one thread per element, A_e in
+//       structure-of-arrays layout, results added into the two edge owners
 //       with atomics (exactly two contributions per entry, so the sum does
 //       not depend on their order)
 //   K2  edge block-Jacobi blocks D = A_e0[edge] + A_e1[edge] and D^-1
@@ -93,66 +92,8 @@ __global__ void __launch_bounds__(128) matvec_kernel(int n, const TA* __restrict
   }
 }
 
-// K6 for symmetric (packed) storage, one thread per (element, row block):
-// a block of four warps covers 32 consecutive elements; warp w forms the ND
-// rows of local edge w (rows w ND ... w ND + ND - 1) over all 4 ND columns,
-// in column order, and lane l works on element 32 blockIdx.x + l.  Every
-// warp load is one contiguous 32-element run of an entry row, and a block
-// has four times the warps of the one-thread-per-element form in flight; an
-// off-diagonal entry is read by the two warps whose rows it couples (the
-// second read is served by L1 or L2).  Same arguments as matvec_kernel.
-template <typename T, int ND, typename TA, int LE>
-__device__ __forceinline__ void matvec_rows(const TA* __restrict__ Ae, int nE, const T* xl,
-                                            T* yE, int nedge, T alpha) {
-  constexpr int NL = 4 * ND;
-#pragma unroll
-  for (int k = 0; k < ND; ++k) {
-    T s = T(0);
-#pragma unroll
-    for (int c = 0; c < NL; ++c) s += load_entry(Ae + (size_t)pk_any(LE * ND + k, c) * nE) * xl[c];
-    atomicAdd(yE + (size_t)k * nedge, alpha * s);
-  }
-}
-
-template <typename T, int ND, typename TA = T, bool MULTI = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 8 ? 4 : 6) matvec_rb_kernel(int n, const TA* __restrict__ A,
-                                                           const T* __restrict__ x,
-                                                           T* __restrict__ y, T alpha,
-                                                           const T* __restrict__ xadd) {
-  constexpr int NL = 4 * ND;
-  const int nE = n * n;
-  const int e = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int le = threadIdx.x >> 5;
-  if (e >= nE) return;
-  const int nedge = 2 * n * (n + 1);
-  if (MULTI) {
-    x += (size_t)blockIdx.y * ND * nedge;
-    y += (size_t)blockIdx.y * ND * nedge;
-    if (xadd) xadd += (size_t)blockIdx.y * 2 * nedge;
-  }
-  int ed[4];
-  elem_edges(n, e, ed);
-  const int E = le == 0 ? ed[0] : le == 1 ? ed[1] : le == 2 ? ed[2] : ed[3];
-  if (bnd_edge(n, E)) return;
-  T xl[NL];
-#pragma unroll
-  for (int c = 0; c < NL; ++c) {
-    const size_t ix = (size_t)(c % ND) * nedge + ed[c / ND];
-    xl[c] = x[ix];
-    if (xadd && c % ND < 2) xl[c] += xadd[ix];
-  }
-  const TA* Ae = A + e;
-  T* yE = y + E;
-  switch (le) {   // warp-uniform
-    case 0: matvec_rows<T, ND, TA, 0>(Ae, nE, xl, yE, nedge, alpha); break;
-    case 1: matvec_rows<T, ND, TA, 1>(Ae, nE, xl, yE, nedge, alpha); break;
-    case 2: matvec_rows<T, ND, TA, 2>(Ae, nE, xl, yE, nedge, alpha); break;
-    default: matvec_rows<T, ND, TA, 3>(Ae, nE, xl, yE, nedge, alpha); break;
-  }
-}
-
-// rows LE ND ... LE ND + ND - 1 of A_e times xl added into y (as
-// matvec_rows, FP64), returning their part of xl^T A_e xl
+// rows LE ND ... LE ND + ND - 1 of A_e (FP64, packed symmetric) times xl,
+// added into y with atomics, returning their part of xl^T A_e xl
 template <int ND, int LE>
 __device__ __forceinline__ double matvec_rows_q(const double* __restrict__ Ae, int nE,
                                                 const double* xl, double* yE, int nedge) {
@@ -175,12 +116,17 @@ __device__ __forceinline__ double matvec_rows_q(const double* __restrict__ Ae, i
 // previous update), and the quadratic form p+ . A p+ = sum_e p+_e^T A_e p+_e
 // summed element by element (each thread over its rows and element groups,
 // then block_sum, then the last block over the block partials in block
-// order) into scal[1], with alpha = scal[0] / scal[1] in scal[2].  Thread
-// layout of matvec_rb_kernel over groups of 32 elements, a fixed grid
-// striding over the groups: warp w forms p+ on local edge w of the group's
-// elements (one fma per value, the same as cg_update_dir_test_kernel's) into
-// shared memory, then every warp reads the element's 4 ND values from there.
-// Rows of Dirichlet edges are skipped, where p+ is zero.
+// order) into scal[1], with alpha = scal[0] / scal[1] in scal[2].  One thread
+// per (element, row block): a block of four warps covers a group of 32
+// consecutive elements (lane l: element 32 g + l) and warp w forms the ND
+// rows of local edge w (every warp load of an entry row is one contiguous
+// 32-element run; the FP64 pipe, not HBM, bounds this kernel, so four times
+// the warps of one thread per element hide its latency).  A fixed grid
+// strides over the groups.  Warp w first forms p+ on local edge w of the
+// group's elements (one fma per value, the same as
+// cg_update_dir_test_kernel's) into shared memory; every warp then reads the
+// element's 4 ND values from there.  Rows of Dirichlet edges are skipped,
+// where p+ is zero.
 template <int ND, typename TZ>
 __global__ void __launch_bounds__(128, 4) cg_matvec_kernel(int n, const double* __restrict__ A,
                                                            const TZ* __restrict__ z,
@@ -488,14 +434,6 @@ template <typename T, int ND, bool NS>
 void launch_matvec_nd(cudaStream_t s, int n, const T* A, const T* x, T* y, T alpha,
                       const T* xadd, int k) {
   note_launch();
-  if (!NS) {
-    if (k > 1)
-      matvec_rb_kernel<T, ND, T, true><<<dim3(nblk(n * n, 32), k), 128, 0, s>>>(n, A, x, y, alpha,
-                                                                              xadd);
-    else
-      matvec_rb_kernel<T, ND><<<nblk(n * n, 32), 128, 0, s>>>(n, A, x, y, alpha, xadd);
-    return;
-  }
   if (k > 1)
     matvec_kernel<T, ND, NS, T, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(n, A, x, y, alpha,
                                                                                  xadd);
@@ -507,15 +445,6 @@ template <int ND, bool NS>
 void launch_matvec_bf16_nd(cudaStream_t s, int n, const __nv_bfloat16* A, const float* x, float* y,
                            float alpha, const float* xadd, int k) {
   note_launch();
-  if (!NS) {
-    if (k > 1)
-      matvec_rb_kernel<float, ND, __nv_bfloat16, true><<<dim3(nblk(n * n, 32), k), 128, 0, s>>>(
-          n, A, x, y, alpha, xadd);
-    else
-      matvec_rb_kernel<float, ND, __nv_bfloat16><<<nblk(n * n, 32), 128, 0, s>>>(n, A, x, y, alpha,
-                                                                                 xadd);
-    return;
-  }
   if (k > 1)
     matvec_kernel<float, ND, NS, __nv_bfloat16, true><<<dim3(nblk(n * n, 128), k), 128, 0, s>>>(
         n, A, x, y, alpha, xadd);

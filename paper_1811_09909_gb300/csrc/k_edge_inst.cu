@@ -2,7 +2,10 @@
 // built once per pair with -DHDGMG_REAL=<double|float> -DHDGMG_ND=<2..9>, and
 // once per ND with -DHDGMG_BF16 for the BF16-storage matvec alone (separate
 // units so that the widest ones compile in parallel).
+#include <cstring>
+
 #include "k_edge.cuh"
+#include "k_mf.cuh"
 
 #ifndef HDGMG_REAL
 #define HDGMG_REAL double
@@ -29,6 +32,10 @@ namespace hdgmg {
 HDGMG_INST(false)
 HDGMG_INST(true)
 #undef HDGMG_INST
+#if !HDGMG_REAL_IS_DOUBLE && HDGMG_ND <= 7
+template void launch_matvec_mf_nd<HDGMG_ND>(cudaStream_t, int, const float*, const double*,
+                                            const float*, float*, float, const float*, int);
+#endif
 #if !HDGMG_REAL_IS_DOUBLE
 template void launch_bj_update_dot_nd<HDGMG_ND>(cudaStream_t, int, const float*, const float*,
                                                 float*, float*, float, const float*,

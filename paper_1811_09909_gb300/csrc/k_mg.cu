@@ -1939,6 +1939,17 @@ void launch_cg_matvec(cudaStream_t s, int n, int nd, const double* A, const floa
 #undef CGM
 }
 
+void launch_matvec_mf(cudaStream_t s, int n, int nd, const float* tables, const double* kap,
+                      const float* x, float* y, float alpha, const float* xadd, int k) {
+  switch (nd) {
+#define MFC(ND) \
+  case ND: launch_matvec_mf_nd<ND>(s, n, tables, kap, x, y, alpha, xadd, k); break;
+    MFC(2) MFC(3) MFC(4) MFC(5) MFC(6) MFC(7)
+#undef MFC
+    default: break;
+  }
+}
+
 void launch_bj_update_dot(cudaStream_t s, int n, int nd, const float* Dinv, const float* r,
                           float* y, float* e, float omega, const float* xadd, const double* r64,
                           double* scal, double* partial, unsigned* counter) {

@@ -53,7 +53,7 @@ class Opts(ctypes.Structure):
                 ("condensation", ctypes.c_int32), ("l2_persist_mb", ctypes.c_int32),
                 ("pcycle", ctypes.c_int32), ("pcycle_tail_n", ctypes.c_int32),
                 ("pcg_graph", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
-                ("pcg_fuse", ctypes.c_int32)]
+                ("pcg_fuse", ctypes.c_int32), ("matrix_free", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
