@@ -34,6 +34,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hdgmg_umesh.h"
@@ -116,21 +117,22 @@ __device__ __forceinline__ double dval(const UTab& T, const Geo<P>& g, int d, in
 
 // F[i][(j,k)] = <psi_jk, phi_i> on edge j (Gauss quadrature on the edge at the
 // volume nodes' coordinates: only the node row / column next to the edge
-// contributes)
+// contributes) = esc w[al] endv Pk[k][al], with the signed trace-basis scale
+// esc = 0.5 sqrt(len_j (2k + 1)) (-1 when the edge's direction flips an odd
+// mode) formed once per (edge, mode) by the caller
 template <int P>
-__device__ __forceinline__ double fval(const UTab& T, const Geo<P>& g, int i, int j, int k) {
+__device__ __forceinline__ double fval_scaled(const UTab& T, double esc, int i, int j, int k) {
   constexpr int P1 = P + 1;
   const int i1 = i % P1, i2 = i / P1;
-  int al, rev;
+  int al;
   double endv;
   switch (j) {
-    case 0: al = i1; endv = T.le[i2]; rev = 0; break;
-    case 1: al = i2; endv = T.re[i1]; rev = 0; break;
-    case 2: al = i1; endv = T.re[i2]; rev = 1; break;
-    default: al = i2; endv = T.le[i1]; rev = 1; break;
+    case 0: al = i1; endv = T.le[i2]; break;
+    case 1: al = i2; endv = T.re[i1]; break;
+    case 2: al = i1; endv = T.re[i2]; break;
+    default: al = i2; endv = T.le[i1]; break;
   }
-  const double sg = (((rev ^ g.flip[j]) & k) & 1) ? -1.0 : 1.0;
-  return 0.5 * sqrt(g.len[j] * (2.0 * k + 1.0)) * T.w[al] * endv * T.Pk[k][al] * sg;
+  return esc * T.w[al] * endv * T.Pk[k][al];
 }
 
 // E[a][b] = <phi_a, phi_b>_dK
@@ -331,16 +333,19 @@ __global__ void u_rhs_kernel(int E, const double* __restrict__ Z, const double* 
   t[x] = s;
 }
 
-// recovery of u and q per element (one block per element)
+// recovery of u and q per element (one block per element; the two
+// triangular solves of S^-1 on warp 0, column by column with the reciprocal
+// pivots, the rest over the block; at most 64 registers so that 8 blocks
+// share an SM)
 template <int P>
-__global__ void __launch_bounds__(128) u_recover_kernel(
+__global__ void __launch_bounds__(128, 8) u_recover_kernel(
     UTab T, const double* __restrict__ xy, const int* __restrict__ quads,
     const double* __restrict__ logk, const int* __restrict__ el_slot,
     const double* __restrict__ L, const double* __restrict__ Z, const double* __restrict__ f,
     const double* __restrict__ lam, double* __restrict__ u, double* __restrict__ q) {
   constexpr int P1 = P + 1, NV = P1 * P1, NT = 4 * P1;
   __shared__ Geo<P> g;
-  __shared__ double le_[NT], y[NV], uu[NV];
+  __shared__ double le_[NT], y[NV], uu[NV], es[NT], rdg[NV];
   const int e = blockIdx.x, tid = threadIdx.x;
   element_geometry<P>(T, xy, quads, e, g);
   for (int c = tid; c < NT; c += blockDim.x) {
@@ -348,19 +353,33 @@ __global__ void __launch_bounds__(128) u_recover_kernel(
     le_[c] = b < 0 ? 0.0 : lam[(size_t)b * P1 + c % P1];
   }
   __syncthreads();
-  for (int a = tid; a < NV; a += blockDim.x) y[a] = g.m[a] * f[(size_t)e * NV + a];
-  __syncthreads();
+  // the signed trace-basis scales of fval_scaled, one FP64 sqrt per (edge,
+  // mode) instead of one per use (the flux term below uses each NV times)
+  for (int c = tid; c < NT; c += blockDim.x) {
+    const int j = c / P1, k = c % P1, rev = j >= 2 ? 1 : 0;
+    const double sg = (((rev ^ g.flip[j]) & k) & 1) ? -1.0 : 1.0;
+    es[c] = 0.5 * sqrt(g.len[j] * (2.0 * k + 1.0)) * sg;
+  }
   const double* Le = L + (size_t)e * NV * NV;
-  if (tid == 0) {                         // S^-1 (M f)
-    for (int r = 0; r < NV; ++r) {
-      double v = y[r];
-      for (int c = 0; c < r; ++c) v -= Le[r * NV + c] * y[c];
-      y[r] = v / Le[r * NV + r];
+  for (int a = tid; a < NV; a += blockDim.x) {
+    y[a] = g.m[a] * f[(size_t)e * NV + a];
+    rdg[a] = 1.0 / Le[a * NV + a];
+  }
+  __syncthreads();
+  if (tid < 32) {                         // S^-1 (M f) = L^-T L^-1 (M f), column by column on warp 0
+    for (int k = 0; k < NV; ++k) {        // forward: y_k /= L_kk, then y_i -= L_ik y_k below
+      if (tid == 0) y[k] *= rdg[k];
+      __syncwarp();
+      const double yk = y[k];
+      for (int i = k + 1 + tid; i < NV; i += 32) y[i] -= Le[i * NV + k] * yk;
+      __syncwarp();
     }
-    for (int r = NV - 1; r >= 0; --r) {
-      double v = y[r];
-      for (int c = r + 1; c < NV; ++c) v -= Le[c * NV + r] * y[c];
-      y[r] = v / Le[r * NV + r];
+    for (int k = NV - 1; k >= 0; --k) {   // backward with L^T: y_k /= L_kk, then y_i -= L_ki y_k above
+      if (tid == 0) y[k] *= rdg[k];
+      __syncwarp();
+      const double yk = y[k];
+      for (int i = tid; i < k; i += 32) y[i] -= Le[k * NV + i] * yk;
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -384,7 +403,7 @@ __global__ void __launch_bounds__(128) u_recover_kernel(
     }
     for (int c = 0; c < NT; ++c) {
       const int j = c / P1;
-      s -= (d == 0 ? g.nx[j] : g.ny[j]) * fval<P>(T, g, a, j, c % P1) * le_[c];
+      s -= (d == 0 ? g.nx[j] : g.ny[j]) * fval_scaled<P>(T, es[c], a, j, c % P1) * le_[c];
     }
     q[(size_t)e * 2 * NV + x] = kap * s / g.m[a];
   }
@@ -450,26 +469,22 @@ __global__ void u_edge_kernel(int n_blk, int nd, const int* __restrict__ t0, con
 
 enum { U_SUM = 0, U_RES = 1, U_SMOOTH = 2 };
 
-// y = A x for one level in one pass, pulled per macro-edge: thread (b, k)
-// forms row k of macro-edge b from its two sides, y_bk = sum over the sides
-// of the element rows (A_e symmetric, stored column by column, so row i is
-// contiguous across k) against the element's gathered x; every element row is
-// read once.  Then SUM: out = y; RES: out = r - y; SMOOTH: out = x + omega
-// Dinv (r - y) on the block (the block's rows meet in shared memory).  out
-// never aliases x: a smoothing step reads every neighbour's old value.
-template <typename T, int ND, int NU>
-__global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const int* __restrict__ el_slot,
-                                                     const int* __restrict__ t0, const int* __restrict__ t1,
-                                                     const T* __restrict__ A, const T* __restrict__ x,
-                                                     const T* __restrict__ r, const T* __restrict__ Dinv,
-                                                     double omega, int mode, T* __restrict__ out) {
-  constexpr int UPB = 128 / ND;
+// The same with one thread per row (thread (b, k) walks b's two sides'
+// padded columns in order, y = side 0 + side 1): the FP64 levels' form.  The
+// warp form below halves the FP32 cycle's pull time but doubles the FP64
+// one's (10.5 against 21.9 us per launch at 97k quadrilaterals, p = 3).
+template <typename T>
+__global__ void __launch_bounds__(128) u_pull_row_kernel(int n_blk, int nu, const int* __restrict__ el_slot,
+                                                         const int* __restrict__ t0, const int* __restrict__ t1,
+                                                         const T* __restrict__ A, const T* __restrict__ x,
+                                                         const T* __restrict__ r, const T* __restrict__ Dinv,
+                                                         double omega, int mode, T* __restrict__ out) {
+  constexpr int ND = 2, UPB = 128 / ND;
   __shared__ T ys[UPB * ND];
-  const int nu = NU > 0 ? NU : nu_rt;
   const int ndm = nu * ND;
   const int lu = threadIdx.x / ND, k = threadIdx.x % ND;
   const int b = blockIdx.x * UPB + lu;
-  const bool act = lu < UPB && b < n_blk;
+  const bool act = b < n_blk;
   T y = 0;
   if (act) {
 #pragma unroll
@@ -479,17 +494,9 @@ __global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const
       const T* Ae = A + (size_t)el * ndm * ndm + sl * ND + k;
       const int* sls = el_slot + (size_t)el * nu;
       T s = 0;
-      if (NU > 0) {
-#pragma unroll
-        for (int j = 0; j < NU * ND; ++j) {
-          const int bj = __ldg(sls + j / ND);
-          if (bj >= 0) s += __ldg(Ae + (size_t)j * ndm) * __ldg(x + (size_t)bj * ND + j % ND);
-        }
-      } else {
-        for (int j = 0; j < ndm; ++j) {
-          const int bj = __ldg(sls + j / ND);
-          if (bj >= 0) s += __ldg(Ae + (size_t)j * ndm) * __ldg(x + (size_t)bj * ND + j % ND);
-        }
+      for (int j = 0; j < ndm; ++j) {
+        const int bj = __ldg(sls + j / ND);
+        if (bj >= 0) s += __ldg(Ae + (size_t)j * ndm) * __ldg(x + (size_t)bj * ND + j % ND);
       }
       y += s;
     }
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const
     if (act) out[(size_t)b * ND + k] = r[(size_t)b * ND + k] - y;
     return;
   }
-  if (lu < UPB) ys[lu * ND + k] = act ? r[(size_t)b * ND + k] - y : T(0);
+  ys[lu * ND + k] = act ? r[(size_t)b * ND + k] - y : T(0);
   __syncthreads();
   if (act) {
     const T* D = Dinv + (size_t)b * ND * ND + k * ND;
@@ -511,6 +518,62 @@ __global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu_rt, const
     for (int l = 0; l < ND; ++l) s += D[l] * ys[lu * ND + l];
     out[(size_t)b * ND + k] = x[(size_t)b * ND + k] + (T)omega * s;
   }
+}
+
+// y = A x for one macro-element level in one pass, pulled per macro-edge
+// (two modes per edge): one warp per unknown block b.  The lanes split the
+// columns of b's two sides (side s, column j of its macro-element's padded
+// matrix; A_e symmetric, stored column by column, so b's two rows are
+// adjacent in every column) and each sums its columns' products for both rows
+// in column order; a butterfly over the warp gives y_b (a fixed order).  Then
+// SUM: out = y; RES: out = r - y; SMOOTH: out = x + omega Dinv (r - y) on the
+// block.  out never aliases x: a smoothing step reads every neighbour's old
+// value.  (One thread per row walked the padded columns serially: 10-18
+// units per macro-element at the deep levels against ~5.5 on average.)
+template <typename T>
+__global__ void __launch_bounds__(128) u_pull_kernel(int n_blk, int nu, const int* __restrict__ el_slot,
+                                                     const int* __restrict__ t0, const int* __restrict__ t1,
+                                                     const T* __restrict__ A, const T* __restrict__ x,
+                                                     const T* __restrict__ r, const T* __restrict__ Dinv,
+                                                     double omega, int mode, T* __restrict__ out) {
+  constexpr int ND = 2;
+  const int b = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= n_blk) return;                   // whole warps
+  const int ndm = nu * ND;
+  const int ts0 = __ldg(t0 + b), ts1 = __ldg(t1 + b);
+  T y0 = 0, y1 = 0;
+  for (int q = lane; q < 2 * ndm; q += 32) {
+    const int side = q >= ndm ? 1 : 0, j = q - side * ndm;
+    const int ts = side ? ts1 : ts0;
+    const int el = ts / nu, sl = ts - el * nu;
+    const int bj = __ldg(el_slot + (size_t)el * nu + j / ND);
+    if (bj >= 0) {
+      const T xv = __ldg(x + (size_t)bj * ND + j % ND);
+      const T* col = A + ((size_t)el * ndm + j) * ndm + sl * ND;
+      y0 += __ldg(col) * xv;
+      y1 += __ldg(col + 1) * xv;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+  }
+  if (lane >= ND) return;
+  const int k = lane;
+  const size_t o = (size_t)b * ND;
+  if (mode == U_SUM) {
+    out[o + k] = k == 0 ? y0 : y1;
+    return;
+  }
+  const T r0 = r[o] - y0, r1 = r[o + 1] - y1;
+  if (mode == U_RES) {
+    out[o + k] = k == 0 ? r0 : r1;
+    return;
+  }
+  const T* D = Dinv + o * ND + k * ND;
+  out[o + k] = x[o + k] + (T)omega * (D[0] * r0 + D[1] * r1);
 }
 
 // per unknown block: out = t(side 0) + t(side 1) (the element-slot sums of
@@ -1098,8 +1161,12 @@ void level_matvec(hdgmg_umesh* c, int k, const T* x, T* y, int mode, const T* r)
                                                            c->opts.omega, mode, y);
   } else {
     note_launch();
-    u_pull_kernel<T, 2, 0><<<nblk(L.n_blk, 64), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1, v.A,
-                                                                x, r, v.Dinv, c->opts.omega, mode, y);
+    if (std::is_same<T, float>::value)
+      u_pull_kernel<T><<<nblk(L.n_blk, 4), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1, v.A,
+                                                            x, r, v.Dinv, c->opts.omega, mode, y);
+    else
+      u_pull_row_kernel<T><<<nblk(L.n_blk, 64), 128, 0, c->s>>>(L.n_blk, L.nu, L.el_slot, L.blk_t0, L.blk_t1,
+                                                                 v.A, x, r, v.Dinv, c->opts.omega, mode, y);
   }
 }
 
