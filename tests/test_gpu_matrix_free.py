@@ -92,3 +92,18 @@ def test_matrix_free_rejected_outside_its_range(kw):
     p = kw.pop("p")
     with pytest.raises(hdgmg.HdgmgError):
         hdgmg.Solver(8, p, matrix_free=1, **kw)
+
+
+def test_matrix_free_under_fp32_refinement():
+    """PREC_FP32_IR: the inner FP32 PCG's V-cycle applies the finest operator
+    matrix-free, the inner matvec and the FP64 residual stay stored."""
+    n, p = 32, 3
+    wl = W.lognormal(n, p, seed=57)
+    f = np.random.default_rng(58).standard_normal(((p + 1) ** 2, n * n))
+    s = hdgmg.Solver(n, p, coarsest_n=4, m_fine=1, m_max=2, rtol=1e-11, precision=hdgmg.PREC_FP32_IR,
+                     matrix_free=1, tau_mode=hdgmg.TAU_OVER_H)
+    s.setup(cuda(wl.log_kappa))
+    lam, _, _, info = s.solve(cuda(f), want_u=False, want_q=False)
+    assert info.converged == 1 and info.rel_res <= 1e-11
+    ref = hdg.HDGProblem(n, p, np.exp(wl.log_kappa), wl.tau()).solve_direct(f)
+    assert rel(host(lam), ref) <= 1e-8

@@ -38,8 +38,11 @@ def rel(a, b):
 
 @pytest.mark.parametrize("precision,pcg_graph", [(hdgmg.PREC_FP32, 1), (hdgmg.PREC_FP64, 1),
                                                  (hdgmg.PREC_BF16, 1), (hdgmg.PREC_FP32, 0)])
-@pytest.mark.parametrize("n,p", [(32, 3), (48, 4)])
+@pytest.mark.parametrize("n,p", [(32, 3), (48, 4), (32, 1), (24, 2)])
 def test_fused_pcg_matches_unfused_and_direct(precision, pcg_graph, n, p):
+    """p = 1: the finest level is the persistent cycle's first P1 level, so
+    r.z falls back to its own kernel; p = 2, 3, 4: r.z in the finest level's
+    last block-Jacobi step."""
     wl = W.lognormal(n, p, seed=31 + p)
     f = np.random.default_rng(32).standard_normal(((p + 1) ** 2, n * n))
     kw = dict(coarsest_n=4, m_fine=1, m_max=2, rtol=1e-12, precision=precision, pcg_graph=pcg_graph,
