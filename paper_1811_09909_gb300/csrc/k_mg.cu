@@ -974,6 +974,42 @@ __device__ __forceinline__ void pc_bulk_copy(void* dst, const void* src, unsigne
       "l"(src), "r"(bytes), "r"(pc_smem_addr(bar))
       : "memory");
 }
+// L2 prefetch of [src, src + bytes): 16-byte aligned start, size a multiple
+// of 16 bytes (no shared memory, no completion to wait for)
+__device__ __forceinline__ void pc_l2_prefetch(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// Thread 0 of every block asks L2 for its share (1 / gridDim.x, in 16-byte
+// units) of each operator array of the grid levels, so that the first step on
+// each level finds its operators in L2 (the FP64 matvec between two cycles
+// streams 124 MB through L2 at 256^2, p = 4).  Every array is a whole device
+// allocation whose size is a multiple of 16 bytes (level sizes: 36 n^2,
+// 3 or 4 * 2 n (n + 1), 36, 64 or 128 * n^2 / 4 entries of 4 or 8 bytes).
+template <typename T, bool NS>
+__device__ void pc_prefetch_grid_levels(const PCycleParams<T>& P, int top) {
+  const int na = NS ? 64 : 36;
+  auto share = [&](const void* base, size_t bytes) {
+    const size_t units = bytes / 16, per = (units + gridDim.x - 1) / gridDim.x;
+    const size_t u0 = per * blockIdx.x;
+    if (u0 >= units) return;
+    const size_t nu = units - u0 < per ? units - u0 : per;
+    pc_l2_prefetch(static_cast<const char*>(base) + 16 * u0, (unsigned)(16 * nu));
+  };
+  for (int l = 0; l < top; ++l) {
+    const PLevel<T>& L = P.lv[l];
+    const size_t nE = L.g.nE, ned = L.g.nedge, nC = nE / 4, sz = sizeof(T);
+    share(L.A, na * nE * sz);
+    share(L.Dinv, (NS ? 4 : 3) * ned * sz);
+    if (l + 1 < P.nlev) {
+      share(L.AIIinv, na * nC * sz);
+      share(L.Y, 128 * nC * sz);
+      share(L.Pi, 64 * nC * sz);
+      if (NS) share(L.Rt, 64 * nC * sz);
+    }
+  }
+}
+
 __device__ __forceinline__ bool pc_mbar_test(unsigned long long* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -1370,6 +1406,10 @@ __global__ void __launch_bounds__(NTHR, 1) pcycle_kernel(const __grid_constant__
   }
   __syncthreads();
   if (!s_ok) return;
+  if (threadIdx.x == 0 && P.nrhs == 1) {
+    const int last = P.nlev - 1;
+    pc_prefetch_grid_levels<T, NS>(P, P.tail < last ? P.tail : last);
+  }
   pc_stamp<T>(P, st, kPcStart);
   pc_body<T, NS, NTHR>(P, sP, pc_smem, &s_mbar, st, &s_ok, &s_tail);
   pc_stamp<T>(P, st, kPcEnd);
