@@ -341,8 +341,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 CONDENSE_TRAFFIC_BYTES = 576512 + 54012416
 # DRAM traffic of one PCG iteration at 256^2, p = 4, mixed form: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels of one
-# iteration (host-driven loop, warm L2); None until captured for these kernels.
-PCG_ITER_TRAFFIC_BYTES = None
+# iteration (host-driven loop, warm L2, average of 56 iterations of the
+# 256 x 256, p = 4 step): persistent cycle 51.2 MB, fused FP64 matvec 131.9,
+# two FP32 finest matvecs 121.2, update 15.8, the two block-Jacobi steps
+# 19.6 + 7.9.  Below the algorithmic bytes because the persistent cycle's
+# steps re-read their level operators from L2.
+PCG_ITER_TRAFFIC_BYTES = 347.69e6
 
 
 def condense_flops(p, nE):
